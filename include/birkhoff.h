@@ -1,0 +1,245 @@
+/*
+ * birkhoff.h -- C ABI of the GB300 Birkhoff trajectory-optimisation hot path.
+ *
+ * Method: arXiv 2509.01855, "A Million-Point Fast Trajectory Optimization Solver".
+ * The library computes, on one GPU, the matrix-free Birkhoff products B v and B^T v on a
+ * Chebyshev-Gauss-Lobatto (CGL) grid, the KKT operator of a Newton step built from them, the
+ * Birkhoff preconditioner, a right-preconditioned Krylov solve and the Newton driver.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Grid: N is a power of two, 4 <= N <= 2^24; the L = N + 1 CGL nodes are
+ *    tau_j = -cos(j pi / N), ascending (Eq. CGLpts), mapped to t_j = t0 + s (tau_j + 1),
+ *    s = (tf - t0) / 2.
+ *  - Vectors are device pointers owned by the caller, one length-L block per component,
+ *    blocks `pitch` elements apart (pitch >= L; the library's own default pitch is L rounded up
+ *    to a multiple of 32). Elements L..pitch-1 of every block are ignored on input; outputs
+ *    written by the library set them to zero. Pointers must be 16-byte aligned.
+ *  - dtype: BK_F64 = IEEE binary64 arithmetic and storage, BK_F32 = binary32.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Every call
+ *    is asynchronous on that stream unless stated otherwise; nothing synchronises the device
+ *    except where a call says so.
+ *  - Errors: every call returns a bk_status; BK_OK = 0 on success. On error nothing is written
+ *    to outputs that the caller can rely on, and bk_last_error() returns a thread-local
+ *    message. Calls never exit the process. A CUDA error from a launch is returned as
+ *    BK_ERR_CUDA.
+ *  - Ownership: plans and problems are created and freed by the library (they own their
+ *    device tables and scratch); all vectors and workspaces are the caller's.
+ */
+#ifndef BIRKHOFF_GB300_H
+#define BIRKHOFF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bk_plan bk_plan;
+typedef struct bk_problem bk_problem;
+
+typedef enum { BK_F64 = 0, BK_F32 = 1 } bk_dtype;
+
+typedef enum {
+  BK_OK = 0,
+  BK_ERR_ARG = 1,            /* invalid argument (size, pointer, alignment, enum)          */
+  BK_ERR_CUDA = 2,           /* a CUDA runtime call or kernel launch failed                */
+  BK_ERR_OOM = 3,            /* device allocation failed                                    */
+  BK_ERR_NOT_CONVERGED = 4,  /* iteration cap reached before the tolerance                  */
+  BK_ERR_TIMEOUT = 5,        /* a bounded device wait gave up                               */
+  BK_ERR_INFEASIBLE = 6,     /* the line search could not reduce the residual               */
+  BK_ERR_UNSUPPORTED = 7     /* valid request the library does not implement               */
+} bk_status;
+
+/* Thread-local text of the last error (never NULL). */
+const char* bk_last_error(void);
+
+/* Library version string. */
+const char* bk_version(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Plan: grid tables (nodes, Clenshaw-Curtis weights, DCT twiddles) and transform scratch.
+ * ------------------------------------------------------------------------------------------ */
+
+/* Create a plan for Birkhoff products on the CGL grid of size N over [t0, tf].
+ *   N          power of two, 4 <= N <= 2^24
+ *   n_comp     components per batch item (>= 1)
+ *   max_batch  largest `batch` later passed to birkhoff_apply / birkhoff_apply_T (>= 1); the
+ *              plan's scratch is sized for max_batch * n_comp vectors
+ *   dtype      arithmetic and storage type
+ *   t0, tf     time interval, tf != t0 (s = (tf - t0) / 2 scales B)
+ *   pitch      distance in elements between component blocks; 0 = default (L rounded up to
+ *              32); otherwise pitch >= N + 1 and pitch * sizeof(dtype) a multiple of 16
+ *   stream     stream for the table-building kernels; the call synchronises it before return
+ * The grid tables are computed on the device (nodes and weights in FP64, copied to FP32 for a
+ * BK_F32 plan). Section "Fast Computation of Birkhoff Matrix-Vector Products". */
+bk_status bk_plan_create(bk_plan** plan, int64_t N, int n_comp, int max_batch, bk_dtype dtype,
+                         double t0, double tf, int64_t pitch, void* stream);
+
+/* Free a plan (NULL is allowed). The caller must make sure no work using it is in flight. */
+void bk_plan_destroy(bk_plan* plan);
+
+/* Grid facts of a plan: N, L, pitch, dtype. Any output pointer may be NULL. */
+bk_status bk_plan_info(const bk_plan* plan, int64_t* N, int64_t* L, int64_t* pitch,
+                       int* dtype);
+
+/* Copy the L node times t_j (FP64) and the L Clenshaw-Curtis weights w_j (FP64, tau-domain,
+ * sum 2; last row of B^a per the remark after Eq. Ba=10) to HOST arrays; either may be NULL.
+ * Synchronous. */
+bk_status bk_plan_grid(const bk_plan* plan, double* t_host, double* w_host);
+
+/* out = B v for `batch * n_comp` vectors, B = s * B^a (Eq. manyDefs; FastBV).
+ *   v, out  device arrays [batch][n_comp][pitch] of the plan's dtype; v == out is allowed
+ *   batch   1 <= batch <= max_batch
+ * Row 0 of the result is 0 and (B 1)_j = t_j - t0. Computed as a DCT-I to Chebyshev
+ * coefficients (Fastv2a, Appendix B), the coefficient-integration stencil with the aliasing
+ * fold (Eqs. c_k=bydef, chatk=) and a DCT-I back to nodal values (Fasta2v); the constant
+ * coefficient c_0 is obtained by making the value at tau = -1 vanish, which is what its
+ * closed form in Eq. c_k=bydef does. */
+bk_status birkhoff_apply(const bk_plan* plan, const void* v, void* out, int batch, void* stream);
+
+/* out = B^T v, the exact transpose of birkhoff_apply (the paper has no transpose product; the
+ * KKT operator needs one). Same arguments and layout as birkhoff_apply. */
+bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int batch,
+                           void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Problems: dynamics x' = f(x, u) of Eq. probPbold, discretised by Eq. Prob-PNa.
+ * ------------------------------------------------------------------------------------------ */
+
+typedef enum {
+  BK_DBL_INT = 0,   /* x = (p, v), x' = (v, u); x(t0) = (0,0); x(tf) = (1,0); F = u^2/2        */
+  BK_ORBIT = 1,     /* x = (r, theta, v_r, v_theta), u = (u_r, u_theta) thrust acceleration:
+                       r' = v_r, theta' = v_theta/r, v_r' = v_theta^2/r - 1/r^2 + u_r,
+                       v_theta' = -v_r v_theta/r + u_theta (dynamics of Eq. ot);
+                       x(t0) = (1,0,0,1); r(tf) = r_f, v_r(tf) = 0, v_theta(tf) = r_f^-1/2;
+                       F = |u|^2/2.  params = {a_nominal, r_f}                              */
+  BK_BILINEAR = 2   /* scalar x' = u x, no cost, no terminal condition; linearised at (X, U)
+                       its state Jacobian is diag(U): the Newton system [I - B diag(d)] dX =
+                       x^a b of Eq. Newton-ivp with d = U. params = {x^a} (default 1)          */
+} bk_kind;
+
+/* Operators addressed by kkt_apply / precond_apply / krylov_solve. */
+typedef enum {
+  BK_OP_STATE = 0,  /* state block G_x = I - s (B (x) I) J_x (FastAX; Eq. Achibetadef);
+                       vectors have n_x component blocks                                   */
+  BK_OP_KKT = 1     /* full KKT matrix of the Newton-Lagrange step; vectors are KKT vectors  */
+} bk_op;
+
+/* Create a problem of `kind` on the CGL grid of size N over [t0, tf], working dtype `dtype`.
+ * The problem owns FP64 plans and linearisation data and, for BK_F32, FP32 copies used by the
+ * Krylov iterations. Synchronises `stream`. */
+bk_status bk_problem_create(bk_problem** prob, int kind, const double* params, int nparams,
+                            int64_t N, bk_dtype dtype, double t0, double tf, void* stream);
+void bk_problem_destroy(bk_problem* prob);
+
+/* Sizes of a problem (any pointer may be NULL):
+ *   n_x, n_u, n_e  state, control and terminal-condition counts
+ *   pitch          component block pitch in elements
+ *   kkt_len        elements of a KKT vector: (2 n_x + n_u) * pitch + 32, laid out as
+ *                  [X_0..X_{n_x-1} | U_0..U_{n_u-1} | lambda_0..lambda_{n_x-1} | nu (n_e, padded
+ *                  to 32)]; each block pitch elements
+ *   state_len      elements of a state vector: n_x * pitch                                   */
+bk_status bk_problem_info(const bk_problem* prob, int* n_x, int* n_u, int* n_e, int64_t* pitch,
+                          int64_t* kkt_len, int64_t* state_len);
+
+/* Linearise the problem at z_lin (a KKT vector in FP64, device): stores per-node Jacobians,
+ * mu = B^T lambda for the Lagrangian Hessian, and the preconditioner's per-node factors and
+ * terminal Schur complement. kkt_apply / precond_apply / krylov_solve use the last
+ * linearisation. Section "Construction of a Low-Memory Fast Million-Point Linear Solver". */
+bk_status bk_linearize(bk_problem* prob, const double* z_lin, void* stream);
+
+/* out = Op * in at the current linearisation, in the problem's working dtype.
+ *   BK_OP_STATE: out = chi - s (B (x) I)(J_x chi)            (FastAX)
+ *   BK_OP_KKT:   out = [H dz + G^T dy ; G dz] with G the Jacobian of (c, e) and H the
+ *                Hessian of the Lagrangian (Newton-Lagrange step).
+ * in and out must not alias. */
+bk_status kkt_apply(bk_problem* prob, int op, const void* in, void* out, void* stream);
+
+/* out = P^{-1} in (transpose = 0) or P^{-T} in (transpose = 1) at the current linearisation.
+ *   BK_OP_STATE: P = I - s (B-tilde (x) I) J_x, B-tilde the lower-triangular Birkhoff-like
+ *                matrix; computed by the forward sweep that FastPinvY intends (the printed
+ *                recurrence does not invert P; the sweep used follows from the rows of P) and
+ *                its backward transpose.
+ *   BK_OP_KKT:   out = K-tilde^{-1} in, K-tilde the KKT matrix with B -> B-tilde in the
+ *                constraint Jacobian and the Hessian reduced to its control-cost part
+ *                (transpose is ignored: K-tilde is symmetric).
+ * in and out must not alias. Section "Development of a Special Birkhoff-Centric
+ * Preconditioner". */
+bk_status precond_apply(bk_problem* prob, int op, const void* in, void* out, int transpose,
+                        void* stream);
+
+typedef struct {
+  double rtol;        /* stop when ||b - A x||_2 <= rtol * ||b||_2 (default 1e-10)           */
+  int restart;        /* GMRES restart length m (default 30, at most 100)                   */
+  int max_iter;       /* total iteration cap (default 300)                                  */
+  int use_precond;    /* 1 = right preconditioning by P^{-1} / K-tilde^{-1} (default 1)      */
+} bk_krylov_opts;
+
+typedef struct {
+  int iterations;     /* Krylov iterations performed                                       */
+  int restarts;       /* restart cycles                                                     */
+  double rel_resid;   /* final ||b - A x|| / ||b|| (recomputed explicitly at exit)          */
+  int converged;      /* 1 if rel_resid <= rtol                                             */
+} bk_krylov_info;
+
+/* Workspace bytes krylov_solve needs for operator `op` with restart m. */
+size_t bk_krylov_workspace_bytes(const bk_problem* prob, int op, int restart);
+
+/* Solve Op x = rhs by right-preconditioned GMRES(m) (Algorithm 2 / FastLinSol: GMRES on
+ * A P^{-1} Upsilon = beta, then x = P^{-1} Upsilon), x0 = 0, in the working dtype.
+ *   rhs, sol   device vectors of the operator's length (working dtype)
+ *   opts       NULL = defaults
+ *   info       host struct, valid on return (the call synchronises `stream`)
+ *   workspace  device buffer of bk_krylov_workspace_bytes(prob, op, m) bytes, 256-aligned
+ * Returns BK_ERR_NOT_CONVERGED (with sol holding the last iterate) if max_iter is reached. */
+bk_status krylov_solve(bk_problem* prob, int op, const void* rhs, void* sol,
+                       const bk_krylov_opts* opts, bk_krylov_info* info, void* workspace,
+                       void* stream);
+
+typedef struct {
+  double tol;         /* stop when the weighted KKT residual norm <= tol (default 1e-10)     */
+  int max_iter;       /* Newton iteration cap (default 30)                                  */
+  double krylov_rtol; /* inner relative tolerance (default 1e-10 in FP64, 1e-5 in FP32)     */
+  int restart;        /* GMRES restart (default 30)                                         */
+  int max_krylov;     /* inner iteration cap per solve (default 300)                        */
+  double ir_rtol;     /* FP32 mode: FP64 iterative refinement until the FP64 residual of the
+                         Newton system is <= ir_rtol * ||F|| (default 1e-10)                 */
+  int max_refine;     /* FP32 mode: refinement sweeps cap (default 10)                      */
+} bk_newton_opts;
+
+typedef struct {
+  int iterations;          /* Newton steps taken                                            */
+  int krylov_iterations;   /* total inner Krylov iterations                                 */
+  int kkt_solves;          /* inner Krylov solves (one per refinement sweep in FP32 mode)   */
+  int backtracks;          /* line-search halvings                                          */
+  double residual;         /* final weighted KKT residual norm                              */
+  double residual0;        /* initial weighted KKT residual norm                            */
+  int converged;
+} bk_newton_info;
+
+/* Workspace bytes newton_solve needs. */
+size_t bk_newton_workspace_bytes(const bk_problem* prob, int restart);
+
+/* Newton-Lagrange solve of the discretised problem (Eq. Prob-PNa with V = f(X, U) eliminated):
+ * F(z, y) = [grad J + G^T y ; c ; e] = 0 with c = X - x0 - s (B (x) I) f(X, U), e the terminal
+ * conditions and J = s sum_i w_i F(x_i, u_i). Each step solves the KKT system by
+ * preconditioned GMRES (BK_F32: FP32 GMRES inside FP64 iterative refinement), then a
+ * backtracking line search (alpha = 1, 1/2, ...; Armijo 1e-4) on the weighted norm
+ *   ||F||_W^2 = sum_i w_i |c_i|^2 + sum_i |g_i|^2 / w_i + |e|^2  (g: gradient rows).
+ *   z_inout    device FP64 KKT vector: initial guess in, solution out (X, U, lambda, nu)
+ *   info       host struct, valid on return (synchronous)
+ * Returns BK_ERR_NOT_CONVERGED / BK_ERR_INFEASIBLE with z_inout holding the last iterate. */
+bk_status newton_solve(bk_problem* prob, double* z_inout, const bk_newton_opts* opts,
+                       bk_newton_info* info, void* workspace, void* stream);
+
+/* KKT residual F at z (FP64 device KKT vector) into F_out (same layout); if wnorm is not NULL
+ * the weighted norm ||F||_W is returned in it (host; synchronous in that case). */
+bk_status bk_kkt_residual(bk_problem* prob, const double* z, double* F_out, double* wnorm,
+                          void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIRKHOFF_GB300_H */

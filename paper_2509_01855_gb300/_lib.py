@@ -1,0 +1,124 @@
+"""ctypes binding of libbirkhoff.so: argument marshalling only.
+
+Every operation runs in the CUDA library; this module turns torch tensors into device pointers
+and sizes and checks the returned status. If the shared library is missing the import fails
+with an error: there is no fallback path.
+"""
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbirkhoff.so")
+
+BK_F64, BK_F32 = 0, 1
+BK_DBL_INT, BK_ORBIT, BK_BILINEAR = 0, 1, 2
+BK_OP_STATE, BK_OP_KKT = 0, 1
+STATUS = {0: "BK_OK", 1: "BK_ERR_ARG", 2: "BK_ERR_CUDA", 3: "BK_ERR_OOM",
+          4: "BK_ERR_NOT_CONVERGED", 5: "BK_ERR_TIMEOUT", 6: "BK_ERR_INFEASIBLE",
+          7: "BK_ERR_UNSUPPORTED"}
+
+# Symbols declared in include/birkhoff.h (checked by the CPU test suite).
+EXPORTS = ["bk_last_error", "bk_version", "bk_plan_create", "bk_plan_destroy", "bk_plan_info",
+           "bk_plan_grid", "birkhoff_apply", "birkhoff_apply_T", "bk_problem_create",
+           "bk_problem_destroy", "bk_problem_info", "bk_linearize", "kkt_apply",
+           "precond_apply", "bk_krylov_workspace_bytes", "krylov_solve",
+           "bk_newton_workspace_bytes", "newton_solve", "bk_kkt_residual"]
+
+
+class BirkhoffError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class KrylovOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("use_precond", ctypes.c_int)]
+
+
+class KrylovInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("rel_resid", ctypes.c_double), ("converged", ctypes.c_int)]
+
+
+class NewtonOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("krylov_rtol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("max_krylov", ctypes.c_int), ("ir_rtol", ctypes.c_double),
+                ("max_refine", ctypes.c_int)]
+
+
+class NewtonInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("krylov_iterations", ctypes.c_int),
+                ("kkt_solves", ctypes.c_int), ("backtracks", ctypes.c_int),
+                ("residual", ctypes.c_double), ("residual0", ctypes.c_double),
+                ("converged", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libbirkhoff.so once; raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libbirkhoff.so not built (run paper_2509_01855_gb300.build.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, c_int, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "bk_last_error": (ctypes.c_char_p, []),
+        "bk_version": (ctypes.c_char_p, []),
+        "bk_plan_create": (c_int, [ctypes.POINTER(vp), i64, c_int, c_int, c_int, dbl, dbl, i64, vp]),
+        "bk_plan_destroy": (None, [vp]),
+        "bk_plan_info": (c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                 ctypes.POINTER(c_int)]),
+        "bk_plan_grid": (c_int, [vp, vp, vp]),
+        "birkhoff_apply": (c_int, [vp, vp, vp, c_int, vp]),
+        "birkhoff_apply_T": (c_int, [vp, vp, vp, c_int, vp]),
+        "bk_problem_create": (c_int, [ctypes.POINTER(vp), c_int, ctypes.POINTER(dbl), c_int, i64,
+                                      c_int, dbl, dbl, vp]),
+        "bk_problem_destroy": (None, [vp]),
+        "bk_problem_info": (c_int, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                    ctypes.POINTER(c_int), ctypes.POINTER(i64),
+                                    ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "bk_linearize": (c_int, [vp, vp, vp]),
+        "kkt_apply": (c_int, [vp, c_int, vp, vp, vp]),
+        "precond_apply": (c_int, [vp, c_int, vp, vp, c_int, vp]),
+        "bk_krylov_workspace_bytes": (ctypes.c_size_t, [vp, c_int, c_int]),
+        "krylov_solve": (c_int, [vp, c_int, vp, vp, ctypes.POINTER(KrylovOpts),
+                                 ctypes.POINTER(KrylovInfo), vp, vp]),
+        "bk_newton_workspace_bytes": (ctypes.c_size_t, [vp, c_int]),
+        "newton_solve": (c_int, [vp, vp, ctypes.POINTER(NewtonOpts), ctypes.POINTER(NewtonInfo),
+                                 vp, vp]),
+        "bk_kkt_residual": (c_int, [vp, vp, vp, ctypes.POINTER(dbl), vp]),
+    }
+    for name, (res, args) in sig.items():
+        if hasattr(L, name):
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(status):
+    if status != 0:
+        raise BirkhoffError(status, lib().bk_last_error().decode())
+    return status
+
+
+def ptr(t):
+    """Device (or host) address of a tensor, or None."""
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)

@@ -1,0 +1,224 @@
+"""Python binding of the C ABI (include/birkhoff.h), with the same call names.
+
+Tensors are torch CUDA tensors; the binding passes their data pointers, sizes and the current
+(or given) CUDA stream to libbirkhoff.so and raises BirkhoffError on a non-zero status.
+"""
+import ctypes
+
+import torch
+
+from . import _lib as L
+
+_TORCH_DTYPE = {L.BK_F64: torch.float64, L.BK_F32: torch.float32}
+
+
+def _dtype_code(dtype):
+    if dtype in (torch.float64, "f64", L.BK_F64):
+        return L.BK_F64
+    if dtype in (torch.float32, "f32", L.BK_F32):
+        return L.BK_F32
+    raise ValueError("dtype must be float64 or float32")
+
+
+class Plan:
+    """A bk_plan: grid tables and scratch for Birkhoff products of size N."""
+
+    def __init__(self, N, n_comp=1, max_batch=1, dtype=torch.float64, t0=-1.0, tf=1.0,
+                 pitch=0, stream=None):
+        lib = L.lib()
+        self._h = ctypes.c_void_p()
+        self.dtype_code = _dtype_code(dtype)
+        L.check(lib.bk_plan_create(ctypes.byref(self._h), int(N), int(n_comp), int(max_batch),
+                                   self.dtype_code, float(t0), float(tf), int(pitch),
+                                   L.stream_ptr(stream)))
+        n, l, p, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        L.check(lib.bk_plan_info(self._h, ctypes.byref(n), ctypes.byref(l), ctypes.byref(p),
+                                 ctypes.byref(d)))
+        self.N, self.L, self.pitch = n.value, l.value, p.value
+        self.n_comp, self.max_batch = int(n_comp), int(max_batch)
+        self.t0, self.tf = float(t0), float(tf)
+        self.dtype = _TORCH_DTYPE[self.dtype_code]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def grid(self):
+        """(t, w): node times and Clenshaw-Curtis weights as host float64 tensors."""
+        t = torch.empty(self.L, dtype=torch.float64)
+        w = torch.empty(self.L, dtype=torch.float64)
+        L.check(L.lib().bk_plan_grid(self._h, L.ptr(t), L.ptr(w)))
+        return t, w
+
+    def empty(self, batch=1, device="cuda"):
+        """A zeroed [batch, n_comp, pitch] tensor of the plan's dtype."""
+        return torch.zeros(batch, self.n_comp, self.pitch, dtype=self.dtype, device=device)
+
+    def close(self):
+        if self._h:
+            L.lib().bk_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check_vec(plan, t, batch):
+    if not t.is_cuda or t.dtype != plan.dtype:
+        raise ValueError("expected a CUDA tensor of dtype %s" % plan.dtype)
+    if not t.is_contiguous() or t.numel() < batch * plan.n_comp * plan.pitch:
+        raise ValueError("vector must be contiguous with batch * n_comp * pitch elements")
+
+
+def birkhoff_apply(plan, v, out, batch=None, stream=None):
+    """out = B v (FastBV) for [batch, n_comp, pitch] tensors."""
+    batch = v.shape[0] if (batch is None and v.dim() == 3) else (batch or 1)
+    _check_vec(plan, v, batch)
+    _check_vec(plan, out, batch)
+    L.check(L.lib().birkhoff_apply(plan.handle, L.ptr(v), L.ptr(out), int(batch),
+                                   L.stream_ptr(stream)))
+    return out
+
+
+def birkhoff_apply_T(plan, v, out, batch=None, stream=None):
+    """out = B^T v for [batch, n_comp, pitch] tensors."""
+    batch = v.shape[0] if (batch is None and v.dim() == 3) else (batch or 1)
+    _check_vec(plan, v, batch)
+    _check_vec(plan, out, batch)
+    L.check(L.lib().birkhoff_apply_T(plan.handle, L.ptr(v), L.ptr(out), int(batch),
+                                     L.stream_ptr(stream)))
+    return out
+
+
+class Problem:
+    """A bk_problem: dynamics kind, grid and linearisation state."""
+
+    def __init__(self, kind, N, dtype=torch.float64, t0=0.0, tf=1.0, params=(), stream=None):
+        lib = L.lib()
+        self._h = ctypes.c_void_p()
+        self.dtype_code = _dtype_code(dtype)
+        self.dtype = _TORCH_DTYPE[self.dtype_code]
+        arr = (ctypes.c_double * max(1, len(params)))(*[float(x) for x in params])
+        L.check(lib.bk_problem_create(ctypes.byref(self._h), int(kind), arr, len(params), int(N),
+                                      self.dtype_code, float(t0), float(tf),
+                                      L.stream_ptr(stream)))
+        nx, nu, ne = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        pitch, klen, slen = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        L.check(lib.bk_problem_info(self._h, ctypes.byref(nx), ctypes.byref(nu), ctypes.byref(ne),
+                                    ctypes.byref(pitch), ctypes.byref(klen), ctypes.byref(slen)))
+        self.kind, self.N, self.L = int(kind), int(N), int(N) + 1
+        self.t0, self.tf, self.params = float(t0), float(tf), tuple(params)
+        self.n_x, self.n_u, self.n_e = nx.value, nu.value, ne.value
+        self.pitch, self.kkt_len, self.state_len = pitch.value, klen.value, slen.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def vec_len(self, op):
+        return self.kkt_len if op == L.BK_OP_KKT else self.state_len
+
+    def zeros(self, op=L.BK_OP_KKT, dtype=None, device="cuda"):
+        return torch.zeros(self.vec_len(op), dtype=dtype or self.dtype, device=device)
+
+    def linearize(self, z_lin, stream=None):
+        if z_lin.dtype != torch.float64 or not z_lin.is_cuda or z_lin.numel() < self.kkt_len:
+            raise ValueError("z_lin must be a CUDA float64 KKT vector")
+        L.check(L.lib().bk_linearize(self._h, L.ptr(z_lin), L.stream_ptr(stream)))
+
+    def residual(self, z, F_out, stream=None):
+        """KKT residual at z into F_out; returns the weighted norm (synchronous)."""
+        wn = ctypes.c_double()
+        L.check(L.lib().bk_kkt_residual(self._h, L.ptr(z), L.ptr(F_out), ctypes.byref(wn),
+                                        L.stream_ptr(stream)))
+        return wn.value
+
+    # layout helpers (views into a KKT vector) -------------------------------------------
+    def split(self, z):
+        P = self.pitch
+        nx, nu = self.n_x, self.n_u
+        X = z[:nx * P].view(nx, P)[:, :self.L]
+        U = z[nx * P:(nx + nu) * P].view(nu, P)[:, :self.L]
+        lam = z[(nx + nu) * P:(2 * nx + nu) * P].view(nx, P)[:, :self.L]
+        nu_ = z[(2 * nx + nu) * P:(2 * nx + nu) * P + self.n_e]
+        return X, U, lam, nu_
+
+    def pack(self, X, U, lam=None, nu=None, dtype=torch.float64, device="cuda"):
+        z = torch.zeros(self.kkt_len, dtype=dtype, device=device)
+        Xv, Uv, lv, nv = self.split(z)
+        Xv.copy_(torch.as_tensor(X))
+        Uv.copy_(torch.as_tensor(U))
+        if lam is not None:
+            lv.copy_(torch.as_tensor(lam))
+        if nu is not None and self.n_e:
+            nv.copy_(torch.as_tensor(nu))
+        return z
+
+    def close(self):
+        if self._h:
+            L.lib().bk_problem_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kkt_apply(prob, op, x, out, stream=None):
+    L.check(L.lib().kkt_apply(prob.handle, int(op), L.ptr(x), L.ptr(out), L.stream_ptr(stream)))
+    return out
+
+
+def precond_apply(prob, op, x, out, transpose=False, stream=None):
+    L.check(L.lib().precond_apply(prob.handle, int(op), L.ptr(x), L.ptr(out), int(bool(transpose)),
+                                  L.stream_ptr(stream)))
+    return out
+
+
+def krylov_workspace(prob, op, restart=30):
+    nbytes = L.lib().bk_krylov_workspace_bytes(prob.handle, int(op), int(restart))
+    return torch.empty(max(1, (nbytes + 255) // 256 * 32), dtype=torch.float64, device="cuda")
+
+
+def krylov_solve(prob, op, rhs, sol, rtol=1e-10, restart=30, max_iter=300, use_precond=True,
+                 workspace=None, stream=None, raise_on_fail=True):
+    """Right-preconditioned GMRES(m); returns a dict of the bk_krylov_info fields."""
+    if workspace is None:
+        workspace = krylov_workspace(prob, op, restart)
+    opts = L.KrylovOpts(float(rtol), int(restart), int(max_iter), int(bool(use_precond)))
+    info = L.KrylovInfo()
+    st = L.lib().krylov_solve(prob.handle, int(op), L.ptr(rhs), L.ptr(sol), ctypes.byref(opts),
+                              ctypes.byref(info), L.ptr(workspace), L.stream_ptr(stream))
+    out = dict(iterations=info.iterations, restarts=info.restarts, rel_resid=info.rel_resid,
+               converged=bool(info.converged), status=st)
+    if raise_on_fail and st != 0:
+        L.check(st)
+    return out
+
+
+def newton_workspace(prob, restart=30):
+    nbytes = L.lib().bk_newton_workspace_bytes(prob.handle, int(restart))
+    return torch.empty(max(1, (nbytes + 255) // 256 * 32), dtype=torch.float64, device="cuda")
+
+
+def newton_solve(prob, z, tol=1e-10, max_iter=30, krylov_rtol=0.0, restart=30, max_krylov=300,
+                 ir_rtol=1e-10, max_refine=10, workspace=None, stream=None, raise_on_fail=True):
+    """Newton-Lagrange solve in place on the FP64 KKT vector z; returns the info fields."""
+    if workspace is None:
+        workspace = newton_workspace(prob, restart)
+    opts = L.NewtonOpts(float(tol), int(max_iter), float(krylov_rtol), int(restart),
+                        int(max_krylov), float(ir_rtol), int(max_refine))
+    info = L.NewtonInfo()
+    st = L.lib().newton_solve(prob.handle, L.ptr(z), ctypes.byref(opts), ctypes.byref(info),
+                              L.ptr(workspace), L.stream_ptr(stream))
+    out = dict(iterations=info.iterations, krylov_iterations=info.krylov_iterations,
+               kkt_solves=info.kkt_solves, backtracks=info.backtracks, residual=info.residual,
+               residual0=info.residual0, converged=bool(info.converged), status=st)
+    if raise_on_fail and st != 0:
+        L.check(st)
+    return out

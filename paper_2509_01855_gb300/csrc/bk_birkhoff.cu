@@ -1,0 +1,723 @@
+// Birkhoff products B v and B^T v on the CGL grid (FastBV and its transpose).
+//
+// Paper: "Fast Computation of Birkhoff Matrix-Vector Products" (Eqs. vi=sumT .. chatk=,
+// algorithms Fasta2v / FastBV) and Appendix B (Fastv2a).
+//
+// Formulation used by the kernels. Let R be the unnormalised type-I DCT of length N+1,
+//   R(x)_k = x_0 + (-1)^k x_N + 2 sum_{m=1}^{N-1} x_m cos(pi k m / N),
+// which is twice the paper's DCT-I (Eq. vm=DCT-1). Write Y = R(v). The Chebyshev coefficients
+// of Fastv2a are a_k = (-1)^k h_k Y_k / N (h = 1/2 at k = 0, N), and the sign (-1)^k that the
+// reversal steps of Fastv2a / Fasta2v introduce cancels inside the integration stencil of
+// Eq. c_k=bydef, so with chat'_k = (-1)^k chat_k:
+//   chat'_1     = (Y_2 - Y_0) / (2N)
+//   chat'_k     = (Y_{k+1} - Y_{k-1}) / (2kN),                 2 <= k <= N-2
+//   chat'_{N-1} = (Y_N/2 - Y_{N-2}) / (2(N-1)N) - (Y_N/2) / (2(N+1)N)   (aliasing fold, Eq. chatk=)
+//   chat'_N     = -Y_{N-1} / (2N^2)
+// and the nodal values are y'_i = sum_k chat'_k cos(pi k i / N) = R(g)_i with g_0 = 0,
+// g_k = chat'_k / 2 (0 < k < N), g_N = chat'_N. The constant coefficient c_0 is not formed:
+// row 0 of B^a is zero (B^a_j(tau^a) = 0, Eq. birk-conditions), and c_0 multiplies T_0 = 1,
+// so B^a v = y' - y'_0. With the time scale s = (tf - t0)/2:  B v = s (y' - y'_0 1).
+// Transpose: B = s (I - 1 e_0^T) R G R / N with R = C W (C symmetric, W = diag(1,2,..,2,1)),
+// so B^T u = (s/N) W R W^{-1} G^T W R W^{-1} (I - e_0 1^T) u, and R W^{-1} (I - e_0 1^T) u =
+// R(W^{-1} u) - (sum u) 1 because column 0 of R is all ones and sum_m (W^{-1}u)_ext = sum u.
+//
+// The DCT-I is computed by a complex FFT of length N of z_j = x_ext[2j] + i x_ext[2j+1]
+// (x_ext the even 2N-periodic extension of x) and the standard real-FFT split:
+//   Y_k = P + Q,  Y_{N-k} = P - Q,  P = Re(Z_k + Z_{N-k}) / 2,
+//   Q = [cos(pi k/N) Im(Z_k + Z_{N-k}) - sin(pi k/N) Re(Z_k - Z_{N-k})] / 2.
+// N <= NSMALL: one CTA per vector does the whole chain in shared memory (one HBM read and one
+// write). Larger N: four-step FFT (N = N1 N2) in two passes per DCT, the integration stencil
+// fused into the load of the second DCT, and the node-0 value gathered from per-CTA partials.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "bk_common.cuh"
+#include "bk_fft.cuh"
+#include "bk_plan.cuh"
+
+namespace bk {
+
+static thread_local std::string g_last_error = "no error";
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+bk_status dmalloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return BK_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    *p = nullptr;
+    set_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? BK_ERR_OOM : BK_ERR_CUDA;
+  }
+  return BK_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Table construction (device, FP64 sincospi; FP32 tables are rounded copies)
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_tw_table(typename V2<T>::t* tw, int64_t n, double denom_half_turns) {
+  // tw[i] = (cos(2 pi i / n), -sin(2 pi i / n)) computed as sincospi(2 i / n)
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi((double)(2 * i) / denom_half_turns, &s, &c);
+    tw[i] = mk2<T>((T)c, (T)(-s));
+  }
+}
+
+template <typename T>
+__global__ void k_post_table(typename V2<T>::t* tp, int64_t N) {
+  // tp[k] = (cos(pi k / N), sin(pi k / N)), k = 0..N/2
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= N / 2;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi((double)k / (double)N, &s, &c);
+    tp[k] = mk2<T>((T)c, (T)s);
+  }
+}
+
+__global__ void k_grid_tables(double* t_nodes, int64_t N, double t0, double s) {
+  // tau_j = -cos(j pi / N) = sin(pi (2j - N) / (2N)) (Eq. CGLpts), t_j = t0 + s (tau_j + 1)
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double tau = sinpi((double)(2 * j - N) / (double)(2 * N));
+    if (j == 0) tau = -1.0;
+    if (j == N) tau = 1.0;
+    t_nodes[j] = t0 + s * (tau + 1.0);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Element accessors of the transform inputs
+// ---------------------------------------------------------------------------------------------
+// Kinds of the first-DCT input x:
+//   IN_PLAIN : x_m = v_m                  (forward product)
+//   IN_WINV  : x_m = v_m / W_m            (transpose product; W = 1 at the ends, 2 inside)
+// Kinds of the second-DCT input (from Y = output of the first DCT):
+//   ST_FWD   : x_m = g_m = G(Y)_m                          (forward stencil, includes 1/N)
+//   ST_TRN   : x_m = W_m^{-1} G^T(W (Y - Y_0))_m          (transposed stencil)
+enum { IN_PLAIN = 0, IN_WINV = 1, ST_FWD = 2, ST_TRN = 3 };
+
+template <typename T>
+__device__ __forceinline__ T stencil_fwd(const T* __restrict__ Y, int m, int N, T invN) {
+  // g_m = chat'_m / 2 for 0 < m < N, g_N = chat'_N, g_0 = 0 (see the file comment)
+  if (m == 0) return T(0);
+  if (m == N) return -Y[N - 1] * (invN / T(2 * N));
+  if (m == 1) return (Y[2] - Y[0]) * (invN * T(0.25));
+  if (m == N - 1) {
+    const T yN = Y[N];
+    return (T(0.5) * yN - Y[N - 2]) * (invN / T(4.0 * (N - 1))) - yN * (invN / T(8.0 * (N + 1)));
+  }
+  return (Y[m + 1] - Y[m - 1]) * (invN / T(4.0 * m));
+}
+
+template <typename T>
+__device__ __forceinline__ T stencil_trn(const T* __restrict__ Q, int m, int N, T Y0) {
+  // r = W (Y - Y0); t = G^T r; return t_m / W_m. G^T rows:
+  //   t_0 = -r_1/4, t_1 = -r_2/8, t_j = r_{j-1}/(4(j-1)) - r_{j+1}/(4(j+1)) (2<=j<=N-2),
+  //   t_{N-1} = r_{N-2}/(4(N-2)) - r_N/(2N), t_N = r_{N-1}/(4(N^2-1)).
+  // r_k = 2 (Y_k - Y0) for 0 < k < N, r_0 = Y_0 - Y0 = 0, r_N = Y_N - Y0.
+  if (m == 0) return -(T(2) * (Q[1] - Y0)) * T(0.25);
+  if (m == N) return (T(2) * (Q[N - 1] - Y0)) / T(4.0 * ((double)N * N - 1.0));
+  T t;
+  if (m == 1) {
+    t = -(T(2) * (Q[2] - Y0)) * T(0.125);
+  } else if (m == N - 1) {
+    t = (T(2) * (Q[N - 2] - Y0)) / T(4.0 * (N - 2)) - (Q[N] - Y0) / T(2.0 * N);
+  } else {
+    t = (T(2) * (Q[m - 1] - Y0)) / T(4.0 * (m - 1)) - (T(2) * (Q[m + 1] - Y0)) / T(4.0 * (m + 1));
+  }
+  return T(0.5) * t;
+}
+
+// Value x_m of the transform input of kind K. `src` is the vector (first DCT) or the stage
+// buffer Y (second DCT). Y0 is used by ST_TRN only.
+template <typename T, int K>
+__device__ __forceinline__ T load_x(const T* __restrict__ src, int m, int N, T invN, T Y0) {
+  if (K == IN_PLAIN) return src[m];
+  if (K == IN_WINV) return (m == 0 || m == N) ? src[m] : T(0.5) * src[m];
+  if (K == ST_FWD) return stencil_fwd<T>(src, m, N, invN);
+  return stencil_trn<T>(src, m, N, Y0);
+}
+
+// z_j = x_ext[2j] + i x_ext[2j+1]
+template <typename T, int K>
+__device__ __forceinline__ typename V2<T>::t load_z(const T* __restrict__ src, int j, int N, T invN,
+                                                    T Y0) {
+  const int m1 = 2 * j, m2 = 2 * j + 1;
+  const int i1 = m1 <= N ? m1 : 2 * N - m1;
+  const int i2 = m2 <= N ? m2 : 2 * N - m2;
+  return mk2<T>(load_x<T, K>(src, i1, N, invN, Y0), load_x<T, K>(src, i2, N, invN, Y0));
+}
+
+// Real-FFT split: from Z_k, Z_{N-k} and (cos, sin)(pi kk / N), kk = min(k, N - k).
+template <typename T>
+__device__ __forceinline__ void split_pair(typename V2<T>::t zk, typename V2<T>::t zc,
+                                           typename V2<T>::t cs, T& yk, T& ynk) {
+  const T P = T(0.5) * (zk.x + zc.x);
+  const T Q = T(0.5) * (cs.x * (zk.y + zc.y) - cs.y * (zk.x - zc.x));
+  yk = P + Q;
+  ynk = P - Q;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Single-CTA fused kernel: the whole chain for one vector in shared memory.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__device__ void dct1_block(const T* __restrict__ X, int kind, T* __restrict__ Y,
+                           typename V2<T>::t* bufA, typename V2<T>::t* bufB, int N, int log2N,
+                           const typename V2<T>::t* __restrict__ tw, int tw_log2,
+                           const typename V2<T>::t* __restrict__ tpost, T invN, T Y0) {
+  typedef typename V2<T>::t C;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    C z;
+    switch (kind) {
+      case IN_PLAIN: z = load_z<T, IN_PLAIN>(X, j, N, invN, Y0); break;
+      case IN_WINV: z = load_z<T, IN_WINV>(X, j, N, invN, Y0); break;
+      case ST_FWD: z = load_z<T, ST_FWD>(X, j, N, invN, Y0); break;
+      default: z = load_z<T, ST_TRN>(X, j, N, invN, Y0); break;
+    }
+    bufA[j] = z;
+  }
+  __syncthreads();
+  C* Z = fft_smem<T>(bufA, bufB, N, log2N, 1, N, tw, tw_log2);
+  for (int k = threadIdx.x; k <= N / 2; k += blockDim.x) {
+    const C zk = Z[k];
+    const C zc = Z[(N - k) & (N - 1)];
+    T yk, ynk;
+    split_pair<T>(zk, zc, tpost[k], yk, ynk);
+    Y[k] = yk;
+    if (k != N / 2) Y[N - k] = ynk;
+  }
+  __syncthreads();
+}
+
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256)
+    k_birkhoff_small(const T* __restrict__ in, T* __restrict__ out, int N, int log2N, int64_t pitch,
+                     T s, const typename V2<T>::t* __restrict__ tw, int tw_log2,
+                     const typename V2<T>::t* __restrict__ tpost) {
+  typedef typename V2<T>::t C;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int L = N + 1;
+  const int Lp = (L + 3) & ~3;
+  T* X = reinterpret_cast<T*>(smem);
+  T* Y = X + Lp;
+  C* bufA = reinterpret_cast<C*>(Y + Lp);
+  C* bufB = bufA + N;
+  const int64_t base = (int64_t)blockIdx.x * pitch;
+  const T* src = in + base;
+  T* dst = out + base;
+  const T invN = T(1) / T(N);
+  for (int m = threadIdx.x; m < L; m += blockDim.x) X[m] = src[m];
+  __syncthreads();
+  if (!TRANS) {
+    dct1_block<T>(X, IN_PLAIN, Y, bufA, bufB, N, log2N, tw, tw_log2, tpost, invN, T(0));
+    dct1_block<T>(Y, ST_FWD, X, bufA, bufB, N, log2N, tw, tw_log2, tpost, invN, T(0));
+    const T y0 = X[0];
+    for (int m = threadIdx.x; m < L; m += blockDim.x) dst[m] = s * (X[m] - y0);
+  } else {
+    dct1_block<T>(X, IN_WINV, Y, bufA, bufB, N, log2N, tw, tw_log2, tpost, invN, T(0));
+    const T y0 = Y[0];
+    dct1_block<T>(Y, ST_TRN, X, bufA, bufB, N, log2N, tw, tw_log2, tpost, invN, y0);
+    const T sN = s * invN;
+    for (int m = threadIdx.x; m < L; m += blockDim.x)
+      dst[m] = (m == 0 || m == N) ? sN * X[m] : T(2) * sN * X[m];
+  }
+  for (int m = L + threadIdx.x; m < pitch; m += blockDim.x) dst[m] = T(0);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Four-step passes for large N (N = N1 * N2, j = N2 j1 + j2, k = k1 + N1 k2).
+// Pass A: per CTA, NB columns j2; FFT over j1 (length N1), twiddle omega_N^{j2 k1}; writes
+//         A[k1][j2]. Also writes the CTA's partial sum of Re z + Im z (the DC value of the DCT).
+// Pass B: per CTA, P row pairs {p, N1 - p} (p = 0 pairs rows 0 and N1/2); FFT over j2 (length
+//         N2), real-FFT split, epilogue.
+// ---------------------------------------------------------------------------------------------
+template <typename T, int K>
+__global__ void __launch_bounds__(256)
+    k_passA(const T* __restrict__ src, int64_t src_stride, typename V2<T>::t* __restrict__ Aout,
+            T* __restrict__ partial, int N, int N1, int log2N1, int N2, int NB,
+            const typename V2<T>::t* __restrict__ tw, int tw_log2,
+            const typename V2<T>::t* __restrict__ twN, const T* __restrict__ y0_partial,
+            int n_y0_partial, T invN) {
+  typedef typename V2<T>::t C;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int bs = N1 + 1;  // padded batch stride
+  C* bufA = reinterpret_cast<C*>(smem);
+  C* bufB = bufA + (size_t)NB * bs;
+  __shared__ T red[32];
+  const int vec = blockIdx.y;
+  const T* x = src + (int64_t)vec * src_stride;
+  const int c0 = blockIdx.x * NB;
+  T Y0 = T(0);
+  if (K == ST_TRN) {
+    // Y0 = DC of the first DCT = sum of the pass-A partials of that DCT
+    T acc = T(0);
+    const T* pp = y0_partial + (int64_t)vec * n_y0_partial;
+    for (int i = threadIdx.x; i < n_y0_partial; i += blockDim.x) acc += pp[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      T a = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (threadIdx.x == 0) red[0] = a;
+    }
+    __syncthreads();
+    Y0 = red[0];
+    __syncthreads();
+  }
+  T dc = T(0);
+  const int total = NB * N1;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int b = idx % NB;
+    const int j1 = idx / NB;
+    const int j = N2 * j1 + c0 + b;
+    const C z = load_z<T, K>(x, j, N, invN, Y0);
+    dc += z.x + z.y;
+    bufA[b * bs + j1] = z;
+  }
+  // block reduction of dc (deterministic order)
+  for (int o = 16; o > 0; o >>= 1) dc += __shfl_xor_sync(0xffffffffu, dc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    T a = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (threadIdx.x == 0) partial[(int64_t)vec * gridDim.x + blockIdx.x] = a;
+  }
+  C* R = fft_smem<T>(bufA, bufB, N1, log2N1, NB, bs, tw, tw_log2);
+  C* A = Aout + (int64_t)vec * N;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int b = idx % NB;
+    const int k1 = idx / NB;
+    const int j2 = c0 + b;
+    const C w = __ldg(&twN[(int64_t)j2 * k1]);
+    A[(int64_t)k1 * N2 + j2] = cmul(R[b * bs + k1], w);
+  }
+}
+
+// Epilogue kinds of pass B:
+//   EP_STORE     : stage[k] = Y_k                          (after the first DCT, forward)
+//   EP_STORE_TRN : stage[k] = Y_k - Y0, Y0 from partials   (after the first DCT, transpose)
+//   EP_FWD_OUT   : out[k] = s (Y_k - Y0), Y0 from partials (after the second DCT, forward)
+//   EP_TRN_OUT   : out[k] = (s/N) W_k Y_k                   (after the second DCT, transpose)
+enum { EP_STORE = 0, EP_STORE_TRN = 1, EP_FWD_OUT = 2, EP_TRN_OUT = 3 };
+
+template <typename T, int E>
+__device__ __forceinline__ void ep_write(T* __restrict__ dst, int k, T yk, int N, T s, T Y0, T invN) {
+  if (E == EP_STORE) dst[k] = yk;
+  else if (E == EP_STORE_TRN) dst[k] = yk - Y0;
+  else if (E == EP_FWD_OUT) dst[k] = s * (yk - Y0);
+  else dst[k] = (k == 0 || k == N) ? s * invN * yk : T(2) * s * invN * yk;
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(256)
+    k_passB(const typename V2<T>::t* __restrict__ Ain, T* __restrict__ dst, int64_t dst_stride,
+            int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial, int N, int N1,
+            int N2, int log2N2, int P, const typename V2<T>::t* __restrict__ tw, int tw_log2,
+            const typename V2<T>::t* __restrict__ tpost, T s, T invN) {
+  typedef typename V2<T>::t C;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int bs = N2 + 1;
+  C* bufA = reinterpret_cast<C*>(smem);
+  C* bufB = bufA + (size_t)2 * P * bs;
+  __shared__ T red[32];
+  const int vec = blockIdx.y;
+  const C* A = Ain + (int64_t)vec * N;
+  T* out = dst + (int64_t)vec * dst_stride;
+  const int p0 = blockIdx.x * P;
+  T Y0 = T(0);
+  if (E == EP_STORE_TRN || E == EP_FWD_OUT) {
+    T acc = T(0);
+    const T* pp = partial + (int64_t)vec * n_partial;
+    for (int i = threadIdx.x; i < n_partial; i += blockDim.x) acc += pp[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      T a = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (threadIdx.x == 0) red[0] = a;
+    }
+    __syncthreads();
+    Y0 = red[0];
+  }
+  // load 2P rows: local row q = 2 i (+1) for pair p0 + i
+  const int total = 2 * P * N2;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int q = idx / N2;
+    const int j2 = idx - q * N2;
+    const int p = p0 + (q >> 1);
+    const int row = (q & 1) == 0 ? p : (p == 0 ? N1 / 2 : N1 - p);
+    bufA[q * bs + j2] = A[(int64_t)row * N2 + j2];
+  }
+  __syncthreads();
+  C* R = fft_smem<T>(bufA, bufB, N2, log2N2, 2 * P, bs, tw, tw_log2);
+  const int half = N / 2;
+  for (int idx = threadIdx.x; idx < P * N2; idx += blockDim.x) {
+    const int i = idx / N2;
+    const int k2 = idx - i * N2;
+    const int p = p0 + i;
+    const C* ra = R + (2 * i) * bs;
+    const C* rb = R + (2 * i + 1) * bs;
+    if (p == 0) {
+      // row 0 pairs internally (k2 <-> N2 - k2); row N1/2 pairs k2 <-> N2 - 1 - k2
+      if (k2 <= N2 / 2) {
+        const int k = N1 * k2;
+        T yk, ynk;
+        split_pair<T>(ra[k2], ra[(N2 - k2) & (N2 - 1)], tpost[k], yk, ynk);
+        ep_write<T, E>(out, k, yk, N, s, Y0, invN);
+        if (k != half) ep_write<T, E>(out, N - k, ynk, N, s, Y0, invN);
+      }
+      if (k2 < N2 / 2) {
+        const int k = N1 / 2 + N1 * k2;
+        T yk, ynk;
+        split_pair<T>(rb[k2], rb[N2 - 1 - k2], tpost[k], yk, ynk);
+        ep_write<T, E>(out, k, yk, N, s, Y0, invN);
+        ep_write<T, E>(out, N - k, ynk, N, s, Y0, invN);
+      }
+    } else {
+      const int k = p + N1 * k2;
+      const C zk = ra[k2];
+      const C zc = rb[N2 - 1 - k2];
+      T yk, ynk;
+      if (k <= half) {
+        split_pair<T>(zk, zc, tpost[k], yk, ynk);
+      } else {
+        split_pair<T>(zc, zk, tpost[N - k], ynk, yk);
+      }
+      ep_write<T, E>(out, k, yk, N, s, Y0, invN);
+      ep_write<T, E>(out, N - k, ynk, N, s, Y0, invN);
+    }
+  }
+  // zero the padding of the output vectors (final epilogues only)
+  if ((E == EP_FWD_OUT || E == EP_TRN_OUT) && blockIdx.x == 0) {
+    for (int64_t m = N + 1 + threadIdx.x; m < pitch_zero_to; m += blockDim.x) out[m] = T(0);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Plan creation / destruction and the apply entry points
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+static bk_status build_tables(Plan* p, cudaStream_t st) {
+  typedef typename V2<T>::t C;
+  const int64_t N = p->N;
+  // sub-FFT twiddle table: length n_tab = max FFT length run in shared memory
+  const int64_t ntab = p->small ? N : (int64_t)std::max(p->N1, p->N2);
+  p->tw_log2 = ilog2(ntab);
+  BK_TRY(dmalloc(&p->tw, sizeof(C) * ntab));
+  k_tw_table<T><<<(int)std::min<int64_t>((ntab + 255) / 256, 4096), 256, 0, st>>>(
+      (C*)p->tw, ntab, (double)ntab);
+  BK_CHECK_LAUNCH();
+  BK_TRY(dmalloc(&p->tpost, sizeof(C) * (N / 2 + 1)));
+  k_post_table<T><<<(int)std::min<int64_t>((N / 2 + 256) / 256, 4096), 256, 0, st>>>((C*)p->tpost, N);
+  BK_CHECK_LAUNCH();
+  if (!p->small) {
+    BK_TRY(dmalloc(&p->twN, sizeof(C) * N));
+    k_tw_table<T><<<(int)std::min<int64_t>((N + 255) / 256, 8192), 256, 0, st>>>((C*)p->twN, N,
+                                                                                  (double)N);
+    BK_CHECK_LAUNCH();
+  }
+  return BK_OK;
+}
+
+__global__ void k_unit_last(double* e, int64_t L, int64_t pitch) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < pitch; i += (int64_t)gridDim.x * blockDim.x)
+    e[i] = (i == L - 1) ? 1.0 : 0.0;
+}
+__global__ void k_d2f(const double* a, float* b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+// Clenshaw-Curtis weights as the last row of B^a: w = (B^a)^T e_N, computed in FP64 with the
+// transpose product itself (O(N log N)). A BK_F32 plan uses a temporary FP64 plan.
+static bk_status compute_weights(Plan* p, cudaStream_t st) {
+  const int64_t L = p->L;
+  Plan* q = p;
+  Plan* tmp = nullptr;
+  if (p->dtype != BK_F64) {
+    BK_TRY(plan_create(&tmp, p->N, 1, 1, BK_F64, 0.0, 2.0, 0, st));
+    q = tmp;
+  }
+  double* e = nullptr;
+  bk_status r = dmalloc((void**)&e, sizeof(double) * q->pitch);
+  if (r == BK_OK) r = dmalloc((void**)&p->w64, sizeof(double) * q->pitch);
+  if (r == BK_OK) {
+    k_unit_last<<<(int)((q->pitch + 255) / 256), 256, 0, st>>>(e, L, q->pitch);
+    r = plan_apply_n(q, e, p->w64, 1, true, 1.0, st);
+  }
+  if (r == BK_OK && p->dtype == BK_F32) {
+    r = dmalloc(&p->wT, sizeof(float) * L);
+    if (r == BK_OK) k_d2f<<<(int)((L + 255) / 256), 256, 0, st>>>(p->w64, (float*)p->wT, L);
+  }
+  if (r == BK_OK && cudaStreamSynchronize(st) != cudaSuccess) { set_error("weights: sync failed"); r = BK_ERR_CUDA; }
+  dfree(e);
+  if (tmp) plan_destroy(tmp);
+  return r;
+}
+
+static int small_limit(int dtype) { return dtype == BK_F64 ? 4096 : 8192; }
+
+template <typename T>
+static size_t smem_small(int64_t N) {
+  const int64_t L = N + 1;
+  const int64_t Lp = (L + 3) & ~3;
+  return sizeof(T) * 2 * Lp + 2 * sizeof(typename V2<T>::t) * N;
+}
+
+static bk_status configure_fourstep(Plan* p) {
+  const int log2N = ilog2(p->N);
+  p->N1 = 1 << (log2N / 2);
+  p->N2 = 1 << (log2N - log2N / 2);
+  const size_t csz = 2 * dtype_size(p->dtype);
+  const size_t budget = 192 * 1024;  // bytes for the two ping-pong buffers
+  // pass A: NB columns of N1 (padded), two buffers
+  int NB = (int)(budget / (2 * csz * (p->N1 + 1)));
+  if (NB > p->N2) NB = p->N2;
+  int nb = 1;
+  while (nb * 2 <= NB) nb *= 2;
+  p->NB = nb;
+  // pass B: P pairs = 2P rows of N2 (padded)
+  int rows = (int)(budget / (2 * csz * (p->N2 + 1)));
+  int P = rows / 2;
+  int pp = 1;
+  while (pp * 2 <= P) pp *= 2;
+  if (pp > p->N1 / 2) pp = p->N1 / 2;
+  p->P = pp;
+  if (p->NB < 1 || p->P < 1) {
+    set_error("four-step configuration failed for N=%lld", (long long)p->N);
+    return BK_ERR_UNSUPPORTED;
+  }
+  p->smemA = 2 * csz * (size_t)p->NB * (p->N1 + 1);
+  p->smemB = 2 * csz * (size_t)2 * p->P * (p->N2 + 1);
+  p->nPartA = p->N2 / p->NB;
+  return BK_OK;
+}
+
+template <typename T>
+static bk_status set_smem_attrs(const Plan* p) {
+  if (p->small) {
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_birkhoff_small<T, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemS));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_birkhoff_small<T, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemS));
+  } else {
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, IN_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemA));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, IN_WINV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemA));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, ST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemA));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, ST_TRN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemA));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemB));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_STORE_TRN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemB));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_FWD_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemB));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_TRN_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemB));
+  }
+  return BK_OK;
+}
+
+bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtype, double t0,
+                      double tf, int64_t pitch, cudaStream_t st) {
+  *out = nullptr;
+  BK_ARG(is_pow2(N) && N >= 4 && N <= (int64_t(1) << 24), "N must be a power of two in [4, 2^24], got %lld", (long long)N);
+  BK_ARG(n_comp >= 1 && n_comp <= 64, "n_comp must be in [1, 64], got %d", n_comp);
+  BK_ARG(max_batch >= 1, "max_batch must be >= 1, got %d", max_batch);
+  BK_ARG(dtype == BK_F64 || dtype == BK_F32, "dtype must be BK_F64 or BK_F32");
+  BK_ARG(tf != t0 && isfinite(t0) && isfinite(tf), "tf must differ from t0 and both be finite");
+  const int64_t L = N + 1;
+  if (pitch == 0) pitch = round_up(L, 32);
+  BK_ARG(pitch >= L, "pitch %lld < N + 1", (long long)pitch);
+  BK_ARG((pitch * (int64_t)dtype_size(dtype)) % 16 == 0, "pitch * sizeof(dtype) must be a multiple of 16");
+  Plan* p = new Plan();
+  p->N = N;
+  p->L = L;
+  p->n_comp = n_comp;
+  p->max_batch = max_batch;
+  p->dtype = dtype;
+  p->t0 = t0;
+  p->tf = tf;
+  p->s = 0.5 * (tf - t0);
+  p->pitch = pitch;
+  p->small = N <= small_limit(dtype);
+  bk_status st_ = BK_OK;
+  do {
+    if (p->small) {
+      p->smemS = dtype == BK_F64 ? smem_small<double>(N) : smem_small<float>(N);
+    } else {
+      if ((st_ = configure_fourstep(p)) != BK_OK) break;
+      const int64_t nvec = (int64_t)n_comp * max_batch;
+      const size_t csz = 2 * dtype_size(dtype);
+      if ((st_ = dmalloc(&p->scrA, csz * (size_t)N * nvec)) != BK_OK) break;
+      if ((st_ = dmalloc(&p->scrY, dtype_size(dtype) * (size_t)(N + 1) * nvec)) != BK_OK) break;
+      if ((st_ = dmalloc(&p->part1, dtype_size(dtype) * (size_t)p->nPartA * nvec)) != BK_OK) break;
+      if ((st_ = dmalloc(&p->part2, dtype_size(dtype) * (size_t)p->nPartA * nvec)) != BK_OK) break;
+    }
+    st_ = dtype == BK_F64 ? build_tables<double>(p, st) : build_tables<float>(p, st);
+    if (st_ != BK_OK) break;
+    if ((st_ = dmalloc((void**)&p->t_nodes, sizeof(double) * (size_t)L)) != BK_OK) break;
+    k_grid_tables<<<(int)((L + 255) / 256), 256, 0, st>>>(p->t_nodes, N, t0, p->s);
+    if (cudaGetLastError() != cudaSuccess) { st_ = BK_ERR_CUDA; set_error("grid table launch failed"); break; }
+    st_ = dtype == BK_F64 ? set_smem_attrs<double>(p) : set_smem_attrs<float>(p);
+    if (st_ != BK_OK) break;
+    if ((st_ = compute_weights(p, st)) != BK_OK) break;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { set_error("plan tables: %s", cudaGetErrorString(e)); st_ = BK_ERR_CUDA; break; }
+  } while (0);
+  if (st_ != BK_OK) {
+    plan_destroy(p);
+    return st_;
+  }
+  *out = p;
+  return BK_OK;
+}
+
+void plan_destroy(Plan* p) {
+  if (!p) return;
+  dfree(p->w64);
+  dfree(p->wT);
+  dfree(p->tw);
+  dfree(p->tpost);
+  dfree(p->twN);
+  dfree(p->scrA);
+  dfree(p->scrY);
+  dfree(p->part1);
+  dfree(p->part2);
+  dfree(p->t_nodes);
+  delete p;
+}
+
+template <typename T>
+static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool trans, double s_scale,
+                            cudaStream_t st, void* scrA, void* scrY, void* part1, void* part2) {
+  typedef typename V2<T>::t C;
+  const int N = (int)p->N;
+  const T s = (T)s_scale;
+  const T invN = T(1) / T(N);
+  if (p->small) {
+    if (!trans)
+      k_birkhoff_small<T, false><<<nvec, 256, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, p->tw_log2, (const C*)p->tpost);
+    else
+      k_birkhoff_small<T, true><<<nvec, 256, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, p->tw_log2, (const C*)p->tpost);
+    BK_CHECK_LAUNCH();
+    return BK_OK;
+  }
+  const int N1 = p->N1, N2 = p->N2, NB = p->NB, P = p->P;
+  const int log2N1 = ilog2(N1), log2N2 = ilog2(N2);
+  C* A = (C*)scrA;
+  T* Ystage = (T*)scrY;
+  T* pa1 = (T*)part1;
+  T* pa2 = (T*)part2;
+  const int nPA = p->nPartA;
+  dim3 gA(N2 / NB, nvec), gB(N1 / 2 / P, nvec);
+  const C* tw = (const C*)p->tw;
+  const C* twN = (const C*)p->twN;
+  const C* tp = (const C*)p->tpost;
+  const int64_t Ls = N + 1;
+  if (!trans) {
+    k_passA<T, IN_PLAIN><<<gA, 256, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN);
+    BK_CHECK_LAUNCH();
+    k_passB<T, EP_STORE><<<gB, 256, p->smemB, st>>>(A, Ystage, Ls, 0, nullptr, 0, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
+    BK_CHECK_LAUNCH();
+    k_passA<T, ST_FWD><<<gA, 256, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN);
+    BK_CHECK_LAUNCH();
+    k_passB<T, EP_FWD_OUT><<<gB, 256, p->smemB, st>>>(A, out, p->pitch, p->pitch, pa2, nPA, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
+    BK_CHECK_LAUNCH();
+  } else {
+    k_passA<T, IN_WINV><<<gA, 256, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN);
+    BK_CHECK_LAUNCH();
+    k_passB<T, EP_STORE_TRN><<<gB, 256, p->smemB, st>>>(A, Ystage, Ls, 0, pa1, nPA, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
+    BK_CHECK_LAUNCH();
+    // the stage buffer already holds Y - Y0, so the transposed stencil runs with Y0 = 0
+    k_passA<T, ST_TRN><<<gA, 256, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN);
+    BK_CHECK_LAUNCH();
+    k_passB<T, EP_TRN_OUT><<<gB, 256, p->smemB, st>>>(A, out, p->pitch, p->pitch, nullptr, 0, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
+    BK_CHECK_LAUNCH();
+  }
+  return BK_OK;
+}
+
+bk_status plan_apply_n(const Plan* p, const void* v, void* out, int nvec, bool trans, double s,
+                       cudaStream_t st) {
+  if (p->dtype == BK_F64)
+    return apply_impl<double>(p, (const double*)v, (double*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2);
+  return apply_impl<float>(p, (const float*)v, (float*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2);
+}
+
+bk_status plan_apply(const Plan* p, const void* v, void* out, int batch, bool trans, cudaStream_t st) {
+  BK_ARG(p != nullptr, "plan is NULL");
+  BK_ARG(v != nullptr && out != nullptr, "NULL vector");
+  BK_ARG(batch >= 1 && batch <= p->max_batch, "batch %d outside [1, max_batch=%d]", batch, p->max_batch);
+  BK_ARG(((uintptr_t)v & 15) == 0 && ((uintptr_t)out & 15) == 0, "vectors must be 16-byte aligned");
+  return plan_apply_n(p, v, out, batch * p->n_comp, trans, p->s, st);
+}
+
+}  // namespace bk
+
+// ---------------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------------
+extern "C" {
+
+const char* bk_last_error(void) { return bk::g_last_error.c_str(); }
+const char* bk_version(void) { return "birkhoff-gb300 0.1 (sm_103a)"; }
+
+bk_status bk_plan_create(bk_plan** plan, int64_t N, int n_comp, int max_batch, bk_dtype dtype,
+                         double t0, double tf, int64_t pitch, void* stream) {
+  BK_ARG(plan != nullptr, "plan output pointer is NULL");
+  bk::Plan* p = nullptr;
+  bk_status s = bk::plan_create(&p, N, n_comp, max_batch, (int)dtype, t0, tf, pitch, (cudaStream_t)stream);
+  *plan = reinterpret_cast<bk_plan*>(p);
+  return s;
+}
+
+void bk_plan_destroy(bk_plan* plan) { bk::plan_destroy(reinterpret_cast<bk::Plan*>(plan)); }
+
+bk_status bk_plan_info(const bk_plan* plan, int64_t* N, int64_t* L, int64_t* pitch, int* dtype) {
+  BK_ARG(plan != nullptr, "plan is NULL");
+  const bk::Plan* p = reinterpret_cast<const bk::Plan*>(plan);
+  if (N) *N = p->N;
+  if (L) *L = p->L;
+  if (pitch) *pitch = p->pitch;
+  if (dtype) *dtype = p->dtype;
+  return BK_OK;
+}
+
+bk_status bk_plan_grid(const bk_plan* plan, double* t_host, double* w_host) {
+  BK_ARG(plan != nullptr, "plan is NULL");
+  const bk::Plan* p = reinterpret_cast<const bk::Plan*>(plan);
+  if (t_host) BK_TRY_CUDA(cudaMemcpy(t_host, p->t_nodes, sizeof(double) * p->L, cudaMemcpyDeviceToHost));
+  if (w_host) BK_TRY_CUDA(cudaMemcpy(w_host, p->w64, sizeof(double) * p->L, cudaMemcpyDeviceToHost));
+  return BK_OK;
+}
+
+bk_status birkhoff_apply(const bk_plan* plan, const void* v, void* out, int batch, void* stream) {
+  return bk::plan_apply(reinterpret_cast<const bk::Plan*>(plan), v, out, batch, false, (cudaStream_t)stream);
+}
+
+bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int batch, void* stream) {
+  return bk::plan_apply(reinterpret_cast<const bk::Plan*>(plan), v, out, batch, true, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,40 @@
+// Plan object of the Birkhoff products (internal).
+#pragma once
+
+#include "bk_common.cuh"
+
+namespace bk {
+
+struct Plan {
+  int64_t N = 0, L = 0, pitch = 0;
+  int n_comp = 1, max_batch = 1, dtype = BK_F64;
+  double t0 = 0, tf = 0, s = 0;
+  bool small = true;          // whole chain in one CTA per vector
+  size_t smemS = 0;           // dynamic shared memory of the single-CTA kernel
+  int N1 = 0, N2 = 0;         // four-step factors, N = N1 * N2
+  int NB = 0, P = 0;          // pass A columns per CTA, pass B row pairs per CTA
+  size_t smemA = 0, smemB = 0;
+  int nPartA = 0;             // pass-A CTAs per vector (partials per vector)
+  int tw_log2 = 0;
+  void* tw = nullptr;         // sub-FFT twiddles (complex, working type)
+  void* tpost = nullptr;      // (cos, sin)(pi k / N), k = 0..N/2 (working type)
+  void* twN = nullptr;        // omega_N^m, m < N (four-step only)
+  void* scrA = nullptr;       // four-step complex scratch, N per vector
+  void* scrY = nullptr;       // stage buffer between the two DCTs, N + 1 per vector
+  void* part1 = nullptr;      // pass-A partial sums, first DCT
+  void* part2 = nullptr;      // pass-A partial sums, second DCT
+  double* t_nodes = nullptr;  // node times t_j (FP64, device)
+  double* w64 = nullptr;      // Clenshaw-Curtis weights (FP64, device, tau-domain)
+  void* wT = nullptr;         // Clenshaw-Curtis weights in the working type (device)
+};
+
+bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtype, double t0,
+                      double tf, int64_t pitch, cudaStream_t st);
+void plan_destroy(Plan* p);
+bk_status plan_apply(const Plan* p, const void* v, void* out, int batch, bool trans,
+                     cudaStream_t st);
+// Apply to `nvec` vectors with an explicit scale (s = 1 gives B^a itself).
+bk_status plan_apply_n(const Plan* p, const void* v, void* out, int nvec, bool trans, double s,
+                       cudaStream_t st);
+
+}  // namespace bk

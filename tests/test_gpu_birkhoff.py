@@ -1,0 +1,130 @@
+"""GPU parity of birkhoff_apply / birkhoff_apply_T against the oracle (through the C ABI)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import birkhoff as ob
+from oracle import grid as og
+from paper_2509_01855_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+# FP64 products must match to 1e-12 relative (2-norm), FP32 to 1e-5.
+TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
+
+
+def _api():
+    from paper_2509_01855_gb300 import api
+    return api
+
+
+def _run(N, dtype, trans, n_comp=3, batch=2, t0=0.0, tf=3.0, V=None, pitch=0):
+    api = _api()
+    plan = api.Plan(N, n_comp=n_comp, max_batch=batch, dtype=dtype, t0=t0, tf=tf, pitch=pitch)
+    L = N + 1
+    if V is None:
+        V = synth.gaussian((batch, n_comp, L), "bk", N, int(trans))
+    v = plan.empty(batch)
+    v[:, :, :L] = torch.as_tensor(V, dtype=dtype)
+    v[:, :, L:] = 7.0          # padding must be ignored
+    out = plan.empty(batch)
+    out.fill_(3.0)
+    (api.birkhoff_apply_T if trans else api.birkhoff_apply)(plan, v, out)
+    torch.cuda.synchronize()
+    o = out.cpu().double().numpy()
+    assert np.all(o[:, :, L:] == 0.0), "padding not zeroed"
+    return o[:, :, :L], V, plan
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N", [4, 8, 16, 64, 256, 1024])
+@pytest.mark.parametrize("trans", [False, True])
+def test_apply_vs_dense_oracle(N, dtype, trans):
+    got, V, _ = _run(N, dtype, trans)
+    B = ob.dense_B(N, 0.0, 3.0)
+    ref = V @ (B if trans else B.T)
+    assert _rel(got, ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N", [2048, 4096, 8192, 16384, 1 << 16])
+@pytest.mark.parametrize("trans", [False, True])
+def test_apply_vs_fastbv_oracle(N, dtype, trans):
+    """Sizes past the dense oracle (and across the single-CTA / four-step boundary): compare
+    with the oracle's FastBV chain on a library DCT."""
+    got, V, _ = _run(N, dtype, trans, n_comp=2, batch=1)
+    ref = (ob.fastbv_T if trans else ob.fastbv)(V, 0.0, 3.0)
+    assert _rel(got, ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("N", [64, 4096, 1 << 15, 1 << 20])
+def test_apply_sparse_modes_exact(N):
+    """B applied to sum_k alpha_k T_k returns the exact integrals (closed forms)."""
+    modes, alphas = synth.sparse_modes(N)
+    v, Bv = ob.sparse_mode_pair(N, modes, alphas, 0.0, 20.0)
+    got, _, _ = _run(N, torch.float64, False, n_comp=1, batch=1, t0=0.0, tf=20.0,
+                     V=v[None, None, :])
+    assert _rel(got[0, 0], Bv) < 1e-12
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N", [16, 4096, 1 << 14, 1 << 18])
+def test_adjoint_dot(N, dtype):
+    """<B x, y> = <x, B^T y> with the library's two products."""
+    api = _api()
+    plan = api.Plan(N, n_comp=1, max_batch=1, dtype=dtype, t0=-1.0, tf=4.0)
+    L = N + 1
+    x = plan.empty(1); y = plan.empty(1)
+    x[0, 0, :L] = torch.as_tensor(synth.gaussian(L, "adj-x", N), dtype=dtype)
+    y[0, 0, :L] = torch.as_tensor(synth.gaussian(L, "adj-y", N), dtype=dtype)
+    Bx = api.birkhoff_apply(plan, x, plan.empty(1))
+    BTy = api.birkhoff_apply_T(plan, y, plan.empty(1))
+    lhs = float((Bx.double() * y.double()).sum())
+    rhs = float((x.double() * BTy.double()).sum())
+    scale = float(Bx.double().norm() * y.double().norm())
+    assert abs(lhs - rhs) / scale < (1e-13 if dtype == torch.float64 else 1e-6)
+
+
+@pytest.mark.parametrize("N", [4, 64, 4096, 1 << 15])
+def test_grid_tables(N):
+    """Plan nodes and Clenshaw-Curtis weights equal the oracle's (Eq. CGLpts, last row of B^a)."""
+    api = _api()
+    plan = api.Plan(N, n_comp=1, dtype=torch.float64, t0=0.5, tf=2.5)
+    t, w = plan.grid()
+    tau = og.cgl_nodes(N)
+    assert np.abs(t.numpy() - (0.5 + 1.0 * (tau + 1.0))).max() < 1e-15 * 4
+    wref = og.cc_weights_sum(N) if N <= 4096 else None
+    if wref is not None:
+        assert np.abs(w.numpy() - wref).max() < 1e-14
+    assert abs(w.sum().item() - 2.0) < 1e-13
+    if N % 2 == 0:
+        assert abs(w[0].item() - 1.0 / (N * N - 1.0)) < 1e-14 / N
+
+
+def test_ones_gives_time():
+    """B 1 = t - t0 at N = 2^20 (large four-step path)."""
+    api = _api()
+    N = 1 << 20
+    plan = api.Plan(N, n_comp=1, dtype=torch.float64, t0=0.0, tf=20.0)
+    v = plan.empty(1)
+    v[0, 0, :N + 1] = 1.0
+    out = api.birkhoff_apply(plan, v, plan.empty(1))
+    t, _ = plan.grid()
+    assert (out[0, 0, :N + 1].cpu() - t).abs().max().item() < 1e-11
+
+
+def test_bad_arguments():
+    api = _api()
+    from paper_2509_01855_gb300._lib import BirkhoffError
+    with pytest.raises(BirkhoffError):
+        api.Plan(100)            # not a power of two
+    with pytest.raises(BirkhoffError):
+        api.Plan(2)              # too small
+    plan = api.Plan(64, n_comp=1, max_batch=1)
+    v = plan.empty(2)
+    with pytest.raises(BirkhoffError):
+        api.birkhoff_apply(plan, v, plan.empty(2), batch=2)   # batch > max_batch
