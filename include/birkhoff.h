@@ -201,7 +201,7 @@ bk_status krylov_solve(bk_problem* prob, int op, const void* rhs, void* sol,
 typedef struct {
   double tol;         /* stop when the weighted KKT residual norm <= tol (default 1e-10)     */
   int max_iter;       /* Newton iteration cap (default 30)                                  */
-  double krylov_rtol; /* inner relative tolerance (default 1e-10 in FP64, 1e-5 in FP32)     */
+  double krylov_rtol; /* inner relative tolerance (default 1e-12 in FP64, 1e-5 in FP32)     */
   int restart;        /* GMRES restart (default 30)                                         */
   int max_krylov;     /* inner iteration cap per solve (default 300)                        */
   double ir_rtol;     /* FP32 mode: FP64 iterative refinement until the FP64 residual of the

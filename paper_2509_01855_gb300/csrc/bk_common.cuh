@@ -17,6 +17,7 @@ void set_error(const char* fmt, ...);
   do {                                                                                \
     cudaError_t e_ = (expr);                                                          \
     if (e_ != cudaSuccess) {                                                          \
+      (void)cudaGetLastError();                                                       \
       bk::set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(e_)); \
       return BK_ERR_CUDA;                                                             \
     }                                                                                 \

@@ -1,0 +1,1240 @@
+// Problems, linearisation, the KKT / state operators, the Birkhoff preconditioner sweeps and the
+// KKT residual.
+//
+// Paper: "Construction of a Low-Memory Fast Million-Point Linear Solver" (Eqs. X-V=nonlin ..
+// Achibetadef, FastAX), "Development of a Special Birkhoff-Centric Preconditioner" (B-tilde,
+// FastBccV, P = I - B-tilde d_X f, FastPinvY), Eq. Prob-PNa (the discretised problem).
+//
+// Preconditioner sweep. Row k of P xi = Y with P = I - s (B-tilde (x) I) J_x reads
+//   (I - h_k J_k) xi_k = Y_k + sigma_k,   sigma_k = s sum_{j<k} w_j J_j xi_j,   h_k = s w_k / 2,
+// so xi_k = K_k (Y_k + sigma_k) with K_k = (I - h_k J_k)^{-1}, and sigma_{k+1} = sigma_k +
+// N_k (Y_k + sigma_k), N_k = 2 h_k J_k K_k. (The sweep printed as FastPinvY subtracts the running
+// sum and accumulates the input instead of the solution, which does not invert P; the recurrence
+// above is what the rows of P give.) The transpose P^T y = r runs backwards:
+//   y_j = K_j^T r_j + N_j^T rho_j,  rho_{j-1} = rho_j + y_j,  (B-tilde^T y)_j = w_j (y_j/2 + rho_j).
+// Both are affine recurrences sigma_{k+1} = (I + N_k) sigma_k + f_k; they run as a chunked scan:
+// segments of SEG nodes (one thread each, sequential), groups of GRP segments, and one CTA that
+// scans the group maps. The matrix parts of the segment and group maps depend only on the
+// linearisation and are formed in bk_linearize; the backward maps are their transposes.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "bk_problem.cuh"
+
+namespace bk {
+
+// ---------------------------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int64_t il_index(int64_t k, int c, int NC) {
+  // interleaved per-node storage: node k = seg * SEG + i, seg = W * 32 + lane
+  const int64_t seg = k / SEG;
+  const int i = (int)(k - seg * SEG);
+  const int64_t W = seg >> 5;
+  const int lane = (int)(seg & 31);
+  return (((W * SEG + i) * NC + c) << 5) + lane;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T a = T(0);
+  if (threadIdx.x < 32) {
+    a = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  }
+  return a;  // valid in thread 0
+}
+
+static inline int nblk(int64_t n, int t = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 65535)); }
+
+// ---------------------------------------------------------------------------------------------
+// Linearisation kernels (FP64 arithmetic, results stored in T)
+// ---------------------------------------------------------------------------------------------
+template <int KIND, int NX>
+__device__ void node_factors(const double* x, const double* u, double h, double* K, double* Nm) {
+  double Jx[NXM * NXM], Ju[NXM * NUM];
+  Dyn<KIND>::template jac<double>(x, u, Jx, Ju);
+  // A = I - h J; K = A^{-1} by Gauss-Jordan with partial pivoting
+  double A[NX * NX], Inv[NX * NX];
+#pragma unroll
+  for (int r = 0; r < NX; ++r)
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
+      A[r * NX + c] = (r == c ? 1.0 : 0.0) - h * Jx[r * NX + c];
+      Inv[r * NX + c] = r == c ? 1.0 : 0.0;
+    }
+#pragma unroll
+  for (int c = 0; c < NX; ++c) {
+    int piv = c;
+    double best = fabs(A[c * NX + c]);
+#pragma unroll
+    for (int r = c + 1; r < NX; ++r)
+      if (fabs(A[r * NX + c]) > best) { best = fabs(A[r * NX + c]); piv = r; }
+    if (piv != c) {
+#pragma unroll
+      for (int q = 0; q < NX; ++q) {
+        double t = A[c * NX + q]; A[c * NX + q] = A[piv * NX + q]; A[piv * NX + q] = t;
+        t = Inv[c * NX + q]; Inv[c * NX + q] = Inv[piv * NX + q]; Inv[piv * NX + q] = t;
+      }
+    }
+    const double ip = 1.0 / A[c * NX + c];
+#pragma unroll
+    for (int q = 0; q < NX; ++q) { A[c * NX + q] *= ip; Inv[c * NX + q] *= ip; }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      if (r == c) continue;
+      const double f = A[r * NX + c];
+#pragma unroll
+      for (int q = 0; q < NX; ++q) { A[r * NX + q] -= f * A[c * NX + q]; Inv[r * NX + q] -= f * Inv[c * NX + q]; }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) K[i] = Inv[i];
+  // N = 2 h J K
+#pragma unroll
+  for (int r = 0; r < NX; ++r)
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
+      double a = 0;
+#pragma unroll
+      for (int q = 0; q < NX; ++q) a += Jx[r * NX + q] * Inv[q * NX + c];
+      Nm[r * NX + c] = 2.0 * h * a;
+    }
+}
+
+template <typename T, int KIND, int NX, int NU>
+__global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, const double* __restrict__ w,
+                            double s, T* __restrict__ Kn, T* __restrict__ Nn, T* __restrict__ xu) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+    double x[NXM], u[NUM];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) x[m] = z[m * P + k];
+#pragma unroll
+    for (int q = 0; q < NU; ++q) u[q] = z[(NX + q) * P + k];
+    double K[NX * NX], Nm[NX * NX];
+    node_factors<KIND, NX>(x, u, 0.5 * s * w[k], K, Nm);
+#pragma unroll
+    for (int c = 0; c < NX * NX; ++c) {
+      Kn[il_index(k, c, NX * NX)] = (T)K[c];
+      Nn[il_index(k, c, NX * NX)] = (T)Nm[c];
+    }
+#pragma unroll
+    for (int m = 0; m < NX + NU; ++m) xu[m * P + k] = (T)z[m * P + k];
+  }
+}
+
+// Segment aggregates A_seg = prod_k (I + N_k) (latest node on the left), FP64 accumulation.
+template <typename T, int NX>
+__global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, T* __restrict__ Aseg) {
+  const int seg = blockIdx.x * blockDim.x + threadIdx.x;
+  if (seg >= nseg) return;
+  double A[NX * NX];
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) A[i] = (i % (NX + 1) == 0) ? 1.0 : 0.0;
+  for (int i = 0; i < SEG; ++i) {
+    const int64_t k = (int64_t)seg * SEG + i;
+    if (k >= L) break;
+    double M[NX * NX], R[NX * NX];
+#pragma unroll
+    for (int c = 0; c < NX * NX; ++c) M[c] = (double)Nn[il_index(k, c, NX * NX)] + ((c % (NX + 1) == 0) ? 1.0 : 0.0);
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int c = 0; c < NX; ++c) {
+        double a = 0;
+#pragma unroll
+        for (int q = 0; q < NX; ++q) a += M[r * NX + q] * A[q * NX + c];
+        R[r * NX + c] = a;
+      }
+#pragma unroll
+    for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
+  }
+#pragma unroll
+  for (int c = 0; c < NX * NX; ++c) Aseg[(int64_t)c * nseg + seg] = (T)A[c];
+}
+
+// Group aggregates from segment aggregates.
+template <typename T, int NX>
+__global__ void k_lin_grp(const T* __restrict__ Aseg, int nseg, int ngrp, T* __restrict__ Agrp) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ngrp) return;
+  double A[NX * NX];
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) A[i] = (i % (NX + 1) == 0) ? 1.0 : 0.0;
+  for (int i = 0; i < GRP; ++i) {
+    const int seg = g * GRP + i;
+    if (seg >= nseg) break;
+    double M[NX * NX], R[NX * NX];
+#pragma unroll
+    for (int c = 0; c < NX * NX; ++c) M[c] = (double)Aseg[(int64_t)c * nseg + seg];
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int c = 0; c < NX; ++c) {
+        double a = 0;
+#pragma unroll
+        for (int q = 0; q < NX; ++q) a += M[r * NX + q] * A[q * NX + c];
+        R[r * NX + c] = a;
+      }
+#pragma unroll
+    for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
+  }
+#pragma unroll
+  for (int c = 0; c < NX * NX; ++c) Agrp[(int64_t)c * ngrp + g] = (T)A[c];
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_convert(const Tin* __restrict__ a, Tout* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (Tout)a[i];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Sweep kernels. Forward (DIR = 0): sigma_{k+1} = (I + N_k) sigma_k + N_k y'_k + 2 h_k g_k with
+// y'_k = Y_k + h_k g_k, output xi_k = K_k (y'_k + sigma_k). Backward (DIR = 1): rho_{j-1} =
+// (I + N_j^T) rho_j + K_j^T r_j, output y_j = K_j^T r_j + N_j^T rho_j, optional b_j =
+// w_j (y_j / 2 + rho_j).
+// ---------------------------------------------------------------------------------------------
+template <typename T, int NX, int DIR>
+__device__ __forceinline__ void node_step(const T* __restrict__ Kn, const T* __restrict__ Nn, int64_t k,
+                                          const T* yin, const T* gin, T h, T* st, T* out, bool want_out) {
+  T Km[NX * NX], Nm[NX * NX];
+#pragma unroll
+  for (int c = 0; c < NX * NX; ++c) {
+    Km[c] = Kn[il_index(k, c, NX * NX)];
+    Nm[c] = Nn[il_index(k, c, NX * NX)];
+  }
+  if (DIR == 0) {
+    T v[NX];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) v[m] = yin[m] + h * gin[m] + st[m];
+    if (want_out) {
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        T a = T(0);
+#pragma unroll
+        for (int c = 0; c < NX; ++c) a += Km[r * NX + c] * v[c];
+        out[r] = a;
+      }
+    }
+    T ns[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      T a = st[r] + T(2) * h * gin[r];
+#pragma unroll
+      for (int c = 0; c < NX; ++c) a += Nm[r * NX + c] * v[c];
+      ns[r] = a;
+    }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) st[r] = ns[r];
+  } else {
+    T y[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      T a = T(0);
+#pragma unroll
+      for (int c = 0; c < NX; ++c) a += Km[c * NX + r] * yin[c] + Nm[c * NX + r] * st[c];
+      y[r] = a;
+    }
+    if (want_out) {
+#pragma unroll
+      for (int r = 0; r < NX; ++r) { out[r] = y[r]; out[NX + r] = y[r] * T(0.5) + st[r]; }
+    }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) st[r] += y[r];
+  }
+}
+
+// Phase 1: per segment, the offset of its affine map (zero incoming state).
+template <typename T, int NX, int DIR>
+__global__ void k_sweep_seg(const T* __restrict__ Kn, const T* __restrict__ Nn, const T* __restrict__ Y,
+                            const T* __restrict__ G, int64_t P, int64_t L, const T* __restrict__ w, T s,
+                            int nseg, T* __restrict__ segb) {
+  const int seg = blockIdx.x * blockDim.x + threadIdx.x;
+  if (seg >= nseg) return;
+  T st[NX], dummy[2 * NX];
+#pragma unroll
+  for (int m = 0; m < NX; ++m) st[m] = T(0);
+  for (int ii = 0; ii < SEG; ++ii) {
+    const int i = DIR == 0 ? ii : SEG - 1 - ii;
+    const int64_t k = (int64_t)seg * SEG + i;
+    if (k >= L) { if (DIR == 0) break; else continue; }
+    T yin[NX], gin[NX];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) { yin[m] = Y[m * P + k]; gin[m] = G ? G[m * P + k] : T(0); }
+    node_step<T, NX, DIR>(Kn, Nn, k, yin, gin, T(0.5) * s * w[k], st, dummy, false);
+  }
+#pragma unroll
+  for (int m = 0; m < NX; ++m) segb[(int64_t)m * nseg + seg] = st[m];
+}
+
+// Phase 2: per group, compose the segment offsets (zero incoming state).
+template <typename T, int NX, int DIR>
+__global__ void k_sweep_grp(const T* __restrict__ Aseg, const T* __restrict__ segb, int nseg, int ngrp,
+                            T* __restrict__ grpb) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ngrp) return;
+  T st[NX];
+#pragma unroll
+  for (int m = 0; m < NX; ++m) st[m] = T(0);
+  for (int ii = 0; ii < GRP; ++ii) {
+    const int i = DIR == 0 ? ii : GRP - 1 - ii;
+    const int seg = g * GRP + i;
+    if (seg >= nseg) { if (DIR == 0) break; else continue; }
+    T ns[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      T a = segb[(int64_t)r * nseg + seg];
+#pragma unroll
+      for (int c = 0; c < NX; ++c)
+        a += (DIR == 0 ? Aseg[(int64_t)(r * NX + c) * nseg + seg] : Aseg[(int64_t)(c * NX + r) * nseg + seg]) * st[c];
+      ns[r] = a;
+    }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) st[r] = ns[r];
+  }
+#pragma unroll
+  for (int m = 0; m < NX; ++m) grpb[(int64_t)m * ngrp + g] = st[m];
+}
+
+// Phase 3: one CTA scans the group maps (in sweep order) and writes each group's incoming state.
+template <typename T, int NX, int DIR>
+__global__ void __launch_bounds__(256) k_sweep_top(const T* __restrict__ Agrp, const T* __restrict__ grpb,
+                                                   int ngrp, T* __restrict__ grpin) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sA = reinterpret_cast<T*>(smem_raw);          // [256][NX*NX]
+  T* sb = sA + 256 * NX * NX;                      // [256][NX]
+  const int t = threadIdx.x;
+  const int per = (ngrp + 255) / 256;
+  // thread t owns sweep-ordered groups [t*per, (t+1)*per)
+  T A[NX * NX], b[NX];
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) A[i] = (i % (NX + 1) == 0) ? T(1) : T(0);
+#pragma unroll
+  for (int i = 0; i < NX; ++i) b[i] = T(0);
+  for (int q = 0; q < per; ++q) {
+    const int o = t * per + q;
+    if (o >= ngrp) break;
+    const int g = DIR == 0 ? o : ngrp - 1 - o;
+    T M[NX * NX], nb[NX], nA[NX * NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int c = 0; c < NX; ++c)
+        M[r * NX + c] = DIR == 0 ? Agrp[(int64_t)(r * NX + c) * ngrp + g] : Agrp[(int64_t)(c * NX + r) * ngrp + g];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      T a = grpb[(int64_t)r * ngrp + g];
+#pragma unroll
+      for (int c = 0; c < NX; ++c) a += M[r * NX + c] * b[c];
+      nb[r] = a;
+#pragma unroll
+      for (int c = 0; c < NX; ++c) {
+        T s2 = T(0);
+#pragma unroll
+        for (int qq = 0; qq < NX; ++qq) s2 += M[r * NX + qq] * A[qq * NX + c];
+        nA[r * NX + c] = s2;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NX * NX; ++i) A[i] = nA[i];
+#pragma unroll
+    for (int i = 0; i < NX; ++i) b[i] = nb[i];
+  }
+#pragma unroll
+  for (int i = 0; i < NX * NX; ++i) sA[t * NX * NX + i] = A[i];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) sb[t * NX + i] = b[i];
+  __syncthreads();
+  // Kogge-Stone inclusive scan of the affine maps: x_t <- x_t o x_{t-d}
+  for (int d = 1; d < 256; d <<= 1) {
+    T pA[NX * NX], pb[NX];
+    const bool act = t >= d;
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < NX * NX; ++i) pA[i] = sA[(t - d) * NX * NX + i];
+#pragma unroll
+      for (int i = 0; i < NX; ++i) pb[i] = sb[(t - d) * NX + i];
+    }
+    __syncthreads();
+    if (act) {
+      T nA[NX * NX], nb[NX];
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        T a = b[r];
+#pragma unroll
+        for (int c = 0; c < NX; ++c) a += A[r * NX + c] * pb[c];
+        nb[r] = a;
+#pragma unroll
+        for (int c = 0; c < NX; ++c) {
+          T s2 = T(0);
+#pragma unroll
+          for (int qq = 0; qq < NX; ++qq) s2 += A[r * NX + qq] * pA[qq * NX + c];
+          nA[r * NX + c] = s2;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NX * NX; ++i) { A[i] = nA[i]; sA[t * NX * NX + i] = nA[i]; }
+#pragma unroll
+      for (int i = 0; i < NX; ++i) { b[i] = nb[i]; sb[t * NX + i] = nb[i]; }
+    }
+    __syncthreads();
+  }
+  // incoming state of thread t's first group = offset of the inclusive map of thread t-1
+  T st[NX];
+#pragma unroll
+  for (int i = 0; i < NX; ++i) st[i] = t > 0 ? sb[(t - 1) * NX + i] : T(0);
+  for (int q = 0; q < per; ++q) {
+    const int o = t * per + q;
+    if (o >= ngrp) break;
+    const int g = DIR == 0 ? o : ngrp - 1 - o;
+#pragma unroll
+    for (int r = 0; r < NX; ++r) grpin[(int64_t)r * ngrp + g] = st[r];
+    T ns[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      T a = grpb[(int64_t)r * ngrp + g];
+#pragma unroll
+      for (int c = 0; c < NX; ++c)
+        a += (DIR == 0 ? Agrp[(int64_t)(r * NX + c) * ngrp + g] : Agrp[(int64_t)(c * NX + r) * ngrp + g]) * st[c];
+      ns[r] = a;
+    }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) st[r] = ns[r];
+  }
+}
+
+// Phase 4: per group, incoming states of its segments (overwrites segb in place).
+template <typename T, int NX, int DIR>
+__global__ void k_sweep_dist(const T* __restrict__ Aseg, T* __restrict__ segb, int nseg, int ngrp,
+                             const T* __restrict__ grpin) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ngrp) return;
+  T st[NX];
+#pragma unroll
+  for (int m = 0; m < NX; ++m) st[m] = grpin[(int64_t)m * ngrp + g];
+  for (int ii = 0; ii < GRP; ++ii) {
+    const int i = DIR == 0 ? ii : GRP - 1 - ii;
+    const int seg = g * GRP + i;
+    if (seg >= nseg) { if (DIR == 0) break; else continue; }
+    T ns[NX];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      T a = segb[(int64_t)r * nseg + seg];
+#pragma unroll
+      for (int c = 0; c < NX; ++c)
+        a += (DIR == 0 ? Aseg[(int64_t)(r * NX + c) * nseg + seg] : Aseg[(int64_t)(c * NX + r) * nseg + seg]) * st[c];
+      ns[r] = a;
+    }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) segb[(int64_t)r * nseg + seg] = st[r];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) st[r] = ns[r];
+  }
+}
+
+// Phase 5: per segment, rerun with the incoming state and write the outputs.
+template <typename T, int NX, int DIR>
+__global__ void k_sweep_out(const T* __restrict__ Kn, const T* __restrict__ Nn, const T* __restrict__ Y,
+                            const T* __restrict__ G, int64_t P, int64_t L, const T* __restrict__ w, T s, int nseg,
+                            const T* __restrict__ segin, T* __restrict__ out, T* __restrict__ bout) {
+  const int seg = blockIdx.x * blockDim.x + threadIdx.x;
+  if (seg >= nseg) return;
+  T st[NX];
+#pragma unroll
+  for (int m = 0; m < NX; ++m) st[m] = segin[(int64_t)m * nseg + seg];
+  for (int ii = 0; ii < SEG; ++ii) {
+    const int i = DIR == 0 ? ii : SEG - 1 - ii;
+    const int64_t k = (int64_t)seg * SEG + i;
+    if (k >= L) { if (DIR == 0) break; else continue; }
+    T yin[NX], gin[NX], o[2 * NX];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) { yin[m] = Y[m * P + k]; gin[m] = G ? G[m * P + k] : T(0); }
+    const T wk = w[k];
+    node_step<T, NX, DIR>(Kn, Nn, k, yin, gin, T(0.5) * s * wk, st, o, true);
+#pragma unroll
+    for (int m = 0; m < NX; ++m) out[m * P + k] = o[m];
+    if (DIR == 1 && bout) {
+#pragma unroll
+      for (int m = 0; m < NX; ++m) bout[m * P + k] = wk * o[NX + m];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_zero_pad(T* __restrict__ v, int nblocks, int64_t P, int64_t L) {
+  const int64_t padn = P - L;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)nblocks * padn;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / padn;
+    v[b * P + L + (i - b * padn)] = T(0);
+  }
+}
+
+// Full sweep: out = P^{-1} (Y, forcing G) (DIR 0) or P^{-T} Y with bout = B-tilde^T out (DIR 1).
+template <typename T, int NX, int DIR>
+static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* out, T* bout, cudaStream_t st) {
+  const int nseg = pr->nseg, ngrp = pr->ngrp;
+  const T s = (T)pr->s;
+  const T* w = (const T*)d.w;
+  k_sweep_seg<T, NX, DIR><<<(nseg + 127) / 128, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, nseg, (T*)d.segb);
+  BK_CHECK_LAUNCH();
+  k_sweep_grp<T, NX, DIR><<<(ngrp + 127) / 128, 128, 0, st>>>((const T*)d.Aseg, (const T*)d.segb, nseg, ngrp, (T*)d.grpb);
+  BK_CHECK_LAUNCH();
+  T* grpin = (T*)d.grpb + (size_t)NX * ngrp;
+  const size_t sm = sizeof(T) * 256 * (NX * NX + NX);
+  k_sweep_top<T, NX, DIR><<<1, 256, sm, st>>>((const T*)d.Agrp, (const T*)d.grpb, ngrp, grpin);
+  BK_CHECK_LAUNCH();
+  k_sweep_dist<T, NX, DIR><<<(ngrp + 127) / 128, 128, 0, st>>>((const T*)d.Aseg, (T*)d.segb, nseg, ngrp, grpin);
+  BK_CHECK_LAUNCH();
+  k_sweep_out<T, NX, DIR><<<(nseg + 127) / 128, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, nseg, (const T*)d.segb, out, bout);
+  BK_CHECK_LAUNCH();
+  if (pr->P > pr->L) {
+    k_zero_pad<T><<<nblk(NX * (pr->P - pr->L)), 256, 0, st>>>(out, NX, pr->P, pr->L);
+    if (bout) k_zero_pad<T><<<nblk(NX * (pr->P - pr->L)), 256, 0, st>>>(bout, NX, pr->P, pr->L);
+  }
+  return BK_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// KKT / state operator kernels (per node, Jacobians and Hessian recomputed from (x, u, mu))
+// ---------------------------------------------------------------------------------------------
+template <typename T, int KIND>
+__global__ void k_jvp(const T* __restrict__ xu, const T* __restrict__ dX, const T* __restrict__ dU, int64_t P,
+                      int64_t L, T* __restrict__ t) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+    T x[NXM], u[NUM], Jx[NXM * NXM], Ju[NXM * NUM];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) x[m] = xu[m * P + k];
+#pragma unroll
+    for (int q = 0; q < NU; ++q) u[q] = xu[(NX + q) * P + k];
+    Dyn<KIND>::template jac<T>(x, u, Jx, Ju);
+#pragma unroll
+    for (int m = 0; m < NX; ++m) {
+      T a = T(0);
+#pragma unroll
+      for (int p = 0; p < NX; ++p) a += Jx[m * NX + p] * dX[p * P + k];
+      if (dU) {
+#pragma unroll
+        for (int q = 0; q < NU; ++q) a += Ju[m * NU + q] * dU[q * P + k];
+      }
+      t[m * P + k] = a;
+    }
+  }
+}
+
+// out = chi - Bt (state operator), padding zeroed.
+template <typename T, int NX>
+__global__ void k_state_post(const T* __restrict__ chi, const T* __restrict__ Bt, int64_t P, int64_t L,
+                             T* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NX * P; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i % P;
+    out[i] = k < L ? chi[i] - Bt[i] : T(0);
+  }
+}
+
+struct TermSpec {
+  int n_e;
+  int idx[NEM];
+  double val[NEM];
+};
+
+// KKT product: out = [H dz + G^T dy ; G dz], with Bt = s B^a (J dz), Mu = s B^aT dlambda.
+template <typename T, int KIND>
+__global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, const T* __restrict__ w, T s,
+                           const T* __restrict__ in, const T* __restrict__ Bt, const T* __restrict__ Mu, int64_t P,
+                           int64_t L, TermSpec ts, T cost_uu, T* __restrict__ out) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu, NV = NX + NU;
+  const T* dX = in;
+  const T* dU = in + NX * P;
+  const T* dL = in + NV * P;
+  const T* dNu = in + (NV + NX) * P;
+  T* oX = out;
+  T* oU = out + NX * P;
+  T* oL = out + NV * P;
+  T* oNu = out + (NV + NX) * P;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k >= L) {
+#pragma unroll
+      for (int m = 0; m < NV + NX; ++m) out[m * P + k] = T(0);
+      continue;
+    }
+    T x[NXM], u[NUM], m_[NXM], Jx[NXM * NXM], Ju[NXM * NUM], H[(NXM + NUM) * (NXM + NUM)], dz[NXM + NUM], mp[NXM];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) { x[m] = xu[m * P + k]; m_[m] = mu[m * P + k]; dz[m] = dX[m * P + k]; mp[m] = Mu[m * P + k]; }
+#pragma unroll
+    for (int q = 0; q < NU; ++q) { u[q] = xu[(NX + q) * P + k]; dz[NX + q] = dU[q * P + k]; }
+    Dyn<KIND>::template jac<T>(x, u, Jx, Ju);
+    Dyn<KIND>::template hess<T>(x, u, m_, H);
+    const T swk = s * w[k] * cost_uu;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      T acc = T(0);
+#pragma unroll
+      for (int b = 0; b < NV; ++b) acc -= H[a * NV + b] * dz[b];
+      if (a >= NX) acc += swk * dz[a];
+      if (a < NX) {
+        acc += dL[a * P + k];
+#pragma unroll
+        for (int m = 0; m < NX; ++m) acc -= Jx[m * NX + a] * mp[m];
+      } else {
+#pragma unroll
+        for (int m = 0; m < NX; ++m) acc -= Ju[m * NU + (a - NX)] * mp[m];
+      }
+      if (a < NX && k == L - 1) {
+        for (int r = 0; r < ts.n_e; ++r)
+          if (ts.idx[r] == a) acc += dNu[r];
+      }
+      if (a < NX) oX[a * P + k] = acc;
+      else oU[(a - NX) * P + k] = acc;
+    }
+#pragma unroll
+    for (int m = 0; m < NX; ++m) oL[m * P + k] = dz[m] - Bt[m * P + k];
+    if (k == L - 1) {
+      for (int r = 0; r < 32; ++r) oNu[r] = r < ts.n_e ? dX[ts.idx[r] * P + k] : T(0);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// KKT preconditioner elementwise kernels
+// ---------------------------------------------------------------------------------------------
+// yu_q = (r_u,q + s sum_m Ju[m][q] b_m) / (s w_k cost_uu);  g_m = sum_q Ju[m][q] yu_q
+template <typename T, int KIND>
+__global__ void k_pre_u(const T* __restrict__ xu, const T* __restrict__ w, T s, T cost_uu, const T* __restrict__ ru,
+                        const T* __restrict__ b, int64_t P, int64_t L, T* __restrict__ yu, T* __restrict__ g,
+                        T gsign) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k >= L) {
+#pragma unroll
+      for (int q = 0; q < NU; ++q) yu[q * P + k] = T(0);
+#pragma unroll
+      for (int m = 0; m < NX; ++m) g[m * P + k] = T(0);
+      continue;
+    }
+    T x[NXM], u[NUM], Jx[NXM * NXM], Ju[NXM * NUM], y[NUM];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) x[m] = xu[m * P + k];
+#pragma unroll
+    for (int q = 0; q < NU; ++q) u[q] = xu[(NX + q) * P + k];
+    Dyn<KIND>::template jac<T>(x, u, Jx, Ju);
+    const T inv = T(1) / (s * w[k] * cost_uu);
+#pragma unroll
+    for (int q = 0; q < NU; ++q) {
+      T a = ru ? ru[q * P + k] : T(0);
+#pragma unroll
+      for (int m = 0; m < NX; ++m) a += s * Ju[m * NU + q] * b[m * P + k];
+      y[q] = a * inv;
+      yu[q * P + k] = y[q];
+    }
+#pragma unroll
+    for (int m = 0; m < NX; ++m) {
+      T a = T(0);
+#pragma unroll
+      for (int q = 0; q < NU; ++q) a += Ju[m * NU + q] * y[q];
+      g[m * P + k] = gsign * a;
+    }
+  }
+}
+
+// y_nu = S^{-1} (q[term, N] - r_nu)   (one thread)
+template <typename T>
+__global__ void k_pre_nu(const T* __restrict__ q, const T* __restrict__ rnu, const T* __restrict__ Sinv, int64_t P,
+                         int64_t L, TermSpec ts, T* __restrict__ ynu) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  T rhs[NEM];
+  for (int r = 0; r < ts.n_e; ++r) rhs[r] = q[ts.idx[r] * P + (L - 1)] - rnu[r];
+  for (int r = 0; r < 32; ++r) {
+    T a = T(0);
+    if (r < ts.n_e)
+      for (int c = 0; c < ts.n_e; ++c) a += Sinv[r * ts.n_e + c] * rhs[c];
+    ynu[r] = a;
+  }
+}
+
+// y_u += HW y_nu; y_x -= Q y_nu; y_lambda -= Z y_nu
+template <typename T, int NX, int NU>
+__global__ void k_pre_fix(const T* __restrict__ Zc, const T* __restrict__ HWc, const T* __restrict__ Qc,
+                          const T* __restrict__ ynu, int n_e, int64_t P, int64_t L, T* __restrict__ yx,
+                          T* __restrict__ yu, T* __restrict__ yl) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+    for (int r = 0; r < n_e; ++r) {
+      const T c = ynu[r];
+#pragma unroll
+      for (int m = 0; m < NX; ++m) {
+        yx[m * P + k] -= c * Qc[((int64_t)r * NX + m) * P + k];
+        yl[m * P + k] -= c * Zc[((int64_t)r * NX + m) * P + k];
+      }
+#pragma unroll
+      for (int q = 0; q < NU; ++q) yu[q * P + k] += c * HWc[((int64_t)r * NU + q) * P + k];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_unit(T* v, int64_t n, int64_t idx) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = i == idx ? T(1) : T(0);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Residual kernels (FP64)
+// ---------------------------------------------------------------------------------------------
+template <int KIND>
+__global__ void k_feval(const double* __restrict__ z, int64_t P, int64_t L, double* __restrict__ fout) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k >= L) {
+#pragma unroll
+      for (int m = 0; m < NX; ++m) fout[m * P + k] = 0.0;
+      continue;
+    }
+    double x[NXM], u[NUM], f[NXM];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) x[m] = z[m * P + k];
+#pragma unroll
+    for (int q = 0; q < NU; ++q) u[q] = z[(NX + q) * P + k];
+    Dyn<KIND>::template f<double>(x, u, f);
+#pragma unroll
+    for (int m = 0; m < NX; ++m) fout[m * P + k] = f[m];
+  }
+}
+
+struct X0Spec {
+  double x0[NXM];
+};
+
+// F = [grad_X L ; grad_U L ; c ; e] and per-block partial sums of the weighted norm.
+template <int KIND>
+__global__ void k_resid_post(const double* __restrict__ z, const double* __restrict__ w, double s,
+                             const double* __restrict__ Bf, const double* __restrict__ Mu, int64_t P, int64_t L,
+                             TermSpec ts, X0Spec x0, double cost_uu, double* __restrict__ F,
+                             double* __restrict__ partial) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu, NV = NX + NU;
+  __shared__ double red[32];
+  const double* X = z;
+  const double* U = z + NX * P;
+  const double* lam = z + NV * P;
+  const double* nu = z + (NV + NX) * P;
+  double acc = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k >= L) {
+#pragma unroll
+      for (int m = 0; m < NV + NX; ++m) F[m * P + k] = 0.0;
+      continue;
+    }
+    double x[NXM], u[NUM], Jx[NXM * NXM], Ju[NXM * NUM], mp[NXM];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) { x[m] = X[m * P + k]; mp[m] = Mu[m * P + k]; }
+#pragma unroll
+    for (int q = 0; q < NU; ++q) u[q] = U[q * P + k];
+    Dyn<KIND>::template jac<double>(x, u, Jx, Ju);
+    const double wk = w[k];
+    const double iw = 1.0 / wk;
+#pragma unroll
+    for (int p = 0; p < NX; ++p) {
+      double g = lam[p * P + k];
+#pragma unroll
+      for (int m = 0; m < NX; ++m) g -= Jx[m * NX + p] * mp[m];
+      if (k == L - 1)
+        for (int r = 0; r < ts.n_e; ++r)
+          if (ts.idx[r] == p) g += nu[r];
+      F[p * P + k] = g;
+      acc += g * g * iw;
+    }
+#pragma unroll
+    for (int q = 0; q < NU; ++q) {
+      double g = s * wk * cost_uu * u[q];
+#pragma unroll
+      for (int m = 0; m < NX; ++m) g -= Ju[m * NU + q] * mp[m];
+      F[(NX + q) * P + k] = g;
+      acc += g * g * iw;
+    }
+#pragma unroll
+    for (int m = 0; m < NX; ++m) {
+      const double c = x[m] - x0.x0[m] - Bf[m * P + k];
+      F[(NV + m) * P + k] = c;
+      acc += wk * c * c;
+    }
+    if (k == L - 1) {
+      for (int r = 0; r < 32; ++r) {
+        double e = r < ts.n_e ? x[ts.idx[r]] - ts.val[r] : 0.0;
+        F[(NV + NX) * P + r] = e;
+        acc += e * e;
+      }
+    }
+  }
+  double tot = block_sum<double>(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// Weighted norm partials of an arbitrary FP64 residual vector.
+template <int NX, int NU>
+__global__ void k_wnorm(const double* __restrict__ F, const double* __restrict__ w, int64_t P, int64_t L, int n_e,
+                        double* __restrict__ partial) {
+  constexpr int NV = NX + NU;
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+    const double wk = w[k], iw = 1.0 / wk;
+#pragma unroll
+    for (int m = 0; m < NV; ++m) { const double g = F[m * P + k]; acc += g * g * iw; }
+#pragma unroll
+    for (int m = 0; m < NX; ++m) { const double c = F[(NV + m) * P + k]; acc += wk * c * c; }
+    if (k == L - 1)
+      for (int r = 0; r < n_e; ++r) { const double e = F[(NV + NX) * P + r]; acc += e * e; }
+  }
+  double tot = block_sum<double>(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += partial[i];
+  double t = block_sum<double>(a, red);
+  if (threadIdx.x == 0) out[0] = t;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------------
+static TermSpec term_spec(const Problem* pr) {
+  TermSpec t;
+  memset(&t, 0, sizeof(t));
+  t.n_e = pr->n_e;
+  for (int r = 0; r < pr->n_e; ++r) { t.idx[r] = pr->term_idx[r]; t.val[r] = pr->term_val[r]; }
+  return t;
+}
+
+template <int KIND> struct KindNX { static constexpr int nx = Dyn<KIND>::nx, nu = Dyn<KIND>::nu; };
+
+#define BK_DISPATCH_KIND(kind, FN, ...)                                   \
+  switch (kind) {                                                         \
+    case BK_DBL_INT: return FN<BK_DBL_INT>(__VA_ARGS__);                  \
+    case BK_ORBIT: return FN<BK_ORBIT>(__VA_ARGS__);                      \
+    case BK_BILINEAR: return FN<BK_BILINEAR>(__VA_ARGS__);                \
+    default: set_error("unknown problem kind"); return BK_ERR_ARG;        \
+  }
+
+static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
+  d.dtype = dtype;
+  const size_t es = dtype_size(dtype);
+  const int64_t P = pr->P;
+  const int nx = pr->n_x, nu = pr->n_u, ne = pr->n_e;
+  BK_TRY(plan_create(&d.plan, pr->N, nx, 1, dtype, pr->t0, pr->tf, P, 0));
+  BK_TRY(dmalloc(&d.xu, es * (nx + nu) * P));
+  BK_TRY(dmalloc(&d.mu, es * nx * P));
+  d.w = dtype == BK_F64 ? (void*)d.plan->w64 : d.plan->wT;
+  const int64_t il = (int64_t)round_up(pr->nseg, 32) * SEG * nx * nx;
+  BK_TRY(dmalloc(&d.Kn, es * il));
+  BK_TRY(dmalloc(&d.Nn, es * il));
+  BK_TRY(dmalloc(&d.Aseg, es * (size_t)pr->nseg * nx * nx));
+  BK_TRY(dmalloc(&d.Agrp, es * (size_t)pr->ngrp * nx * nx));
+  if (ne > 0) {
+    BK_TRY(dmalloc(&d.Zc, es * ne * nx * P));
+    BK_TRY(dmalloc(&d.HWc, es * ne * nu * P));
+    BK_TRY(dmalloc(&d.Qc, es * ne * nx * P));
+    BK_TRY(dmalloc(&d.Sinv, es * NEM * NEM));
+  }
+  BK_TRY(dmalloc(&d.t1, es * (nx + nu) * P));
+  BK_TRY(dmalloc(&d.t2, es * (nx + nu) * P));
+  BK_TRY(dmalloc(&d.t3, es * (nx + nu) * P));
+  BK_TRY(dmalloc(&d.segb, es * (size_t)pr->nseg * nx));
+  BK_TRY(dmalloc(&d.grpb, es * (size_t)pr->ngrp * nx * 2));
+  return BK_OK;
+}
+
+static void free_opdata(OpData& d) {
+  if (d.plan) plan_destroy(d.plan);
+  void* ps[] = {d.xu, d.mu, d.Kn, d.Nn, d.Aseg, d.Agrp, d.Zc, d.HWc, d.Qc, d.Sinv, d.t1, d.t2, d.t3, d.segb, d.grpb};
+  for (void* p : ps) dfree(p);
+  d = OpData();
+}
+
+// --- linearisation ---------------------------------------------------------------------------
+template <typename T, int KIND>
+static bk_status lin_factors(Problem* pr, OpData& d, const double* z, cudaStream_t st) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  k_lin_nodes<T, KIND, NX, NU><<<nblk(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->d64.plan->w64, pr->s, (T*)d.Kn, (T*)d.Nn, (T*)d.xu);
+  BK_CHECK_LAUNCH();
+  k_lin_seg<T, NX><<<(pr->nseg + 127) / 128, 128, 0, st>>>((const T*)d.Nn, pr->L, pr->nseg, (T*)d.Aseg);
+  BK_CHECK_LAUNCH();
+  k_lin_grp<T, NX><<<(pr->ngrp + 127) / 128, 128, 0, st>>>((const T*)d.Aseg, pr->nseg, pr->ngrp, (T*)d.Agrp);
+  BK_CHECK_LAUNCH();
+  return BK_OK;
+}
+
+// Terminal Schur data of the KKT preconditioner (see precond_kkt).
+template <typename T, int KIND>
+static bk_status lin_schur(Problem* pr, OpData& d, cudaStream_t st) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  const int ne = pr->n_e;
+  if (ne == 0 || !pr->has_cost) return BK_OK;
+  const int64_t P = pr->P, L = pr->L;
+  const T s = (T)pr->s;
+  T* Zc = (T*)d.Zc;
+  T* HWc = (T*)d.HWc;
+  T* Qc = (T*)d.Qc;
+  T* unit = (T*)d.t1;   // n_x * P
+  T* bz = (T*)d.t2;     // n_x * P : B-tilde^T Z_r
+  T* g = (T*)d.t3;      // n_x * P : forcing
+  std::vector<double> S(ne * ne);
+  for (int r = 0; r < ne; ++r) {
+    k_unit<T><<<nblk(NX * P), 256, 0, st>>>(unit, NX * P, (int64_t)pr->term_idx[r] * P + (L - 1));
+    BK_CHECK_LAUNCH();
+    T* Z = Zc + (int64_t)r * NX * P;
+    BK_TRY((run_sweep<T, NX, 1>(pr, d, unit, nullptr, Z, bz, st)));
+    // W = Pu^T Z = -s Ju^T (B-tilde^T Z). k_pre_u with r_u = 0 and b = B-tilde^T Z gives
+    // yu = s Ju^T b / (s w) = -H~^{-1} W and g = Ju yu = -Ju H~^{-1} W.
+    T* HW = HWc + (int64_t)r * NU * P;
+    k_pre_u<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.w, s, (T)1, nullptr, bz, P, L, HW, g, T(1));
+    BK_CHECK_LAUNCH();
+    // Q = P^{-1} Pu HW: forward sweep with Y = 0 and forcing -Ju HW = Ju (-HW) = g
+    k_unit<T><<<nblk(NX * P), 256, 0, st>>>(unit, NX * P, -1);
+    BK_CHECK_LAUNCH();
+    T* Q = Qc + (int64_t)r * NX * P;
+    BK_TRY((run_sweep<T, NX, 0>(pr, d, unit, g, Q, nullptr, st)));
+  }
+  // HWc holds -H~^{-1} W here; the caller negates it once all columns are formed.
+  // S = E Q (host): S[r][c] = Q_c[term_idx[r]][N]
+  std::vector<T> hq(ne * ne);
+  for (int c = 0; c < ne; ++c)
+    for (int r = 0; r < ne; ++r)
+      BK_TRY_CUDA(cudaMemcpyAsync(&hq[r * ne + c], Qc + ((int64_t)c * NX + pr->term_idx[r]) * P + (L - 1), sizeof(T),
+                                  cudaMemcpyDeviceToHost, st));
+  BK_TRY_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < ne * ne; ++i) S[i] = (double)hq[i];
+  // invert S (n_e <= 4) by Gauss-Jordan with partial pivoting in FP64
+  std::vector<double> A(S), Inv(ne * ne, 0.0);
+  for (int i = 0; i < ne; ++i) Inv[i * ne + i] = 1.0;
+  for (int c = 0; c < ne; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < ne; ++r)
+      if (fabs(A[r * ne + c]) > fabs(A[piv * ne + c])) piv = r;
+    if (A[piv * ne + c] == 0.0) { set_error("terminal Schur complement is singular"); return BK_ERR_INFEASIBLE; }
+    for (int q = 0; q < ne; ++q) { std::swap(A[c * ne + q], A[piv * ne + q]); std::swap(Inv[c * ne + q], Inv[piv * ne + q]); }
+    const double ip = 1.0 / A[c * ne + c];
+    for (int q = 0; q < ne; ++q) { A[c * ne + q] *= ip; Inv[c * ne + q] *= ip; }
+    for (int r = 0; r < ne; ++r) {
+      if (r == c) continue;
+      const double f = A[r * ne + c];
+      for (int q = 0; q < ne; ++q) { A[r * ne + q] -= f * A[c * ne + q]; Inv[r * ne + q] -= f * Inv[c * ne + q]; }
+    }
+  }
+  std::vector<T> hs(NEM * NEM, T(0));
+  for (int i = 0; i < ne * ne; ++i) hs[i] = (T)Inv[i];
+  BK_TRY_CUDA(cudaMemcpyAsync(d.Sinv, hs.data(), sizeof(T) * ne * ne, cudaMemcpyHostToDevice, st));
+  BK_TRY_CUDA(cudaStreamSynchronize(st));
+  return BK_OK;
+}
+
+template <typename T>
+__global__ void k_negate(T* v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) v[i] = -v[i];
+}
+
+template <int KIND>
+static bk_status linearize_kind(Problem* pr, const double* z, cudaStream_t st) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  const int64_t P = pr->P;
+  // mu = s B^aT lambda (FP64)
+  BK_TRY(plan_apply_n(pr->d64.plan, z + (NX + NU) * P, pr->d64.mu, NX, true, pr->s, st));
+  BK_TRY((lin_factors<double, KIND>(pr, pr->d64, z, st)));
+  if (pr->dtype == BK_F32) {
+    k_convert<double, float><<<nblk(NX * P), 256, 0, st>>>((const double*)pr->d64.mu, (float*)pr->d32.mu, NX * P);
+    BK_CHECK_LAUNCH();
+    BK_TRY((lin_factors<float, KIND>(pr, pr->d32, z, st)));
+  }
+  pr->linearized = true;
+  if (pr->n_e > 0 && pr->has_cost) {
+    BK_TRY((lin_schur<double, KIND>(pr, pr->d64, st)));
+    k_negate<double><<<nblk((int64_t)pr->n_e * NU * P), 256, 0, st>>>((double*)pr->d64.HWc, (int64_t)pr->n_e * NU * P);
+    BK_CHECK_LAUNCH();
+    if (pr->dtype == BK_F32) {
+      BK_TRY((lin_schur<float, KIND>(pr, pr->d32, st)));
+      k_negate<float><<<nblk((int64_t)pr->n_e * NU * P), 256, 0, st>>>((float*)pr->d32.HWc, (int64_t)pr->n_e * NU * P);
+      BK_CHECK_LAUNCH();
+    }
+  }
+  return BK_OK;
+}
+
+bk_status problem_linearize(Problem* pr, const double* z, cudaStream_t st) {
+  BK_ARG(pr != nullptr && z != nullptr, "NULL problem or z_lin");
+  BK_DISPATCH_KIND(pr->kind, linearize_kind, pr, z, st);
+}
+
+// --- operator applies --------------------------------------------------------------------------
+template <typename T, int KIND>
+static bk_status apply_typed(Problem* pr, OpData& d, int op, const T* in, T* out, cudaStream_t st) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  const int64_t P = pr->P, L = pr->L;
+  T* t1 = (T*)d.t1;
+  T* t2 = (T*)d.t2;
+  T* t3 = (T*)d.t3;
+  if (op == BK_OP_STATE) {
+    k_jvp<T, KIND><<<nblk(L), 256, 0, st>>>((const T*)d.xu, in, nullptr, P, L, t1);
+    BK_CHECK_LAUNCH();
+    if (P > L) { k_zero_pad<T><<<nblk(NX * (P - L)), 256, 0, st>>>(t1, NX, P, L); BK_CHECK_LAUNCH(); }
+    BK_TRY(plan_apply_n(d.plan, t1, t2, NX, false, pr->s, st));
+    k_state_post<T, NX><<<nblk(NX * P), 256, 0, st>>>(in, t2, P, L, out);
+    BK_CHECK_LAUNCH();
+    return BK_OK;
+  }
+  k_jvp<T, KIND><<<nblk(L), 256, 0, st>>>((const T*)d.xu, in, in + NX * P, P, L, t1);
+  BK_CHECK_LAUNCH();
+  if (P > L) { k_zero_pad<T><<<nblk(NX * (P - L)), 256, 0, st>>>(t1, NX, P, L); BK_CHECK_LAUNCH(); }
+  BK_TRY(plan_apply_n(d.plan, t1, t2, NX, false, pr->s, st));
+  BK_TRY(plan_apply_n(d.plan, in + (NX + NU) * P, t3, NX, true, pr->s, st));
+  k_kkt_post<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.mu, (const T*)d.w, (T)pr->s, in, t2, t3, P, L,
+                                                term_spec(pr), (T)(pr->has_cost ? 1.0 : 0.0), out);
+  BK_CHECK_LAUNCH();
+  return BK_OK;
+}
+
+template <int KIND>
+static bk_status apply_kind(Problem* pr, OpData& d, int op, const void* in, void* out, cudaStream_t st) {
+  if (d.dtype == BK_F64) return apply_typed<double, KIND>(pr, d, op, (const double*)in, (double*)out, st);
+  return apply_typed<float, KIND>(pr, d, op, (const float*)in, (float*)out, st);
+}
+
+bk_status op_apply(Problem* pr, OpData& d, int op, const void* in, void* out, cudaStream_t st) {
+  BK_ARG(pr->linearized, "problem is not linearised (call bk_linearize first)");
+  BK_ARG(op == BK_OP_STATE || op == BK_OP_KKT, "unknown operator %d", op);
+  BK_DISPATCH_KIND(pr->kind, apply_kind, pr, d, op, in, out, st);
+}
+
+// --- preconditioner ---------------------------------------------------------------------------
+// K-tilde^{-1} r: t_lambda = P^{-T} r_x (with b = B-tilde^T t_lambda); yu = H~^{-1}(r_u - Pu^T
+// t_lambda); q = P^{-1}(r_lambda - Pu yu); y_nu = S^{-1}(E q - r_nu); y_u = yu + H~^{-1} W y_nu;
+// y_x = q - Q y_nu; y_lambda = t_lambda - Z y_nu.  (Pu = -s (B-tilde (x) I) J_u, H~ = s w I.)
+template <typename T, int KIND>
+static bk_status precond_typed(Problem* pr, OpData& d, int op, const T* in, T* out, int transpose, cudaStream_t st) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu, NV = NX + NU;
+  const int64_t P = pr->P, L = pr->L;
+  if (op == BK_OP_STATE) {
+    if (!transpose) return run_sweep<T, NX, 0>(pr, d, in, nullptr, out, nullptr, st);
+    return run_sweep<T, NX, 1>(pr, d, in, nullptr, out, nullptr, st);
+  }
+  BK_ARG(pr->has_cost, "the KKT preconditioner needs a control cost (problem kind has none)");
+  const T* rx = in;
+  const T* ru = in + NX * P;
+  const T* rl = in + NV * P;
+  const T* rnu = in + (NV + NX) * P;
+  T* yx = out;
+  T* yu = out + NX * P;
+  T* yl = out + NV * P;
+  T* ynu = out + (NV + NX) * P;
+  T* b = (T*)d.t1;
+  T* g = (T*)d.t2;
+  BK_TRY((run_sweep<T, NX, 1>(pr, d, rx, nullptr, yl, b, st)));
+  k_pre_u<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.w, (T)pr->s, (T)1, ru, b, P, L, yu, g, T(1));
+  BK_CHECK_LAUNCH();
+  BK_TRY((run_sweep<T, NX, 0>(pr, d, rl, g, yx, nullptr, st)));
+  if (pr->n_e > 0) {
+    k_pre_nu<T><<<1, 32, 0, st>>>(yx, rnu, (const T*)d.Sinv, P, L, term_spec(pr), ynu);
+    BK_CHECK_LAUNCH();
+    k_pre_fix<T, NX, NU><<<nblk(L), 256, 0, st>>>((const T*)d.Zc, (const T*)d.HWc, (const T*)d.Qc, ynu, pr->n_e, P, L, yx, yu, yl);
+    BK_CHECK_LAUNCH();
+  } else {
+    BK_TRY_CUDA(cudaMemsetAsync(ynu, 0, sizeof(T) * 32, st));
+  }
+  return BK_OK;
+}
+
+template <int KIND>
+static bk_status precond_kind(Problem* pr, OpData& d, int op, const void* in, void* out, int transpose, cudaStream_t st) {
+  if (d.dtype == BK_F64) return precond_typed<double, KIND>(pr, d, op, (const double*)in, (double*)out, transpose, st);
+  return precond_typed<float, KIND>(pr, d, op, (const float*)in, (float*)out, transpose, st);
+}
+
+bk_status op_precond(Problem* pr, OpData& d, int op, const void* in, void* out, int transpose, cudaStream_t st) {
+  BK_ARG(pr->linearized, "problem is not linearised (call bk_linearize first)");
+  BK_ARG(op == BK_OP_STATE || op == BK_OP_KKT, "unknown operator %d", op);
+  BK_DISPATCH_KIND(pr->kind, precond_kind, pr, d, op, in, out, transpose, st);
+}
+
+// --- residual -------------------------------------------------------------------------------
+template <int KIND>
+static bk_status residual_kind(Problem* pr, const double* z, double* F, double* wnorm, cudaStream_t st) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  const int64_t P = pr->P, L = pr->L;
+  OpData& d = pr->d64;
+  double* f = (double*)d.t1;
+  double* Bf = (double*)d.t2;
+  double* Mu = (double*)d.t3;
+  k_feval<KIND><<<nblk(P), 256, 0, st>>>(z, P, L, f);
+  BK_CHECK_LAUNCH();
+  BK_TRY(plan_apply_n(d.plan, f, Bf, NX, false, pr->s, st));
+  BK_TRY(plan_apply_n(d.plan, z + (NX + NU) * P, Mu, NX, true, pr->s, st));
+  X0Spec x0;
+  for (int m = 0; m < NXM; ++m) x0.x0[m] = pr->x0[m];
+  const int nb = 592;
+  k_resid_post<KIND><<<nb, 256, 0, st>>>(z, pr->d64.plan->w64, pr->s, Bf, Mu, P, L, term_spec(pr), x0,
+                                         pr->has_cost ? 1.0 : 0.0, F, pr->red);
+  BK_CHECK_LAUNCH();
+  if (wnorm) {
+    k_sum_partials<<<1, 256, 0, st>>>(pr->red, nb, pr->red + 1024);
+    BK_CHECK_LAUNCH();
+    BK_TRY_CUDA(cudaMemcpyAsync(pr->red_host, pr->red + 1024, sizeof(double), cudaMemcpyDeviceToHost, st));
+    BK_TRY_CUDA(cudaStreamSynchronize(st));
+    *wnorm = sqrt(pr->red_host[0]);
+  }
+  return BK_OK;
+}
+
+bk_status problem_residual(Problem* pr, const double* z, double* F, double* wnorm, cudaStream_t st) {
+  BK_DISPATCH_KIND(pr->kind, residual_kind, pr, z, F, wnorm, st);
+}
+
+template <int KIND>
+static bk_status wnorm_kind(Problem* pr, const double* F, double* wnorm, cudaStream_t st) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  const int nb = 592;
+  k_wnorm<NX, NU><<<nb, 256, 0, st>>>(F, pr->d64.plan->w64, pr->P, pr->L, pr->n_e, pr->red);
+  BK_CHECK_LAUNCH();
+  k_sum_partials<<<1, 256, 0, st>>>(pr->red, nb, pr->red + 1024);
+  BK_CHECK_LAUNCH();
+  BK_TRY_CUDA(cudaMemcpyAsync(pr->red_host, pr->red + 1024, sizeof(double), cudaMemcpyDeviceToHost, st));
+  BK_TRY_CUDA(cudaStreamSynchronize(st));
+  *wnorm = sqrt(pr->red_host[0]);
+  return BK_OK;
+}
+
+bk_status problem_wnorm(Problem* pr, const double* F, double* wnorm, cudaStream_t st) {
+  BK_DISPATCH_KIND(pr->kind, wnorm_kind, pr, F, wnorm, st);
+}
+
+// --- creation ---------------------------------------------------------------------------------
+static void problem_free(Problem* pr) {
+  if (!pr) return;
+  free_opdata(pr->d64);
+  free_opdata(pr->d32);
+  dfree(pr->F);
+  dfree(pr->red);
+  if (pr->red_host) cudaFreeHost(pr->red_host);
+  delete pr;
+}
+
+static bk_status problem_create(Problem** out, int kind, const double* params, int nparams, int64_t N, int dtype,
+                                double t0, double tf, cudaStream_t st) {
+  *out = nullptr;
+  BK_ARG(kind == BK_DBL_INT || kind == BK_ORBIT || kind == BK_BILINEAR, "unknown problem kind %d", kind);
+  BK_ARG(dtype == BK_F64 || dtype == BK_F32, "dtype must be BK_F64 or BK_F32");
+  BK_ARG(is_pow2(N) && N >= 4 && N <= (int64_t(1) << 24), "N must be a power of two in [4, 2^24]");
+  BK_ARG(tf > t0, "tf must be > t0");
+  BK_ARG(nparams >= 0 && nparams <= 4 && (nparams == 0 || params), "bad params");
+  Problem* pr = new Problem();
+  pr->kind = kind;
+  pr->dtype = dtype;
+  pr->N = N;
+  pr->L = N + 1;
+  pr->P = round_up(N + 1, 32);
+  pr->t0 = t0;
+  pr->tf = tf;
+  pr->s = 0.5 * (tf - t0);
+  for (int i = 0; i < nparams; ++i) pr->params[i] = params[i];
+  if (kind == BK_DBL_INT) {
+    pr->n_x = 2; pr->n_u = 1; pr->n_e = 2;
+    pr->x0[0] = 0; pr->x0[1] = 0;
+    pr->term_idx[0] = 0; pr->term_val[0] = 1.0;
+    pr->term_idx[1] = 1; pr->term_val[1] = 0.0;
+    pr->has_cost = true;
+  } else if (kind == BK_ORBIT) {
+    if (nparams < 2) { delete pr; set_error("BK_ORBIT needs params {a_nominal, r_f}"); return BK_ERR_ARG; }
+    const double rf = params[1];
+    if (!(rf > 0)) { delete pr; set_error("r_f must be > 0"); return BK_ERR_ARG; }
+    pr->n_x = 4; pr->n_u = 2; pr->n_e = 3;
+    pr->x0[0] = 1; pr->x0[1] = 0; pr->x0[2] = 0; pr->x0[3] = 1;
+    pr->term_idx[0] = 0; pr->term_val[0] = rf;
+    pr->term_idx[1] = 2; pr->term_val[1] = 0.0;
+    pr->term_idx[2] = 3; pr->term_val[2] = 1.0 / sqrt(rf);
+    pr->has_cost = true;
+  } else {
+    pr->n_x = 1; pr->n_u = 1; pr->n_e = 0;
+    pr->x0[0] = nparams >= 1 ? params[0] : 1.0;
+    pr->has_cost = false;
+  }
+  pr->nseg = (int)((pr->L + SEG - 1) / SEG);
+  pr->ngrp = (pr->nseg + GRP - 1) / GRP;
+  bk_status s = alloc_opdata(pr, pr->d64, BK_F64);
+  if (s == BK_OK && dtype == BK_F32) s = alloc_opdata(pr, pr->d32, BK_F32);
+  if (s == BK_OK) s = dmalloc((void**)&pr->F, sizeof(double) * pr->kkt_len());
+  if (s == BK_OK) s = dmalloc((void**)&pr->red, sizeof(double) * 2048);
+  if (s == BK_OK && cudaMallocHost((void**)&pr->red_host, sizeof(double) * 512) != cudaSuccess) {
+    set_error("cudaMallocHost failed");
+    s = BK_ERR_OOM;
+  }
+  if (s == BK_OK && cudaStreamSynchronize(st) != cudaSuccess) { set_error("sync failed"); s = BK_ERR_CUDA; }
+  if (s != BK_OK) { problem_free(pr); return s; }
+  *out = pr;
+  return BK_OK;
+}
+
+}  // namespace bk
+
+// ---------------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------------
+extern "C" {
+
+bk_status bk_problem_create(bk_problem** prob, int kind, const double* params, int nparams, int64_t N,
+                            bk_dtype dtype, double t0, double tf, void* stream) {
+  BK_ARG(prob != nullptr, "problem output pointer is NULL");
+  bk::Problem* p = nullptr;
+  bk_status s = bk::problem_create(&p, kind, params, nparams, N, (int)dtype, t0, tf, (cudaStream_t)stream);
+  *prob = reinterpret_cast<bk_problem*>(p);
+  return s;
+}
+
+void bk_problem_destroy(bk_problem* prob) { bk::problem_free(reinterpret_cast<bk::Problem*>(prob)); }
+
+bk_status bk_problem_info(const bk_problem* prob, int* n_x, int* n_u, int* n_e, int64_t* pitch, int64_t* kkt_len,
+                          int64_t* state_len) {
+  BK_ARG(prob != nullptr, "problem is NULL");
+  const bk::Problem* p = reinterpret_cast<const bk::Problem*>(prob);
+  if (n_x) *n_x = p->n_x;
+  if (n_u) *n_u = p->n_u;
+  if (n_e) *n_e = p->n_e;
+  if (pitch) *pitch = p->P;
+  if (kkt_len) *kkt_len = p->kkt_len();
+  if (state_len) *state_len = p->state_len();
+  return BK_OK;
+}
+
+bk_status bk_linearize(bk_problem* prob, const double* z_lin, void* stream) {
+  BK_ARG(prob != nullptr, "problem is NULL");
+  BK_ARG(((uintptr_t)z_lin & 15) == 0, "z_lin must be 16-byte aligned");
+  return bk::problem_linearize(reinterpret_cast<bk::Problem*>(prob), z_lin, (cudaStream_t)stream);
+}
+
+bk_status kkt_apply(bk_problem* prob, int op, const void* in, void* out, void* stream) {
+  BK_ARG(prob != nullptr && in != nullptr && out != nullptr, "NULL argument");
+  BK_ARG(in != out, "in and out must not alias");
+  bk::Problem* p = reinterpret_cast<bk::Problem*>(prob);
+  return bk::op_apply(p, p->work(), op, in, out, (cudaStream_t)stream);
+}
+
+bk_status precond_apply(bk_problem* prob, int op, const void* in, void* out, int transpose, void* stream) {
+  BK_ARG(prob != nullptr && in != nullptr && out != nullptr, "NULL argument");
+  BK_ARG(in != out, "in and out must not alias");
+  bk::Problem* p = reinterpret_cast<bk::Problem*>(prob);
+  return bk::op_precond(p, p->work(), op, in, out, transpose, (cudaStream_t)stream);
+}
+
+bk_status bk_kkt_residual(bk_problem* prob, const double* z, double* F_out, double* wnorm, void* stream) {
+  BK_ARG(prob != nullptr && z != nullptr && F_out != nullptr, "NULL argument");
+  return bk::problem_residual(reinterpret_cast<bk::Problem*>(prob), z, F_out, wnorm, (cudaStream_t)stream);
+}
+
+}  // extern "C"

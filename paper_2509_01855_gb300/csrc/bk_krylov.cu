@@ -1,0 +1,312 @@
+// Right-preconditioned restarted GMRES (Algorithm 2 / FastLinSol of the paper: GMRES on
+// A P^{-1} Upsilon = beta, then chi = P^{-1} Upsilon), with classical Gram-Schmidt applied
+// twice (CGS2) for the Arnoldi basis.
+//
+// Device work per iteration: one preconditioner apply, one operator apply, two fused multi-dot
+// passes and two fused multi-axpy passes over the basis, and a norm. Dot products accumulate in
+// FP64 with a fixed block count and a fixed reduction order, so results do not depend on
+// scheduling. The (m+1) x m Hessenberg matrix and its Givens rotations live on the host
+// (FP64); the iteration reads back j+2 numbers per step.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "bk_krylov.cuh"
+
+namespace bk {
+
+static constexpr int DOT_BLOCKS = 296;   // 2 blocks per SM on 148+ SMs, fixed for determinism
+static constexpr int MAXM = 100;
+
+// partial[b * (nv) + i] = sum over block b's slice of V_i . w   (i < nv), FP64
+template <typename T>
+__global__ void __launch_bounds__(256) k_multidot(const T* __restrict__ V, int64_t ld, int nv, const T* __restrict__ w,
+                                                  int64_t n, double* __restrict__ partial) {
+  __shared__ double red[8][MAXM + 1];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  for (int i0 = 0; i0 < nv; i0 += 8) {
+    const int cnt = nv - i0 < 8 ? nv - i0 : 8;
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+      const double wk = (double)w[k];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q < cnt) acc[q] += (double)V[(int64_t)(i0 + q) * ld + k] * wk;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      double a = acc[q];
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      double a = 0.0;
+      for (int wp = 0; wp < (int)(blockDim.x >> 5); ++wp) a += red[wp][threadIdx.x];
+      partial[(int64_t)blockIdx.x * nv + i0 + threadIdx.x] = a;
+    }
+    __syncthreads();
+  }
+}
+
+// out[i] = sum_b partial[b * nv + i]
+__global__ void k_reduce_cols(const double* __restrict__ partial, int nb, int nv, double* __restrict__ out) {
+  const int i = blockIdx.x;
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) a += partial[(int64_t)b * nv + i];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) out[i] = t;
+  }
+}
+
+// w <- alpha * w + beta * sum_i c[i] V_i   (c on the device, FP64)
+template <typename T>
+__global__ void k_multiaxpy(const T* __restrict__ V, int64_t ld, int nv, const double* __restrict__ c, double cscale,
+                            T* __restrict__ w, double alpha, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double a = alpha == 0.0 ? 0.0 : alpha * (double)w[k];
+    for (int i = 0; i < nv; ++i) a += cscale * c[i] * (double)V[(int64_t)i * ld + k];
+    w[k] = (T)a;
+  }
+}
+
+// y <- a * x + b * y  (a, b host scalars)
+template <typename T>
+__global__ void k_axpby(const T* __restrict__ x, double a, T* __restrict__ y, double b, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    y[k] = (T)(a * (double)x[k] + (b == 0.0 ? 0.0 : b * (double)y[k]));
+}
+
+// y <- x * (1 / c[0])  (scale by a device scalar)
+template <typename T>
+__global__ void k_scale_inv(const T* __restrict__ x, const double* __restrict__ c, T* __restrict__ y, int64_t n) {
+  const double inv = 1.0 / c[0];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    y[k] = (T)((double)x[k] * inv);
+}
+
+template <typename T>
+static bk_status dots(const T* V, int64_t ld, int nv, const T* w, int64_t n, double* partial, double* out, cudaStream_t st) {
+  k_multidot<T><<<DOT_BLOCKS, 256, 0, st>>>(V, ld, nv, w, n, partial);
+  BK_CHECK_LAUNCH();
+  k_reduce_cols<<<nv, 256, 0, st>>>(partial, DOT_BLOCKS, nv, out);
+  BK_CHECK_LAUNCH();
+  return BK_OK;
+}
+
+static inline int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
+}
+
+size_t gmres_workspace_bytes(int64_t n, int m, int dtype) {
+  const size_t es = dtype_size(dtype);
+  const int64_t ld = round_up(n, 64);
+  size_t b = es * (size_t)ld * (m + 1);      // basis
+  b += es * (size_t)ld * 2;                  // z (preconditioned) and r / correction
+  b += sizeof(double) * (size_t)DOT_BLOCKS * (MAXM + 1);  // dot partials
+  b += sizeof(double) * 4 * (MAXM + 2);      // device scalars
+  return b + 1024;
+}
+
+template <typename T>
+static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, const bk_krylov_opts& o,
+                            bk_krylov_info* info, void* ws, cudaStream_t st, double* hostbuf) {
+  const int64_t n = op == BK_OP_KKT ? pr->kkt_len() : pr->state_len();
+  const int m = o.restart;
+  const int64_t ld = round_up(n, 64);
+  char* p = (char*)ws;
+  auto carve = [&](size_t bytes) { char* r = p; p += (bytes + 255) / 256 * 256; return (void*)r; };
+  T* V = (T*)carve(sizeof(T) * ld * (m + 1));
+  T* z = (T*)carve(sizeof(T) * ld);
+  T* r = (T*)carve(sizeof(T) * ld);
+  double* partial = (double*)carve(sizeof(double) * DOT_BLOCKS * (MAXM + 1));
+  double* dvec = (double*)carve(sizeof(double) * 4 * (MAXM + 2));
+  double* h1 = dvec;
+  double* h2 = dvec + (MAXM + 2);
+  double* yv = dvec + 2 * (MAXM + 2);
+  const int g = grid_for(n);
+
+  // ||b||
+  BK_TRY(dots<T>(b, ld, 1, b, n, partial, h1, st));
+  BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double), cudaMemcpyDeviceToHost, st));
+  BK_TRY_CUDA(cudaStreamSynchronize(st));
+  const double bnorm = sqrt(hostbuf[0]);
+  BK_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
+  info->iterations = 0;
+  info->restarts = 0;
+  info->rel_resid = 0.0;
+  info->converged = 0;
+  if (bnorm == 0.0) { info->converged = 1; return BK_OK; }
+  const double target = o.rtol * bnorm;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  int total = 0;
+  double resid = bnorm;
+  bool first = true;
+  while (true) {
+    // r = b - A x (x = 0 on the first cycle)
+    if (first) {
+      k_axpby<T><<<g, 256, 0, st>>>(b, 1.0, r, 0.0, n);
+      BK_CHECK_LAUNCH();
+    } else {
+      BK_TRY(op_apply(pr, d, op, x, r, st));
+      k_axpby<T><<<g, 256, 0, st>>>(b, 1.0, r, -1.0, n);
+      BK_CHECK_LAUNCH();
+    }
+    first = false;
+    BK_TRY(dots<T>(r, ld, 1, r, n, partial, h1, st));
+    BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    BK_TRY_CUDA(cudaStreamSynchronize(st));
+    const double beta = sqrt(hostbuf[0]);
+    resid = beta;
+    if (beta <= target || total >= o.max_iter) break;
+    k_axpby<T><<<g, 256, 0, st>>>(r, 1.0 / beta, V, 0.0, n);
+    BK_CHECK_LAUNCH();
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int j = 0;
+    for (; j < m && total < o.max_iter; ++j) {
+      T* vj = V + (int64_t)j * ld;
+      T* w = V + (int64_t)(j + 1) * ld;
+      if (o.use_precond) {
+        BK_TRY(op_precond(pr, d, op, vj, z, 0, st));
+        BK_TRY(op_apply(pr, d, op, z, w, st));
+      } else {
+        BK_TRY(op_apply(pr, d, op, vj, w, st));
+      }
+      // CGS2
+      BK_TRY(dots<T>(V, ld, j + 1, w, n, partial, h1, st));
+      k_multiaxpy<T><<<g, 256, 0, st>>>(V, ld, j + 1, h1, -1.0, w, 1.0, n);
+      BK_CHECK_LAUNCH();
+      BK_TRY(dots<T>(V, ld, j + 1, w, n, partial, h2, st));
+      k_multiaxpy<T><<<g, 256, 0, st>>>(V, ld, j + 1, h2, -1.0, w, 1.0, n);
+      BK_CHECK_LAUNCH();
+      BK_TRY(dots<T>(w, ld, 1, w, n, partial, h2 + (j + 1), st));
+      BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
+      BK_TRY_CUDA(cudaMemcpyAsync(hostbuf + (MAXM + 2), h2, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, st));
+      BK_TRY_CUDA(cudaStreamSynchronize(st));
+      const double hnext = sqrt(hostbuf[(MAXM + 2) + j + 1]);
+      for (int i = 0; i <= j; ++i) H[i * m + j] = hostbuf[i] + hostbuf[(MAXM + 2) + i];
+      H[(j + 1) * m + j] = hnext;
+      ++total;
+      // normalise v_{j+1}
+      if (hnext > 0.0) {
+        hostbuf[0] = hnext;
+        BK_TRY_CUDA(cudaMemcpyAsync(h1, hostbuf, sizeof(double), cudaMemcpyHostToDevice, st));
+        k_scale_inv<T><<<g, 256, 0, st>>>(w, h1, w, n);
+        BK_CHECK_LAUNCH();
+      }
+      // Givens
+      for (int i = 0; i < j; ++i) {
+        const double a = H[i * m + j], c = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * c;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[j * m + j], c = H[(j + 1) * m + j];
+      const double den = hypot(a, c);
+      cs[j] = den == 0.0 ? 1.0 : a / den;
+      sn[j] = den == 0.0 ? 0.0 : c / den;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      resid = fabs(gv[j + 1]);
+      if (resid <= target || hnext == 0.0) { ++j; break; }
+    }
+    // y = H(0:j,0:j)^{-1} g
+    for (int i = j - 1; i >= 0; --i) {
+      double a = gv[i];
+      for (int q = i + 1; q < j; ++q) a -= H[i * m + q] * y[q];
+      y[i] = a / H[i * m + i];
+    }
+    BK_TRY_CUDA(cudaMemcpyAsync(yv, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st));
+    // x += M^{-1} (V y)
+    k_multiaxpy<T><<<g, 256, 0, st>>>(V, ld, j, yv, 1.0, r, 0.0, n);
+    BK_CHECK_LAUNCH();
+    if (o.use_precond) {
+      BK_TRY(op_precond(pr, d, op, r, z, 0, st));
+      k_axpby<T><<<g, 256, 0, st>>>(z, 1.0, x, 1.0, n);
+    } else {
+      k_axpby<T><<<g, 256, 0, st>>>(r, 1.0, x, 1.0, n);
+    }
+    BK_CHECK_LAUNCH();
+    ++info->restarts;
+    if (total >= o.max_iter) {
+      // final explicit residual
+      BK_TRY(op_apply(pr, d, op, x, r, st));
+      k_axpby<T><<<g, 256, 0, st>>>(b, 1.0, r, -1.0, n);
+      BK_CHECK_LAUNCH();
+      BK_TRY(dots<T>(r, ld, 1, r, n, partial, h1, st));
+      BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double), cudaMemcpyDeviceToHost, st));
+      BK_TRY_CUDA(cudaStreamSynchronize(st));
+      resid = sqrt(hostbuf[0]);
+      break;
+    }
+  }
+  info->iterations = total;
+  info->rel_resid = resid / bnorm;
+  info->converged = resid <= target ? 1 : 0;
+  return BK_OK;
+}
+
+bk_status gmres(Problem* pr, OpData& d, int op, const void* b, void* x, const bk_krylov_opts& o, bk_krylov_info* info,
+                void* ws, cudaStream_t st) {
+  BK_ARG(o.restart >= 1 && o.restart <= MAXM, "restart must be in [1, %d]", MAXM);
+  BK_ARG(o.max_iter >= 1, "max_iter must be >= 1");
+  BK_ARG(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be 256-byte aligned");
+  if (d.dtype == BK_F64)
+    return gmres_impl<double>(pr, d, op, (const double*)b, (double*)x, o, info, ws, st, pr->red_host);
+  return gmres_impl<float>(pr, d, op, (const float*)b, (float*)x, o, info, ws, st, pr->red_host);
+}
+
+bk_krylov_opts krylov_defaults() {
+  bk_krylov_opts o;
+  o.rtol = 1e-10;
+  o.restart = 30;
+  o.max_iter = 300;
+  o.use_precond = 1;
+  return o;
+}
+
+}  // namespace bk
+
+extern "C" {
+
+size_t bk_krylov_workspace_bytes(const bk_problem* prob, int op, int restart) {
+  const bk::Problem* p = reinterpret_cast<const bk::Problem*>(prob);
+  if (!p) return 0;
+  if (restart <= 0) restart = 30;
+  const int64_t n = op == BK_OP_KKT ? p->kkt_len() : p->state_len();
+  return bk::gmres_workspace_bytes(n, restart, p->dtype);
+}
+
+bk_status krylov_solve(bk_problem* prob, int op, const void* rhs, void* sol, const bk_krylov_opts* opts,
+                       bk_krylov_info* info, void* workspace, void* stream) {
+  BK_ARG(prob != nullptr && rhs != nullptr && sol != nullptr && info != nullptr, "NULL argument");
+  BK_ARG(op == BK_OP_STATE || op == BK_OP_KKT, "unknown operator %d", op);
+  bk::Problem* p = reinterpret_cast<bk::Problem*>(prob);
+  bk_krylov_opts o = opts ? *opts : bk::krylov_defaults();
+  if (o.rtol <= 0) o.rtol = 1e-10;
+  if (o.restart <= 0) o.restart = 30;
+  if (o.max_iter <= 0) o.max_iter = 300;
+  memset(info, 0, sizeof(*info));
+  BK_TRY(bk::gmres(p, p->work(), op, rhs, sol, o, info, workspace, (cudaStream_t)stream));
+  if (!info->converged) {
+    bk::set_error("GMRES stopped after %d iterations at relative residual %.3e", info->iterations, info->rel_resid);
+    return BK_ERR_NOT_CONVERGED;
+  }
+  return BK_OK;
+}
+
+}  // extern "C"

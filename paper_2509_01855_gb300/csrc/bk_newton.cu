@@ -1,0 +1,228 @@
+// Newton-Lagrange driver of the discretised problem (Eq. Prob-PNa).
+//
+// The paper reports SQP iteration counts (Table tab:m) but does not describe its outer loop.
+// This driver takes Newton's method on the KKT conditions F(z, y) = [grad J + G^T y ; c ; e] = 0
+// with the exact Lagrangian Hessian, each step solved by the Birkhoff-preconditioned GMRES, and
+// a backtracking line search (alpha = 1, 1/2, ...; Armijo constant 1e-4) on the quadrature-
+// weighted norm ||F||_W^2 = sum w c^2 + sum g^2 / w + |e|^2, which does not grow with N.
+// The residual, the line search and (for BK_F32 problems) the iterative-refinement residual are
+// FP64; BK_F32 problems run the GMRES iterations and their operator applies in FP32.
+#include <math.h>
+#include <string.h>
+
+#include "bk_krylov.cuh"
+
+namespace bk {
+
+template <typename Tin, typename Tout>
+__global__ void k_cast(const Tin* __restrict__ a, Tout* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (Tout)a[i];
+}
+
+// y = a x + b y (FP64)
+__global__ void k_axpby64(const double* __restrict__ x, double a, double* __restrict__ y, double b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + (b == 0.0 ? 0.0 : b * y[i]);
+}
+
+// y += (double) x (x float)
+__global__ void k_acc32(const float* __restrict__ x, double* __restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += (double)x[i];
+}
+
+// z_t = z + alpha d
+__global__ void k_step(const double* __restrict__ z, const double* __restrict__ d, double alpha,
+                       double* __restrict__ zt, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    zt[i] = z[i] + alpha * d[i];
+}
+
+// sum of squares partials (FP64)
+__global__ void k_sumsq(const double* __restrict__ x, int64_t n, double* __restrict__ partial) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a += x[i] * x[i];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  }
+}
+
+static inline int g1(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
+}
+
+__global__ void k_sum_block(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += partial[i];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) out[0] = t;
+  }
+}
+
+// ||x||_2 (FP64, fixed reduction order), synchronous.
+static bk_status norm2(Problem* pr, const double* x, int64_t n, double* out, cudaStream_t st) {
+  const int nb = 592;
+  k_sumsq<<<nb, 256, 0, st>>>(x, n, pr->red);
+  BK_CHECK_LAUNCH();
+  k_sum_block<<<1, 256, 0, st>>>(pr->red, nb, pr->red + 1024);
+  BK_CHECK_LAUNCH();
+  BK_TRY_CUDA(cudaMemcpyAsync(pr->red_host, pr->red + 1024, sizeof(double), cudaMemcpyDeviceToHost, st));
+  BK_TRY_CUDA(cudaStreamSynchronize(st));
+  *out = sqrt(pr->red_host[0]);
+  return BK_OK;
+}
+
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t newton_workspace(const Problem* pr, int restart) {
+  const int64_t n = pr->kkt_len();
+  size_t b = 0;
+  b += 4 * align256(sizeof(double) * n);   // d, zt, rhs, r
+  if (pr->dtype == BK_F32) b += 2 * align256(sizeof(float) * n);
+  b += align256(gmres_workspace_bytes(n, restart, pr->dtype));
+  return b + 1024;
+}
+
+static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk_newton_info* info, void* ws,
+                             cudaStream_t st) {
+  const int64_t n = pr->kkt_len();
+  char* p = (char*)ws;
+  auto carve = [&](size_t bytes) { char* r = p; p += align256(bytes); return (void*)r; };
+  double* d = (double*)carve(sizeof(double) * n);
+  double* zt = (double*)carve(sizeof(double) * n);
+  double* rhs = (double*)carve(sizeof(double) * n);
+  double* r = (double*)carve(sizeof(double) * n);
+  float* r32 = nullptr;
+  float* d32 = nullptr;
+  if (pr->dtype == BK_F32) {
+    r32 = (float*)carve(sizeof(float) * n);
+    d32 = (float*)carve(sizeof(float) * n);
+  }
+  void* gws = carve(gmres_workspace_bytes(n, o.restart, pr->dtype));
+  double* F = pr->F;
+  const int g = g1(n);
+  bk_krylov_opts ko;
+  ko.restart = o.restart;
+  ko.max_iter = o.max_krylov;
+  ko.use_precond = 1;
+  double phi = 0.0;
+  BK_TRY(problem_residual(pr, z, F, &phi, st));
+  info->residual0 = phi;
+  info->residual = phi;
+  int it = 0;
+  while (phi > o.tol && it < o.max_iter) {
+    BK_TRY(problem_linearize(pr, z, st));
+    k_axpby64<<<g, 256, 0, st>>>(F, -1.0, rhs, 0.0, n);
+    BK_CHECK_LAUNCH();
+    bk_krylov_info ki;
+    if (pr->dtype == BK_F64) {
+      ko.rtol = o.krylov_rtol;
+      BK_TRY(gmres(pr, pr->d64, BK_OP_KKT, rhs, d, ko, &ki, gws, st));
+      info->krylov_iterations += ki.iterations;
+      info->kkt_solves += 1;
+    } else {
+      // FP32 GMRES inside FP64 iterative refinement
+      ko.rtol = o.krylov_rtol;
+      double rn0 = 0.0;
+      BK_TRY(norm2(pr, rhs, n, &rn0, st));
+      BK_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n, st));
+      k_axpby64<<<g, 256, 0, st>>>(rhs, 1.0, r, 0.0, n);
+      BK_CHECK_LAUNCH();
+      for (int sweep = 0; sweep < o.max_refine; ++sweep) {
+        k_cast<double, float><<<g, 256, 0, st>>>(r, r32, n);
+        BK_CHECK_LAUNCH();
+        BK_TRY(gmres(pr, pr->d32, BK_OP_KKT, r32, d32, ko, &ki, gws, st));
+        info->krylov_iterations += ki.iterations;
+        info->kkt_solves += 1;
+        k_acc32<<<g, 256, 0, st>>>(d32, d, n);
+        BK_CHECK_LAUNCH();
+        // r = rhs - K d (FP64)
+        BK_TRY(op_apply(pr, pr->d64, BK_OP_KKT, d, r, st));
+        k_axpby64<<<g, 256, 0, st>>>(rhs, 1.0, r, -1.0, n);
+        BK_CHECK_LAUNCH();
+        double rn = 0.0;
+        BK_TRY(norm2(pr, r, n, &rn, st));
+        if (rn <= o.ir_rtol * rn0) break;
+      }
+    }
+    // backtracking line search on ||F||_W
+    double alpha = 1.0, phit = 0.0;
+    int bt = 0;
+    for (;;) {
+      k_step<<<g, 256, 0, st>>>(z, d, alpha, zt, n);
+      BK_CHECK_LAUNCH();
+      BK_TRY(problem_residual(pr, zt, F, &phit, st));
+      if (phit <= (1.0 - 1e-4 * alpha) * phi || bt >= 30) break;
+      alpha *= 0.5;
+      ++bt;
+    }
+    info->backtracks += bt;
+    if (!(phit <= (1.0 - 1e-4 * alpha) * phi)) {
+      info->iterations = it;
+      info->residual = phi;
+      set_error("line search failed after %d halvings at ||F||_W = %.3e", bt, phi);
+      return BK_ERR_INFEASIBLE;
+    }
+    BK_TRY_CUDA(cudaMemcpyAsync(z, zt, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    phi = phit;
+    ++it;
+  }
+  BK_TRY_CUDA(cudaStreamSynchronize(st));
+  info->iterations = it;
+  info->residual = phi;
+  info->converged = phi <= o.tol ? 1 : 0;
+  return BK_OK;
+}
+
+}  // namespace bk
+
+extern "C" {
+
+size_t bk_newton_workspace_bytes(const bk_problem* prob, int restart) {
+  const bk::Problem* p = reinterpret_cast<const bk::Problem*>(prob);
+  if (!p) return 0;
+  if (restart <= 0) restart = 30;
+  return bk::newton_workspace(p, restart);
+}
+
+bk_status newton_solve(bk_problem* prob, double* z_inout, const bk_newton_opts* opts, bk_newton_info* info,
+                       void* workspace, void* stream) {
+  BK_ARG(prob != nullptr && z_inout != nullptr && info != nullptr, "NULL argument");
+  BK_ARG(workspace != nullptr && ((uintptr_t)workspace & 255) == 0, "workspace must be 256-byte aligned");
+  bk::Problem* p = reinterpret_cast<bk::Problem*>(prob);
+  BK_ARG(p->has_cost, "newton_solve needs a problem kind with a cost (BK_DBL_INT, BK_ORBIT)");
+  bk_newton_opts o;
+  memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.tol <= 0) o.tol = 1e-10;
+  if (o.max_iter <= 0) o.max_iter = 30;
+  if (o.krylov_rtol <= 0) o.krylov_rtol = p->dtype == BK_F64 ? 1e-12 : 1e-5;
+  if (o.restart <= 0) o.restart = 30;
+  if (o.max_krylov <= 0) o.max_krylov = 300;
+  if (o.ir_rtol <= 0) o.ir_rtol = 1e-10;
+  if (o.max_refine <= 0) o.max_refine = 10;
+  memset(info, 0, sizeof(*info));
+  BK_TRY(bk::newton_impl(p, z_inout, o, info, workspace, (cudaStream_t)stream));
+  if (!info->converged) {
+    bk::set_error("Newton stopped after %d iterations at ||F||_W = %.3e", info->iterations, info->residual);
+    return BK_ERR_NOT_CONVERGED;
+  }
+  return BK_OK;
+}
+
+}  // extern "C"

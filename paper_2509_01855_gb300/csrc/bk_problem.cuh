@@ -1,0 +1,163 @@
+// Problem object, dynamics device functions and sweep/operator declarations (internal).
+//
+// Discretisation (Eq. Prob-PNa with V = f(X, U) eliminated and x^a fixed):
+//   c(X, U) = X - x0 (x) 1 - s (B^a (x) I) f(X, U),  e(X) = X[term, N] - target,
+//   J = s sum_i w_i F(x_i, u_i).
+// KKT vectors (component-major, pitch P per block): [X | U | lambda | nu (padded to 32)].
+#pragma once
+
+#include "bk_common.cuh"
+#include "bk_plan.cuh"
+
+namespace bk {
+
+constexpr int NXM = 4;   // largest state dimension of the compiled problem kinds
+constexpr int NUM = 2;   // largest control dimension
+constexpr int NEM = 4;   // largest terminal-condition count
+constexpr int SEG = 32;  // nodes per sweep segment (one thread each)
+constexpr int GRP = 32;  // segments per sweep group
+
+// ---------------------------------------------------------------------------------------------
+// Dynamics of the compiled problem kinds (FP64 or FP32 arithmetic).
+// ---------------------------------------------------------------------------------------------
+template <int KIND> struct Dyn;
+
+// Minimum-energy double integrator: x = (p, v), x' = (v, u), F = u^2 / 2.
+template <> struct Dyn<BK_DBL_INT> {
+  static constexpr int nx = 2, nu = 1;
+  template <typename T> __device__ static void f(const T* x, const T* u, T* fx) {
+    fx[0] = x[1];
+    fx[1] = u[0];
+  }
+  template <typename T> __device__ static void jac(const T* x, const T* u, T* Jx, T* Ju) {
+    Jx[0] = 0; Jx[1] = 1; Jx[2] = 0; Jx[3] = 0;
+    Ju[0] = 0; Ju[1] = 1;
+  }
+  // H[(nx+nu)^2] = sum_m mu_m Hess f_m (zero: f is linear)
+  template <typename T> __device__ static void hess(const T* x, const T* u, const T* mu, T* H) {
+    for (int i = 0; i < 9; ++i) H[i] = 0;
+  }
+};
+
+// Planar orbit in polar coordinates with thrust-vector control (dynamics of Eq. ot):
+// x = (r, theta, v_r, v_theta), u = (u_r, u_theta).
+template <> struct Dyn<BK_ORBIT> {
+  static constexpr int nx = 4, nu = 2;
+  template <typename T> __device__ static void f(const T* x, const T* u, T* fx) {
+    const T r = x[0], vr = x[2], vt = x[3];
+    const T ir = T(1) / r;
+    fx[0] = vr;
+    fx[1] = vt * ir;
+    fx[2] = vt * vt * ir - ir * ir + u[0];
+    fx[3] = -vr * vt * ir + u[1];
+  }
+  template <typename T> __device__ static void jac(const T* x, const T* u, T* Jx, T* Ju) {
+    const T r = x[0], vr = x[2], vt = x[3];
+    const T ir = T(1) / r, ir2 = ir * ir;
+    for (int i = 0; i < 16; ++i) Jx[i] = 0;
+    Jx[0 * 4 + 2] = 1;
+    Jx[1 * 4 + 0] = -vt * ir2;
+    Jx[1 * 4 + 3] = ir;
+    Jx[2 * 4 + 0] = -vt * vt * ir2 + T(2) * ir2 * ir;
+    Jx[2 * 4 + 3] = T(2) * vt * ir;
+    Jx[3 * 4 + 0] = vr * vt * ir2;
+    Jx[3 * 4 + 2] = -vt * ir;
+    Jx[3 * 4 + 3] = -vr * ir;
+    for (int i = 0; i < 8; ++i) Ju[i] = 0;
+    Ju[2 * 2 + 0] = 1;
+    Ju[3 * 2 + 1] = 1;
+  }
+  template <typename T> __device__ static void hess(const T* x, const T* u, const T* mu, T* H) {
+    const T r = x[0], vr = x[2], vt = x[3];
+    const T ir = T(1) / r, ir2 = ir * ir, ir3 = ir2 * ir;
+    const T mth = mu[1], mvr = mu[2], mvt = mu[3];
+    for (int i = 0; i < 36; ++i) H[i] = 0;
+    const int R = 0, VR = 2, VT = 3;
+    T hrr = mth * T(2) * vt * ir3 + mvr * (T(2) * vt * vt * ir3 - T(6) * ir2 * ir2) +
+            mvt * (-T(2) * vr * vt * ir3);
+    T hrvt = mth * (-ir2) + mvr * (-T(2) * vt * ir2) + mvt * (vr * ir2);
+    T hrvr = mvt * (vt * ir2);
+    T hvtvt = mvr * (T(2) * ir);
+    T hvrvt = mvt * (-ir);
+    H[R * 6 + R] = hrr;
+    H[R * 6 + VT] = hrvt; H[VT * 6 + R] = hrvt;
+    H[R * 6 + VR] = hrvr; H[VR * 6 + R] = hrvr;
+    H[VT * 6 + VT] = hvtvt;
+    H[VR * 6 + VT] = hvrvt; H[VT * 6 + VR] = hvrvt;
+  }
+};
+
+// Scalar bilinear x' = u x (no cost): linearised at (X, U) the state Jacobian is diag(U).
+template <> struct Dyn<BK_BILINEAR> {
+  static constexpr int nx = 1, nu = 1;
+  template <typename T> __device__ static void f(const T* x, const T* u, T* fx) { fx[0] = u[0] * x[0]; }
+  template <typename T> __device__ static void jac(const T* x, const T* u, T* Jx, T* Ju) {
+    Jx[0] = u[0];
+    Ju[0] = x[0];
+  }
+  template <typename T> __device__ static void hess(const T* x, const T* u, const T* mu, T* H) {
+    H[0] = 0; H[1] = mu[0]; H[2] = mu[0]; H[3] = 0;
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Problem
+// ---------------------------------------------------------------------------------------------
+// Per-precision operator state: a plan and the linearisation data in that precision.
+struct OpData {
+  int dtype = BK_F64;
+  Plan* plan = nullptr;        // n_comp = n_x, max_batch = 1
+  void* xu = nullptr;          // linearisation point X, U ((n_x + n_u) * P)
+  void* mu = nullptr;          // mu = s (B^a)^T lambda (n_x * P)
+  void* w = nullptr;           // Clenshaw-Curtis weights (L), working type
+  void* Kn = nullptr;          // per-node K_k = (I - h_k J_k)^{-1}, interleaved (n_x^2 per node)
+  void* Nn = nullptr;          // per-node N_k = 2 h_k J_k K_k, interleaved
+  void* Aseg = nullptr;        // segment aggregates of prod (I + N_k) (n_x^2 per segment)
+  void* Agrp = nullptr;        // group aggregates (n_x^2 per group)
+  // KKT preconditioner (terminal Schur data)
+  void* Zc = nullptr;          // n_e state vectors   Z = P^{-T} E^T
+  void* HWc = nullptr;         // n_e control vectors H~^{-1} W, W = Pu^T Z
+  void* Qc = nullptr;          // n_e state vectors   Q = P^{-1} Pu H~^{-1} W
+  void* Sinv = nullptr;        // n_e x n_e inverse of S = E Q (working type, device)
+  // temporaries (each n_x * P or (n_x + n_u) * P, working type)
+  void* t1 = nullptr;
+  void* t2 = nullptr;
+  void* t3 = nullptr;
+  void* segb = nullptr;        // per-segment affine offsets
+  void* grpb = nullptr;        // per-group affine offsets / incoming states
+};
+
+struct Problem {
+  int kind = 0, n_x = 0, n_u = 0, n_e = 0;
+  int dtype = BK_F64;          // working precision of kkt/precond/krylov
+  int64_t N = 0, L = 0, P = 0;
+  double t0 = 0, tf = 0, s = 0;
+  double params[4] = {0, 0, 0, 0};
+  double x0[NXM] = {0, 0, 0, 0};
+  int term_idx[NEM] = {0, 0, 0, 0};
+  double term_val[NEM] = {0, 0, 0, 0};
+  bool has_cost = true;
+  int nseg = 0, ngrp = 0;
+  bool linearized = false;
+  OpData d64;                  // FP64 operators (always)
+  OpData d32;                  // FP32 operators (BK_F32 problems)
+  double* F = nullptr;         // KKT residual scratch (FP64, kkt_len)
+  double* red = nullptr;       // reduction scratch (FP64)
+  double* red_host = nullptr;  // pinned host mirror of reduction results
+  int64_t kkt_len() const { return (2 * n_x + n_u) * P + 32; }
+  int64_t state_len() const { return n_x * P; }
+  OpData& work() { return dtype == BK_F64 ? d64 : d32; }
+};
+
+bk_status problem_linearize(Problem* pr, const double* z_lin, cudaStream_t st);
+// Operator applies on one precision's data (T = double or float).
+bk_status op_apply(Problem* pr, OpData& d, int op, const void* in, void* out, cudaStream_t st);
+bk_status op_precond(Problem* pr, OpData& d, int op, const void* in, void* out, int transpose,
+                     cudaStream_t st);
+// KKT residual at z (FP64) into F; weighted norm partial sums reduced on the host if wnorm.
+bk_status problem_residual(Problem* pr, const double* z, double* F, double* wnorm,
+                           cudaStream_t st);
+// Weighted norm of a residual vector (FP64), synchronous.
+bk_status problem_wnorm(Problem* pr, const double* F, double* wnorm, cudaStream_t st);
+
+}  // namespace bk
