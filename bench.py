@@ -1,0 +1,382 @@
+"""Benchmark of the Birkhoff hot path on GB300.
+
+Default workload: one Newton-Krylov solve of the planar orbit-raising problem on the CGL grid
+with N = 2^20 (L = 1,048,577 nodes), FP64, from the tangential-thrust spiral initial guess.
+A step is the whole path: residual (Birkhoff products of f), linearisation (B^T lambda,
+per-node preconditioner factors, terminal Schur data), preconditioned GMRES on the KKT system
+(KKT products = B and B^T on every state component, preconditioner sweeps), line search.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload newton_f64|newton_f32ir|apply_f64|apply_f32] [--N 20]
+
+Prints one JSON line on rank 0. With N > 1 (torchrun) every rank solves its own instance
+(replicas; the path has no data-path collective) and the time is the max over ranks.
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded sample.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+RF, TF, A_NOM = 1.5, 20.0, 0.01
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP64 FMA rate of GB300: 152 SMs x 2 FP64 FMA / clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s
+# (nominal 1.25 TFLOP/s); the transforms of the FP64 path are bound by it, not by HBM.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5 TFLOP/s nominal FFMA
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="newton_f64",
+                    choices=["newton_f64", "newton_f32ir", "apply_f64", "apply_f32"])
+    ap.add_argument("--N", type=int, default=20, help="log2 of the grid size")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        return rank, world, dist
+    if torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return 0, 1, None
+
+
+def barrier(dist):
+    import torch
+    if dist is not None:
+        dist.barrier()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+
+
+def max_over_ranks(x, dist):
+    import torch
+    if dist is None:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def read_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smmax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        load = [r for r in rows if r["power"] > 200.0] or rows
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load),
+                "sm_max_mhz": max(r["smmax"] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows), "samples_under_load": len(load)}
+
+
+def l2_flush_buffer():
+    import torch
+    return torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 2 x L2
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def make_orbit(N, dtype):
+    import torch
+    from paper_2509_01855_gb300 import _lib, api, synth
+    prob = api.Problem(_lib.BK_ORBIT, N, dtype, 0.0, TF, (A_NOM, RF))
+    t, _ = api.Plan(N, t0=0.0, tf=TF).grid()
+    X, U = synth.orbit_guess(t.numpy(), RF, TF)
+    z0 = prob.pack(X, U)
+    return prob, z0
+
+
+def run_newton(args, rank, world, dist):
+    import torch
+    from paper_2509_01855_gb300 import _lib, api
+    N = 1 << args.N
+    dtype = torch.float64 if args.workload == "newton_f64" else torch.float32
+    prob, z0 = make_orbit(N, dtype)
+    ws = api.newton_workspace(prob)
+    z = torch.empty_like(z0)
+    flush = l2_flush_buffer()
+    infos = []
+
+    def step():
+        z.copy_(z0)
+        return api.newton_solve(prob, z, workspace=ws)
+
+    for _ in range(args.warmup):
+        infos.append(step())
+    lib = _lib.lib()
+    barrier(dist)
+    launches0 = lib.bk_launch_count()
+    times = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            infos.append(step())
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        barrier(dist)
+    launches = lib.bk_launch_count() - launches0
+    ms = sum(times) / len(times)
+    ms_max = max_over_ranks(ms, dist)
+
+    # end to end through the public API: pinned host initial guess in, solution out
+    zh = z0.cpu().pin_memory()
+    outh = torch.empty_like(zh).pin_memory()
+    zd = torch.empty_like(z0)
+    e2e_times = []
+    for i in range(max(2, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        zd.copy_(zh, non_blocking=True)
+        api.newton_solve(prob, zd, workspace=ws)
+        outh.copy_(zd, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = max_over_ranks(sum(e2e_times) / len(e2e_times), dist)
+    nbytes = z0.numel() * z0.element_size()
+    last = infos[-1]
+    res = dict(ms=ms_max, launches=launches, clocks=clk.summary(),
+               e2e={"value": world * 1000.0 / e2e_ms, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+               solve=dict(newton_iterations=last["iterations"], krylov_iterations=last["krylov_iterations"],
+                          kkt_solves=last["kkt_solves"], residual=last["residual"]))
+    return res
+
+
+def measure_apply(N, dtype, reps=20):
+    """Birkhoff apply B v on 4 components, cold L2 between repetitions (CUDA events)."""
+    import torch
+    from paper_2509_01855_gb300 import api
+    plan = api.Plan(N, n_comp=4, max_batch=1, dtype=dtype, t0=0.0, tf=TF)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2509_01855)
+    v = plan.empty(1)
+    v[:, :, :N + 1] = torch.randn(1, 4, N + 1, dtype=dtype, device="cuda", generator=g)
+    out = plan.empty(1)
+    flush = l2_flush_buffer()
+    for _ in range(3):
+        api.birkhoff_apply(plan, v, out)
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        api.birkhoff_apply(plan, v, out)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    es = v.element_size()
+    nbytes = 2 * 4 * (N + 1) * es                     # read v, write B v
+    flops = 4 * 2 * 2.5 * N * math.log2(N)             # two DCT-I per component
+    return ms, nbytes, flops
+
+
+# ------------------------------------------------------------------------------------------
+# Oracle legs (CPU)
+# ------------------------------------------------------------------------------------------
+def oracle_newton_sample(N_sample):
+    """The dense FP64 oracle's Newton solve of the same orbit problem at a small N (seconds)."""
+    from oracle import problems as op
+    from oracle.kkt import DenseKKT
+    from paper_2509_01855_gb300 import synth
+    K = DenseKKT(op.Problem(op.ORBIT, 0.0, TF, (A_NOM, RF)), N_sample)
+    X, U = synth.orbit_guess(K.t, RF, TF)
+    vec0 = K.pack(X, U, np.zeros((4, K.L)), np.zeros(3))
+    t0 = time.perf_counter()
+    _, info = K.newton(vec0)
+    return time.perf_counter() - t0, info
+
+
+def cpu_baseline(N_sample=1024):
+    sec, info = oracle_newton_sample(N_sample)
+    return {"value": 1.0 / sec, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "dense FP64 oracle Newton solve of the same orbit problem at N=%d (one solve, "
+                      "%d Newton steps, LAPACK dense KKT solves; N=2^20 is out of reach of a dense "
+                      "oracle)" % (N_sample, info["iters"])}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    N_sample = 256
+    for _ in range(args.warmup):
+        oracle_newton_sample(N_sample)
+    times = []
+    for _ in range(args.steps):
+        sec, info = oracle_newton_sample(N_sample)
+        times.append(sec)
+    ms = 1000.0 * sum(times) / len(times)
+    value = 1000.0 / ms
+    sample = ("dense FP64 oracle Newton solve of the orbit problem at N=%d per step (the bench "
+              "workload is N=2^%d; a dense oracle cannot reach it)" % (N_sample, args.N))
+    line = {"impl": "reference", "metric": metric_name(args), "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def metric_name(args):
+    if args.workload.startswith("apply"):
+        return "Birkhoff apply GB/s at N=2^%d (B v on 4 components)" % args.N
+    return "Newton-Krylov solve rate at N=2^%d (orbit raising)" % args.N
+
+
+def config(args):
+    prec = {"newton_f64": "f64", "newton_f32ir": "f32 Krylov + f64 refinement",
+            "apply_f64": "f64", "apply_f32": "f32"}[args.workload]
+    c = {"workload": "orbit_raising_newton_krylov" if args.workload.startswith("newton") else "birkhoff_apply",
+         "N": 1 << args.N, "nodes": (1 << args.N) + 1, "precision": prec,
+         "problem": "polar orbit raising r 1->%.1f, t_f=%g, thrust-vector min-energy, x0=(1,0,0,1)" % (RF, TF),
+         "initial_guess": "tangential-thrust spiral", "l2": "flushed between steps (256 MB write)",
+         "parallelism": "replicas x%d" % args.gpus}
+    return c
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    rank, world, dist = dist_setup(args)
+    hbm_peak, peak_kind = read_peaks()
+    N = 1 << args.N
+    dtype_name = "f64" if args.workload in ("newton_f64", "apply_f64") else "f32"
+    line = {"metric": metric_name(args), "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype_name, "data": "synthetic", "config": config(args)}
+    if args.workload.startswith("newton"):
+        r = run_newton(args, rank, world, dist)
+        line.update(value=world * 1000.0 / r["ms"], unit="solves/s", ms_per_step=r["ms"], e2e=r["e2e"],
+                    gpu_launches=r["launches"], clocks=r["clocks"], solve=r["solve"])
+        dt = torch.float64 if args.workload == "newton_f64" else torch.float32
+    else:
+        dt = torch.float64 if args.workload == "apply_f64" else torch.float32
+        from paper_2509_01855_gb300 import _lib
+        lib = _lib.lib()
+        c0 = lib.bk_launch_count()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            ms, nbytes, flops = measure_apply(N, dt, reps=max(args.steps, 5))
+        line.update(value=world * nbytes / ms / 1e6, unit="GB/s", ms_per_step=ms,
+                    gpu_launches=lib.bk_launch_count() - c0, clocks=clk.summary())
+    # roofline of the dominant unit: the 4-component Birkhoff apply (four transform passes)
+    ams, abytes, aflops = measure_apply(N, dt)
+    if dt == torch.float64:
+        peak, unit, achieved = FP64_PEAK_TFLOPS, "TFLOP/s", aflops / ams / 1e9
+        bound = "alu"
+    else:
+        peak, unit, achieved = hbm_peak, "GB/s", abytes / ams / 1e6
+        bound = "hbm"
+    line["roofline"] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                        "frac": achieved / peak, "traffic": None,
+                        "kernel": "birkhoff_apply N=2^%d x4 components (%s)" % (args.N, dtype_name),
+                        "algorithmic": {"bytes": abytes, "flops": aflops},
+                        "peak_source": ("FP64 FMA nominal 1.25 TFLOP/s (2 FP64 FMA/clk/SM)" if bound == "alu"
+                                        else "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind)}
+    line["apply"] = {"ms": ams, "gbs": abytes / ams / 1e6, "tflops": aflops / ams / 1e9, "N": N,
+                     "n_comp": 4, "dtype": dtype_name}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

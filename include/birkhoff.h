@@ -58,6 +58,10 @@ const char* bk_last_error(void);
 /* Library version string. */
 const char* bk_version(void);
 
+/* Number of kernels this library has launched in this process (all threads, all devices). A
+ * diagnostic for benchmarks: the difference across a region counts the library's launches. */
+uint64_t bk_launch_count(void);
+
 /* ------------------------------------------------------------------------------------------
  * Plan: grid tables (nodes, Clenshaw-Curtis weights, DCT twiddles) and transform scratch.
  * ------------------------------------------------------------------------------------------ */

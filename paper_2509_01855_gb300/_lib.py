@@ -20,7 +20,7 @@ STATUS = {0: "BK_OK", 1: "BK_ERR_ARG", 2: "BK_ERR_CUDA", 3: "BK_ERR_OOM",
           7: "BK_ERR_UNSUPPORTED"}
 
 # Symbols declared in include/birkhoff.h (checked by the CPU test suite).
-EXPORTS = ["bk_last_error", "bk_version", "bk_plan_create", "bk_plan_destroy", "bk_plan_info",
+EXPORTS = ["bk_last_error", "bk_version", "bk_launch_count", "bk_plan_create", "bk_plan_destroy", "bk_plan_info",
            "bk_plan_grid", "birkhoff_apply", "birkhoff_apply_T", "bk_problem_create",
            "bk_problem_destroy", "bk_problem_info", "bk_linearize", "kkt_apply",
            "precond_apply", "bk_krylov_workspace_bytes", "krylov_solve",
@@ -72,6 +72,7 @@ def lib():
     sig = {
         "bk_last_error": (ctypes.c_char_p, []),
         "bk_version": (ctypes.c_char_p, []),
+        "bk_launch_count": (ctypes.c_uint64, []),
         "bk_plan_create": (c_int, [ctypes.POINTER(vp), i64, c_int, c_int, c_int, dbl, dbl, i64, vp]),
         "bk_plan_destroy": (None, [vp]),
         "bk_plan_info": (c_int, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),

@@ -34,6 +34,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 
 #include "bk_common.cuh"
@@ -43,6 +44,9 @@
 namespace bk {
 
 static thread_local std::string g_last_error = "no error";
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   char buf[1024];
@@ -468,11 +472,15 @@ static bk_status compute_weights(Plan* p, cudaStream_t st) {
   if (r == BK_OK) r = dmalloc((void**)&p->w64, sizeof(double) * q->pitch);
   if (r == BK_OK) {
     k_unit_last<<<(int)((q->pitch + 255) / 256), 256, 0, st>>>(e, L, q->pitch);
-    r = plan_apply_n(q, e, p->w64, 1, true, 1.0, st);
+    note_launch();
+    r = cudaGetLastError() == cudaSuccess ? plan_apply_n(q, e, p->w64, 1, true, 1.0, st) : BK_ERR_CUDA;
   }
   if (r == BK_OK && p->dtype == BK_F32) {
     r = dmalloc(&p->wT, sizeof(float) * L);
-    if (r == BK_OK) k_d2f<<<(int)((L + 255) / 256), 256, 0, st>>>(p->w64, (float*)p->wT, L);
+    if (r == BK_OK) {
+      k_d2f<<<(int)((L + 255) / 256), 256, 0, st>>>(p->w64, (float*)p->wT, L);
+      note_launch();
+    }
   }
   if (r == BK_OK && cudaStreamSynchronize(st) != cudaSuccess) { set_error("weights: sync failed"); r = BK_ERR_CUDA; }
   dfree(e);
@@ -578,6 +586,7 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
     if (st_ != BK_OK) break;
     if ((st_ = dmalloc((void**)&p->t_nodes, sizeof(double) * (size_t)L)) != BK_OK) break;
     k_grid_tables<<<(int)((L + 255) / 256), 256, 0, st>>>(p->t_nodes, N, t0, p->s);
+    note_launch();
     if (cudaGetLastError() != cudaSuccess) { st_ = BK_ERR_CUDA; set_error("grid table launch failed"); break; }
     st_ = dtype == BK_F64 ? set_smem_attrs<double>(p) : set_smem_attrs<float>(p);
     if (st_ != BK_OK) break;
@@ -682,6 +691,7 @@ extern "C" {
 
 const char* bk_last_error(void) { return bk::g_last_error.c_str(); }
 const char* bk_version(void) { return "birkhoff-gb300 0.1 (sm_103a)"; }
+uint64_t bk_launch_count(void) { return bk::g_launches.load(); }
 
 bk_status bk_plan_create(bk_plan** plan, int64_t N, int n_comp, int max_batch, bk_dtype dtype,
                          double t0, double tf, int64_t pitch, void* stream) {

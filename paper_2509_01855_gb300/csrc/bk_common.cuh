@@ -29,7 +29,14 @@ void set_error(const char* fmt, ...);
     if (s_ != BK_OK) return s_;            \
   } while (0)
 
-#define BK_CHECK_LAUNCH() BK_TRY_CUDA(cudaGetLastError())
+// Every kernel launch of the library is followed by BK_CHECK_LAUNCH(), which also counts it
+// (bk_launch_count()).
+void note_launch();
+#define BK_CHECK_LAUNCH()          \
+  do {                             \
+    bk::note_launch();             \
+    BK_TRY_CUDA(cudaGetLastError()); \
+  } while (0)
 
 #define BK_ARG(cond, ...)                  \
   do {                                     \

@@ -498,7 +498,11 @@ static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* ou
   BK_CHECK_LAUNCH();
   if (pr->P > pr->L) {
     k_zero_pad<T><<<nblk(NX * (pr->P - pr->L)), 256, 0, st>>>(out, NX, pr->P, pr->L);
-    if (bout) k_zero_pad<T><<<nblk(NX * (pr->P - pr->L)), 256, 0, st>>>(bout, NX, pr->P, pr->L);
+    BK_CHECK_LAUNCH();
+    if (bout) {
+      k_zero_pad<T><<<nblk(NX * (pr->P - pr->L)), 256, 0, st>>>(bout, NX, pr->P, pr->L);
+      BK_CHECK_LAUNCH();
+    }
   }
   return BK_OK;
 }
