@@ -497,12 +497,14 @@ static size_t smem_small(int64_t N) {
   return sizeof(T) * 2 * Lp + 2 * sizeof(typename V2<T>::t) * N;
 }
 
+static constexpr size_t FOURSTEP_SMEM_BUDGET = 192 * 1024;
+
 static bk_status configure_fourstep(Plan* p) {
   const int log2N = ilog2(p->N);
   p->N1 = 1 << (log2N / 2);
   p->N2 = 1 << (log2N - log2N / 2);
   const size_t csz = 2 * dtype_size(p->dtype);
-  const size_t budget = 192 * 1024;  // bytes for the two ping-pong buffers
+  const size_t budget = FOURSTEP_SMEM_BUDGET;  // bytes for the two ping-pong buffers
   // pass A: NB columns of N1 (padded), two buffers
   int NB = (int)(budget / (2 * csz * (p->N1 + 1)));
   if (NB > p->N2) NB = p->N2;
@@ -526,22 +528,25 @@ static bk_status configure_fourstep(Plan* p) {
   return BK_OK;
 }
 
+// The dynamic shared-memory cap is a per-function setting shared by every plan, so it is set to
+// the largest size any plan of the type can request (never to one plan's own size, which would
+// lower the cap under plans created earlier).
 template <typename T>
 static bk_status set_smem_attrs(const Plan* p) {
   if (p->small) {
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_birkhoff_small<T, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemS));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_birkhoff_small<T, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemS));
+    const int cap = (int)smem_small<T>(small_limit(p->dtype));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_birkhoff_small<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_birkhoff_small<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
   } else {
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, IN_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemA));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, IN_WINV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemA));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, ST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemA));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, ST_TRN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemA));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemB));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_STORE_TRN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemB));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_FWD_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemB));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_TRN_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemB));
+    const int cap = (int)FOURSTEP_SMEM_BUDGET;
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, IN_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, IN_WINV>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, ST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, ST_TRN>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_STORE_TRN>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_FWD_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_TRN_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
   }
   return BK_OK;
 }
