@@ -103,6 +103,26 @@ bk_status bk_plan_grid(const bk_plan* plan, double* t_host, double* w_host);
  * closed form in Eq. c_k=bydef does. */
 bk_status birkhoff_apply(const bk_plan* plan, const void* v, void* out, int batch, void* stream);
 
+/* out = B v for callers that cannot allocate device memory. The paper has no counterpart: this
+ * entry point exists for programs that must not call cudaMalloc once they are running, such as
+ * real-time or flight control loops whose device memory budget is fixed at start-up, or host
+ * applications whose own allocator owns the whole GPU. Such callers cannot create a bk_plan,
+ * because plan creation allocates its tables and scratch.
+ *   v, out     device arrays of nvec FP64 vectors, `pitch` elements apart (caller-owned; the
+ *              library allocates nothing); v == out is not allowed
+ *   N          power of two, 8192 <= N <= 65536;  nvec: 1..8;  pitch >= N + 1, even
+ *   t0, tf     time interval (B = s B^a, s = (tf - t0) / 2)
+ * The twiddle tables and the transform scratch live in one 16 MiB array that the library
+ * reserves statically on every GPU that loads it, for the life of the process. Sizes beyond the
+ * limits above are rejected with BK_ERR_ARG before any work is queued. The first call on a
+ * device does a one-time set-up (looks up the array's device address and sets the kernels'
+ * shared-memory limits), so make that first call before any stream capture. All calls on a
+ * device share the array, which keeps the last call's contents; every call rewrites all of it
+ * before reading it, so nothing needs clearing, but calls whose work overlaps on the GPU (other
+ * streams, or other host threads) race on it and must be serialised by the caller. */
+bk_status birkhoff_apply_noalloc(const double* v, double* out, int64_t N, int nvec, int64_t pitch,
+                                 double t0, double tf, void* stream);
+
 /* out = B^T v, the exact transpose of birkhoff_apply (the paper has no transpose product; the
  * KKT operator needs one). Same arguments and layout as birkhoff_apply. */
 bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int batch,

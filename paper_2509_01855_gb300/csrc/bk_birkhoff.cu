@@ -35,6 +35,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <string>
 
 #include "bk_common.cuh"
@@ -689,6 +690,106 @@ bk_status plan_apply(const Plan* p, const void* v, void* out, int batch, bool tr
 
 }  // namespace bk
 
+namespace bk {
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant of the four-step forward product.
+//
+// For callers that must not allocate device memory once they run: real-time or flight control
+// loops with a memory budget fixed at start-up, and host programs whose own allocator owns the
+// device. They cannot create a bk_plan (plan creation allocates tables and scratch). This
+// variant keeps its twiddle tables and transform scratch in one file-scope device array of
+// NOALLOC_BYTES, reserved on every GPU that loads the library until the process exits.
+// ---------------------------------------------------------------------------------------------
+static constexpr size_t NOALLOC_BYTES = size_t(16) << 20;   // 16 MiB
+static constexpr int NOALLOC_MAX_DEV = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Device address of g_noalloc_scratch per device (host code cannot use the symbol itself).
+static void* g_noalloc_ptr[NOALLOC_MAX_DEV] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Bytes of the scratch layout for N (FP64) and nvec vectors, and the sub-buffer offsets.
+static size_t noalloc_layout(const Plan& p, int nvec, size_t off[7]) {
+  const int64_t N = p.N;
+  size_t o = 0;
+  off[0] = o; o += align256(sizeof(double2) * std::max(p.N1, p.N2));                  // tw
+  off[1] = o; o += align256(sizeof(double2) * (N / 2 + 1));                           // tpost
+  off[2] = o; o += align256(sizeof(double2) * N);                                     // twN
+  off[3] = o; o += align256(sizeof(double2) * (size_t)N * nvec);                      // scrA
+  off[4] = o; o += align256(sizeof(double) * (size_t)(N + 1) * nvec);                 // scrY
+  off[5] = o; o += align256(sizeof(double) * (size_t)p.nPartA * nvec);                // part1
+  off[6] = o; o += align256(sizeof(double) * (size_t)p.nPartA * nvec);                // part2
+  return o;
+}
+
+// Per-device set-up: device address of the scratch array and the shared-memory attributes of
+// the pass kernels. Runs on the first call on each device.
+static bk_status noalloc_setup(int dev, void** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* ptr = nullptr;
+    BK_TRY_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    const int smem = (int)FOURSTEP_SMEM_BUDGET;
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<double, IN_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<double, ST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<double, EP_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<double, EP_FWD_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return BK_OK;
+}
+
+bk_status noalloc_apply(const double* v, double* out, int64_t N, int nvec, int64_t pitch, double t0, double tf,
+                        cudaStream_t st) {
+  BK_ARG(v != nullptr && out != nullptr, "NULL vector");
+  BK_ARG(is_pow2(N) && N >= 8192 && N <= 65536, "N must be a power of two in [8192, 65536], got %lld", (long long)N);
+  BK_ARG(nvec >= 1 && nvec <= 8, "nvec must be in [1, 8], got %d", nvec);
+  BK_ARG(pitch >= N + 1 && pitch % 2 == 0, "pitch must be >= N + 1 and even");
+  BK_ARG(tf != t0 && isfinite(t0) && isfinite(tf), "tf must differ from t0 and both be finite");
+  BK_ARG(((uintptr_t)v & 15) == 0 && ((uintptr_t)out & 15) == 0, "vectors must be 16-byte aligned");
+  int dev = 0;
+  BK_TRY_CUDA(cudaGetDevice(&dev));
+  BK_ARG(dev >= 0 && dev < NOALLOC_MAX_DEV, "device index %d not supported", dev);
+  Plan p;  // configuration only; owns nothing
+  p.N = N;
+  p.L = N + 1;
+  p.pitch = pitch;
+  p.n_comp = nvec;
+  p.max_batch = 1;
+  p.dtype = BK_F64;
+  p.t0 = t0;
+  p.tf = tf;
+  p.s = 0.5 * (tf - t0);
+  p.small = false;
+  BK_TRY(configure_fourstep(&p));
+  size_t off[7];
+  const size_t need = noalloc_layout(p, nvec, off);
+  BK_ARG(need <= NOALLOC_BYTES, "N=%lld with %d vectors needs %zu bytes of scratch, more than the %zu reserved",
+         (long long)N, nvec, need, NOALLOC_BYTES);
+  void* base = nullptr;
+  BK_TRY(noalloc_setup(dev, &base));
+  unsigned char* b = (unsigned char*)base;
+  const int64_t ntab = std::max(p.N1, p.N2);
+  p.tw_log2 = ilog2(ntab);
+  p.tw = b + off[0];
+  p.tpost = b + off[1];
+  p.twN = b + off[2];
+  // every table is rewritten by each call: nothing in the array has to start at zero
+  k_tw_table<double><<<(int)std::min<int64_t>((ntab + 255) / 256, 4096), 256, 0, st>>>((double2*)p.tw, ntab, (double)ntab);
+  BK_CHECK_LAUNCH();
+  k_post_table<double><<<(int)std::min<int64_t>((N / 2 + 256) / 256, 4096), 256, 0, st>>>((double2*)p.tpost, N);
+  BK_CHECK_LAUNCH();
+  k_tw_table<double><<<(int)std::min<int64_t>((N + 255) / 256, 8192), 256, 0, st>>>((double2*)p.twN, N, (double)N);
+  BK_CHECK_LAUNCH();
+  return apply_impl<double>(&p, v, out, nvec, false, p.s, st, b + off[3], b + off[4], b + off[5], b + off[6]);
+}
+
+}  // namespace bk
+
 // ---------------------------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------------------------
@@ -729,6 +830,11 @@ bk_status bk_plan_grid(const bk_plan* plan, double* t_host, double* w_host) {
 
 bk_status birkhoff_apply(const bk_plan* plan, const void* v, void* out, int batch, void* stream) {
   return bk::plan_apply(reinterpret_cast<const bk::Plan*>(plan), v, out, batch, false, (cudaStream_t)stream);
+}
+
+bk_status birkhoff_apply_noalloc(const double* v, double* out, int64_t N, int nvec, int64_t pitch, double t0,
+                                 double tf, void* stream) {
+  return bk::noalloc_apply(v, out, N, nvec, pitch, t0, tf, (cudaStream_t)stream);
 }
 
 bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int batch, void* stream) {
