@@ -30,6 +30,7 @@
 // fused into the load of the second DCT, and the node-0 value gathered from per-CTA partials.
 #include <math.h>
 #include <stdarg.h>
+#include <stdlib.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -89,6 +90,16 @@ __global__ void k_tw_table(typename V2<T>::t* tw, int64_t n, double denom_half_t
   }
 }
 
+// tw[i] = omega_n^{i * stride}, i < count (sincospi of 2 i stride / n)
+template <typename T>
+__global__ void k_tw_table_strided(typename V2<T>::t* tw, int64_t count, int64_t stride, double n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi((double)(2 * i * stride) / n, &s, &c);
+    tw[i] = mk2<T>((T)c, (T)(-s));
+  }
+}
+
 template <typename T>
 __global__ void k_post_table(typename V2<T>::t* tp, int64_t N) {
   // tp[k] = (cos(pi k / N), sin(pi k / N)), k = 0..N/2
@@ -98,6 +109,13 @@ __global__ void k_post_table(typename V2<T>::t* tp, int64_t N) {
     sincospi((double)k / (double)N, &s, &c);
     tp[k] = mk2<T>((T)c, (T)s);
   }
+}
+
+// rk[k] = 1 / (4k), k >= 1 (rk[0] = 0), rounded once from FP64.
+template <typename T>
+__global__ void k_rk_table(T* rk, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    rk[k] = k == 0 ? T(0) : (T)(1.0 / (4.0 * (double)k));
 }
 
 __global__ void k_grid_tables(double* t_nodes, int64_t N, double t0, double s) {
@@ -122,56 +140,66 @@ __global__ void k_grid_tables(double* t_nodes, int64_t N, double t0, double s) {
 //   ST_TRN   : x_m = W_m^{-1} G^T(W (Y - Y_0))_m          (transposed stencil)
 enum { IN_PLAIN = 0, IN_WINV = 1, ST_FWD = 2, ST_TRN = 3 };
 
+// rk[k] = 1 / (4k) for 1 <= k <= N + 1 (plan table): the stencils multiply instead of divide.
 template <typename T>
-__device__ __forceinline__ T stencil_fwd(const T* __restrict__ Y, int m, int N, T invN) {
+__device__ __forceinline__ T stencil_fwd(const T* __restrict__ Y, int m, int N, T invN, const T* __restrict__ rk) {
   // g_m = chat'_m / 2 for 0 < m < N, g_N = chat'_N, g_0 = 0 (see the file comment)
   if (m == 0) return T(0);
-  if (m == N) return -Y[N - 1] * (invN / T(2 * N));
+  if (m == N) return -Y[N - 1] * (invN * T(2) * rk[N]);
   if (m == 1) return (Y[2] - Y[0]) * (invN * T(0.25));
   if (m == N - 1) {
     const T yN = Y[N];
-    return (T(0.5) * yN - Y[N - 2]) * (invN / T(4.0 * (N - 1))) - yN * (invN / T(8.0 * (N + 1)));
+    return (T(0.5) * yN - Y[N - 2]) * (invN * rk[N - 1]) - yN * (invN * T(0.5) * rk[N + 1]);
   }
-  return (Y[m + 1] - Y[m - 1]) * (invN / T(4.0 * m));
+  return (Y[m + 1] - Y[m - 1]) * (invN * rk[m]);
 }
 
 template <typename T>
-__device__ __forceinline__ T stencil_trn(const T* __restrict__ Q, int m, int N, T Y0) {
+__device__ __forceinline__ T stencil_trn(const T* __restrict__ Q, int m, int N, T Y0, const T* __restrict__ rk,
+                                         T cN) {
   // r = W (Y - Y0); t = G^T r; return t_m / W_m. G^T rows:
   //   t_0 = -r_1/4, t_1 = -r_2/8, t_j = r_{j-1}/(4(j-1)) - r_{j+1}/(4(j+1)) (2<=j<=N-2),
   //   t_{N-1} = r_{N-2}/(4(N-2)) - r_N/(2N), t_N = r_{N-1}/(4(N^2-1)).
   // r_k = 2 (Y_k - Y0) for 0 < k < N, r_0 = Y_0 - Y0 = 0, r_N = Y_N - Y0.
+  // cN = 1 / (4 (N^2 - 1))
   if (m == 0) return -(T(2) * (Q[1] - Y0)) * T(0.25);
-  if (m == N) return (T(2) * (Q[N - 1] - Y0)) / T(4.0 * ((double)N * N - 1.0));
+  if (m == N) return (T(2) * (Q[N - 1] - Y0)) * cN;
   T t;
   if (m == 1) {
     t = -(T(2) * (Q[2] - Y0)) * T(0.125);
   } else if (m == N - 1) {
-    t = (T(2) * (Q[N - 2] - Y0)) / T(4.0 * (N - 2)) - (Q[N] - Y0) / T(2.0 * N);
+    t = (T(2) * (Q[N - 2] - Y0)) * rk[N - 2] - (Q[N] - Y0) * (T(2) * rk[N]);
   } else {
-    t = (T(2) * (Q[m - 1] - Y0)) / T(4.0 * (m - 1)) - (T(2) * (Q[m + 1] - Y0)) / T(4.0 * (m + 1));
+    t = (Q[m - 1] - Y0) * rk[m - 1] - (Q[m + 1] - Y0) * rk[m + 1];
+    return t;
   }
   return T(0.5) * t;
 }
 
 // Value x_m of the transform input of kind K. `src` is the vector (first DCT) or the stage
 // buffer Y (second DCT). Y0 is used by ST_TRN only.
+// Stencil constants passed to the transform kernels.
+template <typename T> struct StencilTab {
+  const T* rk;  // rk[k] = 1/(4k), k = 1..N+1
+  T cN;         // 1/(4(N^2 - 1))
+};
+
 template <typename T, int K>
-__device__ __forceinline__ T load_x(const T* __restrict__ src, int m, int N, T invN, T Y0) {
+__device__ __forceinline__ T load_x(const T* __restrict__ src, int m, int N, T invN, T Y0, StencilTab<T> tb) {
   if (K == IN_PLAIN) return src[m];
   if (K == IN_WINV) return (m == 0 || m == N) ? src[m] : T(0.5) * src[m];
-  if (K == ST_FWD) return stencil_fwd<T>(src, m, N, invN);
-  return stencil_trn<T>(src, m, N, Y0);
+  if (K == ST_FWD) return stencil_fwd<T>(src, m, N, invN, tb.rk);
+  return stencil_trn<T>(src, m, N, Y0, tb.rk, tb.cN);
 }
 
 // z_j = x_ext[2j] + i x_ext[2j+1]
 template <typename T, int K>
 __device__ __forceinline__ typename V2<T>::t load_z(const T* __restrict__ src, int j, int N, T invN,
-                                                    T Y0) {
+                                                    T Y0, StencilTab<T> tb) {
   const int m1 = 2 * j, m2 = 2 * j + 1;
   const int i1 = m1 <= N ? m1 : 2 * N - m1;
   const int i2 = m2 <= N ? m2 : 2 * N - m2;
-  return mk2<T>(load_x<T, K>(src, i1, N, invN, Y0), load_x<T, K>(src, i2, N, invN, Y0));
+  return mk2<T>(load_x<T, K>(src, i1, N, invN, Y0, tb), load_x<T, K>(src, i2, N, invN, Y0, tb));
 }
 
 // Real-FFT split: from Z_k, Z_{N-k} and (cos, sin)(pi kk / N), kk = min(k, N - k).
@@ -189,25 +217,37 @@ __device__ __forceinline__ void split_pair(typename V2<T>::t zk, typename V2<T>:
 // ---------------------------------------------------------------------------------------------
 template <typename T>
 __device__ void dct1_block(const T* __restrict__ X, int kind, T* __restrict__ Y,
-                           typename V2<T>::t* bufA, typename V2<T>::t* bufB, int N, int log2N,
+                           typename V2<T>::t* buf, int N, int log2N,
                            const typename V2<T>::t* __restrict__ tw, int tw_log2,
-                           const typename V2<T>::t* __restrict__ tpost, T invN, T Y0) {
+                           const typename V2<T>::t* __restrict__ tpost, T invN, T Y0, StencilTab<T> tb) {
   typedef typename V2<T>::t C;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
     C z;
     switch (kind) {
-      case IN_PLAIN: z = load_z<T, IN_PLAIN>(X, j, N, invN, Y0); break;
-      case IN_WINV: z = load_z<T, IN_WINV>(X, j, N, invN, Y0); break;
-      case ST_FWD: z = load_z<T, ST_FWD>(X, j, N, invN, Y0); break;
-      default: z = load_z<T, ST_TRN>(X, j, N, invN, Y0); break;
+      case IN_PLAIN: z = load_z<T, IN_PLAIN>(X, j, N, invN, Y0, tb); break;
+      case IN_WINV: z = load_z<T, IN_WINV>(X, j, N, invN, Y0, tb); break;
+      case ST_FWD: z = load_z<T, ST_FWD>(X, j, N, invN, Y0, tb); break;
+      default: z = load_z<T, ST_TRN>(X, j, N, invN, Y0, tb); break;
     }
-    bufA[j] = z;
+    buf[padi(j)] = z;
   }
   __syncthreads();
-  C* Z = fft_smem<T>(bufA, bufB, N, log2N, 1, N, tw, tw_log2);
+  if (N >= 16) {
+    fft16<T>(buf, N, log2N, 1, pad_stride(N), tw, tw_log2);
+  } else {
+    // N = 4 or 8: direct DFT (tw holds omega_N^i, n_tab = N)
+    C zk = mk2<T>(T(0), T(0));
+    const int k = threadIdx.x;
+    if (k < N) {
+      for (int j = 0; j < N; ++j) zk = cadd(zk, cmul(buf[padi(j)], tw[(j * k) & (N - 1)]));
+    }
+    __syncthreads();
+    if (k < N) buf[padi(k)] = zk;
+    __syncthreads();
+  }
   for (int k = threadIdx.x; k <= N / 2; k += blockDim.x) {
-    const C zk = Z[k];
-    const C zc = Z[(N - k) & (N - 1)];
+    const C zk = buf[padi(k)];
+    const C zc = buf[padi((N - k) & (N - 1))];
     T yk, ynk;
     split_pair<T>(zk, zc, tpost[k], yk, ynk);
     Y[k] = yk;
@@ -216,19 +256,22 @@ __device__ void dct1_block(const T* __restrict__ X, int kind, T* __restrict__ Y,
   __syncthreads();
 }
 
+// Thread cap of the transform kernels: each thread stages 16 complex values, so FP64 kernels
+// are limited to 256 threads (up to 255 registers each) and FP32 ones to 512.
+template <typename T> struct MaxThr { static constexpr int v = sizeof(T) == 8 ? 256 : 512; };
+
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(MaxThr<T>::v)
     k_birkhoff_small(const T* __restrict__ in, T* __restrict__ out, int N, int log2N, int64_t pitch,
                      T s, const typename V2<T>::t* __restrict__ tw, int tw_log2,
-                     const typename V2<T>::t* __restrict__ tpost) {
+                     const typename V2<T>::t* __restrict__ tpost, StencilTab<T> tb) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = N + 1;
   const int Lp = (L + 3) & ~3;
   T* X = reinterpret_cast<T*>(smem);
   T* Y = X + Lp;
-  C* bufA = reinterpret_cast<C*>(Y + Lp);
-  C* bufB = bufA + N;
+  C* buf = reinterpret_cast<C*>(Y + Lp);
   const int64_t base = (int64_t)blockIdx.x * pitch;
   const T* src = in + base;
   T* dst = out + base;
@@ -236,14 +279,14 @@ __global__ void __launch_bounds__(256)
   for (int m = threadIdx.x; m < L; m += blockDim.x) X[m] = src[m];
   __syncthreads();
   if (!TRANS) {
-    dct1_block<T>(X, IN_PLAIN, Y, bufA, bufB, N, log2N, tw, tw_log2, tpost, invN, T(0));
-    dct1_block<T>(Y, ST_FWD, X, bufA, bufB, N, log2N, tw, tw_log2, tpost, invN, T(0));
+    dct1_block<T>(X, IN_PLAIN, Y, buf, N, log2N, tw, tw_log2, tpost, invN, T(0), tb);
+    dct1_block<T>(Y, ST_FWD, X, buf, N, log2N, tw, tw_log2, tpost, invN, T(0), tb);
     const T y0 = X[0];
     for (int m = threadIdx.x; m < L; m += blockDim.x) dst[m] = s * (X[m] - y0);
   } else {
-    dct1_block<T>(X, IN_WINV, Y, bufA, bufB, N, log2N, tw, tw_log2, tpost, invN, T(0));
+    dct1_block<T>(X, IN_WINV, Y, buf, N, log2N, tw, tw_log2, tpost, invN, T(0), tb);
     const T y0 = Y[0];
-    dct1_block<T>(Y, ST_TRN, X, bufA, bufB, N, log2N, tw, tw_log2, tpost, invN, y0);
+    dct1_block<T>(Y, ST_TRN, X, buf, N, log2N, tw, tw_log2, tpost, invN, y0, tb);
     const T sN = s * invN;
     for (int m = threadIdx.x; m < L; m += blockDim.x)
       dst[m] = (m == 0 || m == N) ? sN * X[m] : T(2) * sN * X[m];
@@ -259,17 +302,21 @@ __global__ void __launch_bounds__(256)
 //         N2), real-FFT split, epilogue.
 // ---------------------------------------------------------------------------------------------
 template <typename T, int K>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(MaxThr<T>::v)
     k_passA(const T* __restrict__ src, int64_t src_stride, typename V2<T>::t* __restrict__ Aout,
             T* __restrict__ partial, int N, int N1, int log2N1, int N2, int NB,
             const typename V2<T>::t* __restrict__ tw, int tw_log2,
             const typename V2<T>::t* __restrict__ twN, const T* __restrict__ y0_partial,
-            int n_y0_partial, T invN) {
+            int n_y0_partial, T invN, StencilTab<T> tb, const typename V2<T>::t* __restrict__ twLo,
+            const typename V2<T>::t* __restrict__ twHi, int tw_h) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int bs = N1 + 1;  // padded batch stride
-  C* bufA = reinterpret_cast<C*>(smem);
-  C* bufB = bufA + (size_t)NB * bs;
+  const int bs = pad_stride(N1);
+  C* buf = reinterpret_cast<C*>(smem);
+  // FP32: sub-FFT twiddles in shared memory after the tile (FP64 reads the global table)
+  C* tws = buf + (size_t)NB * bs;
+  const bool smem_tw = sizeof(T) == 4;
+  if (smem_tw) load_tw_smem<T>(tws, tw, N1, log2N1, tw_log2);
   __shared__ T red[32];
   const int vec = blockIdx.y;
   const T* x = src + (int64_t)vec * src_stride;
@@ -294,13 +341,26 @@ __global__ void __launch_bounds__(256)
   }
   T dc = T(0);
   const int total = NB * N1;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int b = idx % NB;
-    const int j1 = idx / NB;
-    const int j = N2 * j1 + c0 + b;
-    const C z = load_z<T, K>(x, j, N, invN, Y0);
-    dc += z.x + z.y;
-    bufA[b * bs + j1] = z;
+  // 4 independent element loads in flight per thread before the shared-memory stores
+  for (int idx0 = threadIdx.x; idx0 < total; idx0 += 4 * blockDim.x) {
+    C z[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = idx0 + u * blockDim.x;
+      if (idx < total) {
+        const int b = idx % NB;
+        const int j = N2 * (idx / NB) + c0 + b;
+        z[u] = load_z<T, K>(x, j, N, invN, Y0, tb);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = idx0 + u * blockDim.x;
+      if (idx < total) {
+        dc += z[u].x + z[u].y;
+        buf[(idx % NB) * bs + padi(idx / NB)] = z[u];
+      }
+    }
   }
   // block reduction of dc (deterministic order)
   for (int o = 16; o > 0; o >>= 1) dc += __shfl_xor_sync(0xffffffffu, dc, o);
@@ -311,14 +371,21 @@ __global__ void __launch_bounds__(256)
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (threadIdx.x == 0) partial[(int64_t)vec * gridDim.x + blockIdx.x] = a;
   }
-  C* R = fft_smem<T>(bufA, bufB, N1, log2N1, NB, bs, tw, tw_log2);
+  __syncthreads();
+  if (smem_tw)
+    fft16<T>(buf, N1, log2N1, NB, bs, tws, log2N1);
+  else
+    fft16<T>(buf, N1, log2N1, NB, bs, tw, tw_log2);
   C* A = Aout + (int64_t)vec * N;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const int b = idx % NB;
     const int k1 = idx / NB;
     const int j2 = c0 + b;
-    const C w = __ldg(&twN[(int64_t)j2 * k1]);
-    A[(int64_t)k1 * N2 + j2] = cmul(R[b * bs + k1], w);
+    const int m = j2 * k1;  // < N
+    // FP64: one table of omega_N^m (the FP64 pipe, not memory, bounds these kernels).
+    // FP32: omega_N^m = omega_N^{(m >> h) 2^h} omega_N^{m mod 2^h} from two tables of ~sqrt N.
+    const C w = sizeof(T) == 8 ? __ldg(&twN[m]) : cmul(__ldg(&twHi[m >> tw_h]), __ldg(&twLo[m & ((1 << tw_h) - 1)]));
+    A[(int64_t)k1 * N2 + j2] = cmul(buf[b * bs + padi(k1)], w);
   }
 }
 
@@ -338,16 +405,18 @@ __device__ __forceinline__ void ep_write(T* __restrict__ dst, int k, T yk, int N
 }
 
 template <typename T, int E>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(MaxThr<T>::v)
     k_passB(const typename V2<T>::t* __restrict__ Ain, T* __restrict__ dst, int64_t dst_stride,
             int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial, int N, int N1,
             int N2, int log2N2, int P, const typename V2<T>::t* __restrict__ tw, int tw_log2,
             const typename V2<T>::t* __restrict__ tpost, T s, T invN) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int bs = N2 + 1;
-  C* bufA = reinterpret_cast<C*>(smem);
-  C* bufB = bufA + (size_t)2 * P * bs;
+  const int bs = pad_stride(N2);
+  C* buf = reinterpret_cast<C*>(smem);
+  C* tws = buf + (size_t)2 * P * bs;
+  const bool smem_tw = sizeof(T) == 4;
+  if (smem_tw) load_tw_smem<T>(tws, tw, N2, log2N2, tw_log2);
   __shared__ T red[32];
   const int vec = blockIdx.y;
   const C* A = Ain + (int64_t)vec * N;
@@ -371,42 +440,59 @@ __global__ void __launch_bounds__(256)
   }
   // load 2P rows: local row q = 2 i (+1) for pair p0 + i
   const int total = 2 * P * N2;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int q = idx / N2;
-    const int j2 = idx - q * N2;
-    const int p = p0 + (q >> 1);
-    const int row = (q & 1) == 0 ? p : (p == 0 ? N1 / 2 : N1 - p);
-    bufA[q * bs + j2] = A[(int64_t)row * N2 + j2];
+  for (int idx0 = threadIdx.x; idx0 < total; idx0 += 4 * blockDim.x) {
+    C z[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = idx0 + u * blockDim.x;
+      if (idx < total) {
+        const int q = idx / N2;
+        const int p = p0 + (q >> 1);
+        const int row = (q & 1) == 0 ? p : (p == 0 ? N1 / 2 : N1 - p);
+        z[u] = A[(int64_t)row * N2 + (idx - q * N2)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = idx0 + u * blockDim.x;
+      if (idx < total) {
+        const int q = idx / N2;
+        buf[q * bs + padi(idx - q * N2)] = z[u];
+      }
+    }
   }
   __syncthreads();
-  C* R = fft_smem<T>(bufA, bufB, N2, log2N2, 2 * P, bs, tw, tw_log2);
+  if (smem_tw)
+    fft16<T>(buf, N2, log2N2, 2 * P, bs, tws, log2N2);
+  else
+    fft16<T>(buf, N2, log2N2, 2 * P, bs, tw, tw_log2);
   const int half = N / 2;
   for (int idx = threadIdx.x; idx < P * N2; idx += blockDim.x) {
     const int i = idx / N2;
     const int k2 = idx - i * N2;
     const int p = p0 + i;
-    const C* ra = R + (2 * i) * bs;
-    const C* rb = R + (2 * i + 1) * bs;
+    const C* ra = buf + (2 * i) * bs;
+    const C* rb = buf + (2 * i + 1) * bs;
     if (p == 0) {
       // row 0 pairs internally (k2 <-> N2 - k2); row N1/2 pairs k2 <-> N2 - 1 - k2
       if (k2 <= N2 / 2) {
         const int k = N1 * k2;
         T yk, ynk;
-        split_pair<T>(ra[k2], ra[(N2 - k2) & (N2 - 1)], tpost[k], yk, ynk);
+        split_pair<T>(ra[padi(k2)], ra[padi((N2 - k2) & (N2 - 1))], tpost[k], yk, ynk);
         ep_write<T, E>(out, k, yk, N, s, Y0, invN);
         if (k != half) ep_write<T, E>(out, N - k, ynk, N, s, Y0, invN);
       }
       if (k2 < N2 / 2) {
         const int k = N1 / 2 + N1 * k2;
         T yk, ynk;
-        split_pair<T>(rb[k2], rb[N2 - 1 - k2], tpost[k], yk, ynk);
+        split_pair<T>(rb[padi(k2)], rb[padi(N2 - 1 - k2)], tpost[k], yk, ynk);
         ep_write<T, E>(out, k, yk, N, s, Y0, invN);
         ep_write<T, E>(out, N - k, ynk, N, s, Y0, invN);
       }
     } else {
       const int k = p + N1 * k2;
-      const C zk = ra[k2];
-      const C zc = rb[N2 - 1 - k2];
+      const C zk = ra[padi(k2)];
+      const C zc = rb[padi(N2 - 1 - k2)];
       T yk, ynk;
       if (k <= half) {
         split_pair<T>(zk, zc, tpost[k], yk, ynk);
@@ -437,14 +523,28 @@ static bk_status build_tables(Plan* p, cudaStream_t st) {
   k_tw_table<T><<<(int)std::min<int64_t>((ntab + 255) / 256, 4096), 256, 0, st>>>(
       (C*)p->tw, ntab, (double)ntab);
   BK_CHECK_LAUNCH();
+  BK_TRY(dmalloc(&p->rk, sizeof(T) * (N + 2)));
+  k_rk_table<T><<<(int)std::min<int64_t>((N + 2 + 255) / 256, 4096), 256, 0, st>>>((T*)p->rk, N + 2);
+  BK_CHECK_LAUNCH();
   BK_TRY(dmalloc(&p->tpost, sizeof(C) * (N / 2 + 1)));
   k_post_table<T><<<(int)std::min<int64_t>((N / 2 + 256) / 256, 4096), 256, 0, st>>>((C*)p->tpost, N);
   BK_CHECK_LAUNCH();
   if (!p->small) {
-    BK_TRY(dmalloc(&p->twN, sizeof(C) * N));
-    k_tw_table<T><<<(int)std::min<int64_t>((N + 255) / 256, 8192), 256, 0, st>>>((C*)p->twN, N,
-                                                                                  (double)N);
-    BK_CHECK_LAUNCH();
+    if (sizeof(T) == 8) {
+      BK_TRY(dmalloc(&p->twN, sizeof(C) * N));
+      k_tw_table<T><<<(int)std::min<int64_t>((N + 255) / 256, 8192), 256, 0, st>>>((C*)p->twN, N, (double)N);
+      BK_CHECK_LAUNCH();
+    } else {
+      const int log2N = ilog2(N);
+      p->tw_h = (log2N + 1) / 2;
+      const int64_t nlo = int64_t(1) << p->tw_h, nhi = N >> p->tw_h;
+      BK_TRY(dmalloc(&p->twLo, sizeof(C) * nlo));
+      BK_TRY(dmalloc(&p->twHi, sizeof(C) * nhi));
+      k_tw_table<T><<<(int)((nlo + 255) / 256), 256, 0, st>>>((C*)p->twLo, nlo, (double)N);
+      BK_CHECK_LAUNCH();
+      k_tw_table_strided<T><<<(int)((nhi + 255) / 256), 256, 0, st>>>((C*)p->twHi, nhi, nlo, (double)N);
+      BK_CHECK_LAUNCH();
+    }
   }
   return BK_OK;
 }
@@ -495,36 +595,51 @@ template <typename T>
 static size_t smem_small(int64_t N) {
   const int64_t L = N + 1;
   const int64_t Lp = (L + 3) & ~3;
-  return sizeof(T) * 2 * Lp + 2 * sizeof(typename V2<T>::t) * N;
+  return sizeof(T) * 2 * Lp + sizeof(typename V2<T>::t) * (size_t)pad_stride((int)N);
+}
+
+static int round_threads(int64_t t) {
+  t = (t + 31) / 32 * 32;
+  return (int)std::min<int64_t>(1024, std::max<int64_t>(32, t));
 }
 
 static constexpr size_t FOURSTEP_SMEM_BUDGET = 192 * 1024;
+
+// Complex elements one four-step CTA transforms (its tile: NB columns of N1 in pass A, 2P rows
+// of N2 in pass B; 16 per thread). BK_FOURSTEP_ELEMS overrides the default (tuning).
+static int fourstep_elems(int dtype) {
+  const int cap = dtype == BK_F64 ? 4096 : 8192;  // 16 per thread at the thread cap
+  const char* e = getenv("BK_FOURSTEP_ELEMS");
+  if (e) {
+    long v = atol(e);
+    if (v >= 512 && v <= cap && is_pow2(v)) return (int)v;
+  }
+  return cap;
+}
 
 static bk_status configure_fourstep(Plan* p) {
   const int log2N = ilog2(p->N);
   p->N1 = 1 << (log2N / 2);
   p->N2 = 1 << (log2N - log2N / 2);
   const size_t csz = 2 * dtype_size(p->dtype);
-  const size_t budget = FOURSTEP_SMEM_BUDGET;  // bytes for the two ping-pong buffers
-  // pass A: NB columns of N1 (padded), two buffers
-  int NB = (int)(budget / (2 * csz * (p->N1 + 1)));
+  const int E = fourstep_elems(p->dtype);
+  // pass A: NB columns of N1; pass B: P row pairs (2P rows) of N2
+  int NB = std::max(1, E / p->N1);
   if (NB > p->N2) NB = p->N2;
-  int nb = 1;
-  while (nb * 2 <= NB) nb *= 2;
-  p->NB = nb;
-  // pass B: P pairs = 2P rows of N2 (padded)
-  int rows = (int)(budget / (2 * csz * (p->N2 + 1)));
-  int P = rows / 2;
-  int pp = 1;
-  while (pp * 2 <= P) pp *= 2;
-  if (pp > p->N1 / 2) pp = p->N1 / 2;
-  p->P = pp;
-  if (p->NB < 1 || p->P < 1) {
+  int P = std::max(1, E / (2 * p->N2));
+  if (P > p->N1 / 2) P = p->N1 / 2;
+  p->NB = NB;
+  p->P = P;
+  p->smemA = csz * ((size_t)NB * pad_stride(p->N1) + (p->dtype == BK_F32 ? p->N1 : 0));
+  p->smemB = csz * ((size_t)2 * P * pad_stride(p->N2) + (p->dtype == BK_F32 ? p->N2 : 0));
+  p->thrA = round_threads((int64_t)NB * p->N1 / 16);
+  p->thrB = round_threads((int64_t)2 * P * p->N2 / 16);
+  const int maxthr = p->dtype == BK_F64 ? 256 : 512;
+  if ((int64_t)NB * p->N1 / 16 > maxthr || (int64_t)2 * P * p->N2 / 16 > maxthr || p->smemA > FOURSTEP_SMEM_BUDGET ||
+      p->smemB > FOURSTEP_SMEM_BUDGET) {
     set_error("four-step configuration failed for N=%lld", (long long)p->N);
     return BK_ERR_UNSUPPORTED;
   }
-  p->smemA = 2 * csz * (size_t)p->NB * (p->N1 + 1);
-  p->smemB = 2 * csz * (size_t)2 * p->P * (p->N2 + 1);
   p->nPartA = p->N2 / p->NB;
   return BK_OK;
 }
@@ -532,22 +647,32 @@ static bk_status configure_fourstep(Plan* p) {
 // The dynamic shared-memory cap is a per-function setting shared by every plan, so it is set to
 // the largest size any plan of the type can request (never to one plan's own size, which would
 // lower the cap under plans created earlier).
+// Kernel attributes: the dynamic shared-memory cap (largest size any plan of the type requests)
+// and a carveout that gives shared memory the whole unified L1/shared array, so that several
+// transform CTAs stay resident per SM.
+template <typename K>
+static bk_status smem_attr(K* fn, int cap) {
+  BK_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  BK_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  return BK_OK;
+}
+
 template <typename T>
 static bk_status set_smem_attrs(const Plan* p) {
   if (p->small) {
     const int cap = (int)smem_small<T>(small_limit(p->dtype));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_birkhoff_small<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_birkhoff_small<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    BK_TRY(smem_attr(k_birkhoff_small<T, false>, cap));
+    BK_TRY(smem_attr(k_birkhoff_small<T, true>, cap));
   } else {
     const int cap = (int)FOURSTEP_SMEM_BUDGET;
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, IN_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, IN_WINV>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, ST_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passA<T, ST_TRN>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_STORE_TRN>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_FWD_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    BK_TRY_CUDA(cudaFuncSetAttribute(k_passB<T, EP_TRN_OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    BK_TRY(smem_attr(k_passA<T, IN_PLAIN>, cap));
+    BK_TRY(smem_attr(k_passA<T, IN_WINV>, cap));
+    BK_TRY(smem_attr(k_passA<T, ST_FWD>, cap));
+    BK_TRY(smem_attr(k_passA<T, ST_TRN>, cap));
+    BK_TRY(smem_attr(k_passB<T, EP_STORE>, cap));
+    BK_TRY(smem_attr(k_passB<T, EP_STORE_TRN>, cap));
+    BK_TRY(smem_attr(k_passB<T, EP_FWD_OUT>, cap));
+    BK_TRY(smem_attr(k_passB<T, EP_TRN_OUT>, cap));
   }
   return BK_OK;
 }
@@ -579,6 +704,8 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
   do {
     if (p->small) {
       p->smemS = dtype == BK_F64 ? smem_small<double>(N) : smem_small<float>(N);
+      p->thrS = round_threads(N / 16);
+      if (p->thrS > (dtype == BK_F64 ? 256 : 512)) p->thrS = dtype == BK_F64 ? 256 : 512;
     } else {
       if ((st_ = configure_fourstep(p)) != BK_OK) break;
       const int64_t nvec = (int64_t)n_comp * max_batch;
@@ -614,7 +741,10 @@ void plan_destroy(Plan* p) {
   dfree(p->wT);
   dfree(p->tw);
   dfree(p->tpost);
+  dfree(p->rk);
   dfree(p->twN);
+  dfree(p->twLo);
+  dfree(p->twHi);
   dfree(p->scrA);
   dfree(p->scrY);
   dfree(p->part1);
@@ -630,11 +760,14 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
   const int N = (int)p->N;
   const T s = (T)s_scale;
   const T invN = T(1) / T(N);
+  StencilTab<T> tb;
+  tb.rk = (const T*)p->rk;
+  tb.cN = (T)(1.0 / (4.0 * ((double)N * (double)N - 1.0)));
   if (p->small) {
     if (!trans)
-      k_birkhoff_small<T, false><<<nvec, 256, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, p->tw_log2, (const C*)p->tpost);
+      k_birkhoff_small<T, false><<<nvec, p->thrS, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, p->tw_log2, (const C*)p->tpost, tb);
     else
-      k_birkhoff_small<T, true><<<nvec, 256, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, p->tw_log2, (const C*)p->tpost);
+      k_birkhoff_small<T, true><<<nvec, p->thrS, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, p->tw_log2, (const C*)p->tpost, tb);
     BK_CHECK_LAUNCH();
     return BK_OK;
   }
@@ -651,23 +784,23 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
   const C* tp = (const C*)p->tpost;
   const int64_t Ls = N + 1;
   if (!trans) {
-    k_passA<T, IN_PLAIN><<<gA, 256, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN);
+    k_passA<T, IN_PLAIN><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
-    k_passB<T, EP_STORE><<<gB, 256, p->smemB, st>>>(A, Ystage, Ls, 0, nullptr, 0, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
+    k_passB<T, EP_STORE><<<gB, p->thrB, p->smemB, st>>>(A, Ystage, Ls, 0, nullptr, 0, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
     BK_CHECK_LAUNCH();
-    k_passA<T, ST_FWD><<<gA, 256, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN);
+    k_passA<T, ST_FWD><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
-    k_passB<T, EP_FWD_OUT><<<gB, 256, p->smemB, st>>>(A, out, p->pitch, p->pitch, pa2, nPA, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
+    k_passB<T, EP_FWD_OUT><<<gB, p->thrB, p->smemB, st>>>(A, out, p->pitch, p->pitch, pa2, nPA, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
     BK_CHECK_LAUNCH();
   } else {
-    k_passA<T, IN_WINV><<<gA, 256, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN);
+    k_passA<T, IN_WINV><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
-    k_passB<T, EP_STORE_TRN><<<gB, 256, p->smemB, st>>>(A, Ystage, Ls, 0, pa1, nPA, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
+    k_passB<T, EP_STORE_TRN><<<gB, p->thrB, p->smemB, st>>>(A, Ystage, Ls, 0, pa1, nPA, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
     BK_CHECK_LAUNCH();
     // the stage buffer already holds Y - Y0, so the transposed stencil runs with Y0 = 0
-    k_passA<T, ST_TRN><<<gA, 256, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN);
+    k_passA<T, ST_TRN><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
-    k_passB<T, EP_TRN_OUT><<<gB, 256, p->smemB, st>>>(A, out, p->pitch, p->pitch, nullptr, 0, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
+    k_passB<T, EP_TRN_OUT><<<gB, p->thrB, p->smemB, st>>>(A, out, p->pitch, p->pitch, nullptr, 0, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
     BK_CHECK_LAUNCH();
   }
   return BK_OK;
@@ -712,7 +845,7 @@ static std::mutex g_noalloc_mu;
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Bytes of the scratch layout for N (FP64) and nvec vectors, and the sub-buffer offsets.
-static size_t noalloc_layout(const Plan& p, int nvec, size_t off[7]) {
+static size_t noalloc_layout(const Plan& p, int nvec, size_t off[8]) {
   const int64_t N = p.N;
   size_t o = 0;
   off[0] = o; o += align256(sizeof(double2) * std::max(p.N1, p.N2));                  // tw
@@ -722,6 +855,7 @@ static size_t noalloc_layout(const Plan& p, int nvec, size_t off[7]) {
   off[4] = o; o += align256(sizeof(double) * (size_t)(N + 1) * nvec);                 // scrY
   off[5] = o; o += align256(sizeof(double) * (size_t)p.nPartA * nvec);                // part1
   off[6] = o; o += align256(sizeof(double) * (size_t)p.nPartA * nvec);                // part2
+  off[7] = o; o += align256(sizeof(double) * (size_t)(N + 2));                        // rk
   return o;
 }
 
@@ -766,7 +900,7 @@ bk_status noalloc_apply(const double* v, double* out, int64_t N, int nvec, int64
   p.s = 0.5 * (tf - t0);
   p.small = false;
   BK_TRY(configure_fourstep(&p));
-  size_t off[7];
+  size_t off[8];
   const size_t need = noalloc_layout(p, nvec, off);
   BK_ARG(need <= NOALLOC_BYTES, "N=%lld with %d vectors needs %zu bytes of scratch, more than the %zu reserved",
          (long long)N, nvec, need, NOALLOC_BYTES);
@@ -778,7 +912,10 @@ bk_status noalloc_apply(const double* v, double* out, int64_t N, int nvec, int64
   p.tw = b + off[0];
   p.tpost = b + off[1];
   p.twN = b + off[2];
+  p.rk = b + off[7];
   // every table is rewritten by each call: nothing in the array has to start at zero
+  k_rk_table<double><<<(int)std::min<int64_t>((N + 2 + 255) / 256, 4096), 256, 0, st>>>((double*)p.rk, N + 2);
+  BK_CHECK_LAUNCH();
   k_tw_table<double><<<(int)std::min<int64_t>((ntab + 255) / 256, 4096), 256, 0, st>>>((double2*)p.tw, ntab, (double)ntab);
   BK_CHECK_LAUNCH();
   k_post_table<double><<<(int)std::min<int64_t>((N / 2 + 256) / 256, 4096), 256, 0, st>>>((double2*)p.tpost, N);

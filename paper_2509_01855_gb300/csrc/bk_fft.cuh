@@ -1,15 +1,25 @@
-// Shared-memory batched complex FFT (Stockham autosort, radix 8/4/2) used by the DCT-I
-// transforms of the Birkhoff products. Forward transform, omega_n = exp(-2 pi i / n).
+// Shared-memory batched complex FFT used by the DCT-I transforms of the Birkhoff products.
+// Forward transform, omega_n = exp(-2 pi i / n).
+//
+// In-place Stockham autosort with radix 16 (one mixed radix 2/4/8 stage first when log2 n is
+// not a multiple of 4). Every thread stages exactly 16 values per stage in registers (one
+// radix-16 butterfly, or 16/R butterflies of radix R), so one buffer suffices: read, barrier,
+// compute, write, barrier. Shared addresses are padded, a -> a + a/16, which makes the Stockham
+// writes conflict-free for 8- and 16-byte complex values; batches sit bs >= n + n/16 + 1 apart.
 //
 // Twiddles come from a table tw[i] = (cos(2 pi i / n_tab), -sin(2 pi i / n_tab)), i < n_tab,
-// n_tab = 2^tw_log2 >= n, built on the device with sincospi at plan creation.
+// n_tab = 2^tw_log2 >= n, built on the device with sincospi at plan creation; the table may be
+// the global one or a copy in shared memory (load_tw_smem).
 #pragma once
 
 #include "bk_common.cuh"
 
 namespace bk {
 
-// Radix-R DFT of v[0..R-1] in registers (forward).
+__device__ __forceinline__ int padi(int a) { return a + (a >> 4); }
+__host__ __device__ inline int pad_stride(int n) { return n + (n >> 4) + 1; }
+
+// Radix-R DFT of v[0..R-1] in registers (forward, natural order in and out).
 template <typename C, typename T, int R> struct Radix;
 
 template <typename C, typename T> struct Radix<C, T, 2> {
@@ -33,7 +43,6 @@ template <typename C, typename T> struct Radix<C, T, 4> {
 
 template <typename C, typename T> struct Radix<C, T, 8> {
   static __device__ __forceinline__ void run(C* v) {
-    // even / odd radix-4 halves, then combine with omega_8^k
     C e[4] = {v[0], v[2], v[4], v[6]};
     C o[4] = {v[1], v[3], v[5], v[7]};
     Radix<C, T, 4>::run(e);
@@ -57,70 +66,122 @@ template <typename C, typename T> struct Radix<C, T, 8> {
   }
 };
 
-// One Stockham stage with radix R over `nbatch` transforms of length n (batch stride bs).
-// Ns = product of the radices of the previous stages (1 for the first stage).
-template <typename T, int R>
-__device__ __forceinline__ void stockham_stage(const typename V2<T>::t* __restrict__ src,
-                                               typename V2<T>::t* __restrict__ dst, int n,
-                                               int log2n, int nbatch, int bs, int Ns, int log2Ns,
-                                               const typename V2<T>::t* __restrict__ tw,
-                                               int tw_log2) {
-  typedef typename V2<T>::t C;
-  const int nbf = n / R;  // butterflies per transform
-  const int log2nbf = log2n - (R == 8 ? 3 : (R == 4 ? 2 : 1));
-  const int total = nbatch << log2nbf;
-  const int log2R = (R == 8 ? 3 : (R == 4 ? 2 : 1));
-  const int tw_shift = tw_log2 - (log2Ns + log2R);
-  for (int j = threadIdx.x; j < total; j += blockDim.x) {
-    const int b = j >> log2nbf;
-    const int jj = j & (nbf - 1);
-    const int k = jj & (Ns - 1);
-    const C* s = src + (size_t)b * bs;
-    C v[R];
+// Radix 16 as 4 x 4: r = r1 + 4 r2, s = s1 + 4 s2,
+//   X[s1 + 4 s2] = sum_r1 omega_4^{r1 s2} omega_16^{r1 s1} sum_r2 v[r1 + 4 r2] omega_4^{r2 s1}.
+template <typename C, typename T> struct Radix<C, T, 16> {
+  static __device__ __forceinline__ void run(C* v) {
+    // cos(pi/8) = sqrt(2 + sqrt 2)/2, sin(pi/8) = sqrt(2 - sqrt 2)/2, sqrt(1/2)
+    const T c1 = T(0.92387953251128675612818318939678828682241662586364);
+    const T s1 = T(0.38268343236508977172845998403039886676134456248563);
+    const T h = T(0.70710678118654752440084436210484903928483593768847);
+    C y[4][4];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = s[jj + r * nbf];
-    if (Ns > 1) {
+    for (int r1 = 0; r1 < 4; ++r1) {
+      C t[4] = {v[r1], v[r1 + 4], v[r1 + 8], v[r1 + 12]};
+      Radix<C, T, 4>::run(t);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(&tw[(r * k) << tw_shift]));
+      for (int q = 0; q < 4; ++q) y[r1][q] = t[q];
     }
-    Radix<C, T, R>::run(v);
-    C* d = dst + (size_t)b * bs;
-    const int idxD = ((jj >> log2Ns) << (log2Ns + log2R)) + k;
+    // internal twiddles omega_16^{r1 s1}, r1, s1 in 1..3 (exponents 1,2,3,2,4,6,3,6,9)
+    C a;
+    a = y[1][1]; y[1][1].x = c1 * a.x + s1 * a.y; y[1][1].y = c1 * a.y - s1 * a.x;       // w^1
+    a = y[1][2]; y[1][2].x = h * (a.x + a.y); y[1][2].y = h * (a.y - a.x);                // w^2
+    a = y[1][3]; y[1][3].x = s1 * a.x + c1 * a.y; y[1][3].y = s1 * a.y - c1 * a.x;       // w^3
+    a = y[2][1]; y[2][1].x = h * (a.x + a.y); y[2][1].y = h * (a.y - a.x);                // w^2
+    y[2][2] = cmul_mi(y[2][2]);                                                           // w^4
+    a = y[2][3]; y[2][3].x = h * (a.y - a.x); y[2][3].y = -h * (a.x + a.y);               // w^6
+    a = y[3][1]; y[3][1].x = s1 * a.x + c1 * a.y; y[3][1].y = s1 * a.y - c1 * a.x;       // w^3
+    a = y[3][2]; y[3][2].x = h * (a.y - a.x); y[3][2].y = -h * (a.x + a.y);               // w^6
+    a = y[3][3]; y[3][3].x = -c1 * a.x - s1 * a.y; y[3][3].y = s1 * a.x - c1 * a.y;      // w^9
 #pragma unroll
-    for (int r = 0; r < R; ++r) d[idxD + r * Ns] = v[r];
+    for (int q = 0; q < 4; ++q) {
+      C t[4] = {y[0][q], y[1][q], y[2][q], y[3][q]};
+      Radix<C, T, 4>::run(t);
+#pragma unroll
+      for (int s2 = 0; s2 < 4; ++s2) v[q + 4 * s2] = t[s2];
+    }
+  }
+};
+
+// One in-place stage of radix R (16/R butterflies per thread). Ns = product of the previous
+// radices. Threads t < nbatch * n/16 work; all threads must reach the barriers.
+template <typename T, int R>
+__device__ __forceinline__ void stage16(typename V2<T>::t* __restrict__ buf, int n, int log2n, int nbatch,
+                                        int bs, int Ns, int log2Ns,
+                                        const typename V2<T>::t* __restrict__ tw, int tw_log2) {
+  typedef typename V2<T>::t C;
+  constexpr int log2R = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
+  constexpr int PER = 16 / R;
+  const int log2nb16 = log2n - 4;
+  const int nb16 = 1 << log2nb16;
+  const int t = threadIdx.x;
+  const bool active = t < (nbatch << log2nb16);
+  const int b = t >> log2nb16;
+  const int tt = t & (nb16 - 1);
+  C* base = buf + (size_t)b * bs;
+  const int nR = n >> log2R;
+  C v[16];
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int j = tt + q * nb16;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q * R + r] = base[padi(j + r * nR)];
+    }
+  }
+  __syncthreads();
+  if (active) {
+    const int tw_shift = tw_log2 - (log2Ns + log2R);
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int j = tt + q * nb16;
+      const int k = j & (Ns - 1);
+      C* u = v + q * R;
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw[(r * k) << tw_shift]);
+      }
+      Radix<C, T, R>::run(u);
+      const int idxD = ((j >> log2Ns) << (log2Ns + log2R)) + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) base[padi(idxD + r * Ns)] = u[r];
+    }
+  }
+  __syncthreads();
+}
+
+// Batched in-place forward FFT of length n = 2^log2n (16 <= n) over `nbatch` padded transforms
+// bs apart in shared memory (element i of batch b at buf[b * bs + padi(i)]). The block needs at
+// least nbatch * n / 16 threads. Input complete before the call (barrier); result complete on
+// return, in natural order, in place.
+template <typename T>
+__device__ void fft16(typename V2<T>::t* buf, int n, int log2n, int nbatch, int bs,
+                      const typename V2<T>::t* __restrict__ tw, int tw_log2) {
+  int Ns = 1, log2Ns = 0;
+  const int rem = log2n & 3;
+  if (rem == 1) {
+    stage16<T, 2>(buf, n, log2n, nbatch, bs, Ns, log2Ns, tw, tw_log2);
+    Ns = 2; log2Ns = 1;
+  } else if (rem == 2) {
+    stage16<T, 4>(buf, n, log2n, nbatch, bs, Ns, log2Ns, tw, tw_log2);
+    Ns = 4; log2Ns = 2;
+  } else if (rem == 3) {
+    stage16<T, 8>(buf, n, log2n, nbatch, bs, Ns, log2Ns, tw, tw_log2);
+    Ns = 8; log2Ns = 3;
+  }
+  while (log2Ns < log2n) {
+    stage16<T, 16>(buf, n, log2n, nbatch, bs, Ns, log2Ns, tw, tw_log2);
+    Ns <<= 4;
+    log2Ns += 4;
   }
 }
 
-// Batched forward FFT of length n = 2^log2n over shared buffers a (input) and b (scratch).
-// Returns the buffer holding the result. All threads of the block must call it; the input must
-// be complete (a __syncthreads() before the call); the result is complete on return.
+// Copy omega_n^i, i < n, from the plan table (n_tab = 2^tw_log2 >= n) into shared memory.
 template <typename T>
-__device__ typename V2<T>::t* fft_smem(typename V2<T>::t* a, typename V2<T>::t* b, int n,
-                                       int log2n, int nbatch, int bs,
-                                       const typename V2<T>::t* __restrict__ tw, int tw_log2) {
-  typedef typename V2<T>::t C;
-  C* src = a;
-  C* dst = b;
-  int Ns = 1, log2Ns = 0;
-  const int rem = log2n % 3;
-  if (rem == 1) {
-    stockham_stage<T, 2>(src, dst, n, log2n, nbatch, bs, Ns, log2Ns, tw, tw_log2);
-    __syncthreads();
-    Ns <<= 1; log2Ns += 1;
-    C* t = src; src = dst; dst = t;
-  } else if (rem == 2) {
-    stockham_stage<T, 4>(src, dst, n, log2n, nbatch, bs, Ns, log2Ns, tw, tw_log2);
-    __syncthreads();
-    Ns <<= 2; log2Ns += 2;
-    C* t = src; src = dst; dst = t;
-  }
-  while (log2Ns < log2n) {
-    stockham_stage<T, 8>(src, dst, n, log2n, nbatch, bs, Ns, log2Ns, tw, tw_log2);
-    __syncthreads();
-    Ns <<= 3; log2Ns += 3;
-    C* t = src; src = dst; dst = t;
-  }
-  return src;
+__device__ __forceinline__ void load_tw_smem(typename V2<T>::t* dst, const typename V2<T>::t* __restrict__ tw,
+                                             int n, int log2n, int tw_log2) {
+  const int sh = tw_log2 - log2n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = __ldg(&tw[i << sh]);
 }
 
 }  // namespace bk

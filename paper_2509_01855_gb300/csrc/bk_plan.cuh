@@ -11,14 +11,20 @@ struct Plan {
   double t0 = 0, tf = 0, s = 0;
   bool small = true;          // whole chain in one CTA per vector
   size_t smemS = 0;           // dynamic shared memory of the single-CTA kernel
+  int thrS = 256;             // threads of the single-CTA kernel
   int N1 = 0, N2 = 0;         // four-step factors, N = N1 * N2
   int NB = 0, P = 0;          // pass A columns per CTA, pass B row pairs per CTA
   size_t smemA = 0, smemB = 0;
+  int thrA = 256, thrB = 256; // threads of the pass kernels (16 complex values each)
   int nPartA = 0;             // pass-A CTAs per vector (partials per vector)
   int tw_log2 = 0;
   void* tw = nullptr;         // sub-FFT twiddles (complex, working type)
   void* tpost = nullptr;      // (cos, sin)(pi k / N), k = 0..N/2 (working type)
-  void* twN = nullptr;        // omega_N^m, m < N (four-step only)
+  void* rk = nullptr;         // 1 / (4k), k = 0..N+1 (working type; rk[0] = 0)
+  void* twN = nullptr;        // omega_N^m, m < N (four-step, FP64)
+  void* twLo = nullptr;       // omega_N^m, m < 2^tw_h (four-step, FP32)
+  void* twHi = nullptr;       // omega_N^{m 2^tw_h}, m < N / 2^tw_h (four-step, FP32)
+  int tw_h = 0;
   void* scrA = nullptr;       // four-step complex scratch, N per vector
   void* scrY = nullptr;       // stage buffer between the two DCTs, N + 1 per vector
   void* part1 = nullptr;      // pass-A partial sums, first DCT
