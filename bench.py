@@ -44,7 +44,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="newton_f64",
-                    choices=["newton_f64", "newton_f32ir", "apply_f64", "apply_f32"])
+                    choices=["newton_f64", "newton_f32ir", "apply_f64", "apply_f32", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=0,
+                    help="serving requests (default 4096 for --workload serve, 512 in the default "
+                         "line; -1 skips serving in the default line)")
+    ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--N", type=int, default=20, help="log2 of the grid size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -261,6 +265,34 @@ def measure_apply(N, dtype, reps=20):
     return ms, nbytes, flops
 
 
+def run_serve(n_requests, slots, rank=0, world=1, dist=None):
+    """Serving: 4096-request-class Poisson stream, N = 2^k with k ~ U{8..16}, r_f ~ U[1.2, 2.0],
+    t_f ~ U[10, 30]; offered load 0.8 x the closed-loop maximum rate of this GPU."""
+    import torch
+    from paper_2509_01855_gb300 import synth
+    from paper_2509_01855_gb300.serve import Server, combine_stats, run_schedule, shard_requests
+    srv = Server(dtype=torch.float64, max_slots=slots)
+    warm = [dict(id=i, arrival=0.0, N=1 << k, rf=1.5, tf=20.0) for i, k in enumerate(range(8, 17))]
+    srv.run(warm, realtime=False)
+    probe = shard_requests(synth.serving_requests(256, 1.0, "probe"), rank, world)
+    for r in probe:
+        r["arrival"] = 0.0
+    _, st_closed = srv.run(probe, realtime=False)
+    max_rate = max_over_ranks(-st_closed["solves_per_s"], dist)   # slowest rank sets the rate
+    max_rate = -max_rate * world
+    rate = 0.8 * max_rate
+    reqs = shard_requests(synth.serving_requests(n_requests, rate, "stream"), rank, world)
+    t0 = time.perf_counter()
+    res = run_schedule(reqs, srv.pool, srv.solve, srv.max_slots, realtime=True)
+    st = combine_stats(res, time.perf_counter() - t0, dist)
+    iters = [r["newton_iterations"] for r in res if r.get("status") == "ok"]
+    srv.close()
+    st.update(offered_rate=rate, closed_loop_max_rate=max_rate, slots=slots, dtype="f64",
+              newton_iterations_max=int(max(iters)) if iters else None,
+              workload="orbit raising, N=2^k k~U{8..16}, r_f~U[1.2,2], t_f~U[10,30], Poisson arrivals")
+    return st
+
+
 # ------------------------------------------------------------------------------------------
 # Oracle legs (CPU)
 # ------------------------------------------------------------------------------------------
@@ -318,7 +350,7 @@ def metric_name(args):
 
 def config(args):
     prec = {"newton_f64": "f64", "newton_f32ir": "f32 Krylov + f64 refinement",
-            "apply_f64": "f64", "apply_f32": "f32"}[args.workload]
+            "apply_f64": "f64", "apply_f32": "f32", "serve": "f64"}[args.workload]
     c = {"workload": "orbit_raising_newton_krylov" if args.workload.startswith("newton") else "birkhoff_apply",
          "N": 1 << args.N, "nodes": (1 << args.N) + 1, "precision": prec,
          "problem": "polar orbit raising r 1->%.1f, t_f=%g, thrust-vector min-energy, x0=(1,0,0,1)" % (RF, TF),
@@ -336,11 +368,24 @@ def main():
     rank, world, dist = dist_setup(args)
     hbm_peak, peak_kind = read_peaks()
     N = 1 << args.N
-    dtype_name = "f64" if args.workload in ("newton_f64", "apply_f64") else "f32"
+    dtype_name = "f64" if args.workload in ("newton_f64", "apply_f64", "serve") else "f32"
     line = {"metric": metric_name(args), "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype_name, "data": "synthetic", "config": config(args)}
-    if args.workload.startswith("newton"):
+    if args.workload == "serve":
+        from paper_2509_01855_gb300 import _lib
+        lib = _lib.lib()
+        c0 = lib.bk_launch_count()
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            st = run_serve(args.serve_requests or 4096, args.serve_slots, rank, world, dist)
+        line.update(metric="served Newton-Krylov solves/s (orbit raising, mixed N)", value=st["solves_per_s"],
+                    unit="solves/s", ms_per_step=1000.0 / st["solves_per_s"] if st["solves_per_s"] else None,
+                    gpu_launches=lib.bk_launch_count() - c0, clocks=clk.summary(), serve=st,
+                    e2e={"value": st["solves_per_s"], "unit": "solves/s", "h2d_bytes_per_step": None,
+                         "d2h_bytes_per_step": None, "note": "latency = solution on host - arrival"})
+        line["config"]["workload"] = "serving"
+        dt = torch.float64
+    elif args.workload.startswith("newton"):
         r = run_newton(args, rank, world, dist)
         line.update(value=world * 1000.0 / r["ms"], unit="solves/s", ms_per_step=r["ms"], e2e=r["e2e"],
                     gpu_launches=r["launches"], clocks=r["clocks"], solve=r["solve"])
@@ -370,6 +415,8 @@ def main():
                                         else "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind)}
     line["apply"] = {"ms": ams, "gbs": abytes / ams / 1e6, "tflops": aflops / ams / 1e9, "N": N,
                      "n_comp": 4, "dtype": dtype_name}
+    if args.workload.startswith("newton") and args.serve_requests >= 0:
+        line["serve"] = run_serve(args.serve_requests or 512, args.serve_slots, rank, world, dist)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

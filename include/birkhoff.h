@@ -158,6 +158,17 @@ bk_status bk_problem_create(bk_problem** prob, int kind, const double* params, i
                             int64_t N, bk_dtype dtype, double t0, double tf, void* stream);
 void bk_problem_destroy(bk_problem* prob);
 
+/* Change a problem's parameters and time interval in place (same kind, N and dtype) without
+ * allocating: BK_ORBIT params = {a_nominal, r_f}, BK_BILINEAR params = {x^a}. The previous
+ * linearisation is discarded. For request loops that reuse one problem per grid size. Host only;
+ * must not overlap work queued on the problem. */
+bk_status bk_problem_set_params(bk_problem* prob, const double* params, int nparams, double t0,
+                                double tf);
+
+/* Device bytes the problem holds (its plans, linearisation data and scratch); workspaces are
+ * extra (bk_krylov_workspace_bytes, bk_newton_workspace_bytes). For memory-based admission. */
+size_t bk_problem_device_bytes(const bk_problem* prob);
+
 /* Sizes of a problem (any pointer may be NULL):
  *   n_x, n_u, n_e  state, control and terminal-condition counts
  *   pitch          component block pitch in elements

@@ -118,6 +118,15 @@ class Problem:
     def handle(self):
         return self._h
 
+    def set_params(self, t0, tf, params):
+        """Reuse this problem for new parameters and interval (no allocation)."""
+        arr = (ctypes.c_double * max(1, len(params)))(*[float(x) for x in params])
+        L.check(L.lib().bk_problem_set_params(self._h, arr, len(params), float(t0), float(tf)))
+        self.t0, self.tf, self.params = float(t0), float(tf), tuple(params)
+
+    def device_bytes(self):
+        return int(L.lib().bk_problem_device_bytes(self._h))
+
     def vec_len(self, op):
         return self.kkt_len if op == L.BK_OP_KKT else self.state_len
 

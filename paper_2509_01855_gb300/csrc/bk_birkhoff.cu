@@ -47,6 +47,12 @@ namespace bk {
 
 static thread_local std::string g_last_error = "no error";
 static std::atomic<unsigned long long> g_launches{0};
+// When set (by the creating thread), dmalloc adds every allocation's size to it: plans and
+// problems report their device footprint this way.
+static thread_local size_t* g_alloc_acc = nullptr;
+
+AllocCounter::AllocCounter(size_t* acc) : prev(g_alloc_acc) { g_alloc_acc = acc; }
+AllocCounter::~AllocCounter() { g_alloc_acc = prev; }
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -62,6 +68,7 @@ void set_error(const char* fmt, ...) {
 bk_status dmalloc(void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return BK_OK;
+  if (g_alloc_acc) *g_alloc_acc += bytes;
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
@@ -701,6 +708,7 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
   p->pitch = pitch;
   p->small = N <= small_limit(dtype);
   bk_status st_ = BK_OK;
+  AllocCounter counter(&p->bytes);
   do {
     if (p->small) {
       p->smemS = dtype == BK_F64 ? smem_small<double>(N) : smem_small<float>(N);

@@ -77,4 +77,11 @@ inline size_t dtype_size(int dt) { return dt == BK_F64 ? 8 : 4; }
 bk_status dmalloc(void** p, size_t bytes);
 void dfree(void* p);
 
+// While alive, every dmalloc on this thread adds its size to *acc (nested counters stack).
+struct AllocCounter {
+  explicit AllocCounter(size_t* acc);
+  ~AllocCounter();
+  size_t* prev;
+};
+
 }  // namespace bk

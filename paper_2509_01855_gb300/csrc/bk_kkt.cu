@@ -836,6 +836,7 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
   const int64_t P = pr->P;
   const int nx = pr->n_x, nu = pr->n_u, ne = pr->n_e;
   BK_TRY(plan_create(&d.plan, pr->N, nx, 1, dtype, pr->t0, pr->tf, P, 0));
+  pr->bytes += d.plan->bytes;  // the plan counted its own allocations
   BK_TRY(dmalloc(&d.xu, es * (nx + nu) * P));
   BK_TRY(dmalloc(&d.mu, es * nx * P));
   d.w = dtype == BK_F64 ? (void*)d.plan->w64 : d.plan->wT;
@@ -1130,6 +1131,27 @@ static void problem_free(Problem* pr) {
   delete pr;
 }
 
+// Problem constants (x0, terminal targets, s) from kind, params and [t0, tf]; no allocation.
+static bk_status problem_set_params(Problem* pr, const double* params, int nparams, double t0, double tf) {
+  BK_ARG(tf > t0 && isfinite(t0) && isfinite(tf), "tf must be > t0 and finite");
+  BK_ARG(nparams >= 0 && nparams <= 4 && (nparams == 0 || params), "bad params");
+  if (pr->kind == BK_ORBIT) {
+    BK_ARG(nparams >= 2, "BK_ORBIT needs params {a_nominal, r_f}");
+    BK_ARG(params[1] > 0 && isfinite(params[1]), "r_f must be > 0");
+    pr->term_val[0] = params[1];
+    pr->term_val[1] = 0.0;
+    pr->term_val[2] = 1.0 / sqrt(params[1]);
+  } else if (pr->kind == BK_BILINEAR) {
+    pr->x0[0] = nparams >= 1 ? params[0] : 1.0;
+  }
+  for (int i = 0; i < 4; ++i) pr->params[i] = i < nparams ? params[i] : 0.0;
+  pr->t0 = t0;
+  pr->tf = tf;
+  pr->s = 0.5 * (tf - t0);
+  pr->linearized = false;
+  return BK_OK;
+}
+
 static bk_status problem_create(Problem** out, int kind, const double* params, int nparams, int64_t N, int dtype,
                                 double t0, double tf, cudaStream_t st) {
   *out = nullptr;
@@ -1171,6 +1193,7 @@ static bk_status problem_create(Problem** out, int kind, const double* params, i
   }
   pr->nseg = (int)((pr->L + SEG - 1) / SEG);
   pr->ngrp = (pr->nseg + GRP - 1) / GRP;
+  AllocCounter counter(&pr->bytes);
   bk_status s = alloc_opdata(pr, pr->d64, BK_F64);
   if (s == BK_OK && dtype == BK_F32) s = alloc_opdata(pr, pr->d32, BK_F32);
   if (s == BK_OK) s = dmalloc((void**)&pr->F, sizeof(double) * pr->kkt_len());
@@ -1214,6 +1237,15 @@ bk_status bk_problem_info(const bk_problem* prob, int* n_x, int* n_u, int* n_e, 
   if (kkt_len) *kkt_len = p->kkt_len();
   if (state_len) *state_len = p->state_len();
   return BK_OK;
+}
+
+bk_status bk_problem_set_params(bk_problem* prob, const double* params, int nparams, double t0, double tf) {
+  BK_ARG(prob != nullptr, "problem is NULL");
+  return bk::problem_set_params(reinterpret_cast<bk::Problem*>(prob), params, nparams, t0, tf);
+}
+
+size_t bk_problem_device_bytes(const bk_problem* prob) {
+  return prob ? reinterpret_cast<const bk::Problem*>(prob)->bytes : 0;
 }
 
 bk_status bk_linearize(bk_problem* prob, const double* z_lin, void* stream) {

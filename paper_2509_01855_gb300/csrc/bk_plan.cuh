@@ -32,6 +32,7 @@ struct Plan {
   double* t_nodes = nullptr;  // node times t_j (FP64, device)
   double* w64 = nullptr;      // Clenshaw-Curtis weights (FP64, device, tau-domain)
   void* wT = nullptr;         // Clenshaw-Curtis weights in the working type (device)
+  size_t bytes = 0;           // device bytes this plan allocated
 };
 
 bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtype, double t0,

@@ -144,6 +144,7 @@ struct Problem {
   double* F = nullptr;         // KKT residual scratch (FP64, kkt_len)
   double* red = nullptr;       // reduction scratch (FP64)
   double* red_host = nullptr;  // pinned host mirror of reduction results
+  size_t bytes = 0;            // device bytes this problem (and its plans) allocated
   int64_t kkt_len() const { return (2 * n_x + n_u) * P + 32; }
   int64_t state_len() const { return n_x * P; }
   OpData& work() { return dtype == BK_F64 ? d64 : d32; }
