@@ -236,12 +236,14 @@ bk_status krylov_solve(bk_problem* prob, int op, const void* rhs, void* sol,
 typedef struct {
   double tol;         /* stop when the weighted KKT residual norm <= tol (default 1e-10)     */
   int max_iter;       /* Newton iteration cap (default 30)                                  */
-  double krylov_rtol; /* inner relative tolerance (default 1e-12 in FP64, 1e-5 in FP32)     */
+  double krylov_rtol; /* inner relative tolerance (default 1e-12 in FP64, 1e-4 in FP32)     */
   int restart;        /* GMRES restart (default 30)                                         */
-  int max_krylov;     /* inner iteration cap per solve (default 300)                        */
-  double ir_rtol;     /* FP32 mode: FP64 iterative refinement until the FP64 residual of the
-                         Newton system is <= ir_rtol * ||F|| (default 1e-10)                 */
-  int max_refine;     /* FP32 mode: refinement sweeps cap (default 10)                      */
+  int max_krylov;     /* inner iteration cap per solve (default 300 in FP64, 10 in FP32)    */
+  double ir_rtol;     /* FP32 mode: linear refinement sweeps stop when the FP64 residual of
+                         the Newton system is <= ir_rtol * ||F|| (default 1e-10)             */
+  int max_refine;     /* FP32 mode: FP32 solves per Newton step (default 1: inexact Newton,
+                         the FP64 Newton residual refines the step; > 1 adds linear
+                         refinement sweeps with an FP64 KKT residual)                        */
 } bk_newton_opts;
 
 typedef struct {
@@ -260,7 +262,7 @@ size_t bk_newton_workspace_bytes(const bk_problem* prob, int restart);
 /* Newton-Lagrange solve of the discretised problem (Eq. Prob-PNa with V = f(X, U) eliminated):
  * F(z, y) = [grad J + G^T y ; c ; e] = 0 with c = X - x0 - s (B (x) I) f(X, U), e the terminal
  * conditions and J = s sum_i w_i F(x_i, u_i). Each step solves the KKT system by
- * preconditioned GMRES (BK_F32: FP32 GMRES inside FP64 iterative refinement), then a
+ * preconditioned GMRES (BK_F32: FP32 GMRES, refined by the FP64 Newton residual), then a
  * backtracking line search (alpha = 1, 1/2, ...; Armijo 1e-4) on the weighted norm
  *   ||F||_W^2 = sum_i w_i |c_i|^2 + sum_i |g_i|^2 / w_i + |e|^2  (g: gradient rows).
  *   z_inout    device FP64 KKT vector: initial guess in, solution out (X, U, lambda, nu)

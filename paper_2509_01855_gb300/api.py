@@ -215,9 +215,10 @@ def newton_workspace(prob, restart=30):
     return torch.empty(max(1, (nbytes + 255) // 256 * 32), dtype=torch.float64, device="cuda")
 
 
-def newton_solve(prob, z, tol=1e-10, max_iter=30, krylov_rtol=0.0, restart=30, max_krylov=300,
-                 ir_rtol=1e-10, max_refine=10, workspace=None, stream=None, raise_on_fail=True):
-    """Newton-Lagrange solve in place on the FP64 KKT vector z; returns the info fields."""
+def newton_solve(prob, z, tol=1e-10, max_iter=30, krylov_rtol=0.0, restart=30, max_krylov=0,
+                 ir_rtol=1e-10, max_refine=0, workspace=None, stream=None, raise_on_fail=True):
+    """Newton-Lagrange solve in place on the FP64 KKT vector z; returns the info fields.
+    Zero-valued options take the library defaults for the problem's precision."""
     if workspace is None:
         workspace = newton_workspace(prob, restart)
     opts = L.NewtonOpts(float(tol), int(max_iter), float(krylov_rtol), int(restart),

@@ -131,8 +131,11 @@ __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, 
 }
 
 // Segment aggregates A_seg = prod_k (I + N_k) (latest node on the left), FP64 accumulation.
+// The aggregate matrices and affine offsets of segments and groups are FP64 for both working
+// precisions: they are few, and FP32 products of ~1000 Cayley factors would limit the FP32
+// preconditioner's accuracy at large N.
 template <typename T, int NX>
-__global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, T* __restrict__ Aseg) {
+__global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, double* __restrict__ Aseg) {
   const int seg = blockIdx.x * blockDim.x + threadIdx.x;
   if (seg >= nseg) return;
   double A[NX * NX];
@@ -157,12 +160,12 @@ __global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, T* __re
     for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
   }
 #pragma unroll
-  for (int c = 0; c < NX * NX; ++c) Aseg[(int64_t)c * nseg + seg] = (T)A[c];
+  for (int c = 0; c < NX * NX; ++c) Aseg[(int64_t)c * nseg + seg] = A[c];
 }
 
 // Group aggregates from segment aggregates.
-template <typename T, int NX>
-__global__ void k_lin_grp(const T* __restrict__ Aseg, int nseg, int ngrp, T* __restrict__ Agrp) {
+template <int NX>
+__global__ void k_lin_grp(const double* __restrict__ Aseg, int nseg, int ngrp, double* __restrict__ Agrp) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= ngrp) return;
   double A[NX * NX];
@@ -173,7 +176,7 @@ __global__ void k_lin_grp(const T* __restrict__ Aseg, int nseg, int ngrp, T* __r
     if (seg >= nseg) break;
     double M[NX * NX], R[NX * NX];
 #pragma unroll
-    for (int c = 0; c < NX * NX; ++c) M[c] = (double)Aseg[(int64_t)c * nseg + seg];
+    for (int c = 0; c < NX * NX; ++c) M[c] = Aseg[(int64_t)c * nseg + seg];
 #pragma unroll
     for (int r = 0; r < NX; ++r)
 #pragma unroll
@@ -187,7 +190,7 @@ __global__ void k_lin_grp(const T* __restrict__ Aseg, int nseg, int ngrp, T* __r
     for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
   }
 #pragma unroll
-  for (int c = 0; c < NX * NX; ++c) Agrp[(int64_t)c * ngrp + g] = (T)A[c];
+  for (int c = 0; c < NX * NX; ++c) Agrp[(int64_t)c * ngrp + g] = A[c];
 }
 
 template <typename Tin, typename Tout>
@@ -256,7 +259,7 @@ __device__ __forceinline__ void node_step(const T* __restrict__ Kn, const T* __r
 template <typename T, int NX, int DIR>
 __global__ void k_sweep_seg(const T* __restrict__ Kn, const T* __restrict__ Nn, const T* __restrict__ Y,
                             const T* __restrict__ G, int64_t P, int64_t L, const T* __restrict__ w, T s,
-                            int nseg, T* __restrict__ segb) {
+                            int nseg, double* __restrict__ segb) {
   const int seg = blockIdx.x * blockDim.x + threadIdx.x;
   if (seg >= nseg) return;
   T st[NX], dummy[2 * NX];
@@ -272,13 +275,14 @@ __global__ void k_sweep_seg(const T* __restrict__ Kn, const T* __restrict__ Nn, 
     node_step<T, NX, DIR>(Kn, Nn, k, yin, gin, T(0.5) * s * w[k], st, dummy, false);
   }
 #pragma unroll
-  for (int m = 0; m < NX; ++m) segb[(int64_t)m * nseg + seg] = st[m];
+  for (int m = 0; m < NX; ++m) segb[(int64_t)m * nseg + seg] = (double)st[m];
 }
 
 // Phase 2: per group, compose the segment offsets (zero incoming state).
-template <typename T, int NX, int DIR>
-__global__ void k_sweep_grp(const T* __restrict__ Aseg, const T* __restrict__ segb, int nseg, int ngrp,
-                            T* __restrict__ grpb) {
+template <int NX, int DIR>
+__global__ void k_sweep_grp(const double* __restrict__ Aseg, const double* __restrict__ segb, int nseg, int ngrp,
+                            double* __restrict__ grpb) {
+  typedef double T;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= ngrp) return;
   T st[NX];
@@ -305,9 +309,10 @@ __global__ void k_sweep_grp(const T* __restrict__ Aseg, const T* __restrict__ se
 }
 
 // Phase 3: one CTA scans the group maps (in sweep order) and writes each group's incoming state.
-template <typename T, int NX, int DIR>
-__global__ void __launch_bounds__(256) k_sweep_top(const T* __restrict__ Agrp, const T* __restrict__ grpb,
-                                                   int ngrp, T* __restrict__ grpin) {
+template <int NX, int DIR>
+__global__ void __launch_bounds__(256) k_sweep_top(const double* __restrict__ Agrp, const double* __restrict__ grpb,
+                                                   int ngrp, double* __restrict__ grpin) {
+  typedef double T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sA = reinterpret_cast<T*>(smem_raw);          // [256][NX*NX]
   T* sb = sA + 256 * NX * NX;                      // [256][NX]
@@ -412,9 +417,10 @@ __global__ void __launch_bounds__(256) k_sweep_top(const T* __restrict__ Agrp, c
 }
 
 // Phase 4: per group, incoming states of its segments (overwrites segb in place).
-template <typename T, int NX, int DIR>
-__global__ void k_sweep_dist(const T* __restrict__ Aseg, T* __restrict__ segb, int nseg, int ngrp,
-                             const T* __restrict__ grpin) {
+template <int NX, int DIR>
+__global__ void k_sweep_dist(const double* __restrict__ Aseg, double* __restrict__ segb, int nseg, int ngrp,
+                             const double* __restrict__ grpin) {
+  typedef double T;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= ngrp) return;
   T st[NX];
@@ -444,12 +450,12 @@ __global__ void k_sweep_dist(const T* __restrict__ Aseg, T* __restrict__ segb, i
 template <typename T, int NX, int DIR>
 __global__ void k_sweep_out(const T* __restrict__ Kn, const T* __restrict__ Nn, const T* __restrict__ Y,
                             const T* __restrict__ G, int64_t P, int64_t L, const T* __restrict__ w, T s, int nseg,
-                            const T* __restrict__ segin, T* __restrict__ out, T* __restrict__ bout) {
+                            const double* __restrict__ segin, T* __restrict__ out, T* __restrict__ bout) {
   const int seg = blockIdx.x * blockDim.x + threadIdx.x;
   if (seg >= nseg) return;
   T st[NX];
 #pragma unroll
-  for (int m = 0; m < NX; ++m) st[m] = segin[(int64_t)m * nseg + seg];
+  for (int m = 0; m < NX; ++m) st[m] = (T)segin[(int64_t)m * nseg + seg];
   for (int ii = 0; ii < SEG; ++ii) {
     const int i = DIR == 0 ? ii : SEG - 1 - ii;
     const int64_t k = (int64_t)seg * SEG + i;
@@ -484,17 +490,17 @@ static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* ou
   const int nseg = pr->nseg, ngrp = pr->ngrp;
   const T s = (T)pr->s;
   const T* w = (const T*)d.w;
-  k_sweep_seg<T, NX, DIR><<<(nseg + 127) / 128, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, nseg, (T*)d.segb);
+  k_sweep_seg<T, NX, DIR><<<(nseg + 127) / 128, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, nseg, (double*)d.segb);
   BK_CHECK_LAUNCH();
-  k_sweep_grp<T, NX, DIR><<<(ngrp + 127) / 128, 128, 0, st>>>((const T*)d.Aseg, (const T*)d.segb, nseg, ngrp, (T*)d.grpb);
+  k_sweep_grp<NX, DIR><<<(ngrp + 127) / 128, 128, 0, st>>>((const double*)d.Aseg, (const double*)d.segb, nseg, ngrp, (double*)d.grpb);
   BK_CHECK_LAUNCH();
-  T* grpin = (T*)d.grpb + (size_t)NX * ngrp;
-  const size_t sm = sizeof(T) * 256 * (NX * NX + NX);
-  k_sweep_top<T, NX, DIR><<<1, 256, sm, st>>>((const T*)d.Agrp, (const T*)d.grpb, ngrp, grpin);
+  double* grpin = (double*)d.grpb + (size_t)NX * ngrp;
+  const size_t sm = sizeof(double) * 256 * (NX * NX + NX);
+  k_sweep_top<NX, DIR><<<1, 256, sm, st>>>((const double*)d.Agrp, (const double*)d.grpb, ngrp, grpin);
   BK_CHECK_LAUNCH();
-  k_sweep_dist<T, NX, DIR><<<(ngrp + 127) / 128, 128, 0, st>>>((const T*)d.Aseg, (T*)d.segb, nseg, ngrp, grpin);
+  k_sweep_dist<NX, DIR><<<(ngrp + 127) / 128, 128, 0, st>>>((const double*)d.Aseg, (double*)d.segb, nseg, ngrp, grpin);
   BK_CHECK_LAUNCH();
-  k_sweep_out<T, NX, DIR><<<(nseg + 127) / 128, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, nseg, (const T*)d.segb, out, bout);
+  k_sweep_out<T, NX, DIR><<<(nseg + 127) / 128, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, nseg, (const double*)d.segb, out, bout);
   BK_CHECK_LAUNCH();
   if (pr->P > pr->L) {
     k_zero_pad<T><<<nblk(NX * (pr->P - pr->L)), 256, 0, st>>>(out, NX, pr->P, pr->L);
@@ -843,8 +849,8 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
   const int64_t il = (int64_t)round_up(pr->nseg, 32) * SEG * nx * nx;
   BK_TRY(dmalloc(&d.Kn, es * il));
   BK_TRY(dmalloc(&d.Nn, es * il));
-  BK_TRY(dmalloc(&d.Aseg, es * (size_t)pr->nseg * nx * nx));
-  BK_TRY(dmalloc(&d.Agrp, es * (size_t)pr->ngrp * nx * nx));
+  BK_TRY(dmalloc(&d.Aseg, sizeof(double) * (size_t)pr->nseg * nx * nx));
+  BK_TRY(dmalloc(&d.Agrp, sizeof(double) * (size_t)pr->ngrp * nx * nx));
   if (ne > 0) {
     BK_TRY(dmalloc(&d.Zc, es * ne * nx * P));
     BK_TRY(dmalloc(&d.HWc, es * ne * nu * P));
@@ -854,8 +860,8 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
   BK_TRY(dmalloc(&d.t1, es * (nx + nu) * P));
   BK_TRY(dmalloc(&d.t2, es * (nx + nu) * P));
   BK_TRY(dmalloc(&d.t3, es * (nx + nu) * P));
-  BK_TRY(dmalloc(&d.segb, es * (size_t)pr->nseg * nx));
-  BK_TRY(dmalloc(&d.grpb, es * (size_t)pr->ngrp * nx * 2));
+  BK_TRY(dmalloc(&d.segb, sizeof(double) * (size_t)pr->nseg * nx));
+  BK_TRY(dmalloc(&d.grpb, sizeof(double) * (size_t)pr->ngrp * nx * 2));
   return BK_OK;
 }
 
@@ -872,9 +878,9 @@ static bk_status lin_factors(Problem* pr, OpData& d, const double* z, cudaStream
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   k_lin_nodes<T, KIND, NX, NU><<<nblk(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->d64.plan->w64, pr->s, (T*)d.Kn, (T*)d.Nn, (T*)d.xu);
   BK_CHECK_LAUNCH();
-  k_lin_seg<T, NX><<<(pr->nseg + 127) / 128, 128, 0, st>>>((const T*)d.Nn, pr->L, pr->nseg, (T*)d.Aseg);
+  k_lin_seg<T, NX><<<(pr->nseg + 127) / 128, 128, 0, st>>>((const T*)d.Nn, pr->L, pr->nseg, (double*)d.Aseg);
   BK_CHECK_LAUNCH();
-  k_lin_grp<T, NX><<<(pr->ngrp + 127) / 128, 128, 0, st>>>((const T*)d.Aseg, pr->nseg, pr->ngrp, (T*)d.Agrp);
+  k_lin_grp<NX><<<(pr->ngrp + 127) / 128, 128, 0, st>>>((const double*)d.Aseg, pr->nseg, pr->ngrp, (double*)d.Agrp);
   BK_CHECK_LAUNCH();
   return BK_OK;
 }
@@ -948,13 +954,22 @@ __global__ void k_negate(T* v, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) v[i] = -v[i];
 }
 
+// mu_ready: the caller has just evaluated the KKT residual at this z (problem_residual), which
+// left mu = s B^aT lambda in the FP64 scratch t3; it is reused instead of recomputed.
+// A BK_F32 problem builds its preconditioner data in FP32 only; the FP64 side keeps the
+// linearisation point and mu, which the FP64 KKT product needs.
 template <int KIND>
-static bk_status linearize_kind(Problem* pr, const double* z, cudaStream_t st) {
+static bk_status linearize_kind(Problem* pr, const double* z, bool mu_ready, cudaStream_t st) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   const int64_t P = pr->P;
-  // mu = s B^aT lambda (FP64)
-  BK_TRY(plan_apply_n(pr->d64.plan, z + (NX + NU) * P, pr->d64.mu, NX, true, pr->s, st));
-  BK_TRY((lin_factors<double, KIND>(pr, pr->d64, z, st)));
+  if (mu_ready)
+    BK_TRY_CUDA(cudaMemcpyAsync(pr->d64.mu, pr->d64.t3, sizeof(double) * NX * P, cudaMemcpyDeviceToDevice, st));
+  else
+    BK_TRY(plan_apply_n(pr->d64.plan, z + (NX + NU) * P, pr->d64.mu, NX, true, pr->s, st));
+  if (pr->dtype == BK_F64)
+    BK_TRY((lin_factors<double, KIND>(pr, pr->d64, z, st)));
+  else
+    BK_TRY_CUDA(cudaMemcpyAsync(pr->d64.xu, z, sizeof(double) * (NX + NU) * P, cudaMemcpyDeviceToDevice, st));
   if (pr->dtype == BK_F32) {
     k_convert<double, float><<<nblk(NX * P), 256, 0, st>>>((const double*)pr->d64.mu, (float*)pr->d32.mu, NX * P);
     BK_CHECK_LAUNCH();
@@ -962,10 +977,11 @@ static bk_status linearize_kind(Problem* pr, const double* z, cudaStream_t st) {
   }
   pr->linearized = true;
   if (pr->n_e > 0 && pr->has_cost) {
-    BK_TRY((lin_schur<double, KIND>(pr, pr->d64, st)));
-    k_negate<double><<<nblk((int64_t)pr->n_e * NU * P), 256, 0, st>>>((double*)pr->d64.HWc, (int64_t)pr->n_e * NU * P);
-    BK_CHECK_LAUNCH();
-    if (pr->dtype == BK_F32) {
+    if (pr->dtype == BK_F64) {
+      BK_TRY((lin_schur<double, KIND>(pr, pr->d64, st)));
+      k_negate<double><<<nblk((int64_t)pr->n_e * NU * P), 256, 0, st>>>((double*)pr->d64.HWc, (int64_t)pr->n_e * NU * P);
+      BK_CHECK_LAUNCH();
+    } else {
       BK_TRY((lin_schur<float, KIND>(pr, pr->d32, st)));
       k_negate<float><<<nblk((int64_t)pr->n_e * NU * P), 256, 0, st>>>((float*)pr->d32.HWc, (int64_t)pr->n_e * NU * P);
       BK_CHECK_LAUNCH();
@@ -974,9 +990,9 @@ static bk_status linearize_kind(Problem* pr, const double* z, cudaStream_t st) {
   return BK_OK;
 }
 
-bk_status problem_linearize(Problem* pr, const double* z, cudaStream_t st) {
+bk_status problem_linearize(Problem* pr, const double* z, cudaStream_t st, bool mu_ready) {
   BK_ARG(pr != nullptr && z != nullptr, "NULL problem or z_lin");
-  BK_DISPATCH_KIND(pr->kind, linearize_kind, pr, z, st);
+  BK_DISPATCH_KIND(pr->kind, linearize_kind, pr, z, mu_ready, st);
 }
 
 // --- operator applies --------------------------------------------------------------------------

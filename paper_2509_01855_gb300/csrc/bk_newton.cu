@@ -5,8 +5,9 @@
 // with the exact Lagrangian Hessian, each step solved by the Birkhoff-preconditioned GMRES, and
 // a backtracking line search (alpha = 1, 1/2, ...; Armijo constant 1e-4) on the quadrature-
 // weighted norm ||F||_W^2 = sum w c^2 + sum g^2 / w + |e|^2, which does not grow with N.
-// The residual, the line search and (for BK_F32 problems) the iterative-refinement residual are
-// FP64; BK_F32 problems run the GMRES iterations and their operator applies in FP32.
+// The residual and the line search are FP64. BK_F32 problems run the GMRES iterations and their
+// operator applies in FP32; the FP64 Newton residual then refines their step (inexact Newton),
+// and max_refine > 1 adds linear iterative-refinement sweeps with an FP64 KKT residual.
 #include <math.h>
 #include <string.h>
 
@@ -126,7 +127,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
   info->residual = phi;
   int it = 0;
   while (phi > o.tol && it < o.max_iter) {
-    BK_TRY(problem_linearize(pr, z, st));
+    BK_TRY(problem_linearize(pr, z, st, /*mu_ready=*/true));
     k_axpby64<<<g, 256, 0, st>>>(F, -1.0, rhs, 0.0, n);
     BK_CHECK_LAUNCH();
     bk_krylov_info ki;
@@ -151,6 +152,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
         info->kkt_solves += 1;
         k_acc32<<<g, 256, 0, st>>>(d32, d, n);
         BK_CHECK_LAUNCH();
+        if (sweep + 1 == o.max_refine) break;  // last sweep: the Newton residual checks d
         // r = rhs - K d (FP64)
         BK_TRY(op_apply(pr, pr->d64, BK_OP_KKT, d, r, st));
         k_axpby64<<<g, 256, 0, st>>>(rhs, 1.0, r, -1.0, n);
@@ -211,11 +213,14 @@ bk_status newton_solve(bk_problem* prob, double* z_inout, const bk_newton_opts* 
   if (opts) o = *opts;
   if (o.tol <= 0) o.tol = 1e-10;
   if (o.max_iter <= 0) o.max_iter = 30;
-  if (o.krylov_rtol <= 0) o.krylov_rtol = p->dtype == BK_F64 ? 1e-12 : 1e-5;
+  // FP64: tight inner solves (Newton converges quadratically). FP32: inexact Newton, one FP32
+  // GMRES solve to 1e-4 (at most 10 iterations) per step, refined by the FP64 Newton residual.
+  const bool f64 = p->dtype == BK_F64;
+  if (o.krylov_rtol <= 0) o.krylov_rtol = f64 ? 1e-12 : 1e-4;
   if (o.restart <= 0) o.restart = 30;
-  if (o.max_krylov <= 0) o.max_krylov = 300;
+  if (o.max_krylov <= 0) o.max_krylov = f64 ? 300 : 10;
   if (o.ir_rtol <= 0) o.ir_rtol = 1e-10;
-  if (o.max_refine <= 0) o.max_refine = 10;
+  if (o.max_refine <= 0) o.max_refine = f64 ? 10 : 1;
   memset(info, 0, sizeof(*info));
   BK_TRY(bk::newton_impl(p, z_inout, o, info, workspace, (cudaStream_t)stream));
   if (!info->converged) {

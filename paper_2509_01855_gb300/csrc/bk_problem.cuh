@@ -14,7 +14,10 @@ namespace bk {
 constexpr int NXM = 4;   // largest state dimension of the compiled problem kinds
 constexpr int NUM = 2;   // largest control dimension
 constexpr int NEM = 4;   // largest terminal-condition count
-constexpr int SEG = 32;  // nodes per sweep segment (one thread each)
+#ifndef BK_SWEEP_SEG
+#define BK_SWEEP_SEG 16
+#endif
+constexpr int SEG = BK_SWEEP_SEG;  // nodes per sweep segment (one thread each)
 constexpr int GRP = 32;  // segments per sweep group
 
 // ---------------------------------------------------------------------------------------------
@@ -150,7 +153,8 @@ struct Problem {
   OpData& work() { return dtype == BK_F64 ? d64 : d32; }
 };
 
-bk_status problem_linearize(Problem* pr, const double* z_lin, cudaStream_t st);
+// mu_ready: problem_residual(z_lin) was the last FP64 work on the problem (its mu is reused).
+bk_status problem_linearize(Problem* pr, const double* z_lin, cudaStream_t st, bool mu_ready = false);
 // Operator applies on one precision's data (T = double or float).
 bk_status op_apply(Problem* pr, OpData& d, int op, const void* in, void* out, cudaStream_t st);
 bk_status op_precond(Problem* pr, OpData& d, int op, const void* in, void* out, int transpose,

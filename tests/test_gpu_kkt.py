@@ -181,7 +181,11 @@ def test_newton_orbit_matches_oracle(N, dtype):
     z = from_packed(prob, vec0)
     info = api.newton_solve(prob, z)
     assert info["converged"], info
-    assert info["iterations"] == rinfo["iters"]
+    if dtype == torch.float64:
+        assert info["iterations"] == rinfo["iters"]
+    else:
+        # FP32 inner solves to 1e-4 make the last Newton steps linearly convergent
+        assert rinfo["iters"] <= info["iterations"] <= rinfo["iters"] + 3
     got = to_packed(prob, z)
     Xr, Ur, lr, nr = K.split(ref)
     Xg, Ug, lg, ng = K.split(got)
