@@ -130,10 +130,32 @@ __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, 
   }
 }
 
-// Segment aggregates A_seg = prod_k (I + N_k) (latest node on the left), FP64 accumulation.
-// The aggregate matrices and affine offsets of segments and groups are FP64 for both working
-// precisions: they are few, and FP32 products of ~1000 Cayley factors would limit the FP32
-// preconditioner's accuracy at large N.
+// Aggregates of the sweep's affine maps. Level 0: segments of SEG nodes; level 1: groups of 32
+// segments; level 2: supergroups of 32 groups. A level's aggregate is the product of its items'
+// matrices (latest item on the left); for the backward sweep it is the transpose. They are FP64
+// for both working precisions: few, and FP32 products of ~1000 Cayley factors would cost the
+// FP32 preconditioner its accuracy at large N. Levels 0 and 1 are stored 32-interleaved
+// (element c of item i at il32(i, c, NC)) so that a warp reading 32 consecutive items is
+// coalesced.
+__device__ __forceinline__ int64_t il32(int64_t i, int c, int NC) { return (((i >> 5) * NC + c) << 5) + (i & 31); }
+
+template <int NX>
+__device__ __forceinline__ void mat_left(const double* M, double* A) {
+  // A <- M A
+  double R[NX * NX];
+#pragma unroll
+  for (int r = 0; r < NX; ++r)
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
+      double a = 0;
+#pragma unroll
+      for (int q = 0; q < NX; ++q) a += M[r * NX + q] * A[q * NX + c];
+      R[r * NX + c] = a;
+    }
+#pragma unroll
+  for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
+}
+
 template <typename T, int NX>
 __global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, double* __restrict__ Aseg) {
   const int seg = blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,53 +166,37 @@ __global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, double*
   for (int i = 0; i < SEG; ++i) {
     const int64_t k = (int64_t)seg * SEG + i;
     if (k >= L) break;
-    double M[NX * NX], R[NX * NX];
+    double M[NX * NX];
 #pragma unroll
     for (int c = 0; c < NX * NX; ++c) M[c] = (double)Nn[il_index(k, c, NX * NX)] + ((c % (NX + 1) == 0) ? 1.0 : 0.0);
-#pragma unroll
-    for (int r = 0; r < NX; ++r)
-#pragma unroll
-      for (int c = 0; c < NX; ++c) {
-        double a = 0;
-#pragma unroll
-        for (int q = 0; q < NX; ++q) a += M[r * NX + q] * A[q * NX + c];
-        R[r * NX + c] = a;
-      }
-#pragma unroll
-    for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
+    mat_left<NX>(M, A);
   }
 #pragma unroll
-  for (int c = 0; c < NX * NX; ++c) Aseg[(int64_t)c * nseg + seg] = A[c];
+  for (int c = 0; c < NX * NX; ++c) Aseg[il32(seg, c, NX * NX)] = A[c];
 }
 
-// Group aggregates from segment aggregates.
-template <int NX>
-__global__ void k_lin_grp(const double* __restrict__ Aseg, int nseg, int ngrp, double* __restrict__ Agrp) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= ngrp) return;
+// Level-1 (OUT_IL = true, 32-interleaved output) or level-2 (plain [c][item]) aggregates from
+// 32-interleaved lower-level aggregates.
+template <int NX, bool OUT_IL>
+__global__ void k_lin_up(const double* __restrict__ Alow, int nlow, int nup, double* __restrict__ Aup) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= nup) return;
   double A[NX * NX];
 #pragma unroll
   for (int i = 0; i < NX * NX; ++i) A[i] = (i % (NX + 1) == 0) ? 1.0 : 0.0;
-  for (int i = 0; i < GRP; ++i) {
-    const int seg = g * GRP + i;
-    if (seg >= nseg) break;
-    double M[NX * NX], R[NX * NX];
+  for (int i = 0; i < 32; ++i) {
+    const int lo = u * 32 + i;
+    if (lo >= nlow) break;
+    double M[NX * NX];
 #pragma unroll
-    for (int c = 0; c < NX * NX; ++c) M[c] = Aseg[(int64_t)c * nseg + seg];
-#pragma unroll
-    for (int r = 0; r < NX; ++r)
-#pragma unroll
-      for (int c = 0; c < NX; ++c) {
-        double a = 0;
-#pragma unroll
-        for (int q = 0; q < NX; ++q) a += M[r * NX + q] * A[q * NX + c];
-        R[r * NX + c] = a;
-      }
-#pragma unroll
-    for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
+    for (int c = 0; c < NX * NX; ++c) M[c] = Alow[il32(lo, c, NX * NX)];
+    mat_left<NX>(M, A);
   }
 #pragma unroll
-  for (int c = 0; c < NX * NX; ++c) Agrp[(int64_t)c * ngrp + g] = A[c];
+  for (int c = 0; c < NX * NX; ++c) {
+    if (OUT_IL) Aup[il32(u, c, NX * NX)] = A[c];
+    else Aup[(int64_t)c * nup + u] = A[c];
+  }
 }
 
 template <typename Tin, typename Tout>
@@ -255,207 +261,188 @@ __device__ __forceinline__ void node_step(const T* __restrict__ Kn, const T* __r
   }
 }
 
-// Phase 1: per segment, the offset of its affine map (zero incoming state).
-template <typename T, int NX, int DIR>
-__global__ void k_sweep_seg(const T* __restrict__ Kn, const T* __restrict__ Nn, const T* __restrict__ Y,
-                            const T* __restrict__ G, int64_t P, int64_t L, const T* __restrict__ w, T s,
-                            int nseg, double* __restrict__ segb) {
-  const int seg = blockIdx.x * blockDim.x + threadIdx.x;
-  if (seg >= nseg) return;
-  T st[NX], dummy[2 * NX];
+// One affine step st <- A st + b (DIR 0) or A^T st + b (DIR 1), FP64.
+template <int NX, int DIR>
+__device__ __forceinline__ void affine_step(const double* A, const double* b, double* st) {
+  double ns[NX];
 #pragma unroll
-  for (int m = 0; m < NX; ++m) st[m] = T(0);
-  for (int ii = 0; ii < SEG; ++ii) {
-    const int i = DIR == 0 ? ii : SEG - 1 - ii;
-    const int64_t k = (int64_t)seg * SEG + i;
-    if (k >= L) { if (DIR == 0) break; else continue; }
-    T yin[NX], gin[NX];
+  for (int r = 0; r < NX; ++r) {
+    double a = b[r];
 #pragma unroll
-    for (int m = 0; m < NX; ++m) { yin[m] = Y[m * P + k]; gin[m] = G ? G[m * P + k] : T(0); }
-    node_step<T, NX, DIR>(Kn, Nn, k, yin, gin, T(0.5) * s * w[k], st, dummy, false);
+    for (int c = 0; c < NX; ++c) a += (DIR == 0 ? A[r * NX + c] : A[c * NX + r]) * st[c];
+    ns[r] = a;
   }
 #pragma unroll
-  for (int m = 0; m < NX; ++m) segb[(int64_t)m * nseg + seg] = (double)st[m];
+  for (int r = 0; r < NX; ++r) st[r] = ns[r];
 }
 
-// Phase 2: per group, compose the segment offsets (zero incoming state).
-template <int NX, int DIR>
-__global__ void k_sweep_grp(const double* __restrict__ Aseg, const double* __restrict__ segb, int nseg, int ngrp,
-                            double* __restrict__ grpb) {
-  typedef double T;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= ngrp) return;
-  T st[NX];
+// Stage the 32 items of a block (aggregates A and offsets b, 32-interleaved) into shared memory;
+// items beyond n become the identity map.
+template <int NX>
+__device__ __forceinline__ void stage32(const double* __restrict__ Ag, const double* __restrict__ bg, int64_t item,
+                                        int n, double (*sA)[NX * NX], double (*sb)[NX]) {
+  const int lane = threadIdx.x;
+  const bool ok = item < n;
 #pragma unroll
-  for (int m = 0; m < NX; ++m) st[m] = T(0);
-  for (int ii = 0; ii < GRP; ++ii) {
-    const int i = DIR == 0 ? ii : GRP - 1 - ii;
-    const int seg = g * GRP + i;
-    if (seg >= nseg) { if (DIR == 0) break; else continue; }
-    T ns[NX];
+  for (int c = 0; c < NX * NX; ++c) sA[lane][c] = ok ? Ag[il32(item, c, NX * NX)] : ((c % (NX + 1) == 0) ? 1.0 : 0.0);
 #pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      T a = segb[(int64_t)r * nseg + seg];
+  for (int c = 0; c < NX; ++c) sb[lane][c] = ok ? bg[il32(item, c, NX)] : 0.0;
+  __syncwarp();
+}
+
+// Up-sweep, level 0+1 (one warp per group): each lane runs its segment from a zero state (the
+// segment's offset); lane 0 folds the 32 segment maps into the group's offset.
+template <typename T, int NX, int DIR>
+__global__ void __launch_bounds__(32) k_sw_up01(const T* __restrict__ Kn, const T* __restrict__ Nn,
+                                                const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
+                                                int64_t L, const T* __restrict__ w, T s, int nseg,
+                                                const double* __restrict__ Aseg, double* __restrict__ segb,
+                                                double* __restrict__ grpb) {
+  __shared__ double sA[32][NX * NX];
+  __shared__ double sb[32][NX];
+  const int g = blockIdx.x;
+  const int seg = g * 32 + threadIdx.x;
+  if (seg < nseg) {
+    T st[NX], dummy[2 * NX];
 #pragma unroll
-      for (int c = 0; c < NX; ++c)
-        a += (DIR == 0 ? Aseg[(int64_t)(r * NX + c) * nseg + seg] : Aseg[(int64_t)(c * NX + r) * nseg + seg]) * st[c];
-      ns[r] = a;
+    for (int m = 0; m < NX; ++m) st[m] = T(0);
+    for (int ii = 0; ii < SEG; ++ii) {
+      const int i = DIR == 0 ? ii : SEG - 1 - ii;
+      const int64_t k = (int64_t)seg * SEG + i;
+      if (k >= L) { if (DIR == 0) break; else continue; }
+      T yin[NX], gin[NX];
+#pragma unroll
+      for (int m = 0; m < NX; ++m) { yin[m] = Y[m * P + k]; gin[m] = G ? G[m * P + k] : T(0); }
+      node_step<T, NX, DIR>(Kn, Nn, k, yin, gin, T(0.5) * s * w[k], st, dummy, false);
     }
 #pragma unroll
-    for (int r = 0; r < NX; ++r) st[r] = ns[r];
+    for (int m = 0; m < NX; ++m) segb[il32(seg, m, NX)] = (double)st[m];
   }
+  __syncwarp();
+  stage32<NX>(Aseg, segb, seg, nseg, sA, sb);
+  if (threadIdx.x == 0) {
+    double st[NX];
 #pragma unroll
-  for (int m = 0; m < NX; ++m) grpb[(int64_t)m * ngrp + g] = st[m];
+    for (int m = 0; m < NX; ++m) st[m] = 0.0;
+    for (int ii = 0; ii < 32; ++ii) {
+      const int i = DIR == 0 ? ii : 31 - ii;
+      affine_step<NX, DIR>(sA[i], sb[i], st);
+    }
+#pragma unroll
+    for (int m = 0; m < NX; ++m) grpb[il32(g, m, NX)] = st[m];
+  }
 }
 
-// Phase 3: one CTA scans the group maps (in sweep order) and writes each group's incoming state.
+// Up-sweep, level 2 (one warp per supergroup): fold 32 group maps into the supergroup offset.
 template <int NX, int DIR>
-__global__ void __launch_bounds__(256) k_sweep_top(const double* __restrict__ Agrp, const double* __restrict__ grpb,
-                                                   int ngrp, double* __restrict__ grpin) {
-  typedef double T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sA = reinterpret_cast<T*>(smem_raw);          // [256][NX*NX]
-  T* sb = sA + 256 * NX * NX;                      // [256][NX]
-  const int t = threadIdx.x;
-  const int per = (ngrp + 255) / 256;
-  // thread t owns sweep-ordered groups [t*per, (t+1)*per)
-  T A[NX * NX], b[NX];
+__global__ void __launch_bounds__(32) k_sw_up2(const double* __restrict__ Agrp, const double* __restrict__ grpb,
+                                               int ngrp, int nsg, double* __restrict__ sgb) {
+  __shared__ double sA[32][NX * NX];
+  __shared__ double sb[32][NX];
+  const int sg = blockIdx.x;
+  stage32<NX>(Agrp, grpb, (int64_t)sg * 32 + threadIdx.x, ngrp, sA, sb);
+  if (threadIdx.x == 0) {
+    double st[NX];
 #pragma unroll
-  for (int i = 0; i < NX * NX; ++i) A[i] = (i % (NX + 1) == 0) ? T(1) : T(0);
+    for (int m = 0; m < NX; ++m) st[m] = 0.0;
+    for (int ii = 0; ii < 32; ++ii) affine_step<NX, DIR>(sA[DIR == 0 ? ii : 31 - ii], sb[DIR == 0 ? ii : 31 - ii], st);
 #pragma unroll
-  for (int i = 0; i < NX; ++i) b[i] = T(0);
-  for (int q = 0; q < per; ++q) {
-    const int o = t * per + q;
-    if (o >= ngrp) break;
-    const int g = DIR == 0 ? o : ngrp - 1 - o;
-    T M[NX * NX], nb[NX], nA[NX * NX];
+    for (int m = 0; m < NX; ++m) sgb[(int64_t)m * nsg + sg] = st[m];
+  }
+}
+
+// Top (one warp): incoming state of every supergroup, in sweep order, chunks staged in smem.
+template <int NX, int DIR>
+__global__ void __launch_bounds__(32) k_sw_top(const double* __restrict__ Asg, const double* __restrict__ sgb,
+                                               int nsg, double* __restrict__ sgin) {
+  __shared__ double sA[32][NX * NX];
+  __shared__ double sb[32][NX];
+  double st[NX];
 #pragma unroll
-    for (int r = 0; r < NX; ++r)
+  for (int m = 0; m < NX; ++m) st[m] = 0.0;
+  for (int c0 = 0; c0 < nsg; c0 += 32) {
+    // chunk of 32 supergroups in sweep order
+    const int o = c0 + threadIdx.x;
+    const int sg = DIR == 0 ? o : nsg - 1 - o;
+    const bool ok = o < nsg;
 #pragma unroll
-      for (int c = 0; c < NX; ++c)
-        M[r * NX + c] = DIR == 0 ? Agrp[(int64_t)(r * NX + c) * ngrp + g] : Agrp[(int64_t)(c * NX + r) * ngrp + g];
+    for (int c = 0; c < NX * NX; ++c) sA[threadIdx.x][c] = ok ? Asg[(int64_t)c * nsg + sg] : 0.0;
 #pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      T a = grpb[(int64_t)r * ngrp + g];
+    for (int c = 0; c < NX; ++c) sb[threadIdx.x][c] = ok ? sgb[(int64_t)c * nsg + sg] : 0.0;
+    __syncwarp();
+    if (threadIdx.x == 0) {
+      const int cnt = nsg - c0 < 32 ? nsg - c0 : 32;
+      for (int i = 0; i < cnt; ++i) {
+        const int sgi = DIR == 0 ? c0 + i : nsg - 1 - (c0 + i);
 #pragma unroll
-      for (int c = 0; c < NX; ++c) a += M[r * NX + c] * b[c];
-      nb[r] = a;
-#pragma unroll
-      for (int c = 0; c < NX; ++c) {
-        T s2 = T(0);
-#pragma unroll
-        for (int qq = 0; qq < NX; ++qq) s2 += M[r * NX + qq] * A[qq * NX + c];
-        nA[r * NX + c] = s2;
+        for (int m = 0; m < NX; ++m) sgin[(int64_t)m * nsg + sgi] = st[m];
+        affine_step<NX, DIR>(sA[i], sb[i], st);
       }
     }
-#pragma unroll
-    for (int i = 0; i < NX * NX; ++i) A[i] = nA[i];
-#pragma unroll
-    for (int i = 0; i < NX; ++i) b[i] = nb[i];
-  }
-#pragma unroll
-  for (int i = 0; i < NX * NX; ++i) sA[t * NX * NX + i] = A[i];
-#pragma unroll
-  for (int i = 0; i < NX; ++i) sb[t * NX + i] = b[i];
-  __syncthreads();
-  // Kogge-Stone inclusive scan of the affine maps: x_t <- x_t o x_{t-d}
-  for (int d = 1; d < 256; d <<= 1) {
-    T pA[NX * NX], pb[NX];
-    const bool act = t >= d;
-    if (act) {
-#pragma unroll
-      for (int i = 0; i < NX * NX; ++i) pA[i] = sA[(t - d) * NX * NX + i];
-#pragma unroll
-      for (int i = 0; i < NX; ++i) pb[i] = sb[(t - d) * NX + i];
-    }
-    __syncthreads();
-    if (act) {
-      T nA[NX * NX], nb[NX];
-#pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        T a = b[r];
-#pragma unroll
-        for (int c = 0; c < NX; ++c) a += A[r * NX + c] * pb[c];
-        nb[r] = a;
-#pragma unroll
-        for (int c = 0; c < NX; ++c) {
-          T s2 = T(0);
-#pragma unroll
-          for (int qq = 0; qq < NX; ++qq) s2 += A[r * NX + qq] * pA[qq * NX + c];
-          nA[r * NX + c] = s2;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < NX * NX; ++i) { A[i] = nA[i]; sA[t * NX * NX + i] = nA[i]; }
-#pragma unroll
-      for (int i = 0; i < NX; ++i) { b[i] = nb[i]; sb[t * NX + i] = nb[i]; }
-    }
-    __syncthreads();
-  }
-  // incoming state of thread t's first group = offset of the inclusive map of thread t-1
-  T st[NX];
-#pragma unroll
-  for (int i = 0; i < NX; ++i) st[i] = t > 0 ? sb[(t - 1) * NX + i] : T(0);
-  for (int q = 0; q < per; ++q) {
-    const int o = t * per + q;
-    if (o >= ngrp) break;
-    const int g = DIR == 0 ? o : ngrp - 1 - o;
-#pragma unroll
-    for (int r = 0; r < NX; ++r) grpin[(int64_t)r * ngrp + g] = st[r];
-    T ns[NX];
-#pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      T a = grpb[(int64_t)r * ngrp + g];
-#pragma unroll
-      for (int c = 0; c < NX; ++c)
-        a += (DIR == 0 ? Agrp[(int64_t)(r * NX + c) * ngrp + g] : Agrp[(int64_t)(c * NX + r) * ngrp + g]) * st[c];
-      ns[r] = a;
-    }
-#pragma unroll
-    for (int r = 0; r < NX; ++r) st[r] = ns[r];
+    __syncwarp();
   }
 }
 
-// Phase 4: per group, incoming states of its segments (overwrites segb in place).
+// Down-sweep, level 2 (one warp per supergroup): incoming state of each of its groups.
 template <int NX, int DIR>
-__global__ void k_sweep_dist(const double* __restrict__ Aseg, double* __restrict__ segb, int nseg, int ngrp,
-                             const double* __restrict__ grpin) {
-  typedef double T;
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= ngrp) return;
-  T st[NX];
+__global__ void __launch_bounds__(32) k_sw_down2(const double* __restrict__ Agrp, const double* __restrict__ grpb,
+                                                 int ngrp, int nsg, const double* __restrict__ sgin,
+                                                 double* __restrict__ grpin) {
+  __shared__ double sA[32][NX * NX];
+  __shared__ double sb[32][NX];
+  const int sg = blockIdx.x;
+  stage32<NX>(Agrp, grpb, (int64_t)sg * 32 + threadIdx.x, ngrp, sA, sb);
+  __shared__ double sin_[32][NX];
+  if (threadIdx.x == 0) {
+    double st[NX];
 #pragma unroll
-  for (int m = 0; m < NX; ++m) st[m] = grpin[(int64_t)m * ngrp + g];
-  for (int ii = 0; ii < GRP; ++ii) {
-    const int i = DIR == 0 ? ii : GRP - 1 - ii;
-    const int seg = g * GRP + i;
-    if (seg >= nseg) { if (DIR == 0) break; else continue; }
-    T ns[NX];
+    for (int m = 0; m < NX; ++m) st[m] = sgin[(int64_t)m * nsg + sg];
+    for (int ii = 0; ii < 32; ++ii) {
+      const int i = DIR == 0 ? ii : 31 - ii;
 #pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      T a = segb[(int64_t)r * nseg + seg];
-#pragma unroll
-      for (int c = 0; c < NX; ++c)
-        a += (DIR == 0 ? Aseg[(int64_t)(r * NX + c) * nseg + seg] : Aseg[(int64_t)(c * NX + r) * nseg + seg]) * st[c];
-      ns[r] = a;
+      for (int m = 0; m < NX; ++m) sin_[i][m] = st[m];
+      affine_step<NX, DIR>(sA[i], sb[i], st);
     }
+  }
+  __syncwarp();
+  const int64_t g = (int64_t)sg * 32 + threadIdx.x;
+  if (g < ngrp) {
 #pragma unroll
-    for (int r = 0; r < NX; ++r) segb[(int64_t)r * nseg + seg] = st[r];
-#pragma unroll
-    for (int r = 0; r < NX; ++r) st[r] = ns[r];
+    for (int m = 0; m < NX; ++m) grpin[il32(g, m, NX)] = sin_[threadIdx.x][m];
   }
 }
 
-// Phase 5: per segment, rerun with the incoming state and write the outputs.
+// Down-sweep, level 1+0 (one warp per group): lane 0 forms the incoming state of each segment,
+// then every lane reruns its segment from it and writes the outputs.
 template <typename T, int NX, int DIR>
-__global__ void k_sweep_out(const T* __restrict__ Kn, const T* __restrict__ Nn, const T* __restrict__ Y,
-                            const T* __restrict__ G, int64_t P, int64_t L, const T* __restrict__ w, T s, int nseg,
-                            const double* __restrict__ segin, T* __restrict__ out, T* __restrict__ bout) {
-  const int seg = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32) k_sw_down10(const T* __restrict__ Kn, const T* __restrict__ Nn,
+                                                  const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
+                                                  int64_t L, const T* __restrict__ w, T s, int nseg,
+                                                  const double* __restrict__ Aseg, const double* __restrict__ segb,
+                                                  const double* __restrict__ grpin, T* __restrict__ out,
+                                                  T* __restrict__ bout) {
+  __shared__ double sA[32][NX * NX];
+  __shared__ double sb[32][NX];
+  __shared__ double sin_[32][NX];
+  const int g = blockIdx.x;
+  const int seg = g * 32 + threadIdx.x;
+  stage32<NX>(Aseg, segb, seg, nseg, sA, sb);
+  if (threadIdx.x == 0) {
+    double st[NX];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) st[m] = grpin[il32(g, m, NX)];
+    for (int ii = 0; ii < 32; ++ii) {
+      const int i = DIR == 0 ? ii : 31 - ii;
+#pragma unroll
+      for (int m = 0; m < NX; ++m) sin_[i][m] = st[m];
+      affine_step<NX, DIR>(sA[i], sb[i], st);
+    }
+  }
+  __syncwarp();
   if (seg >= nseg) return;
   T st[NX];
 #pragma unroll
-  for (int m = 0; m < NX; ++m) st[m] = (T)segin[(int64_t)m * nseg + seg];
+  for (int m = 0; m < NX; ++m) st[m] = (T)sin_[threadIdx.x][m];
   for (int ii = 0; ii < SEG; ++ii) {
     const int i = DIR == 0 ? ii : SEG - 1 - ii;
     const int64_t k = (int64_t)seg * SEG + i;
@@ -485,22 +472,28 @@ __global__ void k_zero_pad(T* __restrict__ v, int nblocks, int64_t P, int64_t L)
 }
 
 // Full sweep: out = P^{-1} (Y, forcing G) (DIR 0) or P^{-T} Y with bout = B-tilde^T out (DIR 1).
+// Five launches: two memory-bound node passes (one warp per group) and three warp folds.
 template <typename T, int NX, int DIR>
 static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* out, T* bout, cudaStream_t st) {
-  const int nseg = pr->nseg, ngrp = pr->ngrp;
+  const int nseg = pr->nseg, ngrp = pr->ngrp, nsg = pr->nsg;
   const T s = (T)pr->s;
   const T* w = (const T*)d.w;
-  k_sweep_seg<T, NX, DIR><<<(nseg + 127) / 128, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, nseg, (double*)d.segb);
+  double* segb = (double*)d.segb;
+  double* grpb = (double*)d.grpb;
+  double* grpin = grpb + (size_t)round_up(ngrp, 32) * NX;
+  double* sgb = (double*)d.sgbuf;
+  double* sgin = sgb + (size_t)nsg * NX;
+  k_sw_up01<T, NX, DIR><<<ngrp, 32, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, nseg,
+                                              (const double*)d.Aseg, segb, grpb);
   BK_CHECK_LAUNCH();
-  k_sweep_grp<NX, DIR><<<(ngrp + 127) / 128, 128, 0, st>>>((const double*)d.Aseg, (const double*)d.segb, nseg, ngrp, (double*)d.grpb);
+  k_sw_up2<NX, DIR><<<nsg, 32, 0, st>>>((const double*)d.Agrp, grpb, ngrp, nsg, sgb);
   BK_CHECK_LAUNCH();
-  double* grpin = (double*)d.grpb + (size_t)NX * ngrp;
-  const size_t sm = sizeof(double) * 256 * (NX * NX + NX);
-  k_sweep_top<NX, DIR><<<1, 256, sm, st>>>((const double*)d.Agrp, (const double*)d.grpb, ngrp, grpin);
+  k_sw_top<NX, DIR><<<1, 32, 0, st>>>((const double*)d.Asg, sgb, nsg, sgin);
   BK_CHECK_LAUNCH();
-  k_sweep_dist<NX, DIR><<<(ngrp + 127) / 128, 128, 0, st>>>((const double*)d.Aseg, (double*)d.segb, nseg, ngrp, grpin);
+  k_sw_down2<NX, DIR><<<nsg, 32, 0, st>>>((const double*)d.Agrp, grpb, ngrp, nsg, sgin, grpin);
   BK_CHECK_LAUNCH();
-  k_sweep_out<T, NX, DIR><<<(nseg + 127) / 128, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, nseg, (const double*)d.segb, out, bout);
+  k_sw_down10<T, NX, DIR><<<ngrp, 32, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, nseg,
+                                                (const double*)d.Aseg, segb, grpin, out, bout);
   BK_CHECK_LAUNCH();
   if (pr->P > pr->L) {
     k_zero_pad<T><<<nblk(NX * (pr->P - pr->L)), 256, 0, st>>>(out, NX, pr->P, pr->L);
@@ -849,8 +842,9 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
   const int64_t il = (int64_t)round_up(pr->nseg, 32) * SEG * nx * nx;
   BK_TRY(dmalloc(&d.Kn, es * il));
   BK_TRY(dmalloc(&d.Nn, es * il));
-  BK_TRY(dmalloc(&d.Aseg, sizeof(double) * (size_t)pr->nseg * nx * nx));
-  BK_TRY(dmalloc(&d.Agrp, sizeof(double) * (size_t)pr->ngrp * nx * nx));
+  BK_TRY(dmalloc(&d.Aseg, sizeof(double) * (size_t)round_up(pr->nseg, 32) * nx * nx));
+  BK_TRY(dmalloc(&d.Agrp, sizeof(double) * (size_t)round_up(pr->ngrp, 32) * nx * nx));
+  BK_TRY(dmalloc(&d.Asg, sizeof(double) * (size_t)pr->nsg * nx * nx));
   if (ne > 0) {
     BK_TRY(dmalloc(&d.Zc, es * ne * nx * P));
     BK_TRY(dmalloc(&d.HWc, es * ne * nu * P));
@@ -860,14 +854,15 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
   BK_TRY(dmalloc(&d.t1, es * (nx + nu) * P));
   BK_TRY(dmalloc(&d.t2, es * (nx + nu) * P));
   BK_TRY(dmalloc(&d.t3, es * (nx + nu) * P));
-  BK_TRY(dmalloc(&d.segb, sizeof(double) * (size_t)pr->nseg * nx));
-  BK_TRY(dmalloc(&d.grpb, sizeof(double) * (size_t)pr->ngrp * nx * 2));
+  BK_TRY(dmalloc(&d.segb, sizeof(double) * (size_t)round_up(pr->nseg, 32) * nx));
+  BK_TRY(dmalloc(&d.grpb, sizeof(double) * (size_t)round_up(pr->ngrp, 32) * nx * 2));
+  BK_TRY(dmalloc(&d.sgbuf, sizeof(double) * (size_t)pr->nsg * nx * 2));
   return BK_OK;
 }
 
 static void free_opdata(OpData& d) {
   if (d.plan) plan_destroy(d.plan);
-  void* ps[] = {d.xu, d.mu, d.Kn, d.Nn, d.Aseg, d.Agrp, d.Zc, d.HWc, d.Qc, d.Sinv, d.t1, d.t2, d.t3, d.segb, d.grpb};
+  void* ps[] = {d.xu, d.mu, d.Kn, d.Nn, d.Aseg, d.Agrp, d.Asg, d.Zc, d.HWc, d.Qc, d.Sinv, d.t1, d.t2, d.t3, d.segb, d.grpb, d.sgbuf};
   for (void* p : ps) dfree(p);
   d = OpData();
 }
@@ -880,7 +875,9 @@ static bk_status lin_factors(Problem* pr, OpData& d, const double* z, cudaStream
   BK_CHECK_LAUNCH();
   k_lin_seg<T, NX><<<(pr->nseg + 127) / 128, 128, 0, st>>>((const T*)d.Nn, pr->L, pr->nseg, (double*)d.Aseg);
   BK_CHECK_LAUNCH();
-  k_lin_grp<NX><<<(pr->ngrp + 127) / 128, 128, 0, st>>>((const double*)d.Aseg, pr->nseg, pr->ngrp, (double*)d.Agrp);
+  k_lin_up<NX, true><<<(pr->ngrp + 127) / 128, 128, 0, st>>>((const double*)d.Aseg, pr->nseg, pr->ngrp, (double*)d.Agrp);
+  BK_CHECK_LAUNCH();
+  k_lin_up<NX, false><<<(pr->nsg + 127) / 128, 128, 0, st>>>((const double*)d.Agrp, pr->ngrp, pr->nsg, (double*)d.Asg);
   BK_CHECK_LAUNCH();
   return BK_OK;
 }
@@ -1209,6 +1206,7 @@ static bk_status problem_create(Problem** out, int kind, const double* params, i
   }
   pr->nseg = (int)((pr->L + SEG - 1) / SEG);
   pr->ngrp = (pr->nseg + GRP - 1) / GRP;
+  pr->nsg = (pr->ngrp + 31) / 32;
   AllocCounter counter(&pr->bytes);
   bk_status s = alloc_opdata(pr, pr->d64, BK_F64);
   if (s == BK_OK && dtype == BK_F32) s = alloc_opdata(pr, pr->d32, BK_F32);

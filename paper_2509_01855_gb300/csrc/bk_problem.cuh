@@ -116,7 +116,8 @@ struct OpData {
   void* Kn = nullptr;          // per-node K_k = (I - h_k J_k)^{-1}, interleaved (n_x^2 per node)
   void* Nn = nullptr;          // per-node N_k = 2 h_k J_k K_k, interleaved
   void* Aseg = nullptr;        // segment aggregates of prod (I + N_k) (n_x^2 per segment)
-  void* Agrp = nullptr;        // group aggregates (n_x^2 per group)
+  void* Agrp = nullptr;        // group aggregates (n_x^2 per group, 32 segments each)
+  void* Asg = nullptr;         // supergroup aggregates (n_x^2 per supergroup, 32 groups each)
   // KKT preconditioner (terminal Schur data)
   void* Zc = nullptr;          // n_e state vectors   Z = P^{-T} E^T
   void* HWc = nullptr;         // n_e control vectors H~^{-1} W, W = Pu^T Z
@@ -128,6 +129,7 @@ struct OpData {
   void* t3 = nullptr;
   void* segb = nullptr;        // per-segment affine offsets
   void* grpb = nullptr;        // per-group affine offsets / incoming states
+  void* sgbuf = nullptr;       // per-supergroup offsets / incoming states
 };
 
 struct Problem {
@@ -140,7 +142,7 @@ struct Problem {
   int term_idx[NEM] = {0, 0, 0, 0};
   double term_val[NEM] = {0, 0, 0, 0};
   bool has_cost = true;
-  int nseg = 0, ngrp = 0;
+  int nseg = 0, ngrp = 0, nsg = 0;
   bool linearized = false;
   OpData d64;                  // FP64 operators (always)
   OpData d32;                  // FP32 operators (BK_F32 problems)
