@@ -236,7 +236,9 @@ bk_status krylov_solve(bk_problem* prob, int op, const void* rhs, void* sol,
 typedef struct {
   double tol;         /* stop when the weighted KKT residual norm <= tol (default 1e-10)     */
   int max_iter;       /* Newton iteration cap (default 30)                                  */
-  double krylov_rtol; /* inner relative tolerance (default 1e-12 in FP64, 1e-4 in FP32)     */
+  double krylov_rtol; /* inner relative tolerance; 0 (default) = forcing term
+                         0.1 (||F_k|| / ||F_0||)^2 clamped to [1e-12 (FP64) or 1e-4 (FP32),
+                         1e-2], i.e. loose early Newton steps and tight final ones           */
   int restart;        /* GMRES restart (default 30)                                         */
   int max_krylov;     /* inner iteration cap per solve (default 300 in FP64, 10 in FP32)    */
   double ir_rtol;     /* FP32 mode: linear refinement sweeps stop when the FP64 residual of

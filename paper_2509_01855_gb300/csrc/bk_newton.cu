@@ -127,18 +127,27 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
   info->residual = phi;
   int it = 0;
   while (phi > o.tol && it < o.max_iter) {
+    // Inner tolerance: fixed if the caller set one, else a forcing term that tightens with the
+    // outer residual, rtol_k = 0.1 (phi_k / phi_0)^2 clamped to [floor, 1e-2] (Eisenstat and
+    // Walker's choice 2 with gamma = 0.1, alpha = 2): loose early steps, tight final ones,
+    // quadratic outer convergence kept. Floor 1e-12 in FP64, 1e-4 in FP32.
+    if (o.krylov_rtol > 0) {
+      ko.rtol = o.krylov_rtol;
+    } else {
+      const double r = phi / info->residual0;
+      const double lo = pr->dtype == BK_F64 ? 1e-12 : 1e-4;
+      ko.rtol = fmin(1e-2, fmax(lo, 0.1 * r * r));
+    }
     BK_TRY(problem_linearize(pr, z, st, /*mu_ready=*/true));
     k_axpby64<<<g, 256, 0, st>>>(F, -1.0, rhs, 0.0, n);
     BK_CHECK_LAUNCH();
     bk_krylov_info ki;
     if (pr->dtype == BK_F64) {
-      ko.rtol = o.krylov_rtol;
       BK_TRY(gmres(pr, pr->d64, BK_OP_KKT, rhs, d, ko, &ki, gws, st));
       info->krylov_iterations += ki.iterations;
       info->kkt_solves += 1;
     } else {
       // FP32 GMRES inside FP64 iterative refinement
-      ko.rtol = o.krylov_rtol;
       double rn0 = 0.0;
       BK_TRY(norm2(pr, rhs, n, &rn0, st));
       BK_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n, st));
@@ -213,10 +222,10 @@ bk_status newton_solve(bk_problem* prob, double* z_inout, const bk_newton_opts* 
   if (opts) o = *opts;
   if (o.tol <= 0) o.tol = 1e-10;
   if (o.max_iter <= 0) o.max_iter = 30;
-  // FP64: tight inner solves (Newton converges quadratically). FP32: inexact Newton, one FP32
-  // GMRES solve to 1e-4 (at most 10 iterations) per step, refined by the FP64 Newton residual.
+  // FP64: up to 300 inner iterations. FP32: inexact Newton, one FP32 GMRES solve (at most 10
+  // iterations) per step, refined by the FP64 Newton residual.
   const bool f64 = p->dtype == BK_F64;
-  if (o.krylov_rtol <= 0) o.krylov_rtol = f64 ? 1e-12 : 1e-4;
+  if (o.krylov_rtol < 0) o.krylov_rtol = 0;  // 0 = adaptive forcing term (see newton_impl)
   if (o.restart <= 0) o.restart = 30;
   if (o.max_krylov <= 0) o.max_krylov = f64 ? 300 : 10;
   if (o.ir_rtol <= 0) o.ir_rtol = 1e-10;

@@ -158,12 +158,28 @@ def test_newton_double_integrator_closed_form(N):
     t = t.numpy(); w = w.numpy()
     X, U = synth.double_integrator_guess(t)
     z = prob.pack(X, U)
-    info = api.newton_solve(prob, z)
+    # linear dynamics, quadratic cost: one Newton step with a tight inner solve is exact
+    info = api.newton_solve(prob, z, krylov_rtol=1e-12)
     assert info["converged"] and info["iterations"] == 1
     Xg, Ug, _, _ = [a.cpu().numpy() for a in prob.split(z)]
     assert np.abs(Xg[0] - (3 * t**2 - 2 * t**3)).max() < 1e-9
     assert np.abs(Xg[1] - (6 * t - 6 * t**2)).max() < 1e-9
     assert np.sqrt(0.5 * np.sum(w * (Ug[0] - (6 - 12 * t)) ** 2)) < 1e-9
+
+
+@pytest.mark.parametrize("N", [16, 256])
+def test_newton_double_integrator_forcing_term(N):
+    """Default inner tolerance (forcing term): loose early steps still reach the closed form."""
+    api, lib = _api()
+    prob = api.Problem(lib.BK_DBL_INT, N, torch.float64, 0.0, 1.0)
+    t, _ = api.Plan(N, t0=0.0, tf=1.0).grid()
+    t = t.numpy()
+    X, U = synth.double_integrator_guess(t)
+    z = prob.pack(X, U)
+    info = api.newton_solve(prob, z)
+    assert info["converged"] and 1 <= info["iterations"] <= 4, info
+    Xg = prob.split(z)[0].cpu().numpy()
+    assert np.abs(Xg[0] - (3 * t**2 - 2 * t**3)).max() < 1e-9
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
