@@ -13,9 +13,9 @@
 // above is what the rows of P give.) The transpose P^T y = r runs backwards:
 //   y_j = K_j^T r_j + N_j^T rho_j,  rho_{j-1} = rho_j + y_j,  (B-tilde^T y)_j = w_j (y_j/2 + rho_j).
 // Both are affine recurrences sigma_{k+1} = (I + N_k) sigma_k + f_k; they run as a chunked scan:
-// segments of SEG nodes (one thread each, sequential), groups of GRP segments, and one CTA that
-// scans the group maps. The matrix parts of the segment and group maps depend only on the
-// linearisation and are formed in bk_linearize; the backward maps are their transposes.
+// segments of SEG nodes (one thread each, sequential), then levels of blocks of 32 scanned by
+// warps. The matrix parts of every level's maps depend only on the linearisation and are formed
+// in bk_linearize; the backward maps are their transposes.
 #include <math.h>
 #include <string.h>
 
@@ -130,72 +130,125 @@ __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, 
   }
 }
 
-// Aggregates of the sweep's affine maps. Level 0: segments of SEG nodes; level 1: groups of 32
-// segments; level 2: supergroups of 32 groups. A level's aggregate is the product of its items'
-// matrices (latest item on the left); for the backward sweep it is the transpose. They are FP64
-// for both working precisions: few, and FP32 products of ~1000 Cayley factors would cost the
-// FP32 preconditioner its accuracy at large N. Levels 0 and 1 are stored 32-interleaved
-// (element c of item i at il32(i, c, NC)) so that a warp reading 32 consecutive items is
-// coalesced.
+// Level data of the sweep's affine maps. Level 0 items are segments of SEG nodes, whose map is
+// the product of (I + N_k) over the segment (latest node on the left); a level-(l+1) item is a
+// block of 32 level-l items and its map the product of theirs. The backward sweep uses the
+// transposed maps in reverse order. All level data is FP64 for both working precisions (FP32
+// products of ~1000 Cayley factors would cost the FP32 preconditioner its accuracy at large N)
+// and 32-interleaved (element c of item i at il32(i, c, NC)), so that a warp reading 32
+// consecutive items is coalesced; slot q of a level starts at q * npad * n_x^2, npad = the
+// level's item count rounded up to 32.
 __device__ __forceinline__ int64_t il32(int64_t i, int c, int NC) { return (((i >> 5) * NC + c) << 5) + (i & 31); }
 
+// C = A B (n_x x n_x, row-major)
 template <int NX>
-__device__ __forceinline__ void mat_left(const double* M, double* A) {
-  // A <- M A
-  double R[NX * NX];
+__device__ __forceinline__ void mat_mul(const double* A, const double* B, double* C) {
 #pragma unroll
   for (int r = 0; r < NX; ++r)
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
       double a = 0;
 #pragma unroll
-      for (int q = 0; q < NX; ++q) a += M[r * NX + q] * A[q * NX + c];
-      R[r * NX + c] = a;
+      for (int q = 0; q < NX; ++q) a += A[r * NX + q] * B[q * NX + c];
+      C[r * NX + c] = a;
     }
-#pragma unroll
-  for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
 }
 
+// Level-0 maps: prod over the segment's nodes of (I + N_k), one thread per segment.
 template <typename T, int NX>
-__global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, double* __restrict__ Aseg) {
+__global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, double* __restrict__ A0) {
   const int seg = blockIdx.x * blockDim.x + threadIdx.x;
   if (seg >= nseg) return;
-  double A[NX * NX];
+  double A[NX * NX], M[NX * NX], R[NX * NX];
 #pragma unroll
   for (int i = 0; i < NX * NX; ++i) A[i] = (i % (NX + 1) == 0) ? 1.0 : 0.0;
   for (int i = 0; i < SEG; ++i) {
     const int64_t k = (int64_t)seg * SEG + i;
     if (k >= L) break;
-    double M[NX * NX];
 #pragma unroll
     for (int c = 0; c < NX * NX; ++c) M[c] = (double)Nn[il_index(k, c, NX * NX)] + ((c % (NX + 1) == 0) ? 1.0 : 0.0);
-    mat_left<NX>(M, A);
+    mat_mul<NX>(M, A, R);
+#pragma unroll
+    for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
   }
 #pragma unroll
-  for (int c = 0; c < NX * NX; ++c) Aseg[il32(seg, c, NX * NX)] = A[c];
+  for (int c = 0; c < NX * NX; ++c) A0[il32(seg, c, NX * NX)] = A[c];
 }
 
-// Level-1 (OUT_IL = true, 32-interleaved output) or level-2 (plain [c][item]) aggregates from
-// 32-interleaved lower-level aggregates.
-template <int NX, bool OUT_IL>
-__global__ void k_lin_up(const double* __restrict__ Alow, int nlow, int nup, double* __restrict__ Aup) {
-  const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= nup) return;
-  double A[NX * NX];
+// Slots of one level, one warp per block of 32 items (items at or beyond n are identity maps):
+// spans M_k(j) = M_{k-1}(j) M_{k-1}(j - 2^{k-1}) by doubling (defined for j >= 2^k - 1), Pre(i)
+// and Suf(i) as products of the spans that tile [0, i) and (i, 31], and the block's product
+// M_4(31) M_4(15), which is the map of the parent item at the next level.
+template <int NX>
+__global__ void __launch_bounds__(32) k_lin_level(double* __restrict__ m, int n, double* __restrict__ parent) {
+  constexpr int NC = NX * NX;
+  __shared__ double S[5][32][NC + 1];
+  const int lane = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+  const int64_t slot = (int64_t)gridDim.x * 32 * NC;
 #pragma unroll
-  for (int i = 0; i < NX * NX; ++i) A[i] = (i % (NX + 1) == 0) ? 1.0 : 0.0;
-  for (int i = 0; i < 32; ++i) {
-    const int lo = u * 32 + i;
-    if (lo >= nlow) break;
-    double M[NX * NX];
+  for (int c = 0; c < NC; ++c) {
+    const double idc = (c % (NX + 1) == 0) ? 1.0 : 0.0;
+    const double a = i < n ? m[il32(i, c, NC)] : idc;
+    S[0][lane][c] = a;
+    if (i >= n) m[il32(i, c, NC)] = idc;
+  }
+  __syncwarp();
+  for (int k = 1; k < 5; ++k) {
+    const int h = 1 << (k - 1);
+    double R[NC];
+    if (lane >= 2 * h - 1) {
+      mat_mul<NX>(S[k - 1][lane], S[k - 1][lane - h], R);
+    } else {
 #pragma unroll
-    for (int c = 0; c < NX * NX; ++c) M[c] = Alow[il32(lo, c, NX * NX)];
-    mat_left<NX>(M, A);
+      for (int c = 0; c < NC; ++c) R[c] = (c % (NX + 1) == 0) ? 1.0 : 0.0;
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) S[k][lane][c] = R[c];
+    __syncwarp();
   }
 #pragma unroll
-  for (int c = 0; c < NX * NX; ++c) {
-    if (OUT_IL) Aup[il32(u, c, NX * NX)] = A[c];
-    else Aup[(int64_t)c * nup + u] = A[c];
+  for (int k = 1; k < 5; ++k)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) m[k * slot + il32(i, c, NC)] = S[k][lane][c];
+  double R[NC], Q[NC];
+  // Pre(i) = A_{i-1} ... A_0
+#pragma unroll
+  for (int c = 0; c < NC; ++c) R[c] = (c % (NX + 1) == 0) ? 1.0 : 0.0;
+  int pos = 0;
+  for (int k = 4; k >= 0; --k) {
+    if ((lane >> k) & 1) {
+      mat_mul<NX>(S[k][pos + (1 << k) - 1], R, Q);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) R[c] = Q[c];
+      pos += 1 << k;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) m[SL_PRE * slot + il32(i, c, NC)] = R[c];
+  // Suf(i) = A_31 ... A_{i+1}
+#pragma unroll
+  for (int c = 0; c < NC; ++c) R[c] = (c % (NX + 1) == 0) ? 1.0 : 0.0;
+  int end = 31;
+  const int len = 31 - lane;
+  for (int k = 4; k >= 0; --k) {
+    if ((len >> k) & 1) {
+      mat_mul<NX>(R, S[k][end], Q);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) R[c] = Q[c];
+      end -= 1 << k;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) m[SL_SUF * slot + il32(i, c, NC)] = R[c];
+  if (parent) {
+    for (int c = lane; c < NC; c += 32) {
+      const int r = c / NX, cc = c % NX;
+      double a = 0;
+#pragma unroll
+      for (int q = 0; q < NX; ++q) a += S[4][31][r * NX + q] * S[4][15][q * NX + cc];
+      parent[il32(blockIdx.x, c, NC)] = a;
+    }
   }
 }
 
@@ -210,14 +263,30 @@ __global__ void k_convert(const Tin* __restrict__ a, Tout* __restrict__ b, int64
 // y'_k = Y_k + h_k g_k, output xi_k = K_k (y'_k + sigma_k). Backward (DIR = 1): rho_{j-1} =
 // (I + N_j^T) rho_j + K_j^T r_j, output y_j = K_j^T r_j + N_j^T rho_j, optional b_j =
 // w_j (y_j / 2 + rho_j).
+//
+// A sweep scans the affine maps sigma -> A sigma + b level by level. The up kernels form each
+// item's offset b (its map applied to a zero state) and the inclusive scan e of the offsets
+// within its block of 32: a Kogge-Stone scan over the lanes of a warp with the span matrices,
+// so that every FP64 instruction runs on all 32 lanes (a warp instruction occupies the FP64
+// pipe for its full width whatever its active mask). The down kernel composes, for its segment,
+// the incoming state from the top level down, S <- Pre(i) S + e(i-1) (backward:
+// S <- Suf(i)^T S + e(i+1)), and reruns the segment's nodes from it.
 // ---------------------------------------------------------------------------------------------
+struct Levels {
+  const double* m[MAXLEV];  // matrix slots per level
+  double* o[MAXLEV];        // item offsets from zero, levels >= 1
+  double* e[MAXLEV];        // inclusive in-block scan values
+  int n[MAXLEV];            // items per level
+  int nlev;
+};
+
 template <typename T, int NX, int DIR>
 __device__ __forceinline__ void node_step(const T* __restrict__ Kn, const T* __restrict__ Nn, int64_t k,
                                           const T* yin, const T* gin, T h, T* st, T* out, bool want_out) {
   T Km[NX * NX], Nm[NX * NX];
 #pragma unroll
   for (int c = 0; c < NX * NX; ++c) {
-    Km[c] = Kn[il_index(k, c, NX * NX)];
+    if (DIR == 1 || want_out) Km[c] = Kn[il_index(k, c, NX * NX)];
     Nm[c] = Nn[il_index(k, c, NX * NX)];
   }
   if (DIR == 0) {
@@ -261,191 +330,143 @@ __device__ __forceinline__ void node_step(const T* __restrict__ Kn, const T* __r
   }
 }
 
-// One affine step st <- A st + b (DIR 0) or A^T st + b (DIR 1), FP64.
+// Inclusive scan of the offsets e within block blk (lane i holds item 32 blk + i), level slot
+// size `slot`. DIR 0: e_i += M_k(i) e_{i-2^k}; DIR 1 (reverse order, transposed maps):
+// e_i += M_k(i + 2^k - 1)^T e_{i+2^k}.
 template <int NX, int DIR>
-__device__ __forceinline__ void affine_step(const double* A, const double* b, double* st) {
-  double ns[NX];
+__device__ __forceinline__ void warp_scan(const double* __restrict__ m, int64_t slot, int64_t blk, double* e) {
+  constexpr int NC = NX * NX;
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int r = 0; r < NX; ++r) {
-    double a = b[r];
+  for (int k = 0; k < 5; ++k) {
+    const int d = 1 << k;
+    double pe[NX];
 #pragma unroll
-    for (int c = 0; c < NX; ++c) a += (DIR == 0 ? A[r * NX + c] : A[c * NX + r]) * st[c];
-    ns[r] = a;
+    for (int r = 0; r < NX; ++r)
+      pe[r] = DIR == 0 ? __shfl_up_sync(0xffffffffu, e[r], d) : __shfl_down_sync(0xffffffffu, e[r], d);
+    const bool act = DIR == 0 ? lane >= d : lane + d < 32;
+    if (act) {
+      const int64_t item = blk * 32 + (DIR == 0 ? lane : lane + d - 1);
+      const double* M = m + k * slot;
+      double Mv[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) Mv[c] = M[il32(item, c, NC)];
+#pragma unroll
+      for (int r = 0; r < NX; ++r) {
+        double a = e[r];
+#pragma unroll
+        for (int c = 0; c < NX; ++c) a += (DIR == 0 ? Mv[r * NX + c] : Mv[c * NX + r]) * pe[c];
+        e[r] = a;
+      }
+    }
   }
-#pragma unroll
-  for (int r = 0; r < NX; ++r) st[r] = ns[r];
 }
 
-// Stage the 32 items of a block (aggregates A and offsets b, 32-interleaved) into shared memory;
-// items beyond n become the identity map.
-template <int NX>
-__device__ __forceinline__ void stage32(const double* __restrict__ Ag, const double* __restrict__ bg, int64_t item,
-                                        int n, double (*sA)[NX * NX], double (*sb)[NX]) {
-  const int lane = threadIdx.x;
-  const bool ok = item < n;
-#pragma unroll
-  for (int c = 0; c < NX * NX; ++c) sA[lane][c] = ok ? Ag[il32(item, c, NX * NX)] : ((c % (NX + 1) == 0) ? 1.0 : 0.0);
-#pragma unroll
-  for (int c = 0; c < NX; ++c) sb[lane][c] = ok ? bg[il32(item, c, NX)] : 0.0;
-  __syncwarp();
-}
-
-// Up-sweep, level 0+1 (one warp per group): each lane runs its segment from a zero state (the
-// segment's offset); lane 0 folds the 32 segment maps into the group's offset.
+// Up, level 0 (one warp per block of 32 segments, 4 warps per CTA): each lane runs its segment
+// from a zero state (the segment's offset), then the warp scans the block.
 template <typename T, int NX, int DIR>
-__global__ void __launch_bounds__(32) k_sw_up01(const T* __restrict__ Kn, const T* __restrict__ Nn,
+__global__ void __launch_bounds__(128) k_sw_up0(const T* __restrict__ Kn, const T* __restrict__ Nn,
                                                 const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
-                                                int64_t L, const T* __restrict__ w, T s, int nseg,
-                                                const double* __restrict__ Aseg, double* __restrict__ segb,
-                                                double* __restrict__ grpb) {
-  __shared__ double sA[32][NX * NX];
-  __shared__ double sb[32][NX];
-  const int g = blockIdx.x;
-  const int seg = g * 32 + threadIdx.x;
-  if (seg < nseg) {
-    T st[NX], dummy[2 * NX];
+                                                int64_t L, const T* __restrict__ w, T s, Levels lv) {
+  const int nblk = (lv.n[0] + 31) >> 5;
+  const int g = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (g >= nblk) return;  // whole warps
+  const int lane = threadIdx.x & 31;
+  const int64_t seg = (int64_t)g * 32 + lane;
+  T st[NX];
 #pragma unroll
-    for (int m = 0; m < NX; ++m) st[m] = T(0);
+  for (int m = 0; m < NX; ++m) st[m] = T(0);
+  if (seg < lv.n[0]) {
+    T dummy[2 * NX];
     for (int ii = 0; ii < SEG; ++ii) {
       const int i = DIR == 0 ? ii : SEG - 1 - ii;
-      const int64_t k = (int64_t)seg * SEG + i;
+      const int64_t k = seg * SEG + i;
       if (k >= L) { if (DIR == 0) break; else continue; }
       T yin[NX], gin[NX];
 #pragma unroll
       for (int m = 0; m < NX; ++m) { yin[m] = Y[m * P + k]; gin[m] = G ? G[m * P + k] : T(0); }
       node_step<T, NX, DIR>(Kn, Nn, k, yin, gin, T(0.5) * s * w[k], st, dummy, false);
     }
-#pragma unroll
-    for (int m = 0; m < NX; ++m) segb[il32(seg, m, NX)] = (double)st[m];
   }
-  __syncwarp();
-  stage32<NX>(Aseg, segb, seg, nseg, sA, sb);
-  if (threadIdx.x == 0) {
-    double st[NX];
+  double e[NX];
 #pragma unroll
-    for (int m = 0; m < NX; ++m) st[m] = 0.0;
-    for (int ii = 0; ii < 32; ++ii) {
-      const int i = DIR == 0 ? ii : 31 - ii;
-      affine_step<NX, DIR>(sA[i], sb[i], st);
-    }
+  for (int m = 0; m < NX; ++m) e[m] = (double)st[m];
+  warp_scan<NX, DIR>(lv.m[0], (int64_t)nblk * 32 * NX * NX, g, e);
 #pragma unroll
-    for (int m = 0; m < NX; ++m) grpb[il32(g, m, NX)] = st[m];
+  for (int m = 0; m < NX; ++m) lv.e[0][il32(seg, m, NX)] = e[m];
+  if (lv.nlev > 1 && lane == (DIR == 0 ? 31 : 0)) {
+#pragma unroll
+    for (int m = 0; m < NX; ++m) lv.o[1][il32(g, m, NX)] = e[m];
   }
 }
 
-// Up-sweep, level 2 (one warp per supergroup): fold 32 group maps into the supergroup offset.
+// Up, level l >= 1 (one warp per block of 32 items): scan of the items' offsets.
 template <int NX, int DIR>
-__global__ void __launch_bounds__(32) k_sw_up2(const double* __restrict__ Agrp, const double* __restrict__ grpb,
-                                               int ngrp, int nsg, double* __restrict__ sgb) {
-  __shared__ double sA[32][NX * NX];
-  __shared__ double sb[32][NX];
-  const int sg = blockIdx.x;
-  stage32<NX>(Agrp, grpb, (int64_t)sg * 32 + threadIdx.x, ngrp, sA, sb);
-  if (threadIdx.x == 0) {
-    double st[NX];
+__global__ void __launch_bounds__(128) k_sw_upL(Levels lv, int l) {
+  const int n = lv.n[l];
+  const int nblk = (n + 31) >> 5;
+  const int b = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (b >= nblk) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)b * 32 + lane;
+  const double* o = lv.o[l];
+  double e[NX];
 #pragma unroll
-    for (int m = 0; m < NX; ++m) st[m] = 0.0;
-    for (int ii = 0; ii < 32; ++ii) affine_step<NX, DIR>(sA[DIR == 0 ? ii : 31 - ii], sb[DIR == 0 ? ii : 31 - ii], st);
+  for (int m = 0; m < NX; ++m) e[m] = i < n ? o[il32(i, m, NX)] : 0.0;
+  warp_scan<NX, DIR>(lv.m[l], (int64_t)nblk * 32 * NX * NX, b, e);
+  double* el = lv.e[l];
 #pragma unroll
-    for (int m = 0; m < NX; ++m) sgb[(int64_t)m * nsg + sg] = st[m];
+  for (int m = 0; m < NX; ++m) el[il32(i, m, NX)] = e[m];
+  if (l + 1 < lv.nlev && lane == (DIR == 0 ? 31 : 0)) {
+    double* op = lv.o[l + 1];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) op[il32(b, m, NX)] = e[m];
   }
 }
 
-// Top (one warp): incoming state of every supergroup, in sweep order, chunks staged in smem.
-template <int NX, int DIR>
-__global__ void __launch_bounds__(32) k_sw_top(const double* __restrict__ Asg, const double* __restrict__ sgb,
-                                               int nsg, double* __restrict__ sgin) {
-  __shared__ double sA[32][NX * NX];
-  __shared__ double sb[32][NX];
-  double st[NX];
-#pragma unroll
-  for (int m = 0; m < NX; ++m) st[m] = 0.0;
-  for (int c0 = 0; c0 < nsg; c0 += 32) {
-    // chunk of 32 supergroups in sweep order
-    const int o = c0 + threadIdx.x;
-    const int sg = DIR == 0 ? o : nsg - 1 - o;
-    const bool ok = o < nsg;
-#pragma unroll
-    for (int c = 0; c < NX * NX; ++c) sA[threadIdx.x][c] = ok ? Asg[(int64_t)c * nsg + sg] : 0.0;
-#pragma unroll
-    for (int c = 0; c < NX; ++c) sb[threadIdx.x][c] = ok ? sgb[(int64_t)c * nsg + sg] : 0.0;
-    __syncwarp();
-    if (threadIdx.x == 0) {
-      const int cnt = nsg - c0 < 32 ? nsg - c0 : 32;
-      for (int i = 0; i < cnt; ++i) {
-        const int sgi = DIR == 0 ? c0 + i : nsg - 1 - (c0 + i);
-#pragma unroll
-        for (int m = 0; m < NX; ++m) sgin[(int64_t)m * nsg + sgi] = st[m];
-        affine_step<NX, DIR>(sA[i], sb[i], st);
-      }
-    }
-    __syncwarp();
-  }
-}
-
-// Down-sweep, level 2 (one warp per supergroup): incoming state of each of its groups.
-template <int NX, int DIR>
-__global__ void __launch_bounds__(32) k_sw_down2(const double* __restrict__ Agrp, const double* __restrict__ grpb,
-                                                 int ngrp, int nsg, const double* __restrict__ sgin,
-                                                 double* __restrict__ grpin) {
-  __shared__ double sA[32][NX * NX];
-  __shared__ double sb[32][NX];
-  const int sg = blockIdx.x;
-  stage32<NX>(Agrp, grpb, (int64_t)sg * 32 + threadIdx.x, ngrp, sA, sb);
-  __shared__ double sin_[32][NX];
-  if (threadIdx.x == 0) {
-    double st[NX];
-#pragma unroll
-    for (int m = 0; m < NX; ++m) st[m] = sgin[(int64_t)m * nsg + sg];
-    for (int ii = 0; ii < 32; ++ii) {
-      const int i = DIR == 0 ? ii : 31 - ii;
-#pragma unroll
-      for (int m = 0; m < NX; ++m) sin_[i][m] = st[m];
-      affine_step<NX, DIR>(sA[i], sb[i], st);
-    }
-  }
-  __syncwarp();
-  const int64_t g = (int64_t)sg * 32 + threadIdx.x;
-  if (g < ngrp) {
-#pragma unroll
-    for (int m = 0; m < NX; ++m) grpin[il32(g, m, NX)] = sin_[threadIdx.x][m];
-  }
-}
-
-// Down-sweep, level 1+0 (one warp per group): lane 0 forms the incoming state of each segment,
-// then every lane reruns its segment from it and writes the outputs.
+// Down (one warp per block of 32 segments): incoming state of the lane's segment, composed from
+// the top level down, then the segment's nodes with outputs.
 template <typename T, int NX, int DIR>
-__global__ void __launch_bounds__(32) k_sw_down10(const T* __restrict__ Kn, const T* __restrict__ Nn,
+__global__ void __launch_bounds__(128) k_sw_down0(const T* __restrict__ Kn, const T* __restrict__ Nn,
                                                   const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
-                                                  int64_t L, const T* __restrict__ w, T s, int nseg,
-                                                  const double* __restrict__ Aseg, const double* __restrict__ segb,
-                                                  const double* __restrict__ grpin, T* __restrict__ out,
-                                                  T* __restrict__ bout) {
-  __shared__ double sA[32][NX * NX];
-  __shared__ double sb[32][NX];
-  __shared__ double sin_[32][NX];
-  const int g = blockIdx.x;
-  const int seg = g * 32 + threadIdx.x;
-  stage32<NX>(Aseg, segb, seg, nseg, sA, sb);
-  if (threadIdx.x == 0) {
-    double st[NX];
+                                                  int64_t L, const T* __restrict__ w, T s, Levels lv,
+                                                  T* __restrict__ out, T* __restrict__ bout) {
+  constexpr int NC = NX * NX;
+  const int nblk0 = (lv.n[0] + 31) >> 5;
+  const int g = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (g >= nblk0) return;
+  const int64_t seg = (int64_t)g * 32 + (threadIdx.x & 31);
+  if (seg >= lv.n[0]) return;
+  double S[NX];
 #pragma unroll
-    for (int m = 0; m < NX; ++m) st[m] = grpin[il32(g, m, NX)];
-    for (int ii = 0; ii < 32; ++ii) {
-      const int i = DIR == 0 ? ii : 31 - ii;
+  for (int m = 0; m < NX; ++m) S[m] = 0.0;
+  for (int l = lv.nlev - 1; l >= 0; --l) {
+    const int64_t i = seg >> (5 * l);
+    const int q = (int)(i & 31);
+    if (DIR == 0 ? q == 0 : q == 31) continue;  // first item of its block in sweep order
+    const int64_t slot = (int64_t)((lv.n[l] + 31) >> 5) * 32 * NC;
+    const double* Mt = lv.m[l] + (DIR == 0 ? SL_PRE : SL_SUF) * slot;
+    const double* el = lv.e[l];
+    const int64_t ia = DIR == 0 ? i - 1 : i + 1;
+    double Mv[NC], ns[NX];
 #pragma unroll
-      for (int m = 0; m < NX; ++m) sin_[i][m] = st[m];
-      affine_step<NX, DIR>(sA[i], sb[i], st);
+    for (int c = 0; c < NC; ++c) Mv[c] = Mt[il32(i, c, NC)];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      double a = el[il32(ia, r, NX)];
+#pragma unroll
+      for (int c = 0; c < NX; ++c) a += (DIR == 0 ? Mv[r * NX + c] : Mv[c * NX + r]) * S[c];
+      ns[r] = a;
     }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) S[r] = ns[r];
   }
-  __syncwarp();
-  if (seg >= nseg) return;
   T st[NX];
 #pragma unroll
-  for (int m = 0; m < NX; ++m) st[m] = (T)sin_[threadIdx.x][m];
+  for (int m = 0; m < NX; ++m) st[m] = (T)S[m];
   for (int ii = 0; ii < SEG; ++ii) {
     const int i = DIR == 0 ? ii : SEG - 1 - ii;
-    const int64_t k = (int64_t)seg * SEG + i;
+    const int64_t k = seg * SEG + i;
     if (k >= L) { if (DIR == 0) break; else continue; }
     T yin[NX], gin[NX], o[2 * NX];
 #pragma unroll
@@ -471,29 +492,35 @@ __global__ void k_zero_pad(T* __restrict__ v, int nblocks, int64_t P, int64_t L)
   }
 }
 
+static Levels levels_of(const Problem* pr, const OpData& d) {
+  Levels lv;
+  memset(&lv, 0, sizeof(lv));
+  lv.nlev = pr->nlev;
+  for (int l = 0; l < pr->nlev; ++l) {
+    lv.m[l] = d.lvm[l];
+    lv.o[l] = d.lvo[l];
+    lv.e[l] = d.lve[l];
+    lv.n[l] = pr->lvn[l];
+  }
+  return lv;
+}
+
 // Full sweep: out = P^{-1} (Y, forcing G) (DIR 0) or P^{-T} Y with bout = B-tilde^T out (DIR 1).
-// Five launches: two memory-bound node passes (one warp per group) and three warp folds.
+// nlev + 1 launches: the level-0 up pass, one scan per upper level, the down pass.
 template <typename T, int NX, int DIR>
 static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* out, T* bout, cudaStream_t st) {
-  const int nseg = pr->nseg, ngrp = pr->ngrp, nsg = pr->nsg;
   const T s = (T)pr->s;
   const T* w = (const T*)d.w;
-  double* segb = (double*)d.segb;
-  double* grpb = (double*)d.grpb;
-  double* grpin = grpb + (size_t)round_up(ngrp, 32) * NX;
-  double* sgb = (double*)d.sgbuf;
-  double* sgin = sgb + (size_t)nsg * NX;
-  k_sw_up01<T, NX, DIR><<<ngrp, 32, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, nseg,
-                                              (const double*)d.Aseg, segb, grpb);
+  const Levels lv = levels_of(pr, d);
+  const int g0 = (((pr->lvn[0] + 31) >> 5) + 3) / 4;
+  k_sw_up0<T, NX, DIR><<<g0, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv);
   BK_CHECK_LAUNCH();
-  k_sw_up2<NX, DIR><<<nsg, 32, 0, st>>>((const double*)d.Agrp, grpb, ngrp, nsg, sgb);
-  BK_CHECK_LAUNCH();
-  k_sw_top<NX, DIR><<<1, 32, 0, st>>>((const double*)d.Asg, sgb, nsg, sgin);
-  BK_CHECK_LAUNCH();
-  k_sw_down2<NX, DIR><<<nsg, 32, 0, st>>>((const double*)d.Agrp, grpb, ngrp, nsg, sgin, grpin);
-  BK_CHECK_LAUNCH();
-  k_sw_down10<T, NX, DIR><<<ngrp, 32, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, nseg,
-                                                (const double*)d.Aseg, segb, grpin, out, bout);
+  for (int l = 1; l < pr->nlev; ++l) {
+    const int gl = (((pr->lvn[l] + 31) >> 5) + 3) / 4;
+    k_sw_upL<NX, DIR><<<gl, 128, 0, st>>>(lv, l);
+    BK_CHECK_LAUNCH();
+  }
+  k_sw_down0<T, NX, DIR><<<g0, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv, out, bout);
   BK_CHECK_LAUNCH();
   if (pr->P > pr->L) {
     k_zero_pad<T><<<nblk(NX * (pr->P - pr->L)), 256, 0, st>>>(out, NX, pr->P, pr->L);
@@ -842,9 +869,12 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
   const int64_t il = (int64_t)round_up(pr->nseg, 32) * SEG * nx * nx;
   BK_TRY(dmalloc(&d.Kn, es * il));
   BK_TRY(dmalloc(&d.Nn, es * il));
-  BK_TRY(dmalloc(&d.Aseg, sizeof(double) * (size_t)round_up(pr->nseg, 32) * nx * nx));
-  BK_TRY(dmalloc(&d.Agrp, sizeof(double) * (size_t)round_up(pr->ngrp, 32) * nx * nx));
-  BK_TRY(dmalloc(&d.Asg, sizeof(double) * (size_t)pr->nsg * nx * nx));
+  for (int l = 0; l < pr->nlev; ++l) {
+    const size_t npad = (size_t)round_up(pr->lvn[l], 32);
+    BK_TRY(dmalloc((void**)&d.lvm[l], sizeof(double) * NSLOT * npad * nx * nx));
+    BK_TRY(dmalloc((void**)&d.lve[l], sizeof(double) * npad * nx));
+    if (l > 0) BK_TRY(dmalloc((void**)&d.lvo[l], sizeof(double) * npad * nx));
+  }
   if (ne > 0) {
     BK_TRY(dmalloc(&d.Zc, es * ne * nx * P));
     BK_TRY(dmalloc(&d.HWc, es * ne * nu * P));
@@ -854,16 +884,18 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
   BK_TRY(dmalloc(&d.t1, es * (nx + nu) * P));
   BK_TRY(dmalloc(&d.t2, es * (nx + nu) * P));
   BK_TRY(dmalloc(&d.t3, es * (nx + nu) * P));
-  BK_TRY(dmalloc(&d.segb, sizeof(double) * (size_t)round_up(pr->nseg, 32) * nx));
-  BK_TRY(dmalloc(&d.grpb, sizeof(double) * (size_t)round_up(pr->ngrp, 32) * nx * 2));
-  BK_TRY(dmalloc(&d.sgbuf, sizeof(double) * (size_t)pr->nsg * nx * 2));
   return BK_OK;
 }
 
 static void free_opdata(OpData& d) {
   if (d.plan) plan_destroy(d.plan);
-  void* ps[] = {d.xu, d.mu, d.Kn, d.Nn, d.Aseg, d.Agrp, d.Asg, d.Zc, d.HWc, d.Qc, d.Sinv, d.t1, d.t2, d.t3, d.segb, d.grpb, d.sgbuf};
+  void* ps[] = {d.xu, d.mu, d.Kn, d.Nn, d.Zc, d.HWc, d.Qc, d.Sinv, d.t1, d.t2, d.t3};
   for (void* p : ps) dfree(p);
+  for (int l = 0; l < MAXLEV; ++l) {
+    dfree(d.lvm[l]);
+    dfree(d.lvo[l]);
+    dfree(d.lve[l]);
+  }
   d = OpData();
 }
 
@@ -873,12 +905,12 @@ static bk_status lin_factors(Problem* pr, OpData& d, const double* z, cudaStream
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   k_lin_nodes<T, KIND, NX, NU><<<nblk(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->d64.plan->w64, pr->s, (T*)d.Kn, (T*)d.Nn, (T*)d.xu);
   BK_CHECK_LAUNCH();
-  k_lin_seg<T, NX><<<(pr->nseg + 127) / 128, 128, 0, st>>>((const T*)d.Nn, pr->L, pr->nseg, (double*)d.Aseg);
+  k_lin_seg<T, NX><<<(pr->nseg + 127) / 128, 128, 0, st>>>((const T*)d.Nn, pr->L, pr->nseg, d.lvm[0]);
   BK_CHECK_LAUNCH();
-  k_lin_up<NX, true><<<(pr->ngrp + 127) / 128, 128, 0, st>>>((const double*)d.Aseg, pr->nseg, pr->ngrp, (double*)d.Agrp);
-  BK_CHECK_LAUNCH();
-  k_lin_up<NX, false><<<(pr->nsg + 127) / 128, 128, 0, st>>>((const double*)d.Agrp, pr->ngrp, pr->nsg, (double*)d.Asg);
-  BK_CHECK_LAUNCH();
+  for (int l = 0; l < pr->nlev; ++l) {
+    k_lin_level<NX><<<(pr->lvn[l] + 31) / 32, 32, 0, st>>>(d.lvm[l], pr->lvn[l], l + 1 < pr->nlev ? d.lvm[l + 1] : nullptr);
+    BK_CHECK_LAUNCH();
+  }
   return BK_OK;
 }
 
@@ -1205,8 +1237,12 @@ static bk_status problem_create(Problem** out, int kind, const double* params, i
     pr->has_cost = false;
   }
   pr->nseg = (int)((pr->L + SEG - 1) / SEG);
-  pr->ngrp = (pr->nseg + GRP - 1) / GRP;
-  pr->nsg = (pr->ngrp + 31) / 32;
+  pr->nlev = 1;
+  pr->lvn[0] = pr->nseg;
+  while (pr->lvn[pr->nlev - 1] > 32 && pr->nlev < MAXLEV) {
+    pr->lvn[pr->nlev] = (pr->lvn[pr->nlev - 1] + 31) / 32;
+    ++pr->nlev;
+  }
   AllocCounter counter(&pr->bytes);
   bk_status s = alloc_opdata(pr, pr->d64, BK_F64);
   if (s == BK_OK && dtype == BK_F32) s = alloc_opdata(pr, pr->d32, BK_F32);

@@ -18,7 +18,13 @@ constexpr int NEM = 4;   // largest terminal-condition count
 #define BK_SWEEP_SEG 16
 #endif
 constexpr int SEG = BK_SWEEP_SEG;  // nodes per sweep segment (one thread each)
-constexpr int GRP = 32;  // segments per sweep group
+// Scan levels of the preconditioner sweep: level 0 items are segments, level l + 1 items are
+// blocks of 32 level-l items, up to the first level with at most 32 items (N <= 2^24: 4 levels).
+constexpr int MAXLEV = 5;
+// Matrix slots stored per level item (FP64, 32-interleaved): the item's map A, the spans
+// M_k = product of the 2^k items ending at this one (k = 1..4, within its block of 32), and the
+// products of the items before (Pre) and after (Suf) it in its block.
+enum { SL_A = 0, SL_M1 = 1, SL_PRE = 5, SL_SUF = 6, NSLOT = 7 };
 
 // ---------------------------------------------------------------------------------------------
 // Dynamics of the compiled problem kinds (FP64 or FP32 arithmetic).
@@ -115,9 +121,9 @@ struct OpData {
   void* w = nullptr;           // Clenshaw-Curtis weights (L), working type
   void* Kn = nullptr;          // per-node K_k = (I - h_k J_k)^{-1}, interleaved (n_x^2 per node)
   void* Nn = nullptr;          // per-node N_k = 2 h_k J_k K_k, interleaved
-  void* Aseg = nullptr;        // segment aggregates of prod (I + N_k) (n_x^2 per segment)
-  void* Agrp = nullptr;        // group aggregates (n_x^2 per group, 32 segments each)
-  void* Asg = nullptr;         // supergroup aggregates (n_x^2 per supergroup, 32 groups each)
+  double* lvm[MAXLEV] = {};    // per level: NSLOT matrix slots (n_x^2 per item each), FP64
+  double* lvo[MAXLEV] = {};    // per level >= 1: item offsets from zero (n_x per item), per sweep
+  double* lve[MAXLEV] = {};    // per level: inclusive in-block scan values (n_x per item), per sweep
   // KKT preconditioner (terminal Schur data)
   void* Zc = nullptr;          // n_e state vectors   Z = P^{-T} E^T
   void* HWc = nullptr;         // n_e control vectors H~^{-1} W, W = Pu^T Z
@@ -127,9 +133,6 @@ struct OpData {
   void* t1 = nullptr;
   void* t2 = nullptr;
   void* t3 = nullptr;
-  void* segb = nullptr;        // per-segment affine offsets
-  void* grpb = nullptr;        // per-group affine offsets / incoming states
-  void* sgbuf = nullptr;       // per-supergroup offsets / incoming states
 };
 
 struct Problem {
@@ -142,7 +145,9 @@ struct Problem {
   int term_idx[NEM] = {0, 0, 0, 0};
   double term_val[NEM] = {0, 0, 0, 0};
   bool has_cost = true;
-  int nseg = 0, ngrp = 0, nsg = 0;
+  int nseg = 0;                // sweep segments (level-0 items)
+  int nlev = 0;                // scan levels; level nlev - 1 has at most 32 items
+  int lvn[MAXLEV] = {};        // items per level
   bool linearized = false;
   OpData d64;                  // FP64 operators (always)
   OpData d32;                  // FP32 operators (BK_F32 problems)
