@@ -150,7 +150,8 @@ enum { IN_PLAIN = 0, IN_WINV = 1, ST_FWD = 2, ST_TRN = 3 };
 // rk[k] = 1 / (4k) for 1 <= k <= N + 1 (plan table): the stencils multiply instead of divide.
 template <typename T>
 __device__ __forceinline__ T stencil_fwd(const T* __restrict__ Y, int m, int N, T invN, const T* __restrict__ rk) {
-  // g_m = chat'_m / 2 for 0 < m < N, g_N = chat'_N, g_0 = 0 (see the file comment)
+  // g_m = chat'_m / 2 for 0 < m < N, g_N = chat'_N, g_0 = 0 (see the file comment). invN is 1/N,
+  // or 1 where Y was stored already divided by N.
   if (m == 0) return T(0);
   if (m == N) return -Y[N - 1] * (invN * T(2) * rk[N]);
   if (m == 1) return (Y[2] - Y[0]) * (invN * T(0.25));
@@ -313,8 +314,8 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
     k_passA(const T* __restrict__ src, int64_t src_stride, typename V2<T>::t* __restrict__ Aout,
             T* __restrict__ partial, int N, int N1, int log2N1, int N2, int NB,
             const typename V2<T>::t* __restrict__ tw, int tw_log2,
-            const typename V2<T>::t* __restrict__ twN, const T* __restrict__ y0_partial,
-            int n_y0_partial, T invN, StencilTab<T> tb, const typename V2<T>::t* __restrict__ twLo,
+            const typename V2<T>::t* __restrict__ twN, T invN, StencilTab<T> tb,
+            const typename V2<T>::t* __restrict__ twLo,
             const typename V2<T>::t* __restrict__ twHi, int tw_h) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -328,24 +329,12 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
   const int vec = blockIdx.y;
   const T* x = src + (int64_t)vec * src_stride;
   const int c0 = blockIdx.x * NB;
-  T Y0 = T(0);
-  if (K == ST_TRN) {
-    // Y0 = DC of the first DCT = sum of the pass-A partials of that DCT
-    T acc = T(0);
-    const T* pp = y0_partial + (int64_t)vec * n_y0_partial;
-    for (int i = threadIdx.x; i < n_y0_partial; i += blockDim.x) acc += pp[i];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      T a = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (threadIdx.x == 0) red[0] = a;
-    }
-    __syncthreads();
-    Y0 = red[0];
-    __syncthreads();
-  }
+  // The stage buffer read by the second DCT already holds Y / N (forward) or Y - Y0
+  // (transpose), so its stencils run with scale 1 and Y0 = 0 (constants the compiler folds).
+  const T Y0 = T(0);
+  const T sc = K == ST_FWD ? T(1) : invN;
+  // DC partials: consumed after IN_WINV (the transposed stage) and ST_FWD (the forward output)
+  constexpr bool DC = K == IN_WINV || K == ST_FWD;
   T dc = T(0);
   const int total = NB * N1;
   // 4 independent element loads in flight per thread before the shared-memory stores
@@ -357,28 +346,29 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
       if (idx < total) {
         const int b = idx % NB;
         const int j = N2 * (idx / NB) + c0 + b;
-        z[u] = load_z<T, K>(x, j, N, invN, Y0, tb);
+        z[u] = load_z<T, K>(x, j, N, sc, Y0, tb);
       }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int idx = idx0 + u * blockDim.x;
       if (idx < total) {
-        dc += z[u].x + z[u].y;
+        if (DC) dc += z[u].x + z[u].y;
         buf[(idx % NB) * bs + padi(idx / NB)] = z[u];
       }
     }
   }
-  // block reduction of dc (deterministic order)
-  for (int o = 16; o > 0; o >>= 1) dc += __shfl_xor_sync(0xffffffffu, dc, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dc;
+  if (DC) {
+    // block reduction of dc (deterministic order)
+    for (int o = 16; o > 0; o >>= 1) dc += __shfl_xor_sync(0xffffffffu, dc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dc;
+  }
   __syncthreads();
-  if (threadIdx.x < 32) {
+  if (DC && threadIdx.x < 32) {
     T a = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (threadIdx.x == 0) partial[(int64_t)vec * gridDim.x + blockIdx.x] = a;
   }
-  __syncthreads();
   if (smem_tw)
     fft16<T>(buf, N1, log2N1, NB, bs, tws, log2N1);
   else
@@ -397,7 +387,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
 }
 
 // Epilogue kinds of pass B:
-//   EP_STORE     : stage[k] = Y_k                          (after the first DCT, forward)
+//   EP_STORE     : stage[k] = Y_k / N                      (after the first DCT, forward)
 //   EP_STORE_TRN : stage[k] = Y_k - Y0, Y0 from partials   (after the first DCT, transpose)
 //   EP_FWD_OUT   : out[k] = s (Y_k - Y0), Y0 from partials (after the second DCT, forward)
 //   EP_TRN_OUT   : out[k] = (s/N) W_k Y_k                   (after the second DCT, transpose)
@@ -405,7 +395,7 @@ enum { EP_STORE = 0, EP_STORE_TRN = 1, EP_FWD_OUT = 2, EP_TRN_OUT = 3 };
 
 template <typename T, int E>
 __device__ __forceinline__ void ep_write(T* __restrict__ dst, int k, T yk, int N, T s, T Y0, T invN) {
-  if (E == EP_STORE) dst[k] = yk;
+  if (E == EP_STORE) dst[k] = yk * invN;
   else if (E == EP_STORE_TRN) dst[k] = yk - Y0;
   else if (E == EP_FWD_OUT) dst[k] = s * (yk - Y0);
   else dst[k] = (k == 0 || k == N) ? s * invN * yk : T(2) * s * invN * yk;
@@ -792,21 +782,21 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
   const C* tp = (const C*)p->tpost;
   const int64_t Ls = N + 1;
   if (!trans) {
-    k_passA<T, IN_PLAIN><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    k_passA<T, IN_PLAIN><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
     k_passB<T, EP_STORE><<<gB, p->thrB, p->smemB, st>>>(A, Ystage, Ls, 0, nullptr, 0, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
     BK_CHECK_LAUNCH();
-    k_passA<T, ST_FWD><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    k_passA<T, ST_FWD><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
     k_passB<T, EP_FWD_OUT><<<gB, p->thrB, p->smemB, st>>>(A, out, p->pitch, p->pitch, pa2, nPA, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
     BK_CHECK_LAUNCH();
   } else {
-    k_passA<T, IN_WINV><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    k_passA<T, IN_WINV><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
     k_passB<T, EP_STORE_TRN><<<gB, p->thrB, p->smemB, st>>>(A, Ystage, Ls, 0, pa1, nPA, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
     BK_CHECK_LAUNCH();
     // the stage buffer already holds Y - Y0, so the transposed stencil runs with Y0 = 0
-    k_passA<T, ST_TRN><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, nullptr, 0, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    k_passA<T, ST_TRN><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
     k_passB<T, EP_TRN_OUT><<<gB, p->thrB, p->smemB, st>>>(A, out, p->pitch, p->pitch, nullptr, 0, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
     BK_CHECK_LAUNCH();

@@ -1,16 +1,18 @@
 // Right-preconditioned restarted GMRES (Algorithm 2 / FastLinSol of the paper: GMRES on
-// A P^{-1} Upsilon = beta, then chi = P^{-1} Upsilon), with classical Gram-Schmidt applied
-// twice (CGS2) for the Arnoldi basis. The flexible form is used: the preconditioned vectors
-// z_j = P^{-1} v_j are kept and the iterate is x = x0 + Z y, so the Arnoldi relation holds for
-// the z_j actually computed. A preconditioner applied in finite precision is linear only to its
-// rounding level; forming P^{-1}(V y) afterwards (the textbook right-preconditioned update)
-// would put that level under the attainable residual (measured: ~1e-4 in FP32 at N = 2^20).
+// A P^{-1} Upsilon = beta, then chi = P^{-1} Upsilon). The flexible form is used: the
+// preconditioned vectors z_j = P^{-1} v_j are kept and the iterate is x = x0 + Z y, so the
+// Arnoldi relation holds for the z_j actually computed. A preconditioner applied in finite
+// precision is linear only to its rounding level; forming P^{-1}(V y) afterwards (the textbook
+// right-preconditioned update) would put that level under the attainable residual (measured:
+// ~1e-4 in FP32 at N = 2^20).
 //
-// Device work per iteration: one preconditioner apply, one operator apply, two fused multi-dot
-// passes and two fused multi-axpy passes over the basis, and a norm. Dot products accumulate in
-// FP64 with a fixed block count and a fixed reduction order, so results do not depend on
-// scheduling. The (m+1) x m Hessenberg matrix and its Givens rotations live on the host
-// (FP64); the iteration reads back j+2 numbers per step.
+// Arnoldi orthogonalisation: classical Gram-Schmidt with the Daniel-Gragg-Kaufman-Stewart test.
+// One pass forms h = V^T w and |w|^2, the next w <- w - V h with |w|^2 of the result; a second
+// pass runs only when the norm fell below 1/sqrt 2 of its value (cancellation). The dot and
+// update passes are bound by FP64 FMA throughput (one FMA per 8-byte operand), so each skipped
+// pass counts. Dot products accumulate in FP64 with a fixed block count and reduction order, so
+// results do not depend on scheduling. The (m+1) x m Hessenberg matrix and its Givens rotations
+// live on the host (FP64); the iteration reads back j+3 numbers per step.
 #include <math.h>
 #include <string.h>
 
@@ -20,27 +22,43 @@
 
 namespace bk {
 
-static constexpr int DOT_BLOCKS = 296;   // 2 blocks per SM on 148+ SMs, fixed for determinism
+static constexpr int DOT_BLOCKS = 608;   // 4 blocks per SM on 152 SMs, fixed for determinism
 static constexpr int MAXM = 100;
 
-// partial[b * (nv) + i] = sum over block b's slice of V_i . w   (i < nv), FP64
+template <typename T, int CNT>
+__device__ __forceinline__ void dot_group(const T* __restrict__ V, int64_t ld, const T* __restrict__ w, int64_t lo,
+                                          int64_t hi, double* acc) {
+#pragma unroll 2
+  for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+    const double wk = (double)w[k];
+#pragma unroll
+    for (int q = 0; q < CNT; ++q) acc[q] += (double)V[(int64_t)q * ld + k] * wk;
+  }
+}
+
+// partial[b * nv + i] = sum over block b's slice of V_i . w   (i < nv), FP64
 template <typename T>
 __global__ void __launch_bounds__(256) k_multidot(const T* __restrict__ V, int64_t ld, int nv, const T* __restrict__ w,
                                                   int64_t n, double* __restrict__ partial) {
-  __shared__ double red[8][MAXM + 1];
+  __shared__ double red[8][8];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * chunk;
   const int64_t hi = lo + chunk < n ? lo + chunk : n;
   for (int i0 = 0; i0 < nv; i0 += 8) {
     const int cnt = nv - i0 < 8 ? nv - i0 : 8;
+    const T* Vg = V + (int64_t)i0 * ld;
     double acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-    for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-      const double wk = (double)w[k];
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q < cnt) acc[q] += (double)V[(int64_t)(i0 + q) * ld + k] * wk;
+    switch (cnt) {
+      case 1: dot_group<T, 1>(Vg, ld, w, lo, hi, acc); break;
+      case 2: dot_group<T, 2>(Vg, ld, w, lo, hi, acc); break;
+      case 3: dot_group<T, 3>(Vg, ld, w, lo, hi, acc); break;
+      case 4: dot_group<T, 4>(Vg, ld, w, lo, hi, acc); break;
+      case 5: dot_group<T, 5>(Vg, ld, w, lo, hi, acc); break;
+      case 6: dot_group<T, 6>(Vg, ld, w, lo, hi, acc); break;
+      case 7: dot_group<T, 7>(Vg, ld, w, lo, hi, acc); break;
+      default: dot_group<T, 8>(Vg, ld, w, lo, hi, acc); break;
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -74,14 +92,42 @@ __global__ void k_reduce_cols(const double* __restrict__ partial, int nb, int nv
   }
 }
 
-// w <- alpha * w + beta * sum_i c[i] V_i   (c on the device, FP64)
+// w <- alpha * w + cscale * sum_i c[i] V_i   (c on the device, FP64). With `partial` (grid of
+// DOT_BLOCKS blocks) each block also writes the sum of squares of its slice of the new w.
 template <typename T>
-__global__ void k_multiaxpy(const T* __restrict__ V, int64_t ld, int nv, const double* __restrict__ c, double cscale,
-                            T* __restrict__ w, double alpha, int64_t n) {
+__global__ void __launch_bounds__(256) k_multiaxpy(const T* __restrict__ V, int64_t ld, int nv,
+                                                   const double* __restrict__ c, double cscale, T* __restrict__ w,
+                                                   double alpha, int64_t n, double* __restrict__ partial) {
+  __shared__ double cs[MAXM + 1];
+  __shared__ double red[8];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = cscale * c[i];
+  __syncthreads();
+  double sq = 0.0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     double a = alpha == 0.0 ? 0.0 : alpha * (double)w[k];
-    for (int i = 0; i < nv; ++i) a += cscale * c[i] * (double)V[(int64_t)i * ld + k];
-    w[k] = (T)a;
+    int i = 0;
+    for (; i + 4 <= nv; i += 4) {
+      const double v0 = (double)V[(int64_t)i * ld + k], v1 = (double)V[(int64_t)(i + 1) * ld + k];
+      const double v2 = (double)V[(int64_t)(i + 2) * ld + k], v3 = (double)V[(int64_t)(i + 3) * ld + k];
+      a += cs[i] * v0;
+      a += cs[i + 1] * v1;
+      a += cs[i + 2] * v2;
+      a += cs[i + 3] * v3;
+    }
+    for (; i < nv; ++i) a += cs[i] * (double)V[(int64_t)i * ld + k];
+    const T r = (T)a;
+    w[k] = r;
+    sq += (double)r * (double)r;
+  }
+  if (partial) {
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int wp = 0; wp < (int)(blockDim.x >> 5); ++wp) t += red[wp];
+      partial[blockIdx.x] = t;
+    }
   }
 }
 
@@ -120,7 +166,7 @@ size_t gmres_workspace_bytes(int64_t n, int m, int dtype) {
   size_t b = es * (size_t)ld * (m + 1);      // basis V
   b += es * (size_t)ld * m;                  // preconditioned basis Z
   b += es * (size_t)ld * 2;                  // z scratch and r / correction
-  b += sizeof(double) * (size_t)DOT_BLOCKS * (MAXM + 1);  // dot partials
+  b += sizeof(double) * (size_t)DOT_BLOCKS * (MAXM + 2);  // dot partials
   b += sizeof(double) * 4 * (MAXM + 2);      // device scalars
   return b + 1024;
 }
@@ -137,7 +183,7 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
   T* Zb = (T*)carve(sizeof(T) * ld * m);
   T* z = (T*)carve(sizeof(T) * ld);
   T* r = (T*)carve(sizeof(T) * ld);
-  double* partial = (double*)carve(sizeof(double) * DOT_BLOCKS * (MAXM + 1));
+  double* partial = (double*)carve(sizeof(double) * DOT_BLOCKS * (MAXM + 2));
   double* dvec = (double*)carve(sizeof(double) * 4 * (MAXM + 2));
   double* h1 = dvec;
   double* h2 = dvec + (MAXM + 2);
@@ -192,19 +238,30 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
       } else {
         BK_TRY(op_apply(pr, d, op, vj, w, st));
       }
-      // CGS2
-      BK_TRY(dots<T>(V, ld, j + 1, w, n, partial, h1, st));
-      k_multiaxpy<T><<<g, 256, 0, st>>>(V, ld, j + 1, h1, -1.0, w, 1.0, n);
+      // Gram-Schmidt (DGKS): h1 = [V_0..V_j]^T w and |w|^2 (w = V_{j+1} follows V_j), then
+      // w <- w - V h1 with the new |w|^2; a second pass only on cancellation.
+      BK_TRY(dots<T>(V, ld, j + 2, w, n, partial, h1, st));
+      k_multiaxpy<T><<<DOT_BLOCKS, 256, 0, st>>>(V, ld, j + 1, h1, -1.0, w, 1.0, n, partial);
       BK_CHECK_LAUNCH();
-      BK_TRY(dots<T>(V, ld, j + 1, w, n, partial, h2, st));
-      k_multiaxpy<T><<<g, 256, 0, st>>>(V, ld, j + 1, h2, -1.0, w, 1.0, n);
+      k_reduce_cols<<<1, 256, 0, st>>>(partial, DOT_BLOCKS, 1, h2 + (MAXM + 1));
       BK_CHECK_LAUNCH();
-      BK_TRY(dots<T>(w, ld, 1, w, n, partial, h2 + (j + 1), st));
-      BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, st));
-      BK_TRY_CUDA(cudaMemcpyAsync(hostbuf + (MAXM + 2), h2, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, st));
+      BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, st));
+      BK_TRY_CUDA(cudaMemcpyAsync(hostbuf + (MAXM + 2), h2 + (MAXM + 1), sizeof(double), cudaMemcpyDeviceToHost, st));
       BK_TRY_CUDA(cudaStreamSynchronize(st));
-      const double hnext = sqrt(hostbuf[(MAXM + 2) + j + 1]);
-      for (int i = 0; i <= j; ++i) H[i * m + j] = hostbuf[i] + hostbuf[(MAXM + 2) + i];
+      double w2 = hostbuf[MAXM + 2];
+      for (int i = 0; i <= j; ++i) H[i * m + j] = hostbuf[i];
+      if (w2 < 0.5 * hostbuf[j + 1]) {
+        BK_TRY(dots<T>(V, ld, j + 1, w, n, partial, h2, st));
+        k_multiaxpy<T><<<DOT_BLOCKS, 256, 0, st>>>(V, ld, j + 1, h2, -1.0, w, 1.0, n, partial);
+        BK_CHECK_LAUNCH();
+        k_reduce_cols<<<1, 256, 0, st>>>(partial, DOT_BLOCKS, 1, h2 + (MAXM + 1));
+        BK_CHECK_LAUNCH();
+        BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h2, sizeof(double) * (MAXM + 2), cudaMemcpyDeviceToHost, st));
+        BK_TRY_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i <= j; ++i) H[i * m + j] += hostbuf[i];
+        w2 = hostbuf[MAXM + 1];
+      }
+      const double hnext = sqrt(w2);
       H[(j + 1) * m + j] = hnext;
       ++total;
       // normalise v_{j+1}
@@ -239,7 +296,7 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
     }
     BK_TRY_CUDA(cudaMemcpyAsync(yv, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st));
     // x += Z y (flexible form; Z = V without preconditioning)
-    k_multiaxpy<T><<<g, 256, 0, st>>>(o.use_precond ? Zb : V, ld, j, yv, 1.0, x, 1.0, n);
+    k_multiaxpy<T><<<g, 256, 0, st>>>(o.use_precond ? Zb : V, ld, j, yv, 1.0, x, 1.0, n, nullptr);
     BK_CHECK_LAUNCH();
     ++info->restarts;
     if (total >= o.max_iter) {
