@@ -362,30 +362,92 @@ __device__ __forceinline__ void warp_scan(const double* __restrict__ m, int64_t 
   }
 }
 
+// Per-node vectors of a warp's 32 segments move through shared memory in chunks of CH nodes
+// (one 32-byte sector per segment and component), so that every global access is sector-
+// coalesced: lane l of staging instruction q handles element q*32 + l of the [segment][node]
+// chunk. Reading them lane-by-segment directly (a 16-node stride) wasted most of each sector.
+template <typename T> struct SweepChunk {
+  static constexpr int CH = 32 / (int)sizeof(T);   // nodes per chunk
+  static constexpr int TS = CH + 1;                // padded row (bank spread)
+  static_assert(SEG % CH == 0, "segment length must be a multiple of the staging chunk");
+};
+
+template <typename T>
+__device__ __forceinline__ void stage_in(const T* __restrict__ src, int64_t P, int nc, int64_t L, int64_t seg0,
+                                         int i0, T* __restrict__ tile) {
+  constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS;
+  const int lane = threadIdx.x & 31;
+  for (int c = 0; c < nc; ++c) {
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int e = q * 32 + lane;
+      const int sl = e / CH, nd = e - (e / CH) * CH;
+      const int64_t k = (seg0 + sl) * SEG + i0 + nd;
+      tile[(c * 32 + sl) * TS + nd] = k < L ? src[c * P + k] : T(0);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_out(const T* __restrict__ tile, int nc, int64_t P, int64_t L, int64_t seg0,
+                                          int i0, T* __restrict__ dst) {
+  constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS;
+  const int lane = threadIdx.x & 31;
+  for (int c = 0; c < nc; ++c) {
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int e = q * 32 + lane;
+      const int sl = e / CH, nd = e - (e / CH) * CH;
+      const int64_t k = (seg0 + sl) * SEG + i0 + nd;
+      if (k < L) dst[c * P + k] = tile[(c * 32 + sl) * TS + nd];
+    }
+  }
+}
+
+// Shared tiles of one warp: A (n_x components), B (n_x components), W (1 component).
+template <typename T, int NX> struct SweepTiles {
+  static constexpr int ROWS = 32 * SweepChunk<T>::TS;
+  T a[NX * ROWS], b[NX * ROWS], w[ROWS];
+};
+
 // Up, level 0 (one warp per block of 32 segments, 4 warps per CTA): each lane runs its segment
 // from a zero state (the segment's offset), then the warp scans the block.
 template <typename T, int NX, int DIR>
 __global__ void __launch_bounds__(128) k_sw_up0(const T* __restrict__ Kn, const T* __restrict__ Nn,
                                                 const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
                                                 int64_t L, const T* __restrict__ w, T s, Levels lv) {
+  constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS;
+  __shared__ SweepTiles<T, NX> tiles[4];
   const int nblk = (lv.n[0] + 31) >> 5;
   const int g = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (g >= nblk) return;  // whole warps
+  SweepTiles<T, NX>& tl = tiles[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
-  const int64_t seg = (int64_t)g * 32 + lane;
+  const int64_t seg0 = (int64_t)g * 32;
+  const int64_t seg = seg0 + lane;
   T st[NX];
 #pragma unroll
   for (int m = 0; m < NX; ++m) st[m] = T(0);
-  if (seg < lv.n[0]) {
-    T dummy[2 * NX];
-    for (int ii = 0; ii < SEG; ++ii) {
-      const int i = DIR == 0 ? ii : SEG - 1 - ii;
-      const int64_t k = seg * SEG + i;
-      if (k >= L) { if (DIR == 0) break; else continue; }
-      T yin[NX], gin[NX];
+  for (int c = 0; c < SEG / CH; ++c) {
+    const int i0 = (DIR == 0 ? c : SEG / CH - 1 - c) * CH;
+    __syncwarp();
+    stage_in<T>(Y, P, NX, L, seg0, i0, tl.a);
+    if (G) stage_in<T>(G, P, NX, L, seg0, i0, tl.b);
+    stage_in<T>(w, P, 1, L, seg0, i0, tl.w);
+    __syncwarp();
 #pragma unroll
-      for (int m = 0; m < NX; ++m) { yin[m] = Y[m * P + k]; gin[m] = G ? G[m * P + k] : T(0); }
-      node_step<T, NX, DIR>(Kn, Nn, k, yin, gin, T(0.5) * s * w[k], st, dummy, false);
+    for (int jj = 0; jj < CH; ++jj) {
+      const int nd = DIR == 0 ? jj : CH - 1 - jj;
+      const int64_t k = seg * SEG + i0 + nd;
+      if (seg < lv.n[0] && k < L) {
+        T yin[NX], gin[NX], dummy[2 * NX];
+#pragma unroll
+        for (int m = 0; m < NX; ++m) {
+          yin[m] = tl.a[(m * 32 + lane) * TS + nd];
+          gin[m] = G ? tl.b[(m * 32 + lane) * TS + nd] : T(0);
+        }
+        node_step<T, NX, DIR>(Kn, Nn, k, yin, gin, T(0.5) * s * tl.w[lane * TS + nd], st, dummy, false);
+      }
     }
   }
   double e[NX];
@@ -425,22 +487,27 @@ __global__ void __launch_bounds__(128) k_sw_upL(Levels lv, int l) {
 }
 
 // Down (one warp per block of 32 segments): incoming state of the lane's segment, composed from
-// the top level down, then the segment's nodes with outputs.
+// the top level down, then the segment's nodes with outputs (staged like the inputs).
 template <typename T, int NX, int DIR>
 __global__ void __launch_bounds__(128) k_sw_down0(const T* __restrict__ Kn, const T* __restrict__ Nn,
                                                   const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
                                                   int64_t L, const T* __restrict__ w, T s, Levels lv,
                                                   T* __restrict__ out, T* __restrict__ bout) {
   constexpr int NC = NX * NX;
+  constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS;
+  __shared__ SweepTiles<T, NX> tiles[4];
   const int nblk0 = (lv.n[0] + 31) >> 5;
   const int g = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (g >= nblk0) return;
-  const int64_t seg = (int64_t)g * 32 + (threadIdx.x & 31);
-  if (seg >= lv.n[0]) return;
+  if (g >= nblk0) return;  // whole warps
+  SweepTiles<T, NX>& tl = tiles[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int64_t seg0 = (int64_t)g * 32;
+  const int64_t seg = seg0 + lane;
+  const bool live = seg < lv.n[0];
   double S[NX];
 #pragma unroll
   for (int m = 0; m < NX; ++m) S[m] = 0.0;
-  for (int l = lv.nlev - 1; l >= 0; --l) {
+  for (int l = lv.nlev - 1; l >= 0 && live; --l) {
     const int64_t i = seg >> (5 * l);
     const int q = (int)(i & 31);
     if (DIR == 0 ? q == 0 : q == 31) continue;  // first item of its block in sweep order
@@ -464,21 +531,39 @@ __global__ void __launch_bounds__(128) k_sw_down0(const T* __restrict__ Kn, cons
   T st[NX];
 #pragma unroll
   for (int m = 0; m < NX; ++m) st[m] = (T)S[m];
-  for (int ii = 0; ii < SEG; ++ii) {
-    const int i = DIR == 0 ? ii : SEG - 1 - ii;
-    const int64_t k = seg * SEG + i;
-    if (k >= L) { if (DIR == 0) break; else continue; }
-    T yin[NX], gin[NX], o[2 * NX];
+  const bool wantb = DIR == 1 && bout != nullptr;
+  for (int c = 0; c < SEG / CH; ++c) {
+    const int i0 = (DIR == 0 ? c : SEG / CH - 1 - c) * CH;
+    __syncwarp();
+    stage_in<T>(Y, P, NX, L, seg0, i0, tl.a);
+    if (DIR == 0 && G) stage_in<T>(G, P, NX, L, seg0, i0, tl.b);
+    stage_in<T>(w, P, 1, L, seg0, i0, tl.w);
+    __syncwarp();
 #pragma unroll
-    for (int m = 0; m < NX; ++m) { yin[m] = Y[m * P + k]; gin[m] = G ? G[m * P + k] : T(0); }
-    const T wk = w[k];
-    node_step<T, NX, DIR>(Kn, Nn, k, yin, gin, T(0.5) * s * wk, st, o, true);
+    for (int jj = 0; jj < CH; ++jj) {
+      const int nd = DIR == 0 ? jj : CH - 1 - jj;
+      const int64_t k = seg * SEG + i0 + nd;
+      if (live && k < L) {
+        T yin[NX], gin[NX], o[2 * NX];
 #pragma unroll
-    for (int m = 0; m < NX; ++m) out[m * P + k] = o[m];
-    if (DIR == 1 && bout) {
+        for (int m = 0; m < NX; ++m) {
+          yin[m] = tl.a[(m * 32 + lane) * TS + nd];
+          gin[m] = (DIR == 0 && G) ? tl.b[(m * 32 + lane) * TS + nd] : T(0);
+        }
+        const T wk = tl.w[lane * TS + nd];
+        node_step<T, NX, DIR>(Kn, Nn, k, yin, gin, T(0.5) * s * wk, st, o, true);
+        // outputs replace the inputs just read (same lane, same node)
 #pragma unroll
-      for (int m = 0; m < NX; ++m) bout[m * P + k] = wk * o[NX + m];
+        for (int m = 0; m < NX; ++m) tl.a[(m * 32 + lane) * TS + nd] = o[m];
+        if (wantb) {
+#pragma unroll
+          for (int m = 0; m < NX; ++m) tl.b[(m * 32 + lane) * TS + nd] = wk * o[NX + m];
+        }
+      }
     }
+    __syncwarp();
+    stage_out<T>(tl.a, NX, P, L, seg0, i0, out);
+    if (wantb) stage_out<T>(tl.b, NX, P, L, seg0, i0, bout);
   }
 }
 
@@ -490,6 +575,23 @@ __global__ void k_zero_pad(T* __restrict__ v, int nblocks, int64_t P, int64_t L)
     const int64_t b = i / padn;
     v[b * P + L + (i - b * padn)] = T(0);
   }
+}
+
+// The sweep kernels keep up to four 4-warp CTAs per SM; give shared memory the whole L1 array.
+template <typename T, int NX>
+static bk_status sweep_attrs() {
+  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_up0<T, NX, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_up0<T, NX, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_down0<T, NX, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_down0<T, NX, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  return BK_OK;
+}
+
+template <typename T>
+static bk_status sweep_attrs_nx(int nx) {
+  if (nx == 1) return sweep_attrs<T, 1>();
+  if (nx == 2) return sweep_attrs<T, 2>();
+  return sweep_attrs<T, 4>();
 }
 
 static Levels levels_of(const Problem* pr, const OpData& d) {
@@ -858,6 +960,7 @@ template <int KIND> struct KindNX { static constexpr int nx = Dyn<KIND>::nx, nu 
 
 static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
   d.dtype = dtype;
+  BK_TRY(dtype == BK_F64 ? sweep_attrs_nx<double>(pr->n_x) : sweep_attrs_nx<float>(pr->n_x));
   const size_t es = dtype_size(dtype);
   const int64_t P = pr->P;
   const int nx = pr->n_x, nu = pr->n_u, ne = pr->n_e;
