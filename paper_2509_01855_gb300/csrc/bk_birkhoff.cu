@@ -118,6 +118,21 @@ __global__ void k_post_table(typename V2<T>::t* tp, int64_t N) {
   }
 }
 
+// Stage twiddle table of a length-2^log2n FFT (see bk_fft.cuh): entry off + (r-1) Ns + k of the
+// block of the stage with Ns = 2^l is omega_{16 Ns}^{r k}, from sincospi(2 r k / (16 Ns)).
+template <typename T>
+__global__ void k_stage_tw(typename V2<T>::t* stw, int log2n, int len) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < len; idx += gridDim.x * blockDim.x) {
+    int l = (log2n & 3) ? (log2n & 3) : 4, off = 0;
+    while (idx >= off + (15 << l)) { off += 15 << l; l += 4; }
+    const int e = idx - off;
+    const int r = (e >> l) + 1, k = e & ((1 << l) - 1);
+    double sn, cs;
+    sincospi((double)(2 * r * k) / (double)(16 << l), &sn, &cs);
+    stw[idx] = mk2<T>((T)cs, (T)(-sn));
+  }
+}
+
 // rk[k] = 1 / (4k), k >= 1 (rk[0] = 0), rounded once from FP64.
 template <typename T>
 __global__ void k_rk_table(T* rk, int64_t n) {
@@ -226,7 +241,7 @@ __device__ __forceinline__ void split_pair(typename V2<T>::t zk, typename V2<T>:
 template <typename T>
 __device__ void dct1_block(const T* __restrict__ X, int kind, T* __restrict__ Y,
                            typename V2<T>::t* buf, int N, int log2N,
-                           const typename V2<T>::t* __restrict__ tw, int tw_log2,
+                           const typename V2<T>::t* __restrict__ tw, const typename V2<T>::t* __restrict__ stw,
                            const typename V2<T>::t* __restrict__ tpost, T invN, T Y0, StencilTab<T> tb) {
   typedef typename V2<T>::t C;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
@@ -241,7 +256,7 @@ __device__ void dct1_block(const T* __restrict__ X, int kind, T* __restrict__ Y,
   }
   __syncthreads();
   if (N >= 16) {
-    fft16<T>(buf, N, log2N, 1, pad_stride(N), tw, tw_log2);
+    fft16<T>(buf, N, log2N, 1, pad_stride(N), stw);
   } else {
     // N = 4 or 8: direct DFT (tw holds omega_N^i, n_tab = N)
     C zk = mk2<T>(T(0), T(0));
@@ -271,7 +286,7 @@ template <typename T> struct MaxThr { static constexpr int v = sizeof(T) == 8 ? 
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(MaxThr<T>::v)
     k_birkhoff_small(const T* __restrict__ in, T* __restrict__ out, int N, int log2N, int64_t pitch,
-                     T s, const typename V2<T>::t* __restrict__ tw, int tw_log2,
+                     T s, const typename V2<T>::t* __restrict__ tw, const typename V2<T>::t* __restrict__ stw,
                      const typename V2<T>::t* __restrict__ tpost, StencilTab<T> tb) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -287,14 +302,14 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
   for (int m = threadIdx.x; m < L; m += blockDim.x) X[m] = src[m];
   __syncthreads();
   if (!TRANS) {
-    dct1_block<T>(X, IN_PLAIN, Y, buf, N, log2N, tw, tw_log2, tpost, invN, T(0), tb);
-    dct1_block<T>(Y, ST_FWD, X, buf, N, log2N, tw, tw_log2, tpost, invN, T(0), tb);
+    dct1_block<T>(X, IN_PLAIN, Y, buf, N, log2N, tw, stw, tpost, invN, T(0), tb);
+    dct1_block<T>(Y, ST_FWD, X, buf, N, log2N, tw, stw, tpost, invN, T(0), tb);
     const T y0 = X[0];
     for (int m = threadIdx.x; m < L; m += blockDim.x) dst[m] = s * (X[m] - y0);
   } else {
-    dct1_block<T>(X, IN_WINV, Y, buf, N, log2N, tw, tw_log2, tpost, invN, T(0), tb);
+    dct1_block<T>(X, IN_WINV, Y, buf, N, log2N, tw, stw, tpost, invN, T(0), tb);
     const T y0 = Y[0];
-    dct1_block<T>(Y, ST_TRN, X, buf, N, log2N, tw, tw_log2, tpost, invN, y0, tb);
+    dct1_block<T>(Y, ST_TRN, X, buf, N, log2N, tw, stw, tpost, invN, y0, tb);
     const T sN = s * invN;
     for (int m = threadIdx.x; m < L; m += blockDim.x)
       dst[m] = (m == 0 || m == N) ? sN * X[m] : T(2) * sN * X[m];
@@ -312,23 +327,23 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
 template <typename T, int K>
 __global__ void __launch_bounds__(MaxThr<T>::v)
     k_passA(const T* __restrict__ src, int64_t src_stride, typename V2<T>::t* __restrict__ Aout,
-            T* __restrict__ partial, int N, int N1, int log2N1, int N2, int NB,
-            const typename V2<T>::t* __restrict__ tw, int tw_log2,
+            T* __restrict__ partial, int N, int N1, int log2N1, int N2, int NB, int bs,
+            const typename V2<T>::t* __restrict__ stw,
             const typename V2<T>::t* __restrict__ twN, T invN, StencilTab<T> tb,
             const typename V2<T>::t* __restrict__ twLo,
             const typename V2<T>::t* __restrict__ twHi, int tw_h) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int bs = pad_stride(N1);
   C* buf = reinterpret_cast<C*>(smem);
   // FP32: sub-FFT twiddles in shared memory after the tile (FP64 reads the global table)
   C* tws = buf + (size_t)NB * bs;
   const bool smem_tw = sizeof(T) == 4;
-  if (smem_tw) load_tw_smem<T>(tws, tw, N1, log2N1, tw_log2);
+  if (smem_tw) load_tw_smem<T>(tws, stw, stage_tw_len(log2N1));
   __shared__ T red[32];
   const int vec = blockIdx.y;
   const T* x = src + (int64_t)vec * src_stride;
   const int c0 = blockIdx.x * NB;
+  const int log2NB = __ffs(NB) - 1, log2N2 = __ffs(N2) - 1;  // NB, N2 are powers of two
   // The stage buffer read by the second DCT already holds Y / N (forward) or Y - Y0
   // (transpose), so its stencils run with scale 1 and Y0 = 0 (constants the compiler folds).
   const T Y0 = T(0);
@@ -344,8 +359,8 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
     for (int u = 0; u < 4; ++u) {
       const int idx = idx0 + u * blockDim.x;
       if (idx < total) {
-        const int b = idx % NB;
-        const int j = N2 * (idx / NB) + c0 + b;
+        const int b = idx & (NB - 1);
+        const int j = ((idx >> log2NB) << log2N2) + c0 + b;
         z[u] = load_z<T, K>(x, j, N, sc, Y0, tb);
       }
     }
@@ -354,7 +369,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
       const int idx = idx0 + u * blockDim.x;
       if (idx < total) {
         if (DC) dc += z[u].x + z[u].y;
-        buf[(idx % NB) * bs + padi(idx / NB)] = z[u];
+        buf[(idx & (NB - 1)) * bs + padi(idx >> log2NB)] = z[u];
       }
     }
   }
@@ -369,14 +384,11 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (threadIdx.x == 0) partial[(int64_t)vec * gridDim.x + blockIdx.x] = a;
   }
-  if (smem_tw)
-    fft16<T>(buf, N1, log2N1, NB, bs, tws, log2N1);
-  else
-    fft16<T>(buf, N1, log2N1, NB, bs, tw, tw_log2);
+  fft16<T>(buf, N1, log2N1, NB, bs, smem_tw ? tws : stw);
   C* A = Aout + (int64_t)vec * N;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int b = idx % NB;
-    const int k1 = idx / NB;
+    const int b = idx & (NB - 1);
+    const int k1 = idx >> log2NB;
     const int j2 = c0 + b;
     const int m = j2 * k1;  // < N
     // FP64: one table of omega_N^m (the FP64 pipe, not memory, bounds these kernels).
@@ -405,7 +417,7 @@ template <typename T, int E>
 __global__ void __launch_bounds__(MaxThr<T>::v)
     k_passB(const typename V2<T>::t* __restrict__ Ain, T* __restrict__ dst, int64_t dst_stride,
             int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial, int N, int N1,
-            int N2, int log2N2, int P, const typename V2<T>::t* __restrict__ tw, int tw_log2,
+            int N2, int log2N2, int P, const typename V2<T>::t* __restrict__ stw,
             const typename V2<T>::t* __restrict__ tpost, T s, T invN) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -413,7 +425,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
   C* buf = reinterpret_cast<C*>(smem);
   C* tws = buf + (size_t)2 * P * bs;
   const bool smem_tw = sizeof(T) == 4;
-  if (smem_tw) load_tw_smem<T>(tws, tw, N2, log2N2, tw_log2);
+  if (smem_tw) load_tw_smem<T>(tws, stw, stage_tw_len(log2N2));
   __shared__ T red[32];
   const int vec = blockIdx.y;
   const C* A = Ain + (int64_t)vec * N;
@@ -443,30 +455,27 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
     for (int u = 0; u < 4; ++u) {
       const int idx = idx0 + u * blockDim.x;
       if (idx < total) {
-        const int q = idx / N2;
+        const int q = idx >> log2N2;
         const int p = p0 + (q >> 1);
         const int row = (q & 1) == 0 ? p : (p == 0 ? N1 / 2 : N1 - p);
-        z[u] = A[(int64_t)row * N2 + (idx - q * N2)];
+        z[u] = A[((int64_t)row << log2N2) + (idx & (N2 - 1))];
       }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int idx = idx0 + u * blockDim.x;
       if (idx < total) {
-        const int q = idx / N2;
-        buf[q * bs + padi(idx - q * N2)] = z[u];
+        const int q = idx >> log2N2;
+        buf[q * bs + padi(idx & (N2 - 1))] = z[u];
       }
     }
   }
   __syncthreads();
-  if (smem_tw)
-    fft16<T>(buf, N2, log2N2, 2 * P, bs, tws, log2N2);
-  else
-    fft16<T>(buf, N2, log2N2, 2 * P, bs, tw, tw_log2);
+  fft16<T>(buf, N2, log2N2, 2 * P, bs, smem_tw ? tws : stw);
   const int half = N / 2;
   for (int idx = threadIdx.x; idx < P * N2; idx += blockDim.x) {
-    const int i = idx / N2;
-    const int k2 = idx - i * N2;
+    const int i = idx >> log2N2;
+    const int k2 = idx & (N2 - 1);
     const int p = p0 + i;
     const C* ra = buf + (2 * i) * bs;
     const C* rb = buf + (2 * i + 1) * bs;
@@ -513,13 +522,25 @@ template <typename T>
 static bk_status build_tables(Plan* p, cudaStream_t st) {
   typedef typename V2<T>::t C;
   const int64_t N = p->N;
-  // sub-FFT twiddle table: length n_tab = max FFT length run in shared memory
-  const int64_t ntab = p->small ? N : (int64_t)std::max(p->N1, p->N2);
-  p->tw_log2 = ilog2(ntab);
-  BK_TRY(dmalloc(&p->tw, sizeof(C) * ntab));
-  k_tw_table<T><<<(int)std::min<int64_t>((ntab + 255) / 256, 4096), 256, 0, st>>>(
-      (C*)p->tw, ntab, (double)ntab);
-  BK_CHECK_LAUNCH();
+  // FFT twiddles: single-CTA plans keep omega_N^i (direct DFT for N < 16) and the stage table of
+  // N; four-step plans the stage tables of N1 and N2.
+  auto stage_table = [&](void** dst, int64_t n) -> bk_status {
+    const int len = stage_tw_len(ilog2(n));
+    if (len == 0) return BK_OK;
+    BK_TRY(dmalloc(dst, sizeof(C) * len));
+    k_stage_tw<T><<<(len + 255) / 256, 256, 0, st>>>((C*)*dst, ilog2(n), len);
+    BK_CHECK_LAUNCH();
+    return BK_OK;
+  };
+  if (p->small) {
+    BK_TRY(dmalloc(&p->tw, sizeof(C) * N));
+    k_tw_table<T><<<(int)std::min<int64_t>((N + 255) / 256, 4096), 256, 0, st>>>((C*)p->tw, N, (double)N);
+    BK_CHECK_LAUNCH();
+    if (N >= 16) BK_TRY(stage_table(&p->stw1, N));
+  } else {
+    BK_TRY(stage_table(&p->stw1, p->N1));
+    BK_TRY(stage_table(&p->stw2, p->N2));
+  }
   BK_TRY(dmalloc(&p->rk, sizeof(T) * (N + 2)));
   k_rk_table<T><<<(int)std::min<int64_t>((N + 2 + 255) / 256, 4096), 256, 0, st>>>((T*)p->rk, N + 2);
   BK_CHECK_LAUNCH();
@@ -627,7 +648,14 @@ static bk_status configure_fourstep(Plan* p) {
   if (P > p->N1 / 2) P = p->N1 / 2;
   p->NB = NB;
   p->P = P;
-  p->smemA = csz * ((size_t)NB * pad_stride(p->N1) + (p->dtype == BK_F32 ? p->N1 : 0));
+  // Pass-A batch stride: when a warp's FFT stays inside one batch (N1 / 16 >= 32 threads), the
+  // column-major tile accesses of the load and store phases (lane -> column idx mod NB, row
+  // idx / NB) hit distinct banks if the stride is = W / NB modulo the W complex elements of a
+  // 128-byte wavefront.
+  const int W = (int)(128 / csz);
+  const int padA = (p->N1 / 16 >= 32 && NB < W) ? W / NB : 1;
+  p->bsA = p->N1 + p->N1 / 16 + padA;
+  p->smemA = csz * ((size_t)NB * p->bsA + (p->dtype == BK_F32 ? p->N1 : 0));
   p->smemB = csz * ((size_t)2 * P * pad_stride(p->N2) + (p->dtype == BK_F32 ? p->N2 : 0));
   p->thrA = round_threads((int64_t)NB * p->N1 / 16);
   p->thrB = round_threads((int64_t)2 * P * p->N2 / 16);
@@ -738,6 +766,8 @@ void plan_destroy(Plan* p) {
   dfree(p->w64);
   dfree(p->wT);
   dfree(p->tw);
+  dfree(p->stw1);
+  dfree(p->stw2);
   dfree(p->tpost);
   dfree(p->rk);
   dfree(p->twN);
@@ -763,9 +793,9 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
   tb.cN = (T)(1.0 / (4.0 * ((double)N * (double)N - 1.0)));
   if (p->small) {
     if (!trans)
-      k_birkhoff_small<T, false><<<nvec, p->thrS, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, p->tw_log2, (const C*)p->tpost, tb);
+      k_birkhoff_small<T, false><<<nvec, p->thrS, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, (const C*)p->stw1, (const C*)p->tpost, tb);
     else
-      k_birkhoff_small<T, true><<<nvec, p->thrS, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, p->tw_log2, (const C*)p->tpost, tb);
+      k_birkhoff_small<T, true><<<nvec, p->thrS, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, (const C*)p->stw1, (const C*)p->tpost, tb);
     BK_CHECK_LAUNCH();
     return BK_OK;
   }
@@ -777,28 +807,30 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
   T* pa2 = (T*)part2;
   const int nPA = p->nPartA;
   dim3 gA(N2 / NB, nvec), gB(N1 / 2 / P, nvec);
-  const C* tw = (const C*)p->tw;
+  const C* stw1 = (const C*)p->stw1;
+  const C* stw2 = (const C*)p->stw2;
+  const int bsA = p->bsA;
   const C* twN = (const C*)p->twN;
   const C* tp = (const C*)p->tpost;
   const int64_t Ls = N + 1;
   if (!trans) {
-    k_passA<T, IN_PLAIN><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    k_passA<T, IN_PLAIN><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
-    k_passB<T, EP_STORE><<<gB, p->thrB, p->smemB, st>>>(A, Ystage, Ls, 0, nullptr, 0, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
+    k_passB<T, EP_STORE><<<gB, p->thrB, p->smemB, st>>>(A, Ystage, Ls, 0, nullptr, 0, N, N1, N2, log2N2, P, stw2, tp, s, invN);
     BK_CHECK_LAUNCH();
-    k_passA<T, ST_FWD><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    k_passA<T, ST_FWD><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
-    k_passB<T, EP_FWD_OUT><<<gB, p->thrB, p->smemB, st>>>(A, out, p->pitch, p->pitch, pa2, nPA, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
+    k_passB<T, EP_FWD_OUT><<<gB, p->thrB, p->smemB, st>>>(A, out, p->pitch, p->pitch, pa2, nPA, N, N1, N2, log2N2, P, stw2, tp, s, invN);
     BK_CHECK_LAUNCH();
   } else {
-    k_passA<T, IN_WINV><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    k_passA<T, IN_WINV><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
-    k_passB<T, EP_STORE_TRN><<<gB, p->thrB, p->smemB, st>>>(A, Ystage, Ls, 0, pa1, nPA, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
+    k_passB<T, EP_STORE_TRN><<<gB, p->thrB, p->smemB, st>>>(A, Ystage, Ls, 0, pa1, nPA, N, N1, N2, log2N2, P, stw2, tp, s, invN);
     BK_CHECK_LAUNCH();
     // the stage buffer already holds Y - Y0, so the transposed stencil runs with Y0 = 0
-    k_passA<T, ST_TRN><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, tw, p->tw_log2, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    k_passA<T, ST_TRN><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
-    k_passB<T, EP_TRN_OUT><<<gB, p->thrB, p->smemB, st>>>(A, out, p->pitch, p->pitch, nullptr, 0, N, N1, N2, log2N2, P, tw, p->tw_log2, tp, s, invN);
+    k_passB<T, EP_TRN_OUT><<<gB, p->thrB, p->smemB, st>>>(A, out, p->pitch, p->pitch, nullptr, 0, N, N1, N2, log2N2, P, stw2, tp, s, invN);
     BK_CHECK_LAUNCH();
   }
   return BK_OK;
@@ -843,10 +875,10 @@ static std::mutex g_noalloc_mu;
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 // Bytes of the scratch layout for N (FP64) and nvec vectors, and the sub-buffer offsets.
-static size_t noalloc_layout(const Plan& p, int nvec, size_t off[8]) {
+static size_t noalloc_layout(const Plan& p, int nvec, size_t off[9]) {
   const int64_t N = p.N;
   size_t o = 0;
-  off[0] = o; o += align256(sizeof(double2) * std::max(p.N1, p.N2));                  // tw
+  off[0] = o; o += align256(sizeof(double2) * stage_tw_len(ilog2(p.N1)));             // stw1
   off[1] = o; o += align256(sizeof(double2) * (N / 2 + 1));                           // tpost
   off[2] = o; o += align256(sizeof(double2) * N);                                     // twN
   off[3] = o; o += align256(sizeof(double2) * (size_t)N * nvec);                      // scrA
@@ -854,6 +886,7 @@ static size_t noalloc_layout(const Plan& p, int nvec, size_t off[8]) {
   off[5] = o; o += align256(sizeof(double) * (size_t)p.nPartA * nvec);                // part1
   off[6] = o; o += align256(sizeof(double) * (size_t)p.nPartA * nvec);                // part2
   off[7] = o; o += align256(sizeof(double) * (size_t)(N + 2));                        // rk
+  off[8] = o; o += align256(sizeof(double2) * stage_tw_len(ilog2(p.N2)));             // stw2
   return o;
 }
 
@@ -898,23 +931,25 @@ bk_status noalloc_apply(const double* v, double* out, int64_t N, int nvec, int64
   p.s = 0.5 * (tf - t0);
   p.small = false;
   BK_TRY(configure_fourstep(&p));
-  size_t off[8];
+  size_t off[9];
   const size_t need = noalloc_layout(p, nvec, off);
   BK_ARG(need <= NOALLOC_BYTES, "N=%lld with %d vectors needs %zu bytes of scratch, more than the %zu reserved",
          (long long)N, nvec, need, NOALLOC_BYTES);
   void* base = nullptr;
   BK_TRY(noalloc_setup(dev, &base));
   unsigned char* b = (unsigned char*)base;
-  const int64_t ntab = std::max(p.N1, p.N2);
-  p.tw_log2 = ilog2(ntab);
-  p.tw = b + off[0];
+  p.stw1 = b + off[0];
+  p.stw2 = b + off[8];
   p.tpost = b + off[1];
   p.twN = b + off[2];
   p.rk = b + off[7];
   // every table is rewritten by each call: nothing in the array has to start at zero
   k_rk_table<double><<<(int)std::min<int64_t>((N + 2 + 255) / 256, 4096), 256, 0, st>>>((double*)p.rk, N + 2);
   BK_CHECK_LAUNCH();
-  k_tw_table<double><<<(int)std::min<int64_t>((ntab + 255) / 256, 4096), 256, 0, st>>>((double2*)p.tw, ntab, (double)ntab);
+  const int len1 = stage_tw_len(ilog2(p.N1)), len2 = stage_tw_len(ilog2(p.N2));
+  k_stage_tw<double><<<(len1 + 255) / 256, 256, 0, st>>>((double2*)p.stw1, ilog2(p.N1), len1);
+  BK_CHECK_LAUNCH();
+  k_stage_tw<double><<<(len2 + 255) / 256, 256, 0, st>>>((double2*)p.stw2, ilog2(p.N2), len2);
   BK_CHECK_LAUNCH();
   k_post_table<double><<<(int)std::min<int64_t>((N / 2 + 256) / 256, 4096), 256, 0, st>>>((double2*)p.tpost, N);
   BK_CHECK_LAUNCH();

@@ -7,9 +7,12 @@
 // compute, write, barrier. Shared addresses are padded, a -> a + a/16, which makes the Stockham
 // writes conflict-free for 8- and 16-byte complex values; batches sit bs >= n + n/16 + 1 apart.
 //
-// Twiddles come from a table tw[i] = (cos(2 pi i / n_tab), -sin(2 pi i / n_tab)), i < n_tab,
-// n_tab = 2^tw_log2 >= n, built on the device with sincospi at plan creation; the table may be
-// the global one or a copy in shared memory (load_tw_smem).
+// Twiddles come from a per-size stage table built on the device with sincospi at plan creation:
+// for each radix-16 stage with Ns > 1 (in stage order) a block stw[off + (r - 1) Ns + k] =
+// omega_{16 Ns}^{r k}, r = 1..15, k < Ns. Lanes hold consecutive k, so a warp reads consecutive
+// entries: no shared-memory bank conflicts, coalesced global loads. (Indexing one table of
+// omega_n^i by r k instead gave stride-r lane patterns, up to 16-way conflicts.) The table may
+// be the global one or a copy in shared memory (load_tw_smem).
 #pragma once
 
 #include "bk_common.cuh"
@@ -18,6 +21,13 @@ namespace bk {
 
 __device__ __forceinline__ int padi(int a) { return a + (a >> 4); }
 __host__ __device__ inline int pad_stride(int n) { return n + (n >> 4) + 1; }
+
+// Entries of the stage twiddle table of a length-2^log2n FFT (radix-16 stages with Ns > 1).
+__host__ __device__ inline int stage_tw_len(int log2n) {
+  int len = 0;
+  for (int l = (log2n & 3) ? (log2n & 3) : 4; l < log2n; l += 4) len += 15 << l;
+  return len;
+}
 
 // Radix-R DFT of v[0..R-1] in registers (forward, natural order in and out).
 template <typename C, typename T, int R> struct Radix;
@@ -107,8 +117,7 @@ template <typename C, typename T> struct Radix<C, T, 16> {
 // radices. Threads t < nbatch * n/16 work; all threads must reach the barriers.
 template <typename T, int R>
 __device__ __forceinline__ void stage16(typename V2<T>::t* __restrict__ buf, int n, int log2n, int nbatch,
-                                        int bs, int Ns, int log2Ns,
-                                        const typename V2<T>::t* __restrict__ tw, int tw_log2) {
+                                        int bs, int Ns, int log2Ns, const typename V2<T>::t* __restrict__ stw) {
   typedef typename V2<T>::t C;
   constexpr int log2R = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
   constexpr int PER = 16 / R;
@@ -131,7 +140,6 @@ __device__ __forceinline__ void stage16(typename V2<T>::t* __restrict__ buf, int
   }
   __syncthreads();
   if (active) {
-    const int tw_shift = tw_log2 - (log2Ns + log2R);
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int j = tt + q * nb16;
@@ -139,7 +147,7 @@ __device__ __forceinline__ void stage16(typename V2<T>::t* __restrict__ buf, int
       C* u = v + q * R;
       if (Ns > 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw[(r * k) << tw_shift]);
+        for (int r = 1; r < R; ++r) u[r] = cmul(u[r], stw[(r - 1) * Ns + k]);
       }
       Radix<C, T, R>::run(u);
       const int idxD = ((j >> log2Ns) << (log2Ns + log2R)) + k;
@@ -151,37 +159,38 @@ __device__ __forceinline__ void stage16(typename V2<T>::t* __restrict__ buf, int
 }
 
 // Batched in-place forward FFT of length n = 2^log2n (16 <= n) over `nbatch` padded transforms
-// bs apart in shared memory (element i of batch b at buf[b * bs + padi(i)]). The block needs at
-// least nbatch * n / 16 threads. Input complete before the call (barrier); result complete on
-// return, in natural order, in place.
+// bs apart in shared memory (element i of batch b at buf[b * bs + padi(i)]), stw the stage table
+// of length n. The block needs at least nbatch * n / 16 threads. Input complete before the call
+// (barrier); result complete on return, in natural order, in place.
 template <typename T>
 __device__ void fft16(typename V2<T>::t* buf, int n, int log2n, int nbatch, int bs,
-                      const typename V2<T>::t* __restrict__ tw, int tw_log2) {
+                      const typename V2<T>::t* __restrict__ stw) {
   int Ns = 1, log2Ns = 0;
   const int rem = log2n & 3;
   if (rem == 1) {
-    stage16<T, 2>(buf, n, log2n, nbatch, bs, Ns, log2Ns, tw, tw_log2);
+    stage16<T, 2>(buf, n, log2n, nbatch, bs, Ns, log2Ns, stw);
     Ns = 2; log2Ns = 1;
   } else if (rem == 2) {
-    stage16<T, 4>(buf, n, log2n, nbatch, bs, Ns, log2Ns, tw, tw_log2);
+    stage16<T, 4>(buf, n, log2n, nbatch, bs, Ns, log2Ns, stw);
     Ns = 4; log2Ns = 2;
   } else if (rem == 3) {
-    stage16<T, 8>(buf, n, log2n, nbatch, bs, Ns, log2Ns, tw, tw_log2);
+    stage16<T, 8>(buf, n, log2n, nbatch, bs, Ns, log2Ns, stw);
     Ns = 8; log2Ns = 3;
   }
+  int off = 0;
   while (log2Ns < log2n) {
-    stage16<T, 16>(buf, n, log2n, nbatch, bs, Ns, log2Ns, tw, tw_log2);
+    stage16<T, 16>(buf, n, log2n, nbatch, bs, Ns, log2Ns, stw + off);
+    if (Ns > 1) off += 15 * Ns;
     Ns <<= 4;
     log2Ns += 4;
   }
 }
 
-// Copy omega_n^i, i < n, from the plan table (n_tab = 2^tw_log2 >= n) into shared memory.
+// Copy a stage table (len entries) into shared memory.
 template <typename T>
-__device__ __forceinline__ void load_tw_smem(typename V2<T>::t* dst, const typename V2<T>::t* __restrict__ tw,
-                                             int n, int log2n, int tw_log2) {
-  const int sh = tw_log2 - log2n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = __ldg(&tw[i << sh]);
+__device__ __forceinline__ void load_tw_smem(typename V2<T>::t* dst, const typename V2<T>::t* __restrict__ stw,
+                                             int len) {
+  for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = __ldg(&stw[i]);
 }
 
 }  // namespace bk

@@ -17,8 +17,10 @@ struct Plan {
   size_t smemA = 0, smemB = 0;
   int thrA = 256, thrB = 256; // threads of the pass kernels (16 complex values each)
   int nPartA = 0;             // pass-A CTAs per vector (partials per vector)
-  int tw_log2 = 0;
-  void* tw = nullptr;         // sub-FFT twiddles (complex, working type)
+  int bsA = 0;                // pass-A batch stride in shared memory (complex elements)
+  void* tw = nullptr;         // omega_N^i, i < N (single-CTA plans; the N < 16 direct DFT)
+  void* stw1 = nullptr;       // stage twiddle table of the length-N (single-CTA) or N1 FFT
+  void* stw2 = nullptr;       // stage twiddle table of the length-N2 FFT (four-step)
   void* tpost = nullptr;      // (cos, sin)(pi k / N), k = 0..N/2 (working type)
   void* rk = nullptr;         // 1 / (4k), k = 0..N+1 (working type; rk[0] = 0)
   void* twN = nullptr;        // omega_N^m, m < N (four-step, FP64)
