@@ -231,7 +231,7 @@ def run_newton(args, rank, world, dist):
                e2e={"value": world * 1000.0 / e2e_ms, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
                solve=dict(newton_iterations=last["iterations"], krylov_iterations=last["krylov_iterations"],
-                          kkt_solves=last["kkt_solves"], residual=last["residual"]))
+                          kkt_solves=last["kkt_solves"], backtracks=last["backtracks"], residual=last["residual"]))
     return res
 
 

@@ -265,7 +265,7 @@ size_t bk_newton_workspace_bytes(const bk_problem* prob, int restart);
  * F(z, y) = [grad J + G^T y ; c ; e] = 0 with c = X - x0 - s (B (x) I) f(X, U), e the terminal
  * conditions and J = s sum_i w_i F(x_i, u_i). Each step solves the KKT system by
  * preconditioned GMRES (BK_F32: FP32 GMRES, refined by the FP64 Newton residual), then a
- * backtracking line search (alpha = 1, 1/2, ...; Armijo 1e-4) on the weighted norm
+ * backtracking line search (alpha = 1, then the minimiser of a quadratic model clamped to [alpha/10, alpha/2]; Armijo 1e-4) on the weighted norm
  *   ||F||_W^2 = sum_i w_i |c_i|^2 + sum_i |g_i|^2 / w_i + |e|^2  (g: gradient rows).
  *   z_inout    device FP64 KKT vector: initial guess in, solution out (X, U, lambda, nu)
  *   info       host struct, valid on return (synchronous)

@@ -1086,16 +1086,16 @@ __global__ void k_negate(T* v, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) v[i] = -v[i];
 }
 
-// mu_ready: the caller has just evaluated the KKT residual at this z (problem_residual), which
-// left mu = s B^aT lambda in the FP64 scratch t3; it is reused instead of recomputed.
+// mu (nullable): s B^aT lambda at this z, known to the caller (e.g. from the residual that
+// accepted the step); it is copied instead of recomputed.
 // A BK_F32 problem builds its preconditioner data in FP32 only; the FP64 side keeps the
 // linearisation point and mu, which the FP64 KKT product needs.
 template <int KIND>
-static bk_status linearize_kind(Problem* pr, const double* z, bool mu_ready, cudaStream_t st) {
+static bk_status linearize_kind(Problem* pr, const double* z, const double* mu, cudaStream_t st) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   const int64_t P = pr->P;
-  if (mu_ready)
-    BK_TRY_CUDA(cudaMemcpyAsync(pr->d64.mu, pr->d64.t3, sizeof(double) * NX * P, cudaMemcpyDeviceToDevice, st));
+  if (mu)
+    BK_TRY_CUDA(cudaMemcpyAsync(pr->d64.mu, mu, sizeof(double) * NX * P, cudaMemcpyDeviceToDevice, st));
   else
     BK_TRY(plan_apply_n(pr->d64.plan, z + (NX + NU) * P, pr->d64.mu, NX, true, pr->s, st));
   if (pr->dtype == BK_F64)
@@ -1122,14 +1122,14 @@ static bk_status linearize_kind(Problem* pr, const double* z, bool mu_ready, cud
   return BK_OK;
 }
 
-bk_status problem_linearize(Problem* pr, const double* z, cudaStream_t st, bool mu_ready) {
+bk_status problem_linearize(Problem* pr, const double* z, cudaStream_t st, const double* mu) {
   BK_ARG(pr != nullptr && z != nullptr, "NULL problem or z_lin");
-  BK_DISPATCH_KIND(pr->kind, linearize_kind, pr, z, mu_ready, st);
+  BK_DISPATCH_KIND(pr->kind, linearize_kind, pr, z, mu, st);
 }
 
 // --- operator applies --------------------------------------------------------------------------
 template <typename T, int KIND>
-static bk_status apply_typed(Problem* pr, OpData& d, int op, const T* in, T* out, cudaStream_t st) {
+static bk_status apply_typed(Problem* pr, OpData& d, int op, const T* in, T* out, T* mu_out, cudaStream_t st) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   const int64_t P = pr->P, L = pr->L;
   T* t1 = (T*)d.t1;
@@ -1148,23 +1148,24 @@ static bk_status apply_typed(Problem* pr, OpData& d, int op, const T* in, T* out
   BK_CHECK_LAUNCH();
   if (P > L) { k_zero_pad<T><<<nblk(NX * (P - L)), 256, 0, st>>>(t1, NX, P, L); BK_CHECK_LAUNCH(); }
   BK_TRY(plan_apply_n(d.plan, t1, t2, NX, false, pr->s, st));
-  BK_TRY(plan_apply_n(d.plan, in + (NX + NU) * P, t3, NX, true, pr->s, st));
-  k_kkt_post<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.mu, (const T*)d.w, (T)pr->s, in, t2, t3, P, L,
+  T* Mu = mu_out ? mu_out : t3;
+  BK_TRY(plan_apply_n(d.plan, in + (NX + NU) * P, Mu, NX, true, pr->s, st));
+  k_kkt_post<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.mu, (const T*)d.w, (T)pr->s, in, t2, Mu, P, L,
                                                 term_spec(pr), (T)(pr->has_cost ? 1.0 : 0.0), out);
   BK_CHECK_LAUNCH();
   return BK_OK;
 }
 
 template <int KIND>
-static bk_status apply_kind(Problem* pr, OpData& d, int op, const void* in, void* out, cudaStream_t st) {
-  if (d.dtype == BK_F64) return apply_typed<double, KIND>(pr, d, op, (const double*)in, (double*)out, st);
-  return apply_typed<float, KIND>(pr, d, op, (const float*)in, (float*)out, st);
+static bk_status apply_kind(Problem* pr, OpData& d, int op, const void* in, void* out, void* mu_out, cudaStream_t st) {
+  if (d.dtype == BK_F64) return apply_typed<double, KIND>(pr, d, op, (const double*)in, (double*)out, (double*)mu_out, st);
+  return apply_typed<float, KIND>(pr, d, op, (const float*)in, (float*)out, (float*)mu_out, st);
 }
 
-bk_status op_apply(Problem* pr, OpData& d, int op, const void* in, void* out, cudaStream_t st) {
+bk_status op_apply(Problem* pr, OpData& d, int op, const void* in, void* out, cudaStream_t st, void* mu_out) {
   BK_ARG(pr->linearized, "problem is not linearised (call bk_linearize first)");
   BK_ARG(op == BK_OP_STATE || op == BK_OP_KKT, "unknown operator %d", op);
-  BK_DISPATCH_KIND(pr->kind, apply_kind, pr, d, op, in, out, st);
+  BK_DISPATCH_KIND(pr->kind, apply_kind, pr, d, op, in, out, mu_out, st);
 }
 
 // --- preconditioner ---------------------------------------------------------------------------
@@ -1219,17 +1220,18 @@ bk_status op_precond(Problem* pr, OpData& d, int op, const void* in, void* out, 
 
 // --- residual -------------------------------------------------------------------------------
 template <int KIND>
-static bk_status residual_kind(Problem* pr, const double* z, double* F, double* wnorm, cudaStream_t st) {
+static bk_status residual_kind(Problem* pr, const double* z, double* F, double* wnorm, double* Mu, bool mu_given,
+                               cudaStream_t st) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   const int64_t P = pr->P, L = pr->L;
   OpData& d = pr->d64;
   double* f = (double*)d.t1;
   double* Bf = (double*)d.t2;
-  double* Mu = (double*)d.t3;
+  if (!Mu) Mu = (double*)d.t3;
   k_feval<KIND><<<nblk(P), 256, 0, st>>>(z, P, L, f);
   BK_CHECK_LAUNCH();
   BK_TRY(plan_apply_n(d.plan, f, Bf, NX, false, pr->s, st));
-  BK_TRY(plan_apply_n(d.plan, z + (NX + NU) * P, Mu, NX, true, pr->s, st));
+  if (!mu_given) BK_TRY(plan_apply_n(d.plan, z + (NX + NU) * P, Mu, NX, true, pr->s, st));
   X0Spec x0;
   for (int m = 0; m < NXM; ++m) x0.x0[m] = pr->x0[m];
   const int nb = 592;
@@ -1246,8 +1248,9 @@ static bk_status residual_kind(Problem* pr, const double* z, double* F, double* 
   return BK_OK;
 }
 
-bk_status problem_residual(Problem* pr, const double* z, double* F, double* wnorm, cudaStream_t st) {
-  BK_DISPATCH_KIND(pr->kind, residual_kind, pr, z, F, wnorm, st);
+bk_status problem_residual(Problem* pr, const double* z, double* F, double* wnorm, cudaStream_t st, double* Mu,
+                           bool mu_given) {
+  BK_DISPATCH_KIND(pr->kind, residual_kind, pr, z, F, wnorm, Mu, mu_given, st);
 }
 
 template <int KIND>

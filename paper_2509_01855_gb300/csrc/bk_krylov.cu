@@ -173,7 +173,7 @@ size_t gmres_workspace_bytes(int64_t n, int m, int dtype) {
 
 template <typename T>
 static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, const bk_krylov_opts& o,
-                            bk_krylov_info* info, void* ws, cudaStream_t st, double* hostbuf) {
+                            bk_krylov_info* info, void* ws, cudaStream_t st, double* hostbuf, const KrylovMu* aux) {
   const int64_t n = op == BK_OP_KKT ? pr->kkt_len() : pr->state_len();
   const int m = o.restart;
   const int64_t ld = round_up(n, 64);
@@ -196,6 +196,7 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
   BK_TRY_CUDA(cudaStreamSynchronize(st));
   const double bnorm = sqrt(hostbuf[0]);
   BK_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * n, st));
+  if (aux) BK_TRY_CUDA(cudaMemsetAsync(aux->Td, 0, sizeof(double) * aux->n, st));
   info->iterations = 0;
   info->restarts = 0;
   info->rel_resid = 0.0;
@@ -234,9 +235,9 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
       if (o.use_precond) {
         T* zj = Zb + (int64_t)j * ld;
         BK_TRY(op_precond(pr, d, op, vj, zj, 0, st));
-        BK_TRY(op_apply(pr, d, op, zj, w, st));
+        BK_TRY(op_apply(pr, d, op, zj, w, st, aux ? (void*)(aux->T + (int64_t)j * aux->ld) : nullptr));
       } else {
-        BK_TRY(op_apply(pr, d, op, vj, w, st));
+        BK_TRY(op_apply(pr, d, op, vj, w, st, aux ? (void*)(aux->T + (int64_t)j * aux->ld) : nullptr));
       }
       // Gram-Schmidt (DGKS): h1 = [V_0..V_j]^T w and |w|^2 (w = V_{j+1} follows V_j), then
       // w <- w - V h1 with the new |w|^2; a second pass only on cancellation.
@@ -298,6 +299,10 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
     // x += Z y (flexible form; Z = V without preconditioning)
     k_multiaxpy<T><<<g, 256, 0, st>>>(o.use_precond ? Zb : V, ld, j, yv, 1.0, x, 1.0, n, nullptr);
     BK_CHECK_LAUNCH();
+    if (aux) {
+      k_multiaxpy<double><<<grid_for(aux->n), 256, 0, st>>>(aux->T, aux->ld, j, yv, 1.0, aux->Td, 1.0, aux->n, nullptr);
+      BK_CHECK_LAUNCH();
+    }
     ++info->restarts;
     if (total >= o.max_iter) {
       // final explicit residual
@@ -318,13 +323,14 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
 }
 
 bk_status gmres(Problem* pr, OpData& d, int op, const void* b, void* x, const bk_krylov_opts& o, bk_krylov_info* info,
-                void* ws, cudaStream_t st) {
+                void* ws, cudaStream_t st, const KrylovMu* aux) {
   BK_ARG(o.restart >= 1 && o.restart <= MAXM, "restart must be in [1, %d]", MAXM);
   BK_ARG(o.max_iter >= 1, "max_iter must be >= 1");
   BK_ARG(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be 256-byte aligned");
+  BK_ARG(aux == nullptr || (d.dtype == BK_F64 && op == BK_OP_KKT), "transposed-product record needs the FP64 KKT operator");
   if (d.dtype == BK_F64)
-    return gmres_impl<double>(pr, d, op, (const double*)b, (double*)x, o, info, ws, st, pr->red_host);
-  return gmres_impl<float>(pr, d, op, (const float*)b, (float*)x, o, info, ws, st, pr->red_host);
+    return gmres_impl<double>(pr, d, op, (const double*)b, (double*)x, o, info, ws, st, pr->red_host, aux);
+  return gmres_impl<float>(pr, d, op, (const float*)b, (float*)x, o, info, ws, st, pr->red_host, nullptr);
 }
 
 bk_krylov_opts krylov_defaults() {

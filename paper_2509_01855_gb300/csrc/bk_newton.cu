@@ -3,13 +3,24 @@
 // The paper reports SQP iteration counts (Table tab:m) but does not describe its outer loop.
 // This driver takes Newton's method on the KKT conditions F(z, y) = [grad J + G^T y ; c ; e] = 0
 // with the exact Lagrangian Hessian, each step solved by the Birkhoff-preconditioned GMRES, and
-// a backtracking line search (alpha = 1, 1/2, ...; Armijo constant 1e-4) on the quadrature-
+// a backtracking line search (alpha = 1, then quadratic-model steps; Armijo constant 1e-4) on the quadrature-
 // weighted norm ||F||_W^2 = sum w c^2 + sum g^2 / w + |e|^2, which does not grow with N.
 // The residual and the line search are FP64. BK_F32 problems run the GMRES iterations and their
 // operator applies in FP32; the FP64 Newton residual then refines their step (inexact Newton),
 // and max_refine > 1 adds linear iterative-refinement sweeps with an FP64 KKT residual.
+//
+// Products per step. The residual's multiplier term mu = s B^aT lambda is linear in lambda, so
+// along a step mu(z + alpha d) = mu + alpha mu_d with mu_d = s B^aT d_lambda: only the initial
+// residual applies B^T to lambda. FP64 solves get mu_d from the Krylov iteration itself (each
+// KKT apply already forms B^T of its lambda block; GMRES combines them with the solution's
+// coefficients); FP32 solves form it with one FP64 product per step. Each line-search trial then
+// costs one forward product. Backtracking takes the minimiser of the quadratic model of
+// ||F||_W^2 along d (slope -2 ||F||_W^2 at alpha = 0, the Newton value), safeguarded to
+// [alpha / 10, alpha / 2], instead of halving.
 #include <math.h>
 #include <string.h>
+
+#include <utility>
 
 #include "bk_krylov.cuh"
 
@@ -92,8 +103,11 @@ static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 size_t newton_workspace(const Problem* pr, int restart) {
   const int64_t n = pr->kkt_len();
+  const int64_t nxP = (int64_t)pr->n_x * pr->P;
   size_t b = 0;
   b += 4 * align256(sizeof(double) * n);   // d, zt, rhs, r
+  b += 3 * align256(sizeof(double) * nxP); // mu, mu_t, mu_d
+  if (pr->dtype == BK_F64) b += align256(sizeof(double) * nxP * restart);  // Krylov B^T records
   if (pr->dtype == BK_F32) b += 2 * align256(sizeof(float) * n);
   b += align256(gmres_workspace_bytes(n, restart, pr->dtype));
   return b + 1024;
@@ -115,6 +129,12 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     d32 = (float*)carve(sizeof(float) * n);
   }
   void* gws = carve(gmres_workspace_bytes(n, o.restart, pr->dtype));
+  const int64_t nxP = (int64_t)pr->n_x * pr->P;
+  double* Mu = (double*)carve(sizeof(double) * nxP);
+  double* Mut = (double*)carve(sizeof(double) * nxP);
+  double* Mud = (double*)carve(sizeof(double) * nxP);
+  double* Trec = pr->dtype == BK_F64 ? (double*)carve(sizeof(double) * nxP * o.restart) : nullptr;
+  const double* dlam = d + (int64_t)(pr->n_x + pr->n_u) * pr->P;
   double* F = pr->F;
   const int g = g1(n);
   bk_krylov_opts ko;
@@ -122,7 +142,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
   ko.max_iter = o.max_krylov;
   ko.use_precond = 1;
   double phi = 0.0;
-  BK_TRY(problem_residual(pr, z, F, &phi, st));
+  BK_TRY(problem_residual(pr, z, F, &phi, st, Mu, false));
   info->residual0 = phi;
   info->residual = phi;
   int it = 0;
@@ -138,12 +158,13 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
       const double lo = pr->dtype == BK_F64 ? 1e-12 : 1e-4;
       ko.rtol = fmin(1e-2, fmax(lo, 0.1 * r * r));
     }
-    BK_TRY(problem_linearize(pr, z, st, /*mu_ready=*/true));
+    BK_TRY(problem_linearize(pr, z, st, Mu));
     k_axpby64<<<g, 256, 0, st>>>(F, -1.0, rhs, 0.0, n);
     BK_CHECK_LAUNCH();
     bk_krylov_info ki;
     if (pr->dtype == BK_F64) {
-      BK_TRY(gmres(pr, pr->d64, BK_OP_KKT, rhs, d, ko, &ki, gws, st));
+      const KrylovMu aux = {Trec, nxP, Mud, nxP};
+      BK_TRY(gmres(pr, pr->d64, BK_OP_KKT, rhs, d, ko, &ki, gws, st, &aux));
       info->krylov_iterations += ki.iterations;
       info->kkt_solves += 1;
     } else {
@@ -170,16 +191,23 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
         BK_TRY(norm2(pr, r, n, &rn, st));
         if (rn <= o.ir_rtol * rn0) break;
       }
+      BK_TRY(plan_apply_n(pr->d64.plan, dlam, Mud, pr->n_x, true, pr->s, st));
     }
     // backtracking line search on ||F||_W
     double alpha = 1.0, phit = 0.0;
     int bt = 0;
+    const double phi2 = phi * phi;
     for (;;) {
       k_step<<<g, 256, 0, st>>>(z, d, alpha, zt, n);
       BK_CHECK_LAUNCH();
-      BK_TRY(problem_residual(pr, zt, F, &phit, st));
+      k_step<<<g1(nxP), 256, 0, st>>>(Mu, Mud, alpha, Mut, nxP);
+      BK_CHECK_LAUNCH();
+      BK_TRY(problem_residual(pr, zt, F, &phit, st, Mut, true));
       if (phit <= (1.0 - 1e-4 * alpha) * phi || bt >= 30) break;
-      alpha *= 0.5;
+      double an = phi2 * alpha * alpha / (phit * phit - phi2 + 2.0 * phi2 * alpha);
+      if (!(an >= 0.1 * alpha)) an = 0.1 * alpha;  // also catches a non-finite trial residual
+      if (an > 0.5 * alpha) an = 0.5 * alpha;
+      alpha = an;
       ++bt;
     }
     info->backtracks += bt;
@@ -190,6 +218,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
       return BK_ERR_INFEASIBLE;
     }
     BK_TRY_CUDA(cudaMemcpyAsync(z, zt, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    std::swap(Mu, Mut);
     phi = phit;
     ++it;
   }

@@ -160,15 +160,20 @@ struct Problem {
   OpData& work() { return dtype == BK_F64 ? d64 : d32; }
 };
 
-// mu_ready: problem_residual(z_lin) was the last FP64 work on the problem (its mu is reused).
-bk_status problem_linearize(Problem* pr, const double* z_lin, cudaStream_t st, bool mu_ready = false);
-// Operator applies on one precision's data (T = double or float).
-bk_status op_apply(Problem* pr, OpData& d, int op, const void* in, void* out, cudaStream_t st);
+// mu (nullable): s B^aT lambda at z_lin, already known to the caller (FP64, n_x * P); when
+// null it is computed with one transposed product.
+bk_status problem_linearize(Problem* pr, const double* z_lin, cudaStream_t st, const double* mu = nullptr);
+// Operator applies on one precision's data (T = double or float). For BK_OP_KKT, mu_out
+// (nullable, n_x * P of T) receives s B^aT in_lambda, the operator's transposed product.
+bk_status op_apply(Problem* pr, OpData& d, int op, const void* in, void* out, cudaStream_t st,
+                   void* mu_out = nullptr);
 bk_status op_precond(Problem* pr, OpData& d, int op, const void* in, void* out, int transpose,
                      cudaStream_t st);
 // KKT residual at z (FP64) into F; weighted norm partial sums reduced on the host if wnorm.
-bk_status problem_residual(Problem* pr, const double* z, double* F, double* wnorm,
-                           cudaStream_t st);
+// Mu (n_x * P, FP64) holds s B^aT lambda: given by the caller when mu_given, else computed into
+// it (null: into the problem's scratch).
+bk_status problem_residual(Problem* pr, const double* z, double* F, double* wnorm, cudaStream_t st,
+                           double* Mu = nullptr, bool mu_given = false);
 // Weighted norm of a residual vector (FP64), synchronous.
 bk_status problem_wnorm(Problem* pr, const double* F, double* wnorm, cudaStream_t st);
 
