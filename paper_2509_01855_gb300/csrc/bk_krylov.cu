@@ -217,11 +217,14 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
       k_axpby<T><<<g, 256, 0, st>>>(b, 1.0, r, -1.0, n);
       BK_CHECK_LAUNCH();
     }
+    double beta = bnorm;  // r = b on the first cycle
+    if (!first) {
+      BK_TRY(dots<T>(r, ld, 1, r, n, partial, h1, st));
+      BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double), cudaMemcpyDeviceToHost, st));
+      BK_TRY_CUDA(cudaStreamSynchronize(st));
+      beta = sqrt(hostbuf[0]);
+    }
     first = false;
-    BK_TRY(dots<T>(r, ld, 1, r, n, partial, h1, st));
-    BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double), cudaMemcpyDeviceToHost, st));
-    BK_TRY_CUDA(cudaStreamSynchronize(st));
-    const double beta = sqrt(hostbuf[0]);
     resid = beta;
     if (beta <= target || total >= o.max_iter) break;
     k_axpby<T><<<g, 256, 0, st>>>(r, 1.0 / beta, V, 0.0, n);
@@ -304,6 +307,11 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
       BK_CHECK_LAUNCH();
     }
     ++info->restarts;
+    // A converged cycle returns on its Arnoldi residual estimate |g_{j+1}|: in the flexible form
+    // it is the residual of the iterate built from the z_j actually computed, and recomputing
+    // b - A x would cost one more operator apply per solve. The true residual is formed on
+    // restarts and at the iteration cap.
+    if (resid <= target) break;
     if (total >= o.max_iter) {
       // final explicit residual
       BK_TRY(op_apply(pr, d, op, x, r, st));
