@@ -14,9 +14,11 @@ Prints one JSON line on rank 0. With N > 1 (torchrun) every rank solves its own 
 --impl reference times the FP64 CPU oracle (test infrastructure) on a bounded sample.
 """
 import argparse
+import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -235,6 +237,31 @@ def run_newton(args, rank, world, dist):
     return res
 
 
+TRAFFIC_DOC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "birkhoff_apply_N2p20x4_traffic.md")
+TRANSFORM_SOURCES = ("bk_birkhoff.cu", "bk_fft.cuh", "bk_plan.cuh", "bk_common.cuh")
+
+
+def recorded_traffic(dtype_name, N):
+    """DRAM bytes of one 4-component product at N = 2^20 from the committed ncu summary, or None
+    when N differs or the transform sources changed since that capture (hash check)."""
+    if N != 1 << 20:
+        return None
+    try:
+        text = open(TRAFFIC_DOC).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_product %s: (\d+)" % dtype_name, text)
+    h = re.search(r"source_sha256_16: ([0-9a-f]{16})", text)
+    if not m or not h:
+        return None
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2509_01855_gb300", "csrc")
+    sha = hashlib.sha256()
+    for f in TRANSFORM_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            sha.update(fh.read())
+    return int(m.group(1)) if sha.hexdigest()[:16] == h.group(1) else None
+
+
 def measure_apply(N, dtype, reps=20):
     """Birkhoff apply B v on 4 components, cold L2 between repetitions (CUDA events)."""
     import torch
@@ -408,7 +435,8 @@ def main():
         peak, unit, achieved = hbm_peak, "GB/s", abytes / ams / 1e6
         bound = "hbm"
     line["roofline"] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                        "frac": achieved / peak, "traffic": None,
+                        "frac": achieved / peak, "traffic": recorded_traffic(dtype_name if args.workload != "serve" else "f64", N),
+                        "traffic_source": os.path.relpath(TRAFFIC_DOC, os.path.dirname(os.path.abspath(__file__))),
                         "kernel": "birkhoff_apply N=2^%d x4 components (%s)" % (args.N, dtype_name),
                         "algorithmic": {"bytes": abytes, "flops": aflops},
                         "peak_source": ("FP64 FMA nominal 1.25 TFLOP/s (2 FP64 FMA/clk/SM)" if bound == "alu"
