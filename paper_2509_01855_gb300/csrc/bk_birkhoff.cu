@@ -398,6 +398,36 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
   }
 }
 
+// Second-DCT input as its own elementwise pass (planned applies): x_m of kind K (ST_FWD with
+// scale sc, or ST_TRN) for every m <= N, written to G, with per-CTA partial sums of W_m x_m
+// (the DC value R(x)_0 of the DCT, W = 1 at the ends, 2 inside) when `partial` is given. Fusing
+// the stencil into the pass-A loads instead exposes its neighbour loads: those passes ran
+// 25-40% longer than plain-load ones.
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_stencil(const T* __restrict__ stage, int64_t Ls, T* __restrict__ G, int N,
+                                                 T sc, StencilTab<T> tb, T* __restrict__ partial) {
+  __shared__ T red[8];
+  const int vec = blockIdx.y;
+  const T* Y = stage + (int64_t)vec * Ls;
+  T* g = G + (int64_t)vec * Ls;
+  T acc = T(0);
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m <= N; m += gridDim.x * blockDim.x) {
+    const T x = load_x<T, K>(Y, m, N, sc, T(0), tb);
+    g[m] = x;
+    acc += (m == 0 || m == N) ? x : T(2) * x;
+  }
+  if (partial) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T a = T(0);
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
+      partial[(int64_t)vec * gridDim.x + blockIdx.x] = a;
+    }
+  }
+}
+
 // Epilogue kinds of pass B:
 //   EP_STORE     : stage[k] = Y_k / N                      (after the first DCT, forward)
 //   EP_STORE_TRN : stage[k] = Y_k - Y0, Y0 from partials   (after the first DCT, transpose)
@@ -738,6 +768,7 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
       const size_t csz = 2 * dtype_size(dtype);
       if ((st_ = dmalloc(&p->scrA, csz * (size_t)N * nvec)) != BK_OK) break;
       if ((st_ = dmalloc(&p->scrY, dtype_size(dtype) * (size_t)(N + 1) * nvec)) != BK_OK) break;
+      if ((st_ = dmalloc(&p->scrG, dtype_size(dtype) * (size_t)(N + 1) * nvec)) != BK_OK) break;
       if ((st_ = dmalloc(&p->part1, dtype_size(dtype) * (size_t)p->nPartA * nvec)) != BK_OK) break;
       if ((st_ = dmalloc(&p->part2, dtype_size(dtype) * (size_t)p->nPartA * nvec)) != BK_OK) break;
     }
@@ -775,6 +806,7 @@ void plan_destroy(Plan* p) {
   dfree(p->twHi);
   dfree(p->scrA);
   dfree(p->scrY);
+  dfree(p->scrG);
   dfree(p->part1);
   dfree(p->part2);
   dfree(p->t_nodes);
@@ -783,7 +815,7 @@ void plan_destroy(Plan* p) {
 
 template <typename T>
 static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool trans, double s_scale,
-                            cudaStream_t st, void* scrA, void* scrY, void* part1, void* part2) {
+                            cudaStream_t st, void* scrA, void* scrY, void* part1, void* part2, void* scrG) {
   typedef typename V2<T>::t C;
   const int N = (int)p->N;
   const T s = (T)s_scale;
@@ -813,12 +845,20 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
   const C* twN = (const C*)p->twN;
   const C* tp = (const C*)p->tpost;
   const int64_t Ls = N + 1;
+  T* Gst = (T*)scrG;  // separate stencil pass when given (see k_stencil)
+  const dim3 gS(nPA, nvec);
   if (!trans) {
     k_passA<T, IN_PLAIN><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
     BK_CHECK_LAUNCH();
     k_passB<T, EP_STORE><<<gB, p->thrB, p->smemB, st>>>(A, Ystage, Ls, 0, nullptr, 0, N, N1, N2, log2N2, P, stw2, tp, s, invN);
     BK_CHECK_LAUNCH();
-    k_passA<T, ST_FWD><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    if (Gst) {
+      k_stencil<T, ST_FWD><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, pa2);
+      BK_CHECK_LAUNCH();
+      k_passA<T, IN_PLAIN><<<gA, p->thrA, p->smemA, st>>>(Gst, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    } else {
+      k_passA<T, ST_FWD><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    }
     BK_CHECK_LAUNCH();
     k_passB<T, EP_FWD_OUT><<<gB, p->thrB, p->smemB, st>>>(A, out, p->pitch, p->pitch, pa2, nPA, N, N1, N2, log2N2, P, stw2, tp, s, invN);
     BK_CHECK_LAUNCH();
@@ -828,7 +868,13 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
     k_passB<T, EP_STORE_TRN><<<gB, p->thrB, p->smemB, st>>>(A, Ystage, Ls, 0, pa1, nPA, N, N1, N2, log2N2, P, stw2, tp, s, invN);
     BK_CHECK_LAUNCH();
     // the stage buffer already holds Y - Y0, so the transposed stencil runs with Y0 = 0
-    k_passA<T, ST_TRN><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    if (Gst) {
+      k_stencil<T, ST_TRN><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, nullptr);
+      BK_CHECK_LAUNCH();
+      k_passA<T, IN_PLAIN><<<gA, p->thrA, p->smemA, st>>>(Gst, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    } else {
+      k_passA<T, ST_TRN><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    }
     BK_CHECK_LAUNCH();
     k_passB<T, EP_TRN_OUT><<<gB, p->thrB, p->smemB, st>>>(A, out, p->pitch, p->pitch, nullptr, 0, N, N1, N2, log2N2, P, stw2, tp, s, invN);
     BK_CHECK_LAUNCH();
@@ -839,8 +885,8 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
 bk_status plan_apply_n(const Plan* p, const void* v, void* out, int nvec, bool trans, double s,
                        cudaStream_t st) {
   if (p->dtype == BK_F64)
-    return apply_impl<double>(p, (const double*)v, (double*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2);
-  return apply_impl<float>(p, (const float*)v, (float*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2);
+    return apply_impl<double>(p, (const double*)v, (double*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2, p->scrG);
+  return apply_impl<float>(p, (const float*)v, (float*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2, p->scrG);
 }
 
 bk_status plan_apply(const Plan* p, const void* v, void* out, int batch, bool trans, cudaStream_t st) {
@@ -955,7 +1001,7 @@ bk_status noalloc_apply(const double* v, double* out, int64_t N, int nvec, int64
   BK_CHECK_LAUNCH();
   k_tw_table<double><<<(int)std::min<int64_t>((N + 255) / 256, 8192), 256, 0, st>>>((double2*)p.twN, N, (double)N);
   BK_CHECK_LAUNCH();
-  return apply_impl<double>(&p, v, out, nvec, false, p.s, st, b + off[3], b + off[4], b + off[5], b + off[6]);
+  return apply_impl<double>(&p, v, out, nvec, false, p.s, st, b + off[3], b + off[4], b + off[5], b + off[6], nullptr);
 }
 
 }  // namespace bk

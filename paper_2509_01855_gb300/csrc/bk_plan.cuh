@@ -29,6 +29,7 @@ struct Plan {
   int tw_h = 0;
   void* scrA = nullptr;       // four-step complex scratch, N per vector
   void* scrY = nullptr;       // stage buffer between the two DCTs, N + 1 per vector
+  void* scrG = nullptr;       // second-DCT input (stencil output), N + 1 per vector
   void* part1 = nullptr;      // pass-A partial sums, first DCT
   void* part2 = nullptr;      // pass-A partial sums, second DCT
   double* t_nodes = nullptr;  // node times t_j (FP64, device)
