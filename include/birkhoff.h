@@ -246,16 +246,22 @@ typedef struct {
   int max_refine;     /* FP32 mode: FP32 solves per Newton step (default 1: inexact Newton,
                          the FP64 Newton residual refines the step; > 1 adds linear
                          refinement sweeps with an FP64 KKT residual)                        */
+  int precond_reuse;  /* preconditioner reuse after a full step that cut ||F||_W >= 10x:
+                         0 (default) rebuild at every step; 1 keep the terminal Schur data
+                         of the last rebuild; 2 keep all preconditioner data (node factors,
+                         sweep levels, Schur data). The KKT operator always uses the new
+                         linearisation point; flexible GMRES accepts any preconditioner.   */
 } bk_newton_opts;
 
 typedef struct {
   int iterations;          /* Newton steps taken                                            */
   int krylov_iterations;   /* total inner Krylov iterations                                 */
   int kkt_solves;          /* inner Krylov solves (one per refinement sweep in FP32 mode)   */
-  int backtracks;          /* line-search halvings                                          */
+  int backtracks;          /* line-search step reductions                                   */
   double residual;         /* final weighted KKT residual norm                              */
   double residual0;        /* initial weighted KKT residual norm                            */
   int converged;
+  int precond_builds;      /* full preconditioner rebuilds (node factors and Schur data)     */
 } bk_newton_info;
 
 /* Workspace bytes newton_solve needs. */

@@ -47,14 +47,14 @@ class NewtonOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("krylov_rtol", ctypes.c_double), ("restart", ctypes.c_int),
                 ("max_krylov", ctypes.c_int), ("ir_rtol", ctypes.c_double),
-                ("max_refine", ctypes.c_int)]
+                ("max_refine", ctypes.c_int), ("precond_reuse", ctypes.c_int)]
 
 
 class NewtonInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("krylov_iterations", ctypes.c_int),
                 ("kkt_solves", ctypes.c_int), ("backtracks", ctypes.c_int),
                 ("residual", ctypes.c_double), ("residual0", ctypes.c_double),
-                ("converged", ctypes.c_int)]
+                ("converged", ctypes.c_int), ("precond_builds", ctypes.c_int)]
 
 
 _lib = None

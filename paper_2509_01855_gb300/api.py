@@ -216,19 +216,21 @@ def newton_workspace(prob, restart=30):
 
 
 def newton_solve(prob, z, tol=1e-10, max_iter=30, krylov_rtol=0.0, restart=30, max_krylov=0,
-                 ir_rtol=1e-10, max_refine=0, workspace=None, stream=None, raise_on_fail=True):
+                 ir_rtol=1e-10, max_refine=0, precond_reuse=0, workspace=None, stream=None,
+                 raise_on_fail=True):
     """Newton-Lagrange solve in place on the FP64 KKT vector z; returns the info fields.
     Zero-valued options take the library defaults for the problem's precision."""
     if workspace is None:
         workspace = newton_workspace(prob, restart)
     opts = L.NewtonOpts(float(tol), int(max_iter), float(krylov_rtol), int(restart),
-                        int(max_krylov), float(ir_rtol), int(max_refine))
+                        int(max_krylov), float(ir_rtol), int(max_refine), int(precond_reuse))
     info = L.NewtonInfo()
     st = L.lib().newton_solve(prob.handle, L.ptr(z), ctypes.byref(opts), ctypes.byref(info),
                               L.ptr(workspace), L.stream_ptr(stream))
     out = dict(iterations=info.iterations, krylov_iterations=info.krylov_iterations,
                kkt_solves=info.kkt_solves, backtracks=info.backtracks, residual=info.residual,
-               residual0=info.residual0, converged=bool(info.converged), status=st)
+               residual0=info.residual0, converged=bool(info.converged),
+               precond_builds=info.precond_builds, status=st)
     if raise_on_fail and st != 0:
         L.check(st)
     return out

@@ -1091,23 +1091,30 @@ __global__ void k_negate(T* v, int64_t n) {
 // A BK_F32 problem builds its preconditioner data in FP32 only; the FP64 side keeps the
 // linearisation point and mu, which the FP64 KKT product needs.
 template <int KIND>
-static bk_status linearize_kind(Problem* pr, const double* z, const double* mu, cudaStream_t st) {
+static bk_status linearize_kind(Problem* pr, const double* z, const double* mu, int keep, cudaStream_t st) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   const int64_t P = pr->P;
+  if (!pr->linearized) keep = LIN_FULL;
   if (mu)
     BK_TRY_CUDA(cudaMemcpyAsync(pr->d64.mu, mu, sizeof(double) * NX * P, cudaMemcpyDeviceToDevice, st));
   else
     BK_TRY(plan_apply_n(pr->d64.plan, z + (NX + NU) * P, pr->d64.mu, NX, true, pr->s, st));
-  if (pr->dtype == BK_F64)
+  if (pr->dtype == BK_F64 && keep != LIN_KEEP_PRECOND)
     BK_TRY((lin_factors<double, KIND>(pr, pr->d64, z, st)));
   else
     BK_TRY_CUDA(cudaMemcpyAsync(pr->d64.xu, z, sizeof(double) * (NX + NU) * P, cudaMemcpyDeviceToDevice, st));
   if (pr->dtype == BK_F32) {
     k_convert<double, float><<<nblk(NX * P), 256, 0, st>>>((const double*)pr->d64.mu, (float*)pr->d32.mu, NX * P);
     BK_CHECK_LAUNCH();
-    BK_TRY((lin_factors<float, KIND>(pr, pr->d32, z, st)));
+    if (keep != LIN_KEEP_PRECOND) {
+      BK_TRY((lin_factors<float, KIND>(pr, pr->d32, z, st)));
+    } else {
+      k_convert<double, float><<<nblk((NX + NU) * P), 256, 0, st>>>(z, (float*)pr->d32.xu, (NX + NU) * P);
+      BK_CHECK_LAUNCH();
+    }
   }
   pr->linearized = true;
+  if (keep != LIN_FULL) return BK_OK;
   if (pr->n_e > 0 && pr->has_cost) {
     if (pr->dtype == BK_F64) {
       BK_TRY((lin_schur<double, KIND>(pr, pr->d64, st)));
@@ -1122,9 +1129,9 @@ static bk_status linearize_kind(Problem* pr, const double* z, const double* mu, 
   return BK_OK;
 }
 
-bk_status problem_linearize(Problem* pr, const double* z, cudaStream_t st, const double* mu) {
+bk_status problem_linearize(Problem* pr, const double* z, cudaStream_t st, const double* mu, int keep) {
   BK_ARG(pr != nullptr && z != nullptr, "NULL problem or z_lin");
-  BK_DISPATCH_KIND(pr->kind, linearize_kind, pr, z, mu, st);
+  BK_DISPATCH_KIND(pr->kind, linearize_kind, pr, z, mu, keep, st);
 }
 
 // --- operator applies --------------------------------------------------------------------------

@@ -146,6 +146,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
   info->residual0 = phi;
   info->residual = phi;
   int it = 0;
+  bool fast = false;  // the last step was a full step that cut ||F||_W at least 10x
   while (phi > o.tol && it < o.max_iter) {
     // Inner tolerance: fixed if the caller set one, else a forcing term that tightens with the
     // outer residual, rtol_k = 0.1 (phi_k / phi_0)^2 clamped to [floor, 1e-2] (Eisenstat and
@@ -158,7 +159,10 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
       const double lo = pr->dtype == BK_F64 ? 1e-12 : 1e-4;
       ko.rtol = fmin(1e-2, fmax(lo, 0.1 * r * r));
     }
-    BK_TRY(problem_linearize(pr, z, st, Mu));
+    const int keep = (fast && o.precond_reuse > 0) ? (o.precond_reuse >= 2 ? LIN_KEEP_PRECOND : LIN_KEEP_SCHUR)
+                                                  : LIN_FULL;
+    if (keep == LIN_FULL) ++info->precond_builds;
+    BK_TRY(problem_linearize(pr, z, st, Mu, keep));
     k_axpby64<<<g, 256, 0, st>>>(F, -1.0, rhs, 0.0, n);
     BK_CHECK_LAUNCH();
     bk_krylov_info ki;
@@ -219,6 +223,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     }
     BK_TRY_CUDA(cudaMemcpyAsync(z, zt, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     std::swap(Mu, Mut);
+    fast = bt == 0 && phit <= 0.1 * phi;
     phi = phit;
     ++it;
   }

@@ -161,8 +161,12 @@ struct Problem {
 };
 
 // mu (nullable): s B^aT lambda at z_lin, already known to the caller (FP64, n_x * P); when
-// null it is computed with one transposed product.
-bk_status problem_linearize(Problem* pr, const double* z_lin, cudaStream_t st, const double* mu = nullptr);
+// null it is computed with one transposed product. `keep` keeps part of the preconditioner of
+// the previous linearisation: LIN_FULL rebuilds everything, LIN_KEEP_SCHUR keeps the terminal
+// Schur data, LIN_KEEP_PRECOND keeps all of it (the operator data is always updated).
+enum { LIN_FULL = 0, LIN_KEEP_SCHUR = 1, LIN_KEEP_PRECOND = 2 };
+bk_status problem_linearize(Problem* pr, const double* z_lin, cudaStream_t st, const double* mu = nullptr,
+                            int keep = LIN_FULL);
 // Operator applies on one precision's data (T = double or float). For BK_OP_KKT, mu_out
 // (nullable, n_x * P of T) receives s B^aT in_lambda, the operator's transposed product.
 bk_status op_apply(Problem* pr, OpData& d, int op, const void* in, void* out, cudaStream_t st,

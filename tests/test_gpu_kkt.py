@@ -209,3 +209,23 @@ def test_newton_orbit_matches_oracle(N, dtype):
     wq = K.s * K.w
     assert np.sqrt(np.sum(wq * (Ug - Ur) ** 2)) < 1e-9
     assert np.sqrt(np.sum((lg - lr) ** 2 / wq)) < 1e-9 * max(1.0, np.sqrt(np.sum(lr**2 / wq)))
+
+
+@pytest.mark.parametrize("reuse", [1, 2])
+def test_newton_precond_reuse_same_solution(reuse):
+    """Keeping (part of) the preconditioner across steps changes the Krylov path, not the
+    Newton solution: the FP64 solve reaches the same point as with rebuilds every step."""
+    api, lib = _api()
+    N, rf, tf = 256, 1.5, 20.0
+    prob = api.Problem(lib.BK_ORBIT, N, torch.float64, 0.0, tf, (0.01, rf))
+    t, _ = api.Plan(N, t0=0.0, tf=tf).grid()
+    X, U = synth.orbit_guess(t.numpy(), rf, tf)
+    z0 = prob.pack(X, U)
+    z_ref = z0.clone()
+    ref = api.newton_solve(prob, z_ref, tol=1e-12)
+    z = z0.clone()
+    info = api.newton_solve(prob, z, tol=1e-12, precond_reuse=reuse)
+    assert ref["converged"] and info["converged"]
+    assert ref["precond_builds"] == ref["iterations"]
+    assert 1 <= info["precond_builds"] <= info["iterations"]
+    assert (z - z_ref).abs().max().item() < 1e-9
