@@ -13,7 +13,7 @@
 // above is what the rows of P give.) The transpose P^T y = r runs backwards:
 //   y_j = K_j^T r_j + N_j^T rho_j,  rho_{j-1} = rho_j + y_j,  (B-tilde^T y)_j = w_j (y_j/2 + rho_j).
 // Both are affine recurrences sigma_{k+1} = (I + N_k) sigma_k + f_k; they run as a chunked scan:
-// segments of SEG nodes (one thread each, sequential), then levels of blocks of 32 scanned by
+// segments of SEG nodes (one thread each, sequential; SEG = Seg<T>::v), then levels of blocks of 32 scanned by
 // warps. The matrix parts of every level's maps depend only on the linearisation and are formed
 // in bk_linearize; the backward maps are their transposes.
 #include <math.h>
@@ -29,6 +29,7 @@ namespace bk {
 // ---------------------------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------------------------
+template <int SEG>
 __device__ __forceinline__ int64_t il_index(int64_t k, int c, int NC) {
   // interleaved per-node storage: node k = seg * SEG + i, seg = W * 32 + lane
   const int64_t seg = k / SEG;
@@ -122,8 +123,8 @@ __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, 
     node_factors<KIND, NX>(x, u, 0.5 * s * w[k], K, Nm);
 #pragma unroll
     for (int c = 0; c < NX * NX; ++c) {
-      Kn[il_index(k, c, NX * NX)] = (T)K[c];
-      Nn[il_index(k, c, NX * NX)] = (T)Nm[c];
+      Kn[il_index<Seg<T>::v>(k, c, NX * NX)] = (T)K[c];
+      Nn[il_index<Seg<T>::v>(k, c, NX * NX)] = (T)Nm[c];
     }
 #pragma unroll
     for (int m = 0; m < NX + NU; ++m) xu[m * P + k] = (T)z[m * P + k];
@@ -162,11 +163,12 @@ __global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, double*
   double A[NX * NX], M[NX * NX], R[NX * NX];
 #pragma unroll
   for (int i = 0; i < NX * NX; ++i) A[i] = (i % (NX + 1) == 0) ? 1.0 : 0.0;
+  constexpr int SEG = Seg<T>::v;
   for (int i = 0; i < SEG; ++i) {
     const int64_t k = (int64_t)seg * SEG + i;
     if (k >= L) break;
 #pragma unroll
-    for (int c = 0; c < NX * NX; ++c) M[c] = (double)Nn[il_index(k, c, NX * NX)] + ((c % (NX + 1) == 0) ? 1.0 : 0.0);
+    for (int c = 0; c < NX * NX; ++c) M[c] = (double)Nn[il_index<Seg<T>::v>(k, c, NX * NX)] + ((c % (NX + 1) == 0) ? 1.0 : 0.0);
     mat_mul<NX>(M, A, R);
 #pragma unroll
     for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
@@ -286,8 +288,8 @@ __device__ __forceinline__ void node_step(const T* __restrict__ Kn, const T* __r
   T Km[NX * NX], Nm[NX * NX];
 #pragma unroll
   for (int c = 0; c < NX * NX; ++c) {
-    if (DIR == 1 || want_out) Km[c] = Kn[il_index(k, c, NX * NX)];
-    Nm[c] = Nn[il_index(k, c, NX * NX)];
+    if (DIR == 1 || want_out) Km[c] = Kn[il_index<Seg<T>::v>(k, c, NX * NX)];
+    Nm[c] = Nn[il_index<Seg<T>::v>(k, c, NX * NX)];
   }
   if (DIR == 0) {
     T v[NX];
@@ -369,13 +371,13 @@ __device__ __forceinline__ void warp_scan(const double* __restrict__ m, int64_t 
 template <typename T> struct SweepChunk {
   static constexpr int CH = 32 / (int)sizeof(T);   // nodes per chunk
   static constexpr int TS = CH + 1;                // padded row (bank spread)
-  static_assert(SEG % CH == 0, "segment length must be a multiple of the staging chunk");
+  static_assert(Seg<T>::v % CH == 0, "segment length must be a multiple of the staging chunk");
 };
 
 template <typename T>
 __device__ __forceinline__ void stage_in(const T* __restrict__ src, int64_t P, int nc, int64_t L, int64_t seg0,
                                          int i0, T* __restrict__ tile) {
-  constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS;
+  constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS, SEG = Seg<T>::v;
   const int lane = threadIdx.x & 31;
   for (int c = 0; c < nc; ++c) {
 #pragma unroll
@@ -391,7 +393,7 @@ __device__ __forceinline__ void stage_in(const T* __restrict__ src, int64_t P, i
 template <typename T>
 __device__ __forceinline__ void stage_out(const T* __restrict__ tile, int nc, int64_t P, int64_t L, int64_t seg0,
                                           int i0, T* __restrict__ dst) {
-  constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS;
+  constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS, SEG = Seg<T>::v;
   const int lane = threadIdx.x & 31;
   for (int c = 0; c < nc; ++c) {
 #pragma unroll
@@ -416,7 +418,7 @@ template <typename T, int NX, int DIR>
 __global__ void __launch_bounds__(128) k_sw_up0(const T* __restrict__ Kn, const T* __restrict__ Nn,
                                                 const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
                                                 int64_t L, const T* __restrict__ w, T s, Levels lv) {
-  constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS;
+  constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS, SEG = Seg<T>::v;
   __shared__ SweepTiles<T, NX> tiles[4];
   const int nblk = (lv.n[0] + 31) >> 5;
   const int g = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(128) k_sw_down0(const T* __restrict__ Kn, cons
                                                   int64_t L, const T* __restrict__ w, T s, Levels lv,
                                                   T* __restrict__ out, T* __restrict__ bout) {
   constexpr int NC = NX * NX;
-  constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS;
+  constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS, SEG = Seg<T>::v;
   __shared__ SweepTiles<T, NX> tiles[4];
   const int nblk0 = (lv.n[0] + 31) >> 5;
   const int g = blockIdx.x * 4 + (threadIdx.x >> 5);
@@ -611,6 +613,8 @@ static Levels levels_of(const Problem* pr, const OpData& d) {
 // nlev + 1 launches: the level-0 up pass, one scan per upper level, the down pass.
 template <typename T, int NX, int DIR>
 static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* out, T* bout, cudaStream_t st) {
+  // segment length and level data follow the problem's working precision
+  BK_ARG(d.dtype == pr->dtype && d.Kn != nullptr, "sweeps run in the problem's working precision only");
   const T s = (T)pr->s;
   const T* w = (const T*)d.w;
   const Levels lv = levels_of(pr, d);
@@ -969,16 +973,21 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
   BK_TRY(dmalloc(&d.xu, es * (nx + nu) * P));
   BK_TRY(dmalloc(&d.mu, es * nx * P));
   d.w = dtype == BK_F64 ? (void*)d.plan->w64 : d.plan->wT;
-  const int64_t il = (int64_t)round_up(pr->nseg, 32) * SEG * nx * nx;
-  BK_TRY(dmalloc(&d.Kn, es * il));
-  BK_TRY(dmalloc(&d.Nn, es * il));
-  for (int l = 0; l < pr->nlev; ++l) {
+  // preconditioner data only in the working precision (an FP32 problem's FP64 side serves the
+  // residual and the refinement products)
+  const bool pre = dtype == pr->dtype;
+  const int64_t il = (int64_t)round_up(pr->nseg, 32) * seg_nodes(pr->dtype) * nx * nx;
+  if (pre) {
+    BK_TRY(dmalloc(&d.Kn, es * il));
+    BK_TRY(dmalloc(&d.Nn, es * il));
+  }
+  for (int l = 0; pre && l < pr->nlev; ++l) {
     const size_t npad = (size_t)round_up(pr->lvn[l], 32);
     BK_TRY(dmalloc((void**)&d.lvm[l], sizeof(double) * NSLOT * npad * nx * nx));
     BK_TRY(dmalloc((void**)&d.lve[l], sizeof(double) * npad * nx));
     if (l > 0) BK_TRY(dmalloc((void**)&d.lvo[l], sizeof(double) * npad * nx));
   }
-  if (ne > 0) {
+  if (pre && ne > 0) {
     BK_TRY(dmalloc(&d.Zc, es * ne * nx * P));
     BK_TRY(dmalloc(&d.HWc, es * ne * nu * P));
     BK_TRY(dmalloc(&d.Qc, es * ne * nx * P));
@@ -1349,7 +1358,8 @@ static bk_status problem_create(Problem** out, int kind, const double* params, i
     pr->x0[0] = nparams >= 1 ? params[0] : 1.0;
     pr->has_cost = false;
   }
-  pr->nseg = (int)((pr->L + SEG - 1) / SEG);
+  const int seg = seg_nodes(dtype);  // sweeps run in the working precision only
+  pr->nseg = (int)((pr->L + seg - 1) / seg);
   pr->nlev = 1;
   pr->lvn[0] = pr->nseg;
   while (pr->lvn[pr->nlev - 1] > 32 && pr->nlev < MAXLEV) {
