@@ -229,11 +229,24 @@ def run_newton(args, rank, world, dist):
     e2e_ms = max_over_ranks(sum(e2e_times) / len(e2e_times), dist)
     nbytes = z0.numel() * z0.element_size()
     last = infos[-1]
+    err = None
+    if dtype == torch.float32:
+        # trajectory error of the FP32-inner solve against an FP64 solve of the same problem
+        # (untimed; the FP64 GPU path itself matches the dense oracle to 1e-9 at small N)
+        p64, _ = make_orbit(N, torch.float64)
+        z64 = z0.clone()
+        api.newton_solve(p64, z64, workspace=api.newton_workspace(p64))
+        X32, U32, _, _ = prob.split(z)
+        X64, U64, _, _ = p64.split(z64)
+        err = {"state_max_abs": float((X32 - X64).abs().max()), "control_max_abs": float((U32 - U64).abs().max()),
+               "state_scale": float(X64.abs().max())}
+        p64.close()
     res = dict(ms=ms_max, launches=launches, clocks=clk.summary(),
                e2e={"value": world * 1000.0 / e2e_ms, "unit": "solves/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
                solve=dict(newton_iterations=last["iterations"], krylov_iterations=last["krylov_iterations"],
-                          kkt_solves=last["kkt_solves"], backtracks=last["backtracks"], residual=last["residual"]))
+                          kkt_solves=last["kkt_solves"], backtracks=last["backtracks"], residual=last["residual"],
+                          error_vs_f64_solve=err))
     return res
 
 
@@ -298,7 +311,7 @@ def run_serve(n_requests, slots, rank=0, world=1, dist=None):
     import torch
     from paper_2509_01855_gb300 import synth
     from paper_2509_01855_gb300.serve import Server, combine_stats, run_schedule, shard_requests
-    srv = Server(dtype=torch.float64, max_slots=slots)
+    srv = Server(dtype=torch.float32, max_slots=slots)   # FP32 Krylov + FP64 Newton residual
     warm = [dict(id=i, arrival=0.0, N=1 << k, rf=1.5, tf=20.0) for i, k in enumerate(range(8, 17))]
     srv.run(warm, realtime=False)
     probe = shard_requests(synth.serving_requests(256, 1.0, "probe"), rank, world)
@@ -314,7 +327,7 @@ def run_serve(n_requests, slots, rank=0, world=1, dist=None):
     st = combine_stats(res, time.perf_counter() - t0, dist)
     iters = [r["newton_iterations"] for r in res if r.get("status") == "ok"]
     srv.close()
-    st.update(offered_rate=rate, closed_loop_max_rate=max_rate, slots=slots, dtype="f64",
+    st.update(offered_rate=rate, closed_loop_max_rate=max_rate, slots=slots, dtype="f32ir",
               newton_iterations_max=int(max(iters)) if iters else None,
               workload="orbit raising, N=2^k k~U{8..16}, r_f~U[1.2,2], t_f~U[10,30], Poisson arrivals")
     return st
@@ -377,7 +390,7 @@ def metric_name(args):
 
 def config(args):
     prec = {"newton_f64": "f64", "newton_f32ir": "f32 Krylov + f64 refinement",
-            "apply_f64": "f64", "apply_f32": "f32", "serve": "f64"}[args.workload]
+            "apply_f64": "f64", "apply_f32": "f32", "serve": "f32ir"}[args.workload]
     c = {"workload": "orbit_raising_newton_krylov" if args.workload.startswith("newton") else "birkhoff_apply",
          "N": 1 << args.N, "nodes": (1 << args.N) + 1, "precision": prec,
          "problem": "polar orbit raising r 1->%.1f, t_f=%g, thrust-vector min-energy, x0=(1,0,0,1)" % (RF, TF),
@@ -395,7 +408,7 @@ def main():
     rank, world, dist = dist_setup(args)
     hbm_peak, peak_kind = read_peaks()
     N = 1 << args.N
-    dtype_name = "f64" if args.workload in ("newton_f64", "apply_f64", "serve") else "f32"
+    dtype_name = "f64" if args.workload in ("newton_f64", "apply_f64") else "f32"
     line = {"metric": metric_name(args), "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype_name, "data": "synthetic", "config": config(args)}
@@ -411,7 +424,7 @@ def main():
                     e2e={"value": st["solves_per_s"], "unit": "solves/s", "h2d_bytes_per_step": None,
                          "d2h_bytes_per_step": None, "note": "latency = solution on host - arrival"})
         line["config"]["workload"] = "serving"
-        dt = torch.float64
+        dt = torch.float32
     elif args.workload.startswith("newton"):
         r = run_newton(args, rank, world, dist)
         line.update(value=world * 1000.0 / r["ms"], unit="solves/s", ms_per_step=r["ms"], e2e=r["e2e"],
@@ -435,7 +448,7 @@ def main():
         peak, unit, achieved = hbm_peak, "GB/s", abytes / ams / 1e6
         bound = "hbm"
     line["roofline"] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                        "frac": achieved / peak, "traffic": recorded_traffic(dtype_name if args.workload != "serve" else "f64", N),
+                        "frac": achieved / peak, "traffic": recorded_traffic(dtype_name, N),
                         "traffic_source": os.path.relpath(TRAFFIC_DOC, os.path.dirname(os.path.abspath(__file__))),
                         "kernel": "birkhoff_apply N=2^%d x4 components (%s)" % (args.N, dtype_name),
                         "algorithmic": {"bytes": abytes, "flops": aflops},

@@ -58,40 +58,42 @@ static inline int nblk(int64_t n, int t = 256) { return (int)std::max<int64_t>(1
 // ---------------------------------------------------------------------------------------------
 // Linearisation kernels (FP64 arithmetic, results stored in T)
 // ---------------------------------------------------------------------------------------------
-template <int KIND, int NX>
-__device__ void node_factors(const double* x, const double* u, double h, double* K, double* Nm) {
-  double Jx[NXM * NXM], Ju[NXM * NUM];
-  Dyn<KIND>::template jac<double>(x, u, Jx, Ju);
+// Node factors in the compute type Tc: FP64 for FP64 problems; FP32 for FP32 problems, whose
+// preconditioner works to FP32 accuracy anyway (the level products stay FP64).
+template <typename Tc, int KIND, int NX>
+__device__ void node_factors(const Tc* x, const Tc* u, Tc h, Tc* K, Tc* Nm) {
+  Tc Jx[NXM * NXM], Ju[NXM * NUM];
+  Dyn<KIND>::template jac<Tc>(x, u, Jx, Ju);
   // A = I - h J; K = A^{-1} by Gauss-Jordan with partial pivoting
-  double A[NX * NX], Inv[NX * NX];
+  Tc A[NX * NX], Inv[NX * NX];
 #pragma unroll
   for (int r = 0; r < NX; ++r)
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
-      A[r * NX + c] = (r == c ? 1.0 : 0.0) - h * Jx[r * NX + c];
-      Inv[r * NX + c] = r == c ? 1.0 : 0.0;
+      A[r * NX + c] = (r == c ? Tc(1) : Tc(0)) - h * Jx[r * NX + c];
+      Inv[r * NX + c] = r == c ? Tc(1) : Tc(0);
     }
 #pragma unroll
   for (int c = 0; c < NX; ++c) {
     int piv = c;
-    double best = fabs(A[c * NX + c]);
+    Tc best = fabs((Tc)A[c * NX + c]);
 #pragma unroll
     for (int r = c + 1; r < NX; ++r)
-      if (fabs(A[r * NX + c]) > best) { best = fabs(A[r * NX + c]); piv = r; }
+      if (fabs((Tc)A[r * NX + c]) > best) { best = fabs((Tc)A[r * NX + c]); piv = r; }
     if (piv != c) {
 #pragma unroll
       for (int q = 0; q < NX; ++q) {
-        double t = A[c * NX + q]; A[c * NX + q] = A[piv * NX + q]; A[piv * NX + q] = t;
+        Tc t = A[c * NX + q]; A[c * NX + q] = A[piv * NX + q]; A[piv * NX + q] = t;
         t = Inv[c * NX + q]; Inv[c * NX + q] = Inv[piv * NX + q]; Inv[piv * NX + q] = t;
       }
     }
-    const double ip = 1.0 / A[c * NX + c];
+    const Tc ip = Tc(1) / A[c * NX + c];
 #pragma unroll
     for (int q = 0; q < NX; ++q) { A[c * NX + q] *= ip; Inv[c * NX + q] *= ip; }
 #pragma unroll
     for (int r = 0; r < NX; ++r) {
       if (r == c) continue;
-      const double f = A[r * NX + c];
+      const Tc f = A[r * NX + c];
 #pragma unroll
       for (int q = 0; q < NX; ++q) { A[r * NX + q] -= f * A[c * NX + q]; Inv[r * NX + q] -= f * Inv[c * NX + q]; }
     }
@@ -103,10 +105,10 @@ __device__ void node_factors(const double* x, const double* u, double h, double*
   for (int r = 0; r < NX; ++r)
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
-      double a = 0;
+      Tc a = Tc(0);
 #pragma unroll
       for (int q = 0; q < NX; ++q) a += Jx[r * NX + q] * Inv[q * NX + c];
-      Nm[r * NX + c] = 2.0 * h * a;
+      Nm[r * NX + c] = Tc(2) * h * a;
     }
 }
 
@@ -114,13 +116,13 @@ template <typename T, int KIND, int NX, int NU>
 __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, const double* __restrict__ w,
                             double s, T* __restrict__ Kn, T* __restrict__ Nn, T* __restrict__ xu) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
-    double x[NXM], u[NUM];
+    T x[NXM], u[NUM];
 #pragma unroll
-    for (int m = 0; m < NX; ++m) x[m] = z[m * P + k];
+    for (int m = 0; m < NX; ++m) x[m] = (T)z[m * P + k];
 #pragma unroll
-    for (int q = 0; q < NU; ++q) u[q] = z[(NX + q) * P + k];
-    double K[NX * NX], Nm[NX * NX];
-    node_factors<KIND, NX>(x, u, 0.5 * s * w[k], K, Nm);
+    for (int q = 0; q < NU; ++q) u[q] = (T)z[(NX + q) * P + k];
+    T K[NX * NX], Nm[NX * NX];
+    node_factors<T, KIND, NX>(x, u, (T)(0.5 * s * w[k]), K, Nm);
 #pragma unroll
     for (int c = 0; c < NX * NX; ++c) {
       Kn[il_index<Seg<T>::v>(k, c, NX * NX)] = (T)K[c];
@@ -142,13 +144,13 @@ __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, 
 __device__ __forceinline__ int64_t il32(int64_t i, int c, int NC) { return (((i >> 5) * NC + c) << 5) + (i & 31); }
 
 // C = A B (n_x x n_x, row-major)
-template <int NX>
-__device__ __forceinline__ void mat_mul(const double* A, const double* B, double* C) {
+template <int NX, typename Tm = double>
+__device__ __forceinline__ void mat_mul(const Tm* A, const Tm* B, Tm* C) {
 #pragma unroll
   for (int r = 0; r < NX; ++r)
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
-      double a = 0;
+      Tm a = 0;
 #pragma unroll
       for (int q = 0; q < NX; ++q) a += A[r * NX + q] * B[q * NX + c];
       C[r * NX + c] = a;
@@ -160,21 +162,23 @@ template <typename T, int NX>
 __global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, double* __restrict__ A0) {
   const int seg = blockIdx.x * blockDim.x + threadIdx.x;
   if (seg >= nseg) return;
-  double A[NX * NX], M[NX * NX], R[NX * NX];
+  // products over one segment in the working type (16 FP32 factors keep FP32 accuracy); the
+  // level products above are FP64
+  T A[NX * NX], M[NX * NX], R[NX * NX];
 #pragma unroll
-  for (int i = 0; i < NX * NX; ++i) A[i] = (i % (NX + 1) == 0) ? 1.0 : 0.0;
+  for (int i = 0; i < NX * NX; ++i) A[i] = (i % (NX + 1) == 0) ? T(1) : T(0);
   constexpr int SEG = Seg<T>::v;
   for (int i = 0; i < SEG; ++i) {
     const int64_t k = (int64_t)seg * SEG + i;
     if (k >= L) break;
 #pragma unroll
-    for (int c = 0; c < NX * NX; ++c) M[c] = (double)Nn[il_index<Seg<T>::v>(k, c, NX * NX)] + ((c % (NX + 1) == 0) ? 1.0 : 0.0);
-    mat_mul<NX>(M, A, R);
+    for (int c = 0; c < NX * NX; ++c) M[c] = Nn[il_index<Seg<T>::v>(k, c, NX * NX)] + ((c % (NX + 1) == 0) ? T(1) : T(0));
+    mat_mul<NX, T>(M, A, R);
 #pragma unroll
     for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
   }
 #pragma unroll
-  for (int c = 0; c < NX * NX; ++c) A0[il32(seg, c, NX * NX)] = A[c];
+  for (int c = 0; c < NX * NX; ++c) A0[il32(seg, c, NX * NX)] = (double)A[c];
 }
 
 // Slots of one level, one warp per block of 32 items (items at or beyond n are identity maps):
