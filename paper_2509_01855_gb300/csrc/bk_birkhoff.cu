@@ -225,6 +225,63 @@ __device__ __forceinline__ typename V2<T>::t load_z(const T* __restrict__ src, i
   return mk2<T>(load_x<T, K>(src, i1, N, invN, Y0, tb), load_x<T, K>(src, i2, N, invN, Y0, tb));
 }
 
+// Split DCT-I (four-step plans): the DCT-I of length N+1 of x is, at even indices, the DCT-I of
+// length M+1 (M = N/2) of the pair sums a_i = x_i + x_{N-i} (a_M = 2 x_M) and, at odd indices
+// 2m+1, the DCT-III of length M, sum_{i<M} u_i cos(pi i (2m+1) / (2M)), of the pair differences
+// u_0 = x_0 - x_N, u_i = 2 (x_i - x_{N-i}). Pass-A load modes:
+//   PM_FULL : the unsplit length-N FFT input (load_z)
+//   PM_PAIR : z_j of the length-M DCT-I of the pair sums (n = M)
+//   PM_DCT3 : conj Z_k (k < n = M/2) of the DCT-III by a length-M/2 inverse FFT (Makhoul):
+//             H_0 = u_0, H_k = e^{i theta k} (u_k - i u_{M-k}) / 2 (theta = pi / (2M) = pi / N,
+//             u_M = 0), Z_k = (H_k + conj H_{M/2-k}) + i e^{2 pi i k / M} (H_k - conj H_{M/2-k});
+//             the inverse FFT runs as conj(FFT(conj Z)).
+enum { PM_FULL = 0, PM_PAIR = 1, PM_DCT3 = 2 };
+
+template <typename T, int K>
+__device__ __forceinline__ T pair_sum(const T* __restrict__ src, int i, int Ns) {
+  // a_i = x_i + x_{Ns-i}; IN_WINV halves interior samples (i = 0 pairs the two end samples)
+  const T a = src[i] + src[Ns - i];
+  return (K == IN_WINV && i != 0) ? T(0.5) * a : a;
+}
+
+template <typename T, int K>
+__device__ __forceinline__ typename V2<T>::t load_z_pair(const T* __restrict__ src, int j, int n, StencilTab<T> tb) {
+  const int Ns = 2 * n;
+  const int m1 = 2 * j, m2 = 2 * j + 1;
+  const int i1 = m1 <= n ? m1 : 2 * n - m1;
+  const int i2 = m2 <= n ? m2 : 2 * n - m2;
+  return mk2<T>(pair_sum<T, K>(src, i1, Ns), pair_sum<T, K>(src, i2, Ns));
+}
+
+// H_k of the DCT-III input (see above), with the factors folded: for k >= 1 every sample is an
+// interior one, so H_k = c e^{i theta k} ((x_k - x_{N-k}) - i (x_{M-k} - x_{M+k})) with c = 1
+// (IN_PLAIN) or 1/2 (IN_WINV halves interior samples); H_0 = u_0 = W-scaled x_0 - x_N.
+template <typename T, int K>
+__device__ __forceinline__ typename V2<T>::t dct3_H(const T* __restrict__ src, int i, int M,
+                                                   const typename V2<T>::t* __restrict__ tpost) {
+  const int N = 2 * M;
+  if (i == 0) return mk2<T>(src[0] - src[N], T(0));
+  const T a = src[i] - src[N - i], b = src[M - i] - src[M + i];
+  typename V2<T>::t cs = tpost[i];  // (cos, sin)(pi i / N)
+  if (K == IN_WINV) { cs.x *= T(0.5); cs.y *= T(0.5); }
+  return mk2<T>(a * cs.x + b * cs.y, a * cs.y - b * cs.x);
+}
+
+template <typename T, int K>
+__device__ __forceinline__ typename V2<T>::t load_z_dct3(const T* __restrict__ src, int k, int n,
+                                                        const typename V2<T>::t* __restrict__ tpost,
+                                                        const typename V2<T>::t* __restrict__ eo, StencilTab<T> tb) {
+  typedef typename V2<T>::t C;
+  const int M = 2 * n;
+  const C Hk = dct3_H<T, K>(src, k, M, tpost);
+  const C Hm = dct3_H<T, K>(src, n - k, M, tpost);  // H_{M/2 - k}; conj taken below
+  const C E = mk2<T>(Hk.x + Hm.x, Hk.y - Hm.y);
+  const C D = mk2<T>(Hk.x - Hm.x, Hk.y + Hm.y);
+  const C w = eo[k];  // omega_M^k; e^{2 pi i k / M} = conj w
+  const C O = mk2<T>(D.x * w.x + D.y * w.y, D.y * w.x - D.x * w.y);
+  return mk2<T>(E.x - O.y, -(E.y + O.x));
+}
+
 // Real-FFT split: from Z_k, Z_{N-k} and (cos, sin)(pi kk / N), kk = min(k, N - k).
 template <typename T>
 __device__ __forceinline__ void split_pair(typename V2<T>::t zk, typename V2<T>::t zc,
@@ -324,14 +381,15 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
 // Pass B: per CTA, P row pairs {p, N1 - p} (p = 0 pairs rows 0 and N1/2); FFT over j2 (length
 //         N2), real-FFT split, epilogue.
 // ---------------------------------------------------------------------------------------------
-template <typename T, int K>
-__global__ void __launch_bounds__(MaxThr<T>::v)
-    k_passA(const T* __restrict__ src, int64_t src_stride, typename V2<T>::t* __restrict__ Aout,
+template <typename T, int K, int MODE>
+__device__ __forceinline__ void passA_body(
+            int bid, int nbid, const T* __restrict__ src, int64_t src_stride, typename V2<T>::t* __restrict__ Aout,
             T* __restrict__ partial, int N, int N1, int log2N1, int N2, int NB, int bs,
             const typename V2<T>::t* __restrict__ stw,
             const typename V2<T>::t* __restrict__ twN, T invN, StencilTab<T> tb,
             const typename V2<T>::t* __restrict__ twLo,
-            const typename V2<T>::t* __restrict__ twHi, int tw_h) {
+            const typename V2<T>::t* __restrict__ twHi, int tw_h,
+            const typename V2<T>::t* __restrict__ tpost, const typename V2<T>::t* __restrict__ eo) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem[];
   C* buf = reinterpret_cast<C*>(smem);
@@ -342,14 +400,15 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
   __shared__ T red[32];
   const int vec = blockIdx.y;
   const T* x = src + (int64_t)vec * src_stride;
-  const int c0 = blockIdx.x * NB;
+  const int c0 = bid * NB;
   const int log2NB = __ffs(NB) - 1, log2N2 = __ffs(N2) - 1;  // NB, N2 are powers of two
   // The stage buffer read by the second DCT already holds Y / N (forward) or Y - Y0
   // (transpose), so its stencils run with scale 1 and Y0 = 0 (constants the compiler folds).
   const T Y0 = T(0);
   const T sc = K == ST_FWD ? T(1) : invN;
-  // DC partials: consumed after IN_WINV (the transposed stage) and ST_FWD (the forward output)
-  constexpr bool DC = K == IN_WINV || K == ST_FWD;
+  // DC partials: consumed after IN_WINV (the transposed stage) and ST_FWD (the forward output);
+  // in split plans the DC value is the even half's (the DCT-III has none)
+  constexpr bool DC = (K == IN_WINV || K == ST_FWD) && MODE != PM_DCT3;
   T dc = T(0);
   const int total = NB * N1;
   // 4 independent element loads in flight per thread before the shared-memory stores
@@ -361,7 +420,9 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
       if (idx < total) {
         const int b = idx & (NB - 1);
         const int j = ((idx >> log2NB) << log2N2) + c0 + b;
-        z[u] = load_z<T, K>(x, j, N, sc, Y0, tb);
+        if (MODE == PM_FULL) z[u] = load_z<T, K>(x, j, N, sc, Y0, tb);
+        else if (MODE == PM_PAIR) z[u] = load_z_pair<T, K>(x, j, N, tb);
+        else z[u] = load_z_dct3<T, K>(x, j, N, tpost, eo, tb);
       }
     }
 #pragma unroll
@@ -382,7 +443,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
   if (DC && threadIdx.x < 32) {
     T a = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (threadIdx.x == 0) partial[(int64_t)vec * gridDim.x + blockIdx.x] = a;
+    if (threadIdx.x == 0) partial[(int64_t)vec * nbid + bid] = a;
   }
   fft16<T>(buf, N1, log2N1, NB, bs, smem_tw ? tws : stw);
   C* A = Aout + (int64_t)vec * N;
@@ -396,6 +457,35 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
     const C w = sizeof(T) == 8 ? __ldg(&twN[m]) : cmul(__ldg(&twHi[m >> tw_h]), __ldg(&twLo[m & ((1 << tw_h) - 1)]));
     A[(int64_t)k1 * N2 + j2] = cmul(buf[b * bs + padi(k1)], w);
   }
+}
+
+#define BK_PASSA_PARAMS(S)                                                                           \
+  const T* __restrict__ src##S, int64_t src_stride##S, typename V2<T>::t* __restrict__ Aout##S,              \
+      T* __restrict__ partial##S, int N##S, int N1##S, int log2N1##S, int N2##S, int NB##S, int bs##S,      \
+      const typename V2<T>::t* __restrict__ stw##S, const typename V2<T>::t* __restrict__ twN##S,           \
+      const typename V2<T>::t* __restrict__ twLo##S, const typename V2<T>::t* __restrict__ twHi##S, int tw_h##S
+#define BK_PASSA_ARGS(S)                                                                             \
+  src##S, src_stride##S, Aout##S, partial##S, N##S, N1##S, log2N1##S, N2##S, NB##S, bs##S, stw##S, twN##S
+#define BK_PASSA_TAIL(S) twLo##S, twHi##S, tw_h##S
+
+// Pass A of one transform (unsplit, or one half of a split DCT-I).
+template <typename T, int K, int MODE = PM_FULL>
+__global__ void __launch_bounds__(MaxThr<T>::v)
+    k_passA(BK_PASSA_PARAMS(), T invN, StencilTab<T> tb, const typename V2<T>::t* __restrict__ tpost = nullptr,
+            const typename V2<T>::t* __restrict__ eo = nullptr) {
+  passA_body<T, K, MODE>(blockIdx.x, gridDim.x, BK_PASSA_ARGS(), invN, tb, BK_PASSA_TAIL(), tpost, eo);
+}
+
+// Pass A of both halves of a split DCT-I in one launch: CTAs [0, gE) run the even half (pair
+// sums), the rest the odd half (DCT-III); one launch fills the GPU better than two smaller ones.
+template <typename T, int K>
+__global__ void __launch_bounds__(MaxThr<T>::v)
+    k_passA_split(int gE, BK_PASSA_PARAMS(E), BK_PASSA_PARAMS(O), T invN, StencilTab<T> tb,
+                  const typename V2<T>::t* __restrict__ tpost, const typename V2<T>::t* __restrict__ eo) {
+  if ((int)blockIdx.x < gE)
+    passA_body<T, K, PM_PAIR>(blockIdx.x, gE, BK_PASSA_ARGS(E), invN, tb, BK_PASSA_TAIL(E), tpost, eo);
+  else
+    passA_body<T, K, PM_DCT3>(blockIdx.x - gE, gridDim.x - gE, BK_PASSA_ARGS(O), invN, tb, BK_PASSA_TAIL(O), tpost, eo);
 }
 
 // Second-DCT input as its own elementwise pass (planned applies): x_m of kind K (ST_FWD with
@@ -443,12 +533,17 @@ __device__ __forceinline__ void ep_write(T* __restrict__ dst, int k, T yk, int N
   else dst[k] = (k == 0 || k == N) ? s * invN * yk : T(2) * s * invN * yk;
 }
 
-template <typename T, int E>
-__global__ void __launch_bounds__(MaxThr<T>::v)
-    k_passB(const typename V2<T>::t* __restrict__ Ain, T* __restrict__ dst, int64_t dst_stride,
+// Pass-B modes: PB_PAIRS, row pairs {p, N1 - p} and the real-FFT split of a DCT-I (outputs at
+// ostride k of a transform of parent size Npar; (cos, sin)(pi k / n) read as tpost[tps k]);
+// PB_ROWS, plain rows of the DCT-III's inverse FFT (outputs unpacked to the odd indices).
+enum { PB_PAIRS = 0, PB_ROWS = 1 };
+
+template <typename T, int E, int MODE>
+__device__ __forceinline__ void passB_body(
+            int bid, const typename V2<T>::t* __restrict__ Ain, T* __restrict__ dst, int64_t dst_stride,
             int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial, int N, int N1,
             int N2, int log2N2, int P, const typename V2<T>::t* __restrict__ stw,
-            const typename V2<T>::t* __restrict__ tpost, T s, T invN) {
+            const typename V2<T>::t* __restrict__ tpost, T s, T invN, int ostride, int tps, int Npar) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem[];
   const int bs = pad_stride(N2);
@@ -460,7 +555,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
   const int vec = blockIdx.y;
   const C* A = Ain + (int64_t)vec * N;
   T* out = dst + (int64_t)vec * dst_stride;
-  const int p0 = blockIdx.x * P;
+  const int p0 = bid * P;
   T Y0 = T(0);
   if (E == EP_STORE_TRN || E == EP_FWD_OUT) {
     T acc = T(0);
@@ -477,7 +572,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
     __syncthreads();
     Y0 = red[0];
   }
-  // load 2P rows: local row q = 2 i (+1) for pair p0 + i
+  // load 2P rows: PB_PAIRS local row q = 2 i (+1) for pair p0 + i; PB_ROWS rows 2 p0 + q
   const int total = 2 * P * N2;
   for (int idx0 = threadIdx.x; idx0 < total; idx0 += 4 * blockDim.x) {
     C z[4];
@@ -486,8 +581,13 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
       const int idx = idx0 + u * blockDim.x;
       if (idx < total) {
         const int q = idx >> log2N2;
-        const int p = p0 + (q >> 1);
-        const int row = (q & 1) == 0 ? p : (p == 0 ? N1 / 2 : N1 - p);
+        int row;
+        if (MODE == PB_ROWS) {
+          row = 2 * p0 + q;
+        } else {
+          const int p = p0 + (q >> 1);
+          row = (q & 1) == 0 ? p : (p == 0 ? N1 / 2 : N1 - p);
+        }
         z[u] = A[((int64_t)row << log2N2) + (idx & (N2 - 1))];
       }
     }
@@ -502,6 +602,23 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
   }
   __syncthreads();
   fft16<T>(buf, N2, log2N2, 2 * P, bs, smem_tw ? tws : stw);
+  if (MODE == PB_ROWS) {
+    // output p = k1 + N1 k2 of the inverse FFT is z_p = conj(result): r_{2p} = Re, r_{2p+1} = -Im;
+    // X_{2j} = r_j, X_{2j+1} = r_{M-1-j} (j < M/2 = N), and Y_{2m+1} = X_m
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int q = idx >> log2N2;
+      const int k2 = idx & (N2 - 1);
+      const C R = buf[q * bs + padi(k2)];
+      const int64_t pz = (int64_t)(2 * p0 + q) + (int64_t)N1 * k2;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int64_t r = 2 * pz + t;
+        const int64_t m = r < N ? 2 * r : 2 * (2 * (int64_t)N - 1 - r) + 1;
+        ep_write<T, E>(out, (int)(2 * m + 1), t == 0 ? R.x : -R.y, Npar, s, Y0, invN);
+      }
+    }
+    return;
+  }
   const int half = N / 2;
   for (int idx = threadIdx.x; idx < P * N2; idx += blockDim.x) {
     const int i = idx >> log2N2;
@@ -514,16 +631,16 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
       if (k2 <= N2 / 2) {
         const int k = N1 * k2;
         T yk, ynk;
-        split_pair<T>(ra[padi(k2)], ra[padi((N2 - k2) & (N2 - 1))], tpost[k], yk, ynk);
-        ep_write<T, E>(out, k, yk, N, s, Y0, invN);
-        if (k != half) ep_write<T, E>(out, N - k, ynk, N, s, Y0, invN);
+        split_pair<T>(ra[padi(k2)], ra[padi((N2 - k2) & (N2 - 1))], tpost[k * tps], yk, ynk);
+        ep_write<T, E>(out, k * ostride, yk, Npar, s, Y0, invN);
+        if (k != half) ep_write<T, E>(out, (N - k) * ostride, ynk, Npar, s, Y0, invN);
       }
       if (k2 < N2 / 2) {
         const int k = N1 / 2 + N1 * k2;
         T yk, ynk;
-        split_pair<T>(rb[padi(k2)], rb[padi(N2 - 1 - k2)], tpost[k], yk, ynk);
-        ep_write<T, E>(out, k, yk, N, s, Y0, invN);
-        ep_write<T, E>(out, N - k, ynk, N, s, Y0, invN);
+        split_pair<T>(rb[padi(k2)], rb[padi(N2 - 1 - k2)], tpost[k * tps], yk, ynk);
+        ep_write<T, E>(out, k * ostride, yk, Npar, s, Y0, invN);
+        ep_write<T, E>(out, (N - k) * ostride, ynk, Npar, s, Y0, invN);
       }
     } else {
       const int k = p + N1 * k2;
@@ -531,23 +648,93 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
       const C zc = rb[padi(N2 - 1 - k2)];
       T yk, ynk;
       if (k <= half) {
-        split_pair<T>(zk, zc, tpost[k], yk, ynk);
+        split_pair<T>(zk, zc, tpost[k * tps], yk, ynk);
       } else {
-        split_pair<T>(zc, zk, tpost[N - k], ynk, yk);
+        split_pair<T>(zc, zk, tpost[(N - k) * tps], ynk, yk);
       }
-      ep_write<T, E>(out, k, yk, N, s, Y0, invN);
-      ep_write<T, E>(out, N - k, ynk, N, s, Y0, invN);
+      ep_write<T, E>(out, k * ostride, yk, Npar, s, Y0, invN);
+      ep_write<T, E>(out, (N - k) * ostride, ynk, Npar, s, Y0, invN);
     }
   }
   // zero the padding of the output vectors (final epilogues only)
-  if ((E == EP_FWD_OUT || E == EP_TRN_OUT) && blockIdx.x == 0) {
-    for (int64_t m = N + 1 + threadIdx.x; m < pitch_zero_to; m += blockDim.x) out[m] = T(0);
+  if ((E == EP_FWD_OUT || E == EP_TRN_OUT) && bid == 0) {
+    for (int64_t m = Npar + 1 + threadIdx.x; m < pitch_zero_to; m += blockDim.x) out[m] = T(0);
   }
+}
+
+#define BK_PASSB_PARAMS(S)                                                                           \
+  const typename V2<T>::t* __restrict__ Ain##S, int N##S, int N1##S, int N2##S, int log2N2##S, int P##S, \
+      const typename V2<T>::t* __restrict__ stw##S
+
+template <typename T, int E, int MODE = PB_PAIRS>
+__global__ void __launch_bounds__(MaxThr<T>::v)
+    k_passB(const typename V2<T>::t* __restrict__ Ain, T* __restrict__ dst, int64_t dst_stride,
+            int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial, int N, int N1,
+            int N2, int log2N2, int P, const typename V2<T>::t* __restrict__ stw,
+            const typename V2<T>::t* __restrict__ tpost, T s, T invN, int ostride, int tps, int Npar) {
+  passB_body<T, E, MODE>(blockIdx.x, Ain, dst, dst_stride, pitch_zero_to, partial, n_partial, N, N1, N2, log2N2, P, stw,
+                         tpost, s, invN, ostride, tps, Npar);
+}
+
+// Pass B of both halves of a split DCT-I in one launch: CTAs [0, gE) the even half's row pairs
+// and real split (outputs at even indices), the rest the odd half's rows (odd indices).
+template <typename T, int E>
+__global__ void __launch_bounds__(MaxThr<T>::v)
+    k_passB_split(int gE, BK_PASSB_PARAMS(E), BK_PASSB_PARAMS(O), T* __restrict__ dst, int64_t dst_stride,
+                  int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial,
+                  const typename V2<T>::t* __restrict__ tpost, T s, T invN, int Npar) {
+  if ((int)blockIdx.x < gE)
+    passB_body<T, E, PB_PAIRS>(blockIdx.x, AinE, dst, dst_stride, pitch_zero_to, partial, n_partial, NE, N1E, N2E,
+                               log2N2E, PE, stwE, tpost, s, invN, 2, 2, Npar);
+  else
+    passB_body<T, E, PB_ROWS>(blockIdx.x - gE, AinO, dst, dst_stride, 0, partial, n_partial, NO, N1O, N2O, log2N2O,
+                              PO, stwO, tpost, s, invN, 1, 1, Npar);
 }
 
 // ---------------------------------------------------------------------------------------------
 // Plan creation / destruction and the apply entry points
 // ---------------------------------------------------------------------------------------------
+// Stage tables and the inter-pass twiddle table of one four-step layout.
+template <typename T>
+static bk_status build_fs_tables(FourStep& f, cudaStream_t st) {
+  typedef typename V2<T>::t C;
+  for (int w = 0; w < 2; ++w) {
+    const int n = w == 0 ? f.N1 : f.N2;
+    void** dst = w == 0 ? &f.stw1 : &f.stw2;
+    const int len = stage_tw_len(ilog2(n));
+    if (len == 0) continue;
+    BK_TRY(dmalloc(dst, sizeof(C) * len));
+    k_stage_tw<T><<<(len + 255) / 256, 256, 0, st>>>((C*)*dst, ilog2(n), len);
+    BK_CHECK_LAUNCH();
+  }
+  const int64_t n = f.n;
+  if (sizeof(T) == 8) {
+    BK_TRY(dmalloc(&f.twN, sizeof(C) * n));
+    k_tw_table<T><<<(int)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, st>>>((C*)f.twN, n, (double)n);
+    BK_CHECK_LAUNCH();
+  } else {
+    const int log2n = ilog2(n);
+    f.tw_h = (log2n + 1) / 2;
+    const int64_t nlo = int64_t(1) << f.tw_h, nhi = n >> f.tw_h;
+    BK_TRY(dmalloc(&f.twLo, sizeof(C) * nlo));
+    BK_TRY(dmalloc(&f.twHi, sizeof(C) * nhi));
+    k_tw_table<T><<<(int)((nlo + 255) / 256), 256, 0, st>>>((C*)f.twLo, nlo, (double)n);
+    BK_CHECK_LAUNCH();
+    k_tw_table_strided<T><<<(int)((nhi + 255) / 256), 256, 0, st>>>((C*)f.twHi, nhi, nlo, (double)n);
+    BK_CHECK_LAUNCH();
+  }
+  return BK_OK;
+}
+
+static void free_fs(FourStep& f) {
+  dfree(f.stw1);
+  dfree(f.stw2);
+  dfree(f.twN);
+  dfree(f.twLo);
+  dfree(f.twHi);
+  f = FourStep();
+}
+
 template <typename T>
 static bk_status build_tables(Plan* p, cudaStream_t st) {
   typedef typename V2<T>::t C;
@@ -566,10 +753,17 @@ static bk_status build_tables(Plan* p, cudaStream_t st) {
     BK_TRY(dmalloc(&p->tw, sizeof(C) * N));
     k_tw_table<T><<<(int)std::min<int64_t>((N + 255) / 256, 4096), 256, 0, st>>>((C*)p->tw, N, (double)N);
     BK_CHECK_LAUNCH();
-    if (N >= 16) BK_TRY(stage_table(&p->stw1, N));
+    if (N >= 16) BK_TRY(stage_table(&p->stwS, N));
   } else {
-    BK_TRY(stage_table(&p->stw1, p->N1));
-    BK_TRY(stage_table(&p->stw2, p->N2));
+    BK_TRY(build_fs_tables<T>(p->fs, st));
+    if (p->split) {
+      BK_TRY(build_fs_tables<T>(p->fso, st));
+      const int64_t M = N / 2;
+      BK_TRY(dmalloc(&p->eo, sizeof(C) * (M / 2)));
+      // exp(+2 pi i k / M) = conj(omega_M^k)
+      k_tw_table<T><<<(int)std::min<int64_t>((M / 2 + 255) / 256, 4096), 256, 0, st>>>((C*)p->eo, M / 2, (double)M);
+      BK_CHECK_LAUNCH();
+    }
   }
   BK_TRY(dmalloc(&p->rk, sizeof(T) * (N + 2)));
   k_rk_table<T><<<(int)std::min<int64_t>((N + 2 + 255) / 256, 4096), 256, 0, st>>>((T*)p->rk, N + 2);
@@ -577,23 +771,6 @@ static bk_status build_tables(Plan* p, cudaStream_t st) {
   BK_TRY(dmalloc(&p->tpost, sizeof(C) * (N / 2 + 1)));
   k_post_table<T><<<(int)std::min<int64_t>((N / 2 + 256) / 256, 4096), 256, 0, st>>>((C*)p->tpost, N);
   BK_CHECK_LAUNCH();
-  if (!p->small) {
-    if (sizeof(T) == 8) {
-      BK_TRY(dmalloc(&p->twN, sizeof(C) * N));
-      k_tw_table<T><<<(int)std::min<int64_t>((N + 255) / 256, 8192), 256, 0, st>>>((C*)p->twN, N, (double)N);
-      BK_CHECK_LAUNCH();
-    } else {
-      const int log2N = ilog2(N);
-      p->tw_h = (log2N + 1) / 2;
-      const int64_t nlo = int64_t(1) << p->tw_h, nhi = N >> p->tw_h;
-      BK_TRY(dmalloc(&p->twLo, sizeof(C) * nlo));
-      BK_TRY(dmalloc(&p->twHi, sizeof(C) * nhi));
-      k_tw_table<T><<<(int)((nlo + 255) / 256), 256, 0, st>>>((C*)p->twLo, nlo, (double)N);
-      BK_CHECK_LAUNCH();
-      k_tw_table_strided<T><<<(int)((nhi + 255) / 256), 256, 0, st>>>((C*)p->twHi, nhi, nlo, (double)N);
-      BK_CHECK_LAUNCH();
-    }
-  }
   return BK_OK;
 }
 
@@ -665,37 +842,61 @@ static int fourstep_elems(int dtype) {
   return cap;
 }
 
-static bk_status configure_fourstep(Plan* p) {
-  const int log2N = ilog2(p->N);
-  p->N1 = 1 << (log2N / 2);
-  p->N2 = 1 << (log2N - log2N / 2);
-  const size_t csz = 2 * dtype_size(p->dtype);
-  const int E = fourstep_elems(p->dtype);
+// Smallest log2 N planned with the split DCT-I: 2^19 in FP64, 2^21 in FP32 (BK_SPLIT_MIN_LOG2
+// overrides both for tuning; 30 disables the split). Below them the half-size launches fill the
+// GPU poorly. Measured products, 2^20 x 4 components: FP64 1.21 split vs 1.35 ms unsplit, FP32
+// 0.235 vs 0.219; at 2^18 FP64 0.47 vs 0.39; at 2^22 FP32 0.80 vs 0.88. FP64 at 2^24 needs the
+// split (the unsplit length-2^24 FFT exceeds the FP64 four-step shapes).
+static int split_min_log2(int dtype) {
+  const char* e = getenv("BK_SPLIT_MIN_LOG2");
+  if (e) {
+    const long v = atol(e);
+    if (v >= 13 && v <= 30) return (int)v;
+  }
+  return dtype == BK_F64 ? 19 : 21;
+}
+
+static bk_status configure_fourstep(FourStep& f, int64_t n, int dtype) {
+  const int log2n = ilog2(n);
+  f = FourStep();
+  f.n = n;
+  // balanced factors, with the rows short enough for one row pair per CTA (2 N2 / 16 threads)
+  // and the columns for one column per CTA (N1 / 16 threads) under the thread cap
+  const int maxthr = dtype == BK_F64 ? 256 : 512;
+  int l2 = log2n - log2n / 2;
+  while (l2 > 0 && (2 << l2) / 16 > maxthr) --l2;
+  f.N2 = 1 << l2;
+  f.N1 = 1 << (log2n - l2);
+  if (f.N1 / 16 > maxthr) {
+    set_error("four-step configuration failed for n=%lld (transform too long for this precision)", (long long)n);
+    return BK_ERR_UNSUPPORTED;
+  }
+  const size_t csz = 2 * dtype_size(dtype);
+  const int E = fourstep_elems(dtype);
   // pass A: NB columns of N1; pass B: P row pairs (2P rows) of N2
-  int NB = std::max(1, E / p->N1);
-  if (NB > p->N2) NB = p->N2;
-  int P = std::max(1, E / (2 * p->N2));
-  if (P > p->N1 / 2) P = p->N1 / 2;
-  p->NB = NB;
-  p->P = P;
+  int NB = std::max(1, E / f.N1);
+  if (NB > f.N2) NB = f.N2;
+  int P = std::max(1, E / (2 * f.N2));
+  if (P > f.N1 / 2) P = f.N1 / 2;
+  f.NB = NB;
+  f.P = P;
   // Pass-A batch stride: when a warp's FFT stays inside one batch (N1 / 16 >= 32 threads), the
   // column-major tile accesses of the load and store phases (lane -> column idx mod NB, row
   // idx / NB) hit distinct banks if the stride is = W / NB modulo the W complex elements of a
   // 128-byte wavefront.
   const int W = (int)(128 / csz);
-  const int padA = (p->N1 / 16 >= 32 && NB < W) ? W / NB : 1;
-  p->bsA = p->N1 + p->N1 / 16 + padA;
-  p->smemA = csz * ((size_t)NB * p->bsA + (p->dtype == BK_F32 ? p->N1 : 0));
-  p->smemB = csz * ((size_t)2 * P * pad_stride(p->N2) + (p->dtype == BK_F32 ? p->N2 : 0));
-  p->thrA = round_threads((int64_t)NB * p->N1 / 16);
-  p->thrB = round_threads((int64_t)2 * P * p->N2 / 16);
-  const int maxthr = p->dtype == BK_F64 ? 256 : 512;
-  if ((int64_t)NB * p->N1 / 16 > maxthr || (int64_t)2 * P * p->N2 / 16 > maxthr || p->smemA > FOURSTEP_SMEM_BUDGET ||
-      p->smemB > FOURSTEP_SMEM_BUDGET) {
-    set_error("four-step configuration failed for N=%lld", (long long)p->N);
+  const int padA = (f.N1 / 16 >= 32 && NB < W) ? W / NB : 1;
+  f.bsA = f.N1 + f.N1 / 16 + padA;
+  f.smemA = csz * ((size_t)NB * f.bsA + (dtype == BK_F32 ? f.N1 : 0));
+  f.smemB = csz * ((size_t)2 * P * pad_stride(f.N2) + (dtype == BK_F32 ? f.N2 : 0));
+  f.thrA = round_threads((int64_t)NB * f.N1 / 16);
+  f.thrB = round_threads((int64_t)2 * P * f.N2 / 16);
+  if ((int64_t)NB * f.N1 / 16 > maxthr || (int64_t)2 * P * f.N2 / 16 > maxthr || f.smemA > FOURSTEP_SMEM_BUDGET ||
+      f.smemB > FOURSTEP_SMEM_BUDGET) {
+    set_error("four-step configuration failed for n=%lld", (long long)n);
     return BK_ERR_UNSUPPORTED;
   }
-  p->nPartA = p->N2 / p->NB;
+  f.nPartA = f.N2 / f.NB;
   return BK_OK;
 }
 
@@ -728,6 +929,12 @@ static bk_status set_smem_attrs(const Plan* p) {
     BK_TRY(smem_attr(k_passB<T, EP_STORE_TRN>, cap));
     BK_TRY(smem_attr(k_passB<T, EP_FWD_OUT>, cap));
     BK_TRY(smem_attr(k_passB<T, EP_TRN_OUT>, cap));
+    BK_TRY(smem_attr(k_passA_split<T, IN_PLAIN>, cap));
+    BK_TRY(smem_attr(k_passA_split<T, IN_WINV>, cap));
+    BK_TRY(smem_attr(k_passB_split<T, EP_STORE>, cap));
+    BK_TRY(smem_attr(k_passB_split<T, EP_STORE_TRN>, cap));
+    BK_TRY(smem_attr(k_passB_split<T, EP_FWD_OUT>, cap));
+    BK_TRY(smem_attr(k_passB_split<T, EP_TRN_OUT>, cap));
   }
   return BK_OK;
 }
@@ -763,14 +970,21 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
       p->thrS = round_threads(N / 16);
       if (p->thrS > (dtype == BK_F64 ? 256 : 512)) p->thrS = dtype == BK_F64 ? 256 : 512;
     } else {
-      if ((st_ = configure_fourstep(p)) != BK_OK) break;
+      // split DCT-I from 2^split_min_log2() on: fs the length-N/2 FFT, fso the length-N/4 one
+      p->split = ilog2(N) >= split_min_log2(dtype);
+      if (p->split) {
+        if ((st_ = configure_fourstep(p->fs, N / 2, dtype)) != BK_OK) break;
+        if ((st_ = configure_fourstep(p->fso, N / 4, dtype)) != BK_OK) break;
+      } else if ((st_ = configure_fourstep(p->fs, N, dtype)) != BK_OK) {
+        break;
+      }
       const int64_t nvec = (int64_t)n_comp * max_batch;
       const size_t csz = 2 * dtype_size(dtype);
       if ((st_ = dmalloc(&p->scrA, csz * (size_t)N * nvec)) != BK_OK) break;
       if ((st_ = dmalloc(&p->scrY, dtype_size(dtype) * (size_t)(N + 1) * nvec)) != BK_OK) break;
       if ((st_ = dmalloc(&p->scrG, dtype_size(dtype) * (size_t)(N + 1) * nvec)) != BK_OK) break;
-      if ((st_ = dmalloc(&p->part1, dtype_size(dtype) * (size_t)p->nPartA * nvec)) != BK_OK) break;
-      if ((st_ = dmalloc(&p->part2, dtype_size(dtype) * (size_t)p->nPartA * nvec)) != BK_OK) break;
+      if ((st_ = dmalloc(&p->part1, dtype_size(dtype) * (size_t)p->fs.nPartA * nvec)) != BK_OK) break;
+      if ((st_ = dmalloc(&p->part2, dtype_size(dtype) * (size_t)p->fs.nPartA * nvec)) != BK_OK) break;
     }
     st_ = dtype == BK_F64 ? build_tables<double>(p, st) : build_tables<float>(p, st);
     if (st_ != BK_OK) break;
@@ -797,13 +1011,12 @@ void plan_destroy(Plan* p) {
   dfree(p->w64);
   dfree(p->wT);
   dfree(p->tw);
-  dfree(p->stw1);
-  dfree(p->stw2);
+  dfree(p->stwS);
+  free_fs(p->fs);
+  free_fs(p->fso);
+  dfree(p->eo);
   dfree(p->tpost);
   dfree(p->rk);
-  dfree(p->twN);
-  dfree(p->twLo);
-  dfree(p->twHi);
   dfree(p->scrA);
   dfree(p->scrY);
   dfree(p->scrG);
@@ -811,6 +1024,37 @@ void plan_destroy(Plan* p) {
   dfree(p->part2);
   dfree(p->t_nodes);
   delete p;
+}
+
+// One split DCT-I of the vectors at src (input kind K) into dst with epilogue E: pass A of the
+// even half (pair sums, length-N/2 FFT on fs) and of the odd half (pair differences, length-N/4
+// inverse FFT on fso), then both pass-B launches writing even and odd output indices. partA
+// receives the even half's DC partial sums (IN_WINV); partB holds the partials the epilogue
+// reads for Y0.
+template <typename T, int K, int E>
+static bk_status split_dct(const Plan* p, const T* src, int64_t sstride, T* dst, int64_t dstride, int64_t zero_to,
+                           int nvec, void* scrA, T* partA, const T* partB, int npartB, T s, T invN, StencilTab<T> tb,
+                           cudaStream_t st) {
+  typedef typename V2<T>::t C;
+  const int N = (int)p->N, M = N / 2;
+  const FourStep& e = p->fs;
+  const FourStep& o = p->fso;
+  C* Ae = (C*)scrA;
+  C* Ao = Ae + (int64_t)nvec * M;
+  const C* tp = (const C*)p->tpost;
+  const int gE = e.N2 / e.NB, gO = o.N2 / o.NB;
+  k_passA_split<T, K><<<dim3(gE + gO, nvec), std::max(e.thrA, o.thrA), std::max(e.smemA, o.smemA), st>>>(
+      gE, src, sstride, Ae, partA, M, e.N1, ilog2(e.N1), e.N2, e.NB, e.bsA, (const C*)e.stw1, (const C*)e.twN,
+      (const C*)e.twLo, (const C*)e.twHi, e.tw_h,
+      src, sstride, Ao, nullptr, M / 2, o.N1, ilog2(o.N1), o.N2, o.NB, o.bsA, (const C*)o.stw1, (const C*)o.twN,
+      (const C*)o.twLo, (const C*)o.twHi, o.tw_h, invN, tb, tp, (const C*)p->eo);
+  BK_CHECK_LAUNCH();
+  const int hE = e.N1 / 2 / e.P, hO = o.N1 / 2 / o.P;
+  k_passB_split<T, E><<<dim3(hE + hO, nvec), std::max(e.thrB, o.thrB), std::max(e.smemB, o.smemB), st>>>(
+      hE, Ae, M, e.N1, e.N2, ilog2(e.N2), e.P, (const C*)e.stw2, Ao, M / 2, o.N1, o.N2, ilog2(o.N2), o.P,
+      (const C*)o.stw2, dst, dstride, zero_to, partB, npartB, tp, s, invN, N);
+  BK_CHECK_LAUNCH();
+  return BK_OK;
 }
 
 template <typename T>
@@ -825,58 +1069,80 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
   tb.cN = (T)(1.0 / (4.0 * ((double)N * (double)N - 1.0)));
   if (p->small) {
     if (!trans)
-      k_birkhoff_small<T, false><<<nvec, p->thrS, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, (const C*)p->stw1, (const C*)p->tpost, tb);
+      k_birkhoff_small<T, false><<<nvec, p->thrS, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, (const C*)p->stwS, (const C*)p->tpost, tb);
     else
-      k_birkhoff_small<T, true><<<nvec, p->thrS, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, (const C*)p->stw1, (const C*)p->tpost, tb);
+      k_birkhoff_small<T, true><<<nvec, p->thrS, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, (const C*)p->stwS, (const C*)p->tpost, tb);
     BK_CHECK_LAUNCH();
     return BK_OK;
   }
-  const int N1 = p->N1, N2 = p->N2, NB = p->NB, P = p->P;
+  if (p->split && scrG) {
+    const int64_t Ls = N + 1;
+    T* Ystage = (T*)scrY;
+    T* Gst = (T*)scrG;
+    T* pa1 = (T*)part1;
+    T* pa2 = (T*)part2;
+    const int nPA = p->fs.nPartA;
+    const dim3 gS(nPA, nvec);
+    if (!trans) {
+      BK_TRY((split_dct<T, IN_PLAIN, EP_STORE>(p, v, p->pitch, Ystage, Ls, 0, nvec, scrA, nullptr, nullptr, 0, s, invN, tb, st)));
+      k_stencil<T, ST_FWD><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, pa2);
+      BK_CHECK_LAUNCH();
+      BK_TRY((split_dct<T, IN_PLAIN, EP_FWD_OUT>(p, Gst, Ls, out, p->pitch, p->pitch, nvec, scrA, nullptr, pa2, nPA, s, invN, tb, st)));
+    } else {
+      BK_TRY((split_dct<T, IN_WINV, EP_STORE_TRN>(p, v, p->pitch, Ystage, Ls, 0, nvec, scrA, pa1, pa1, nPA, s, invN, tb, st)));
+      k_stencil<T, ST_TRN><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, nullptr);
+      BK_CHECK_LAUNCH();
+      BK_TRY((split_dct<T, IN_PLAIN, EP_TRN_OUT>(p, Gst, Ls, out, p->pitch, p->pitch, nvec, scrA, nullptr, nullptr, 0, s, invN, tb, st)));
+    }
+    return BK_OK;
+  }
+  const FourStep& f = p->fs;
+  const int N1 = f.N1, N2 = f.N2, NB = f.NB, P = f.P;
   const int log2N1 = ilog2(N1), log2N2 = ilog2(N2);
   C* A = (C*)scrA;
   T* Ystage = (T*)scrY;
   T* pa1 = (T*)part1;
   T* pa2 = (T*)part2;
-  const int nPA = p->nPartA;
+  const int nPA = f.nPartA;
   dim3 gA(N2 / NB, nvec), gB(N1 / 2 / P, nvec);
-  const C* stw1 = (const C*)p->stw1;
-  const C* stw2 = (const C*)p->stw2;
-  const int bsA = p->bsA;
-  const C* twN = (const C*)p->twN;
+  const C* stw1 = (const C*)f.stw1;
+  const C* stw2 = (const C*)f.stw2;
+  const int bsA = f.bsA;
+  const C* twN = (const C*)f.twN;
   const C* tp = (const C*)p->tpost;
   const int64_t Ls = N + 1;
   T* Gst = (T*)scrG;  // separate stencil pass when given (see k_stencil)
   const dim3 gS(nPA, nvec);
   if (!trans) {
-    k_passA<T, IN_PLAIN><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    k_passA<T, IN_PLAIN><<<gA, f.thrA, f.smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
     BK_CHECK_LAUNCH();
-    k_passB<T, EP_STORE><<<gB, p->thrB, p->smemB, st>>>(A, Ystage, Ls, 0, nullptr, 0, N, N1, N2, log2N2, P, stw2, tp, s, invN);
+    k_passB<T, EP_STORE><<<gB, f.thrB, f.smemB, st>>>(A, Ystage, Ls, 0, nullptr, 0, N, N1, N2, log2N2, P, stw2, tp, s, invN, 1, 1, N);
     BK_CHECK_LAUNCH();
     if (Gst) {
       k_stencil<T, ST_FWD><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, pa2);
       BK_CHECK_LAUNCH();
-      k_passA<T, IN_PLAIN><<<gA, p->thrA, p->smemA, st>>>(Gst, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+      k_passA<T, IN_PLAIN><<<gA, f.thrA, f.smemA, st>>>(Gst, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
     } else {
-      k_passA<T, ST_FWD><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+      k_passA<T, ST_FWD><<<gA, f.thrA, f.smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
     }
     BK_CHECK_LAUNCH();
-    k_passB<T, EP_FWD_OUT><<<gB, p->thrB, p->smemB, st>>>(A, out, p->pitch, p->pitch, pa2, nPA, N, N1, N2, log2N2, P, stw2, tp, s, invN);
+    k_passB<T, EP_FWD_OUT><<<gB, f.thrB, f.smemB, st>>>(A, out, p->pitch, p->pitch, pa2, nPA, N, N1, N2, log2N2, P, stw2, tp, s, invN, 1, 1, N);
     BK_CHECK_LAUNCH();
   } else {
-    k_passA<T, IN_WINV><<<gA, p->thrA, p->smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+    k_passA<T, IN_WINV><<<gA, f.thrA, f.smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
     BK_CHECK_LAUNCH();
-    k_passB<T, EP_STORE_TRN><<<gB, p->thrB, p->smemB, st>>>(A, Ystage, Ls, 0, pa1, nPA, N, N1, N2, log2N2, P, stw2, tp, s, invN);
+    k_passB<T, EP_STORE_TRN><<<gB, f.thrB, f.smemB, st>>>(A, Ystage, Ls, 0, pa1, nPA, N, N1, N2, log2N2, P, stw2, tp, s, invN, 1, 1, N);
     BK_CHECK_LAUNCH();
     // the stage buffer already holds Y - Y0, so the transposed stencil runs with Y0 = 0
     if (Gst) {
       k_stencil<T, ST_TRN><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, nullptr);
       BK_CHECK_LAUNCH();
-      k_passA<T, IN_PLAIN><<<gA, p->thrA, p->smemA, st>>>(Gst, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+      k_passA<T, IN_PLAIN><<<gA, f.thrA, f.smemA, st>>>(Gst, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
     } else {
-      k_passA<T, ST_TRN><<<gA, p->thrA, p->smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, invN, tb, (const C*)p->twLo, (const C*)p->twHi, p->tw_h);
+      k_passA<T, ST_TRN><<<gA, f.thrA, f.smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
     }
     BK_CHECK_LAUNCH();
-    k_passB<T, EP_TRN_OUT><<<gB, p->thrB, p->smemB, st>>>(A, out, p->pitch, p->pitch, nullptr, 0, N, N1, N2, log2N2, P, stw2, tp, s, invN);
+    k_passB<T, EP_TRN_OUT><<<gB, f.thrB, f.smemB, st>>>(A, out, p->pitch, p->pitch, nullptr, 0, N, N1, N2, log2N2, P, stw2, tp, s, invN, 1, 1, N);
     BK_CHECK_LAUNCH();
   }
   return BK_OK;
@@ -924,15 +1190,15 @@ static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 static size_t noalloc_layout(const Plan& p, int nvec, size_t off[9]) {
   const int64_t N = p.N;
   size_t o = 0;
-  off[0] = o; o += align256(sizeof(double2) * stage_tw_len(ilog2(p.N1)));             // stw1
+  off[0] = o; o += align256(sizeof(double2) * stage_tw_len(ilog2(p.fs.N1)));          // stw1
   off[1] = o; o += align256(sizeof(double2) * (N / 2 + 1));                           // tpost
   off[2] = o; o += align256(sizeof(double2) * N);                                     // twN
   off[3] = o; o += align256(sizeof(double2) * (size_t)N * nvec);                      // scrA
   off[4] = o; o += align256(sizeof(double) * (size_t)(N + 1) * nvec);                 // scrY
-  off[5] = o; o += align256(sizeof(double) * (size_t)p.nPartA * nvec);                // part1
-  off[6] = o; o += align256(sizeof(double) * (size_t)p.nPartA * nvec);                // part2
+  off[5] = o; o += align256(sizeof(double) * (size_t)p.fs.nPartA * nvec);             // part1
+  off[6] = o; o += align256(sizeof(double) * (size_t)p.fs.nPartA * nvec);             // part2
   off[7] = o; o += align256(sizeof(double) * (size_t)(N + 2));                        // rk
-  off[8] = o; o += align256(sizeof(double2) * stage_tw_len(ilog2(p.N2)));             // stw2
+  off[8] = o; o += align256(sizeof(double2) * stage_tw_len(ilog2(p.fs.N2)));          // stw2
   return o;
 }
 
@@ -976,7 +1242,7 @@ bk_status noalloc_apply(const double* v, double* out, int64_t N, int nvec, int64
   p.tf = tf;
   p.s = 0.5 * (tf - t0);
   p.small = false;
-  BK_TRY(configure_fourstep(&p));
+  BK_TRY(configure_fourstep(p.fs, N, BK_F64));
   size_t off[9];
   const size_t need = noalloc_layout(p, nvec, off);
   BK_ARG(need <= NOALLOC_BYTES, "N=%lld with %d vectors needs %zu bytes of scratch, more than the %zu reserved",
@@ -984,22 +1250,22 @@ bk_status noalloc_apply(const double* v, double* out, int64_t N, int nvec, int64
   void* base = nullptr;
   BK_TRY(noalloc_setup(dev, &base));
   unsigned char* b = (unsigned char*)base;
-  p.stw1 = b + off[0];
-  p.stw2 = b + off[8];
+  p.fs.stw1 = b + off[0];
+  p.fs.stw2 = b + off[8];
   p.tpost = b + off[1];
-  p.twN = b + off[2];
+  p.fs.twN = b + off[2];
   p.rk = b + off[7];
   // every table is rewritten by each call: nothing in the array has to start at zero
   k_rk_table<double><<<(int)std::min<int64_t>((N + 2 + 255) / 256, 4096), 256, 0, st>>>((double*)p.rk, N + 2);
   BK_CHECK_LAUNCH();
-  const int len1 = stage_tw_len(ilog2(p.N1)), len2 = stage_tw_len(ilog2(p.N2));
-  k_stage_tw<double><<<(len1 + 255) / 256, 256, 0, st>>>((double2*)p.stw1, ilog2(p.N1), len1);
+  const int len1 = stage_tw_len(ilog2(p.fs.N1)), len2 = stage_tw_len(ilog2(p.fs.N2));
+  k_stage_tw<double><<<(len1 + 255) / 256, 256, 0, st>>>((double2*)p.fs.stw1, ilog2(p.fs.N1), len1);
   BK_CHECK_LAUNCH();
-  k_stage_tw<double><<<(len2 + 255) / 256, 256, 0, st>>>((double2*)p.stw2, ilog2(p.N2), len2);
+  k_stage_tw<double><<<(len2 + 255) / 256, 256, 0, st>>>((double2*)p.fs.stw2, ilog2(p.fs.N2), len2);
   BK_CHECK_LAUNCH();
   k_post_table<double><<<(int)std::min<int64_t>((N / 2 + 256) / 256, 4096), 256, 0, st>>>((double2*)p.tpost, N);
   BK_CHECK_LAUNCH();
-  k_tw_table<double><<<(int)std::min<int64_t>((N + 255) / 256, 8192), 256, 0, st>>>((double2*)p.twN, N, (double)N);
+  k_tw_table<double><<<(int)std::min<int64_t>((N + 255) / 256, 8192), 256, 0, st>>>((double2*)p.fs.twN, N, (double)N);
   BK_CHECK_LAUNCH();
   return apply_impl<double>(&p, v, out, nvec, false, p.s, st, b + off[3], b + off[4], b + off[5], b + off[6], nullptr);
 }

@@ -5,6 +5,24 @@
 
 namespace bk {
 
+// One four-step complex FFT layout of length n = N1 * N2 (pass A: columns of length N1, pass B:
+// rows of length N2) and its tables in the working type.
+struct FourStep {
+  int64_t n = 0;
+  int N1 = 0, N2 = 0;
+  int NB = 0, P = 0;          // pass A columns per CTA, pass B rows (or row pairs) per CTA
+  int bsA = 0;                // pass-A batch stride in shared memory (complex elements)
+  size_t smemA = 0, smemB = 0;
+  int thrA = 256, thrB = 256; // threads of the pass kernels (16 complex values each)
+  int nPartA = 0;             // pass-A CTAs per vector (partials per vector)
+  void* stw1 = nullptr;       // stage twiddle table of the length-N1 FFT
+  void* stw2 = nullptr;       // stage twiddle table of the length-N2 FFT
+  void* twN = nullptr;        // omega_n^m, m < n (FP64)
+  void* twLo = nullptr;       // omega_n^m, m < 2^tw_h (FP32)
+  void* twHi = nullptr;       // omega_n^{m 2^tw_h}, m < n / 2^tw_h (FP32)
+  int tw_h = 0;
+};
+
 struct Plan {
   int64_t N = 0, L = 0, pitch = 0;
   int n_comp = 1, max_batch = 1, dtype = BK_F64;
@@ -12,21 +30,16 @@ struct Plan {
   bool small = true;          // whole chain in one CTA per vector
   size_t smemS = 0;           // dynamic shared memory of the single-CTA kernel
   int thrS = 256;             // threads of the single-CTA kernel
-  int N1 = 0, N2 = 0;         // four-step factors, N = N1 * N2
-  int NB = 0, P = 0;          // pass A columns per CTA, pass B row pairs per CTA
-  size_t smemA = 0, smemB = 0;
-  int thrA = 256, thrB = 256; // threads of the pass kernels (16 complex values each)
-  int nPartA = 0;             // pass-A CTAs per vector (partials per vector)
-  int bsA = 0;                // pass-A batch stride in shared memory (complex elements)
   void* tw = nullptr;         // omega_N^i, i < N (single-CTA plans; the N < 16 direct DFT)
-  void* stw1 = nullptr;       // stage twiddle table of the length-N (single-CTA) or N1 FFT
-  void* stw2 = nullptr;       // stage twiddle table of the length-N2 FFT (four-step)
+  void* stwS = nullptr;       // stage twiddle table of the length-N FFT (single-CTA plans)
+  // Four-step plans. Unsplit: fs is the length-N FFT of the DCT-I. Split: each DCT-I of length
+  // N+1 is the DCT-I of length N/2+1 of its pair sums (even outputs; fs, length N/2) and the
+  // DCT-III of length N/2 of its pair differences (odd outputs; fso, length N/4).
+  FourStep fs, fso;
+  bool split = false;
+  void* eo = nullptr;         // split: exp(2 pi i k / (N/2)), k < N/4 (DCT-III pre-processing)
   void* tpost = nullptr;      // (cos, sin)(pi k / N), k = 0..N/2 (working type)
   void* rk = nullptr;         // 1 / (4k), k = 0..N+1 (working type; rk[0] = 0)
-  void* twN = nullptr;        // omega_N^m, m < N (four-step, FP64)
-  void* twLo = nullptr;       // omega_N^m, m < 2^tw_h (four-step, FP32)
-  void* twHi = nullptr;       // omega_N^{m 2^tw_h}, m < N / 2^tw_h (four-step, FP32)
-  int tw_h = 0;
   void* scrA = nullptr;       // four-step complex scratch, N per vector
   void* scrY = nullptr;       // stage buffer between the two DCTs, N + 1 per vector
   void* scrG = nullptr;       // second-DCT input (stencil output), N + 1 per vector

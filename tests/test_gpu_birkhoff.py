@@ -61,6 +61,32 @@ def test_apply_vs_fastbv_oracle(N, dtype, trans):
     assert _rel(got, ref) < TOL[dtype]
 
 
+@pytest.fixture
+def force_split(monkeypatch):
+    """Plans created while this is active use the split DCT-I from N = 2^13 on (the tuning
+    variable is read at plan creation)."""
+    monkeypatch.setenv("BK_SPLIT_MIN_LOG2", "13")
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N", [8192, 16384, 1 << 16])
+@pytest.mark.parametrize("trans", [False, True])
+def test_split_dct_vs_fastbv_oracle(N, dtype, trans, force_split):
+    """The split DCT-I (even half: DCT-I of the pair sums; odd half: DCT-III of the pair
+    differences by a quarter-length inverse FFT) against the oracle's FastBV chain."""
+    got, V, _ = _run(N, dtype, trans, n_comp=3, batch=2)
+    ref = (ob.fastbv_T if trans else ob.fastbv)(V, 0.0, 3.0)
+    assert _rel(got, ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("N", [1 << 14, 1 << 17])
+def test_split_sparse_modes_exact(N, force_split):
+    modes, alphas = synth.sparse_modes(N)
+    v, Bv = ob.sparse_mode_pair(N, modes, alphas, 0.0, 20.0)
+    got, _, _ = _run(N, torch.float64, False, n_comp=1, batch=1, t0=0.0, tf=20.0, V=v[None, None, :])
+    assert _rel(got[0, 0], Bv) < 1e-12
+
+
 @pytest.mark.parametrize("N", [64, 4096, 1 << 15, 1 << 20])
 def test_apply_sparse_modes_exact(N):
     """B applied to sum_k alpha_k T_k returns the exact integrals (closed forms)."""
@@ -72,7 +98,7 @@ def test_apply_sparse_modes_exact(N):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("N", [16, 4096, 1 << 14, 1 << 18])
+@pytest.mark.parametrize("N", [16, 4096, 1 << 14, 1 << 18, 1 << 20, 1 << 22])
 def test_adjoint_dot(N, dtype):
     """<B x, y> = <x, B^T y> with the library's two products."""
     api = _api()
