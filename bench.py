@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--N", type=int, default=20, help="log2 of the grid size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", type=int, default=1, help="1 (default): add the apply sweep N=2^10..2^24")
     return ap.parse_args()
 
 
@@ -275,8 +276,8 @@ def recorded_traffic(dtype_name, N):
     return int(m.group(1)) if sha.hexdigest()[:16] == h.group(1) else None
 
 
-def measure_apply(N, dtype, reps=20):
-    """Birkhoff apply B v on 4 components, cold L2 between repetitions (CUDA events)."""
+def measure_apply(N, dtype, reps=20, trans=False):
+    """Birkhoff apply B v (or B^T v) on 4 components, cold L2 between repetitions (CUDA events)."""
     import torch
     from paper_2509_01855_gb300 import api
     plan = api.Plan(N, n_comp=4, max_batch=1, dtype=dtype, t0=0.0, tf=TF)
@@ -286,15 +287,16 @@ def measure_apply(N, dtype, reps=20):
     v[:, :, :N + 1] = torch.randn(1, 4, N + 1, dtype=dtype, device="cuda", generator=g)
     out = plan.empty(1)
     flush = l2_flush_buffer()
+    fn = api.birkhoff_apply_T if trans else api.birkhoff_apply
     for _ in range(3):
-        api.birkhoff_apply(plan, v, out)
+        fn(plan, v, out)
     times = []
     for _ in range(reps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        api.birkhoff_apply(plan, v, out)
+        fn(plan, v, out)
         e1.record()
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -302,12 +304,46 @@ def measure_apply(N, dtype, reps=20):
     es = v.element_size()
     nbytes = 2 * 4 * (N + 1) * es                     # read v, write B v
     flops = 4 * 2 * 2.5 * N * math.log2(N)             # two DCT-I per component
+    plan.close()
     return ms, nbytes, flops
 
 
-def run_serve(n_requests, slots, rank=0, world=1, dist=None):
-    """Serving: 4096-request-class Poisson stream, N = 2^k with k ~ U{8..16}, r_f ~ U[1.2, 2.0],
-    t_f ~ U[10, 30]; offered load 0.8 x the closed-loop maximum rate of this GPU."""
+def apply_sweep(lgs=range(10, 25), reps=5):
+    """B and B^T on 4 components for N = 2^10..2^24 in FP64 and FP32, cold L2: median ms and
+    algorithmic GB/s (read v + write the product)."""
+    import torch
+    out = {}
+    for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        rows = {}
+        for lg in lgs:
+            fwd, nbytes, flops = measure_apply(1 << lg, dt, reps=reps)
+            trn, _, _ = measure_apply(1 << lg, dt, reps=reps, trans=True)
+            rows[str(lg)] = {"B_ms": round(fwd, 5), "BT_ms": round(trn, 5), "B_gbs": round(nbytes / fwd / 1e6, 2),
+                             "BT_gbs": round(nbytes / trn / 1e6, 2), "B_tflops": round(flops / fwd / 1e9, 4)}
+        out[name] = rows
+    return out
+
+
+def cpu_apply_baseline(N):
+    """The oracle's FastBV chain (SciPy DCT-I, as it stands) on 4 FP64 components at N, on the
+    host cores; one product, so the default run stays short."""
+    from oracle import birkhoff as ob
+    v = np.random.default_rng(2509_01855).standard_normal((4, N + 1))
+    ob.fastbv(v[:, :1025], 0.0, TF)        # warm-up at N = 1024 (imports, FFT set-up)
+    t0 = time.perf_counter()
+    ob.fastbv(v, 0.0, TF)
+    sec = time.perf_counter() - t0
+    nbytes = 2 * 4 * (N + 1) * 8
+    return {"value": nbytes / sec / 1e9, "unit": "GB/s", "ms": 1e3 * sec, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "oracle FastBV (SciPy DCT-I) on 4 FP64 components at N=2^%d, one product" % int(math.log2(N))}
+
+
+def run_serve(n_requests, slots, rank=0, world=1, dist=None, loads=(0.8,), extra_requests=1024):
+    """Serving: Poisson stream, N = 2^k with k ~ U{8..16}, r_f ~ U[1.2, 2.0], t_f ~ U[10, 30],
+    FP32 Krylov with the FP64 Newton residual. The closed-loop maximum rate of this GPU is
+    measured first; the stream is then offered at `loads` x that rate (the first load with
+    n_requests, the others with extra_requests). Returns the first load's statistics, with the
+    others under "load_sweep"."""
     import torch
     from paper_2509_01855_gb300 import synth
     from paper_2509_01855_gb300.serve import Server, combine_stats, run_schedule, shard_requests
@@ -320,16 +356,24 @@ def run_serve(n_requests, slots, rank=0, world=1, dist=None):
     _, st_closed = srv.run(probe, realtime=False)
     max_rate = max_over_ranks(-st_closed["solves_per_s"], dist)   # slowest rank sets the rate
     max_rate = -max_rate * world
-    rate = 0.8 * max_rate
-    reqs = shard_requests(synth.serving_requests(n_requests, rate, "stream"), rank, world)
-    t0 = time.perf_counter()
-    res = run_schedule(reqs, srv.pool, srv.solve, srv.max_slots, realtime=True)
-    st = combine_stats(res, time.perf_counter() - t0, dist)
-    iters = [r["newton_iterations"] for r in res if r.get("status") == "ok"]
+    results = []
+    for i, load in enumerate(loads):
+        rate = load * max_rate
+        n = n_requests if i == 0 else extra_requests
+        reqs = shard_requests(synth.serving_requests(n, rate, "stream-%d" % i), rank, world)
+        t0 = time.perf_counter()
+        res = run_schedule(reqs, srv.pool, srv.solve, srv.max_slots, realtime=True)
+        st = combine_stats(res, time.perf_counter() - t0, dist)
+        iters = [r["newton_iterations"] for r in res if r.get("status") == "ok"]
+        st.update(load=load, offered_rate=rate, newton_iterations_max=int(max(iters)) if iters else None)
+        results.append(st)
     srv.close()
-    st.update(offered_rate=rate, closed_loop_max_rate=max_rate, slots=slots, dtype="f32ir",
-              newton_iterations_max=int(max(iters)) if iters else None,
+    st = dict(results[0])
+    st.update(closed_loop_max_rate=max_rate, slots=slots, dtype="f32ir",
               workload="orbit raising, N=2^k k~U{8..16}, r_f~U[1.2,2], t_f~U[10,30], Poisson arrivals")
+    if len(results) > 1:
+        st["load_sweep"] = [{k: r[k] for k in ("load", "offered_rate", "solves_per_s", "p50_ms", "p99_ms", "solved",
+                                               "requests")} for r in results]
     return st
 
 
@@ -417,7 +461,7 @@ def main():
         lib = _lib.lib()
         c0 = lib.bk_launch_count()
         with ClockSampler(torch.cuda.current_device()) as clk:
-            st = run_serve(args.serve_requests or 4096, args.serve_slots, rank, world, dist)
+            st = run_serve(args.serve_requests or 4096, args.serve_slots, rank, world, dist, loads=(0.8, 0.5, 0.95))
         line.update(metric="served Newton-Krylov solves/s (orbit raising, mixed N)", value=st["solves_per_s"],
                     unit="solves/s", ms_per_step=1000.0 / st["solves_per_s"] if st["solves_per_s"] else None,
                     gpu_launches=lib.bk_launch_count() - c0, clocks=clk.summary(), serve=st,
@@ -456,10 +500,13 @@ def main():
                                         else "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_kind)}
     line["apply"] = {"ms": ams, "gbs": abytes / ams / 1e6, "tflops": aflops / ams / 1e9, "N": N,
                      "n_comp": 4, "dtype": dtype_name}
+    if args.sweep:
+        line["apply_sweep"] = apply_sweep()
     if args.workload.startswith("newton") and args.serve_requests >= 0:
         line["serve"] = run_serve(args.serve_requests or 512, args.serve_slots, rank, world, dist)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_apply_baseline"] = cpu_apply_baseline(N)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
