@@ -814,7 +814,20 @@ static bk_status compute_weights(Plan* p, cudaStream_t st) {
   return r;
 }
 
-static int small_limit(int dtype) { return dtype == BK_F64 ? 4096 : 8192; }
+// Largest N run by the single-CTA kernel (one CTA per vector): 2048 in FP64, whose single CTA
+// runs on one SM's FP64 pipe (at 4096 x 4 components: 0.129 ms single-CTA vs 0.066 ms four-step),
+// 8192 in FP32 (at 8192: 0.027 vs 0.033 ms). BK_SMALL_MAX_LOG2 overrides it for tuning (at least
+// 2^4; at most the shared-memory limit of 4096 in FP64, 8192 in FP32).
+static int small_default(int dtype) { return dtype == BK_F64 ? 2048 : 8192; }
+static int small_limit(int dtype) {
+  const int cap = dtype == BK_F64 ? 4096 : 8192;
+  const char* e = getenv("BK_SMALL_MAX_LOG2");
+  if (e) {
+    const long v = atol(e);
+    if (v >= 4 && v <= 13) return std::min(cap, 1 << (int)v);
+  }
+  return small_default(dtype);
+}
 
 template <typename T>
 static size_t smem_small(int64_t N) {
@@ -832,14 +845,32 @@ static constexpr size_t FOURSTEP_SMEM_BUDGET = 192 * 1024;
 
 // Complex elements one four-step CTA transforms (its tile: NB columns of N1 in pass A, 2P rows
 // of N2 in pass B; 16 per thread). BK_FOURSTEP_ELEMS overrides the default (tuning).
-static int fourstep_elems(int dtype) {
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 152;
+  }
+  return n;
+}
+
+// Complex elements per four-step CTA (16 per thread): enough CTAs for two per SM over the plan's
+// vectors, at least one column of N1 and one row pair of 2 N2, at most the thread cap. Small
+// transforms thus run many one-warp CTAs instead of a few full ones (at 2^14 x 4 components the
+// full-size tiles gave 16 CTAs per pass). BK_FOURSTEP_ELEMS fixes it (tuning).
+static int fourstep_elems(int dtype, int64_t n, int nvec, int N1, int N2) {
   const int cap = dtype == BK_F64 ? 4096 : 8192;  // 16 per thread at the thread cap
   const char* e = getenv("BK_FOURSTEP_ELEMS");
   if (e) {
     long v = atol(e);
-    if (v >= 512 && v <= cap && is_pow2(v)) return (int)v;
+    if (v >= 16 && v <= cap && is_pow2(v)) return std::max<int>((int)v, std::max(N1, 2 * N2));
   }
-  return cap;
+  int64_t target = n * (int64_t)std::max(1, nvec) / (2 * sm_count());
+  int64_t E = 1;
+  while (E * 2 <= target) E *= 2;
+  E = std::max<int64_t>(E, std::max(N1, 2 * N2));
+  return (int)std::min<int64_t>(E, cap);
 }
 
 // Smallest log2 N planned with the split DCT-I: 2^19 in FP64, 2^21 in FP32 (BK_SPLIT_MIN_LOG2
@@ -856,7 +887,7 @@ static int split_min_log2(int dtype) {
   return dtype == BK_F64 ? 19 : 21;
 }
 
-static bk_status configure_fourstep(FourStep& f, int64_t n, int dtype) {
+static bk_status configure_fourstep(FourStep& f, int64_t n, int dtype, int nvec) {
   const int log2n = ilog2(n);
   f = FourStep();
   f.n = n;
@@ -872,7 +903,7 @@ static bk_status configure_fourstep(FourStep& f, int64_t n, int dtype) {
     return BK_ERR_UNSUPPORTED;
   }
   const size_t csz = 2 * dtype_size(dtype);
-  const int E = fourstep_elems(dtype);
+  const int E = fourstep_elems(dtype, n, nvec, f.N1, f.N2);
   // pass A: NB columns of N1; pass B: P row pairs (2P rows) of N2
   int NB = std::max(1, E / f.N1);
   if (NB > f.N2) NB = f.N2;
@@ -916,7 +947,7 @@ static bk_status smem_attr(K* fn, int cap) {
 template <typename T>
 static bk_status set_smem_attrs(const Plan* p) {
   if (p->small) {
-    const int cap = (int)smem_small<T>(small_limit(p->dtype));
+    const int cap = (int)smem_small<T>(p->dtype == BK_F64 ? 4096 : 8192);
     BK_TRY(smem_attr(k_birkhoff_small<T, false>, cap));
     BK_TRY(smem_attr(k_birkhoff_small<T, true>, cap));
   } else {
@@ -973,9 +1004,9 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
       // split DCT-I from 2^split_min_log2() on: fs the length-N/2 FFT, fso the length-N/4 one
       p->split = ilog2(N) >= split_min_log2(dtype);
       if (p->split) {
-        if ((st_ = configure_fourstep(p->fs, N / 2, dtype)) != BK_OK) break;
-        if ((st_ = configure_fourstep(p->fso, N / 4, dtype)) != BK_OK) break;
-      } else if ((st_ = configure_fourstep(p->fs, N, dtype)) != BK_OK) {
+        if ((st_ = configure_fourstep(p->fs, N / 2, dtype, n_comp * max_batch)) != BK_OK) break;
+        if ((st_ = configure_fourstep(p->fso, N / 4, dtype, n_comp * max_batch)) != BK_OK) break;
+      } else if ((st_ = configure_fourstep(p->fs, N, dtype, n_comp * max_batch)) != BK_OK) {
         break;
       }
       const int64_t nvec = (int64_t)n_comp * max_batch;
@@ -1242,7 +1273,7 @@ bk_status noalloc_apply(const double* v, double* out, int64_t N, int nvec, int64
   p.tf = tf;
   p.s = 0.5 * (tf - t0);
   p.small = false;
-  BK_TRY(configure_fourstep(p.fs, N, BK_F64));
+  BK_TRY(configure_fourstep(p.fs, N, BK_F64, nvec));
   size_t off[9];
   const size_t need = noalloc_layout(p, nvec, off);
   BK_ARG(need <= NOALLOC_BYTES, "N=%lld with %d vectors needs %zu bytes of scratch, more than the %zu reserved",
