@@ -1030,9 +1030,15 @@ static bk_status lin_factors(Problem* pr, OpData& d, const double* z, cudaStream
   return BK_OK;
 }
 
-// Terminal Schur data of the KKT preconditioner (see precond_kkt).
+template <typename T>
+__global__ void k_negate(T* v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) v[i] = -v[i];
+}
+
+// Terminal Schur data of the KKT preconditioner (see precond_kkt): the launches, ending with the
+// n_e x n_e entries of S copied into pinned host memory (lin_schur_finish inverts S).
 template <typename T, int KIND>
-static bk_status lin_schur(Problem* pr, OpData& d, cudaStream_t st) {
+static bk_status lin_schur_launch(Problem* pr, OpData& d, cudaStream_t st) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   const int ne = pr->n_e;
   if (ne == 0 || !pr->has_cost) return BK_OK;
@@ -1044,7 +1050,6 @@ static bk_status lin_schur(Problem* pr, OpData& d, cudaStream_t st) {
   T* unit = (T*)d.t1;   // n_x * P
   T* bz = (T*)d.t2;     // n_x * P : B-tilde^T Z_r
   T* g = (T*)d.t3;      // n_x * P : forcing
-  std::vector<double> S(ne * ne);
   for (int r = 0; r < ne; ++r) {
     k_unit<T><<<nblk(NX * P), 256, 0, st>>>(unit, NX * P, (int64_t)pr->term_idx[r] * P + (L - 1));
     BK_CHECK_LAUNCH();
@@ -1061,14 +1066,24 @@ static bk_status lin_schur(Problem* pr, OpData& d, cudaStream_t st) {
     T* Q = Qc + (int64_t)r * NX * P;
     BK_TRY((run_sweep<T, NX, 0>(pr, d, unit, g, Q, nullptr, st)));
   }
-  // HWc holds -H~^{-1} W here; the caller negates it once all columns are formed.
-  // S = E Q (host): S[r][c] = Q_c[term_idx[r]][N]
-  std::vector<T> hq(ne * ne);
+  // HWc holds -H~^{-1} W: negate it
+  k_negate<T><<<nblk((int64_t)ne * NU * P), 256, 0, st>>>(HWc, (int64_t)ne * NU * P);
+  BK_CHECK_LAUNCH();
+  // S = E Q: S[r][c] = Q_c[term_idx[r]][N], into pinned host memory
+  T* hq = reinterpret_cast<T*>(pr->red_host + 256);
   for (int c = 0; c < ne; ++c)
     for (int r = 0; r < ne; ++r)
       BK_TRY_CUDA(cudaMemcpyAsync(&hq[r * ne + c], Qc + ((int64_t)c * NX + pr->term_idx[r]) * P + (L - 1), sizeof(T),
                                   cudaMemcpyDeviceToHost, st));
+  return BK_OK;
+}
+
+template <typename T>
+static bk_status lin_schur_finish(Problem* pr, OpData& d, cudaStream_t st) {
+  const int ne = pr->n_e;
+  std::vector<double> S(ne * ne);
   BK_TRY_CUDA(cudaStreamSynchronize(st));
+  const T* hq = reinterpret_cast<const T*>(pr->red_host + 256);
   for (int i = 0; i < ne * ne; ++i) S[i] = (double)hq[i];
   // invert S (n_e <= 4) by Gauss-Jordan with partial pivoting in FP64
   std::vector<double> A(S), Inv(ne * ne, 0.0);
@@ -1092,11 +1107,6 @@ static bk_status lin_schur(Problem* pr, OpData& d, cudaStream_t st) {
   BK_TRY_CUDA(cudaMemcpyAsync(d.Sinv, hs.data(), sizeof(T) * ne * ne, cudaMemcpyHostToDevice, st));
   BK_TRY_CUDA(cudaStreamSynchronize(st));
   return BK_OK;
-}
-
-template <typename T>
-__global__ void k_negate(T* v, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) v[i] = -v[i];
 }
 
 // mu (nullable): s B^aT lambda at this z, known to the caller (e.g. from the residual that
@@ -1129,15 +1139,9 @@ static bk_status linearize_kind(Problem* pr, const double* z, const double* mu, 
   pr->linearized = true;
   if (keep != LIN_FULL) return BK_OK;
   if (pr->n_e > 0 && pr->has_cost) {
-    if (pr->dtype == BK_F64) {
-      BK_TRY((lin_schur<double, KIND>(pr, pr->d64, st)));
-      k_negate<double><<<nblk((int64_t)pr->n_e * NU * P), 256, 0, st>>>((double*)pr->d64.HWc, (int64_t)pr->n_e * NU * P);
-      BK_CHECK_LAUNCH();
-    } else {
-      BK_TRY((lin_schur<float, KIND>(pr, pr->d32, st)));
-      k_negate<float><<<nblk((int64_t)pr->n_e * NU * P), 256, 0, st>>>((float*)pr->d32.HWc, (int64_t)pr->n_e * NU * P);
-      BK_CHECK_LAUNCH();
-    }
+    OpData& d = pr->work();
+    BK_TRY((d.dtype == BK_F64 ? lin_schur_launch<double, KIND>(pr, d, st) : lin_schur_launch<float, KIND>(pr, d, st)));
+    BK_TRY(d.dtype == BK_F64 ? lin_schur_finish<double>(pr, d, st) : lin_schur_finish<float>(pr, d, st));
   }
   return BK_OK;
 }
@@ -1182,10 +1186,15 @@ static bk_status apply_kind(Problem* pr, OpData& d, int op, const void* in, void
   return apply_typed<float, KIND>(pr, d, op, (const float*)in, (float*)out, (float*)mu_out, st);
 }
 
+static bk_status op_apply_direct(Problem* pr, OpData& d, int op, const void* in, void* out, cudaStream_t st,
+                                 void* mu_out) {
+  BK_DISPATCH_KIND(pr->kind, apply_kind, pr, d, op, in, out, mu_out, st);
+}
+
 bk_status op_apply(Problem* pr, OpData& d, int op, const void* in, void* out, cudaStream_t st, void* mu_out) {
   BK_ARG(pr->linearized, "problem is not linearised (call bk_linearize first)");
   BK_ARG(op == BK_OP_STATE || op == BK_OP_KKT, "unknown operator %d", op);
-  BK_DISPATCH_KIND(pr->kind, apply_kind, pr, d, op, in, out, mu_out, st);
+  return op_apply_direct(pr, d, op, in, out, st, mu_out);
 }
 
 // --- preconditioner ---------------------------------------------------------------------------
@@ -1232,16 +1241,21 @@ static bk_status precond_kind(Problem* pr, OpData& d, int op, const void* in, vo
   return precond_typed<float, KIND>(pr, d, op, (const float*)in, (float*)out, transpose, st);
 }
 
+static bk_status op_precond_direct(Problem* pr, OpData& d, int op, const void* in, void* out, int transpose,
+                                   cudaStream_t st) {
+  BK_DISPATCH_KIND(pr->kind, precond_kind, pr, d, op, in, out, transpose, st);
+}
+
 bk_status op_precond(Problem* pr, OpData& d, int op, const void* in, void* out, int transpose, cudaStream_t st) {
   BK_ARG(pr->linearized, "problem is not linearised (call bk_linearize first)");
   BK_ARG(op == BK_OP_STATE || op == BK_OP_KKT, "unknown operator %d", op);
-  BK_DISPATCH_KIND(pr->kind, precond_kind, pr, d, op, in, out, transpose, st);
+  return op_precond_direct(pr, d, op, in, out, transpose, st);
 }
 
 // --- residual -------------------------------------------------------------------------------
 template <int KIND>
-static bk_status residual_kind(Problem* pr, const double* z, double* F, double* wnorm, double* Mu, bool mu_given,
-                               cudaStream_t st) {
+static bk_status residual_launch(Problem* pr, const double* z, double* F, bool want_norm, double* Mu, bool mu_given,
+                                 cudaStream_t st) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   const int64_t P = pr->P, L = pr->L;
   OpData& d = pr->d64;
@@ -1258,19 +1272,34 @@ static bk_status residual_kind(Problem* pr, const double* z, double* F, double* 
   k_resid_post<KIND><<<nb, 256, 0, st>>>(z, pr->d64.plan->w64, pr->s, Bf, Mu, P, L, term_spec(pr), x0,
                                          pr->has_cost ? 1.0 : 0.0, F, pr->red);
   BK_CHECK_LAUNCH();
-  if (wnorm) {
+  if (want_norm) {
     k_sum_partials<<<1, 256, 0, st>>>(pr->red, nb, pr->red + 1024);
     BK_CHECK_LAUNCH();
     BK_TRY_CUDA(cudaMemcpyAsync(pr->red_host, pr->red + 1024, sizeof(double), cudaMemcpyDeviceToHost, st));
-    BK_TRY_CUDA(cudaStreamSynchronize(st));
-    *wnorm = sqrt(pr->red_host[0]);
   }
   return BK_OK;
 }
 
+template <int KIND>
+static bk_status residual_kind(Problem* pr, const double* z, double* F, bool want_norm, double* Mu, bool mu_given,
+                               cudaStream_t st) {
+  return residual_launch<KIND>(pr, z, F, want_norm, Mu, mu_given, st);
+}
+
+static bk_status residual_dispatch(Problem* pr, const double* z, double* F, bool want, double* Mu, bool mu_given,
+                                   cudaStream_t st) {
+  BK_DISPATCH_KIND(pr->kind, residual_kind, pr, z, F, want, Mu, mu_given, st);
+}
+
 bk_status problem_residual(Problem* pr, const double* z, double* F, double* wnorm, cudaStream_t st, double* Mu,
                            bool mu_given) {
-  BK_DISPATCH_KIND(pr->kind, residual_kind, pr, z, F, wnorm, Mu, mu_given, st);
+  const bool want = wnorm != nullptr;
+  BK_TRY(residual_dispatch(pr, z, F, want, Mu, mu_given, st));
+  if (wnorm) {
+    BK_TRY_CUDA(cudaStreamSynchronize(st));
+    *wnorm = sqrt(pr->red_host[0]);
+  }
+  return BK_OK;
 }
 
 template <int KIND>

@@ -203,7 +203,7 @@ class Server:
         s.tau = self._nodes(N)
         s.nbytes = s.prob.device_bytes() + s.ws.numel() * 8 + s.z.numel() * 8
         self._bytes[N] = s.nbytes
-        torch.cuda.synchronize()
+        s.stream.synchronize()   # this slot only: other slots keep running
         return s
 
     def _free_slot(self, s):
