@@ -501,10 +501,21 @@ __global__ void __launch_bounds__(256) k_stencil(const T* __restrict__ stage, in
   const T* Y = stage + (int64_t)vec * Ls;
   T* g = G + (int64_t)vec * Ls;
   T acc = T(0);
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m <= N; m += gridDim.x * blockDim.x) {
-    const T x = load_x<T, K>(Y, m, N, sc, T(0), tb);
+  // interior nodes 2..N-2 by the plain three-point formulas (the boundary cases, if-converted
+  // into the same loop, tripled its FP64 instructions); the four boundary nodes by one thread
+  const T* __restrict__ rk = tb.rk;
+  for (int m = 2 + blockIdx.x * blockDim.x + threadIdx.x; m <= N - 2; m += gridDim.x * blockDim.x) {
+    const T x = K == ST_FWD ? (Y[m + 1] - Y[m - 1]) * (sc * rk[m]) : Y[m - 1] * rk[m - 1] - Y[m + 1] * rk[m + 1];
     g[m] = x;
-    acc += (m == 0 || m == N) ? x : T(2) * x;
+    acc += T(2) * x;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int mb[4] = {0, 1, N - 1, N};
+    for (int i = 0; i < 4; ++i) {
+      const T x = load_x<T, K>(Y, mb[i], N, sc, T(0), tb);
+      g[mb[i]] = x;
+      acc += (mb[i] == 0 || mb[i] == N) ? x : T(2) * x;
+    }
   }
   if (partial) {
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
