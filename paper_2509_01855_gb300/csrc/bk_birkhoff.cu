@@ -447,15 +447,28 @@ __device__ __forceinline__ void passA_body(
   }
   fft16<T>(buf, N1, log2N1, NB, bs, smem_tw ? tws : stw);
   C* A = Aout + (int64_t)vec * N;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int b = idx & (NB - 1);
-    const int k1 = idx >> log2NB;
-    const int j2 = c0 + b;
-    const int m = j2 * k1;  // < N
-    // FP64: one table of omega_N^m (the FP64 pipe, not memory, bounds these kernels).
-    // FP32: omega_N^m = omega_N^{(m >> h) 2^h} omega_N^{m mod 2^h} from two tables of ~sqrt N.
-    const C w = sizeof(T) == 8 ? __ldg(&twN[m]) : cmul(__ldg(&twHi[m >> tw_h]), __ldg(&twLo[m & ((1 << tw_h) - 1)]));
-    A[(int64_t)k1 * N2 + j2] = cmul(buf[b * bs + padi(k1)], w);
+  // inter-pass twiddles omega_N^{j2 k1}, 4 independent table loads in flight per thread.
+  // FP64: one table of omega_N^m (the FP64 pipe, not memory, bounds these kernels).
+  // FP32: omega_N^m = omega_N^{(m >> h) 2^h} omega_N^{m mod 2^h} from two tables of ~sqrt N.
+  for (int idx0 = threadIdx.x; idx0 < total; idx0 += 4 * blockDim.x) {
+    C w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = idx0 + u * blockDim.x;
+      if (idx < total) {
+        const int m = (c0 + (idx & (NB - 1))) * (idx >> log2NB);  // < N
+        w[u] = sizeof(T) == 8 ? __ldg(&twN[m]) : cmul(__ldg(&twHi[m >> tw_h]), __ldg(&twLo[m & ((1 << tw_h) - 1)]));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = idx0 + u * blockDim.x;
+      if (idx < total) {
+        const int b = idx & (NB - 1);
+        const int k1 = idx >> log2NB;
+        A[(int64_t)k1 * N2 + c0 + b] = cmul(buf[b * bs + padi(k1)], w[u]);
+      }
+    }
   }
 }
 
@@ -631,40 +644,55 @@ __device__ __forceinline__ void passB_body(
     return;
   }
   const int half = N / 2;
-  for (int idx = threadIdx.x; idx < P * N2; idx += blockDim.x) {
-    const int i = idx >> log2N2;
-    const int k2 = idx & (N2 - 1);
-    const int p = p0 + i;
-    const C* ra = buf + (2 * i) * bs;
-    const C* rb = buf + (2 * i + 1) * bs;
-    if (p == 0) {
-      // row 0 pairs internally (k2 <-> N2 - k2); row N1/2 pairs k2 <-> N2 - 1 - k2
-      if (k2 <= N2 / 2) {
-        const int k = N1 * k2;
+  // Row pair i of the CTA and column k2 give outputs k = p0 + i + N1 k2 and N - k: lanes take
+  // consecutive i (P-long runs of consecutive outputs) and load 4 split twiddles at a time.
+  const int log2P = __ffs(P) - 1;  // P is a power of two
+  for (int idx0 = threadIdx.x; idx0 < P * N2; idx0 += 4 * blockDim.x) {
+    C cs[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = idx0 + u * blockDim.x;
+      const int k = p0 + (idx & (P - 1)) + N1 * (idx >> log2P);
+      if (idx < P * N2 && p0 + (idx & (P - 1)) != 0) cs[u] = tpost[(k <= half ? k : N - k) * tps];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = idx0 + u * blockDim.x;
+      if (idx >= P * N2) continue;
+      const int i = idx & (P - 1);
+      const int k2 = idx >> log2P;
+      const int p = p0 + i;
+      const C* ra = buf + (2 * i) * bs;
+      const C* rb = buf + (2 * i + 1) * bs;
+      if (p == 0) {
+        // row 0 pairs internally (k2 <-> N2 - k2); row N1/2 pairs k2 <-> N2 - 1 - k2
+        if (k2 <= N2 / 2) {
+          const int k = N1 * k2;
+          T yk, ynk;
+          split_pair<T>(ra[padi(k2)], ra[padi((N2 - k2) & (N2 - 1))], tpost[k * tps], yk, ynk);
+          ep_write<T, E>(out, k * ostride, yk, Npar, s, Y0, invN);
+          if (k != half) ep_write<T, E>(out, (N - k) * ostride, ynk, Npar, s, Y0, invN);
+        }
+        if (k2 < N2 / 2) {
+          const int k = N1 / 2 + N1 * k2;
+          T yk, ynk;
+          split_pair<T>(rb[padi(k2)], rb[padi(N2 - 1 - k2)], tpost[k * tps], yk, ynk);
+          ep_write<T, E>(out, k * ostride, yk, Npar, s, Y0, invN);
+          ep_write<T, E>(out, (N - k) * ostride, ynk, Npar, s, Y0, invN);
+        }
+      } else {
+        const int k = p + N1 * k2;
+        const C zk = ra[padi(k2)];
+        const C zc = rb[padi(N2 - 1 - k2)];
         T yk, ynk;
-        split_pair<T>(ra[padi(k2)], ra[padi((N2 - k2) & (N2 - 1))], tpost[k * tps], yk, ynk);
-        ep_write<T, E>(out, k * ostride, yk, Npar, s, Y0, invN);
-        if (k != half) ep_write<T, E>(out, (N - k) * ostride, ynk, Npar, s, Y0, invN);
-      }
-      if (k2 < N2 / 2) {
-        const int k = N1 / 2 + N1 * k2;
-        T yk, ynk;
-        split_pair<T>(rb[padi(k2)], rb[padi(N2 - 1 - k2)], tpost[k * tps], yk, ynk);
+        if (k <= half) {
+          split_pair<T>(zk, zc, cs[u], yk, ynk);
+        } else {
+          split_pair<T>(zc, zk, cs[u], ynk, yk);
+        }
         ep_write<T, E>(out, k * ostride, yk, Npar, s, Y0, invN);
         ep_write<T, E>(out, (N - k) * ostride, ynk, Npar, s, Y0, invN);
       }
-    } else {
-      const int k = p + N1 * k2;
-      const C zk = ra[padi(k2)];
-      const C zc = rb[padi(N2 - 1 - k2)];
-      T yk, ynk;
-      if (k <= half) {
-        split_pair<T>(zk, zc, tpost[k * tps], yk, ynk);
-      } else {
-        split_pair<T>(zc, zk, tpost[(N - k) * tps], ynk, yk);
-      }
-      ep_write<T, E>(out, k * ostride, yk, Npar, s, Y0, invN);
-      ep_write<T, E>(out, (N - k) * ostride, ynk, Npar, s, Y0, invN);
     }
   }
   // zero the padding of the output vectors (final epilogues only)

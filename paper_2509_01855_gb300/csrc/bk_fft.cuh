@@ -113,29 +113,44 @@ template <typename C, typename T> struct Radix<C, T, 16> {
   }
 };
 
-// One in-place stage of radix R (16/R butterflies per thread). Ns = product of the previous
-// radices. Threads t < nbatch * n/16 work; all threads must reach the barriers.
-template <typename T, int R>
-__device__ __forceinline__ void stage16(typename V2<T>::t* __restrict__ buf, int n, int log2n, int nbatch,
-                                        int bs, int Ns, int log2Ns, const typename V2<T>::t* __restrict__ stw) {
+// One in-place stage of radix R (16/R butterflies per thread) of a length-2^LOG2N FFT whose
+// previous radices multiply to Ns = 2^LOG2NS. Threads t < nbatch * n/16 work; all threads must
+// reach the barriers.
+//
+// Addressing. padi(a + c) = padi(a) + padi(c) whenever (a mod 16) + (c mod 16) < 16, so with
+// n and Ns known at compile time every shared address of a stage is one per-thread base plus an
+// immediate offset:
+//   reads  tt + q n/16 + r n/R : all offsets multiples of 16 once n >= 256 (smaller n: generic);
+//   writes idxD + r Ns, idxD = (j / Ns) 16 Ns + (j mod Ns): idxD mod 16 = j mod Ns < Ns when
+//          Ns < 16 and r Ns mod 16 <= 16 - Ns, or both offsets multiples of 16 (Ns >= 16); in
+//          the first stage (Ns = 1) idxD = R j is a multiple of R and r < R;
+//   twiddles stw[(r - 1) Ns + k] from stw + k.
+template <typename T, int LOG2N, int R, int LOG2NS>
+__device__ __forceinline__ void stage_ct(typename V2<T>::t* __restrict__ buf, int nbatch, int bs,
+                                         const typename V2<T>::t* __restrict__ stw) {
   typedef typename V2<T>::t C;
   constexpr int log2R = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
   constexpr int PER = 16 / R;
-  const int log2nb16 = log2n - 4;
-  const int nb16 = 1 << log2nb16;
+  constexpr int LOG2NB16 = LOG2N - 4;
+  constexpr int nb16 = 1 << LOG2NB16;
+  constexpr int nR = (1 << LOG2N) >> log2R;
+  constexpr int Ns = 1 << LOG2NS;
+  constexpr bool lin_rd = (nR % 16 == 0) && (PER == 1 || nb16 % 16 == 0);
+  static_assert(PER == 1 || LOG2NS == 0, "mixed radix only as the first stage");
   const int t = threadIdx.x;
-  const bool active = t < (nbatch << log2nb16);
-  const int b = t >> log2nb16;
+  const bool active = t < (nbatch << LOG2NB16);
   const int tt = t & (nb16 - 1);
-  C* base = buf + (size_t)b * bs;
-  const int nR = n >> log2R;
+  C* base = buf + (size_t)(t >> LOG2NB16) * bs;
   C v[16];
   if (active) {
+    const C* src = base + padi(tt);
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-      const int j = tt + q * nb16;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[q * R + r] = base[padi(j + r * nR)];
+      for (int r = 0; r < R; ++r) {
+        const int c = q * nb16 + r * nR;
+        v[q * R + r] = lin_rd ? src[c + (c >> 4)] : base[padi(tt + c)];
+      }
     }
   }
   __syncthreads();
@@ -146,44 +161,60 @@ __device__ __forceinline__ void stage16(typename V2<T>::t* __restrict__ buf, int
       const int k = j & (Ns - 1);
       C* u = v + q * R;
       if (Ns > 1) {
+        const C* tw = stw + k;
 #pragma unroll
-        for (int r = 1; r < R; ++r) u[r] = cmul(u[r], stw[(r - 1) * Ns + k]);
+        for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw[(r - 1) * Ns]);
       }
       Radix<C, T, R>::run(u);
-      const int idxD = ((j >> log2Ns) << (log2Ns + log2R)) + k;
+      C* dst = base + padi(((j >> LOG2NS) << (LOG2NS + log2R)) + k);
 #pragma unroll
-      for (int r = 0; r < R; ++r) base[padi(idxD + r * Ns)] = u[r];
+      for (int r = 0; r < R; ++r) {
+        const int c = r * Ns;
+        dst[c + (c >> 4)] = u[r];
+      }
     }
   }
   __syncthreads();
 }
 
-// Batched in-place forward FFT of length n = 2^log2n (16 <= n) over `nbatch` padded transforms
-// bs apart in shared memory (element i of batch b at buf[b * bs + padi(i)]), stw the stage table
-// of length n. The block needs at least nbatch * n / 16 threads. Input complete before the call
-// (barrier); result complete on return, in natural order, in place.
+// Radix-16 stages from Ns = 2^LOG2NS on; OFF is the stage table offset of the first of them.
+template <typename T, int LOG2N, int LOG2NS, int OFF>
+__device__ __forceinline__ void fft_ct_r16(typename V2<T>::t* buf, int nbatch, int bs,
+                                           const typename V2<T>::t* __restrict__ stw) {
+  if constexpr (LOG2NS < LOG2N) {
+    stage_ct<T, LOG2N, 16, LOG2NS>(buf, nbatch, bs, stw + OFF);
+    fft_ct_r16<T, LOG2N, LOG2NS + 4, OFF + (LOG2NS > 0 ? (15 << LOG2NS) : 0)>(buf, nbatch, bs, stw);
+  }
+}
+
+// Length-2^LOG2N FFT: one mixed radix-2/4/8 stage when LOG2N is not a multiple of 4, then
+// radix-16 stages.
+template <typename T, int LOG2N>
+__device__ __forceinline__ void fft_ct(typename V2<T>::t* buf, int nbatch, int bs,
+                                       const typename V2<T>::t* __restrict__ stw) {
+  constexpr int rem = LOG2N & 3;
+  if constexpr (rem != 0) stage_ct<T, LOG2N, (1 << rem), 0>(buf, nbatch, bs, stw);
+  fft_ct_r16<T, LOG2N, rem, 0>(buf, nbatch, bs, stw);
+}
+
+template <typename T, int LO, int HI>
+__device__ __forceinline__ void fft_ct_dispatch(typename V2<T>::t* buf, int log2n, int nbatch, int bs,
+                                                const typename V2<T>::t* __restrict__ stw) {
+  if constexpr (LO <= HI) {
+    if (log2n == LO) fft_ct<T, LO>(buf, nbatch, bs, stw);
+    else fft_ct_dispatch<T, LO + 1, HI>(buf, log2n, nbatch, bs, stw);
+  }
+}
+
+// Batched in-place forward FFT of length n = 2^log2n (16 <= n <= 8192) over `nbatch` padded
+// transforms bs apart in shared memory (element i of batch b at buf[b * bs + padi(i)]), stw the
+// stage table of length n. The block needs at least nbatch * n / 16 threads. Input complete
+// before the call (barrier); result complete on return, in natural order, in place. Each length
+// is its own compile-time instance (log2n is uniform over the block).
 template <typename T>
-__device__ void fft16(typename V2<T>::t* buf, int n, int log2n, int nbatch, int bs,
-                      const typename V2<T>::t* __restrict__ stw) {
-  int Ns = 1, log2Ns = 0;
-  const int rem = log2n & 3;
-  if (rem == 1) {
-    stage16<T, 2>(buf, n, log2n, nbatch, bs, Ns, log2Ns, stw);
-    Ns = 2; log2Ns = 1;
-  } else if (rem == 2) {
-    stage16<T, 4>(buf, n, log2n, nbatch, bs, Ns, log2Ns, stw);
-    Ns = 4; log2Ns = 2;
-  } else if (rem == 3) {
-    stage16<T, 8>(buf, n, log2n, nbatch, bs, Ns, log2Ns, stw);
-    Ns = 8; log2Ns = 3;
-  }
-  int off = 0;
-  while (log2Ns < log2n) {
-    stage16<T, 16>(buf, n, log2n, nbatch, bs, Ns, log2Ns, stw + off);
-    if (Ns > 1) off += 15 * Ns;
-    Ns <<= 4;
-    log2Ns += 4;
-  }
+__device__ __forceinline__ void fft16(typename V2<T>::t* buf, int n, int log2n, int nbatch, int bs,
+                                      const typename V2<T>::t* __restrict__ stw) {
+  fft_ct_dispatch<T, 4, 13>(buf, log2n, nbatch, bs, stw);
 }
 
 // Copy a stage table (len entries) into shared memory.

@@ -136,8 +136,9 @@ __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, 
 // Level data of the sweep's affine maps. Level 0 items are segments of SEG nodes, whose map is
 // the product of (I + N_k) over the segment (latest node on the left); a level-(l+1) item is a
 // block of 32 level-l items and its map the product of theirs. The backward sweep uses the
-// transposed maps in reverse order. All level data is FP64 for both working precisions (FP32
-// products of ~1000 Cayley factors would cost the FP32 preconditioner its accuracy at large N)
+// transposed maps in reverse order. Level data is in the working precision (each node's map is
+// a product of one factor per level, O(log N) roundings deep, which an FP32 preconditioner
+// feeding FP32 GMRES tolerates; FP64 levels cost FP32 problems FP64-pipe time in every sweep)
 // and 32-interleaved (element c of item i at il32(i, c, NC)), so that a warp reading 32
 // consecutive items is coalesced; slot q of a level starts at q * npad * n_x^2, npad = the
 // level's item count rounded up to 32.
@@ -159,11 +160,9 @@ __device__ __forceinline__ void mat_mul(const Tm* A, const Tm* B, Tm* C) {
 
 // Level-0 maps: prod over the segment's nodes of (I + N_k), one thread per segment.
 template <typename T, int NX>
-__global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, double* __restrict__ A0) {
+__global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, T* __restrict__ A0) {
   const int seg = blockIdx.x * blockDim.x + threadIdx.x;
   if (seg >= nseg) return;
-  // products over one segment in the working type (16 FP32 factors keep FP32 accuracy); the
-  // level products above are FP64
   T A[NX * NX], M[NX * NX], R[NX * NX];
 #pragma unroll
   for (int i = 0; i < NX * NX; ++i) A[i] = (i % (NX + 1) == 0) ? T(1) : T(0);
@@ -178,36 +177,36 @@ __global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, double*
     for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
   }
 #pragma unroll
-  for (int c = 0; c < NX * NX; ++c) A0[il32(seg, c, NX * NX)] = (double)A[c];
+  for (int c = 0; c < NX * NX; ++c) A0[il32(seg, c, NX * NX)] = A[c];
 }
 
 // Slots of one level, one warp per block of 32 items (items at or beyond n are identity maps):
 // spans M_k(j) = M_{k-1}(j) M_{k-1}(j - 2^{k-1}) by doubling (defined for j >= 2^k - 1), Pre(i)
 // and Suf(i) as products of the spans that tile [0, i) and (i, 31], and the block's product
 // M_4(31) M_4(15), which is the map of the parent item at the next level.
-template <int NX>
-__global__ void __launch_bounds__(32) k_lin_level(double* __restrict__ m, int n, double* __restrict__ parent) {
+template <typename T, int NX>
+__global__ void __launch_bounds__(32) k_lin_level(T* __restrict__ m, int n, T* __restrict__ parent) {
   constexpr int NC = NX * NX;
-  __shared__ double S[5][32][NC + 1];
+  __shared__ T S[5][32][NC + 1];
   const int lane = threadIdx.x;
   const int64_t i = (int64_t)blockIdx.x * 32 + lane;
   const int64_t slot = (int64_t)gridDim.x * 32 * NC;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    const double idc = (c % (NX + 1) == 0) ? 1.0 : 0.0;
-    const double a = i < n ? m[il32(i, c, NC)] : idc;
+    const T idc = (c % (NX + 1) == 0) ? T(1) : T(0);
+    const T a = i < n ? m[il32(i, c, NC)] : idc;
     S[0][lane][c] = a;
     if (i >= n) m[il32(i, c, NC)] = idc;
   }
   __syncwarp();
   for (int k = 1; k < 5; ++k) {
     const int h = 1 << (k - 1);
-    double R[NC];
+    T R[NC];
     if (lane >= 2 * h - 1) {
-      mat_mul<NX>(S[k - 1][lane], S[k - 1][lane - h], R);
+      mat_mul<NX, T>(S[k - 1][lane], S[k - 1][lane - h], R);
     } else {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) R[c] = (c % (NX + 1) == 0) ? 1.0 : 0.0;
+      for (int c = 0; c < NC; ++c) R[c] = (c % (NX + 1) == 0) ? T(1) : T(0);
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) S[k][lane][c] = R[c];
@@ -217,14 +216,14 @@ __global__ void __launch_bounds__(32) k_lin_level(double* __restrict__ m, int n,
   for (int k = 1; k < 5; ++k)
 #pragma unroll
     for (int c = 0; c < NC; ++c) m[k * slot + il32(i, c, NC)] = S[k][lane][c];
-  double R[NC], Q[NC];
+  T R[NC], Q[NC];
   // Pre(i) = A_{i-1} ... A_0
 #pragma unroll
-  for (int c = 0; c < NC; ++c) R[c] = (c % (NX + 1) == 0) ? 1.0 : 0.0;
+  for (int c = 0; c < NC; ++c) R[c] = (c % (NX + 1) == 0) ? T(1) : T(0);
   int pos = 0;
   for (int k = 4; k >= 0; --k) {
     if ((lane >> k) & 1) {
-      mat_mul<NX>(S[k][pos + (1 << k) - 1], R, Q);
+      mat_mul<NX, T>(S[k][pos + (1 << k) - 1], R, Q);
 #pragma unroll
       for (int c = 0; c < NC; ++c) R[c] = Q[c];
       pos += 1 << k;
@@ -234,12 +233,12 @@ __global__ void __launch_bounds__(32) k_lin_level(double* __restrict__ m, int n,
   for (int c = 0; c < NC; ++c) m[SL_PRE * slot + il32(i, c, NC)] = R[c];
   // Suf(i) = A_31 ... A_{i+1}
 #pragma unroll
-  for (int c = 0; c < NC; ++c) R[c] = (c % (NX + 1) == 0) ? 1.0 : 0.0;
+  for (int c = 0; c < NC; ++c) R[c] = (c % (NX + 1) == 0) ? T(1) : T(0);
   int end = 31;
   const int len = 31 - lane;
   for (int k = 4; k >= 0; --k) {
     if ((len >> k) & 1) {
-      mat_mul<NX>(R, S[k][end], Q);
+      mat_mul<NX, T>(R, S[k][end], Q);
 #pragma unroll
       for (int c = 0; c < NC; ++c) R[c] = Q[c];
       end -= 1 << k;
@@ -250,7 +249,7 @@ __global__ void __launch_bounds__(32) k_lin_level(double* __restrict__ m, int n,
   if (parent) {
     for (int c = lane; c < NC; c += 32) {
       const int r = c / NX, cc = c % NX;
-      double a = 0;
+      T a = 0;
 #pragma unroll
       for (int q = 0; q < NX; ++q) a += S[4][31][r * NX + q] * S[4][15][q * NX + cc];
       parent[il32(blockIdx.x, c, NC)] = a;
@@ -278,11 +277,11 @@ __global__ void k_convert(const Tin* __restrict__ a, Tout* __restrict__ b, int64
 // the incoming state from the top level down, S <- Pre(i) S + e(i-1) (backward:
 // S <- Suf(i)^T S + e(i+1)), and reruns the segment's nodes from it.
 // ---------------------------------------------------------------------------------------------
-struct Levels {
-  const double* m[MAXLEV];  // matrix slots per level
-  double* o[MAXLEV];        // item offsets from zero, levels >= 1
-  double* e[MAXLEV];        // inclusive in-block scan values
-  int n[MAXLEV];            // items per level
+template <typename T> struct Levels {
+  const T* m[MAXLEV];  // matrix slots per level
+  T* o[MAXLEV];        // item offsets from zero, levels >= 1
+  T* e[MAXLEV];        // inclusive in-block scan values
+  int n[MAXLEV];       // items per level
   int nlev;
 };
 
@@ -339,27 +338,27 @@ __device__ __forceinline__ void node_step(const T* __restrict__ Kn, const T* __r
 // Inclusive scan of the offsets e within block blk (lane i holds item 32 blk + i), level slot
 // size `slot`. DIR 0: e_i += M_k(i) e_{i-2^k}; DIR 1 (reverse order, transposed maps):
 // e_i += M_k(i + 2^k - 1)^T e_{i+2^k}.
-template <int NX, int DIR>
-__device__ __forceinline__ void warp_scan(const double* __restrict__ m, int64_t slot, int64_t blk, double* e) {
+template <typename T, int NX, int DIR>
+__device__ __forceinline__ void warp_scan(const T* __restrict__ m, int64_t slot, int64_t blk, T* e) {
   constexpr int NC = NX * NX;
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const int d = 1 << k;
-    double pe[NX];
+    T pe[NX];
 #pragma unroll
     for (int r = 0; r < NX; ++r)
       pe[r] = DIR == 0 ? __shfl_up_sync(0xffffffffu, e[r], d) : __shfl_down_sync(0xffffffffu, e[r], d);
     const bool act = DIR == 0 ? lane >= d : lane + d < 32;
     if (act) {
       const int64_t item = blk * 32 + (DIR == 0 ? lane : lane + d - 1);
-      const double* M = m + k * slot;
-      double Mv[NC];
+      const T* M = m + k * slot;
+      T Mv[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) Mv[c] = M[il32(item, c, NC)];
 #pragma unroll
       for (int r = 0; r < NX; ++r) {
-        double a = e[r];
+        T a = e[r];
 #pragma unroll
         for (int c = 0; c < NX; ++c) a += (DIR == 0 ? Mv[r * NX + c] : Mv[c * NX + r]) * pe[c];
         e[r] = a;
@@ -421,7 +420,7 @@ template <typename T, int NX> struct SweepTiles {
 template <typename T, int NX, int DIR>
 __global__ void __launch_bounds__(128) k_sw_up0(const T* __restrict__ Kn, const T* __restrict__ Nn,
                                                 const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
-                                                int64_t L, const T* __restrict__ w, T s, Levels lv) {
+                                                int64_t L, const T* __restrict__ w, T s, Levels<T> lv) {
   constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS, SEG = Seg<T>::v;
   __shared__ SweepTiles<T, NX> tiles[4];
   const int nblk = (lv.n[0] + 31) >> 5;
@@ -456,10 +455,10 @@ __global__ void __launch_bounds__(128) k_sw_up0(const T* __restrict__ Kn, const 
       }
     }
   }
-  double e[NX];
+  T e[NX];
 #pragma unroll
-  for (int m = 0; m < NX; ++m) e[m] = (double)st[m];
-  warp_scan<NX, DIR>(lv.m[0], (int64_t)nblk * 32 * NX * NX, g, e);
+  for (int m = 0; m < NX; ++m) e[m] = st[m];
+  warp_scan<T, NX, DIR>(lv.m[0], (int64_t)nblk * 32 * NX * NX, g, e);
 #pragma unroll
   for (int m = 0; m < NX; ++m) lv.e[0][il32(seg, m, NX)] = e[m];
   if (lv.nlev > 1 && lane == (DIR == 0 ? 31 : 0)) {
@@ -469,24 +468,24 @@ __global__ void __launch_bounds__(128) k_sw_up0(const T* __restrict__ Kn, const 
 }
 
 // Up, level l >= 1 (one warp per block of 32 items): scan of the items' offsets.
-template <int NX, int DIR>
-__global__ void __launch_bounds__(128) k_sw_upL(Levels lv, int l) {
+template <typename T, int NX, int DIR>
+__global__ void __launch_bounds__(128) k_sw_upL(Levels<T> lv, int l) {
   const int n = lv.n[l];
   const int nblk = (n + 31) >> 5;
   const int b = blockIdx.x * 4 + (threadIdx.x >> 5);
   if (b >= nblk) return;
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)b * 32 + lane;
-  const double* o = lv.o[l];
-  double e[NX];
+  const T* o = lv.o[l];
+  T e[NX];
 #pragma unroll
-  for (int m = 0; m < NX; ++m) e[m] = i < n ? o[il32(i, m, NX)] : 0.0;
-  warp_scan<NX, DIR>(lv.m[l], (int64_t)nblk * 32 * NX * NX, b, e);
-  double* el = lv.e[l];
+  for (int m = 0; m < NX; ++m) e[m] = i < n ? o[il32(i, m, NX)] : T(0);
+  warp_scan<T, NX, DIR>(lv.m[l], (int64_t)nblk * 32 * NX * NX, b, e);
+  T* el = lv.e[l];
 #pragma unroll
   for (int m = 0; m < NX; ++m) el[il32(i, m, NX)] = e[m];
   if (l + 1 < lv.nlev && lane == (DIR == 0 ? 31 : 0)) {
-    double* op = lv.o[l + 1];
+    T* op = lv.o[l + 1];
 #pragma unroll
     for (int m = 0; m < NX; ++m) op[il32(b, m, NX)] = e[m];
   }
@@ -497,7 +496,7 @@ __global__ void __launch_bounds__(128) k_sw_upL(Levels lv, int l) {
 template <typename T, int NX, int DIR>
 __global__ void __launch_bounds__(128) k_sw_down0(const T* __restrict__ Kn, const T* __restrict__ Nn,
                                                   const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
-                                                  int64_t L, const T* __restrict__ w, T s, Levels lv,
+                                                  int64_t L, const T* __restrict__ w, T s, Levels<T> lv,
                                                   T* __restrict__ out, T* __restrict__ bout) {
   constexpr int NC = NX * NX;
   constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS, SEG = Seg<T>::v;
@@ -510,23 +509,23 @@ __global__ void __launch_bounds__(128) k_sw_down0(const T* __restrict__ Kn, cons
   const int64_t seg0 = (int64_t)g * 32;
   const int64_t seg = seg0 + lane;
   const bool live = seg < lv.n[0];
-  double S[NX];
+  T S[NX];
 #pragma unroll
-  for (int m = 0; m < NX; ++m) S[m] = 0.0;
+  for (int m = 0; m < NX; ++m) S[m] = T(0);
   for (int l = lv.nlev - 1; l >= 0 && live; --l) {
     const int64_t i = seg >> (5 * l);
     const int q = (int)(i & 31);
     if (DIR == 0 ? q == 0 : q == 31) continue;  // first item of its block in sweep order
     const int64_t slot = (int64_t)((lv.n[l] + 31) >> 5) * 32 * NC;
-    const double* Mt = lv.m[l] + (DIR == 0 ? SL_PRE : SL_SUF) * slot;
-    const double* el = lv.e[l];
+    const T* Mt = lv.m[l] + (DIR == 0 ? SL_PRE : SL_SUF) * slot;
+    const T* el = lv.e[l];
     const int64_t ia = DIR == 0 ? i - 1 : i + 1;
-    double Mv[NC], ns[NX];
+    T Mv[NC], ns[NX];
 #pragma unroll
     for (int c = 0; c < NC; ++c) Mv[c] = Mt[il32(i, c, NC)];
 #pragma unroll
     for (int r = 0; r < NX; ++r) {
-      double a = el[il32(ia, r, NX)];
+      T a = el[il32(ia, r, NX)];
 #pragma unroll
       for (int c = 0; c < NX; ++c) a += (DIR == 0 ? Mv[r * NX + c] : Mv[c * NX + r]) * S[c];
       ns[r] = a;
@@ -536,7 +535,7 @@ __global__ void __launch_bounds__(128) k_sw_down0(const T* __restrict__ Kn, cons
   }
   T st[NX];
 #pragma unroll
-  for (int m = 0; m < NX; ++m) st[m] = (T)S[m];
+  for (int m = 0; m < NX; ++m) st[m] = S[m];
   const bool wantb = DIR == 1 && bout != nullptr;
   for (int c = 0; c < SEG / CH; ++c) {
     const int i0 = (DIR == 0 ? c : SEG / CH - 1 - c) * CH;
@@ -600,14 +599,15 @@ static bk_status sweep_attrs_nx(int nx) {
   return sweep_attrs<T, 4>();
 }
 
-static Levels levels_of(const Problem* pr, const OpData& d) {
-  Levels lv;
+template <typename T>
+static Levels<T> levels_of(const Problem* pr, const OpData& d) {
+  Levels<T> lv;
   memset(&lv, 0, sizeof(lv));
   lv.nlev = pr->nlev;
   for (int l = 0; l < pr->nlev; ++l) {
-    lv.m[l] = d.lvm[l];
-    lv.o[l] = d.lvo[l];
-    lv.e[l] = d.lve[l];
+    lv.m[l] = (const T*)d.lvm[l];
+    lv.o[l] = (T*)d.lvo[l];
+    lv.e[l] = (T*)d.lve[l];
     lv.n[l] = pr->lvn[l];
   }
   return lv;
@@ -621,13 +621,13 @@ static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* ou
   BK_ARG(d.dtype == pr->dtype && d.Kn != nullptr, "sweeps run in the problem's working precision only");
   const T s = (T)pr->s;
   const T* w = (const T*)d.w;
-  const Levels lv = levels_of(pr, d);
+  const Levels<T> lv = levels_of<T>(pr, d);
   const int g0 = (((pr->lvn[0] + 31) >> 5) + 3) / 4;
   k_sw_up0<T, NX, DIR><<<g0, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv);
   BK_CHECK_LAUNCH();
   for (int l = 1; l < pr->nlev; ++l) {
     const int gl = (((pr->lvn[l] + 31) >> 5) + 3) / 4;
-    k_sw_upL<NX, DIR><<<gl, 128, 0, st>>>(lv, l);
+    k_sw_upL<T, NX, DIR><<<gl, 128, 0, st>>>(lv, l);
     BK_CHECK_LAUNCH();
   }
   k_sw_down0<T, NX, DIR><<<g0, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv, out, bout);
@@ -807,16 +807,26 @@ __global__ void k_pre_fix(const T* __restrict__ Zc, const T* __restrict__ HWc, c
                           const T* __restrict__ ynu, int n_e, int64_t P, int64_t L, T* __restrict__ yx,
                           T* __restrict__ yu, T* __restrict__ yl) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+    // the node's outputs stay in registers over the n_e columns (one read and one write each)
+    T ax[NX], al[NX], au[NU];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) { ax[m] = yx[m * P + k]; al[m] = yl[m * P + k]; }
+#pragma unroll
+    for (int q = 0; q < NU; ++q) au[q] = yu[q * P + k];
     for (int r = 0; r < n_e; ++r) {
       const T c = ynu[r];
 #pragma unroll
       for (int m = 0; m < NX; ++m) {
-        yx[m * P + k] -= c * Qc[((int64_t)r * NX + m) * P + k];
-        yl[m * P + k] -= c * Zc[((int64_t)r * NX + m) * P + k];
+        ax[m] -= c * Qc[((int64_t)r * NX + m) * P + k];
+        al[m] -= c * Zc[((int64_t)r * NX + m) * P + k];
       }
 #pragma unroll
-      for (int q = 0; q < NU; ++q) yu[q * P + k] += c * HWc[((int64_t)r * NU + q) * P + k];
+      for (int q = 0; q < NU; ++q) au[q] += c * HWc[((int64_t)r * NU + q) * P + k];
     }
+#pragma unroll
+    for (int m = 0; m < NX; ++m) { yx[m * P + k] = ax[m]; yl[m * P + k] = al[m]; }
+#pragma unroll
+    for (int q = 0; q < NU; ++q) yu[q * P + k] = au[q];
   }
 }
 
@@ -987,9 +997,9 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
   }
   for (int l = 0; pre && l < pr->nlev; ++l) {
     const size_t npad = (size_t)round_up(pr->lvn[l], 32);
-    BK_TRY(dmalloc((void**)&d.lvm[l], sizeof(double) * NSLOT * npad * nx * nx));
-    BK_TRY(dmalloc((void**)&d.lve[l], sizeof(double) * npad * nx));
-    if (l > 0) BK_TRY(dmalloc((void**)&d.lvo[l], sizeof(double) * npad * nx));
+    BK_TRY(dmalloc(&d.lvm[l], es * NSLOT * npad * nx * nx));
+    BK_TRY(dmalloc(&d.lve[l], es * npad * nx));
+    if (l > 0) BK_TRY(dmalloc(&d.lvo[l], es * npad * nx));
   }
   if (pre && ne > 0) {
     BK_TRY(dmalloc(&d.Zc, es * ne * nx * P));
@@ -1021,10 +1031,11 @@ static bk_status lin_factors(Problem* pr, OpData& d, const double* z, cudaStream
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   k_lin_nodes<T, KIND, NX, NU><<<nblk(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->d64.plan->w64, pr->s, (T*)d.Kn, (T*)d.Nn, (T*)d.xu);
   BK_CHECK_LAUNCH();
-  k_lin_seg<T, NX><<<(pr->nseg + 127) / 128, 128, 0, st>>>((const T*)d.Nn, pr->L, pr->nseg, d.lvm[0]);
+  k_lin_seg<T, NX><<<(pr->nseg + 127) / 128, 128, 0, st>>>((const T*)d.Nn, pr->L, pr->nseg, (T*)d.lvm[0]);
   BK_CHECK_LAUNCH();
   for (int l = 0; l < pr->nlev; ++l) {
-    k_lin_level<NX><<<(pr->lvn[l] + 31) / 32, 32, 0, st>>>(d.lvm[l], pr->lvn[l], l + 1 < pr->nlev ? d.lvm[l + 1] : nullptr);
+    k_lin_level<T, NX><<<(pr->lvn[l] + 31) / 32, 32, 0, st>>>((T*)d.lvm[l], pr->lvn[l],
+                                                              l + 1 < pr->nlev ? (T*)d.lvm[l + 1] : nullptr);
     BK_CHECK_LAUNCH();
   }
   return BK_OK;

@@ -8,10 +8,13 @@
 //
 // Arnoldi orthogonalisation: classical Gram-Schmidt with the Daniel-Gragg-Kaufman-Stewart test.
 // One pass forms h = V^T w and |w|^2, the next w <- w - V h with |w|^2 of the result; a second
-// pass runs only when the norm fell below 1/sqrt 2 of its value (cancellation). The dot and
-// update passes are bound by FP64 FMA throughput (one FMA per 8-byte operand), so each skipped
-// pass counts. Dot products accumulate in FP64 with a fixed block count and reduction order, so
-// results do not depend on scheduling. The (m+1) x m Hessenberg matrix and its Givens rotations
+// pass runs only when the norm fell below 1/sqrt 2 of its value (cancellation). In FP64 the dot
+// and update passes are bound by FP64 FMA throughput (one FMA per 8-byte operand), so each
+// skipped pass counts. Dot products are FP64 sums with a fixed block count and reduction order,
+// so results do not depend on scheduling. FP32 vectors are multiplied and summed in FP32 over
+// runs of 16 elements per thread, each run then added to the thread's FP64 total: on GB300 FP64
+// (and every float-to-double conversion) runs at 1/64 of the FP32 rate, and converting each
+// operand made the FP32 passes slower than the FP64 ones. The (m+1) x m Hessenberg matrix and its Givens rotations
 // live on the host (FP64); the iteration reads back j+3 numbers per step.
 #include <math.h>
 #include <string.h>
@@ -25,14 +28,34 @@ namespace bk {
 static constexpr int DOT_BLOCKS = 608;   // 4 blocks per SM on 152 SMs, fixed for determinism
 static constexpr int MAXM = 100;
 
+// FP32 elements per thread summed in FP32 before each FP64 accumulation.
+constexpr int RUN32 = 16;
+
 template <typename T, int CNT>
 __device__ __forceinline__ void dot_group(const T* __restrict__ V, int64_t ld, const T* __restrict__ w, int64_t lo,
                                           int64_t hi, double* acc) {
+  if constexpr (sizeof(T) == 8) {
 #pragma unroll 2
-  for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-    const double wk = (double)w[k];
+    for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+      const double wk = w[k];
 #pragma unroll
-    for (int q = 0; q < CNT; ++q) acc[q] += (double)V[(int64_t)q * ld + k] * wk;
+      for (int q = 0; q < CNT; ++q) acc[q] += V[(int64_t)q * ld + k] * wk;
+    }
+  } else {
+    int64_t k = lo + threadIdx.x;
+    while (k < hi) {
+      float a[CNT];
+#pragma unroll
+      for (int q = 0; q < CNT; ++q) a[q] = 0.f;
+#pragma unroll 4
+      for (int it = 0; it < RUN32 && k < hi; ++it, k += blockDim.x) {
+        const float wk = w[k];
+#pragma unroll
+        for (int q = 0; q < CNT; ++q) a[q] = fmaf(V[(int64_t)q * ld + k], wk, a[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < CNT; ++q) acc[q] += (double)a[q];
+    }
   }
 }
 
@@ -99,25 +122,53 @@ __global__ void __launch_bounds__(256) k_multiaxpy(const T* __restrict__ V, int6
                                                    const double* __restrict__ c, double cscale, T* __restrict__ w,
                                                    double alpha, int64_t n, double* __restrict__ partial) {
   __shared__ double cs[MAXM + 1];
+  __shared__ float cs32[MAXM + 1];
   __shared__ double red[8];
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) cs[i] = cscale * c[i];
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    cs[i] = cscale * c[i];
+    cs32[i] = (float)(cscale * c[i]);
+  }
   __syncthreads();
   double sq = 0.0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    double a = alpha == 0.0 ? 0.0 : alpha * (double)w[k];
-    int i = 0;
-    for (; i + 4 <= nv; i += 4) {
-      const double v0 = (double)V[(int64_t)i * ld + k], v1 = (double)V[(int64_t)(i + 1) * ld + k];
-      const double v2 = (double)V[(int64_t)(i + 2) * ld + k], v3 = (double)V[(int64_t)(i + 3) * ld + k];
-      a += cs[i] * v0;
-      a += cs[i + 1] * v1;
-      a += cs[i + 2] * v2;
-      a += cs[i + 3] * v3;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if constexpr (sizeof(T) == 8) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride) {
+      double a = alpha == 0.0 ? 0.0 : alpha * w[k];
+      int i = 0;
+      for (; i + 4 <= nv; i += 4) {
+        const double v0 = V[(int64_t)i * ld + k], v1 = V[(int64_t)(i + 1) * ld + k];
+        const double v2 = V[(int64_t)(i + 2) * ld + k], v3 = V[(int64_t)(i + 3) * ld + k];
+        a += cs[i] * v0;
+        a += cs[i + 1] * v1;
+        a += cs[i + 2] * v2;
+        a += cs[i + 3] * v3;
+      }
+      for (; i < nv; ++i) a += cs[i] * V[(int64_t)i * ld + k];
+      w[k] = a;
+      sq += a * a;
     }
-    for (; i < nv; ++i) a += cs[i] * (double)V[(int64_t)i * ld + k];
-    const T r = (T)a;
-    w[k] = r;
-    sq += (double)r * (double)r;
+  } else {
+    const float al = (float)alpha;
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    while (k < n) {
+      float s32 = 0.f;
+      for (int it = 0; it < RUN32 && k < n; ++it, k += stride) {
+        float a = alpha == 0.0 ? 0.f : al * (float)w[k];
+        int i = 0;
+        for (; i + 4 <= nv; i += 4) {
+          const float v0 = V[(int64_t)i * ld + k], v1 = V[(int64_t)(i + 1) * ld + k];
+          const float v2 = V[(int64_t)(i + 2) * ld + k], v3 = V[(int64_t)(i + 3) * ld + k];
+          a = fmaf(cs32[i], v0, a);
+          a = fmaf(cs32[i + 1], v1, a);
+          a = fmaf(cs32[i + 2], v2, a);
+          a = fmaf(cs32[i + 3], v3, a);
+        }
+        for (; i < nv; ++i) a = fmaf(cs32[i], (float)V[(int64_t)i * ld + k], a);
+        w[k] = (T)a;
+        s32 = fmaf(a, a, s32);
+      }
+      sq += (double)s32;
+    }
   }
   if (partial) {
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -134,16 +185,17 @@ __global__ void __launch_bounds__(256) k_multiaxpy(const T* __restrict__ V, int6
 // y <- a * x + b * y  (a, b host scalars)
 template <typename T>
 __global__ void k_axpby(const T* __restrict__ x, double a, T* __restrict__ y, double b, int64_t n) {
+  const T aa = (T)a, bb = (T)b;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    y[k] = (T)(a * (double)x[k] + (b == 0.0 ? 0.0 : b * (double)y[k]));
+    y[k] = b == 0.0 ? aa * x[k] : aa * x[k] + bb * y[k];
 }
 
 // y <- x * (1 / c[0])  (scale by a device scalar)
 template <typename T>
 __global__ void k_scale_inv(const T* __restrict__ x, const double* __restrict__ c, T* __restrict__ y, int64_t n) {
-  const double inv = 1.0 / c[0];
+  const T inv = (T)(1.0 / c[0]);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    y[k] = (T)((double)x[k] * inv);
+    y[k] = x[k] * inv;
 }
 
 template <typename T>

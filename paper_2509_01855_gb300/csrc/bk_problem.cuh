@@ -22,7 +22,7 @@ inline int seg_nodes(int dtype) { return dtype == BK_F64 ? Seg<double>::v : Seg<
 // Scan levels of the preconditioner sweep: level 0 items are segments, level l + 1 items are
 // blocks of 32 level-l items, up to the first level with at most 32 items (N <= 2^24: 4 levels).
 constexpr int MAXLEV = 5;
-// Matrix slots stored per level item (FP64, 32-interleaved): the item's map A, the spans
+// Matrix slots stored per level item (working type, 32-interleaved): the item's map A, the spans
 // M_k = product of the 2^k items ending at this one (k = 1..4, within its block of 32), and the
 // products of the items before (Pre) and after (Suf) it in its block.
 enum { SL_A = 0, SL_M1 = 1, SL_PRE = 5, SL_SUF = 6, NSLOT = 7 };
@@ -122,9 +122,9 @@ struct OpData {
   void* w = nullptr;           // Clenshaw-Curtis weights (L), working type
   void* Kn = nullptr;          // per-node K_k = (I - h_k J_k)^{-1}, interleaved (n_x^2 per node)
   void* Nn = nullptr;          // per-node N_k = 2 h_k J_k K_k, interleaved
-  double* lvm[MAXLEV] = {};    // per level: NSLOT matrix slots (n_x^2 per item each), FP64
-  double* lvo[MAXLEV] = {};    // per level >= 1: item offsets from zero (n_x per item), per sweep
-  double* lve[MAXLEV] = {};    // per level: inclusive in-block scan values (n_x per item), per sweep
+  void* lvm[MAXLEV] = {};      // per level: NSLOT matrix slots (n_x^2 per item each), working type
+  void* lvo[MAXLEV] = {};      // per level >= 1: item offsets from zero (n_x per item), per sweep
+  void* lve[MAXLEV] = {};      // per level: inclusive in-block scan values (n_x per item), per sweep
   // KKT preconditioner (terminal Schur data)
   void* Zc = nullptr;          // n_e state vectors   Z = P^{-T} E^T
   void* HWc = nullptr;         // n_e control vectors H~^{-1} W, W = Pu^T Z
