@@ -128,6 +128,22 @@ bk_status birkhoff_apply_noalloc(const double* v, double* out, int64_t N, int nv
 bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int batch,
                            void* stream);
 
+/* Switch a BK_F32 plan with N <= 1024 between the FFT chain (on = 0) and the dense product on
+ * the tensor cores (on = 1) for birkhoff_apply, birkhoff_apply_T and every operator built on the
+ * plan. The dense path multiplies by B^a itself (the matrix of Eq. manyDefs, formed once from
+ * the FP64 FFT product of the unit vectors) split into two TF32 parts, three tcgen05 TF32
+ * products per block accumulated in FP32 (the paper's Fig. 5 compares FastBV with the dense
+ * product on a CPU). The first switch on builds the tables (two N+1 x N+1 matrices of 8-byte
+ * hi/lo pairs, ~19 MB at N = 1024) on `stream` and synchronises it; the plan owns them.
+ * Errors: BK_ERR_UNSUPPORTED for FP64 plans or N > 1024; BK_ERR_OOM; BK_ERR_CUDA. Not thread
+ * safe against applies of the same plan in flight. */
+bk_status bk_plan_set_dense(bk_plan* plan, int on, void* stream);
+
+/* Read (and clear) the dense kernel's error word: *err = 0 when every dense product so far
+ * completed; otherwise a wait inside the kernel ran out (1: operand copy or MMA completion,
+ * 2: accumulator read) and that product's output is not valid. Synchronous (device sync). */
+bk_status bk_plan_dense_check(const bk_plan* plan, int* err);
+
 /* ------------------------------------------------------------------------------------------
  * Problems: dynamics x' = f(x, u) of Eq. probPbold, discretised by Eq. Prob-PNa.
  * ------------------------------------------------------------------------------------------ */

@@ -50,6 +50,17 @@ class Plan:
         L.check(L.lib().bk_plan_grid(self._h, L.ptr(t), L.ptr(w)))
         return t, w
 
+    def set_dense(self, on=True, stream=None):
+        """Products through the dense tensor-core path (BK_F32 plans, N <= 1024) or the FFT chain."""
+        L.check(L.lib().bk_plan_set_dense(self._h, 1 if on else 0, L.stream_ptr(stream)))
+        self.dense = bool(on)
+
+    def dense_check(self):
+        """Error word of the dense kernel since the last check (0: every product completed)."""
+        e = ctypes.c_int(0)
+        L.check(L.lib().bk_plan_dense_check(self._h, ctypes.byref(e)))
+        return e.value
+
     def empty(self, batch=1, device="cuda"):
         """A zeroed [batch, n_comp, pitch] tensor of the plan's dtype."""
         return torch.zeros(batch, self.n_comp, self.pitch, dtype=self.dtype, device=device)

@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-DNDEBUG"]
-SOURCES = ["bk_birkhoff.cu", "bk_kkt.cu", "bk_krylov.cu", "bk_newton.cu"]
+SOURCES = ["bk_birkhoff.cu", "bk_dense.cu", "bk_kkt.cu", "bk_krylov.cu", "bk_newton.cu"]
 
 
 def _nvcc():

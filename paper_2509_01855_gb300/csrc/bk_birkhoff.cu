@@ -339,6 +339,10 @@ __device__ void dct1_block(const T* __restrict__ X, int kind, T* __restrict__ Y,
 // Thread cap of the transform kernels: each thread stages 16 complex values, so FP64 kernels
 // are limited to 256 threads (up to 255 registers each) and FP32 ones to 512.
 template <typename T> struct MaxThr { static constexpr int v = sizeof(T) == 8 ? 256 : 512; };
+// Element loads each thread keeps in flight in the pass kernels' load phases.
+// FP32: 8 (latency-bound passes; 16 spilled under the 64-register cap of two 512-thread CTAs
+// per SM), FP64: 4 (FP64-pipe-bound, register-heavy).
+template <typename T> struct InFlight { static constexpr int v = sizeof(T) == 8 ? 4 : 8; };
 
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(MaxThr<T>::v)
@@ -411,11 +415,12 @@ __device__ __forceinline__ void passA_body(
   constexpr bool DC = (K == IN_WINV || K == ST_FWD) && MODE != PM_DCT3;
   T dc = T(0);
   const int total = NB * N1;
-  // 4 independent element loads in flight per thread before the shared-memory stores
-  for (int idx0 = threadIdx.x; idx0 < total; idx0 += 4 * blockDim.x) {
-    C z[4];
+  // independent element loads in flight per thread before the shared-memory stores
+  constexpr int LD = InFlight<T>::v;
+  for (int idx0 = threadIdx.x; idx0 < total; idx0 += LD * blockDim.x) {
+    C z[LD];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < LD; ++u) {
       const int idx = idx0 + u * blockDim.x;
       if (idx < total) {
         const int b = idx & (NB - 1);
@@ -426,7 +431,7 @@ __device__ __forceinline__ void passA_body(
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < LD; ++u) {
       const int idx = idx0 + u * blockDim.x;
       if (idx < total) {
         if (DC) dc += z[u].x + z[u].y;
@@ -483,7 +488,7 @@ __device__ __forceinline__ void passA_body(
 
 // Pass A of one transform (unsplit, or one half of a split DCT-I).
 template <typename T, int K, int MODE = PM_FULL>
-__global__ void __launch_bounds__(MaxThr<T>::v)
+__global__ void __launch_bounds__(MaxThr<T>::v, 2)
     k_passA(BK_PASSA_PARAMS(), T invN, StencilTab<T> tb, const typename V2<T>::t* __restrict__ tpost = nullptr,
             const typename V2<T>::t* __restrict__ eo = nullptr) {
   passA_body<T, K, MODE>(blockIdx.x, gridDim.x, BK_PASSA_ARGS(), invN, tb, BK_PASSA_TAIL(), tpost, eo);
@@ -492,7 +497,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
 // Pass A of both halves of a split DCT-I in one launch: CTAs [0, gE) run the even half (pair
 // sums), the rest the odd half (DCT-III); one launch fills the GPU better than two smaller ones.
 template <typename T, int K>
-__global__ void __launch_bounds__(MaxThr<T>::v)
+__global__ void __launch_bounds__(MaxThr<T>::v, 2)
     k_passA_split(int gE, BK_PASSA_PARAMS(E), BK_PASSA_PARAMS(O), T invN, StencilTab<T> tb,
                   const typename V2<T>::t* __restrict__ tpost, const typename V2<T>::t* __restrict__ eo) {
   if ((int)blockIdx.x < gE)
@@ -598,10 +603,11 @@ __device__ __forceinline__ void passB_body(
   }
   // load 2P rows: PB_PAIRS local row q = 2 i (+1) for pair p0 + i; PB_ROWS rows 2 p0 + q
   const int total = 2 * P * N2;
-  for (int idx0 = threadIdx.x; idx0 < total; idx0 += 4 * blockDim.x) {
-    C z[4];
+  constexpr int LD = InFlight<T>::v;
+  for (int idx0 = threadIdx.x; idx0 < total; idx0 += LD * blockDim.x) {
+    C z[LD];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < LD; ++u) {
       const int idx = idx0 + u * blockDim.x;
       if (idx < total) {
         const int q = idx >> log2N2;
@@ -616,7 +622,7 @@ __device__ __forceinline__ void passB_body(
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < LD; ++u) {
       const int idx = idx0 + u * blockDim.x;
       if (idx < total) {
         const int q = idx >> log2N2;
@@ -706,7 +712,7 @@ __device__ __forceinline__ void passB_body(
       const typename V2<T>::t* __restrict__ stw##S
 
 template <typename T, int E, int MODE = PB_PAIRS>
-__global__ void __launch_bounds__(MaxThr<T>::v)
+__global__ void __launch_bounds__(MaxThr<T>::v, 2)
     k_passB(const typename V2<T>::t* __restrict__ Ain, T* __restrict__ dst, int64_t dst_stride,
             int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial, int N, int N1,
             int N2, int log2N2, int P, const typename V2<T>::t* __restrict__ stw,
@@ -718,7 +724,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
 // Pass B of both halves of a split DCT-I in one launch: CTAs [0, gE) the even half's row pairs
 // and real split (outputs at even indices), the rest the odd half's rows (odd indices).
 template <typename T, int E>
-__global__ void __launch_bounds__(MaxThr<T>::v)
+__global__ void __launch_bounds__(MaxThr<T>::v, 2)
     k_passB_split(int gE, BK_PASSB_PARAMS(E), BK_PASSB_PARAMS(O), T* __restrict__ dst, int64_t dst_stride,
                   int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial,
                   const typename V2<T>::t* __restrict__ tpost, T s, T invN, int Npar) {
@@ -853,11 +859,12 @@ static bk_status compute_weights(Plan* p, cudaStream_t st) {
   return r;
 }
 
-// Largest N run by the single-CTA kernel (one CTA per vector): 2048 in FP64, whose single CTA
-// runs on one SM's FP64 pipe (at 4096 x 4 components: 0.129 ms single-CTA vs 0.066 ms four-step),
-// 8192 in FP32 (at 8192: 0.027 vs 0.033 ms). BK_SMALL_MAX_LOG2 overrides it for tuning (at least
-// 2^4; at most the shared-memory limit of 4096 in FP64, 8192 in FP32).
-static int small_default(int dtype) { return dtype == BK_F64 ? 2048 : 8192; }
+// Largest N run by the single-CTA kernel (one CTA per vector): 128 in FP64, whose single CTA
+// runs on one SM's FP64 pipe (4 components, cold L2, B / four-step ms: 2^8 0.062 / 0.056,
+// 2^10 0.089 / 0.068, 2^11 0.097 / 0.074), 4096 in FP32 (2^12 0.034 / 0.038, 2^13 0.044 /
+// 0.042). BK_SMALL_MAX_LOG2 overrides it for tuning (at least 2^4; at most the shared-memory
+// limit of 4096 in FP64, 8192 in FP32). The four-step kernels need N >= 256.
+static int small_default(int dtype) { return dtype == BK_F64 ? 128 : 4096; }
 static int small_limit(int dtype) {
   const int cap = dtype == BK_F64 ? 4096 : 8192;
   const char* e = getenv("BK_SMALL_MAX_LOG2");
@@ -1093,6 +1100,9 @@ void plan_destroy(Plan* p) {
   dfree(p->part1);
   dfree(p->part2);
   dfree(p->t_nodes);
+  dfree(p->dA[0]);
+  dfree(p->dA[1]);
+  dfree(p->derr);
   delete p;
 }
 
@@ -1220,6 +1230,7 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
 
 bk_status plan_apply_n(const Plan* p, const void* v, void* out, int nvec, bool trans, double s,
                        cudaStream_t st) {
+  if (p->dense) return dense_apply(p, (const float*)v, (float*)out, nvec, trans, s, st);
   if (p->dtype == BK_F64)
     return apply_impl<double>(p, (const double*)v, (double*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2, p->scrG);
   return apply_impl<float>(p, (const float*)v, (float*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2, p->scrG);
@@ -1391,6 +1402,36 @@ bk_status birkhoff_apply_noalloc(const double* v, double* out, int64_t N, int nv
 
 bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int batch, void* stream) {
   return bk::plan_apply(reinterpret_cast<const bk::Plan*>(plan), v, out, batch, true, (cudaStream_t)stream);
+}
+
+bk_status bk_plan_set_dense(bk_plan* plan, int on, void* stream) {
+  BK_ARG(plan != nullptr, "plan is NULL");
+  bk::Plan* p = reinterpret_cast<bk::Plan*>(plan);
+  if (!on) {
+    p->dense = false;
+    return BK_OK;
+  }
+  if (p->dtype != BK_F32 || !bk::dense_supported(p->N)) {
+    bk::set_error("dense products need a BK_F32 plan with N <= 1024 (N = %lld)", (long long)p->N);
+    return BK_ERR_UNSUPPORTED;
+  }
+  if (!p->dA[0]) {
+    bk::AllocCounter counter(&p->bytes);
+    BK_TRY(bk::dense_build(p, (cudaStream_t)stream));
+  }
+  p->dense = true;
+  return BK_OK;
+}
+
+bk_status bk_plan_dense_check(const bk_plan* plan, int* err) {
+  BK_ARG(plan != nullptr && err != nullptr, "NULL argument");
+  const bk::Plan* p = reinterpret_cast<const bk::Plan*>(plan);
+  *err = 0;
+  if (!p->derr) return BK_OK;
+  BK_TRY_CUDA(cudaDeviceSynchronize());
+  BK_TRY_CUDA(cudaMemcpy(err, p->derr, sizeof(int), cudaMemcpyDeviceToHost));
+  BK_TRY_CUDA(cudaMemset(p->derr, 0, sizeof(int)));
+  return BK_OK;
 }
 
 }  // extern "C"

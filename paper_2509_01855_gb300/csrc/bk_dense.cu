@@ -1,0 +1,335 @@
+// Dense small-N Birkhoff products on the 5th-generation tensor cores (tcgen05).
+//
+// For small N the FFT chain of a product is latency-bound (one CTA per vector runs two DCTs and
+// the stencil one after the other), while the dense product out = s B^a V is a small GEMM:
+// M = N + 1 output nodes, K = N + 1 input nodes, one column per vector. This path keeps B^a
+// (and its transpose, for B^T) as a pre-tiled FP32 matrix split into two TF32 parts,
+// A = A_hi + A_lo (each rounded to TF32), and multiplies on the tensor cores with kind::tf32:
+//   D = A_hi V_hi + A_hi V_lo + A_lo V_hi        (3xTF32; the A_lo V_lo term is below FP32),
+// accumulating in FP32 in tensor memory. B^a itself comes from the FP64 FFT product applied to
+// the unit vectors (columns of B^a, Eq. xN=Birka+b: the a-form integration matrix), so its
+// entries are FP64-exact before the split.
+//
+// Kernel shape (one CTA of 4 warps per 128 output rows and 16 vectors):
+//   - thread 0 streams the CTA's A panel through two shared-memory stages with bulk copies
+//     (cp.async.bulk, completion on an mbarrier) and issues the MMAs (M = 128, N = 16, K = 8);
+//   - all threads stage the CTA's 16 vectors once, split into TF32 hi and lo parts;
+//   - tcgen05.commit arrives on an mbarrier when a stage's MMAs are done (the stage is then
+//     refilled) and when the last MMA is done (the epilogue then reads the accumulator);
+//   - each warp reads its 32 accumulator lanes with tcgen05.ld and writes s D to the output.
+// Every wait is bounded; on a timeout the kernel records an error code, waits (bounded) for its
+// copies in flight, frees its tensor memory and returns.
+//
+// Shared-memory operand layout (no swizzle, K-major): core matrices of 8 rows x 16 bytes (8 x 4
+// TF32 values, rows 16 bytes apart). For one MMA k-step (8 values of K) the two core matrices
+// along K sit 128 bytes apart (leading byte offset) and successive 8-row groups 256 bytes apart
+// (stride byte offset); k-steps follow each other. Both strides stay inside the k-step's block
+// whichever way the two offsets are read, so a misread layout gives wrong values, never an
+// out-of-range shared access.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "bk_plan.cuh"
+
+namespace bk {
+
+constexpr int DT_M = 128;                              // output rows per CTA (MMA M)
+constexpr int DT_N = 16;                               // vectors per CTA (MMA N)
+constexpr int DT_KC = 32;                              // K values per pipeline chunk (4 k-steps)
+constexpr int DT_STAGES = 2;                           // A chunk buffers
+constexpr int DT_PART = DT_M * DT_KC * 4;              // one TF32 part of a chunk: 16 KB
+constexpr int DT_CHUNK = 2 * DT_PART;                  // hi + lo: 32 KB
+constexpr int DT_TMEM_COLS = 32;                       // accumulator columns allocated (>= DT_N)
+constexpr unsigned DT_SPIN = 1u << 20;                 // mbarrier polls before a timeout
+constexpr int DENSE_MAX_N = 1024;                      // V (2 parts x 16 x K) stays in shared memory
+
+// Byte offset of A element (m, k), m < 128, k < 32, inside one part of a chunk.
+__host__ __device__ inline int dt_a_off(int m, int k) {
+  return (k >> 3) * 4096 + (m >> 3) * 256 + ((k >> 2) & 1) * 128 + (m & 7) * 16 + (k & 3) * 4;
+}
+// Byte offset of V element (vector n < 16, node k) inside one part of the staged vectors.
+__host__ __device__ inline int dt_v_off(int n, int k) {
+  return (k >> 3) * 512 + (n >> 3) * 256 + ((k >> 2) & 1) * 128 + (n & 7) * 16 + (k & 3) * 4;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Round to TF32 (10 explicit mantissa bits), to nearest, ties away from zero.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Shared-memory matrix descriptor: start address, leading and stride byte offsets (all >> 4),
+// descriptor version 1 (bits 46-48 = 0b001), base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t dt_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
+// 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t dt_idesc() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(DT_N >> 3) << 17) | ((uint32_t)(DT_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (unsigned i = 0; i < DT_SPIN; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// out[n][m] = s (A V)[m][n] for m < L, n < nvec, with A = A_hi + A_lo pre-tiled in `At`
+// (chunk (mt, c) of 128 rows x 32 columns at ((mt nK + c) * 32 KB), hi part then lo part).
+// V and out: nvec vectors `pitch` apart; out's padding [L, pitch) is zeroed.
+__global__ void __launch_bounds__(128, 1)
+    k_dense_tc(const unsigned char* __restrict__ At, const float* __restrict__ V, float* __restrict__ out, int nvec,
+               int L, int64_t pitch, int nK, float s, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar_full[DT_STAGES];
+  __shared__ __align__(8) uint64_t bar_empty[DT_STAGES];
+  __shared__ __align__(8) uint64_t bar_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mt = blockIdx.x, n0 = blockIdx.y * DT_N;
+  const int Kpad = nK * DT_KC;
+  unsigned char* sA = smem;                          // DT_STAGES chunks
+  unsigned char* sV = smem + DT_STAGES * DT_CHUNK;   // hi part, then lo part
+  const int vpart = Kpad * DT_N * 4;
+  const uint32_t aA = smem_u32(sA), aV = smem_u32(sV);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(DT_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < DT_STAGES; ++i) {
+      mbar_init(smem_u32(&bar_full[i]), 1);
+      mbar_init(smem_u32(&bar_empty[i]), 1);
+    }
+    mbar_init(smem_u32(&bar_done), 1);
+    fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem_d = tmem_slot;
+
+  // first chunks in flight while the vectors are staged
+  const unsigned char* Ablk = At + (size_t)mt * nK * DT_CHUNK;
+  if (tid == 0) {
+    for (int c = 0; c < DT_STAGES && c < nK; ++c) {
+      mbar_expect_tx(smem_u32(&bar_full[c]), DT_CHUNK);
+      bulk_g2s(aA + c * DT_CHUNK, Ablk + (size_t)c * DT_CHUNK, DT_CHUNK, smem_u32(&bar_full[c]));
+    }
+  }
+  // vectors n0..n0+15, nodes k < Kpad (zero beyond L and nvec), split into TF32 hi and lo
+  for (int i = tid; i < DT_N * Kpad; i += blockDim.x) {
+    const int n = i / Kpad, k = i - n * Kpad;
+    float v = 0.f;
+    if (n0 + n < nvec && k < L) v = V[(int64_t)(n0 + n) * pitch + k];
+    const float hi = tf32_rna(v);
+    const float lo = tf32_rna(v - hi);
+    const int off = dt_v_off(n, k);
+    *reinterpret_cast<float*>(sV + off) = hi;
+    *reinterpret_cast<float*>(sV + vpart + off) = lo;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // staged vectors -> tensor core reads
+  __syncthreads();
+
+  if (tid == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    constexpr uint32_t idesc = dt_idesc();
+    int issued = nK < DT_STAGES ? nK : DT_STAGES;  // chunks whose copies were started
+    int c = 0;
+    bool ok = true;
+    for (; c < nK; ++c) {
+      const int st = c % DT_STAGES;
+      const uint32_t ph = (uint32_t)(c / DT_STAGES) & 1u;
+      if (!mbar_wait(smem_u32(&bar_full[st]), ph)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int ks = 0; ks < DT_KC / 8; ++ks) {
+        const uint32_t ahi = aA + st * DT_CHUNK + ks * 4096, alo = ahi + DT_PART;
+        const int kg = c * (DT_KC / 8) + ks;
+        const uint32_t vhi = aV + kg * 512, vlo = vhi + vpart;
+        const uint64_t dAh = dt_desc(ahi, 128, 256), dAl = dt_desc(alo, 128, 256);
+        const uint64_t dVh = dt_desc(vhi, 128, 256), dVl = dt_desc(vlo, 128, 256);
+        tc_mma(tmem_d, dAh, dVh, idesc, (c | ks) != 0 ? 1u : 0u);
+        tc_mma(tmem_d, dAh, dVl, idesc, 1u);
+        tc_mma(tmem_d, dAl, dVh, idesc, 1u);
+      }
+      tc_commit(smem_u32(&bar_empty[st]));
+      if (c + DT_STAGES < nK) {
+        // refill this stage once its MMAs have read it
+        if (!mbar_wait(smem_u32(&bar_empty[st]), ph)) { ok = false; ++c; break; }
+        mbar_expect_tx(smem_u32(&bar_full[st]), DT_CHUNK);
+        bulk_g2s(aA + st * DT_CHUNK, Ablk + (size_t)(c + DT_STAGES) * DT_CHUNK, DT_CHUNK, smem_u32(&bar_full[st]));
+        ++issued;
+      }
+    }
+    tc_commit(smem_u32(&bar_done));
+    if (!ok) {
+      fail = 1;
+      // copies started but not consumed: wait for them (bounded) before the CTA may exit
+      for (int q = c; q < issued; ++q) (void)mbar_wait(smem_u32(&bar_full[q % DT_STAGES]), (uint32_t)(q / DT_STAGES) & 1u);
+    }
+  }
+  // every lane waits (bounded); the warp then agrees, since tcgen05.ld is warp-collective
+  const bool mine = mbar_wait(smem_u32(&bar_done), 0);
+  __syncwarp();
+  const bool done = __all_sync(0xffffffffu, mine);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (done) {
+    uint32_t r[16];
+    const uint32_t taddr = tmem_d + ((uint32_t)(warp * 32) << 16);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int m = mt * DT_M + warp * 32 + lane;
+    if (m < L) {
+#pragma unroll
+      for (int n = 0; n < DT_N; ++n)
+        if (n0 + n < nvec) out[(int64_t)(n0 + n) * pitch + m] = s * __uint_as_float(r[n]);
+    }
+  } else if (lane == 0) {
+    fail = 2;
+  }
+  if (mt == 0) {
+    for (int n = 0; n < DT_N && n0 + n < nvec; ++n)
+      for (int64_t m = L + tid; m < pitch; m += blockDim.x) out[(int64_t)(n0 + n) * pitch + m] = 0.f;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(DT_TMEM_COLS) : "memory");
+  if (tid == 0 && fail) atomicExch(err, fail);
+}
+
+// Pre-tiled A = B^a (trans = 0) or (B^a)^T (trans = 1) from the columns of B^a (FP64,
+// column k at cols[k * pitch], entry m = B^a[m][k]), zero outside L x L.
+__global__ void k_dense_tile(const double* __restrict__ cols, int64_t pitch, int L, int Mt, int nK, int trans,
+                             unsigned char* __restrict__ dst) {
+  const int Kpad = nK * DT_KC;
+  const int64_t total = (int64_t)Mt * DT_M * Kpad;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(i / Kpad), k = (int)(i - (int64_t)m * Kpad);
+    double a = 0.0;
+    if (m < L && k < L) a = trans ? cols[(int64_t)m * pitch + k] : cols[(int64_t)k * pitch + m];
+    const float hi = tf32_rna((float)a);
+    const float lo = tf32_rna((float)(a - (double)hi));
+    unsigned char* blk = dst + ((size_t)(m / DT_M) * nK + k / DT_KC) * DT_CHUNK;
+    const int off = dt_a_off(m % DT_M, k % DT_KC);
+    *reinterpret_cast<float*>(blk + off) = hi;
+    *reinterpret_cast<float*>(blk + DT_PART + off) = lo;
+  }
+}
+
+__global__ void k_identity(double* __restrict__ e, int L, int64_t pitch) {
+  const int64_t total = (int64_t)L * pitch;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / pitch, m = i - k * pitch;
+    e[i] = (m == k) ? 1.0 : 0.0;
+  }
+}
+
+size_t dense_smem_bytes(int64_t N) {
+  const int64_t L = N + 1;
+  const int64_t Kpad = round_up(L, DT_KC);
+  return (size_t)DT_STAGES * DT_CHUNK + (size_t)2 * Kpad * DT_N * 4;
+}
+
+bool dense_supported(int64_t N) { return N >= 4 && N <= DENSE_MAX_N; }
+
+bk_status dense_build(Plan* p, cudaStream_t st) {
+  BK_ARG(p->dtype == BK_F32 && dense_supported(p->N), "dense tables: FP32 plans with N <= %d only", DENSE_MAX_N);
+  const int64_t N = p->N, L = p->L;
+  const int Mt = (int)((L + DT_M - 1) / DT_M);
+  const int nK = (int)((L + DT_KC - 1) / DT_KC);
+  p->dMt = Mt;
+  p->dnK = nK;
+  p->dsmem = dense_smem_bytes(N);
+  const size_t bytes = (size_t)Mt * nK * DT_CHUNK;
+  for (int t = 0; t < 2; ++t) BK_TRY(dmalloc(&p->dA[t], bytes));
+  BK_TRY(dmalloc((void**)&p->derr, sizeof(int)));
+  BK_TRY_CUDA(cudaMemsetAsync(p->derr, 0, sizeof(int), st));
+  // columns of B^a from the FP64 FFT product of the unit vectors (unit time scale)
+  Plan* q = nullptr;
+  const int64_t qp = round_up(L, 32);
+  BK_TRY(plan_create(&q, N, 1, (int)L, BK_F64, -1.0, 1.0, qp, st));
+  double* e = nullptr;
+  double* cols = nullptr;
+  bk_status r = dmalloc((void**)&e, sizeof(double) * (size_t)L * qp);
+  if (r == BK_OK) r = dmalloc((void**)&cols, sizeof(double) * (size_t)L * qp);
+  if (r == BK_OK) {
+    k_identity<<<(int)std::min<int64_t>((L * qp + 255) / 256, 4096), 256, 0, st>>>(e, (int)L, qp);
+    note_launch();
+    r = cudaGetLastError() == cudaSuccess ? plan_apply_n(q, e, cols, (int)L, false, 1.0, st) : BK_ERR_CUDA;
+  }
+  for (int t = 0; t < 2 && r == BK_OK; ++t) {
+    const int64_t total = (int64_t)Mt * DT_M * nK * DT_KC;
+    k_dense_tile<<<(int)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(cols, qp, (int)L, Mt, nK, t,
+                                                                                   (unsigned char*)p->dA[t]);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) { r = BK_ERR_CUDA; set_error("dense tile launch failed"); }
+  }
+  if (r == BK_OK && cudaStreamSynchronize(st) != cudaSuccess) { set_error("dense tables: sync failed"); r = BK_ERR_CUDA; }
+  dfree(e);
+  dfree(cols);
+  plan_destroy(q);
+  if (r != BK_OK) return r;
+  BK_TRY_CUDA(cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes(DENSE_MAX_N)));
+  return BK_OK;
+}
+
+bk_status dense_apply(const Plan* p, const float* v, float* out, int nvec, bool trans, double s, cudaStream_t st) {
+  const dim3 grid(p->dMt, (nvec + DT_N - 1) / DT_N);
+  k_dense_tc<<<grid, 128, p->dsmem, st>>>((const unsigned char*)p->dA[trans ? 1 : 0], v, out, nvec, (int)p->L, p->pitch,
+                                          p->dnK, (float)s, p->derr);
+  BK_CHECK_LAUNCH();
+  return BK_OK;
+}
+
+}  // namespace bk

@@ -49,6 +49,13 @@ struct Plan {
   double* w64 = nullptr;      // Clenshaw-Curtis weights (FP64, device, tau-domain)
   void* wT = nullptr;         // Clenshaw-Curtis weights in the working type (device)
   size_t bytes = 0;           // device bytes this plan allocated
+  // Dense tensor-core path (FP32 plans, N <= 1024): B^a and (B^a)^T pre-tiled as TF32 hi/lo
+  // parts (dA[0], dA[1]); used by the applies while `dense` is set.
+  bool dense = false;
+  void* dA[2] = {nullptr, nullptr};
+  int* derr = nullptr;        // device error word of the dense kernel (0 = no timeout)
+  int dMt = 0, dnK = 0;       // 128-row output tiles, 32-wide K chunks
+  size_t dsmem = 0;           // dynamic shared memory of the dense kernel
 };
 
 bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtype, double t0,
@@ -59,5 +66,10 @@ bk_status plan_apply(const Plan* p, const void* v, void* out, int batch, bool tr
 // Apply to `nvec` vectors with an explicit scale (s = 1 gives B^a itself).
 bk_status plan_apply_n(const Plan* p, const void* v, void* out, int nvec, bool trans, double s,
                        cudaStream_t st);
+
+// Dense tensor-core path (bk_dense.cu).
+bool dense_supported(int64_t N);
+bk_status dense_build(Plan* p, cudaStream_t st);
+bk_status dense_apply(const Plan* p, const float* v, float* out, int nvec, bool trans, double s, cudaStream_t st);
 
 }  // namespace bk

@@ -1,0 +1,97 @@
+"""GPU parity of the dense tensor-core product (tcgen05, 3xTF32) against the oracle's dense B^a.
+
+The dense path multiplies by B^a itself, so the reference is the oracle's matrix of integrated
+Lagrange polynomials (Eq. manyDefs with B = s B^a); the tolerance is the FP32 product bound,
+1e-5 relative in the 2-norm, as for the FP32 FFT chain.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import birkhoff as ob
+from paper_2509_01855_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+
+
+def _api():
+    from paper_2509_01855_gb300 import api
+    return api
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _dense_run(N, trans, n_comp, batch, t0=0.0, tf=3.0, dense=True):
+    api = _api()
+    plan = api.Plan(N, n_comp=n_comp, max_batch=batch, dtype=torch.float32, t0=t0, tf=tf)
+    if dense:
+        plan.set_dense(True)
+    L = N + 1
+    V = synth.gaussian((batch, n_comp, L), "dense", N, int(trans))
+    v = plan.empty(batch)
+    v[:, :, :L] = torch.as_tensor(V, dtype=torch.float32)
+    v[:, :, L:] = 7.0          # padding must be ignored
+    out = plan.empty(batch)
+    out.fill_(3.0)
+    (api.birkhoff_apply_T if trans else api.birkhoff_apply)(plan, v, out)
+    torch.cuda.synchronize()
+    o = out.cpu().double().numpy()
+    assert np.all(o[:, :, L:] == 0.0), "padding not zeroed"
+    if dense:
+        assert plan.dense_check() == 0, "dense kernel reported a timeout"
+    return o[:, :, :L], V
+
+
+@pytest.mark.parametrize("N", [4, 8, 16, 64, 128, 256, 512, 1024])
+@pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("n_comp,batch", [(1, 1), (3, 2), (17, 1), (4, 10)])
+def test_dense_vs_dense_oracle(N, trans, n_comp, batch):
+    """1, 6, 17 and 40 vectors: one 16-vector tile, a ragged tile, and several tiles."""
+    got, V = _dense_run(N, trans, n_comp, batch)
+    B = ob.dense_B(N, 0.0, 3.0)
+    ref = V @ (B if trans else B.T)
+    assert _rel(got, ref) < TOL32
+
+
+@pytest.mark.parametrize("N", [16, 256, 1024])
+def test_dense_matches_fft_chain(N):
+    """The two FP32 paths of one plan agree to FP32 rounding."""
+    a, V = _dense_run(N, False, 4, 2, dense=True)
+    b, V2 = _dense_run(N, False, 4, 2, dense=False)
+    assert np.array_equal(V, V2)
+    assert _rel(a, b) < 2 * TOL32
+
+
+def test_dense_constant_and_row0():
+    """B 1 = t - t0 at every node and row 0 of B is zero (Eq. birk-conditions)."""
+    api = _api()
+    N = 512
+    plan = api.Plan(N, n_comp=1, dtype=torch.float32, t0=1.0, tf=4.0)
+    plan.set_dense(True)
+    t, _ = plan.grid()
+    v = plan.empty(1)
+    v[:, :, :N + 1] = 1.0
+    out = plan.empty(1)
+    api.birkhoff_apply(plan, v, out)
+    torch.cuda.synchronize()
+    o = out[0, 0, :N + 1].cpu().double().numpy()
+    assert o[0] == 0.0 or abs(o[0]) < 1e-6
+    assert np.max(np.abs(o - (t.numpy() - 1.0))) < 1e-5 * 3.0
+
+
+def test_dense_switch_back_and_unsupported():
+    api = _api()
+    from paper_2509_01855_gb300._lib import BirkhoffError
+    p64 = api.Plan(256, dtype=torch.float64)
+    with pytest.raises(BirkhoffError):
+        p64.set_dense(True)
+    big = api.Plan(2048, dtype=torch.float32)
+    with pytest.raises(BirkhoffError):
+        big.set_dense(True)
+    a, V = _dense_run(64, True, 2, 1, dense=True)
+    B = ob.dense_B(64, 0.0, 3.0)
+    assert _rel(a, V @ B) < TOL32
