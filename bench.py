@@ -276,11 +276,15 @@ def recorded_traffic(dtype_name, N):
     return int(m.group(1)) if sha.hexdigest()[:16] == h.group(1) else None
 
 
-def measure_apply(N, dtype, reps=20, trans=False):
-    """Birkhoff apply B v (or B^T v) on 4 components, cold L2 between repetitions (CUDA events)."""
+def measure_apply(N, dtype, reps=20, trans=False, dense=None):
+    """Birkhoff apply B v (or B^T v) on 4 components, cold L2 between repetitions (CUDA events).
+    dense: None keeps the plan's default path; True / False force the tensor-core dense product
+    or the FFT chain (FP32, N <= 1024)."""
     import torch
     from paper_2509_01855_gb300 import api
     plan = api.Plan(N, n_comp=4, max_batch=1, dtype=dtype, t0=0.0, tf=TF)
+    if dense is not None:
+        plan.set_dense(dense)
     g = torch.Generator(device="cuda")
     g.manual_seed(2509_01855)
     v = plan.empty(1)
@@ -322,6 +326,18 @@ def apply_sweep(lgs=range(10, 25), reps=5):
                              "BT_gbs": round(nbytes / trn / 1e6, 2), "B_tflops": round(flops / fwd / 1e9, 4)}
         out[name] = rows
     return out
+
+
+def dense_crossover(lgs=range(4, 11), reps=9):
+    """FP32 products on 4 components, FFT chain vs the dense tensor-core product (the GPU
+    analogue of the paper's Fig. BVisNlogN), cold L2: median ms of B v."""
+    import torch
+    rows = {}
+    for lg in lgs:
+        fft, _, _ = measure_apply(1 << lg, torch.float32, reps=reps, dense=False)
+        dense, _, _ = measure_apply(1 << lg, torch.float32, reps=reps, dense=True)
+        rows[str(lg)] = {"fft_ms": round(fft, 5), "dense_ms": round(dense, 5)}
+    return rows
 
 
 def cpu_apply_baseline(N):
@@ -502,6 +518,7 @@ def main():
                      "n_comp": 4, "dtype": dtype_name}
     if args.sweep:
         line["apply_sweep"] = apply_sweep()
+        line["dense_crossover"] = dense_crossover()
     if args.workload.startswith("newton") and args.serve_requests >= 0:
         line["serve"] = run_serve(args.serve_requests or 512, args.serve_slots, rank, world, dist)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

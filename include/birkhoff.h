@@ -139,6 +139,12 @@ bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int ba
  * safe against applies of the same plan in flight. */
 bk_status bk_plan_set_dense(bk_plan* plan, int on, void* stream);
 
+/* *on = 1 while the plan's products take the dense tensor-core path, else 0. BK_F32 plans with
+ * 64 <= N <= 1024 and n_comp * max_batch <= 16 start on it (where it measured faster than the
+ * FFT chain); the environment variable BK_DENSE=0 (read at plan creation) keeps every plan on
+ * the FFT chain, BK_DENSE=1 starts every supported plan on the dense path. */
+bk_status bk_plan_dense_state(const bk_plan* plan, int* on);
+
 /* Read (and clear) the dense kernel's error word: *err = 0 when every dense product so far
  * completed; otherwise a wait inside the kernel ran out (1: operand copy or MMA completion,
  * 2: accumulator read) and that product's output is not valid. Synchronous (device sync). */

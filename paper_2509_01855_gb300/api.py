@@ -53,7 +53,12 @@ class Plan:
     def set_dense(self, on=True, stream=None):
         """Products through the dense tensor-core path (BK_F32 plans, N <= 1024) or the FFT chain."""
         L.check(L.lib().bk_plan_set_dense(self._h, 1 if on else 0, L.stream_ptr(stream)))
-        self.dense = bool(on)
+
+    def is_dense(self):
+        """True while the plan's products take the dense tensor-core path."""
+        on = ctypes.c_int(0)
+        L.check(L.lib().bk_plan_dense_state(self._h, ctypes.byref(on)))
+        return bool(on.value)
 
     def dense_check(self):
         """Error word of the dense kernel since the last check (0: every product completed)."""

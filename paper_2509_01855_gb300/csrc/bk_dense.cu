@@ -10,13 +10,16 @@
 // the unit vectors (columns of B^a, Eq. xN=Birka+b: the a-form integration matrix), so its
 // entries are FP64-exact before the split.
 //
-// Kernel shape (one CTA of 4 warps per 128 output rows and 16 vectors):
-//   - thread 0 streams the CTA's A panel through two shared-memory stages with bulk copies
-//     (cp.async.bulk, completion on an mbarrier) and issues the MMAs (M = 128, N = 16, K = 8);
-//   - all threads stage the CTA's 16 vectors once, split into TF32 hi and lo parts;
+// Kernel shape (CTAs of 4 warps; a tile is 128 output rows x 16 vectors, its K range split
+// over up to 8 CTAs so that small products still spread over the GPU):
+//   - thread 0 streams the CTA's part of the A panel through up to four shared-memory stages
+//     with bulk copies (cp.async.bulk, completion on an mbarrier) and issues the MMAs
+//     (M = 128, N = 16, K = 8);
+//   - all threads stage the CTA's K range of the 16 vectors once, split into TF32 hi and lo;
 //   - tcgen05.commit arrives on an mbarrier when a stage's MMAs are done (the stage is then
 //     refilled) and when the last MMA is done (the epilogue then reads the accumulator);
-//   - each warp reads its 32 accumulator lanes with tcgen05.ld and writes s D to the output.
+//   - each warp reads its 32 accumulator lanes with tcgen05.ld; split tiles add their partials
+//     in a fixed order in the last CTA to finish (no CTA waits for another).
 // Every wait is bounded; on a timeout the kernel records an error code, waits (bounded) for its
 // copies in flight, frees its tensor memory and returns.
 //
@@ -27,6 +30,7 @@
 // whichever way the two offsets are read, so a misread layout gives wrong values, never an
 // out-of-range shared access.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -38,12 +42,12 @@ namespace bk {
 constexpr int DT_M = 128;                              // output rows per CTA (MMA M)
 constexpr int DT_N = 16;                               // vectors per CTA (MMA N)
 constexpr int DT_KC = 32;                              // K values per pipeline chunk (4 k-steps)
-constexpr int DT_STAGES = 2;                           // A chunk buffers
+constexpr int DT_SMAX = 4;                             // A chunk buffers at most
 constexpr int DT_PART = DT_M * DT_KC * 4;              // one TF32 part of a chunk: 16 KB
 constexpr int DT_CHUNK = 2 * DT_PART;                  // hi + lo: 32 KB
 constexpr int DT_TMEM_COLS = 32;                       // accumulator columns allocated (>= DT_N)
 constexpr unsigned DT_SPIN = 1u << 20;                 // mbarrier polls before a timeout
-constexpr int DENSE_MAX_N = 1024;                      // V (2 parts x 16 x K) stays in shared memory
+constexpr int DENSE_MAX_N = 1024;                      // V (2 parts x 16 x K) fits in shared memory
 
 // Byte offset of A element (m, k), m < 128, k < 32, inside one part of a chunk.
 __host__ __device__ inline int dt_a_off(int m, int k) {
@@ -116,21 +120,30 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
 // out[n][m] = s (A V)[m][n] for m < L, n < nvec, with A = A_hi + A_lo pre-tiled in `At`
 // (chunk (mt, c) of 128 rows x 32 columns at ((mt nK + c) * 32 KB), hi part then lo part).
 // V and out: nvec vectors `pitch` apart; out's padding [L, pitch) is zeroed.
+// Split K: CTA z of the KS CTAs of a tile (blockIdx.z) takes chunks [z nK / KS, (z+1) nK / KS)
+// through S shared-memory stages. With KS > 1 each CTA writes its 128 x 16 partial to `part` and
+// counts itself in cnt[tile]; the last CTA to arrive sums the KS partials in the order z = 0, 1,
+// ... (the result does not depend on arrival order), writes the output and resets the counter.
+// No CTA waits for another.
 __global__ void __launch_bounds__(128, 1)
     k_dense_tc(const unsigned char* __restrict__ At, const float* __restrict__ V, float* __restrict__ out, int nvec,
-               int L, int64_t pitch, int nK, float s, int* __restrict__ err) {
+               int L, int64_t pitch, int nK, int KS, int S, float s, float* __restrict__ part,
+               unsigned* __restrict__ cnt, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar_full[DT_STAGES];
-  __shared__ __align__(8) uint64_t bar_empty[DT_STAGES];
+  __shared__ __align__(8) uint64_t bar_full[DT_SMAX];
+  __shared__ __align__(8) uint64_t bar_empty[DT_SMAX];
   __shared__ __align__(8) uint64_t bar_done;
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
+  __shared__ int last;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int mt = blockIdx.x, n0 = blockIdx.y * DT_N;
-  const int Kpad = nK * DT_KC;
-  unsigned char* sA = smem;                          // DT_STAGES chunks
-  unsigned char* sV = smem + DT_STAGES * DT_CHUNK;   // hi part, then lo part
-  const int vpart = Kpad * DT_N * 4;
+  const int mt = blockIdx.x, n0 = blockIdx.y * DT_N, z = blockIdx.z;
+  const int tile = blockIdx.y * gridDim.x + mt;
+  const int cb = (int)((int64_t)z * nK / KS), nloc = (int)((int64_t)(z + 1) * nK / KS) - cb;
+  const int Kloc = nloc * DT_KC;
+  unsigned char* sA = smem;                  // S chunks
+  unsigned char* sV = smem + S * DT_CHUNK;   // hi part, then lo part (this CTA's K range)
+  const int vpart = Kloc * DT_N * 4;
   const uint32_t aA = smem_u32(sA), aV = smem_u32(sV);
 
   if (warp == 0) {
@@ -140,7 +153,7 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < DT_STAGES; ++i) {
+    for (int i = 0; i < S; ++i) {
       mbar_init(smem_u32(&bar_full[i]), 1);
       mbar_init(smem_u32(&bar_empty[i]), 1);
     }
@@ -154,18 +167,20 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t tmem_d = tmem_slot;
 
   // first chunks in flight while the vectors are staged
-  const unsigned char* Ablk = At + (size_t)mt * nK * DT_CHUNK;
+  const unsigned char* Ablk = At + ((size_t)mt * nK + cb) * DT_CHUNK;
   if (tid == 0) {
-    for (int c = 0; c < DT_STAGES && c < nK; ++c) {
+    for (int c = 0; c < S && c < nloc; ++c) {
       mbar_expect_tx(smem_u32(&bar_full[c]), DT_CHUNK);
       bulk_g2s(aA + c * DT_CHUNK, Ablk + (size_t)c * DT_CHUNK, DT_CHUNK, smem_u32(&bar_full[c]));
     }
   }
-  // vectors n0..n0+15, nodes k < Kpad (zero beyond L and nvec), split into TF32 hi and lo
-  for (int i = tid; i < DT_N * Kpad; i += blockDim.x) {
-    const int n = i / Kpad, k = i - n * Kpad;
+  // vectors n0..n0+15, nodes of this CTA's K range (zero beyond L and nvec), split into TF32 hi
+  // and lo
+  const int k0 = cb * DT_KC;
+  for (int i = tid; i < DT_N * Kloc; i += blockDim.x) {
+    const int n = i / Kloc, k = i - n * Kloc;
     float v = 0.f;
-    if (n0 + n < nvec && k < L) v = V[(int64_t)(n0 + n) * pitch + k];
+    if (n0 + n < nvec && k0 + k < L) v = V[(int64_t)(n0 + n) * pitch + k0 + k];
     const float hi = tf32_rna(v);
     const float lo = tf32_rna(v - hi);
     const int off = dt_v_off(n, k);
@@ -178,12 +193,12 @@ __global__ void __launch_bounds__(128, 1)
   if (tid == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     constexpr uint32_t idesc = dt_idesc();
-    int issued = nK < DT_STAGES ? nK : DT_STAGES;  // chunks whose copies were started
+    int issued = nloc < S ? nloc : S;  // chunks whose copies were started
     int c = 0;
     bool ok = true;
-    for (; c < nK; ++c) {
-      const int st = c % DT_STAGES;
-      const uint32_t ph = (uint32_t)(c / DT_STAGES) & 1u;
+    for (; c < nloc; ++c) {
+      const int st = c % S;
+      const uint32_t ph = (uint32_t)(c / S) & 1u;
       if (!mbar_wait(smem_u32(&bar_full[st]), ph)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -198,11 +213,11 @@ __global__ void __launch_bounds__(128, 1)
         tc_mma(tmem_d, dAl, dVh, idesc, 1u);
       }
       tc_commit(smem_u32(&bar_empty[st]));
-      if (c + DT_STAGES < nK) {
+      if (c + S < nloc) {
         // refill this stage once its MMAs have read it
         if (!mbar_wait(smem_u32(&bar_empty[st]), ph)) { ok = false; ++c; break; }
         mbar_expect_tx(smem_u32(&bar_full[st]), DT_CHUNK);
-        bulk_g2s(aA + st * DT_CHUNK, Ablk + (size_t)(c + DT_STAGES) * DT_CHUNK, DT_CHUNK, smem_u32(&bar_full[st]));
+        bulk_g2s(aA + st * DT_CHUNK, Ablk + (size_t)(c + S) * DT_CHUNK, DT_CHUNK, smem_u32(&bar_full[st]));
         ++issued;
       }
     }
@@ -210,7 +225,7 @@ __global__ void __launch_bounds__(128, 1)
     if (!ok) {
       fail = 1;
       // copies started but not consumed: wait for them (bounded) before the CTA may exit
-      for (int q = c; q < issued; ++q) (void)mbar_wait(smem_u32(&bar_full[q % DT_STAGES]), (uint32_t)(q / DT_STAGES) & 1u);
+      for (int q = c; q < issued; ++q) (void)mbar_wait(smem_u32(&bar_full[q % S]), (uint32_t)(q / S) & 1u);
     }
   }
   // every lane waits (bounded); the warp then agrees, since tcgen05.ld is warp-collective
@@ -218,8 +233,10 @@ __global__ void __launch_bounds__(128, 1)
   __syncwarp();
   const bool done = __all_sync(0xffffffffu, mine);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  uint32_t r[16];
+#pragma unroll
+  for (int n = 0; n < DT_N; ++n) r[n] = 0u;
   if (done) {
-    uint32_t r[16];
     const uint32_t taddr = tmem_d + ((uint32_t)(warp * 32) << 16);
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
@@ -228,18 +245,51 @@ __global__ void __launch_bounds__(128, 1)
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int m = mt * DT_M + warp * 32 + lane;
+  } else if (lane == 0) {
+    fail = 2;
+  }
+  const int row = warp * 32 + lane;
+  const int m = mt * DT_M + row;
+  if (KS == 1) {
     if (m < L) {
 #pragma unroll
       for (int n = 0; n < DT_N; ++n)
         if (n0 + n < nvec) out[(int64_t)(n0 + n) * pitch + m] = s * __uint_as_float(r[n]);
     }
-  } else if (lane == 0) {
-    fail = 2;
+  } else {
+    float4* mine4 = reinterpret_cast<float4*>(part + (((size_t)tile * KS + z) * DT_M + row) * DT_N);
+#pragma unroll
+    for (int q = 0; q < DT_N / 4; ++q)
+      mine4[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]), __uint_as_float(r[4 * q + 2]),
+                             __uint_as_float(r[4 * q + 3]));
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(&cnt[tile], 1u) == (unsigned)(KS - 1);
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      float acc[DT_N];
+#pragma unroll
+      for (int n = 0; n < DT_N; ++n) acc[n] = 0.f;
+      for (int q = 0; q < KS; ++q) {
+        const float4* src = reinterpret_cast<const float4*>(part + (((size_t)tile * KS + q) * DT_M + row) * DT_N);
+#pragma unroll
+        for (int u = 0; u < DT_N / 4; ++u) {
+          const float4 x = __ldcg(src + u);
+          acc[4 * u] += x.x; acc[4 * u + 1] += x.y; acc[4 * u + 2] += x.z; acc[4 * u + 3] += x.w;
+        }
+      }
+      if (m < L) {
+#pragma unroll
+        for (int n = 0; n < DT_N; ++n)
+          if (n0 + n < nvec) out[(int64_t)(n0 + n) * pitch + m] = s * acc[n];
+      }
+      if (tid == 0) cnt[tile] = 0u;  // ready for the next product
+    }
   }
-  if (mt == 0) {
+  if (mt == 0 && z == 0) {
     for (int n = 0; n < DT_N && n0 + n < nvec; ++n)
-      for (int64_t m = L + tid; m < pitch; m += blockDim.x) out[(int64_t)(n0 + n) * pitch + m] = 0.f;
+      for (int64_t mm = L + tid; mm < pitch; mm += blockDim.x) out[(int64_t)(n0 + n) * pitch + mm] = 0.f;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -275,10 +325,36 @@ __global__ void k_identity(double* __restrict__ e, int L, int64_t pitch) {
   }
 }
 
-size_t dense_smem_bytes(int64_t N) {
-  const int64_t L = N + 1;
-  const int64_t Kpad = round_up(L, DT_KC);
-  return (size_t)DT_STAGES * DT_CHUNK + (size_t)2 * Kpad * DT_N * 4;
+constexpr size_t DT_SMEM_BUDGET = 200 * 1024;       // dynamic shared memory of one CTA at most
+constexpr int DT_KS_MAX = 8;                           // K splits per tile at most
+
+static int dense_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 148;
+  return n;
+}
+
+// Launch shape of one dense product of nvec vectors: K splits KS (about two CTAs per SM over all
+// tiles, at most 8 and at most one per chunk; BK_DENSE_KSPLIT overrides), pipeline stages S
+// (up to 4, within the shared-memory budget next to the staged vectors).
+struct DenseShape {
+  int KS, S;
+  size_t smem;
+};
+static DenseShape dense_shape(const Plan* p, int nvec) {
+  const int ny = (nvec + DT_N - 1) / DT_N;
+  const int tiles = p->dMt * ny;
+  int KS = std::max(1, std::min(std::min(DT_KS_MAX, p->dnK), 2 * dense_sms() / std::max(1, tiles)));
+  if (const char* e = getenv("BK_DENSE_KSPLIT")) {
+    const long v = atol(e);
+    if (v >= 1) KS = (int)std::min<long>(std::min<long>(v, DT_KS_MAX), p->dnK);
+  }
+  const int nloc = (p->dnK + KS - 1) / KS;
+  const size_t vbytes = (size_t)2 * nloc * DT_KC * DT_N * 4;
+  int S = std::min(DT_SMAX, nloc);
+  while (S > 1 && S * (size_t)DT_CHUNK + vbytes > DT_SMEM_BUDGET) --S;
+  return {KS, S, S * (size_t)DT_CHUNK + vbytes};
 }
 
 bool dense_supported(int64_t N) { return N >= 4 && N <= DENSE_MAX_N; }
@@ -290,11 +366,15 @@ bk_status dense_build(Plan* p, cudaStream_t st) {
   const int nK = (int)((L + DT_KC - 1) / DT_KC);
   p->dMt = Mt;
   p->dnK = nK;
-  p->dsmem = dense_smem_bytes(N);
   const size_t bytes = (size_t)Mt * nK * DT_CHUNK;
   for (int t = 0; t < 2; ++t) BK_TRY(dmalloc(&p->dA[t], bytes));
   BK_TRY(dmalloc((void**)&p->derr, sizeof(int)));
   BK_TRY_CUDA(cudaMemsetAsync(p->derr, 0, sizeof(int), st));
+  // split-K partials and arrival counters for the plan's largest product
+  const int ny = (p->n_comp * p->max_batch + DT_N - 1) / DT_N;
+  BK_TRY(dmalloc(&p->dpart, sizeof(float) * (size_t)Mt * ny * DT_KS_MAX * DT_M * DT_N));
+  BK_TRY(dmalloc((void**)&p->dcnt, sizeof(unsigned) * (size_t)Mt * ny));
+  BK_TRY_CUDA(cudaMemsetAsync(p->dcnt, 0, sizeof(unsigned) * (size_t)Mt * ny, st));
   // columns of B^a from the FP64 FFT product of the unit vectors (unit time scale)
   Plan* q = nullptr;
   const int64_t qp = round_up(L, 32);
@@ -320,14 +400,15 @@ bk_status dense_build(Plan* p, cudaStream_t st) {
   dfree(cols);
   plan_destroy(q);
   if (r != BK_OK) return r;
-  BK_TRY_CUDA(cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dense_smem_bytes(DENSE_MAX_N)));
+  BK_TRY_CUDA(cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DT_SMEM_BUDGET));
   return BK_OK;
 }
 
 bk_status dense_apply(const Plan* p, const float* v, float* out, int nvec, bool trans, double s, cudaStream_t st) {
-  const dim3 grid(p->dMt, (nvec + DT_N - 1) / DT_N);
-  k_dense_tc<<<grid, 128, p->dsmem, st>>>((const unsigned char*)p->dA[trans ? 1 : 0], v, out, nvec, (int)p->L, p->pitch,
-                                          p->dnK, (float)s, p->derr);
+  const DenseShape sh = dense_shape(p, nvec);
+  const dim3 grid(p->dMt, (nvec + DT_N - 1) / DT_N, sh.KS);
+  k_dense_tc<<<grid, 128, sh.smem, st>>>((const unsigned char*)p->dA[trans ? 1 : 0], v, out, nvec, (int)p->L, p->pitch,
+                                         p->dnK, sh.KS, sh.S, (float)s, (float*)p->dpart, p->dcnt, p->derr);
   BK_CHECK_LAUNCH();
   return BK_OK;
 }

@@ -55,7 +55,8 @@ struct Plan {
   void* dA[2] = {nullptr, nullptr};
   int* derr = nullptr;        // device error word of the dense kernel (0 = no timeout)
   int dMt = 0, dnK = 0;       // 128-row output tiles, 32-wide K chunks
-  size_t dsmem = 0;           // dynamic shared memory of the dense kernel
+  void* dpart = nullptr;      // split-K partial sums (FP32)
+  unsigned* dcnt = nullptr;   // split-K arrival counters, one per output tile (self-resetting)
 };
 
 bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtype, double t0,

@@ -28,8 +28,7 @@ def _rel(a, b):
 def _dense_run(N, trans, n_comp, batch, t0=0.0, tf=3.0, dense=True):
     api = _api()
     plan = api.Plan(N, n_comp=n_comp, max_batch=batch, dtype=torch.float32, t0=t0, tf=tf)
-    if dense:
-        plan.set_dense(True)
+    plan.set_dense(dense)
     L = N + 1
     V = synth.gaussian((batch, n_comp, L), "dense", N, int(trans))
     v = plan.empty(batch)
@@ -81,6 +80,47 @@ def test_dense_constant_and_row0():
     o = out[0, 0, :N + 1].cpu().double().numpy()
     assert o[0] == 0.0 or abs(o[0]) < 1e-6
     assert np.max(np.abs(o - (t.numpy() - 1.0))) < 1e-5 * 3.0
+
+
+@pytest.mark.parametrize("ksplit", ["1", "3", "8"])
+@pytest.mark.parametrize("N", [64, 1024])
+def test_dense_k_splits(N, ksplit, monkeypatch):
+    """Unsplit tiles, an uneven split (chunks per CTA differ) and the largest split give the
+    same product (partials are added in a fixed order)."""
+    monkeypatch.setenv("BK_DENSE_KSPLIT", ksplit)
+    got, V = _dense_run(N, False, 4, 5)
+    B = ob.dense_B(N, 0.0, 3.0)
+    assert _rel(got, V @ B.T) < TOL32
+
+
+def test_dense_repeat_is_bitwise():
+    """Repeated products of one plan (counters reset by the last CTA of each tile) are
+    bit-identical."""
+    api = _api()
+    N = 512
+    plan = api.Plan(N, n_comp=4, max_batch=3, dtype=torch.float32, t0=0.0, tf=3.0)
+    plan.set_dense(True)
+    v = plan.empty(3)
+    v[:, :, :N + 1] = torch.as_tensor(synth.gaussian((3, 4, N + 1), "dense-rep"), dtype=torch.float32)
+    outs = []
+    for _ in range(3):
+        o = plan.empty(3)
+        api.birkhoff_apply(plan, v, o)
+        outs.append(o)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    assert plan.dense_check() == 0
+
+
+def test_dense_default_policy(monkeypatch):
+    """FP32 plans with 64 <= N <= 1024 and at most 16 vectors start on the dense path."""
+    api = _api()
+    for N, n_comp, batch, want in [(32, 4, 1, False), (64, 4, 1, True), (1024, 4, 4, True),
+                                   (1024, 4, 5, False), (2048, 4, 1, False)]:
+        p = api.Plan(N, n_comp=n_comp, max_batch=batch, dtype=torch.float32)
+        assert p.is_dense() == want, (N, n_comp, batch)
+    monkeypatch.setenv("BK_DENSE", "0")
+    assert not api.Plan(256, n_comp=4, dtype=torch.float32).is_dense()
 
 
 def test_dense_switch_back_and_unsupported():
