@@ -139,6 +139,13 @@ bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int ba
  * safe against applies of the same plan in flight. */
 bk_status bk_plan_set_dense(bk_plan* plan, int on, void* stream);
 
+/* How a plan computes its products. *path: 0 one CTA per vector (small N), 1 four-step FFT,
+ * 2 four-step with the split DCT-I, 3 dense tensor-core product. For paths 1 and 2: the FFT
+ * factors N1 x N2 of the (even-half) transform and the complex elements per CTA, as chosen by
+ * the tile autotuner at plan creation (or by the occupancy heuristic when tuning is off:
+ * environment BK_AUTOTUNE=0). Outputs may be NULL. */
+bk_status bk_plan_shape(const bk_plan* plan, int* path, int* N1, int* N2, int* elems);
+
 /* *on = 1 while the plan's products take the dense tensor-core path, else 0. BK_F32 plans with
  * 64 <= N <= 1024 and n_comp * max_batch <= 16 start on it (where it measured faster than the
  * FFT chain); the environment variable BK_DENSE=0 (read at plan creation) keeps every plan on

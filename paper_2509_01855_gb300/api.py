@@ -54,6 +54,13 @@ class Plan:
         """Products through the dense tensor-core path (BK_F32 plans, N <= 1024) or the FFT chain."""
         L.check(L.lib().bk_plan_set_dense(self._h, 1 if on else 0, L.stream_ptr(stream)))
 
+    def shape(self):
+        """{"path": "single_cta" | "four_step" | "split_four_step" | "dense", "N1", "N2", "elems"}."""
+        v = [ctypes.c_int(0) for _ in range(4)]
+        L.check(L.lib().bk_plan_shape(self._h, *[ctypes.byref(x) for x in v]))
+        names = ("single_cta", "four_step", "split_four_step", "dense")
+        return {"path": names[v[0].value], "N1": v[1].value, "N2": v[2].value, "elems": v[3].value}
+
     def is_dense(self):
         """True while the plan's products take the dense tensor-core path."""
         on = ctypes.c_int(0)

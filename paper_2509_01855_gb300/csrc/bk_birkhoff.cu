@@ -36,7 +36,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 
 #include "bk_common.cuh"
@@ -905,8 +907,9 @@ static int sm_count() {
 // vectors, at least one column of N1 and one row pair of 2 N2, at most the thread cap. Small
 // transforms thus run many one-warp CTAs instead of a few full ones (at 2^14 x 4 components the
 // full-size tiles gave 16 CTAs per pass). BK_FOURSTEP_ELEMS fixes it (tuning).
-static int fourstep_elems(int dtype, int64_t n, int nvec, int N1, int N2) {
+static int fourstep_elems(int dtype, int64_t n, int nvec, int N1, int N2, int Eforce = 0) {
   const int cap = dtype == BK_F64 ? 4096 : 8192;  // 16 per thread at the thread cap
+  if (Eforce > 0) return std::min(cap, std::max(Eforce, std::max(N1, 2 * N2)));
   const char* e = getenv("BK_FOURSTEP_ELEMS");
   if (e) {
     long v = atol(e);
@@ -933,9 +936,10 @@ static int split_min_log2(int dtype) {
   return dtype == BK_F64 ? 19 : 21;
 }
 
-static bk_status configure_fourstep(FourStep& f, int64_t n, int dtype, int nvec) {
+// Shapes of one four-step layout (tables untouched, so a built plan can be re-shaped); Eforce
+// > 0 fixes the elements per CTA (the autotuner's candidates), 0 takes fourstep_elems.
+static bk_status configure_fourstep(FourStep& f, int64_t n, int dtype, int nvec, int Eforce = 0) {
   const int log2n = ilog2(n);
-  f = FourStep();
   f.n = n;
   // balanced factors, with the rows short enough for one row pair per CTA (2 N2 / 16 threads)
   // and the columns for one column per CTA (N1 / 16 threads) under the thread cap
@@ -949,7 +953,7 @@ static bk_status configure_fourstep(FourStep& f, int64_t n, int dtype, int nvec)
     return BK_ERR_UNSUPPORTED;
   }
   const size_t csz = 2 * dtype_size(dtype);
-  const int E = fourstep_elems(dtype, n, nvec, f.N1, f.N2);
+  const int E = fourstep_elems(dtype, n, nvec, f.N1, f.N2, Eforce);
   // pass A: NB columns of N1; pass B: P row pairs (2P rows) of N2
   int NB = std::max(1, E / f.N1);
   if (NB > f.N2) NB = f.N2;
@@ -1028,6 +1032,94 @@ static bool dense_default(int dtype, int64_t N, int nvec) {
   return N >= 64 && nvec <= 16;
 }
 
+// Four-step shapes of a plan for E complex elements per CTA (0: the occupancy heuristic).
+static bk_status fourstep_shapes(Plan* p, int E) {
+  const int nvec = p->n_comp * p->max_batch;
+  if (p->split) {
+    BK_TRY(configure_fourstep(p->fs, p->N / 2, p->dtype, nvec, E));
+    BK_TRY(configure_fourstep(p->fso, p->N / 4, p->dtype, nvec, E));
+    return BK_OK;
+  }
+  return configure_fourstep(p->fs, p->N, p->dtype, nvec, E);
+}
+
+// Tile autotuner of the four-step transforms. The elements per CTA E (powers of two from one
+// column and one row pair up to the thread cap) set the CTA count, shared memory per CTA and how
+// many CTAs share an SM; the best E depends on N, the vector count and the GPU. For each
+// candidate the plan is re-shaped and timed (CUDA events, one B and one B^T after a warm-up
+// pair, on zero vectors: the kernels have no data-dependent paths); the fastest stays. Results
+// are cached per (N, dtype, vectors, SM count, device) for the process, so plans of one size
+// share one shape (and bitwise the same results). BK_AUTOTUNE=0 keeps the heuristic shape;
+// BK_FOURSTEP_ELEMS, a fixed shape, also skips tuning.
+static bool autotune_enabled() {
+  const char* e = getenv("BK_AUTOTUNE");
+  if (e && e[0] == '0') return false;
+  return getenv("BK_FOURSTEP_ELEMS") == nullptr;
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int64_t, int, int, int, int>, int> g_tune;
+
+static bk_status autotune_tiles(Plan* p, cudaStream_t st) {
+  const int nvec = p->n_comp * p->max_batch;
+  int dev = 0;
+  BK_TRY_CUDA(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(p->N, p->dtype, nvec, sm_count(), dev);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      p->tileE = it->second;
+      return fourstep_shapes(p, it->second);
+    }
+  }
+  const int cap = p->dtype == BK_F64 ? 4096 : 8192;
+  const int emin = std::max(p->fs.N1, 2 * p->fs.N2);
+  const size_t vbytes = dtype_size(p->dtype) * (size_t)p->pitch * nvec;
+  void* vin = nullptr;
+  void* vout = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bk_status r = dmalloc(&vin, vbytes);
+  if (r == BK_OK) r = dmalloc(&vout, vbytes);
+  if (r == BK_OK && (cudaMemsetAsync(vin, 0, vbytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+                     cudaEventCreate(&e1) != cudaSuccess)) {
+    set_error("autotune: set-up failed");
+    r = BK_ERR_CUDA;
+  }
+  int best = 0;
+  float best_ms = 0.f;
+  for (int E = emin; r == BK_OK && E <= cap; E *= 2) {
+    if (fourstep_shapes(p, E) != BK_OK) continue;  // shape outside the thread/shared-memory caps
+    r = plan_apply_n(p, vin, vout, nvec, false, p->s, st);
+    if (r == BK_OK) r = plan_apply_n(p, vin, vout, nvec, true, p->s, st);
+    if (r == BK_OK && cudaEventRecord(e0, st) != cudaSuccess) r = BK_ERR_CUDA;
+    if (r == BK_OK) r = plan_apply_n(p, vin, vout, nvec, false, p->s, st);
+    if (r == BK_OK) r = plan_apply_n(p, vin, vout, nvec, true, p->s, st);
+    float ms = 0.f;
+    if (r == BK_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                       cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)) {
+      set_error("autotune: timing failed");
+      r = BK_ERR_CUDA;
+    }
+    if (r == BK_OK && (best == 0 || ms < best_ms)) {
+      best = E;
+      best_ms = ms;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dfree(vin);
+  dfree(vout);
+  if (r != BK_OK) return r;
+  if (best == 0) return fourstep_shapes(p, 0);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+  }
+  p->tileE = best;
+  return fourstep_shapes(p, best);
+}
+
 bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtype, double t0,
                       double tf, int64_t pitch, cudaStream_t st) {
   *out = nullptr;
@@ -1061,19 +1153,17 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
     } else {
       // split DCT-I from 2^split_min_log2() on: fs the length-N/2 FFT, fso the length-N/4 one
       p->split = ilog2(N) >= split_min_log2(dtype);
-      if (p->split) {
-        if ((st_ = configure_fourstep(p->fs, N / 2, dtype, n_comp * max_batch)) != BK_OK) break;
-        if ((st_ = configure_fourstep(p->fso, N / 4, dtype, n_comp * max_batch)) != BK_OK) break;
-      } else if ((st_ = configure_fourstep(p->fs, N, dtype, n_comp * max_batch)) != BK_OK) {
-        break;
-      }
+      if ((st_ = fourstep_shapes(p, 0)) != BK_OK) break;
       const int64_t nvec = (int64_t)n_comp * max_batch;
       const size_t csz = 2 * dtype_size(dtype);
       if ((st_ = dmalloc(&p->scrA, csz * (size_t)N * nvec)) != BK_OK) break;
       if ((st_ = dmalloc(&p->scrY, dtype_size(dtype) * (size_t)(N + 1) * nvec)) != BK_OK) break;
       if ((st_ = dmalloc(&p->scrG, dtype_size(dtype) * (size_t)(N + 1) * nvec)) != BK_OK) break;
-      if ((st_ = dmalloc(&p->part1, dtype_size(dtype) * (size_t)p->fs.nPartA * nvec)) != BK_OK) break;
-      if ((st_ = dmalloc(&p->part2, dtype_size(dtype) * (size_t)p->fs.nPartA * nvec)) != BK_OK) break;
+      // partial sums for the narrowest pass-A tile any shape may take (most CTAs per vector)
+      const int nbMin = std::max(1, std::max(p->fs.N1, 2 * p->fs.N2) / p->fs.N1);
+      const size_t nPartMax = (size_t)std::max(p->fs.nPartA, p->fs.N2 / std::min(nbMin, p->fs.N2));
+      if ((st_ = dmalloc(&p->part1, dtype_size(dtype) * nPartMax * nvec)) != BK_OK) break;
+      if ((st_ = dmalloc(&p->part2, dtype_size(dtype) * nPartMax * nvec)) != BK_OK) break;
     }
     st_ = dtype == BK_F64 ? build_tables<double>(p, st) : build_tables<float>(p, st);
     if (st_ != BK_OK) break;
@@ -1084,6 +1174,9 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
     st_ = dtype == BK_F64 ? set_smem_attrs<double>(p) : set_smem_attrs<float>(p);
     if (st_ != BK_OK) break;
     if ((st_ = compute_weights(p, st)) != BK_OK) break;
+    if (!p->small && autotune_enabled()) {
+      if ((st_ = autotune_tiles(p, st)) != BK_OK) break;
+    }
     if (dense_default(dtype, N, n_comp * max_batch)) {
       if ((st_ = dense_build(p, st)) != BK_OK) break;
       p->dense = true;
@@ -1438,6 +1531,17 @@ bk_status bk_plan_set_dense(bk_plan* plan, int on, void* stream) {
     BK_TRY(bk::dense_build(p, (cudaStream_t)stream));
   }
   p->dense = true;
+  return BK_OK;
+}
+
+bk_status bk_plan_shape(const bk_plan* plan, int* path, int* N1, int* N2, int* elems) {
+  BK_ARG(plan != nullptr, "plan is NULL");
+  const bk::Plan* p = reinterpret_cast<const bk::Plan*>(plan);
+  const int pth = p->dense ? 3 : (p->small ? 0 : (p->split ? 2 : 1));
+  if (path) *path = pth;
+  if (N1) *N1 = (pth == 1 || pth == 2) ? p->fs.N1 : 0;
+  if (N2) *N2 = (pth == 1 || pth == 2) ? p->fs.N2 : 0;
+  if (elems) *elems = (pth == 1 || pth == 2) ? p->fs.NB * p->fs.N1 : 0;
   return BK_OK;
 }
 

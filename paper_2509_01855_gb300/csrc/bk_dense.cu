@@ -11,7 +11,8 @@
 // entries are FP64-exact before the split.
 //
 // Kernel shape (CTAs of 4 warps; a tile is 128 output rows x 16 vectors, its K range split
-// over up to 8 CTAs so that small products still spread over the GPU):
+// over up to 16 CTAs so that small products still spread over the GPU; at N = 1024 the product
+// streams its 9.8 MB matrix, which bounds it):
 //   - thread 0 streams the CTA's part of the A panel through up to four shared-memory stages
 //     with bulk copies (cp.async.bulk, completion on an mbarrier) and issues the MMAs
 //     (M = 128, N = 16, K = 8);
@@ -326,7 +327,7 @@ __global__ void k_identity(double* __restrict__ e, int L, int64_t pitch) {
 }
 
 constexpr size_t DT_SMEM_BUDGET = 200 * 1024;       // dynamic shared memory of one CTA at most
-constexpr int DT_KS_MAX = 8;                           // K splits per tile at most
+constexpr int DT_KS_MAX = 16;                          // K splits per tile at most
 
 static int dense_sms() {
   int dev = 0, n = 0;
@@ -336,7 +337,7 @@ static int dense_sms() {
 }
 
 // Launch shape of one dense product of nvec vectors: K splits KS (about two CTAs per SM over all
-// tiles, at most 8 and at most one per chunk; BK_DENSE_KSPLIT overrides), pipeline stages S
+// tiles, at most 16 and at most one per chunk; BK_DENSE_KSPLIT overrides), pipeline stages S
 // (up to 4, within the shared-memory budget next to the staged vectors).
 struct DenseShape {
   int KS, S;

@@ -28,6 +28,7 @@ struct Plan {
   int n_comp = 1, max_batch = 1, dtype = BK_F64;
   double t0 = 0, tf = 0, s = 0;
   bool small = true;          // whole chain in one CTA per vector
+  int tileE = 0;              // four-step elements per CTA chosen by the autotuner (0: heuristic)
   size_t smemS = 0;           // dynamic shared memory of the single-CTA kernel
   int thrS = 256;             // threads of the single-CTA kernel
   void* tw = nullptr;         // omega_N^i, i < N (single-CTA plans; the N < 16 direct DFT)

@@ -154,3 +154,46 @@ def test_bad_arguments():
     v = plan.empty(2)
     with pytest.raises(BirkhoffError):
         api.birkhoff_apply(plan, v, plan.empty(2), batch=2)   # batch > max_batch
+
+
+def _apply_with(plan, V, trans=False):
+    api = _api()
+    L = plan.N + 1
+    v = plan.empty(V.shape[0])
+    v[:, :, :L] = torch.as_tensor(V, dtype=plan.dtype)
+    out = plan.empty(V.shape[0])
+    (api.birkhoff_apply_T if trans else api.birkhoff_apply)(plan, v, out)
+    torch.cuda.synchronize()
+    return out.cpu().double().numpy()[:, :, :L]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_autotuned_tiles(dtype, monkeypatch):
+    """The tile autotuner picks a valid four-step shape, plans of one size share it (cached),
+    and the tuned and the heuristic shapes both match the oracle."""
+    api = _api()
+    N = 1 << 16
+    p1 = api.Plan(N, n_comp=4, dtype=dtype, t0=0.0, tf=3.0)
+    s1 = p1.shape()
+    assert s1["path"] == "four_step"
+    assert s1["N1"] * s1["N2"] == N
+    assert s1["elems"] >= max(s1["N1"], 2 * s1["N2"]) and s1["elems"] & (s1["elems"] - 1) == 0
+    p2 = api.Plan(N, n_comp=4, dtype=dtype, t0=0.0, tf=3.0)
+    assert p2.shape() == s1
+    monkeypatch.setenv("BK_AUTOTUNE", "0")
+    p3 = api.Plan(N, n_comp=4, dtype=dtype, t0=0.0, tf=3.0)
+    V = synth.gaussian((1, 4, N + 1), "tune", N)
+    ref = ob.fastbv(V, 0.0, 3.0)
+    refT = ob.fastbv_T(V, 0.0, 3.0)
+    for p in (p1, p3):
+        assert _rel(_apply_with(p, V), ref) < TOL[dtype]
+        assert _rel(_apply_with(p, V, True), refT) < TOL[dtype]
+
+
+def test_plan_shapes():
+    api = _api()
+    assert api.Plan(64, dtype=torch.float64).shape()["path"] == "single_cta"
+    assert api.Plan(512, dtype=torch.float64).shape()["path"] == "four_step"
+    assert api.Plan(1 << 19, n_comp=1, dtype=torch.float64).shape()["path"] == "split_four_step"
+    assert api.Plan(256, n_comp=4, dtype=torch.float32).shape()["path"] == "dense"
+    assert api.Plan(32, n_comp=4, dtype=torch.float32).shape()["path"] == "single_cta"

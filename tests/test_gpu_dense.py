@@ -82,10 +82,10 @@ def test_dense_constant_and_row0():
     assert np.max(np.abs(o - (t.numpy() - 1.0))) < 1e-5 * 3.0
 
 
-@pytest.mark.parametrize("ksplit", ["1", "3", "8"])
+@pytest.mark.parametrize("ksplit", ["1", "3", "8", "16"])
 @pytest.mark.parametrize("N", [64, 1024])
 def test_dense_k_splits(N, ksplit, monkeypatch):
-    """Unsplit tiles, an uneven split (chunks per CTA differ) and the largest split give the
+    """Unsplit tiles, an uneven split (chunks per CTA differ) and the largest splits give the
     same product (partials are added in a fixed order)."""
     monkeypatch.setenv("BK_DENSE_KSPLIT", ksplit)
     got, V = _dense_run(N, False, 4, 5)
