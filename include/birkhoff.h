@@ -8,7 +8,8 @@
  *
  * Conventions shared by every call
  * --------------------------------
- *  - Grid: N is a power of two, 4 <= N <= 2^24; the L = N + 1 CGL nodes are
+ *  - Grid: N is a power of two, 4 <= N <= 2^24, or any N with 4 <= N <= 1024; the L = N + 1
+ *    CGL nodes are
  *    tau_j = -cos(j pi / N), ascending (Eq. CGLpts), mapped to t_j = t0 + s (tau_j + 1),
  *    s = (tf - t0) / 2.
  *  - Vectors are device pointers owned by the caller, one length-L block per component,
@@ -67,7 +68,12 @@ uint64_t bk_launch_count(void);
  * ------------------------------------------------------------------------------------------ */
 
 /* Create a plan for Birkhoff products on the CGL grid of size N over [t0, tf].
- *   N          power of two, 4 <= N <= 2^24
+ *   N          power of two, 4 <= N <= 2^24, or any N in [4, 1024]. A power of two takes the
+ *              FFT chain (or, with n_comp * max_batch <= 16, the dense product: BK_F32 on the
+ *              tensor cores for 256 <= N <= 1024, BK_F64 on the CUDA cores for 64 <= N <= 1024);
+ *              any other N takes the dense product in both precisions (B^a formed once in FP64
+ *              from its definition: Chebyshev coefficients of the Lagrange basis times the
+ *              closed-form integrals of T_k, Eq. intChebPoly=)
  *   n_comp     components per batch item (>= 1)
  *   max_batch  largest `batch` later passed to birkhoff_apply / birkhoff_apply_T (>= 1); the
  *              plan's scratch is sized for max_batch * n_comp vectors
@@ -128,15 +134,16 @@ bk_status birkhoff_apply_noalloc(const double* v, double* out, int64_t N, int nv
 bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int batch,
                            void* stream);
 
-/* Switch a BK_F32 plan with N <= 1024 between the FFT chain (on = 0) and the dense product on
- * the tensor cores (on = 1) for birkhoff_apply, birkhoff_apply_T and every operator built on the
- * plan. The dense path multiplies by B^a itself (the matrix of Eq. manyDefs, formed once from
- * the FP64 FFT product of the unit vectors) split into two TF32 parts, three tcgen05 TF32
- * products per block accumulated in FP32 (the paper's Fig. 5 compares FastBV with the dense
- * product on a CPU). The first switch on builds the tables (two N+1 x N+1 matrices of 8-byte
- * hi/lo pairs, ~19 MB at N = 1024) on `stream` and synchronises it; the plan owns them.
- * Errors: BK_ERR_UNSUPPORTED for FP64 plans or N > 1024; BK_ERR_OOM; BK_ERR_CUDA. Not thread
- * safe against applies of the same plan in flight. */
+/* Switch a plan with N <= 1024 between the FFT chain (on = 0) and the dense product (on = 1)
+ * for birkhoff_apply, birkhoff_apply_T and every operator built on the plan. The dense path
+ * multiplies by B^a itself (the matrix of Eq. manyDefs, formed once in FP64 from its
+ * definition). BK_F32: B^a split into two TF32 parts, three tcgen05 TF32 products per block
+ * accumulated in FP32; BK_F64: FP64 FMAs on the CUDA cores (tcgen05 has no FP64 kind). The
+ * paper's Fig. 5 compares FastBV with the dense product on a CPU. The first switch on builds the
+ * tables (two N+1 x N+1 matrices of 8-byte entries, ~17-19 MB at N = 1024) on `stream` and
+ * synchronises it; the plan owns them. Errors: BK_ERR_UNSUPPORTED for N > 1024, or on = 0 for
+ * an N that is not a power of two; BK_ERR_OOM; BK_ERR_CUDA. Not thread safe against applies of
+ * the same plan in flight. */
 bk_status bk_plan_set_dense(bk_plan* plan, int on, void* stream);
 
 /* How a plan computes its products. *path: 0 one CTA per vector (small N), 1 four-step FFT,
@@ -146,10 +153,11 @@ bk_status bk_plan_set_dense(bk_plan* plan, int on, void* stream);
  * environment BK_AUTOTUNE=0). Outputs may be NULL. */
 bk_status bk_plan_shape(const bk_plan* plan, int* path, int* N1, int* N2, int* elems);
 
-/* *on = 1 while the plan's products take the dense tensor-core path, else 0. BK_F32 plans with
- * 64 <= N <= 1024 and n_comp * max_batch <= 16 start on it (where it measured faster than the
- * FFT chain); the environment variable BK_DENSE=0 (read at plan creation) keeps every plan on
- * the FFT chain, BK_DENSE=1 starts every supported plan on the dense path. */
+/* *on = 1 while the plan's products take the dense path, else 0. Plans with n_comp * max_batch
+ * <= 16 start on it where it measured faster than the FFT chain (BK_F32 256 <= N <= 1024,
+ * BK_F64 64 <= N <= 1024), and so does every N that is not a power of two; the environment
+ * variable BK_DENSE=0 (read at plan creation) keeps power-of-two plans on the FFT chain,
+ * BK_DENSE=1 starts every supported plan on the dense path. */
 bk_status bk_plan_dense_state(const bk_plan* plan, int* on);
 
 /* Read (and clear) the dense kernel's error word: *err = 0 when every dense product so far

@@ -1020,16 +1020,19 @@ static bk_status set_smem_attrs(const Plan* p) {
   return BK_OK;
 }
 
-// FP32 plans take the dense tensor-core product by default where it measured faster than the
-// FFT chain (cold L2, 4 vectors, FFT / dense ms: 2^6 0.013 / 0.011, 2^8 0.019 / 0.013, 2^10
-// 0.027 / 0.017; 64 vectors: 2^10 0.025 / 0.027): 64 <= N <= 1024 with at most 16 vectors per
-// product. BK_DENSE=0 turns the default off, BK_DENSE=1 extends it to every supported size.
+// Plans take the dense product by default where it measured faster than the FFT chain, with
+// at most 16 vectors per product. FP32 (tensor cores): 256 <= N <= 1024 (4 vectors, FFT /
+// dense: warm L2, back-to-back products, 2^8 10.3 / 9.3 us, 2^9 16.4 / 12.4 us, 2^10 16.4 /
+// 14.3 us; cold L2 2^10 0.019-0.027 / 0.017-0.019 ms; equal at 2^6-2^7). FP64 (CUDA cores):
+// 64 <= N <= 1024 (cold L2, ms: 2^6 0.033 / 0.019, 2^8 0.056 / 0.023, 2^10 0.068 / 0.036).
+// With 64 vectors the FFT chain wins from 2^10. BK_DENSE=0 turns the default off, BK_DENSE=1
+// extends it to every supported size.
 static bool dense_default(int dtype, int64_t N, int nvec) {
-  if (dtype != BK_F32 || !dense_supported(N)) return false;
+  if (!dense_supported(N)) return false;
   const char* e = getenv("BK_DENSE");
   if (e && e[0] == '0') return false;
   if (e && e[0] == '1') return true;
-  return N >= 64 && nvec <= 16;
+  return (dtype == BK_F64 ? N >= 64 : N >= 256) && nvec <= 16;
 }
 
 // Four-step shapes of a plan for E complex elements per CTA (0: the occupancy heuristic).
@@ -1123,7 +1126,8 @@ static bk_status autotune_tiles(Plan* p, cudaStream_t st) {
 bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtype, double t0,
                       double tf, int64_t pitch, cudaStream_t st) {
   *out = nullptr;
-  BK_ARG(is_pow2(N) && N >= 4 && N <= (int64_t(1) << 24), "N must be a power of two in [4, 2^24], got %lld", (long long)N);
+  BK_ARG(N >= 4 && (is_pow2(N) ? N <= (int64_t(1) << 24) : dense_supported(N)),
+         "N must be a power of two in [4, 2^24] or any N in [4, 1024], got %lld", (long long)N);
   BK_ARG(n_comp >= 1 && n_comp <= 64, "n_comp must be in [1, 64], got %d", n_comp);
   BK_ARG(max_batch >= 1, "max_batch must be >= 1, got %d", max_batch);
   BK_ARG(dtype == BK_F64 || dtype == BK_F32, "dtype must be BK_F64 or BK_F32");
@@ -1142,10 +1146,23 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
   p->tf = tf;
   p->s = 0.5 * (tf - t0);
   p->pitch = pitch;
-  p->small = N <= small_limit(dtype);
+  // N not a power of two: the FFT chain does not apply; every product is the dense one
+  p->generic = !is_pow2(N);
+  p->small = !p->generic && N <= small_limit(dtype);
   bk_status st_ = BK_OK;
   AllocCounter counter(&p->bytes);
   do {
+    if (p->generic) {
+      if ((st_ = dmalloc((void**)&p->t_nodes, sizeof(double) * (size_t)L)) != BK_OK) break;
+      k_grid_tables<<<(int)((L + 255) / 256), 256, 0, st>>>(p->t_nodes, N, t0, p->s);
+      note_launch();
+      if (cudaGetLastError() != cudaSuccess) { st_ = BK_ERR_CUDA; set_error("grid table launch failed"); break; }
+      if ((st_ = dense_build(p, st)) != BK_OK) break;  // also the weights (last row of B^a)
+      p->dense = true;
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) { set_error("plan tables: %s", cudaGetErrorString(e)); st_ = BK_ERR_CUDA; }
+      break;
+    }
     if (p->small) {
       p->smemS = dtype == BK_F64 ? smem_small<double>(N) : smem_small<float>(N);
       p->thrS = round_threads(N / 16);
@@ -1341,7 +1358,7 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
 
 bk_status plan_apply_n(const Plan* p, const void* v, void* out, int nvec, bool trans, double s,
                        cudaStream_t st) {
-  if (p->dense) return dense_apply(p, (const float*)v, (float*)out, nvec, trans, s, st);
+  if (p->dense) return dense_apply(p, v, out, nvec, trans, s, st);
   if (p->dtype == BK_F64)
     return apply_impl<double>(p, (const double*)v, (double*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2, p->scrG);
   return apply_impl<float>(p, (const float*)v, (float*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2, p->scrG);
@@ -1519,11 +1536,15 @@ bk_status bk_plan_set_dense(bk_plan* plan, int on, void* stream) {
   BK_ARG(plan != nullptr, "plan is NULL");
   bk::Plan* p = reinterpret_cast<bk::Plan*>(plan);
   if (!on) {
+    if (p->generic) {
+      bk::set_error("N = %lld is not a power of two: the plan has no FFT path", (long long)p->N);
+      return BK_ERR_UNSUPPORTED;
+    }
     p->dense = false;
     return BK_OK;
   }
-  if (p->dtype != BK_F32 || !bk::dense_supported(p->N)) {
-    bk::set_error("dense products need a BK_F32 plan with N <= 1024 (N = %lld)", (long long)p->N);
+  if (!bk::dense_supported(p->N)) {
+    bk::set_error("dense products need N <= 1024 (N = %lld)", (long long)p->N);
     return BK_ERR_UNSUPPORTED;
   }
   if (!p->dA[0]) {

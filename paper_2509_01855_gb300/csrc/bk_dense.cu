@@ -299,16 +299,16 @@ __global__ void __launch_bounds__(128, 1)
   if (tid == 0 && fail) atomicExch(err, fail);
 }
 
-// Pre-tiled A = B^a (trans = 0) or (B^a)^T (trans = 1) from the columns of B^a (FP64,
-// column k at cols[k * pitch], entry m = B^a[m][k]), zero outside L x L.
-__global__ void k_dense_tile(const double* __restrict__ cols, int64_t pitch, int L, int Mt, int nK, int trans,
+// Pre-tiled A = B^a (trans = 0) or (B^a)^T (trans = 1) from B^a (FP64, row-major L x L), zero
+// outside L x L.
+__global__ void k_dense_tile(const double* __restrict__ B, int L, int Mt, int nK, int trans,
                              unsigned char* __restrict__ dst) {
   const int Kpad = nK * DT_KC;
   const int64_t total = (int64_t)Mt * DT_M * Kpad;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int m = (int)(i / Kpad), k = (int)(i - (int64_t)m * Kpad);
     double a = 0.0;
-    if (m < L && k < L) a = trans ? cols[(int64_t)m * pitch + k] : cols[(int64_t)k * pitch + m];
+    if (m < L && k < L) a = trans ? B[(int64_t)k * L + m] : B[(int64_t)m * L + k];
     const float hi = tf32_rna((float)a);
     const float lo = tf32_rna((float)(a - (double)hi));
     unsigned char* blk = dst + ((size_t)(m / DT_M) * nK + k / DT_KC) * DT_CHUNK;
@@ -318,11 +318,182 @@ __global__ void k_dense_tile(const double* __restrict__ cols, int64_t pitch, int
   }
 }
 
-__global__ void k_identity(double* __restrict__ e, int L, int64_t pitch) {
-  const int64_t total = (int64_t)L * pitch;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = i / pitch, m = i - k * pitch;
-    e[i] = (m == k) ? 1.0 : 0.0;
+// ---------------------------------------------------------------------------------------------
+// B^a in FP64 for any N (not only powers of two), from its definition: row i of B^a integrates
+// the Lagrange basis of the CGL nodes over [-1, tau_i] (Eq. xN=Birka+b with Eq. birk-conditions).
+// Each basis polynomial is a Chebyshev series, l_j = sum_k Psi[k][j] T_k with the discrete
+// Chebyshev coefficients Psi[k][j] = 2 / (N c_k c_j) T_k(tau_j) (c_0 = c_N = 2, else 1), and
+// each T_k integrates in closed form (Eq. intChebPoly=): Phi[i][k] = int_{-1}^{tau_i} T_k, so
+// B^a = Phi Psi. With tau_j = -cos(j pi / N), T_m(tau_i) = (-1)^m cos(pi m i / N), read from a
+// table of cos(pi q / N), q < 2N, at q = m i mod 2N. Row 0 is exactly zero.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_cospi_table(double* __restrict__ c, int N) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 2 * N; q += gridDim.x * blockDim.x) c[q] = cospi((double)q / N);
+}
+
+__device__ __forceinline__ double cheb_at_node(const double* __restrict__ c, int N, int m, int i) {
+  const double v = c[(int)(((int64_t)m * i) % (2 * N))];
+  return (m & 1) ? -v : v;
+}
+
+__global__ void k_form_phi(double* __restrict__ Phi, int N, const double* __restrict__ c) {
+  const int L = N + 1;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)L * L;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / L), k = (int)(idx - (int64_t)i * L);
+    double tau = sinpi((double)(2 * i - N) / (double)(2 * N));
+    if (i == 0) tau = -1.0;
+    if (i == N) tau = 1.0;
+    double v;
+    if (k == 0) {
+      v = tau + 1.0;
+    } else if (k == 1) {
+      v = 0.5 * (tau * tau - 1.0);
+    } else {
+      // T_{k+1} / (2(k+1)) - T_{k-1} / (2(k-1)), minus its value at -1: (-1)^{k+1} / (k^2 - 1) added
+      v = cheb_at_node(c, N, k + 1, i) / (2.0 * (k + 1)) - cheb_at_node(c, N, k - 1, i) / (2.0 * (k - 1)) +
+          ((k & 1) ? 1.0 : -1.0) / ((double)k * k - 1.0);
+    }
+    Phi[idx] = i == 0 ? 0.0 : v;
+  }
+}
+
+__global__ void k_form_psi(double* __restrict__ Psi, int N, const double* __restrict__ c) {
+  const int L = N + 1;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)L * L;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx / L), j = (int)(idx - (int64_t)k * L);
+    const double ck = (k == 0 || k == N) ? 2.0 : 1.0, cj = (j == 0 || j == N) ? 2.0 : 1.0;
+    Psi[idx] = 2.0 / ((double)N * ck * cj) * cheb_at_node(c, N, k, j);
+  }
+}
+
+// C = A B, all row-major n x n FP64 (plan set-up only): 32 x 32 output tiles, 2 x 2 per thread.
+__global__ void __launch_bounds__(256) k_gemm64(const double* __restrict__ A, const double* __restrict__ B,
+                                                double* __restrict__ C, int n) {
+  __shared__ double As[32][33], Bs[32][33];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int q = threadIdx.x; q < 32 * 32; q += 256) {
+      const int rr = q >> 5, cc = q & 31;
+      As[rr][cc] = (r0 + rr < n && k0 + cc < n) ? A[(int64_t)(r0 + rr) * n + k0 + cc] : 0.0;
+      Bs[rr][cc] = (k0 + rr < n && c0 + cc < n) ? B[(int64_t)(k0 + rr) * n + c0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const double a0 = As[ty][kk], a1 = As[ty + 16][kk];
+      const double b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+      acc[0][0] = fma(a0, b0, acc[0][0]);
+      acc[0][1] = fma(a0, b1, acc[0][1]);
+      acc[1][0] = fma(a1, b0, acc[1][0]);
+      acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int r = r0 + ty + 16 * a, cc = c0 + tx + 16 * b;
+      if (r < n && cc < n) C[(int64_t)r * n + cc] = acc[a][b];
+    }
+}
+
+// Column-major FP64 copy of A = B^a (trans = 0) or (B^a)^T (trans = 1): Acm[k Mp + m], zero for
+// m >= L.
+__global__ void k_dense_cm64(const double* __restrict__ B, int L, int Mp, int trans, double* __restrict__ Acm) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)L * Mp;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx / Mp), m = (int)(idx - (int64_t)k * Mp);
+    Acm[idx] = m < L ? (trans ? B[(int64_t)k * L + m] : B[(int64_t)m * L + k]) : 0.0;
+  }
+}
+
+// Clenshaw-Curtis weights: the last row of B^a (the remark after Eq. Ba=10).
+__global__ void k_last_row(const double* __restrict__ B, int L, double* __restrict__ w64, float* __restrict__ w32) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < L; j += gridDim.x * blockDim.x) {
+    const double v = B[(int64_t)(L - 1) * L + j];
+    w64[j] = v;
+    if (w32) w32[j] = (float)v;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP64 dense product on the CUDA cores (GB300 has no FP64 tensor-core kind in tcgen05): one
+// thread per output row, NC vectors per CTA, the K range split over KS CTAs per tile with the
+// same last-arriver reduction in fixed order as the FP32 kernel. Per 8-byte matrix element NC
+// FP64 FMAs: the FP64 pipe bounds it (L^2 nvec FMAs; N = 1024, 4 vectors: ~7 us at 1.25 TFLOP/s).
+// ---------------------------------------------------------------------------------------------
+template <int NC>
+__global__ void __launch_bounds__(128)
+    k_dense_f64(const double* __restrict__ Acm, int Mp, const double* __restrict__ V, double* __restrict__ out,
+                int nvec, int L, int64_t pitch, int KS, double s, double* __restrict__ part,
+                unsigned* __restrict__ cnt) {
+  constexpr int KC = 64;
+  __shared__ double Vs[NC][KC];
+  __shared__ int last;
+  const int tid = threadIdx.x;
+  const int m = blockIdx.x * 128 + tid;  // < Mp (rows >= L are zero)
+  const int n0 = blockIdx.y * NC, z = blockIdx.z;
+  const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+  const int kb = (int)((int64_t)z * L / KS), ke = (int)((int64_t)(z + 1) * L / KS);
+  double acc[NC];
+#pragma unroll
+  for (int n = 0; n < NC; ++n) acc[n] = 0.0;
+  for (int k0 = kb; k0 < ke; k0 += KC) {
+    const int kc = min(KC, ke - k0);
+    __syncthreads();
+    for (int i = tid; i < NC * KC; i += blockDim.x) {
+      const int n = i / KC, kk = i - n * KC;
+      Vs[n][kk] = (kk < kc && n0 + n < nvec) ? V[(int64_t)(n0 + n) * pitch + k0 + kk] : 0.0;
+    }
+    __syncthreads();
+    const double* a = Acm + (int64_t)k0 * Mp + m;
+#pragma unroll 8
+    for (int kk = 0; kk < kc; ++kk) {
+      const double av = a[(int64_t)kk * Mp];
+#pragma unroll
+      for (int n = 0; n < NC; ++n) acc[n] = fma(av, Vs[n][kk], acc[n]);
+    }
+  }
+  if (KS == 1) {
+    if (m < L) {
+#pragma unroll
+      for (int n = 0; n < NC; ++n)
+        if (n0 + n < nvec) out[(int64_t)(n0 + n) * pitch + m] = s * acc[n];
+    }
+  } else {
+    double* mine = part + (((size_t)tile * KS + z) * 128 + tid) * NC;
+#pragma unroll
+    for (int n = 0; n < NC; ++n) mine[n] = acc[n];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(&cnt[tile], 1u) == (unsigned)(KS - 1);
+    __syncthreads();
+    if (last) {
+      __threadfence();
+      double sum[NC];
+#pragma unroll
+      for (int n = 0; n < NC; ++n) sum[n] = 0.0;
+      for (int q = 0; q < KS; ++q) {
+        const double* src = part + (((size_t)tile * KS + q) * 128 + tid) * NC;
+#pragma unroll
+        for (int n = 0; n < NC; ++n) sum[n] += __ldcg(src + n);
+      }
+      if (m < L) {
+#pragma unroll
+        for (int n = 0; n < NC; ++n)
+          if (n0 + n < nvec) out[(int64_t)(n0 + n) * pitch + m] = s * sum[n];
+      }
+      if (tid == 0) cnt[tile] = 0u;
+    }
+  }
+  if (blockIdx.x == 0 && z == 0) {
+    for (int n = 0; n < NC && n0 + n < nvec; ++n)
+      for (int64_t mm = L + tid; mm < pitch; mm += blockDim.x) out[(int64_t)(n0 + n) * pitch + mm] = 0.0;
   }
 }
 
@@ -360,56 +531,108 @@ static DenseShape dense_shape(const Plan* p, int nvec) {
 
 bool dense_supported(int64_t N) { return N >= 4 && N <= DENSE_MAX_N; }
 
+static int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)); }
+
 bk_status dense_build(Plan* p, cudaStream_t st) {
-  BK_ARG(p->dtype == BK_F32 && dense_supported(p->N), "dense tables: FP32 plans with N <= %d only", DENSE_MAX_N);
-  const int64_t N = p->N, L = p->L;
-  const int Mt = (int)((L + DT_M - 1) / DT_M);
-  const int nK = (int)((L + DT_KC - 1) / DT_KC);
-  p->dMt = Mt;
-  p->dnK = nK;
-  const size_t bytes = (size_t)Mt * nK * DT_CHUNK;
-  for (int t = 0; t < 2; ++t) BK_TRY(dmalloc(&p->dA[t], bytes));
+  BK_ARG(dense_supported(p->N), "dense products: N <= %d only", DENSE_MAX_N);
+  const int N = (int)p->N, L = (int)p->L;
+  const bool f32 = p->dtype == BK_F32;
+  const int nvec = p->n_comp * p->max_batch;
   BK_TRY(dmalloc((void**)&p->derr, sizeof(int)));
   BK_TRY_CUDA(cudaMemsetAsync(p->derr, 0, sizeof(int), st));
-  // split-K partials and arrival counters for the plan's largest product
-  const int ny = (p->n_comp * p->max_batch + DT_N - 1) / DT_N;
-  BK_TRY(dmalloc(&p->dpart, sizeof(float) * (size_t)Mt * ny * DT_KS_MAX * DT_M * DT_N));
-  BK_TRY(dmalloc((void**)&p->dcnt, sizeof(unsigned) * (size_t)Mt * ny));
-  BK_TRY_CUDA(cudaMemsetAsync(p->dcnt, 0, sizeof(unsigned) * (size_t)Mt * ny, st));
-  // columns of B^a from the FP64 FFT product of the unit vectors (unit time scale)
-  Plan* q = nullptr;
-  const int64_t qp = round_up(L, 32);
-  BK_TRY(plan_create(&q, N, 1, (int)L, BK_F64, -1.0, 1.0, qp, st));
-  double* e = nullptr;
-  double* cols = nullptr;
-  bk_status r = dmalloc((void**)&e, sizeof(double) * (size_t)L * qp);
-  if (r == BK_OK) r = dmalloc((void**)&cols, sizeof(double) * (size_t)L * qp);
+  if (f32) {
+    p->dMt = (L + DT_M - 1) / DT_M;
+    p->dnK = (L + DT_KC - 1) / DT_KC;
+    const size_t bytes = (size_t)p->dMt * p->dnK * DT_CHUNK;
+    for (int t = 0; t < 2; ++t) BK_TRY(dmalloc(&p->dA[t], bytes));
+    const int ny = (nvec + DT_N - 1) / DT_N;
+    BK_TRY(dmalloc(&p->dpart, sizeof(float) * (size_t)p->dMt * ny * DT_KS_MAX * DT_M * DT_N));
+    BK_TRY(dmalloc((void**)&p->dcnt, sizeof(unsigned) * (size_t)p->dMt * ny));
+    BK_TRY_CUDA(cudaMemsetAsync(p->dcnt, 0, sizeof(unsigned) * (size_t)p->dMt * ny, st));
+  } else {
+    p->dMp = (int)round_up(L, 128);
+    for (int t = 0; t < 2; ++t) BK_TRY(dmalloc(&p->dA[t], sizeof(double) * (size_t)L * p->dMp));
+    // partials: 128 rows x (vectors rounded up to the 4- or 16-vector tile) x K splits;
+    // counters: one per tile, most tiles with 4 vectors per CTA
+    const int mt = p->dMp / 128;
+    const int tiles = mt * ((nvec + 3) / 4);
+    BK_TRY(dmalloc(&p->dpart, sizeof(double) * (size_t)mt * round_up(nvec, 16) * DT_KS_MAX * 128));
+    BK_TRY(dmalloc((void**)&p->dcnt, sizeof(unsigned) * (size_t)tiles));
+    BK_TRY_CUDA(cudaMemsetAsync(p->dcnt, 0, sizeof(unsigned) * (size_t)tiles, st));
+  }
+  // B^a = Phi Psi in FP64
+  double *c = nullptr, *Phi = nullptr, *Psi = nullptr, *B = nullptr;
+  const size_t mat = sizeof(double) * (size_t)L * L;
+  bk_status r = dmalloc((void**)&c, sizeof(double) * 2 * (size_t)N);
+  if (r == BK_OK) r = dmalloc((void**)&Phi, mat);
+  if (r == BK_OK) r = dmalloc((void**)&Psi, mat);
+  if (r == BK_OK) r = dmalloc((void**)&B, mat);
   if (r == BK_OK) {
-    k_identity<<<(int)std::min<int64_t>((L * qp + 255) / 256, 4096), 256, 0, st>>>(e, (int)L, qp);
-    note_launch();
-    r = cudaGetLastError() == cudaSuccess ? plan_apply_n(q, e, cols, (int)L, false, 1.0, st) : BK_ERR_CUDA;
+    k_cospi_table<<<grid_for(2 * N), 256, 0, st>>>(c, N);
+    k_form_phi<<<grid_for((int64_t)L * L), 256, 0, st>>>(Phi, N, c);
+    k_form_psi<<<grid_for((int64_t)L * L), 256, 0, st>>>(Psi, N, c);
+    k_gemm64<<<dim3((L + 31) / 32, (L + 31) / 32), 256, 0, st>>>(Phi, Psi, B, L);
+    for (int q = 0; q < 4; ++q) note_launch();
+    if (cudaGetLastError() != cudaSuccess) { r = BK_ERR_CUDA; set_error("dense matrix launch failed"); }
+  }
+  // weights (last row) when the plan has none yet (plans off the FFT path)
+  if (r == BK_OK && !p->w64) {
+    r = dmalloc((void**)&p->w64, sizeof(double) * p->pitch);
+    if (r == BK_OK && f32) r = dmalloc(&p->wT, sizeof(float) * p->pitch);
+    if (r == BK_OK && cudaMemsetAsync(p->w64, 0, sizeof(double) * p->pitch, st) != cudaSuccess) r = BK_ERR_CUDA;
+    if (r == BK_OK && f32 && cudaMemsetAsync(p->wT, 0, sizeof(float) * p->pitch, st) != cudaSuccess) r = BK_ERR_CUDA;
+    if (r == BK_OK) {
+      k_last_row<<<grid_for(L), 256, 0, st>>>(B, L, p->w64, f32 ? (float*)p->wT : nullptr);
+      note_launch();
+      if (cudaGetLastError() != cudaSuccess) { r = BK_ERR_CUDA; set_error("weights launch failed"); }
+    }
   }
   for (int t = 0; t < 2 && r == BK_OK; ++t) {
-    const int64_t total = (int64_t)Mt * DT_M * nK * DT_KC;
-    k_dense_tile<<<(int)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, st>>>(cols, qp, (int)L, Mt, nK, t,
-                                                                                   (unsigned char*)p->dA[t]);
+    if (f32) {
+      const int64_t total = (int64_t)p->dMt * DT_M * p->dnK * DT_KC;
+      k_dense_tile<<<grid_for(total), 256, 0, st>>>(B, L, p->dMt, p->dnK, t, (unsigned char*)p->dA[t]);
+    } else {
+      k_dense_cm64<<<grid_for((int64_t)L * p->dMp), 256, 0, st>>>(B, L, p->dMp, t, (double*)p->dA[t]);
+    }
     note_launch();
-    if (cudaGetLastError() != cudaSuccess) { r = BK_ERR_CUDA; set_error("dense tile launch failed"); }
+    if (cudaGetLastError() != cudaSuccess) { r = BK_ERR_CUDA; set_error("dense layout launch failed"); }
   }
   if (r == BK_OK && cudaStreamSynchronize(st) != cudaSuccess) { set_error("dense tables: sync failed"); r = BK_ERR_CUDA; }
-  dfree(e);
-  dfree(cols);
-  plan_destroy(q);
+  dfree(c);
+  dfree(Phi);
+  dfree(Psi);
+  dfree(B);
   if (r != BK_OK) return r;
-  BK_TRY_CUDA(cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DT_SMEM_BUDGET));
+  if (f32) BK_TRY_CUDA(cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DT_SMEM_BUDGET));
   return BK_OK;
 }
 
-bk_status dense_apply(const Plan* p, const float* v, float* out, int nvec, bool trans, double s, cudaStream_t st) {
+static bk_status dense_apply64(const Plan* p, const double* v, double* out, int nvec, bool trans, double s,
+                               cudaStream_t st) {
+  const int NC = nvec <= 4 ? 4 : 16;
+  const int mt = p->dMp / 128, ny = (nvec + NC - 1) / NC;
+  int KS = std::max(1, std::min(std::min(DT_KS_MAX, (int)((p->L + 31) / 32)), 2 * dense_sms() / std::max(1, mt * ny)));
+  if (const char* e = getenv("BK_DENSE_KSPLIT")) {
+    const long q = atol(e);
+    if (q >= 1) KS = (int)std::min<long>(std::min<long>(q, DT_KS_MAX), (p->L + 31) / 32);
+  }
+  const dim3 grid(mt, ny, KS);
+  const double* A = (const double*)p->dA[trans ? 1 : 0];
+  if (NC == 4)
+    k_dense_f64<4><<<grid, 128, 0, st>>>(A, p->dMp, v, out, nvec, (int)p->L, p->pitch, KS, s, (double*)p->dpart, p->dcnt);
+  else
+    k_dense_f64<16><<<grid, 128, 0, st>>>(A, p->dMp, v, out, nvec, (int)p->L, p->pitch, KS, s, (double*)p->dpart, p->dcnt);
+  BK_CHECK_LAUNCH();
+  return BK_OK;
+}
+
+bk_status dense_apply(const Plan* p, const void* v, void* out, int nvec, bool trans, double s, cudaStream_t st) {
+  if (p->dtype == BK_F64) return dense_apply64(p, (const double*)v, (double*)out, nvec, trans, s, st);
   const DenseShape sh = dense_shape(p, nvec);
   const dim3 grid(p->dMt, (nvec + DT_N - 1) / DT_N, sh.KS);
-  k_dense_tc<<<grid, 128, sh.smem, st>>>((const unsigned char*)p->dA[trans ? 1 : 0], v, out, nvec, (int)p->L, p->pitch,
-                                         p->dnK, sh.KS, sh.S, (float)s, (float*)p->dpart, p->dcnt, p->derr);
+  k_dense_tc<<<grid, 128, sh.smem, st>>>((const unsigned char*)p->dA[trans ? 1 : 0], (const float*)v, (float*)out, nvec,
+                                         (int)p->L, p->pitch, p->dnK, sh.KS, sh.S, (float)s, (float*)p->dpart, p->dcnt,
+                                         p->derr);
   BK_CHECK_LAUNCH();
   return BK_OK;
 }

@@ -28,6 +28,7 @@ struct Plan {
   int n_comp = 1, max_batch = 1, dtype = BK_F64;
   double t0 = 0, tf = 0, s = 0;
   bool small = true;          // whole chain in one CTA per vector
+  bool generic = false;       // N not a power of two: dense products only
   int tileE = 0;              // four-step elements per CTA chosen by the autotuner (0: heuristic)
   size_t smemS = 0;           // dynamic shared memory of the single-CTA kernel
   int thrS = 256;             // threads of the single-CTA kernel
@@ -50,10 +51,11 @@ struct Plan {
   double* w64 = nullptr;      // Clenshaw-Curtis weights (FP64, device, tau-domain)
   void* wT = nullptr;         // Clenshaw-Curtis weights in the working type (device)
   size_t bytes = 0;           // device bytes this plan allocated
-  // Dense tensor-core path (FP32 plans, N <= 1024): B^a and (B^a)^T pre-tiled as TF32 hi/lo
-  // parts (dA[0], dA[1]); used by the applies while `dense` is set.
+  // Dense path (N <= 1024): B^a and (B^a)^T, FP32 plans pre-tiled as TF32 hi/lo parts for the
+  // tensor cores, FP64 plans column-major FP64 (dA[0], dA[1]); used while `dense` is set.
   bool dense = false;
   void* dA[2] = {nullptr, nullptr};
+  int dMp = 0;                // FP64 layout: rows padded to a multiple of 128
   int* derr = nullptr;        // device error word of the dense kernel (0 = no timeout)
   int dMt = 0, dnK = 0;       // 128-row output tiles, 32-wide K chunks
   void* dpart = nullptr;      // split-K partial sums (FP32)
@@ -72,6 +74,6 @@ bk_status plan_apply_n(const Plan* p, const void* v, void* out, int nvec, bool t
 // Dense tensor-core path (bk_dense.cu).
 bool dense_supported(int64_t N);
 bk_status dense_build(Plan* p, cudaStream_t st);
-bk_status dense_apply(const Plan* p, const float* v, float* out, int nvec, bool trans, double s, cudaStream_t st);
+bk_status dense_apply(const Plan* p, const void* v, void* out, int nvec, bool trans, double s, cudaStream_t st);
 
 }  // namespace bk

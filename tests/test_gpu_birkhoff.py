@@ -18,9 +18,11 @@ def _api():
     return api
 
 
-def _run(N, dtype, trans, n_comp=3, batch=2, t0=0.0, tf=3.0, V=None, pitch=0):
+def _run(N, dtype, trans, n_comp=3, batch=2, t0=0.0, tf=3.0, V=None, pitch=0, dense=None):
     api = _api()
     plan = api.Plan(N, n_comp=n_comp, max_batch=batch, dtype=dtype, t0=t0, tf=tf, pitch=pitch)
+    if dense is not None:
+        plan.set_dense(dense)
     L = N + 1
     if V is None:
         V = synth.gaussian((batch, n_comp, L), "bk", N, int(trans))
@@ -48,6 +50,16 @@ def test_apply_vs_dense_oracle(N, dtype, trans):
     B = ob.dense_B(N, 0.0, 3.0)
     ref = V @ (B if trans else B.T)
     assert _rel(got, ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N", [64, 128, 256, 512, 1024])
+@pytest.mark.parametrize("trans", [False, True])
+def test_fft_chain_where_dense_is_default(N, dtype, trans):
+    """The FFT chain at the sizes whose plans default to the dense product."""
+    got, V, _ = _run(N, dtype, trans, dense=False)
+    B = ob.dense_B(N, 0.0, 3.0)
+    assert _rel(got, V @ (B if trans else B.T)) < TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -147,9 +159,11 @@ def test_bad_arguments():
     api = _api()
     from paper_2509_01855_gb300._lib import BirkhoffError
     with pytest.raises(BirkhoffError):
-        api.Plan(100)            # not a power of two
+        api.Plan(1500)           # not a power of two and above the dense limit of 1024
     with pytest.raises(BirkhoffError):
         api.Plan(2)              # too small
+    with pytest.raises(BirkhoffError):
+        api.Plan(1 << 25)        # above 2^24
     plan = api.Plan(64, n_comp=1, max_batch=1)
     v = plan.empty(2)
     with pytest.raises(BirkhoffError):
@@ -192,8 +206,9 @@ def test_autotuned_tiles(dtype, monkeypatch):
 
 def test_plan_shapes():
     api = _api()
-    assert api.Plan(64, dtype=torch.float64).shape()["path"] == "single_cta"
-    assert api.Plan(512, dtype=torch.float64).shape()["path"] == "four_step"
+    assert api.Plan(32, dtype=torch.float64).shape()["path"] == "single_cta"
+    assert api.Plan(512, dtype=torch.float64).shape()["path"] == "dense"
+    assert api.Plan(2048, dtype=torch.float64).shape()["path"] == "four_step"
     assert api.Plan(1 << 19, n_comp=1, dtype=torch.float64).shape()["path"] == "split_four_step"
     assert api.Plan(256, n_comp=4, dtype=torch.float32).shape()["path"] == "dense"
     assert api.Plan(32, n_comp=4, dtype=torch.float32).shape()["path"] == "single_cta"

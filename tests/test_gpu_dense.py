@@ -113,25 +113,92 @@ def test_dense_repeat_is_bitwise():
 
 
 def test_dense_default_policy(monkeypatch):
-    """FP32 plans with 64 <= N <= 1024 and at most 16 vectors start on the dense path."""
+    """FP32 plans with 256 <= N <= 1024 and FP64 plans with 64 <= N <= 1024, at most 16
+    vectors, start on the dense path."""
     api = _api()
-    for N, n_comp, batch, want in [(32, 4, 1, False), (64, 4, 1, True), (1024, 4, 4, True),
+    for N, n_comp, batch, want in [(128, 4, 1, False), (256, 4, 1, True), (1024, 4, 4, True),
                                    (1024, 4, 5, False), (2048, 4, 1, False)]:
         p = api.Plan(N, n_comp=n_comp, max_batch=batch, dtype=torch.float32)
         assert p.is_dense() == want, (N, n_comp, batch)
+    for N, want in [(32, False), (64, True), (1024, True), (2048, False)]:
+        assert api.Plan(N, n_comp=4, dtype=torch.float64).is_dense() == want, N
     monkeypatch.setenv("BK_DENSE", "0")
     assert not api.Plan(256, n_comp=4, dtype=torch.float32).is_dense()
+    assert not api.Plan(256, n_comp=4, dtype=torch.float64).is_dense()
+    assert api.Plan(100, n_comp=4, dtype=torch.float64).is_dense()   # no FFT path for N = 100
+
+
+def _run_any(N, dtype, trans, n_comp, batch, dense=None):
+    api = _api()
+    plan = api.Plan(N, n_comp=n_comp, max_batch=batch, dtype=dtype, t0=0.0, tf=3.0)
+    if dense is not None:
+        plan.set_dense(dense)
+    L = N + 1
+    V = synth.gaussian((batch, n_comp, L), "any", N, int(trans))
+    v = plan.empty(batch)
+    v[:, :, :L] = torch.as_tensor(V, dtype=dtype)
+    v[:, :, L:] = 7.0
+    out = plan.empty(batch)
+    out.fill_(3.0)
+    (api.birkhoff_apply_T if trans else api.birkhoff_apply)(plan, v, out)
+    torch.cuda.synchronize()
+    o = out.cpu().double().numpy()
+    assert np.all(o[:, :, L:] == 0.0), "padding not zeroed"
+    return o[:, :, :L], V, plan
+
+
+TOL = {torch.float64: 1e-12, torch.float32: TOL32}
+
+
+@pytest.mark.parametrize("N", [4, 8, 64, 256, 1024])
+@pytest.mark.parametrize("trans", [False, True])
+@pytest.mark.parametrize("n_comp,batch", [(4, 1), (5, 4)])
+def test_dense_f64_vs_dense_oracle(N, trans, n_comp, batch):
+    """FP64 dense product (CUDA-core FMAs, split K) against the oracle's B^a at 1e-12."""
+    got, V, _ = _run_any(N, torch.float64, trans, n_comp, batch, dense=True)
+    B = ob.dense_B(N, 0.0, 3.0)
+    assert _rel(got, V @ (B if trans else B.T)) < 1e-12
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("N", [5, 6, 7, 12, 100, 300, 1000])
+@pytest.mark.parametrize("trans", [False, True])
+def test_any_N_products(N, dtype, trans):
+    """N not a power of two: the plan takes the dense product, B^a formed from its definition."""
+    got, V, plan = _run_any(N, dtype, trans, 3, 2)
+    assert plan.shape()["path"] == "dense"
+    B = ob.dense_B(N, 0.0, 3.0)
+    assert _rel(got, V @ (B if trans else B.T)) < TOL[dtype]
+
+
+@pytest.mark.parametrize("N", [5, 12, 100, 1000])
+def test_any_N_grid(N):
+    """Nodes and Clenshaw-Curtis weights (the last row of B^a) for an N that is not a power of
+    two: against the oracle's nodes and closed-form weights; B 1 = t - t0."""
+    from oracle import grid as og
+    api = _api()
+    plan = api.Plan(N, dtype=torch.float64, t0=0.0, tf=2.0)
+    t, w = plan.grid()
+    tau = og.cgl_nodes(N)
+    assert np.max(np.abs(t.numpy() - (tau + 1.0))) < 1e-15
+    assert np.max(np.abs(w.numpy() - og.cc_weights_sum(N))) < 1e-13
+    v = plan.empty(1)
+    v[:, :, :N + 1] = 1.0
+    out = plan.empty(1)
+    api.birkhoff_apply(plan, v, out)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(out[0, 0, :N + 1].cpu().numpy() - t.numpy())) < 1e-13
 
 
 def test_dense_switch_back_and_unsupported():
     api = _api()
     from paper_2509_01855_gb300._lib import BirkhoffError
-    p64 = api.Plan(256, dtype=torch.float64)
-    with pytest.raises(BirkhoffError):
-        p64.set_dense(True)
     big = api.Plan(2048, dtype=torch.float32)
     with pytest.raises(BirkhoffError):
         big.set_dense(True)
+    odd = api.Plan(100, dtype=torch.float64)
+    with pytest.raises(BirkhoffError):
+        odd.set_dense(False)
     a, V = _dense_run(64, True, 2, 1, dense=True)
     B = ob.dense_B(64, 0.0, 3.0)
     assert _rel(a, V @ B) < TOL32

@@ -81,7 +81,8 @@ def test_state_operator_and_preconditioner(kind, N, dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("kind,N", [(op.ORBIT, 16), (op.ORBIT, 128), (op.DBL_INT, 32), (op.DBL_INT, 8)])
+@pytest.mark.parametrize("kind,N", [(op.ORBIT, 16), (op.ORBIT, 128), (op.DBL_INT, 32), (op.DBL_INT, 8),
+                                    (op.ORBIT, 45), (op.DBL_INT, 100)])
 def test_kkt_operator_and_preconditioner(kind, N, dtype):
     api, lib, prob, K, vec = _setup(kind, N, dtype)
     g = synth.rng("kkt-in", kind, N)
@@ -150,7 +151,7 @@ def test_preconditioned_iterations_fall_with_N():
     assert counts[-1] <= 10, counts
 
 
-@pytest.mark.parametrize("N", [4, 16, 64, 256])
+@pytest.mark.parametrize("N", [4, 16, 64, 256, 6, 100, 1000])
 def test_newton_double_integrator_closed_form(N):
     api, lib = _api()
     prob = api.Problem(lib.BK_DBL_INT, N, torch.float64, 0.0, 1.0)
@@ -183,7 +184,7 @@ def test_newton_double_integrator_forcing_term(N):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("N", [32, 128])
+@pytest.mark.parametrize("N", [32, 128, 48, 96])
 def test_newton_orbit_matches_oracle(N, dtype):
     api, lib = _api()
     rf, tf = 1.5, 20.0
