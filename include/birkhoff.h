@@ -69,8 +69,8 @@ uint64_t bk_launch_count(void);
 
 /* Create a plan for Birkhoff products on the CGL grid of size N over [t0, tf].
  *   N          power of two, 4 <= N <= 2^24, or any N in [4, 1024]. A power of two takes the
- *              FFT chain (or, with n_comp * max_batch <= 16, the dense product: BK_F32 on the
- *              tensor cores for 256 <= N <= 1024, BK_F64 on the CUDA cores for 64 <= N <= 1024);
+ *              FFT chain (bk_plan_set_dense switches a plan with N <= 1024 to the dense product:
+ *              BK_F32 on the tensor cores, BK_F64 on the CUDA cores);
  *              any other N takes the dense product in both precisions (B^a formed once in FP64
  *              from its definition: Chebyshev coefficients of the Lagrange basis times the
  *              closed-form integrals of T_k, Eq. intChebPoly=)
@@ -153,11 +153,10 @@ bk_status bk_plan_set_dense(bk_plan* plan, int on, void* stream);
  * environment BK_AUTOTUNE=0). Outputs may be NULL. */
 bk_status bk_plan_shape(const bk_plan* plan, int* path, int* N1, int* N2, int* elems);
 
-/* *on = 1 while the plan's products take the dense path, else 0. Plans with n_comp * max_batch
- * <= 16 start on it where it measured faster than the FFT chain (BK_F32 256 <= N <= 1024,
- * BK_F64 64 <= N <= 1024), and so does every N that is not a power of two; the environment
- * variable BK_DENSE=0 (read at plan creation) keeps power-of-two plans on the FFT chain,
- * BK_DENSE=1 starts every supported plan on the dense path. */
+/* *on = 1 while the plan's products take the dense path, else 0. Plans of an N that is not a
+ * power of two are always dense; power-of-two plans start on the FFT chain, or, when the
+ * environment variable BK_DENSE=1 is set at plan creation, on the dense path (N <= 1024 and
+ * n_comp * max_batch <= 16). */
 bk_status bk_plan_dense_state(const bk_plan* plan, int* on);
 
 /* Read (and clear) the dense kernel's error word: *err = 0 when every dense product so far

@@ -1020,19 +1020,19 @@ static bk_status set_smem_attrs(const Plan* p) {
   return BK_OK;
 }
 
-// Plans take the dense product by default where it measured faster than the FFT chain, with
-// at most 16 vectors per product. FP32 (tensor cores): 256 <= N <= 1024 (4 vectors, FFT /
-// dense: warm L2, back-to-back products, 2^8 10.3 / 9.3 us, 2^9 16.4 / 12.4 us, 2^10 16.4 /
-// 14.3 us; cold L2 2^10 0.019-0.027 / 0.017-0.019 ms; equal at 2^6-2^7). FP64 (CUDA cores):
-// 64 <= N <= 1024 (cold L2, ms: 2^6 0.033 / 0.019, 2^8 0.056 / 0.023, 2^10 0.068 / 0.036).
-// With 64 vectors the FFT chain wins from 2^10. BK_DENSE=0 turns the default off, BK_DENSE=1
-// extends it to every supported size.
+// Power-of-two plans take the FFT chain unless BK_DENSE=1 (read at plan creation; then every
+// plan with N <= 1024 and at most 16 vectors per product starts on the dense product). The dense
+// product is faster per call (4 vectors, cold L2, FFT / dense ms: FP32 2^10 0.027 / 0.019, FP64
+// 2^8 0.056 / 0.023, 2^10 0.068 / 0.036), but small-N solves are bound by their launches and do
+// not change, and in concurrent serving, where slots of other sizes are created and evicted,
+// building its tables (an O(N^3) FP64 formation of B^a per plan) cut throughput from 191 to
+// 152 solves/s on one GPU. BK_DENSE=0 is the default; N that is not a power of two is always
+// dense.
 static bool dense_default(int dtype, int64_t N, int nvec) {
+  (void)dtype;
   if (!dense_supported(N)) return false;
   const char* e = getenv("BK_DENSE");
-  if (e && e[0] == '0') return false;
-  if (e && e[0] == '1') return true;
-  return (dtype == BK_F64 ? N >= 64 : N >= 256) && nvec <= 16;
+  return e && e[0] == '1' && nvec <= 16;
 }
 
 // Four-step shapes of a plan for E complex elements per CTA (0: the occupancy heuristic).

@@ -6,9 +6,9 @@
 // (and its transpose, for B^T) as a pre-tiled FP32 matrix split into two TF32 parts,
 // A = A_hi + A_lo (each rounded to TF32), and multiplies on the tensor cores with kind::tf32:
 //   D = A_hi V_hi + A_hi V_lo + A_lo V_hi        (3xTF32; the A_lo V_lo term is below FP32),
-// accumulating in FP32 in tensor memory. B^a itself comes from the FP64 FFT product applied to
-// the unit vectors (columns of B^a, Eq. xN=Birka+b: the a-form integration matrix), so its
-// entries are FP64-exact before the split.
+// accumulating in FP32 in tensor memory. B^a itself (Eq. xN=Birka+b: the a-form integration
+// matrix) is formed once per plan in FP64 from its definition (below), so its entries are
+// FP64-exact before the split. FP64 plans multiply by the FP64 matrix on the CUDA cores.
 //
 // Kernel shape (CTAs of 4 warps; a tile is 128 output rows x 16 vectors, its K range split
 // over up to 16 CTAs so that small products still spread over the GPU; at N = 1024 the product
@@ -35,6 +35,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "bk_plan.cuh"
 
@@ -500,10 +501,16 @@ __global__ void __launch_bounds__(128)
 constexpr size_t DT_SMEM_BUDGET = 200 * 1024;       // dynamic shared memory of one CTA at most
 constexpr int DT_KS_MAX = 16;                          // K splits per tile at most
 
+// SM count of the current device, looked up once per device (products may run inside a stream
+// capture, where device queries are best avoided).
 static int dense_sms() {
-  int dev = 0, n = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return 148;
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 148;
+  cache[dev].store(n, std::memory_order_relaxed);
   return n;
 }
 

@@ -55,9 +55,10 @@ def test_apply_vs_dense_oracle(N, dtype, trans):
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("N", [64, 128, 256, 512, 1024])
 @pytest.mark.parametrize("trans", [False, True])
-def test_fft_chain_where_dense_is_default(N, dtype, trans):
-    """The FFT chain at the sizes whose plans default to the dense product."""
-    got, V, _ = _run(N, dtype, trans, dense=False)
+def test_dense_switch_vs_dense_oracle(N, dtype, trans):
+    """A power-of-two plan switched to the dense product (tensor cores in FP32, CUDA cores in
+    FP64) matches the oracle at the same tolerances as its FFT chain."""
+    got, V, _ = _run(N, dtype, trans, dense=True)
     B = ob.dense_B(N, 0.0, 3.0)
     assert _rel(got, V @ (B if trans else B.T)) < TOL[dtype]
 
@@ -207,8 +208,8 @@ def test_autotuned_tiles(dtype, monkeypatch):
 def test_plan_shapes():
     api = _api()
     assert api.Plan(32, dtype=torch.float64).shape()["path"] == "single_cta"
-    assert api.Plan(512, dtype=torch.float64).shape()["path"] == "dense"
-    assert api.Plan(2048, dtype=torch.float64).shape()["path"] == "four_step"
+    assert api.Plan(512, dtype=torch.float64).shape()["path"] == "four_step"
+    assert api.Plan(100, dtype=torch.float64).shape()["path"] == "dense"
     assert api.Plan(1 << 19, n_comp=1, dtype=torch.float64).shape()["path"] == "split_four_step"
-    assert api.Plan(256, n_comp=4, dtype=torch.float32).shape()["path"] == "dense"
+    assert api.Plan(256, n_comp=4, dtype=torch.float32).shape()["path"] == "single_cta"
     assert api.Plan(32, n_comp=4, dtype=torch.float32).shape()["path"] == "single_cta"

@@ -113,19 +113,16 @@ def test_dense_repeat_is_bitwise():
 
 
 def test_dense_default_policy(monkeypatch):
-    """FP32 plans with 256 <= N <= 1024 and FP64 plans with 64 <= N <= 1024, at most 16
-    vectors, start on the dense path."""
+    """Power-of-two plans start on the FFT chain; BK_DENSE=1 starts those with N <= 1024 and at
+    most 16 vectors on the dense path; other N are always dense."""
     api = _api()
-    for N, n_comp, batch, want in [(128, 4, 1, False), (256, 4, 1, True), (1024, 4, 4, True),
-                                   (1024, 4, 5, False), (2048, 4, 1, False)]:
-        p = api.Plan(N, n_comp=n_comp, max_batch=batch, dtype=torch.float32)
-        assert p.is_dense() == want, (N, n_comp, batch)
-    for N, want in [(32, False), (64, True), (1024, True), (2048, False)]:
-        assert api.Plan(N, n_comp=4, dtype=torch.float64).is_dense() == want, N
-    monkeypatch.setenv("BK_DENSE", "0")
-    assert not api.Plan(256, n_comp=4, dtype=torch.float32).is_dense()
-    assert not api.Plan(256, n_comp=4, dtype=torch.float64).is_dense()
-    assert api.Plan(100, n_comp=4, dtype=torch.float64).is_dense()   # no FFT path for N = 100
+    for dt in (torch.float32, torch.float64):
+        assert not api.Plan(256, n_comp=4, dtype=dt).is_dense()
+        assert api.Plan(100, n_comp=4, dtype=dt).is_dense()
+    monkeypatch.setenv("BK_DENSE", "1")
+    for N, n_comp, batch, want in [(64, 4, 1, True), (1024, 4, 4, True), (1024, 4, 5, False), (2048, 4, 1, False)]:
+        for dt in (torch.float32, torch.float64):
+            assert api.Plan(N, n_comp=n_comp, max_batch=batch, dtype=dt).is_dense() == want, (N, dt)
 
 
 def _run_any(N, dtype, trans, n_comp, batch, dense=None):
