@@ -385,7 +385,8 @@ def run_serve(n_requests, slots, rank=0, world=1, dist=None, loads=(0.8,), extra
         results.append(st)
     srv.close()
     st = dict(results[0])
-    st.update(closed_loop_max_rate=max_rate, slots=slots, dtype="f32ir",
+    st.update(closed_loop_max_rate=max_rate, slots=slots, cached_slots=srv.cache_slots, slots_created=srv.pool.created,
+              slots_evicted=srv.pool.evicted, dtype="f32ir",
               workload="orbit raising, N=2^k k~U{8..16}, r_f~U[1.2,2], t_f~U[10,30], Poisson arrivals")
     if len(results) > 1:
         st["load_sweep"] = [{k: r[k] for k in ("load", "offered_rate", "solves_per_s", "p50_ms", "p99_ms", "solved",

@@ -6,7 +6,7 @@ one; admitted requests run concurrently, each slot on its own CUDA stream driven
 host thread (the C calls release the GIL), so their kernels overlap on the device. A slot owns
 a bk_problem of its grid size, a Newton workspace and pinned host buffers, and is reused by
 later requests of the same N (bk_problem_set_params); idle slots of other sizes are evicted
-when memory is needed. Each request's result does not depend on what else runs: every slot has
+when memory or the slot cache is full. Each request's result does not depend on what else runs: every slot has
 its own buffers and every reduction has a fixed order.
 
 Latency = time the solution reaches host memory - arrival time.
@@ -160,7 +160,12 @@ def summarize(results, wall):
 class Server:
     """GPU server for orbit-raising requests (one bk_problem per slot, one stream per slot)."""
 
-    def __init__(self, dtype=None, max_slots=16, budget_bytes=None, newton_opts=None, restart=30):
+    def __init__(self, dtype=None, max_slots=16, budget_bytes=None, newton_opts=None, restart=30, cache_slots=None):
+        """max_slots: concurrent solves (worker threads, streams). cache_slots: solver slots kept
+        (busy + idle; default 4 x max_slots) within the memory budget, so that idle slots of
+        every size stay for later requests instead of being evicted and rebuilt (a slot's
+        problem, plans and workspace take milliseconds to build, and their frees synchronise
+        the device)."""
         import torch
         from . import _lib, api
         self.torch, self.api, self.lib = torch, api, _lib
@@ -173,7 +178,9 @@ class Server:
         self._tau = {}
         self._bytes = {}
         self._lock = threading.Lock()
-        self.pool = SlotPool(self.budget, max_slots, self._make_slot, self._free_slot, self._slot_bytes)
+        self.cache_slots = int(cache_slots if cache_slots is not None else 4 * max_slots)
+        self.pool = SlotPool(self.budget, max(self.cache_slots, max_slots), self._make_slot, self._free_slot,
+                             self._slot_bytes)
 
     def _nodes(self, N):
         if N not in self._tau:
