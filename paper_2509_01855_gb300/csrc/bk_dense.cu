@@ -11,8 +11,8 @@
 // FP64-exact before the split. FP64 plans multiply by the FP64 matrix on the CUDA cores.
 //
 // Kernel shape (CTAs of 4 warps; a tile is 128 output rows x 16 vectors, its K range split
-// over up to 16 CTAs so that small products still spread over the GPU; at N = 1024 the product
-// streams its 9.8 MB matrix, which bounds it):
+// over up to 8 CTAs so that small products still spread over the GPU; each product is one
+// latency chain of copies, MMAs and the split-K sum):
 //   - thread 0 streams the CTA's part of the A panel through up to four shared-memory stages
 //     with bulk copies (cp.async.bulk, completion on an mbarrier) and issues the MMAs
 //     (M = 128, N = 16, K = 8);
@@ -499,7 +499,8 @@ __global__ void __launch_bounds__(128)
 }
 
 constexpr size_t DT_SMEM_BUDGET = 200 * 1024;       // dynamic shared memory of one CTA at most
-constexpr int DT_KS_MAX = 16;                          // K splits per tile at most
+constexpr int DT_KS_MAX = 16;                          // K splits per tile at most (FP64 kernel)
+constexpr int DT_KS_MAX_TC = 8;                        // K splits per tile at most (tensor-core kernel)
 
 // SM count of the current device, looked up once per device (products may run inside a stream
 // capture, where device queries are best avoided).
@@ -515,7 +516,8 @@ static int dense_sms() {
 }
 
 // Launch shape of one dense product of nvec vectors: K splits KS (about two CTAs per SM over all
-// tiles, at most 16 and at most one per chunk; BK_DENSE_KSPLIT overrides), pipeline stages S
+// tiles, at most 8 and at most one per chunk; BK_DENSE_KSPLIT overrides; at N = 1024, 16 splits
+// measured 15.9 us against 14.4 us for 8), pipeline stages S
 // (up to 4, within the shared-memory budget next to the staged vectors).
 struct DenseShape {
   int KS, S;
@@ -524,10 +526,10 @@ struct DenseShape {
 static DenseShape dense_shape(const Plan* p, int nvec) {
   const int ny = (nvec + DT_N - 1) / DT_N;
   const int tiles = p->dMt * ny;
-  int KS = std::max(1, std::min(std::min(DT_KS_MAX, p->dnK), 2 * dense_sms() / std::max(1, tiles)));
+  int KS = std::max(1, std::min(std::min(DT_KS_MAX_TC, p->dnK), 2 * dense_sms() / std::max(1, tiles)));
   if (const char* e = getenv("BK_DENSE_KSPLIT")) {
     const long v = atol(e);
-    if (v >= 1) KS = (int)std::min<long>(std::min<long>(v, DT_KS_MAX), p->dnK);
+    if (v >= 1) KS = (int)std::min<long>(std::min<long>(v, DT_KS_MAX_TC), p->dnK);
   }
   const int nloc = (p->dnK + KS - 1) / KS;
   const size_t vbytes = (size_t)2 * nloc * DT_KC * DT_N * 4;

@@ -570,15 +570,13 @@ __global__ void __launch_bounds__(128) k_sw_down0(const T* __restrict__ Kn, cons
     stage_out<T>(tl.a, NX, P, L, seg0, i0, out);
     if (wantb) stage_out<T>(tl.b, NX, P, L, seg0, i0, bout);
   }
-}
-
-template <typename T>
-__global__ void k_zero_pad(T* __restrict__ v, int nblocks, int64_t P, int64_t L) {
-  const int64_t padn = P - L;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)nblocks * padn;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = i / padn;
-    v[b * P + L + (i - b * padn)] = T(0);
+  // the warp of the last block also zeroes the outputs' padding (elements L..P-1)
+  if (g == nblk0 - 1) {
+    for (int c = 0; c < NX; ++c)
+      for (int64_t k = L + lane; k < P; k += 32) {
+        out[c * P + k] = T(0);
+        if (wantb) bout[c * P + k] = T(0);
+      }
   }
 }
 
@@ -632,14 +630,6 @@ static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* ou
   }
   k_sw_down0<T, NX, DIR><<<g0, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv, out, bout);
   BK_CHECK_LAUNCH();
-  if (pr->P > pr->L) {
-    k_zero_pad<T><<<nblk(NX * (pr->P - pr->L)), 256, 0, st>>>(out, NX, pr->P, pr->L);
-    BK_CHECK_LAUNCH();
-    if (bout) {
-      k_zero_pad<T><<<nblk(NX * (pr->P - pr->L)), 256, 0, st>>>(bout, NX, pr->P, pr->L);
-      BK_CHECK_LAUNCH();
-    }
-  }
   return BK_OK;
 }
 
@@ -1171,9 +1161,9 @@ static bk_status apply_typed(Problem* pr, OpData& d, int op, const T* in, T* out
   T* t2 = (T*)d.t2;
   T* t3 = (T*)d.t3;
   if (op == BK_OP_STATE) {
+    // the product ignores t1's padding (elements L..P-1), so it is never written
     k_jvp<T, KIND><<<nblk(L), 256, 0, st>>>((const T*)d.xu, in, nullptr, P, L, t1);
     BK_CHECK_LAUNCH();
-    if (P > L) { k_zero_pad<T><<<nblk(NX * (P - L)), 256, 0, st>>>(t1, NX, P, L); BK_CHECK_LAUNCH(); }
     BK_TRY(plan_apply_n(d.plan, t1, t2, NX, false, pr->s, st));
     k_state_post<T, NX><<<nblk(NX * P), 256, 0, st>>>(in, t2, P, L, out);
     BK_CHECK_LAUNCH();
@@ -1181,7 +1171,6 @@ static bk_status apply_typed(Problem* pr, OpData& d, int op, const T* in, T* out
   }
   k_jvp<T, KIND><<<nblk(L), 256, 0, st>>>((const T*)d.xu, in, in + NX * P, P, L, t1);
   BK_CHECK_LAUNCH();
-  if (P > L) { k_zero_pad<T><<<nblk(NX * (P - L)), 256, 0, st>>>(t1, NX, P, L); BK_CHECK_LAUNCH(); }
   BK_TRY(plan_apply_n(d.plan, t1, t2, NX, false, pr->s, st));
   T* Mu = mu_out ? mu_out : t3;
   BK_TRY(plan_apply_n(d.plan, in + (NX + NU) * P, Mu, NX, true, pr->s, st));

@@ -59,21 +59,56 @@ __device__ __forceinline__ void dot_group(const T* __restrict__ V, int64_t ld, c
   }
 }
 
-// partial[b * nv + i] = sum over block b's slice of V_i . w   (i < nv), FP64
+// out = sum_b partial[b * nv + i] over nb blocks, by one block in a fixed order (thread t takes
+// b = t, t + blockDim, ..., then warp and block tree sums). All threads of the block call it.
+__device__ void block_sum_column(const double* __restrict__ partial, int nb, int nv, int i, double* __restrict__ out) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) a += __ldcg(partial + (int64_t)b * nv + i);
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) *out = t;
+  }
+  __syncthreads();
+}
+
+// After every block wrote its partials: true in the last block to arrive at *cnt, which then
+// resets the counter for the next launch (the partials are visible to it after the fences).
+__device__ bool last_block(unsigned* cnt) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+    if (last) *cnt = 0u;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// out[i] = V_i . w (i < nv), FP64 sums: each block writes partial[b * nv + i] for its slice and
+// the last block to finish adds the partials of every column in block order (one launch, the
+// result independent of scheduling).
 template <typename T>
 __global__ void __launch_bounds__(256) k_multidot(const T* __restrict__ V, int64_t ld, int nv, const T* __restrict__ w,
-                                                  int64_t n, double* __restrict__ partial) {
+                                                  int64_t n, double* __restrict__ partial, double* __restrict__ out,
+                                                  unsigned* __restrict__ cnt) {
   __shared__ double red[8][8];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * chunk;
   const int64_t hi = lo + chunk < n ? lo + chunk : n;
   for (int i0 = 0; i0 < nv; i0 += 8) {
-    const int cnt = nv - i0 < 8 ? nv - i0 : 8;
+    const int ng = nv - i0 < 8 ? nv - i0 : 8;
     const T* Vg = V + (int64_t)i0 * ld;
     double acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-    switch (cnt) {
+    switch (ng) {
       case 1: dot_group<T, 1>(Vg, ld, w, lo, hi, acc); break;
       case 2: dot_group<T, 2>(Vg, ld, w, lo, hi, acc); break;
       case 3: dot_group<T, 3>(Vg, ld, w, lo, hi, acc); break;
@@ -90,37 +125,26 @@ __global__ void __launch_bounds__(256) k_multidot(const T* __restrict__ V, int64
       if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = a;
     }
     __syncthreads();
-    if (threadIdx.x < cnt) {
+    if (threadIdx.x < ng) {
       double a = 0.0;
       for (int wp = 0; wp < (int)(blockDim.x >> 5); ++wp) a += red[wp][threadIdx.x];
       partial[(int64_t)blockIdx.x * nv + i0 + threadIdx.x] = a;
     }
     __syncthreads();
   }
+  if (last_block(cnt))
+    for (int i = 0; i < nv; ++i) block_sum_column(partial, gridDim.x, nv, i, out + i);
 }
 
-// out[i] = sum_b partial[b * nv + i]
-__global__ void k_reduce_cols(const double* __restrict__ partial, int nb, int nv, double* __restrict__ out) {
-  const int i = blockIdx.x;
-  __shared__ double red[32];
-  double a = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) a += partial[(int64_t)b * nv + i];
-  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) out[i] = t;
-  }
-}
-
-// w <- alpha * w + cscale * sum_i c[i] V_i   (c on the device, FP64). With `partial` (grid of
-// DOT_BLOCKS blocks) each block also writes the sum of squares of its slice of the new w.
+// w <- alpha * w + cscale * sum_i c[i] V_i   (c on the device, FP64). With `partial`, each block
+// also writes the sum of squares of its slice of the new w and the last block to finish writes
+// their sum, |w|^2, to *sq_out (block order, as k_multidot).
 template <typename T>
 __global__ void __launch_bounds__(256) k_multiaxpy(const T* __restrict__ V, int64_t ld, int nv,
                                                    const double* __restrict__ c, double cscale, T* __restrict__ w,
-                                                   double alpha, int64_t n, double* __restrict__ partial) {
+                                                   double alpha, int64_t n, double* __restrict__ partial,
+                                                   double* __restrict__ sq_out = nullptr,
+                                                   unsigned* __restrict__ cnt = nullptr) {
   __shared__ double cs[MAXM + 1];
   __shared__ float cs32[MAXM + 1];
   __shared__ double red[8];
@@ -179,6 +203,7 @@ __global__ void __launch_bounds__(256) k_multiaxpy(const T* __restrict__ V, int6
       for (int wp = 0; wp < (int)(blockDim.x >> 5); ++wp) t += red[wp];
       partial[blockIdx.x] = t;
     }
+    if (last_block(cnt)) block_sum_column(partial, gridDim.x, 1, 0, sq_out);
   }
 }
 
@@ -199,10 +224,9 @@ __global__ void k_scale_inv(const T* __restrict__ x, const double* __restrict__ 
 }
 
 template <typename T>
-static bk_status dots(const T* V, int64_t ld, int nv, const T* w, int64_t n, double* partial, double* out, cudaStream_t st) {
-  k_multidot<T><<<DOT_BLOCKS, 256, 0, st>>>(V, ld, nv, w, n, partial);
-  BK_CHECK_LAUNCH();
-  k_reduce_cols<<<nv, 256, 0, st>>>(partial, DOT_BLOCKS, nv, out);
+static bk_status dots(const T* V, int64_t ld, int nv, const T* w, int64_t n, double* partial, double* out,
+                      unsigned* cnt, cudaStream_t st) {
+  k_multidot<T><<<DOT_BLOCKS, 256, 0, st>>>(V, ld, nv, w, n, partial, out, cnt);
   BK_CHECK_LAUNCH();
   return BK_OK;
 }
@@ -240,10 +264,14 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
   double* h1 = dvec;
   double* h2 = dvec + (MAXM + 2);
   double* yv = dvec + 2 * (MAXM + 2);
+  // arrival counters of the one-launch reductions (k_multidot, k_multiaxpy); each launch's
+  // last block resets its counter, so one clear per solve suffices
+  unsigned* cnt = reinterpret_cast<unsigned*>(dvec + 3 * (MAXM + 2));
+  BK_TRY_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned), st));
   const int g = grid_for(n);
 
   // ||b||
-  BK_TRY(dots<T>(b, ld, 1, b, n, partial, h1, st));
+  BK_TRY(dots<T>(b, ld, 1, b, n, partial, h1, cnt, st));
   BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double), cudaMemcpyDeviceToHost, st));
   BK_TRY_CUDA(cudaStreamSynchronize(st));
   const double bnorm = sqrt(hostbuf[0]);
@@ -271,7 +299,7 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
     }
     double beta = bnorm;  // r = b on the first cycle
     if (!first) {
-      BK_TRY(dots<T>(r, ld, 1, r, n, partial, h1, st));
+      BK_TRY(dots<T>(r, ld, 1, r, n, partial, h1, cnt, st));
       BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double), cudaMemcpyDeviceToHost, st));
       BK_TRY_CUDA(cudaStreamSynchronize(st));
       beta = sqrt(hostbuf[0]);
@@ -296,10 +324,8 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
       }
       // Gram-Schmidt (DGKS): h1 = [V_0..V_j]^T w and |w|^2 (w = V_{j+1} follows V_j), then
       // w <- w - V h1 with the new |w|^2; a second pass only on cancellation.
-      BK_TRY(dots<T>(V, ld, j + 2, w, n, partial, h1, st));
-      k_multiaxpy<T><<<DOT_BLOCKS, 256, 0, st>>>(V, ld, j + 1, h1, -1.0, w, 1.0, n, partial);
-      BK_CHECK_LAUNCH();
-      k_reduce_cols<<<1, 256, 0, st>>>(partial, DOT_BLOCKS, 1, h2 + (MAXM + 1));
+      BK_TRY(dots<T>(V, ld, j + 2, w, n, partial, h1, cnt, st));
+      k_multiaxpy<T><<<DOT_BLOCKS, 256, 0, st>>>(V, ld, j + 1, h1, -1.0, w, 1.0, n, partial, h2 + (MAXM + 1), cnt + 1);
       BK_CHECK_LAUNCH();
       BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, st));
       BK_TRY_CUDA(cudaMemcpyAsync(hostbuf + (MAXM + 2), h2 + (MAXM + 1), sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -307,10 +333,8 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
       double w2 = hostbuf[MAXM + 2];
       for (int i = 0; i <= j; ++i) H[i * m + j] = hostbuf[i];
       if (w2 < 0.5 * hostbuf[j + 1]) {
-        BK_TRY(dots<T>(V, ld, j + 1, w, n, partial, h2, st));
-        k_multiaxpy<T><<<DOT_BLOCKS, 256, 0, st>>>(V, ld, j + 1, h2, -1.0, w, 1.0, n, partial);
-        BK_CHECK_LAUNCH();
-        k_reduce_cols<<<1, 256, 0, st>>>(partial, DOT_BLOCKS, 1, h2 + (MAXM + 1));
+        BK_TRY(dots<T>(V, ld, j + 1, w, n, partial, h2, cnt, st));
+        k_multiaxpy<T><<<DOT_BLOCKS, 256, 0, st>>>(V, ld, j + 1, h2, -1.0, w, 1.0, n, partial, h2 + (MAXM + 1), cnt + 1);
         BK_CHECK_LAUNCH();
         BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h2, sizeof(double) * (MAXM + 2), cudaMemcpyDeviceToHost, st));
         BK_TRY_CUDA(cudaStreamSynchronize(st));
@@ -369,7 +393,7 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
       BK_TRY(op_apply(pr, d, op, x, r, st));
       k_axpby<T><<<g, 256, 0, st>>>(b, 1.0, r, -1.0, n);
       BK_CHECK_LAUNCH();
-      BK_TRY(dots<T>(r, ld, 1, r, n, partial, h1, st));
+      BK_TRY(dots<T>(r, ld, 1, r, n, partial, h1, cnt, st));
       BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double), cudaMemcpyDeviceToHost, st));
       BK_TRY_CUDA(cudaStreamSynchronize(st));
       resid = sqrt(hostbuf[0]);
