@@ -922,19 +922,19 @@ static int fourstep_elems(int dtype, int64_t n, int nvec, int N1, int N2, int Ef
   return (int)std::min<int64_t>(E, cap);
 }
 
-// Smallest log2 N planned with the split DCT-I: 2^19 in FP64, 2^23 in FP32 (BK_SPLIT_MIN_LOG2
+// Smallest log2 N planned with the split DCT-I: 2^17 in FP64, 2^23 in FP32 (BK_SPLIT_MIN_LOG2
 // overrides both for tuning; 30 disables the split). Below them the half-size launches fill the
-// GPU poorly. Measured products, 4 components: FP64 2^20 1.21 split vs 1.35 ms unsplit, 2^18
-// 0.47 vs 0.39; FP32 (tuned tiles) 2^20 0.21 vs 0.166, 2^21 0.349 vs 0.322, 2^22 0.715 vs 0.713,
-// 2^23 1.55 vs 1.88. At 2^24 both precisions need the split (the unsplit length-2^24 FFT exceeds
-// the four-step shapes).
+// GPU poorly. Measured products (tuned tiles, 4 components, split vs unsplit ms): FP64 2^16
+// 0.158 vs 0.124, 2^17 0.179 vs 0.189, 2^18 0.316 vs 0.351, 2^19 0.570 vs 0.638, 2^20 1.09 vs 1.27; FP32 2^20 0.21 vs 0.166, 2^21 0.349
+// vs 0.322, 2^22 0.715 vs 0.713, 2^23 1.55 vs 1.88. At 2^24 both precisions need the split (the
+// unsplit length-2^24 FFT exceeds the four-step shapes).
 static int split_min_log2(int dtype) {
   const char* e = getenv("BK_SPLIT_MIN_LOG2");
   if (e) {
     const long v = atol(e);
     if (v >= 13 && v <= 30) return (int)v;
   }
-  return dtype == BK_F64 ? 19 : 23;
+  return dtype == BK_F64 ? 17 : 23;
 }
 
 // Shapes of one four-step layout (tables untouched, so a built plan can be re-shaped); Eforce

@@ -80,11 +80,19 @@ __device__ void node_factors(const Tc* x, const Tc* u, Tc h, Tc* K, Tc* Nm) {
 #pragma unroll
     for (int r = c + 1; r < NX; ++r)
       if (fabs((Tc)A[r * NX + c]) > best) { best = fabs((Tc)A[r * NX + c]); piv = r; }
-    if (piv != c) {
+    // row swap by selects over the candidate rows: every index stays a compile-time constant,
+    // so A and Inv live in registers (indexing by the run-time pivot put them in local memory)
+#pragma unroll
+    for (int r = c + 1; r < NX; ++r) {
+      const bool sw = r == piv;
 #pragma unroll
       for (int q = 0; q < NX; ++q) {
-        Tc t = A[c * NX + q]; A[c * NX + q] = A[piv * NX + q]; A[piv * NX + q] = t;
-        t = Inv[c * NX + q]; Inv[c * NX + q] = Inv[piv * NX + q]; Inv[piv * NX + q] = t;
+        const Tc a = A[c * NX + q], b = A[r * NX + q];
+        A[c * NX + q] = sw ? b : a;
+        A[r * NX + q] = sw ? a : b;
+        const Tc ia = Inv[c * NX + q], ib = Inv[r * NX + q];
+        Inv[c * NX + q] = sw ? ib : ia;
+        Inv[r * NX + q] = sw ? ia : ib;
       }
     }
     const Tc ip = Tc(1) / A[c * NX + c];
@@ -415,8 +423,16 @@ template <typename T, int NX> struct SweepTiles {
   T a[NX * ROWS], b[NX * ROWS], w[ROWS];
 };
 
+// Nonzero test on the bit pattern (integer pipe; +0 and -0 count as zero): the sweeps use it to
+// skip work whose inputs are all zero without spending FP64 instructions on the test.
+__device__ __forceinline__ bool nonzero(double x) { return (__double_as_longlong(x) << 1) != 0; }
+__device__ __forceinline__ bool nonzero(float x) { return (__float_as_int(x) << 1) != 0; }
+
 // Up, level 0 (one warp per block of 32 segments, 4 warps per CTA): each lane runs its segment
-// from a zero state (the segment's offset), then the warp scans the block.
+// from a zero state (the segment's offset), then the warp scans the block. A chunk whose inputs
+// and states are zero on every lane leaves the states zero and is skipped, and a block whose
+// offsets are all zero has zero scan values: the terminal Schur columns' right-hand sides are
+// unit vectors at the last node, so their up passes do almost no FP64 work.
 template <typename T, int NX, int DIR>
 __global__ void __launch_bounds__(128) k_sw_up0(const T* __restrict__ Kn, const T* __restrict__ Nn,
                                                 const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
@@ -440,6 +456,17 @@ __global__ void __launch_bounds__(128) k_sw_up0(const T* __restrict__ Kn, const 
     if (G) stage_in<T>(G, P, NX, L, seg0, i0, tl.b);
     stage_in<T>(w, P, 1, L, seg0, i0, tl.w);
     __syncwarp();
+    bool act = false;
+#pragma unroll
+    for (int m = 0; m < NX; ++m) {
+      act |= nonzero(st[m]);
+#pragma unroll
+      for (int jj = 0; jj < CH; ++jj) {
+        act |= nonzero(tl.a[(m * 32 + lane) * TS + jj]);
+        if (G) act |= nonzero(tl.b[(m * 32 + lane) * TS + jj]);
+      }
+    }
+    if (!__any_sync(0xffffffffu, act)) continue;
 #pragma unroll
     for (int jj = 0; jj < CH; ++jj) {
       const int nd = DIR == 0 ? jj : CH - 1 - jj;
@@ -456,9 +483,13 @@ __global__ void __launch_bounds__(128) k_sw_up0(const T* __restrict__ Kn, const 
     }
   }
   T e[NX];
+  bool any = false;
 #pragma unroll
-  for (int m = 0; m < NX; ++m) e[m] = st[m];
-  warp_scan<T, NX, DIR>(lv.m[0], (int64_t)nblk * 32 * NX * NX, g, e);
+  for (int m = 0; m < NX; ++m) {
+    e[m] = st[m];
+    any |= nonzero(st[m]);
+  }
+  if (__any_sync(0xffffffffu, any)) warp_scan<T, NX, DIR>(lv.m[0], (int64_t)nblk * 32 * NX * NX, g, e);
 #pragma unroll
   for (int m = 0; m < NX; ++m) lv.e[0][il32(seg, m, NX)] = e[m];
   if (lv.nlev > 1 && lane == (DIR == 0 ? 31 : 0)) {
@@ -478,9 +509,13 @@ __global__ void __launch_bounds__(128) k_sw_upL(Levels<T> lv, int l) {
   const int64_t i = (int64_t)b * 32 + lane;
   const T* o = lv.o[l];
   T e[NX];
+  bool any = false;
 #pragma unroll
-  for (int m = 0; m < NX; ++m) e[m] = i < n ? o[il32(i, m, NX)] : T(0);
-  warp_scan<T, NX, DIR>(lv.m[l], (int64_t)nblk * 32 * NX * NX, b, e);
+  for (int m = 0; m < NX; ++m) {
+    e[m] = i < n ? o[il32(i, m, NX)] : T(0);
+    any |= nonzero(e[m]);
+  }
+  if (__any_sync(0xffffffffu, any)) warp_scan<T, NX, DIR>(lv.m[l], (int64_t)nblk * 32 * NX * NX, b, e);
   T* el = lv.e[l];
 #pragma unroll
   for (int m = 0; m < NX; ++m) el[il32(i, m, NX)] = e[m];
