@@ -47,6 +47,8 @@
 
 namespace bk {
 
+#ifndef BK_TRANSFORM_KERNEL_UNIT  // one definition of the library's globals, in the main unit
+// (bk_birkhoff_f64.cu and bk_birkhoff_f32.cu include this file for the transform kernels only)
 static thread_local std::string g_last_error = "no error";
 static std::atomic<unsigned long long> g_launches{0};
 // When set (by the creating thread), dmalloc adds every allocation's size to it: plans and
@@ -84,6 +86,8 @@ bk_status dmalloc(void** p, size_t bytes) {
 void dfree(void* p) {
   if (p) cudaFree(p);
 }
+
+#endif  // BK_TRANSFORM_KERNEL_UNIT
 
 // ---------------------------------------------------------------------------------------------
 // Table construction (device, FP64 sincospi; FP32 tables are rounded copies)
@@ -142,6 +146,7 @@ __global__ void k_rk_table(T* rk, int64_t n) {
     rk[k] = k == 0 ? T(0) : (T)(1.0 / (4.0 * (double)k));
 }
 
+#ifndef BK_TRANSFORM_KERNEL_UNIT
 __global__ void k_grid_tables(double* t_nodes, int64_t N, double t0, double s) {
   // tau_j = -cos(j pi / N) = sin(pi (2j - N) / (2N)) (Eq. CGLpts), t_j = t0 + s (tau_j + 1)
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= N;
@@ -152,6 +157,7 @@ __global__ void k_grid_tables(double* t_nodes, int64_t N, double t0, double s) {
     t_nodes[j] = t0 + s * (tau + 1.0);
   }
 }
+#endif  // BK_TRANSFORM_KERNEL_UNIT
 
 // ---------------------------------------------------------------------------------------------
 // Element accessors of the transform inputs
@@ -237,7 +243,14 @@ __device__ __forceinline__ typename V2<T>::t load_z(const T* __restrict__ src, i
 //             H_0 = u_0, H_k = e^{i theta k} (u_k - i u_{M-k}) / 2 (theta = pi / (2M) = pi / N,
 //             u_M = 0), Z_k = (H_k + conj H_{M/2-k}) + i e^{2 pi i k / M} (H_k - conj H_{M/2-k});
 //             the inverse FFT runs as conj(FFT(conj Z)).
-enum { PM_FULL = 0, PM_PAIR = 1, PM_DCT3 = 2 };
+// Two-level split (largest plans): the even half's DCT-I of length M+1 of a is split once more,
+// so R(x)_{4m} is the DCT-I of length Q+1 (Q = N/4) of aa_i = a_i + a_{M-i}, R(x)_{4m+2} the
+// DCT-III of length Q of u'_0 = a_0 - a_M, u'_i = 2 (a_i - a_{M-i}), and R(x)_{2m+1} the
+// DCT-III of x's pair differences as above: FFTs of N/4 + N/8 + N/4 points instead of
+// N/2 + N/4. The pair sums a are formed on the fly from x in the loads:
+//   PM_PAIR2 : z_j of the length-Q DCT-I of aa (n = Q)
+//   PM_DCT3A : conj Z_k (k < n = Q/2) of the DCT-III of u' (as PM_DCT3, on a)
+enum { PM_FULL = 0, PM_PAIR = 1, PM_DCT3 = 2, PM_PAIR2 = 3, PM_DCT3A = 4 };
 
 template <typename T, int K>
 __device__ __forceinline__ T pair_sum(const T* __restrict__ src, int i, int Ns) {
@@ -280,6 +293,46 @@ __device__ __forceinline__ typename V2<T>::t load_z_dct3(const T* __restrict__ s
   const C E = mk2<T>(Hk.x + Hm.x, Hk.y - Hm.y);
   const C D = mk2<T>(Hk.x - Hm.x, Hk.y + Hm.y);
   const C w = eo[k];  // omega_M^k; e^{2 pi i k / M} = conj w
+  const C O = mk2<T>(D.x * w.x + D.y * w.y, D.y * w.x - D.x * w.y);
+  return mk2<T>(E.x - O.y, -(E.y + O.x));
+}
+
+// z_j of the length-Q DCT-I of aa (n = Q, x of length 4Q + 1): aa_i = a_i + a_{2Q-i}.
+template <typename T, int K>
+__device__ __forceinline__ typename V2<T>::t load_z_pair2(const T* __restrict__ src, int j, int n) {
+  const int Nf = 4 * n, M = 2 * n;
+  const int m1 = 2 * j, m2 = 2 * j + 1;
+  const int i1 = m1 <= n ? m1 : 2 * n - m1;
+  const int i2 = m2 <= n ? m2 : 2 * n - m2;
+  return mk2<T>(pair_sum<T, K>(src, i1, Nf) + pair_sum<T, K>(src, M - i1, Nf),
+                pair_sum<T, K>(src, i2, Nf) + pair_sum<T, K>(src, M - i2, Nf));
+}
+
+// H_k of the DCT-III of length Q of u' (pair differences of a, x of length 4Q + 1): as dct3_H on
+// a with theta = pi / (2Q), (cos, sin)(pi i / (2Q)) = tpost[2i]; a carries the W^{-1} scaling of
+// IN_WINV already, so the factor c is 1.
+template <typename T, int K>
+__device__ __forceinline__ typename V2<T>::t dct3_H_pairs(const T* __restrict__ src, int i, int Q,
+                                                         const typename V2<T>::t* __restrict__ tpost) {
+  const int M = 2 * Q, Nf = 4 * Q;
+  if (i == 0) return mk2<T>(pair_sum<T, K>(src, 0, Nf) - pair_sum<T, K>(src, M, Nf), T(0));
+  const T a = pair_sum<T, K>(src, i, Nf) - pair_sum<T, K>(src, M - i, Nf);
+  const T b = pair_sum<T, K>(src, Q - i, Nf) - pair_sum<T, K>(src, Q + i, Nf);
+  const typename V2<T>::t cs = tpost[2 * i];
+  return mk2<T>(a * cs.x + b * cs.y, a * cs.y - b * cs.x);
+}
+
+template <typename T, int K>
+__device__ __forceinline__ typename V2<T>::t load_z_dct3a(const T* __restrict__ src, int k, int n,
+                                                         const typename V2<T>::t* __restrict__ tpost,
+                                                         const typename V2<T>::t* __restrict__ eo) {
+  typedef typename V2<T>::t C;
+  const int Q = 2 * n;
+  const C Hk = dct3_H_pairs<T, K>(src, k, Q, tpost);
+  const C Hm = dct3_H_pairs<T, K>(src, n - k, Q, tpost);
+  const C E = mk2<T>(Hk.x + Hm.x, Hk.y - Hm.y);
+  const C D = mk2<T>(Hk.x - Hm.x, Hk.y + Hm.y);
+  const C w = eo[2 * k];  // the table is built for the DCT-III of length 2Q
   const C O = mk2<T>(D.x * w.x + D.y * w.y, D.y * w.x - D.x * w.y);
   return mk2<T>(E.x - O.y, -(E.y + O.x));
 }
@@ -414,7 +467,7 @@ __device__ __forceinline__ void passA_body(
   const T sc = K == ST_FWD ? T(1) : invN;
   // DC partials: consumed after IN_WINV (the transposed stage) and ST_FWD (the forward output);
   // in split plans the DC value is the even half's (the DCT-III has none)
-  constexpr bool DC = (K == IN_WINV || K == ST_FWD) && MODE != PM_DCT3;
+  constexpr bool DC = (K == IN_WINV || K == ST_FWD) && MODE != PM_DCT3 && MODE != PM_DCT3A;
   T dc = T(0);
   const int total = NB * N1;
   // independent element loads in flight per thread before the shared-memory stores
@@ -429,6 +482,8 @@ __device__ __forceinline__ void passA_body(
         const int j = ((idx >> log2NB) << log2N2) + c0 + b;
         if (MODE == PM_FULL) z[u] = load_z<T, K>(x, j, N, sc, Y0, tb);
         else if (MODE == PM_PAIR) z[u] = load_z_pair<T, K>(x, j, N, tb);
+        else if (MODE == PM_PAIR2) z[u] = load_z_pair2<T, K>(x, j, N);
+        else if (MODE == PM_DCT3A) z[u] = load_z_dct3a<T, K>(x, j, N, tpost, eo);
         else z[u] = load_z_dct3<T, K>(x, j, N, tpost, eo, tb);
       }
     }
@@ -508,6 +563,23 @@ __global__ void __launch_bounds__(MaxThr<T>::v, 2)
     passA_body<T, K, PM_DCT3>(blockIdx.x - gE, gridDim.x - gE, BK_PASSA_ARGS(O), invN, tb, BK_PASSA_TAIL(O), tpost, eo);
 }
 
+// Pass A of the three parts of a two-level split DCT-I in one launch: CTAs [0, g1) the DCT-I of
+// aa, [g1, g1 + g2) the DCT-III of a's pair differences, the rest the DCT-III of x's.
+template <typename T, int K>
+__global__ void __launch_bounds__(MaxThr<T>::v, 2)
+    k_passA_split3(int g1, int g2, BK_PASSA_PARAMS(E), BK_PASSA_PARAMS(D), BK_PASSA_PARAMS(O), T invN,
+                   StencilTab<T> tb, const typename V2<T>::t* __restrict__ tpost,
+                   const typename V2<T>::t* __restrict__ eo) {
+  const int b = blockIdx.x;
+  if (b < g1)
+    passA_body<T, K, PM_PAIR2>(b, g1, BK_PASSA_ARGS(E), invN, tb, BK_PASSA_TAIL(E), tpost, eo);
+  else if (b < g1 + g2)
+    passA_body<T, K, PM_DCT3A>(b - g1, g2, BK_PASSA_ARGS(D), invN, tb, BK_PASSA_TAIL(D), tpost, eo);
+  else
+    passA_body<T, K, PM_DCT3>(b - g1 - g2, gridDim.x - g1 - g2, BK_PASSA_ARGS(O), invN, tb, BK_PASSA_TAIL(O), tpost,
+                              eo);
+}
+
 // Second-DCT input as its own elementwise pass (planned applies): x_m of kind K (ST_FWD with
 // scale sc, or ST_TRN) for every m <= N, written to G, with per-CTA partial sums of W_m x_m
 // (the DC value R(x)_0 of the DCT, W = 1 at the ends, 2 inside) when `partial` is given. Fusing
@@ -566,7 +638,8 @@ __device__ __forceinline__ void ep_write(T* __restrict__ dst, int k, T yk, int N
 
 // Pass-B modes: PB_PAIRS, row pairs {p, N1 - p} and the real-FFT split of a DCT-I (outputs at
 // ostride k of a transform of parent size Npar; (cos, sin)(pi k / n) read as tpost[tps k]);
-// PB_ROWS, plain rows of the DCT-III's inverse FFT (outputs unpacked to the odd indices).
+// PB_ROWS, plain rows of the DCT-III's inverse FFT (outputs unpacked to the odd indices of the
+// sub-transform, ostride (2m+1) of the whole one).
 enum { PB_PAIRS = 0, PB_ROWS = 1 };
 
 template <typename T, int E, int MODE>
@@ -646,7 +719,7 @@ __device__ __forceinline__ void passB_body(
       for (int t = 0; t < 2; ++t) {
         const int64_t r = 2 * pz + t;
         const int64_t m = r < N ? 2 * r : 2 * (2 * (int64_t)N - 1 - r) + 1;
-        ep_write<T, E>(out, (int)(2 * m + 1), t == 0 ? R.x : -R.y, Npar, s, Y0, invN);
+        ep_write<T, E>(out, (int)(ostride * (2 * m + 1)), t == 0 ? R.x : -R.y, Npar, s, Y0, invN);
       }
     }
     return;
@@ -738,6 +811,25 @@ __global__ void __launch_bounds__(MaxThr<T>::v, 2)
                               PO, stwO, tpost, s, invN, 1, 1, Npar);
 }
 
+// Pass B of a two-level split: the DCT-I of aa (outputs 4k), the DCT-III of a's pair
+// differences (outputs 4m + 2) and the DCT-III of x's (outputs 2m + 1).
+template <typename T, int E>
+__global__ void __launch_bounds__(MaxThr<T>::v, 2)
+    k_passB_split3(int h1, int h2, BK_PASSB_PARAMS(E), BK_PASSB_PARAMS(D), BK_PASSB_PARAMS(O), T* __restrict__ dst,
+                   int64_t dst_stride, int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial,
+                   const typename V2<T>::t* __restrict__ tpost, T s, T invN, int Npar) {
+  const int b = blockIdx.x;
+  if (b < h1)
+    passB_body<T, E, PB_PAIRS>(b, AinE, dst, dst_stride, pitch_zero_to, partial, n_partial, NE, N1E, N2E, log2N2E, PE,
+                               stwE, tpost, s, invN, 4, 4, Npar);
+  else if (b < h1 + h2)
+    passB_body<T, E, PB_ROWS>(b - h1, AinD, dst, dst_stride, 0, partial, n_partial, ND, N1D, N2D, log2N2D, PD, stwD,
+                              tpost, s, invN, 2, 2, Npar);
+  else
+    passB_body<T, E, PB_ROWS>(b - h1 - h2, AinO, dst, dst_stride, 0, partial, n_partial, NO, N1O, N2O, log2N2O, PO,
+                              stwO, tpost, s, invN, 1, 1, Npar);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Plan creation / destruction and the apply entry points
 // ---------------------------------------------------------------------------------------------
@@ -805,6 +897,7 @@ static bk_status build_tables(Plan* p, cudaStream_t st) {
     BK_TRY(build_fs_tables<T>(p->fs, st));
     if (p->split) {
       BK_TRY(build_fs_tables<T>(p->fso, st));
+      if (p->split == 2) BK_TRY(build_fs_tables<T>(p->fse, st));
       const int64_t M = N / 2;
       BK_TRY(dmalloc(&p->eo, sizeof(C) * (M / 2)));
       // exp(+2 pi i k / M) = conj(omega_M^k)
@@ -821,6 +914,7 @@ static bk_status build_tables(Plan* p, cudaStream_t st) {
   return BK_OK;
 }
 
+#ifndef BK_TRANSFORM_KERNEL_UNIT
 __global__ void k_unit_last(double* e, int64_t L, int64_t pitch) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < pitch; i += (int64_t)gridDim.x * blockDim.x)
     e[i] = (i == L - 1) ? 1.0 : 0.0;
@@ -860,6 +954,7 @@ static bk_status compute_weights(Plan* p, cudaStream_t st) {
   if (tmp) plan_destroy(tmp);
   return r;
 }
+#endif  // BK_TRANSFORM_KERNEL_UNIT
 
 // Largest N run by the single-CTA kernel (one CTA per vector): 128 in FP64, whose single CTA
 // runs on one SM's FP64 pipe (4 components, cold L2, B / four-step ms: 2^8 0.062 / 0.056,
@@ -922,12 +1017,26 @@ static int fourstep_elems(int dtype, int64_t n, int nvec, int N1, int N2, int Ef
   return (int)std::min<int64_t>(E, cap);
 }
 
+// Smallest log2 N planned with the two-level split: 2^18 in FP64, 2^24 in FP32
+// (BK_SPLIT2_MIN_LOG2 overrides both; 30 disables). Measured products (4 components, two-level
+// vs one-level ms): FP64 2^17 0.181 vs 0.178, 2^18 0.272 vs 0.313, 2^20 0.978 vs 1.084, 2^22
+// 3.88 vs 4.38, 2^24 17.6 vs 19.3; FP32 2^23 1.557 vs 1.556, 2^24 4.02 vs 4.17.
+static int split2_min_log2(int dtype) {
+  const char* e = getenv("BK_SPLIT2_MIN_LOG2");
+  if (e) {
+    const long v = atol(e);
+    if (v >= 13 && v <= 30) return (int)v;
+  }
+  return dtype == BK_F64 ? 18 : 24;
+}
+
 // Smallest log2 N planned with the split DCT-I: 2^17 in FP64, 2^23 in FP32 (BK_SPLIT_MIN_LOG2
 // overrides both for tuning; 30 disables the split). Below them the half-size launches fill the
 // GPU poorly. Measured products (tuned tiles, 4 components, split vs unsplit ms): FP64 2^16
-// 0.158 vs 0.124, 2^17 0.179 vs 0.189, 2^18 0.316 vs 0.351, 2^19 0.570 vs 0.638, 2^20 1.09 vs 1.27; FP32 2^20 0.21 vs 0.166, 2^21 0.349
-// vs 0.322, 2^22 0.715 vs 0.713, 2^23 1.55 vs 1.88. At 2^24 both precisions need the split (the
-// unsplit length-2^24 FFT exceeds the four-step shapes).
+// 0.158 vs 0.124, 2^17 0.179 vs 0.189, 2^18 0.316 vs 0.351, 2^19 0.570 vs 0.638, 2^20 1.09
+// vs 1.27; FP32 2^20 0.21 vs 0.166, 2^21 0.349 vs 0.322, 2^22 0.715 vs 0.713, 2^23 1.55 vs
+// 1.88. At 2^24 both precisions need the split (the unsplit length-2^24 FFT exceeds the
+// four-step shapes).
 static int split_min_log2(int dtype) {
   const char* e = getenv("BK_SPLIT_MIN_LOG2");
   if (e) {
@@ -996,7 +1105,7 @@ static bk_status smem_attr(K* fn, int cap) {
 }
 
 template <typename T>
-static bk_status set_smem_attrs(const Plan* p) {
+bk_status set_smem_attrs(const Plan* p) {
   if (p->small) {
     const int cap = (int)smem_small<T>(p->dtype == BK_F64 ? 4096 : 8192);
     BK_TRY(smem_attr(k_birkhoff_small<T, false>, cap));
@@ -1005,8 +1114,10 @@ static bk_status set_smem_attrs(const Plan* p) {
     const int cap = (int)FOURSTEP_SMEM_BUDGET;
     BK_TRY(smem_attr(k_passA<T, IN_PLAIN>, cap));
     BK_TRY(smem_attr(k_passA<T, IN_WINV>, cap));
-    BK_TRY(smem_attr(k_passA<T, ST_FWD>, cap));
-    BK_TRY(smem_attr(k_passA<T, ST_TRN>, cap));
+    if constexpr (sizeof(T) == 8) {
+      BK_TRY(smem_attr(k_passA<T, ST_FWD>, cap));
+      BK_TRY(smem_attr(k_passA<T, ST_TRN>, cap));
+    }
     BK_TRY(smem_attr(k_passB<T, EP_STORE>, cap));
     BK_TRY(smem_attr(k_passB<T, EP_STORE_TRN>, cap));
     BK_TRY(smem_attr(k_passB<T, EP_FWD_OUT>, cap));
@@ -1017,9 +1128,21 @@ static bk_status set_smem_attrs(const Plan* p) {
     BK_TRY(smem_attr(k_passB_split<T, EP_STORE_TRN>, cap));
     BK_TRY(smem_attr(k_passB_split<T, EP_FWD_OUT>, cap));
     BK_TRY(smem_attr(k_passB_split<T, EP_TRN_OUT>, cap));
+    BK_TRY(smem_attr(k_passA_split3<T, IN_PLAIN>, cap));
+    BK_TRY(smem_attr(k_passA_split3<T, IN_WINV>, cap));
+    BK_TRY(smem_attr(k_passB_split3<T, EP_STORE>, cap));
+    BK_TRY(smem_attr(k_passB_split3<T, EP_STORE_TRN>, cap));
+    BK_TRY(smem_attr(k_passB_split3<T, EP_FWD_OUT>, cap));
+    BK_TRY(smem_attr(k_passB_split3<T, EP_TRN_OUT>, cap));
   }
   return BK_OK;
 }
+#ifndef BK_TRANSFORM_KERNEL_UNIT
+// The instances of set_smem_attrs and apply_impl (and with them every transform kernel) are
+// compiled in bk_birkhoff_f64.cu and bk_birkhoff_f32.cu, in parallel with this unit.
+extern template bk_status set_smem_attrs<double>(const Plan* p);
+extern template bk_status set_smem_attrs<float>(const Plan* p);
+#endif
 
 // Power-of-two plans take the FFT chain unless BK_DENSE=1 (read at plan creation; then every
 // plan with N <= 1024 and at most 16 vectors per product starts on the dense product). The dense
@@ -1039,6 +1162,12 @@ static bool dense_default(int dtype, int64_t N, int nvec) {
 // Four-step shapes of a plan for E complex elements per CTA (0: the occupancy heuristic).
 static bk_status fourstep_shapes(Plan* p, int E) {
   const int nvec = p->n_comp * p->max_batch;
+  if (p->split == 2) {
+    BK_TRY(configure_fourstep(p->fs, p->N / 4, p->dtype, nvec, E));
+    BK_TRY(configure_fourstep(p->fse, p->N / 8, p->dtype, nvec, E));
+    BK_TRY(configure_fourstep(p->fso, p->N / 4, p->dtype, nvec, E));
+    return BK_OK;
+  }
   if (p->split) {
     BK_TRY(configure_fourstep(p->fs, p->N / 2, p->dtype, nvec, E));
     BK_TRY(configure_fourstep(p->fso, p->N / 4, p->dtype, nvec, E));
@@ -1124,6 +1253,7 @@ static bk_status autotune_tiles(Plan* p, cudaStream_t st) {
   return fourstep_shapes(p, best);
 }
 
+#ifndef BK_TRANSFORM_KERNEL_UNIT
 bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtype, double t0,
                       double tf, int64_t pitch, cudaStream_t st) {
   *out = nullptr;
@@ -1170,7 +1300,7 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
       if (p->thrS > (dtype == BK_F64 ? 256 : 512)) p->thrS = dtype == BK_F64 ? 256 : 512;
     } else {
       // split DCT-I from 2^split_min_log2() on: fs the length-N/2 FFT, fso the length-N/4 one
-      p->split = ilog2(N) >= split_min_log2(dtype);
+      p->split = ilog2(N) >= split2_min_log2(dtype) ? 2 : (ilog2(N) >= split_min_log2(dtype) ? 1 : 0);
       if ((st_ = fourstep_shapes(p, 0)) != BK_OK) break;
       const int64_t nvec = (int64_t)n_comp * max_batch;
       const size_t csz = 2 * dtype_size(dtype);
@@ -1218,6 +1348,7 @@ void plan_destroy(Plan* p) {
   dfree(p->stwS);
   free_fs(p->fs);
   free_fs(p->fso);
+  free_fs(p->fse);
   dfree(p->eo);
   dfree(p->tpost);
   dfree(p->rk);
@@ -1234,6 +1365,7 @@ void plan_destroy(Plan* p) {
   dfree(p->dcnt);
   delete p;
 }
+#endif  // BK_TRANSFORM_KERNEL_UNIT
 
 // One split DCT-I of the vectors at src (input kind K) into dst with epilogue E: pass A of the
 // even half (pair sums, length-N/2 FFT on fs) and of the odd half (pair differences, length-N/4
@@ -1266,8 +1398,54 @@ static bk_status split_dct(const Plan* p, const T* src, int64_t sstride, T* dst,
   return BK_OK;
 }
 
+// One two-level split DCT-I (see PM_PAIR2): pass A of its three parts in one launch, then pass B
+// of the three in one launch writing outputs 4k, 4m + 2 and 2m + 1.
+template <typename T, int K, int E>
+static bk_status split_dct3(const Plan* p, const T* src, int64_t sstride, T* dst, int64_t dstride, int64_t zero_to,
+                            int nvec, void* scrA, T* partA, const T* partB, int npartB, T s, T invN, StencilTab<T> tb,
+                            cudaStream_t st) {
+  typedef typename V2<T>::t C;
+  const int N = (int)p->N, Q = N / 4;
+  const FourStep& e = p->fs;   // length Q: DCT-I of aa
+  const FourStep& d = p->fse;  // length Q/2: DCT-III of a's pair differences
+  const FourStep& o = p->fso;  // length Q: DCT-III of x's pair differences
+  C* Ae = (C*)scrA;
+  C* Ad = Ae + (int64_t)nvec * Q;
+  C* Ao = Ad + (int64_t)nvec * (Q / 2);
+  const C* tp = (const C*)p->tpost;
+  const int g1 = e.N2 / e.NB, g2 = d.N2 / d.NB, g3 = o.N2 / o.NB;
+  const int thrA = std::max(e.thrA, std::max(d.thrA, o.thrA));
+  const size_t smA = std::max(e.smemA, std::max(d.smemA, o.smemA));
+  k_passA_split3<T, K><<<dim3(g1 + g2 + g3, nvec), thrA, smA, st>>>(
+      g1, g2, src, sstride, Ae, partA, Q, e.N1, ilog2(e.N1), e.N2, e.NB, e.bsA, (const C*)e.stw1, (const C*)e.twN,
+      (const C*)e.twLo, (const C*)e.twHi, e.tw_h,
+      src, sstride, Ad, nullptr, Q / 2, d.N1, ilog2(d.N1), d.N2, d.NB, d.bsA, (const C*)d.stw1, (const C*)d.twN,
+      (const C*)d.twLo, (const C*)d.twHi, d.tw_h,
+      src, sstride, Ao, nullptr, Q, o.N1, ilog2(o.N1), o.N2, o.NB, o.bsA, (const C*)o.stw1, (const C*)o.twN,
+      (const C*)o.twLo, (const C*)o.twHi, o.tw_h, invN, tb, tp, (const C*)p->eo);
+  BK_CHECK_LAUNCH();
+  const int h1 = e.N1 / 2 / e.P, h2 = d.N1 / 2 / d.P, h3 = o.N1 / 2 / o.P;
+  const int thrB = std::max(e.thrB, std::max(d.thrB, o.thrB));
+  const size_t smB = std::max(e.smemB, std::max(d.smemB, o.smemB));
+  k_passB_split3<T, E><<<dim3(h1 + h2 + h3, nvec), thrB, smB, st>>>(
+      h1, h2, Ae, Q, e.N1, e.N2, ilog2(e.N2), e.P, (const C*)e.stw2, Ad, Q / 2, d.N1, d.N2, ilog2(d.N2), d.P,
+      (const C*)d.stw2, Ao, Q, o.N1, o.N2, ilog2(o.N2), o.P, (const C*)o.stw2, dst, dstride, zero_to, partB, npartB, tp,
+      s, invN, N);
+  BK_CHECK_LAUNCH();
+  return BK_OK;
+}
+
+template <typename T, int K, int E>
+static bk_status split_any(const Plan* p, const T* src, int64_t sstride, T* dst, int64_t dstride, int64_t zero_to,
+                           int nvec, void* scrA, T* partA, const T* partB, int npartB, T s, T invN, StencilTab<T> tb,
+                           cudaStream_t st) {
+  if (p->split == 2)
+    return split_dct3<T, K, E>(p, src, sstride, dst, dstride, zero_to, nvec, scrA, partA, partB, npartB, s, invN, tb, st);
+  return split_dct<T, K, E>(p, src, sstride, dst, dstride, zero_to, nvec, scrA, partA, partB, npartB, s, invN, tb, st);
+}
+
 template <typename T>
-static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool trans, double s_scale,
+bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool trans, double s_scale,
                             cudaStream_t st, void* scrA, void* scrY, void* part1, void* part2, void* scrG) {
   typedef typename V2<T>::t C;
   const int N = (int)p->N;
@@ -1293,15 +1471,15 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
     const int nPA = p->fs.nPartA;
     const dim3 gS(nPA, nvec);
     if (!trans) {
-      BK_TRY((split_dct<T, IN_PLAIN, EP_STORE>(p, v, p->pitch, Ystage, Ls, 0, nvec, scrA, nullptr, nullptr, 0, s, invN, tb, st)));
+      BK_TRY((split_any<T, IN_PLAIN, EP_STORE>(p, v, p->pitch, Ystage, Ls, 0, nvec, scrA, nullptr, nullptr, 0, s, invN, tb, st)));
       k_stencil<T, ST_FWD><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, pa2);
       BK_CHECK_LAUNCH();
-      BK_TRY((split_dct<T, IN_PLAIN, EP_FWD_OUT>(p, Gst, Ls, out, p->pitch, p->pitch, nvec, scrA, nullptr, pa2, nPA, s, invN, tb, st)));
+      BK_TRY((split_any<T, IN_PLAIN, EP_FWD_OUT>(p, Gst, Ls, out, p->pitch, p->pitch, nvec, scrA, nullptr, pa2, nPA, s, invN, tb, st)));
     } else {
-      BK_TRY((split_dct<T, IN_WINV, EP_STORE_TRN>(p, v, p->pitch, Ystage, Ls, 0, nvec, scrA, pa1, pa1, nPA, s, invN, tb, st)));
+      BK_TRY((split_any<T, IN_WINV, EP_STORE_TRN>(p, v, p->pitch, Ystage, Ls, 0, nvec, scrA, pa1, pa1, nPA, s, invN, tb, st)));
       k_stencil<T, ST_TRN><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, nullptr);
       BK_CHECK_LAUNCH();
-      BK_TRY((split_dct<T, IN_PLAIN, EP_TRN_OUT>(p, Gst, Ls, out, p->pitch, p->pitch, nvec, scrA, nullptr, nullptr, 0, s, invN, tb, st)));
+      BK_TRY((split_any<T, IN_PLAIN, EP_TRN_OUT>(p, Gst, Ls, out, p->pitch, p->pitch, nvec, scrA, nullptr, nullptr, 0, s, invN, tb, st)));
     }
     return BK_OK;
   }
@@ -1331,8 +1509,12 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
       k_stencil<T, ST_FWD><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, pa2);
       BK_CHECK_LAUNCH();
       k_passA<T, IN_PLAIN><<<gA, f.thrA, f.smemA, st>>>(Gst, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
-    } else {
+    } else if constexpr (sizeof(T) == 8) {
+      // fused stencil loads: only the allocation-free FP64 entry point has no stencil buffer
       k_passA<T, ST_FWD><<<gA, f.thrA, f.smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
+    } else {
+      set_error("internal: FP32 products need the stencil buffer");
+      return BK_ERR_ARG;
     }
     BK_CHECK_LAUNCH();
     k_passB<T, EP_FWD_OUT><<<gB, f.thrB, f.smemB, st>>>(A, out, p->pitch, p->pitch, pa2, nPA, N, N1, N2, log2N2, P, stw2, tp, s, invN, 1, 1, N);
@@ -1347,8 +1529,11 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
       k_stencil<T, ST_TRN><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, nullptr);
       BK_CHECK_LAUNCH();
       k_passA<T, IN_PLAIN><<<gA, f.thrA, f.smemA, st>>>(Gst, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
-    } else {
+    } else if constexpr (sizeof(T) == 8) {
       k_passA<T, ST_TRN><<<gA, f.thrA, f.smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
+    } else {
+      set_error("internal: FP32 products need the stencil buffer");
+      return BK_ERR_ARG;
     }
     BK_CHECK_LAUNCH();
     k_passB<T, EP_TRN_OUT><<<gB, f.thrB, f.smemB, st>>>(A, out, p->pitch, p->pitch, nullptr, 0, N, N1, N2, log2N2, P, stw2, tp, s, invN, 1, 1, N);
@@ -1356,6 +1541,14 @@ static bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool tr
   }
   return BK_OK;
 }
+
+#ifndef BK_TRANSFORM_KERNEL_UNIT
+extern template bk_status apply_impl<double>(const Plan* p, const double* v, double* out, int nvec, bool trans,
+                                             double s_scale, cudaStream_t st, void* scrA, void* scrY, void* part1,
+                                             void* part2, void* scrG);
+extern template bk_status apply_impl<float>(const Plan* p, const float* v, float* out, int nvec, bool trans,
+                                            double s_scale, cudaStream_t st, void* scrA, void* scrY, void* part1,
+                                            void* part2, void* scrG);
 
 bk_status plan_apply_n(const Plan* p, const void* v, void* out, int nvec, bool trans, double s,
                        cudaStream_t st) {
@@ -1373,7 +1566,10 @@ bk_status plan_apply(const Plan* p, const void* v, void* out, int batch, bool tr
   return plan_apply_n(p, v, out, batch * p->n_comp, trans, p->s, st);
 }
 
+#endif  // BK_TRANSFORM_KERNEL_UNIT
 }  // namespace bk
+
+#ifndef BK_TRANSFORM_KERNEL_UNIT
 
 namespace bk {
 
@@ -1585,3 +1781,5 @@ bk_status bk_plan_dense_check(const bk_plan* plan, int* err) {
 }
 
 }  // extern "C"
+
+#endif  // BK_TRANSFORM_KERNEL_UNIT

@@ -34,11 +34,13 @@ struct Plan {
   int thrS = 256;             // threads of the single-CTA kernel
   void* tw = nullptr;         // omega_N^i, i < N (single-CTA plans; the N < 16 direct DFT)
   void* stwS = nullptr;       // stage twiddle table of the length-N FFT (single-CTA plans)
-  // Four-step plans. Unsplit: fs is the length-N FFT of the DCT-I. Split: each DCT-I of length
-  // N+1 is the DCT-I of length N/2+1 of its pair sums (even outputs; fs, length N/2) and the
-  // DCT-III of length N/2 of its pair differences (odd outputs; fso, length N/4).
-  FourStep fs, fso;
-  bool split = false;
+  // Four-step plans. Unsplit: fs is the length-N FFT of the DCT-I. Split (split = 1): each DCT-I
+  // of length N+1 is the DCT-I of length N/2+1 of its pair sums (even outputs; fs, length N/2)
+  // and the DCT-III of length N/2 of its pair differences (odd outputs; fso, length N/4).
+  // Two-level split (split = 2): the even half split once more, fs the length-N/4 FFT of the
+  // DCT-I of length N/4+1, fse the length-N/8 FFT of the DCT-III of length N/4, fso as above.
+  FourStep fs, fso, fse;
+  int split = 0;
   void* eo = nullptr;         // split: exp(2 pi i k / (N/2)), k < N/4 (DCT-III pre-processing)
   void* tpost = nullptr;      // (cos, sin)(pi k / N), k = 0..N/2 (working type)
   void* rk = nullptr;         // 1 / (4k), k = 0..N+1 (working type; rk[0] = 0)
