@@ -21,6 +21,16 @@ the same for every N (the mesh independence of Table tab:m).
 
 Vector layout (component-major, matching the library): z = [X_0..X_{n_x-1}, U_0..U_{n_u-1}],
 y = [lambda_0..lambda_{n_x-1}, nu], each X_m, U_q, lambda_m a length-L block.
+
+Free final time (ORBIT_MT, Eq. ot). The time scale s = (t_f - t_0)/2 is one more unknown, stored
+after nu: vec = [X, U, lambda, nu, s]. The cost is J = t_f - t_0 = 2 s, so the Lagrangian
+2 s + lambda . c + nu . e has the extra gradient row
+
+    g_s = dL/ds = 2 - lambda . (B^a (x) I) f(X, U),
+
+and the KKT matrix gains one row and column: d g_X / ds = -J_x^T (B^aT lambda),
+d g_U / ds = -J_u^T (B^aT lambda), d c / ds = -(B^a (x) I) f, zero against nu and s. The
+weighted norm adds |g_s|^2.
 """
 import numpy as np
 
@@ -43,7 +53,8 @@ class DenseKKT:
         nx, nu, L = prob.n_x, prob.n_u, self.L
         self.nz = (nx + nu) * L
         self.nc = nx * L
-        self.n = self.nz + self.nc + prob.n_e
+        self.free = bool(getattr(prob, 'free_time', False))
+        self.n = self.nz + self.nc + prob.n_e + (1 if self.free else 0)
 
     # ---- packing --------------------------------------------------------------------------
     def split(self, vec):
@@ -51,16 +62,35 @@ class DenseKKT:
         X = vec[:p.n_x * L].reshape(p.n_x, L)
         U = vec[p.n_x * L:self.nz].reshape(p.n_u, L)
         lam = vec[self.nz:self.nz + self.nc].reshape(p.n_x, L)
-        nu = vec[self.nz + self.nc:]
+        nu = vec[self.nz + self.nc:self.nz + self.nc + p.n_e]
         return X, U, lam, nu
 
-    def pack(self, X, U, lam, nu):
-        return np.concatenate([X.ravel(), U.ravel(), lam.ravel(), np.asarray(nu, float).ravel()])
+    def s_of(self, vec):
+        """Time scale at vec: the last entry for a free final time, else (t_f - t_0)/2."""
+        return float(vec[-1]) if self.free else self.s
+
+    def pack(self, X, U, lam, nu, s=None):
+        parts = [X.ravel(), U.ravel(), lam.ravel(), np.asarray(nu, float).ravel()]
+        if self.free:
+            parts.append([self.s if s is None else float(s)])
+        return np.concatenate(parts)
+
+    def border(self, vec):
+        """Free final time: the KKT matrix's s column, [d g_X/ds ; d g_U/ds ; d c/ds ; 0 ; 0]."""
+        p, B = self.prob, self.Ba
+        X, U, lam, nu = self.split(vec)
+        Jx, Ju = p.jac(X, U)
+        muh = (B.T @ lam.T).T                      # B^aT lambda, unscaled
+        col = np.zeros(self.n)
+        col[:p.n_x * self.L] = -np.einsum('kmp,mk->pk', Jx, muh).ravel()
+        col[p.n_x * self.L:self.nz] = -np.einsum('kmq,mk->qk', Ju, muh).ravel()
+        col[self.nz:self.nz + self.nc] = -(B @ p.f(X, U).T).T.ravel()
+        return col
 
     # ---- residual ---------------------------------------------------------------------------
     def residual(self, vec):
         """F = [grad_z L ; c ; e] at vec = (X, U, lambda, nu)."""
-        p, s, B = self.prob, self.s, self.Ba
+        p, s, B = self.prob, self.s_of(vec), self.Ba
         X, U, lam, nu = self.split(vec)
         f = p.f(X, U)
         c = X - p.x0[:, None] - s * (B @ f.T).T
@@ -71,11 +101,14 @@ class DenseKKT:
         gU = s * self.w[None, :] * p.cost_grad_u(U) - s * np.einsum('kmq,mk->qk', Ju, mu)
         for r, (i, _) in enumerate(zip(p.term_idx, p.term_val)):
             gX[i, -1] += nu[r]
-        return np.concatenate([gX.ravel(), gU.ravel(), c.ravel(), e])
+        tail = [e]
+        if self.free:
+            tail.append([2.0 - float(np.sum(lam * (B @ f.T).T))])
+        return np.concatenate([gX.ravel(), gU.ravel(), c.ravel()] + tail)
 
     # ---- Jacobian of F (the KKT matrix) ---------------------------------------------------
     def matrix(self, vec):
-        p, s, B, L = self.prob, self.s, self.Ba, self.L
+        p, s, B, L = self.prob, self.s_of(vec), self.Ba, self.L
         nx, nu_ = p.n_x, p.n_u
         X, U, lam, nu = self.split(vec)
         Jx, Ju = p.jac(X, U)
@@ -102,9 +135,14 @@ class DenseKKT:
             Ge[r, i * L + L - 1] = 1.0
         A = np.vstack([G, Ge])
         K = np.zeros((self.n, self.n))
+        ny = self.nc + p.n_e
         K[:self.nz, :self.nz] = H
-        K[:self.nz, self.nz:] = A.T
-        K[self.nz:, :self.nz] = A
+        K[:self.nz, self.nz:self.nz + ny] = A.T
+        K[self.nz:self.nz + ny, :self.nz] = A
+        if self.free:
+            col = self.border(vec)
+            K[:, -1] = col
+            K[-1, :] = col
         return K
 
     def apply(self, vec, dvec):
@@ -118,7 +156,7 @@ class DenseKKT:
         gX = F[:p.n_x * L].reshape(p.n_x, L)
         gU = F[p.n_x * L:self.nz].reshape(p.n_u, L)
         c = F[self.nz:self.nz + self.nc].reshape(p.n_x, L)
-        e = F[self.nz + self.nc:]
+        e = F[self.nz + self.nc:]                  # e, and g_s for a free final time
         return float(np.sqrt((w * c * c).sum() + (gX * gX / w).sum() + (gU * gU / w).sum()
                              + (e * e).sum()))
 
@@ -137,12 +175,18 @@ class DenseKKT:
             d = np.linalg.solve(self.matrix(vec), -F)
             alpha = 1.0
             f0 = norms[-1]
+            accepted = False
             for _ in range(max_backtrack):
                 trial = vec + alpha * d
-                Ft = self.residual(trial)
-                if self.weighted_norm(Ft) <= (1.0 - armijo * alpha) * f0:
-                    break
+                # a free final time must stay positive: a trial with s <= 0 is rejected
+                if self.s_of(trial) > 0.0:
+                    Ft = self.residual(trial)
+                    if self.weighted_norm(Ft) <= (1.0 - armijo * alpha) * f0:
+                        accepted = True
+                        break
                 alpha *= 0.5
+            if not accepted:
+                break                                   # line search failed: stop here
             vec, F = trial, Ft
             alphas.append(alpha)
             norms.append(self.weighted_norm(F))
@@ -164,9 +208,15 @@ class DenseKKT:
         system of the Newton step the same substitution is made in the constraint block and
         the Lagrangian Hessian is replaced by its control-cost part, which is SPD. The
         preconditioner applied by the library is K-tilde^{-1}.
+
+        Free final time (ORBIT_MT, no running cost): Huu is the per-node bound
+        a |mu_v,k| + 1e-3 s w_k of the angle's Lagrangian curvature a (mu_vr sin u + mu_vt cos u),
+        mu = s B^aT lambda (the two agree where the angle is stationary; the floor keeps Huu
+        positive where mu_v vanishes), and K-tilde is bordered by the KKT matrix's own s row and
+        column (zero diagonal), so that the preconditioner eliminates s exactly.
         """
         from .birkhoff import dense_Btilde
-        p, s, L = self.prob, self.s, self.L
+        p, s, L = self.prob, self.s_of(vec), self.L
         nx, nu_ = p.n_x, p.n_u
         X, U, lam, nu = self.split(vec)
         Jx, Ju = p.jac(X, U)
@@ -181,13 +231,17 @@ class DenseKKT:
                 P[m * L:(m + 1) * L, q * L:(q + 1) * L] = blk
             for q in range(nu_):
                 Pu[m * L:(m + 1) * L, q * L:(q + 1) * L] = -s * Bt * Ju[:, m, q][None, :]
-        Huu = np.diag(np.tile(s * self.w * p.cost_hess_uu(), nu_))
+        if self.free:
+            mu = s * (self.Ba.T @ lam.T).T
+            Huu = np.diag(p.a * np.hypot(mu[2], mu[3]) + 1e-3 * s * self.w)
+        else:
+            Huu = np.diag(np.tile(s * self.w * p.cost_hess_uu(), nu_))
         E = np.zeros((p.n_e, self.nc))
         for r, i in enumerate(p.term_idx):
             E[r, i * L + L - 1] = 1.0
         nz, nc, ne = self.nz, self.nc, p.n_e
         Kt = np.zeros((self.n, self.n))
-        xs, us, ls, es = slice(0, nc), slice(nc, nz), slice(nz, nz + nc), slice(nz + nc, self.n)
+        xs, us, ls, es = slice(0, nc), slice(nc, nz), slice(nz, nz + nc), slice(nz + nc, nz + nc + ne)
         Kt[xs, ls] = P.T
         Kt[xs, es] = E.T
         Kt[us, us] = Huu
@@ -195,7 +249,33 @@ class DenseKKT:
         Kt[ls, xs] = P
         Kt[ls, us] = Pu
         Kt[es, xs] = E
+        if self.free:
+            col = self.border(vec)
+            Kt[:, -1] = col
+            Kt[-1, :] = col
         return Kt
+
+    def min_time_seed(self, K_me, vec_me):
+        """Initial point of a free-final-time orbit solve from a solved minimum-energy transfer.
+
+        K_me is the DenseKKT of the ORBIT problem (same N, a, r_f) at a fixed t_f and vec_me its
+        solution. The states and multipliers are kept, the steering angle is the direction of
+        the thrust vector, u = atan2(u_r, u_theta) (thrust a (sin u, cos u)), s is K_me's, and
+        lambda, nu are scaled by kappa = 2 / (lambda . (B^a (x) I) f) so that g_s = 0. Reading:
+        the paper does not say how its solve is started; the minimum-energy solution has the
+        same stationarity structure (thrust along B^aT lambda), so only the scale of the
+        multipliers must change.
+        """
+        assert self.free and K_me.N == self.N
+        X, U, lam, nu = K_me.split(vec_me)
+        Um = np.arctan2(U[0], U[1])[None, :]
+        vec = self.pack(X.copy(), Um, lam.copy(), nu.copy(), K_me.s)
+        S = 2.0 - self.residual(vec)[-1]           # lambda . (B^a (x) I) f at the seed
+        if not S > 0.0:
+            raise ValueError("minimum-energy multipliers give a non-positive time gradient")
+        kappa = 2.0 / S
+        vec[self.nz:self.n - 1] *= kappa
+        return vec
 
     def state_matrix(self, vec):
         """G_x = I - s (B^a (x) I) J_x: the state block of the constraint Jacobian."""

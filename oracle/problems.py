@@ -22,10 +22,18 @@ ORBIT     x = (r, theta, v_r, v_theta), u = (u_r, u_theta) thrust acceleration v
 BILINEAR  scalar x' = u * x with no cost and no terminal condition. Linearised at (X, U) its
           state Jacobian is diag(U), so setting U = d gives the Newton system
           [I - s B diag(d)] dX = x^a b of Eq. Newton-ivp (the paper's linear-solve experiment).
+ORBIT_MT  the minimum-time orbit transfer of Eq. ot: the same state and dynamics with the
+          fixed-magnitude thrust a (sin u, cos u), u the steering angle (n_u = 1), cost
+          J = T = t_f - t_0 (the final time is free: s = T / 2 is one more unknown),
+          x(t0) = (1, 0, 0, 1), terminal r = r_f, v_r = 0, v_theta = 1/sqrt(r_f), theta free.
+          Eq. ot orders the state (r, v_r, v_theta, theta); the library keeps (r, theta, v_r,
+          v_theta) for both orbit kinds. Reading: the paper does not give a; params = (a, r_f),
+          with a = 0.1 and r_f = 6 (the paper's target) as the worked case. The time tf given
+          to the problem is only the initial value of the free final time.
 """
 import numpy as np
 
-DBL_INT, ORBIT, BILINEAR = 0, 1, 2
+DBL_INT, ORBIT, BILINEAR, ORBIT_MT = 0, 1, 2, 3
 
 
 class Problem:
@@ -36,6 +44,7 @@ class Problem:
         self.t0 = float(t0)
         self.tf = float(tf)
         self.params = tuple(float(p) for p in params)
+        self.free_time = kind == ORBIT_MT
         if kind == DBL_INT:
             self.n_x, self.n_u = 2, 1
             self.x0 = np.array([0.0, 0.0])
@@ -46,6 +55,14 @@ class Problem:
             a, rf = self.params
             self.a, self.rf = a, rf
             self.n_x, self.n_u = 4, 2
+            self.x0 = np.array([1.0, 0.0, 0.0, 1.0])
+            self.term_idx = [0, 2, 3]
+            self.term_val = [rf, 0.0, 1.0 / np.sqrt(rf)]
+            self.has_cost = True
+        elif kind == ORBIT_MT:
+            a, rf = self.params
+            self.a, self.rf = a, rf
+            self.n_x, self.n_u = 4, 1
             self.x0 = np.array([1.0, 0.0, 0.0, 1.0])
             self.term_idx = [0, 2, 3]
             self.term_val = [rf, 0.0, 1.0 / np.sqrt(rf)]
@@ -68,6 +85,11 @@ class Problem:
             r, th, vr, vt = X
             return np.stack([vr, vt / r, vt * vt / r - 1.0 / (r * r) + U[0],
                              -vr * vt / r + U[1]])
+        if self.kind == ORBIT_MT:
+            r, th, vr, vt = X
+            u = U[0]
+            return np.stack([vr, vt / r, vt * vt / r - 1.0 / (r * r) + self.a * np.sin(u),
+                             -vr * vt / r + self.a * np.cos(u)])
         return (U[0] * X[0])[None, :]
 
     def jac(self, X, U):
@@ -78,7 +100,7 @@ class Problem:
         if self.kind == DBL_INT:
             Jx[:, 0, 1] = 1.0
             Ju[:, 1, 0] = 1.0
-        elif self.kind == ORBIT:
+        elif self.kind in (ORBIT, ORBIT_MT):
             r, th, vr, vt = X
             Jx[:, 0, 2] = 1.0
             Jx[:, 1, 0] = -vt / r**2
@@ -88,8 +110,12 @@ class Problem:
             Jx[:, 3, 0] = vr * vt / r**2
             Jx[:, 3, 2] = -vt / r
             Jx[:, 3, 3] = -vr / r
-            Ju[:, 2, 0] = 1.0
-            Ju[:, 3, 1] = 1.0
+            if self.kind == ORBIT:
+                Ju[:, 2, 0] = 1.0
+                Ju[:, 3, 1] = 1.0
+            else:
+                Ju[:, 2, 0] = self.a * np.cos(U[0])
+                Ju[:, 3, 0] = -self.a * np.sin(U[0])
         else:
             Jx[:, 0, 0] = U[0]
             Ju[:, 0, 0] = X[0]
@@ -102,7 +128,7 @@ class Problem:
         H = np.zeros((L, n, n))
         if self.kind == DBL_INT:
             return H
-        if self.kind == ORBIT:
+        if self.kind in (ORBIT, ORBIT_MT):
             r, th, vr, vt = X
             m_th, m_vr, m_vt = mu[1], mu[2], mu[3]
             R, VR, VT = 0, 2, 3
@@ -121,18 +147,25 @@ class Problem:
             # symmetrise the off-diagonal entries written above the diagonal
             for (i, j) in [(R, VT), (R, VR), (VR, VT)]:
                 H[:, j, i] = H[:, i, j]
+            if self.kind == ORBIT_MT:
+                # a sin u and a cos u: second derivatives -a sin u, -a cos u in the angle
+                u = U[0]
+                H[:, 4, 4] = -self.a * (m_vr * np.sin(u) + m_vt * np.cos(u))
             return H
         # BILINEAR: f = u x
         H[:, 0, 1] = mu[0]
         H[:, 1, 0] = mu[0]
         return H
 
-    # ---- running cost F(x, u) = |u|^2 / 2 -------------------------------------------------
+    # ---- running cost F(x, u) = |u|^2 / 2 (none for ORBIT_MT, whose cost is T) ----------------
+    def running_cost(self):
+        return self.has_cost and not self.free_time
+
     def cost_grad_u(self, U):
-        return U.copy() if self.has_cost else np.zeros_like(U)
+        return U.copy() if self.running_cost() else np.zeros_like(U)
 
     def cost_hess_uu(self):
-        return 1.0 if self.has_cost else 0.0
+        return 1.0 if self.running_cost() else 0.0
 
     def terminal_residual(self, X):
         return np.array([X[i, -1] - v for i, v in zip(self.term_idx, self.term_val)])
