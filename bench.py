@@ -340,6 +340,42 @@ def dense_crossover(lgs=range(4, 11), reps=9):
     return rows
 
 
+def min_time_table(lgs=range(10, 21), a=0.05, rf=6.0, t_seed=24.0):
+    """The minimum-time orbit transfer of Eq. ot (free final time, thrust a = 0.05, r 1 -> 6) for
+    N = 2^10..2^20: a minimum-energy solve at t_f = 24 seeds it (bk_min_time_seed), then the
+    Newton-Krylov solve of the free-time KKT system. Per N: Newton iterations, KKT solves and
+    Krylov iterations (Table tab:m's columns, with this library's outer loop), the final time T and
+    the solve's device time (CUDA events, FP64; the 2^20 row also with FP32 inner solves)."""
+    import torch
+    from paper_2509_01855_gb300 import _lib, api, synth
+    rows = {}
+    cases = [(lg, torch.float64) for lg in lgs] + [(max(lgs), torch.float32)]
+    for lg, dt in cases:
+        N = 1 << lg
+        me = api.Problem(_lib.BK_ORBIT, N, torch.float64, 0.0, t_seed, (a, rf))
+        t, _ = api.Plan(N, t0=0.0, tf=t_seed).grid()
+        X, U = synth.orbit_guess(t.numpy(), rf, t_seed)
+        zme = me.pack(X, U)
+        ime = api.newton_solve(me, zme, tol=1e-11, krylov_rtol=1e-12, max_iter=60)
+        mt = api.Problem(_lib.BK_ORBIT_MT, N, dt, 0.0, t_seed, (a, rf))
+        z = mt.zeros(dtype=torch.float64)
+        api.min_time_seed(mt, me, zme, z)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        info = api.newton_solve(mt, z, tol=1e-10, max_iter=60, raise_on_fail=False)
+        e1.record()
+        torch.cuda.synchronize()
+        key = str(lg) + ("" if dt == torch.float64 else "_f32inner")
+        rows[key] = {"seed_newton_its": ime["iterations"], "newton_its": info["iterations"],
+                     "kkt_solves": info["kkt_solves"], "krylov_its": info["krylov_iterations"],
+                     "converged": bool(info["converged"]), "residual": info["residual"],
+                     "T": 2.0 * z[mt.s_index].item(), "ms": round(e0.elapsed_time(e1), 3)}
+        me.close()
+        mt.close()
+    return rows
+
+
 def cpu_apply_baseline(N):
     """The oracle's FastBV chain (SciPy DCT-I, as it stands) on 4 FP64 components at N, on the
     host cores; one product, so the default run stays short."""
@@ -520,6 +556,7 @@ def main():
     if args.sweep:
         line["apply_sweep"] = apply_sweep()
         line["dense_crossover"] = dense_crossover()
+        line["min_time_table"] = min_time_table()
     if args.workload.startswith("newton") and args.serve_requests >= 0:
         line["serve"] = run_serve(args.serve_requests or 512, args.serve_slots, rank, world, dist)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

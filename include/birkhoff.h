@@ -175,9 +175,16 @@ typedef enum {
                        v_theta' = -v_r v_theta/r + u_theta (dynamics of Eq. ot);
                        x(t0) = (1,0,0,1); r(tf) = r_f, v_r(tf) = 0, v_theta(tf) = r_f^-1/2;
                        F = |u|^2/2.  params = {a_nominal, r_f}                              */
-  BK_BILINEAR = 2   /* scalar x' = u x, no cost, no terminal condition; linearised at (X, U)
+  BK_BILINEAR = 2,  /* scalar x' = u x, no cost, no terminal condition; linearised at (X, U)
                        its state Jacobian is diag(U): the Newton system [I - B diag(d)] dX =
                        x^a b of Eq. Newton-ivp with d = U. params = {x^a} (default 1)          */
+  BK_ORBIT_MT = 3   /* minimum-time orbit transfer of Eq. ot: the BK_ORBIT state and dynamics
+                       with the fixed-magnitude thrust a (sin u, cos u), u the steering angle
+                       (n_u = 1); cost J = t_f - t_0 with t_f free: the time scale
+                       s = (t_f - t_0)/2 is an unknown kept in the KKT vector's tail slot after
+                       nu (index (2 n_x + n_u) pitch + n_e), and the tf given at creation only
+                       sets the problem's initial s. params = {a, r_f}, a > 0 (the paper does
+                       not give a; its target is r_f = 6). Start from bk_min_time_seed.        */
 } bk_kind;
 
 /* Operators addressed by kkt_apply / precond_apply / krylov_solve. */
@@ -316,9 +323,23 @@ bk_status newton_solve(bk_problem* prob, double* z_inout, const bk_newton_opts* 
                        bk_newton_info* info, void* workspace, void* stream);
 
 /* KKT residual F at z (FP64 device KKT vector) into F_out (same layout); if wnorm is not NULL
- * the weighted norm ||F||_W is returned in it (host; synchronous in that case). */
+ * the weighted norm ||F||_W is returned in it (host; synchronous in that case).
+ * BK_ORBIT_MT: F_out's tail slot after e holds the time gradient g_s = 2 - lambda . (B^a (x) I) f,
+ * and ||F||_W adds |g_s|^2; the problem's time scale is read from z (synchronous). bk_linearize
+ * reads it from z_lin the same way. */
 bk_status bk_kkt_residual(bk_problem* prob, const double* z, double* F_out, double* wnorm,
                           void* stream);
+
+/* Initial point of a minimum-time solve (BK_ORBIT_MT) from a solved minimum-energy transfer
+ * (BK_ORBIT, same N, a, r_f and t0; any tf):
+ *   z_me   device FP64 KKT vector of `me` (its solution)
+ *   z_mt   device FP64 KKT vector of `mt`, written: X, lambda and nu of z_me, the steering angle
+ *          u = atan2(u_r, u_theta) of the thrust vector, s = me's time scale; then lambda and nu
+ *          scaled by 2 / (lambda . (B^a (x) I) f), which zeroes the time gradient.
+ * Synchronous. BK_ERR_ARG if the problems do not match or lambda . (B^a f) <= 0. The paper does
+ * not say how its solve is started; this is the library's reading. */
+bk_status bk_min_time_seed(bk_problem* mt, const bk_problem* me, const double* z_me, double* z_mt,
+                           void* stream);
 
 #ifdef __cplusplus
 }

@@ -28,7 +28,7 @@ ORBIT_MT  the minimum-time orbit transfer of Eq. ot: the same state and dynamics
           x(t0) = (1, 0, 0, 1), terminal r = r_f, v_r = 0, v_theta = 1/sqrt(r_f), theta free.
           Eq. ot orders the state (r, v_r, v_theta, theta); the library keeps (r, theta, v_r,
           v_theta) for both orbit kinds. Reading: the paper does not give a; params = (a, r_f),
-          with a = 0.1 and r_f = 6 (the paper's target) as the worked case. The time tf given
+          with a = 0.05 and r_f = 6 (the paper's target) as the worked case. The time tf given
           to the problem is only the initial value of the free final time.
 """
 import numpy as np

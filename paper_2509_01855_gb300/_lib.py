@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbirkhoff.so")
 
 BK_F64, BK_F32 = 0, 1
-BK_DBL_INT, BK_ORBIT, BK_BILINEAR = 0, 1, 2
+BK_DBL_INT, BK_ORBIT, BK_BILINEAR, BK_ORBIT_MT = 0, 1, 2, 3
 BK_OP_STATE, BK_OP_KKT = 0, 1
 STATUS = {0: "BK_OK", 1: "BK_ERR_ARG", 2: "BK_ERR_CUDA", 3: "BK_ERR_OOM",
           4: "BK_ERR_NOT_CONVERGED", 5: "BK_ERR_TIMEOUT", 6: "BK_ERR_INFEASIBLE",
@@ -25,7 +25,7 @@ EXPORTS = ["bk_last_error", "bk_version", "bk_launch_count", "bk_plan_create", "
            "bk_plan_dense_state", "bk_plan_dense_check", "bk_plan_shape", "bk_problem_create",
            "bk_problem_destroy", "bk_problem_set_params", "bk_problem_device_bytes", "bk_problem_info", "bk_linearize", "kkt_apply",
            "precond_apply", "bk_krylov_workspace_bytes", "krylov_solve",
-           "bk_newton_workspace_bytes", "newton_solve", "bk_kkt_residual"]
+           "bk_newton_workspace_bytes", "newton_solve", "bk_kkt_residual", "bk_min_time_seed"]
 
 
 class BirkhoffError(RuntimeError):
@@ -105,6 +105,7 @@ def lib():
         "newton_solve": (c_int, [vp, vp, ctypes.POINTER(NewtonOpts), ctypes.POINTER(NewtonInfo),
                                  vp, vp]),
         "bk_kkt_residual": (c_int, [vp, vp, vp, ctypes.POINTER(dbl), vp]),
+        "bk_min_time_seed": (c_int, [vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):

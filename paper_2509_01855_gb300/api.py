@@ -178,7 +178,7 @@ class Problem:
         nu_ = z[(2 * nx + nu) * P:(2 * nx + nu) * P + self.n_e]
         return X, U, lam, nu_
 
-    def pack(self, X, U, lam=None, nu=None, dtype=torch.float64, device="cuda"):
+    def pack(self, X, U, lam=None, nu=None, dtype=torch.float64, device="cuda", s=None):
         z = torch.zeros(self.kkt_len, dtype=dtype, device=device)
         Xv, Uv, lv, nv = self.split(z)
         Xv.copy_(torch.as_tensor(X))
@@ -187,7 +187,19 @@ class Problem:
             lv.copy_(torch.as_tensor(lam))
         if nu is not None and self.n_e:
             nv.copy_(torch.as_tensor(nu))
+        if self.free_time:
+            z[self.s_index] = 0.5 * (self.tf - self.t0) if s is None else float(s)
         return z
+
+    @property
+    def free_time(self):
+        """BK_ORBIT_MT: the time scale s = (t_f - t_0)/2 is an unknown kept in the KKT vector."""
+        return self.kind == L.BK_ORBIT_MT
+
+    @property
+    def s_index(self):
+        """Index of s in a KKT vector (the tail slot after nu) for a free final time."""
+        return (2 * self.n_x + self.n_u) * self.pitch + self.n_e
 
     def close(self):
         if self._h:
@@ -199,6 +211,16 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def min_time_seed(mt, me, z_me, z_mt, stream=None):
+    """Seed the minimum-time problem `mt` (BK_ORBIT_MT) from the solved minimum-energy transfer
+    z_me of `me` (BK_ORBIT, same N): writes z_mt (synchronous)."""
+    for z, p in ((z_me, me), (z_mt, mt)):
+        if z.dtype != torch.float64 or not z.is_cuda or z.numel() < p.kkt_len:
+            raise ValueError("z_me and z_mt must be CUDA float64 KKT vectors of their problems")
+    L.check(L.lib().bk_min_time_seed(mt.handle, me.handle, L.ptr(z_me), L.ptr(z_mt), L.stream_ptr(stream)))
+    return z_mt
 
 
 def kkt_apply(prob, op, x, out, stream=None):

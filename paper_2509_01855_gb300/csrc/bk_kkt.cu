@@ -54,6 +54,8 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 }
 
 static inline int nblk(int64_t n, int t = 256) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 65535)); }
+// Grid of the free-final-time reductions (grid-stride; partials fit the 2048-entry scratch).
+constexpr int FT_NB = 608;
 
 // ---------------------------------------------------------------------------------------------
 // Linearisation kernels (FP64 arithmetic, results stored in T)
@@ -61,9 +63,9 @@ static inline int nblk(int64_t n, int t = 256) { return (int)std::max<int64_t>(1
 // Node factors in the compute type Tc: FP64 for FP64 problems; FP32 for FP32 problems, whose
 // preconditioner works to FP32 accuracy anyway (the level products stay FP64).
 template <typename Tc, int KIND, int NX>
-__device__ void node_factors(const Tc* x, const Tc* u, Tc h, Tc* K, Tc* Nm) {
+__device__ void node_factors(const Tc* x, const Tc* u, Tc h, Tc* K, Tc* Nm, Tc pa) {
   Tc Jx[NXM * NXM], Ju[NXM * NUM];
-  Dyn<KIND>::template jac<Tc>(x, u, Jx, Ju);
+  Dyn<KIND>::template jac<Tc>(x, u, Jx, Ju, pa);
   // A = I - h J; K = A^{-1} by Gauss-Jordan with partial pivoting
   Tc A[NX * NX], Inv[NX * NX];
 #pragma unroll
@@ -122,7 +124,7 @@ __device__ void node_factors(const Tc* x, const Tc* u, Tc h, Tc* K, Tc* Nm) {
 
 template <typename T, int KIND, int NX, int NU>
 __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, const double* __restrict__ w,
-                            double s, T* __restrict__ Kn, T* __restrict__ Nn, T* __restrict__ xu) {
+                            double s, T* __restrict__ Kn, T* __restrict__ Nn, T* __restrict__ xu, double pa) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
     T x[NXM], u[NUM];
 #pragma unroll
@@ -130,7 +132,7 @@ __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, 
 #pragma unroll
     for (int q = 0; q < NU; ++q) u[q] = (T)z[(NX + q) * P + k];
     T K[NX * NX], Nm[NX * NX];
-    node_factors<T, KIND, NX>(x, u, (T)(0.5 * s * w[k]), K, Nm);
+    node_factors<T, KIND, NX>(x, u, (T)(0.5 * s * w[k]), K, Nm, (T)pa);
 #pragma unroll
     for (int c = 0; c < NX * NX; ++c) {
       Kn[il_index<Seg<T>::v>(k, c, NX * NX)] = (T)K[c];
@@ -671,20 +673,24 @@ static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* ou
 // ---------------------------------------------------------------------------------------------
 // KKT / state operator kernels (per node, Jacobians and Hessian recomputed from (x, u, mu))
 // ---------------------------------------------------------------------------------------------
+// t = J dz per node; with a free final time (ds != null) t += (ds / s) f, so that the product
+// s B^a t adds the column d c / ds = -B^a f times ds.
 template <typename T, int KIND>
 __global__ void k_jvp(const T* __restrict__ xu, const T* __restrict__ dX, const T* __restrict__ dU, int64_t P,
-                      int64_t L, T* __restrict__ t) {
+                      int64_t L, T* __restrict__ t, T pa, const T* __restrict__ ds, T inv_s) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  const T dss = ds ? ds[0] * inv_s : T(0);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
-    T x[NXM], u[NUM], Jx[NXM * NXM], Ju[NXM * NUM];
+    T x[NXM], u[NUM], Jx[NXM * NXM], Ju[NXM * NUM], fx[NXM];
 #pragma unroll
     for (int m = 0; m < NX; ++m) x[m] = xu[m * P + k];
 #pragma unroll
     for (int q = 0; q < NU; ++q) u[q] = xu[(NX + q) * P + k];
-    Dyn<KIND>::template jac<T>(x, u, Jx, Ju);
+    Dyn<KIND>::template jac<T>(x, u, Jx, Ju, pa);
+    if (ds) Dyn<KIND>::template f<T>(x, u, fx, pa);
 #pragma unroll
     for (int m = 0; m < NX; ++m) {
-      T a = T(0);
+      T a = ds ? dss * fx[m] : T(0);
 #pragma unroll
       for (int p = 0; p < NX; ++p) a += Jx[m * NX + p] * dX[p * P + k];
       if (dU) {
@@ -713,11 +719,18 @@ struct TermSpec {
 };
 
 // KKT product: out = [H dz + G^T dy ; G dz], with Bt = s B^a (J dz), Mu = s B^aT dlambda.
+// Free final time (part != null): the gradient rows add ds d g / ds = -(ds / s) J^T mu, and each
+// block writes its partial of mu . (J dz) + f . Mu; the s row is -(1/s) times their sum
+// (k_free_finish), i.e. -(B^aT lambda) . (J dz) - (B^a f) . dlambda.
 template <typename T, int KIND>
 __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, const T* __restrict__ w, T s,
                            const T* __restrict__ in, const T* __restrict__ Bt, const T* __restrict__ Mu, int64_t P,
-                           int64_t L, TermSpec ts, T cost_uu, T* __restrict__ out) {
+                           int64_t L, TermSpec ts, T cost_uu, T* __restrict__ out, T pa, int64_t s_idx,
+                           double* __restrict__ part) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu, NV = NX + NU;
+  __shared__ double red[32];
+  const T dss = part ? in[s_idx] / s : T(0);
+  double sacc = 0.0;
   const T* dX = in;
   const T* dU = in + NX * P;
   const T* dL = in + NV * P;
@@ -737,9 +750,22 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
     for (int m = 0; m < NX; ++m) { x[m] = xu[m * P + k]; m_[m] = mu[m * P + k]; dz[m] = dX[m * P + k]; mp[m] = Mu[m * P + k]; }
 #pragma unroll
     for (int q = 0; q < NU; ++q) { u[q] = xu[(NX + q) * P + k]; dz[NX + q] = dU[q * P + k]; }
-    Dyn<KIND>::template jac<T>(x, u, Jx, Ju);
-    Dyn<KIND>::template hess<T>(x, u, m_, H);
+    Dyn<KIND>::template jac<T>(x, u, Jx, Ju, pa);
+    Dyn<KIND>::template hess<T>(x, u, m_, H, pa);
     const T swk = s * w[k] * cost_uu;
+    if (part) {
+      T fx[NXM];
+      Dyn<KIND>::template f<T>(x, u, fx, pa);
+#pragma unroll
+      for (int m = 0; m < NX; ++m) {
+        T jd = T(0);
+#pragma unroll
+        for (int p = 0; p < NX; ++p) jd += Jx[m * NX + p] * dz[p];
+#pragma unroll
+        for (int q = 0; q < NU; ++q) jd += Ju[m * NU + q] * dz[NX + q];
+        sacc += (double)m_[m] * (double)jd + (double)fx[m] * (double)mp[m];
+      }
+    }
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
       T acc = T(0);
@@ -749,10 +775,10 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
       if (a < NX) {
         acc += dL[a * P + k];
 #pragma unroll
-        for (int m = 0; m < NX; ++m) acc -= Jx[m * NX + a] * mp[m];
+        for (int m = 0; m < NX; ++m) acc -= Jx[m * NX + a] * (mp[m] + dss * m_[m]);
       } else {
 #pragma unroll
-        for (int m = 0; m < NX; ++m) acc -= Ju[m * NU + (a - NX)] * mp[m];
+        for (int m = 0; m < NX; ++m) acc -= Ju[m * NU + (a - NX)] * (mp[m] + dss * m_[m]);
       }
       if (a < NX && k == L - 1) {
         for (int r = 0; r < ts.n_e; ++r)
@@ -767,6 +793,113 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
       for (int r = 0; r < 32; ++r) oNu[r] = r < ts.n_e ? dX[ts.idx[r] * P + k] : T(0);
     }
   }
+  if (part) {
+    const double tot = block_sum<double>(sacc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+  }
+}
+
+// One block: *out = scale * sum of n partials (fixed order).
+template <typename T>
+__global__ void k_free_finish(const double* __restrict__ part, int n, double scale, T* __restrict__ out) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
+  const double t = block_sum<double>(a, red);
+  if (threadIdx.x == 0) out[0] = (T)(scale * t);
+}
+
+// Border of the KKT preconditioner (free final time). a = the KKT matrix's s column:
+// [-(1/s) J_x^T mu ; -(1/s) J_u^T mu ; -B^a f ; 0], mu = s B^aT lambda at the linearisation.
+template <typename T, int KIND>
+__global__ void k_border(const T* __restrict__ xu, const T* __restrict__ mu, const T* __restrict__ Baf, T inv_s,
+                         int64_t P, int64_t L, T pa, T* __restrict__ a) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu, NV = NX + NU;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k < 32) a[(NV + NX) * P + k] = T(0);
+    if (k >= L) {
+#pragma unroll
+      for (int m = 0; m < NV + NX; ++m) a[m * P + k] = T(0);
+      continue;
+    }
+    T x[NXM], u[NUM], m_[NXM], Jx[NXM * NXM], Ju[NXM * NUM];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) { x[m] = xu[m * P + k]; m_[m] = mu[m * P + k]; }
+#pragma unroll
+    for (int q = 0; q < NU; ++q) u[q] = xu[(NX + q) * P + k];
+    Dyn<KIND>::template jac<T>(x, u, Jx, Ju, pa);
+#pragma unroll
+    for (int p = 0; p < NX; ++p) {
+      T g = T(0);
+#pragma unroll
+      for (int m = 0; m < NX; ++m) g -= Jx[m * NX + p] * m_[m];
+      a[p * P + k] = g * inv_s;
+    }
+#pragma unroll
+    for (int q = 0; q < NU; ++q) {
+      T g = T(0);
+#pragma unroll
+      for (int m = 0; m < NX; ++m) g -= Ju[m * NU + q] * m_[m];
+      a[(NX + q) * P + k] = g * inv_s;
+    }
+#pragma unroll
+    for (int m = 0; m < NX; ++m) a[(NV + m) * P + k] = -Baf[m * P + k];
+  }
+}
+
+// f at the linearisation point, working type (padding left unwritten: products ignore it).
+template <typename T, int KIND>
+__global__ void k_fT(const T* __restrict__ xu, int64_t P, int64_t L, T pa, T* __restrict__ f) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+    T x[NXM], u[NUM], fx[NXM];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) x[m] = xu[m * P + k];
+#pragma unroll
+    for (int q = 0; q < NU; ++q) u[q] = xu[(NX + q) * P + k];
+    Dyn<KIND>::template f<T>(x, u, fx, pa);
+#pragma unroll
+    for (int m = 0; m < NX; ++m) f[m * P + k] = fx[m];
+  }
+}
+
+// Partials of x . y over n elements (FP64 accumulation), one per block.
+template <typename T>
+__global__ void k_dot_part(const T* __restrict__ x, const T* __restrict__ y, int64_t n, double* __restrict__ part) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a += (double)x[i] * (double)y[i];
+  const double t = block_sum<double>(a, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// gam[0] = 1 / sum(part) (the border's a . q), one block.
+__global__ void k_border_gamma(const double* __restrict__ part, int n, double* __restrict__ gam) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
+  const double t = block_sum<double>(a, red);
+  if (threadIdx.x == 0) gam[0] = 1.0 / t;
+}
+
+// Bordered solve, step 2 (one block): ds = (a . t - r_s) / (a . q) into gam[1].
+template <typename T>
+__global__ void k_border_ds(const double* __restrict__ part, int n, const T* __restrict__ rs, double* __restrict__ gam) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
+  const double t = block_sum<double>(a, red);
+  if (threadIdx.x == 0) gam[1] = (t - (double)rs[0]) * gam[0];
+}
+
+// Bordered solve, step 3: y = t - ds q, y_s = ds.
+template <typename T>
+__global__ void k_border_fix(const T* __restrict__ q, const double* __restrict__ gam, int64_t n, int64_t s_idx,
+                             T* __restrict__ y) {
+  const T ds = (T)gam[1];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = i == s_idx ? ds : y[i] - ds * q[i];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -776,7 +909,7 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
 template <typename T, int KIND>
 __global__ void k_pre_u(const T* __restrict__ xu, const T* __restrict__ w, T s, T cost_uu, const T* __restrict__ ru,
                         const T* __restrict__ b, int64_t P, int64_t L, T* __restrict__ yu, T* __restrict__ g,
-                        T gsign) {
+                        T gsign, const T* __restrict__ mu, T pa) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
     if (k >= L) {
@@ -791,8 +924,11 @@ __global__ void k_pre_u(const T* __restrict__ xu, const T* __restrict__ w, T s, 
     for (int m = 0; m < NX; ++m) x[m] = xu[m * P + k];
 #pragma unroll
     for (int q = 0; q < NU; ++q) u[q] = xu[(NX + q) * P + k];
-    Dyn<KIND>::template jac<T>(x, u, Jx, Ju);
-    const T inv = T(1) / (s * w[k] * cost_uu);
+    Dyn<KIND>::template jac<T>(x, u, Jx, Ju, pa);
+    T mk[NXM];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) mk[m] = Dyn<KIND>::huu_needs_mu ? mu[m * P + k] : T(0);
+    const T inv = T(1) / Dyn<KIND>::template pre_huu<T>(mk, s * w[k] * cost_uu, pa);
 #pragma unroll
     for (int q = 0; q < NU; ++q) {
       T a = ru ? ru[q * P + k] : T(0);
@@ -865,7 +1001,7 @@ __global__ void k_unit(T* v, int64_t n, int64_t idx) {
 // Residual kernels (FP64)
 // ---------------------------------------------------------------------------------------------
 template <int KIND>
-__global__ void k_feval(const double* __restrict__ z, int64_t P, int64_t L, double* __restrict__ fout) {
+__global__ void k_feval(const double* __restrict__ z, int64_t P, int64_t L, double* __restrict__ fout, double pa) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
     if (k >= L) {
@@ -878,7 +1014,7 @@ __global__ void k_feval(const double* __restrict__ z, int64_t P, int64_t L, doub
     for (int m = 0; m < NX; ++m) x[m] = z[m * P + k];
 #pragma unroll
     for (int q = 0; q < NU; ++q) u[q] = z[(NX + q) * P + k];
-    Dyn<KIND>::template f<double>(x, u, f);
+    Dyn<KIND>::template f<double>(x, u, f, pa);
 #pragma unroll
     for (int m = 0; m < NX; ++m) fout[m * P + k] = f[m];
   }
@@ -893,14 +1029,14 @@ template <int KIND>
 __global__ void k_resid_post(const double* __restrict__ z, const double* __restrict__ w, double s,
                              const double* __restrict__ Bf, const double* __restrict__ Mu, int64_t P, int64_t L,
                              TermSpec ts, X0Spec x0, double cost_uu, double* __restrict__ F,
-                             double* __restrict__ partial) {
+                             double* __restrict__ partial, double pa, double* __restrict__ partial2) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu, NV = NX + NU;
   __shared__ double red[32];
   const double* X = z;
   const double* U = z + NX * P;
   const double* lam = z + NV * P;
   const double* nu = z + (NV + NX) * P;
-  double acc = 0.0;
+  double acc = 0.0, acc2 = 0.0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
     if (k >= L) {
 #pragma unroll
@@ -912,7 +1048,7 @@ __global__ void k_resid_post(const double* __restrict__ z, const double* __restr
     for (int m = 0; m < NX; ++m) { x[m] = X[m * P + k]; mp[m] = Mu[m * P + k]; }
 #pragma unroll
     for (int q = 0; q < NU; ++q) u[q] = U[q * P + k];
-    Dyn<KIND>::template jac<double>(x, u, Jx, Ju);
+    Dyn<KIND>::template jac<double>(x, u, Jx, Ju, pa);
     const double wk = w[k];
     const double iw = 1.0 / wk;
 #pragma unroll
@@ -939,6 +1075,7 @@ __global__ void k_resid_post(const double* __restrict__ z, const double* __restr
       const double c = x[m] - x0.x0[m] - Bf[m * P + k];
       F[(NV + m) * P + k] = c;
       acc += wk * c * c;
+      if (partial2) acc2 += lam[m * P + k] * Bf[m * P + k];
     }
     if (k == L - 1) {
       for (int r = 0; r < 32; ++r) {
@@ -950,6 +1087,26 @@ __global__ void k_resid_post(const double* __restrict__ z, const double* __restr
   }
   double tot = block_sum<double>(acc, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+  if (partial2) {
+    tot = block_sum<double>(acc2, red);
+    if (threadIdx.x == 0) partial2[blockIdx.x] = tot;
+  }
+}
+
+// Free final time (one block): g_s = 2 - (1/s) sum lambda . Bf (Bf = s B^a f) into F_s, and the
+// squared weighted norm sum(partial) + g_s^2 into out.
+__global__ void k_resid_free(const double* __restrict__ partial, const double* __restrict__ partial2, int n,
+                             double inv_s, double* __restrict__ Fs, double* __restrict__ out) {
+  __shared__ double red[32];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { a += partial[i]; b += partial2[i]; }
+  const double ta = block_sum<double>(a, red);
+  const double tb = block_sum<double>(b, red);
+  if (threadIdx.x == 0) {
+    const double gs = 2.0 - inv_s * tb;
+    Fs[0] = gs;
+    out[0] = ta + gs * gs;
+  }
 }
 
 // Weighted norm partials of an arbitrary FP64 residual vector.
@@ -998,6 +1155,7 @@ template <int KIND> struct KindNX { static constexpr int nx = Dyn<KIND>::nx, nu 
     case BK_DBL_INT: return FN<BK_DBL_INT>(__VA_ARGS__);                  \
     case BK_ORBIT: return FN<BK_ORBIT>(__VA_ARGS__);                      \
     case BK_BILINEAR: return FN<BK_BILINEAR>(__VA_ARGS__);                \
+    case BK_ORBIT_MT: return FN<BK_ORBIT_MT>(__VA_ARGS__);                \
     default: set_error("unknown problem kind"); return BK_ERR_ARG;        \
   }
 
@@ -1026,6 +1184,11 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
     BK_TRY(dmalloc(&d.lve[l], es * npad * nx));
     if (l > 0) BK_TRY(dmalloc(&d.lvo[l], es * npad * nx));
   }
+  if (pre && pr->free_time) {
+    BK_TRY(dmalloc(&d.brd, es * pr->kkt_len()));
+    BK_TRY(dmalloc(&d.brq, es * pr->kkt_len()));
+    BK_TRY(dmalloc((void**)&d.bgam, sizeof(double) * 2));
+  }
   if (pre && ne > 0) {
     BK_TRY(dmalloc(&d.Zc, es * ne * nx * P));
     BK_TRY(dmalloc(&d.HWc, es * ne * nu * P));
@@ -1040,7 +1203,7 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
 
 static void free_opdata(OpData& d) {
   if (d.plan) plan_destroy(d.plan);
-  void* ps[] = {d.xu, d.mu, d.Kn, d.Nn, d.Zc, d.HWc, d.Qc, d.Sinv, d.t1, d.t2, d.t3};
+  void* ps[] = {d.xu, d.mu, d.Kn, d.Nn, d.Zc, d.HWc, d.Qc, d.Sinv, d.t1, d.t2, d.t3, d.brd, d.brq, d.bgam};
   for (void* p : ps) dfree(p);
   for (int l = 0; l < MAXLEV; ++l) {
     dfree(d.lvm[l]);
@@ -1054,7 +1217,8 @@ static void free_opdata(OpData& d) {
 template <typename T, int KIND>
 static bk_status lin_factors(Problem* pr, OpData& d, const double* z, cudaStream_t st) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
-  k_lin_nodes<T, KIND, NX, NU><<<nblk(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->d64.plan->w64, pr->s, (T*)d.Kn, (T*)d.Nn, (T*)d.xu);
+  k_lin_nodes<T, KIND, NX, NU><<<nblk(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->d64.plan->w64, pr->s, (T*)d.Kn, (T*)d.Nn, (T*)d.xu,
+                                                             pr->dyn_param());
   BK_CHECK_LAUNCH();
   k_lin_seg<T, NX><<<(pr->nseg + 127) / 128, 128, 0, st>>>((const T*)d.Nn, pr->L, pr->nseg, (T*)d.lvm[0]);
   BK_CHECK_LAUNCH();
@@ -1094,7 +1258,8 @@ static bk_status lin_schur_launch(Problem* pr, OpData& d, cudaStream_t st) {
     // W = Pu^T Z = -s Ju^T (B-tilde^T Z). k_pre_u with r_u = 0 and b = B-tilde^T Z gives
     // yu = s Ju^T b / (s w) = -H~^{-1} W and g = Ju yu = -Ju H~^{-1} W.
     T* HW = HWc + (int64_t)r * NU * P;
-    k_pre_u<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.w, s, (T)1, nullptr, bz, P, L, HW, g, T(1));
+    k_pre_u<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.w, s, (T)1, nullptr, bz, P, L, HW, g, T(1),
+                                              (const T*)d.mu, (T)pr->dyn_param());
     BK_CHECK_LAUNCH();
     // Q = P^{-1} Pu HW: forward sweep with Y = 0 and forcing -Ju HW = Ju (-HW) = g
     k_unit<T><<<nblk(NX * P), 256, 0, st>>>(unit, NX * P, -1);
@@ -1145,6 +1310,9 @@ static bk_status lin_schur_finish(Problem* pr, OpData& d, cudaStream_t st) {
   return BK_OK;
 }
 
+template <typename T, int KIND>
+static bk_status lin_border(Problem* pr, OpData& d, cudaStream_t st);
+
 // mu (nullable): s B^aT lambda at this z, known to the caller (e.g. from the residual that
 // accepted the step); it is copied instead of recomputed.
 // A BK_F32 problem builds its preconditioner data in FP32 only; the FP64 side keeps the
@@ -1153,7 +1321,7 @@ template <int KIND>
 static bk_status linearize_kind(Problem* pr, const double* z, const double* mu, int keep, cudaStream_t st) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   const int64_t P = pr->P;
-  if (!pr->linearized) keep = LIN_FULL;
+  if (!pr->linearized || pr->free_time) keep = LIN_FULL;
   if (mu)
     BK_TRY_CUDA(cudaMemcpyAsync(pr->d64.mu, mu, sizeof(double) * NX * P, cudaMemcpyDeviceToDevice, st));
   else
@@ -1179,6 +1347,10 @@ static bk_status linearize_kind(Problem* pr, const double* z, const double* mu, 
     BK_TRY((d.dtype == BK_F64 ? lin_schur_launch<double, KIND>(pr, d, st) : lin_schur_launch<float, KIND>(pr, d, st)));
     BK_TRY(d.dtype == BK_F64 ? lin_schur_finish<double>(pr, d, st) : lin_schur_finish<float>(pr, d, st));
   }
+  if (pr->free_time) {
+    OpData& d = pr->work();
+    BK_TRY((d.dtype == BK_F64 ? lin_border<double, KIND>(pr, d, st) : lin_border<float, KIND>(pr, d, st)));
+  }
   return BK_OK;
 }
 
@@ -1197,21 +1369,29 @@ static bk_status apply_typed(Problem* pr, OpData& d, int op, const T* in, T* out
   T* t3 = (T*)d.t3;
   if (op == BK_OP_STATE) {
     // the product ignores t1's padding (elements L..P-1), so it is never written
-    k_jvp<T, KIND><<<nblk(L), 256, 0, st>>>((const T*)d.xu, in, nullptr, P, L, t1);
+    k_jvp<T, KIND><<<nblk(L), 256, 0, st>>>((const T*)d.xu, in, nullptr, P, L, t1, (T)pr->dyn_param(), nullptr, T(0));
     BK_CHECK_LAUNCH();
     BK_TRY(plan_apply_n(d.plan, t1, t2, NX, false, pr->s, st));
     k_state_post<T, NX><<<nblk(NX * P), 256, 0, st>>>(in, t2, P, L, out);
     BK_CHECK_LAUNCH();
     return BK_OK;
   }
-  k_jvp<T, KIND><<<nblk(L), 256, 0, st>>>((const T*)d.xu, in, in + NX * P, P, L, t1);
+  const bool ft = pr->free_time;
+  const T pa = (T)pr->dyn_param();
+  k_jvp<T, KIND><<<nblk(L), 256, 0, st>>>((const T*)d.xu, in, in + NX * P, P, L, t1, pa,
+                                          ft ? in + pr->s_idx() : nullptr, (T)(1.0 / pr->s));
   BK_CHECK_LAUNCH();
   BK_TRY(plan_apply_n(d.plan, t1, t2, NX, false, pr->s, st));
   T* Mu = mu_out ? mu_out : t3;
   BK_TRY(plan_apply_n(d.plan, in + (NX + NU) * P, Mu, NX, true, pr->s, st));
-  k_kkt_post<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.mu, (const T*)d.w, (T)pr->s, in, t2, Mu, P, L,
-                                                term_spec(pr), (T)(pr->has_cost ? 1.0 : 0.0), out);
+  k_kkt_post<T, KIND><<<ft ? FT_NB : nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.mu, (const T*)d.w, (T)pr->s, in,
+                                                            t2, Mu, P, L, term_spec(pr), (T)pr->cost_uu(), out, pa,
+                                                            pr->s_idx(), ft ? pr->sred : nullptr);
   BK_CHECK_LAUNCH();
+  if (ft) {
+    k_free_finish<T><<<1, 256, 0, st>>>(pr->sred, FT_NB, -1.0 / pr->s, out + pr->s_idx());
+    BK_CHECK_LAUNCH();
+  }
   return BK_OK;
 }
 
@@ -1237,7 +1417,8 @@ bk_status op_apply(Problem* pr, OpData& d, int op, const void* in, void* out, cu
 // t_lambda); q = P^{-1}(r_lambda - Pu yu); y_nu = S^{-1}(E q - r_nu); y_u = yu + H~^{-1} W y_nu;
 // y_x = q - Q y_nu; y_lambda = t_lambda - Z y_nu.  (Pu = -s (B-tilde (x) I) J_u, H~ = s w I.)
 template <typename T, int KIND>
-static bk_status precond_typed(Problem* pr, OpData& d, int op, const T* in, T* out, int transpose, cudaStream_t st) {
+static bk_status precond_typed(Problem* pr, OpData& d, int op, const T* in, T* out, int transpose, cudaStream_t st,
+                               bool border = true) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu, NV = NX + NU;
   const int64_t P = pr->P, L = pr->L;
   if (op == BK_OP_STATE) {
@@ -1256,7 +1437,8 @@ static bk_status precond_typed(Problem* pr, OpData& d, int op, const T* in, T* o
   T* b = (T*)d.t1;
   T* g = (T*)d.t2;
   BK_TRY((run_sweep<T, NX, 1>(pr, d, rx, nullptr, yl, b, st)));
-  k_pre_u<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.w, (T)pr->s, (T)1, ru, b, P, L, yu, g, T(1));
+  k_pre_u<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.w, (T)pr->s, (T)1, ru, b, P, L, yu, g, T(1),
+                                            (const T*)d.mu, (T)pr->dyn_param());
   BK_CHECK_LAUNCH();
   BK_TRY((run_sweep<T, NX, 0>(pr, d, rl, g, yx, nullptr, st)));
   if (pr->n_e > 0) {
@@ -1267,6 +1449,39 @@ static bk_status precond_typed(Problem* pr, OpData& d, int op, const T* in, T* o
   } else {
     BK_TRY_CUDA(cudaMemsetAsync(ynu, 0, sizeof(T) * 32, st));
   }
+  if (pr->free_time && border) {
+    // bordered by the s row and column a (zero diagonal): with t = K-tilde^{-1} r (above) and
+    // q = K-tilde^{-1} a, ds = (a . t - r_s) / (a . q), y = t - ds q, y_s = ds
+    const int64_t n = pr->kkt_len();
+    k_dot_part<T><<<FT_NB, 256, 0, st>>>((const T*)d.brd, out, n, pr->sred);
+    BK_CHECK_LAUNCH();
+    k_border_ds<T><<<1, 256, 0, st>>>(pr->sred, FT_NB, in + pr->s_idx(), d.bgam);
+    BK_CHECK_LAUNCH();
+    k_border_fix<T><<<nblk(n), 256, 0, st>>>((const T*)d.brq, d.bgam, n, pr->s_idx(), out);
+    BK_CHECK_LAUNCH();
+  }
+  return BK_OK;
+}
+
+// Free final time: the border a of the KKT preconditioner (the KKT matrix's s column at the
+// linearisation), q = K-tilde^{-1} a and 1 / (a . q).
+template <typename T, int KIND>
+static bk_status lin_border(Problem* pr, OpData& d, cudaStream_t st) {
+  constexpr int NX = Dyn<KIND>::nx;
+  const int64_t P = pr->P, L = pr->L;
+  T* f = (T*)d.t1;
+  T* Baf = (T*)d.t2;
+  k_fT<T, KIND><<<nblk(L), 256, 0, st>>>((const T*)d.xu, P, L, (T)pr->dyn_param(), f);
+  BK_CHECK_LAUNCH();
+  BK_TRY(plan_apply_n(d.plan, f, Baf, NX, false, 1.0, st));
+  k_border<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.mu, Baf, (T)(1.0 / pr->s), P, L,
+                                             (T)pr->dyn_param(), (T*)d.brd);
+  BK_CHECK_LAUNCH();
+  BK_TRY((precond_typed<T, KIND>(pr, d, BK_OP_KKT, (const T*)d.brd, (T*)d.brq, 0, st, false)));
+  k_dot_part<T><<<FT_NB, 256, 0, st>>>((const T*)d.brd, (const T*)d.brq, pr->kkt_len(), pr->sred);
+  BK_CHECK_LAUNCH();
+  k_border_gamma<<<1, 256, 0, st>>>(pr->sred, FT_NB, d.bgam);
+  BK_CHECK_LAUNCH();
   return BK_OK;
 }
 
@@ -1297,7 +1512,7 @@ static bk_status residual_launch(Problem* pr, const double* z, double* F, bool w
   double* f = (double*)d.t1;
   double* Bf = (double*)d.t2;
   if (!Mu) Mu = (double*)d.t3;
-  k_feval<KIND><<<nblk(P), 256, 0, st>>>(z, P, L, f);
+  k_feval<KIND><<<nblk(P), 256, 0, st>>>(z, P, L, f, pr->dyn_param());
   BK_CHECK_LAUNCH();
   BK_TRY(plan_apply_n(d.plan, f, Bf, NX, false, pr->s, st));
   if (!mu_given) BK_TRY(plan_apply_n(d.plan, z + (NX + NU) * P, Mu, NX, true, pr->s, st));
@@ -1305,9 +1520,16 @@ static bk_status residual_launch(Problem* pr, const double* z, double* F, bool w
   for (int m = 0; m < NXM; ++m) x0.x0[m] = pr->x0[m];
   const int nb = 592;
   k_resid_post<KIND><<<nb, 256, 0, st>>>(z, pr->d64.plan->w64, pr->s, Bf, Mu, P, L, term_spec(pr), x0,
-                                         pr->has_cost ? 1.0 : 0.0, F, pr->red);
+                                         pr->cost_uu(), F, pr->red, pr->dyn_param(),
+                                         pr->free_time ? pr->sred : nullptr);
   BK_CHECK_LAUNCH();
-  if (want_norm) {
+  if (pr->free_time) {
+    // the time gradient g_s goes into F whether or not the norm is wanted
+    k_resid_free<<<1, 256, 0, st>>>(pr->red, pr->sred, nb, 1.0 / pr->s, F + pr->s_idx(), pr->red + 1024);
+    BK_CHECK_LAUNCH();
+    if (want_norm)
+      BK_TRY_CUDA(cudaMemcpyAsync(pr->red_host, pr->red + 1024, sizeof(double), cudaMemcpyDeviceToHost, st));
+  } else if (want_norm) {
     k_sum_partials<<<1, 256, 0, st>>>(pr->red, nb, pr->red + 1024);
     BK_CHECK_LAUNCH();
     BK_TRY_CUDA(cudaMemcpyAsync(pr->red_host, pr->red + 1024, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1341,7 +1563,8 @@ template <int KIND>
 static bk_status wnorm_kind(Problem* pr, const double* F, double* wnorm, cudaStream_t st) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   const int nb = 592;
-  k_wnorm<NX, NU><<<nb, 256, 0, st>>>(F, pr->d64.plan->w64, pr->P, pr->L, pr->n_e, pr->red);
+  // the tail holds e and, for a free final time, g_s right after it
+  k_wnorm<NX, NU><<<nb, 256, 0, st>>>(F, pr->d64.plan->w64, pr->P, pr->L, pr->n_e + (pr->free_time ? 1 : 0), pr->red);
   BK_CHECK_LAUNCH();
   k_sum_partials<<<1, 256, 0, st>>>(pr->red, nb, pr->red + 1024);
   BK_CHECK_LAUNCH();
@@ -1362,6 +1585,7 @@ static void problem_free(Problem* pr) {
   free_opdata(pr->d32);
   dfree(pr->F);
   dfree(pr->red);
+  dfree(pr->sred);
   if (pr->red_host) cudaFreeHost(pr->red_host);
   delete pr;
 }
@@ -1370,9 +1594,10 @@ static void problem_free(Problem* pr) {
 static bk_status problem_set_params(Problem* pr, const double* params, int nparams, double t0, double tf) {
   BK_ARG(tf > t0 && isfinite(t0) && isfinite(tf), "tf must be > t0 and finite");
   BK_ARG(nparams >= 0 && nparams <= 4 && (nparams == 0 || params), "bad params");
-  if (pr->kind == BK_ORBIT) {
-    BK_ARG(nparams >= 2, "BK_ORBIT needs params {a_nominal, r_f}");
+  if (pr->kind == BK_ORBIT || pr->kind == BK_ORBIT_MT) {
+    BK_ARG(nparams >= 2, "the orbit kinds need params {a, r_f}");
     BK_ARG(params[1] > 0 && isfinite(params[1]), "r_f must be > 0");
+    BK_ARG(pr->kind == BK_ORBIT || (params[0] > 0 && isfinite(params[0])), "BK_ORBIT_MT needs a thrust a > 0");
     pr->term_val[0] = params[1];
     pr->term_val[1] = 0.0;
     pr->term_val[2] = 1.0 / sqrt(params[1]);
@@ -1390,7 +1615,8 @@ static bk_status problem_set_params(Problem* pr, const double* params, int npara
 static bk_status problem_create(Problem** out, int kind, const double* params, int nparams, int64_t N, int dtype,
                                 double t0, double tf, cudaStream_t st) {
   *out = nullptr;
-  BK_ARG(kind == BK_DBL_INT || kind == BK_ORBIT || kind == BK_BILINEAR, "unknown problem kind %d", kind);
+  BK_ARG(kind == BK_DBL_INT || kind == BK_ORBIT || kind == BK_BILINEAR || kind == BK_ORBIT_MT,
+         "unknown problem kind %d", kind);
   BK_ARG(dtype == BK_F64 || dtype == BK_F32, "dtype must be BK_F64 or BK_F32");
   BK_ARG(N >= 4 && (is_pow2(N) ? N <= (int64_t(1) << 24) : dense_supported(N)),
          "N must be a power of two in [4, 2^24] or any N in [4, 1024]");
@@ -1412,11 +1638,17 @@ static bk_status problem_create(Problem** out, int kind, const double* params, i
     pr->term_idx[0] = 0; pr->term_val[0] = 1.0;
     pr->term_idx[1] = 1; pr->term_val[1] = 0.0;
     pr->has_cost = true;
-  } else if (kind == BK_ORBIT) {
-    if (nparams < 2) { delete pr; set_error("BK_ORBIT needs params {a_nominal, r_f}"); return BK_ERR_ARG; }
+  } else if (kind == BK_ORBIT || kind == BK_ORBIT_MT) {
+    if (nparams < 2) { delete pr; set_error("the orbit kinds need params {a, r_f}"); return BK_ERR_ARG; }
     const double rf = params[1];
     if (!(rf > 0)) { delete pr; set_error("r_f must be > 0"); return BK_ERR_ARG; }
-    pr->n_x = 4; pr->n_u = 2; pr->n_e = 3;
+    if (kind == BK_ORBIT_MT && !(params[0] > 0 && isfinite(params[0]))) {
+      delete pr;
+      set_error("BK_ORBIT_MT needs a thrust a > 0");
+      return BK_ERR_ARG;
+    }
+    pr->n_x = 4; pr->n_u = kind == BK_ORBIT ? 2 : 1; pr->n_e = 3;
+    pr->free_time = kind == BK_ORBIT_MT;
     pr->x0[0] = 1; pr->x0[1] = 0; pr->x0[2] = 0; pr->x0[3] = 1;
     pr->term_idx[0] = 0; pr->term_val[0] = rf;
     pr->term_idx[1] = 2; pr->term_val[1] = 0.0;
@@ -1440,6 +1672,7 @@ static bk_status problem_create(Problem** out, int kind, const double* params, i
   if (s == BK_OK && dtype == BK_F32) s = alloc_opdata(pr, pr->d32, BK_F32);
   if (s == BK_OK) s = dmalloc((void**)&pr->F, sizeof(double) * pr->kkt_len());
   if (s == BK_OK) s = dmalloc((void**)&pr->red, sizeof(double) * 2048);
+  if (s == BK_OK && pr->free_time) s = dmalloc((void**)&pr->sred, sizeof(double) * 2048);
   if (s == BK_OK && cudaMallocHost((void**)&pr->red_host, sizeof(double) * 512) != cudaSuccess) {
     set_error("cudaMallocHost failed");
     s = BK_ERR_OOM;
@@ -1447,6 +1680,64 @@ static bk_status problem_create(Problem** out, int kind, const double* params, i
   if (s == BK_OK && cudaStreamSynchronize(st) != cudaSuccess) { set_error("sync failed"); s = BK_ERR_CUDA; }
   if (s != BK_OK) { problem_free(pr); return s; }
   *out = pr;
+  return BK_OK;
+}
+
+// Free final time: the problem's s from z's tail slot (synchronous); other kinds: nothing.
+static bk_status sync_time_scale(Problem* pr, const double* z, cudaStream_t st) {
+  if (!pr->free_time) return BK_OK;
+  double* hs = pr->red_host + 200;
+  BK_TRY_CUDA(cudaMemcpyAsync(hs, z + pr->s_idx(), sizeof(double), cudaMemcpyDeviceToHost, st));
+  BK_TRY_CUDA(cudaStreamSynchronize(st));
+  BK_ARG(hs[0] > 0.0 && isfinite(hs[0]), "free final time: the time scale in z must be positive (got %g)", hs[0]);
+  pr->s = hs[0];
+  return BK_OK;
+}
+
+// Minimum-time seed from a minimum-energy KKT vector (layouts of BK_ORBIT and BK_ORBIT_MT, same
+// pitch): X and lambda copied, u = atan2(u_r, u_theta) (the thrust direction as the angle of
+// a (sin u, cos u)), nu copied, s from the minimum-energy problem.
+__global__ void k_seed_mt(const double* __restrict__ zme, int64_t P, int64_t L, double s, double* __restrict__ zmt) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      zmt[m * P + k] = zme[m * P + k];
+      zmt[(5 + m) * P + k] = zme[(6 + m) * P + k];
+    }
+    zmt[4 * P + k] = k < L ? atan2(zme[4 * P + k], zme[5 * P + k]) : 0.0;
+    if (k < 32) zmt[9 * P + k] = k < 3 ? zme[10 * P + k] : (k == 3 ? s : 0.0);
+  }
+}
+
+__global__ void k_scale64(double* __restrict__ v, int64_t n, double a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] *= a;
+}
+
+// Seed, then scale lambda and nu by kappa = 2 / (lambda . (B^a (x) I) f), which zeroes the time
+// gradient g_s = 2 - lambda . (B^a (x) I) f of the seed (the minimum-energy solution's thrust is
+// already along B^aT lambda, so only the multipliers' scale differs).
+static bk_status min_time_seed(Problem* mt, const Problem* me, const double* z_me, double* z_mt, cudaStream_t st) {
+  BK_ARG(mt->kind == BK_ORBIT_MT && me->kind == BK_ORBIT, "seed needs a BK_ORBIT_MT and a BK_ORBIT problem");
+  BK_ARG(mt->N == me->N && mt->P == me->P, "the two problems must have the same N");
+  BK_ARG(mt->t0 == me->t0, "the two problems must start at the same t0");
+  const int64_t P = mt->P;
+  k_seed_mt<<<nblk(P), 256, 0, st>>>(z_me, P, mt->L, me->s, z_mt);
+  BK_CHECK_LAUNCH();
+  mt->s = me->s;
+  double wn = 0.0;
+  BK_TRY(problem_residual(mt, z_mt, mt->F, &wn, st));
+  double* hs = mt->red_host + 200;
+  BK_TRY_CUDA(cudaMemcpyAsync(hs, mt->F + mt->s_idx(), sizeof(double), cudaMemcpyDeviceToHost, st));
+  BK_TRY_CUDA(cudaStreamSynchronize(st));
+  const double S = 2.0 - hs[0];
+  if (!(S > 0.0) || !isfinite(S)) {
+    set_error("minimum-energy multipliers give a non-positive time gradient (%g)", S);
+    return BK_ERR_ARG;
+  }
+  k_scale64<<<nblk(4 * P + 3), 256, 0, st>>>(z_mt + 5 * P, 4 * P + 3, 2.0 / S);
+  BK_CHECK_LAUNCH();
+  BK_TRY_CUDA(cudaStreamSynchronize(st));
   return BK_OK;
 }
 
@@ -1493,7 +1784,9 @@ size_t bk_problem_device_bytes(const bk_problem* prob) {
 bk_status bk_linearize(bk_problem* prob, const double* z_lin, void* stream) {
   BK_ARG(prob != nullptr, "problem is NULL");
   BK_ARG(((uintptr_t)z_lin & 15) == 0, "z_lin must be 16-byte aligned");
-  return bk::problem_linearize(reinterpret_cast<bk::Problem*>(prob), z_lin, (cudaStream_t)stream);
+  bk::Problem* p = reinterpret_cast<bk::Problem*>(prob);
+  BK_TRY(bk::sync_time_scale(p, z_lin, (cudaStream_t)stream));
+  return bk::problem_linearize(p, z_lin, (cudaStream_t)stream);
 }
 
 bk_status kkt_apply(bk_problem* prob, int op, const void* in, void* out, void* stream) {
@@ -1512,7 +1805,16 @@ bk_status precond_apply(bk_problem* prob, int op, const void* in, void* out, int
 
 bk_status bk_kkt_residual(bk_problem* prob, const double* z, double* F_out, double* wnorm, void* stream) {
   BK_ARG(prob != nullptr && z != nullptr && F_out != nullptr, "NULL argument");
-  return bk::problem_residual(reinterpret_cast<bk::Problem*>(prob), z, F_out, wnorm, (cudaStream_t)stream);
+  bk::Problem* p = reinterpret_cast<bk::Problem*>(prob);
+  BK_TRY(bk::sync_time_scale(p, z, (cudaStream_t)stream));
+  return bk::problem_residual(p, z, F_out, wnorm, (cudaStream_t)stream);
+}
+
+bk_status bk_min_time_seed(bk_problem* mt, const bk_problem* me, const double* z_me, double* z_mt, void* stream) {
+  BK_ARG(mt != nullptr && me != nullptr && z_me != nullptr && z_mt != nullptr, "NULL argument");
+  BK_ARG(z_me != z_mt, "z_me and z_mt must not alias");
+  return bk::min_time_seed(reinterpret_cast<bk::Problem*>(mt), reinterpret_cast<const bk::Problem*>(me), z_me, z_mt,
+                           (cudaStream_t)stream);
 }
 
 }  // extern "C"

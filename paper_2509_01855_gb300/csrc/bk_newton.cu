@@ -17,6 +17,11 @@
 // costs one forward product. Backtracking takes the minimiser of the quadratic model of
 // ||F||_W^2 along d (slope -2 ||F||_W^2 at alpha = 0, the Newton value), safeguarded to
 // [alpha / 10, alpha / 2], instead of halving.
+//
+// Free final time (BK_ORBIT_MT): s = (t_f - t_0)/2 sits in z's tail slot. The problem's s follows
+// z (read back once per step, with the step's ds), trials with s <= 0 are rejected, and mu is
+// recomputed for every trial (s B^aT lambda is bilinear in s and lambda, so the update above
+// does not apply).
 #include <math.h>
 #include <string.h>
 
@@ -142,6 +147,17 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
   ko.max_iter = o.max_krylov;
   ko.use_precond = 1;
   double phi = 0.0;
+  const bool ft = pr->free_time;
+  double* hs = pr->red_host + 200;  // pinned: s or ds read back for a free final time
+  if (ft) {
+    BK_TRY_CUDA(cudaMemcpyAsync(hs, z + pr->s_idx(), sizeof(double), cudaMemcpyDeviceToHost, st));
+    BK_TRY_CUDA(cudaStreamSynchronize(st));
+    if (!(hs[0] > 0.0) || !isfinite(hs[0])) {
+      set_error("free final time: the time scale in z must be positive (got %g)", hs[0]);
+      return BK_ERR_ARG;
+    }
+    pr->s = hs[0];
+  }
   BK_TRY(problem_residual(pr, z, F, &phi, st, Mu, false));
   info->residual0 = phi;
   info->residual = phi;
@@ -154,6 +170,12 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     // quadratic outer convergence kept. Floor 1e-12 in FP64, 1e-4 in FP32.
     if (o.krylov_rtol > 0) {
       ko.rtol = o.krylov_rtol;
+    } else if (ft) {
+      // Free final time: tight inner solves. GMRES measures its residual in the 2-norm while the
+      // merit divides the gradient rows by w (w_0 ~ 1/N^2); on the minimum-time orbit the loose
+      // early steps of the forcing term stopped being descent directions of ||F||_W from
+      // N = 2^12 (measured), while steps solved to 1e-12 gave the same Newton count for every N.
+      ko.rtol = 1e-12;
     } else {
       const double r = phi / info->residual0;
       const double lo = pr->dtype == BK_F64 ? 1e-12 : 1e-4;
@@ -168,7 +190,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     bk_krylov_info ki;
     if (pr->dtype == BK_F64) {
       const KrylovMu aux = {Trec, nxP, Mud, nxP};
-      BK_TRY(gmres(pr, pr->d64, BK_OP_KKT, rhs, d, ko, &ki, gws, st, &aux));
+      BK_TRY(gmres(pr, pr->d64, BK_OP_KKT, rhs, d, ko, &ki, gws, st, ft ? nullptr : &aux));
       info->krylov_iterations += ki.iterations;
       info->kkt_solves += 1;
     } else {
@@ -195,7 +217,14 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
         BK_TRY(norm2(pr, r, n, &rn, st));
         if (rn <= o.ir_rtol * rn0) break;
       }
-      BK_TRY(plan_apply_n(pr->d64.plan, dlam, Mud, pr->n_x, true, pr->s, st));
+      if (!ft) BK_TRY(plan_apply_n(pr->d64.plan, dlam, Mud, pr->n_x, true, pr->s, st));
+    }
+    const double s0 = pr->s;
+    double ds = 0.0;
+    if (ft) {
+      BK_TRY_CUDA(cudaMemcpyAsync(hs, d + pr->s_idx(), sizeof(double), cudaMemcpyDeviceToHost, st));
+      BK_TRY_CUDA(cudaStreamSynchronize(st));
+      ds = hs[0];
     }
     // backtracking line search on ||F||_W
     double alpha = 1.0, phit = 0.0;
@@ -204,9 +233,18 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     for (;;) {
       k_step<<<g, 256, 0, st>>>(z, d, alpha, zt, n);
       BK_CHECK_LAUNCH();
-      k_step<<<g1(nxP), 256, 0, st>>>(Mu, Mud, alpha, Mut, nxP);
-      BK_CHECK_LAUNCH();
-      BK_TRY(problem_residual(pr, zt, F, &phit, st, Mut, true));
+      if (ft) {
+        pr->s = s0 + alpha * ds;
+        if (!(pr->s > 0.0)) {
+          phit = INFINITY;  // a non-positive final time: shrink the step
+        } else {
+          BK_TRY(problem_residual(pr, zt, F, &phit, st, Mut, false));
+        }
+      } else {
+        k_step<<<g1(nxP), 256, 0, st>>>(Mu, Mud, alpha, Mut, nxP);
+        BK_CHECK_LAUNCH();
+        BK_TRY(problem_residual(pr, zt, F, &phit, st, Mut, true));
+      }
       if (phit <= (1.0 - 1e-4 * alpha) * phi || bt >= 30) break;
       double an = phi2 * alpha * alpha / (phit * phit - phi2 + 2.0 * phi2 * alpha);
       if (!(an >= 0.1 * alpha)) an = 0.1 * alpha;  // also catches a non-finite trial residual
@@ -216,6 +254,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     }
     info->backtracks += bt;
     if (!(phit <= (1.0 - 1e-4 * alpha) * phi)) {
+      pr->s = s0;
       info->iterations = it;
       info->residual = phi;
       set_error("line search failed after %d halvings at ||F||_W = %.3e", bt, phi);

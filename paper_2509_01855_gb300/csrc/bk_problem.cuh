@@ -3,7 +3,8 @@
 // Discretisation (Eq. Prob-PNa with V = f(X, U) eliminated and x^a fixed):
 //   c(X, U) = X - x0 (x) 1 - s (B^a (x) I) f(X, U),  e(X) = X[term, N] - target,
 //   J = s sum_i w_i F(x_i, u_i).
-// KKT vectors (component-major, pitch P per block): [X | U | lambda | nu (padded to 32)].
+// KKT vectors (component-major, pitch P per block): [X | U | lambda | nu (padded to 32)]; a free
+// final time (BK_ORBIT_MT) keeps s = (t_f - t_0)/2 in the tail slot after nu.
 #pragma once
 
 #include "bk_common.cuh"
@@ -32,19 +33,25 @@ enum { SL_A = 0, SL_M1 = 1, SL_PRE = 5, SL_SUF = 6, NSLOT = 7 };
 // ---------------------------------------------------------------------------------------------
 template <int KIND> struct Dyn;
 
+__device__ inline void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ inline void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
+
 // Minimum-energy double integrator: x = (p, v), x' = (v, u), F = u^2 / 2.
 template <> struct Dyn<BK_DBL_INT> {
   static constexpr int nx = 2, nu = 1;
-  template <typename T> __device__ static void f(const T* x, const T* u, T* fx) {
+  // control block of the KKT preconditioner at a node: s w_k times the running cost's curvature
+  static constexpr bool huu_needs_mu = false;
+  template <typename T> __device__ static T pre_huu(const T* mu, T swk, T) { return swk; }
+  template <typename T> __device__ static void f(const T* x, const T* u, T* fx, T) {
     fx[0] = x[1];
     fx[1] = u[0];
   }
-  template <typename T> __device__ static void jac(const T* x, const T* u, T* Jx, T* Ju) {
+  template <typename T> __device__ static void jac(const T* x, const T* u, T* Jx, T* Ju, T) {
     Jx[0] = 0; Jx[1] = 1; Jx[2] = 0; Jx[3] = 0;
     Ju[0] = 0; Ju[1] = 1;
   }
   // H[(nx+nu)^2] = sum_m mu_m Hess f_m (zero: f is linear)
-  template <typename T> __device__ static void hess(const T* x, const T* u, const T* mu, T* H) {
+  template <typename T> __device__ static void hess(const T* x, const T* u, const T* mu, T* H, T) {
     for (int i = 0; i < 9; ++i) H[i] = 0;
   }
 };
@@ -53,7 +60,10 @@ template <> struct Dyn<BK_DBL_INT> {
 // x = (r, theta, v_r, v_theta), u = (u_r, u_theta).
 template <> struct Dyn<BK_ORBIT> {
   static constexpr int nx = 4, nu = 2;
-  template <typename T> __device__ static void f(const T* x, const T* u, T* fx) {
+  // control block of the KKT preconditioner at a node: s w_k times the running cost's curvature
+  static constexpr bool huu_needs_mu = false;
+  template <typename T> __device__ static T pre_huu(const T* mu, T swk, T) { return swk; }
+  template <typename T> __device__ static void f(const T* x, const T* u, T* fx, T) {
     const T r = x[0], vr = x[2], vt = x[3];
     const T ir = T(1) / r;
     fx[0] = vr;
@@ -61,7 +71,7 @@ template <> struct Dyn<BK_ORBIT> {
     fx[2] = vt * vt * ir - ir * ir + u[0];
     fx[3] = -vr * vt * ir + u[1];
   }
-  template <typename T> __device__ static void jac(const T* x, const T* u, T* Jx, T* Ju) {
+  template <typename T> __device__ static void jac(const T* x, const T* u, T* Jx, T* Ju, T) {
     const T r = x[0], vr = x[2], vt = x[3];
     const T ir = T(1) / r, ir2 = ir * ir;
     for (int i = 0; i < 16; ++i) Jx[i] = 0;
@@ -77,7 +87,7 @@ template <> struct Dyn<BK_ORBIT> {
     Ju[2 * 2 + 0] = 1;
     Ju[3 * 2 + 1] = 1;
   }
-  template <typename T> __device__ static void hess(const T* x, const T* u, const T* mu, T* H) {
+  template <typename T> __device__ static void hess(const T* x, const T* u, const T* mu, T* H, T) {
     const T r = x[0], vr = x[2], vt = x[3];
     const T ir = T(1) / r, ir2 = ir * ir, ir3 = ir2 * ir;
     const T mth = mu[1], mvr = mu[2], mvt = mu[3];
@@ -100,13 +110,56 @@ template <> struct Dyn<BK_ORBIT> {
 // Scalar bilinear x' = u x (no cost): linearised at (X, U) the state Jacobian is diag(U).
 template <> struct Dyn<BK_BILINEAR> {
   static constexpr int nx = 1, nu = 1;
-  template <typename T> __device__ static void f(const T* x, const T* u, T* fx) { fx[0] = u[0] * x[0]; }
-  template <typename T> __device__ static void jac(const T* x, const T* u, T* Jx, T* Ju) {
+  // control block of the KKT preconditioner at a node: s w_k times the running cost's curvature
+  static constexpr bool huu_needs_mu = false;
+  template <typename T> __device__ static T pre_huu(const T* mu, T swk, T) { return swk; }
+  template <typename T> __device__ static void f(const T* x, const T* u, T* fx, T) { fx[0] = u[0] * x[0]; }
+  template <typename T> __device__ static void jac(const T* x, const T* u, T* Jx, T* Ju, T) {
     Jx[0] = u[0];
     Ju[0] = x[0];
   }
-  template <typename T> __device__ static void hess(const T* x, const T* u, const T* mu, T* H) {
+  template <typename T> __device__ static void hess(const T* x, const T* u, const T* mu, T* H, T) {
     H[0] = 0; H[1] = mu[0]; H[2] = mu[0]; H[3] = 0;
+  }
+};
+
+// Minimum-time orbit transfer of Eq. ot: the same state, fixed-magnitude thrust a (sin u, cos u)
+// steered by the angle u (pa = a), cost T = t_f - t_0 with the final time free.
+template <> struct Dyn<BK_ORBIT_MT> {
+  static constexpr int nx = 4, nu = 1;
+  template <typename T> __device__ static void f(const T* x, const T* u, T* fx, T a) {
+    const T r = x[0], vr = x[2], vt = x[3];
+    const T ir = T(1) / r;
+    T su, cu;
+    sincos_t(u[0], &su, &cu);
+    fx[0] = vr;
+    fx[1] = vt * ir;
+    fx[2] = vt * vt * ir - ir * ir + a * su;
+    fx[3] = -vr * vt * ir + a * cu;
+  }
+  template <typename T> __device__ static void jac(const T* x, const T* u, T* Jx, T* Ju, T a) {
+    Dyn<BK_ORBIT>::jac<T>(x, u, Jx, Ju, a);   // the state Jacobian is the same
+    T su, cu;
+    sincos_t(u[0], &su, &cu);
+    for (int i = 0; i < 4; ++i) Ju[i] = 0;
+    Ju[2] = a * cu;
+    Ju[3] = -a * su;
+  }
+  // state block as BK_ORBIT; the angle adds d2/du2 (mu . f) = -a (mu_vr sin u + mu_vt cos u)
+  template <typename T> __device__ static void hess(const T* x, const T* u, const T* mu, T* H, T a) {
+    T H6[36];
+    Dyn<BK_ORBIT>::hess<T>(x, u, mu, H6, a);
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) H[i * 5 + j] = (i < 4 && j < 4) ? H6[i * 6 + j] : T(0);
+    T su, cu;
+    sincos_t(u[0], &su, &cu);
+    H[24] = -a * (mu[2] * su + mu[3] * cu);
+  }
+  // the angle's Lagrangian curvature a (mu_vr sin u + mu_vt cos u) is bounded by a |mu_v|; the
+  // preconditioner takes that bound plus 1e-3 s w_k (positive where mu_v vanishes)
+  static constexpr bool huu_needs_mu = true;
+  template <typename T> __device__ static T pre_huu(const T* mu, T swk, T a) {
+    return a * sqrt(mu[2] * mu[2] + mu[3] * mu[3]) + T(1e-3) * swk;
   }
 };
 
@@ -130,6 +183,10 @@ struct OpData {
   void* HWc = nullptr;         // n_e control vectors H~^{-1} W, W = Pu^T Z
   void* Qc = nullptr;          // n_e state vectors   Q = P^{-1} Pu H~^{-1} W
   void* Sinv = nullptr;        // n_e x n_e inverse of S = E Q (working type, device)
+  // free final time: the KKT matrix's s column a, q = K-tilde^{-1} a and 1 / (a . q)
+  void* brd = nullptr;         // kkt_len, working type
+  void* brq = nullptr;         // kkt_len, working type
+  double* bgam = nullptr;      // device scalar 1 / (a . q), then per apply the s component
   // temporaries (each n_x * P or (n_x + n_u) * P, working type)
   void* t1 = nullptr;
   void* t2 = nullptr;
@@ -146,6 +203,7 @@ struct Problem {
   int term_idx[NEM] = {0, 0, 0, 0};
   double term_val[NEM] = {0, 0, 0, 0};
   bool has_cost = true;
+  bool free_time = false;      // BK_ORBIT_MT: s = (t_f - t_0)/2 is an unknown, kept at s_idx()
   int nseg = 0;                // sweep segments (level-0 items)
   int nlev = 0;                // scan levels; level nlev - 1 has at most 32 items
   int lvn[MAXLEV] = {};        // items per level
@@ -156,7 +214,15 @@ struct Problem {
   double* red = nullptr;       // reduction scratch (FP64)
   double* red_host = nullptr;  // pinned host mirror of reduction results
   size_t bytes = 0;            // device bytes this problem (and its plans) allocated
+  double* sred = nullptr;      // reduction scratch of the free-time terms (FP64, 2048)
   int64_t kkt_len() const { return (2 * n_x + n_u) * P + 32; }
+  // tail slot of s in a KKT vector (after nu) for a free final time
+  int64_t s_idx() const { return (2 * n_x + n_u) * P + n_e; }
+  // curvature of the running cost in u: |u|^2/2 for the cost-carrying kinds; BK_ORBIT_MT's
+  // cost is the final time
+  double cost_uu() const { return has_cost && !free_time ? 1.0 : 0.0; }
+  // the kind's parameter inside the dynamics (the thrust a of BK_ORBIT_MT)
+  double dyn_param() const { return kind == BK_ORBIT_MT ? params[0] : 0.0; }
   int64_t state_len() const { return n_x * P; }
   OpData& work() { return dtype == BK_F64 ? d64 : d32; }
 };

@@ -4,6 +4,11 @@ import numpy as np
 import torch
 
 
+def _ntail(prob):
+    """Tail entries of a KKT vector: nu, and s for a free final time (right after nu)."""
+    return prob.n_e + (1 if getattr(prob, "free_time", False) else 0)
+
+
 def to_packed(prob, vec, op_kkt=True):
     """Pitched device vector -> packed float64 numpy vector in the oracle's ordering."""
     v = vec.detach().double().cpu().numpy()
@@ -12,7 +17,7 @@ def to_packed(prob, vec, op_kkt=True):
     blocks = [v[b * P:b * P + L] for b in range(nb)]
     out = np.concatenate(blocks)
     if op_kkt:
-        out = np.concatenate([out, v[nb * P:nb * P + prob.n_e]])
+        out = np.concatenate([out, v[nb * P:nb * P + _ntail(prob)]])
     return out
 
 
@@ -24,7 +29,8 @@ def from_packed(prob, x, dtype=torch.float64, op_kkt=True):
     for b in range(nb):
         out[b * P:b * P + L] = torch.as_tensor(x[b * L:(b + 1) * L])
     if op_kkt:
-        out[nb * P:nb * P + prob.n_e] = torch.as_tensor(x[nb * L:nb * L + prob.n_e])
+        nt = _ntail(prob)
+        out[nb * P:nb * P + nt] = torch.as_tensor(x[nb * L:nb * L + nt])
     return out.to(dtype).cuda()
 
 
