@@ -556,7 +556,10 @@ def main():
     if args.sweep:
         line["apply_sweep"] = apply_sweep()
         line["dense_crossover"] = dense_crossover()
-        line["min_time_table"] = min_time_table()
+        try:
+            line["min_time_table"] = min_time_table()
+        except Exception as e:  # the headline line must still print
+            line["min_time_table"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if args.workload.startswith("newton") and args.serve_requests >= 0:
         line["serve"] = run_serve(args.serve_requests or 512, args.serve_slots, rank, world, dist)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
