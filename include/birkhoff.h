@@ -318,6 +318,10 @@ size_t bk_newton_workspace_bytes(const bk_problem* prob, int restart);
  *   ||F||_W^2 = sum_i w_i |c_i|^2 + sum_i |g_i|^2 / w_i + |e|^2  (g: gradient rows).
  *   z_inout    device FP64 KKT vector: initial guess in, solution out (X, U, lambda, nu)
  *   info       host struct, valid on return (synchronous)
+ * BK_ORBIT_MT (free final time): J = t_f - t_0 = 2 s, s is read from and written to z_inout's
+ * tail slot (it must start > 0; trials with s <= 0 are rejected), the residual carries the time
+ * gradient, and the inner tolerance defaults to 1e-12 instead of the forcing term. Start it from
+ * bk_min_time_seed.
  * Returns BK_ERR_NOT_CONVERGED / BK_ERR_INFEASIBLE with z_inout holding the last iterate. */
 bk_status newton_solve(bk_problem* prob, double* z_inout, const bk_newton_opts* opts,
                        bk_newton_info* info, void* workspace, void* stream);
