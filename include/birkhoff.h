@@ -294,6 +294,12 @@ typedef struct {
                          of the last rebuild; 2 keep all preconditioner data (node factors,
                          sweep levels, Schur data). The KKT operator always uses the new
                          linearisation point; flexible GMRES accepts any preconditioner.   */
+  int weighted_inner; /* 1: GMRES minimises the Newton system's residual in the merit's norm
+                         ||.||_W (the system scaled by D = diag(w^-1/2 on gradient rows, w^1/2
+                         on constraint rows, 1 on the tail), preconditioner applied to D^-1 v),
+                         so that every inexact step with relative residual < 1 descends
+                         ||F||_W; 0 (default): the 2-norm. BK_ORBIT_MT then also takes the
+                         forcing term instead of its default 1e-12                           */
 } bk_newton_opts;
 
 typedef struct {

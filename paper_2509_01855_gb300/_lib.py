@@ -48,7 +48,8 @@ class NewtonOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("krylov_rtol", ctypes.c_double), ("restart", ctypes.c_int),
                 ("max_krylov", ctypes.c_int), ("ir_rtol", ctypes.c_double),
-                ("max_refine", ctypes.c_int), ("precond_reuse", ctypes.c_int)]
+                ("max_refine", ctypes.c_int), ("precond_reuse", ctypes.c_int),
+                ("weighted_inner", ctypes.c_int)]
 
 
 class NewtonInfo(ctypes.Structure):

@@ -262,13 +262,15 @@ def newton_workspace(prob, restart=30):
 
 def newton_solve(prob, z, tol=1e-10, max_iter=30, krylov_rtol=0.0, restart=30, max_krylov=0,
                  ir_rtol=1e-10, max_refine=0, precond_reuse=0, workspace=None, stream=None,
-                 raise_on_fail=True):
+                 raise_on_fail=True, weighted_inner=False):
     """Newton-Lagrange solve in place on the FP64 KKT vector z; returns the info fields.
-    Zero-valued options take the library defaults for the problem's precision."""
+    Zero-valued options take the library defaults for the problem's precision;
+    weighted_inner runs the inner GMRES in the merit norm ||.||_W."""
     if workspace is None:
         workspace = newton_workspace(prob, restart)
     opts = L.NewtonOpts(float(tol), int(max_iter), float(krylov_rtol), int(restart),
-                        int(max_krylov), float(ir_rtol), int(max_refine), int(precond_reuse))
+                        int(max_krylov), float(ir_rtol), int(max_refine), int(precond_reuse),
+                        int(bool(weighted_inner)))
     info = L.NewtonInfo()
     st = L.lib().newton_solve(prob.handle, L.ptr(z), ctypes.byref(opts), ctypes.byref(info),
                               L.ptr(workspace), L.stream_ptr(stream))

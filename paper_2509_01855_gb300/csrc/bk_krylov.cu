@@ -247,9 +247,27 @@ size_t gmres_workspace_bytes(int64_t n, int m, int dtype) {
   return b + 1024;
 }
 
+// out = D in (inv = 0) or D^-1 in (inv = 1) for a KKT vector: the first nz blocks (gradient rows)
+// scale by w^-1/2, the next nl blocks (constraint rows) by w^1/2, the tail and padding by 1.
+template <typename T>
+__global__ void k_wscale(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ w, int64_t P,
+                         int64_t L, int nz, int nl, int64_t n, int inv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t blk = i / P, k = i - blk * P;
+    T f = T(1);
+    if (k < L && blk < nz + nl) {
+      const T r = sqrt(w[k]);
+      const bool grad = blk < nz;
+      f = (grad != (inv != 0)) ? T(1) / r : r;
+    }
+    out[i] = f * in[i];
+  }
+}
+
 template <typename T>
 static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, const bk_krylov_opts& o,
-                            bk_krylov_info* info, void* ws, cudaStream_t st, double* hostbuf, const KrylovMu* aux) {
+                            bk_krylov_info* info, void* ws, cudaStream_t st, double* hostbuf, const KrylovMu* aux,
+                            bool weighted) {
   const int64_t n = op == BK_OP_KKT ? pr->kkt_len() : pr->state_len();
   const int m = o.restart;
   const int64_t ld = round_up(n, 64);
@@ -269,9 +287,22 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
   unsigned* cnt = reinterpret_cast<unsigned*>(dvec + 3 * (MAXM + 2));
   BK_TRY_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned), st));
   const int g = grid_for(n);
+  weighted = weighted && op == BK_OP_KKT && o.use_precond;
+  const int wz = pr->n_x + pr->n_u, wl = pr->n_x;
+  auto wscale = [&](const T* in, T* out, int inv) -> bk_status {
+    k_wscale<T><<<g, 256, 0, st>>>(in, out, (const T*)d.w, pr->P, pr->L, wz, wl, n, inv);
+    BK_CHECK_LAUNCH();
+    return BK_OK;
+  };
+  // the right-hand side the iteration sees: D b (weighted) or b
+  const T* bw = b;
+  if (weighted) {
+    BK_TRY(wscale(b, r, 0));
+    bw = r;
+  }
 
   // ||b||
-  BK_TRY(dots<T>(b, ld, 1, b, n, partial, h1, cnt, st));
+  BK_TRY(dots<T>(bw, ld, 1, bw, n, partial, h1, cnt, st));
   BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double), cudaMemcpyDeviceToHost, st));
   BK_TRY_CUDA(cudaStreamSynchronize(st));
   const double bnorm = sqrt(hostbuf[0]);
@@ -290,12 +321,15 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
   while (true) {
     // r = b - A x (x = 0 on the first cycle)
     if (first) {
-      k_axpby<T><<<g, 256, 0, st>>>(b, 1.0, r, 0.0, n);
-      BK_CHECK_LAUNCH();
+      if (!weighted) {  // weighted: r already holds D b
+        k_axpby<T><<<g, 256, 0, st>>>(b, 1.0, r, 0.0, n);
+        BK_CHECK_LAUNCH();
+      }
     } else {
       BK_TRY(op_apply(pr, d, op, x, r, st));
       k_axpby<T><<<g, 256, 0, st>>>(b, 1.0, r, -1.0, n);
       BK_CHECK_LAUNCH();
+      if (weighted) BK_TRY(wscale(r, r, 0));
     }
     double beta = bnorm;  // r = b on the first cycle
     if (!first) {
@@ -317,8 +351,14 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
       T* w = V + (int64_t)(j + 1) * ld;
       if (o.use_precond) {
         T* zj = Zb + (int64_t)j * ld;
-        BK_TRY(op_precond(pr, d, op, vj, zj, 0, st));
+        if (weighted) {
+          BK_TRY(wscale(vj, z, 1));
+          BK_TRY(op_precond(pr, d, op, z, zj, 0, st));
+        } else {
+          BK_TRY(op_precond(pr, d, op, vj, zj, 0, st));
+        }
         BK_TRY(op_apply(pr, d, op, zj, w, st, aux ? (void*)(aux->T + (int64_t)j * aux->ld) : nullptr));
+        if (weighted) BK_TRY(wscale(w, w, 0));
       } else {
         BK_TRY(op_apply(pr, d, op, vj, w, st, aux ? (void*)(aux->T + (int64_t)j * aux->ld) : nullptr));
       }
@@ -393,6 +433,7 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
       BK_TRY(op_apply(pr, d, op, x, r, st));
       k_axpby<T><<<g, 256, 0, st>>>(b, 1.0, r, -1.0, n);
       BK_CHECK_LAUNCH();
+      if (weighted) BK_TRY(wscale(r, r, 0));
       BK_TRY(dots<T>(r, ld, 1, r, n, partial, h1, cnt, st));
       BK_TRY_CUDA(cudaMemcpyAsync(hostbuf, h1, sizeof(double), cudaMemcpyDeviceToHost, st));
       BK_TRY_CUDA(cudaStreamSynchronize(st));
@@ -407,14 +448,14 @@ static bk_status gmres_impl(Problem* pr, OpData& d, int op, const T* b, T* x, co
 }
 
 bk_status gmres(Problem* pr, OpData& d, int op, const void* b, void* x, const bk_krylov_opts& o, bk_krylov_info* info,
-                void* ws, cudaStream_t st, const KrylovMu* aux) {
+                void* ws, cudaStream_t st, const KrylovMu* aux, bool weighted) {
   BK_ARG(o.restart >= 1 && o.restart <= MAXM, "restart must be in [1, %d]", MAXM);
   BK_ARG(o.max_iter >= 1, "max_iter must be >= 1");
   BK_ARG(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be 256-byte aligned");
   BK_ARG(aux == nullptr || (d.dtype == BK_F64 && op == BK_OP_KKT), "transposed-product record needs the FP64 KKT operator");
   if (d.dtype == BK_F64)
-    return gmres_impl<double>(pr, d, op, (const double*)b, (double*)x, o, info, ws, st, pr->red_host, aux);
-  return gmres_impl<float>(pr, d, op, (const float*)b, (float*)x, o, info, ws, st, pr->red_host, nullptr);
+    return gmres_impl<double>(pr, d, op, (const double*)b, (double*)x, o, info, ws, st, pr->red_host, aux, weighted);
+  return gmres_impl<float>(pr, d, op, (const float*)b, (float*)x, o, info, ws, st, pr->red_host, nullptr, weighted);
 }
 
 bk_krylov_opts krylov_defaults() {

@@ -170,7 +170,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     // quadratic outer convergence kept. Floor 1e-12 in FP64, 1e-4 in FP32.
     if (o.krylov_rtol > 0) {
       ko.rtol = o.krylov_rtol;
-    } else if (ft) {
+    } else if (ft && !o.weighted_inner) {
       // Free final time: tight inner solves. GMRES measures its residual in the 2-norm while the
       // merit divides the gradient rows by w (w_0 ~ 1/N^2); on the minimum-time orbit the loose
       // early steps of the forcing term stopped being descent directions of ||F||_W from
@@ -190,7 +190,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     bk_krylov_info ki;
     if (pr->dtype == BK_F64) {
       const KrylovMu aux = {Trec, nxP, Mud, nxP};
-      BK_TRY(gmres(pr, pr->d64, BK_OP_KKT, rhs, d, ko, &ki, gws, st, ft ? nullptr : &aux));
+      BK_TRY(gmres(pr, pr->d64, BK_OP_KKT, rhs, d, ko, &ki, gws, st, ft ? nullptr : &aux, o.weighted_inner != 0));
       info->krylov_iterations += ki.iterations;
       info->kkt_solves += 1;
     } else {
@@ -203,7 +203,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
       for (int sweep = 0; sweep < o.max_refine; ++sweep) {
         k_cast<double, float><<<g, 256, 0, st>>>(r, r32, n);
         BK_CHECK_LAUNCH();
-        BK_TRY(gmres(pr, pr->d32, BK_OP_KKT, r32, d32, ko, &ki, gws, st));
+        BK_TRY(gmres(pr, pr->d32, BK_OP_KKT, r32, d32, ko, &ki, gws, st, nullptr, o.weighted_inner != 0));
         info->krylov_iterations += ki.iterations;
         info->kkt_solves += 1;
         k_acc32<<<g, 256, 0, st>>>(d32, d, n);

@@ -205,3 +205,25 @@ def test_invalid_time_scale_and_seed_mismatch():
         api.min_time_seed(mt, me, me.zeros(), mt.zeros())
     with pytest.raises(BirkhoffError):
         api.Problem(lib.BK_ORBIT_MT, 64, torch.float64, 0.0, T_SEED, (0.0, R_F))
+
+
+def test_weighted_inner_solves():
+    """Inner GMRES in the merit norm (weighted_inner): the forcing term's loose steps then descend
+    ||F||_W. The minimum-energy transfer to r_f = 6 converges with it (the 2-norm forcing term
+    does not, in 30 steps), and the minimum-time solve reaches the tight solve's final time."""
+    api, lib = _api()
+    N = 1 << 12
+    me = api.Problem(lib.BK_ORBIT, N, torch.float64, 0.0, T_SEED, (A_THRUST, R_F))
+    t, _ = api.Plan(N, t0=0.0, tf=T_SEED).grid()
+    X, U = synth.orbit_guess(t.numpy(), R_F, T_SEED)
+    zme = me.pack(X, U)
+    info = api.newton_solve(me, zme, tol=1e-11, weighted_inner=True, max_iter=40)
+    assert info["converged"] and info["iterations"] <= 15, info
+    mt = api.Problem(lib.BK_ORBIT_MT, N, torch.float64, 0.0, T_SEED, (A_THRUST, R_F))
+    z = mt.zeros(dtype=torch.float64)
+    api.min_time_seed(mt, me, zme, z)
+    z_ref = z.clone()
+    ref = api.newton_solve(mt, z_ref, tol=1e-10, max_iter=40)
+    got = api.newton_solve(mt, z, tol=1e-10, max_iter=40, weighted_inner=True)
+    assert ref["converged"] and got["converged"], (ref, got)
+    assert abs(z[mt.s_index].item() - z_ref[mt.s_index].item()) < 1e-9
