@@ -9,6 +9,10 @@ per-node preconditioner factors, terminal Schur data), preconditioned GMRES on t
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
                   [--workload newton_f64|newton_f32ir|apply_f64|apply_f32] [--N 20]
 
+With the default --sweep 1 the line also carries the product sweep (N = 2^10..2^24), the FFT vs
+dense tensor-core crossover, and the minimum-time orbit table (Eq. ot, free final time,
+N = 2^10..2^20: Newton and KKT-solve counts per N, the measure of Table tab:m).
+
 Prints one JSON line on rank 0. With N > 1 (torchrun) every rank solves its own instance
 (replicas; the path has no data-path collective) and the time is the max over ranks.
 --impl reference times the FP64 CPU oracle (test infrastructure) on a bounded sample.
