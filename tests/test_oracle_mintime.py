@@ -133,9 +133,9 @@ def test_seed_zeroes_time_gradient_and_keeps_thrust_direction():
 def test_bordered_preconditioner_eliminates_time_scale():
     """The bordered K-tilde shares the KKT matrix's s row and column, and right-preconditioned
     GMRES on the Newton system converges in a handful of iterations at the seed and at the
-    solution (unpreconditioned it stalls)."""
+    solution; without the border it stalls above the tolerance."""
     import scipy.sparse.linalg as sla
-    K, seed, vec, info = _solve(48)
+    K, seed, vec, info = _solve(64)
     assert info["converged"]
     for v in (seed, vec):
         A = K.matrix(v)
@@ -149,6 +149,16 @@ def test_bordered_preconditioner_eliminates_time_scale():
                             callback=lambda _: its.__setitem__(0, its[0] + 1), callback_type='pr_norm')
         assert flag == 0 and its[0] <= 15
         assert np.linalg.norm(A @ (Mi @ y) - b) <= 1e-9 * np.linalg.norm(b)
+        # the border matters: with the identity in the s slot instead, the true residual stalls
+        # above 1e-10 (near 5e-10 at N = 64), short of the free-time solve's inner tolerance
+        Mu = M.copy()
+        Mu[:, -1] = 0.0
+        Mu[-1, :] = 0.0
+        Mu[-1, -1] = 1.0
+        Mui = np.linalg.inv(Mu)
+        APu = sla.LinearOperator(A.shape, matvec=lambda x: A @ (Mui @ x))
+        yu, _ = sla.gmres(APu, b, rtol=1e-10, restart=30, maxiter=2)
+        assert np.linalg.norm(A @ (Mui @ yu) - b) > 1e-10 * np.linalg.norm(b)
 
 
 # ---- Pontryagin's principle, solved by shooting (independent of the Birkhoff discretisation) --
