@@ -313,6 +313,11 @@ typedef struct {
   int precond_builds;      /* full preconditioner rebuilds (node factors and Schur data)     */
 } bk_newton_info;
 
+/* sizeof of the option and info structs as this library was compiled (which: 0 bk_krylov_opts,
+ * 1 bk_krylov_info, 2 bk_newton_opts, 3 bk_newton_info; 0 for any other value), so that a
+ * binding can check its own layout of them. Host only. */
+size_t bk_abi_struct_size(int which);
+
 /* Workspace bytes newton_solve needs. */
 size_t bk_newton_workspace_bytes(const bk_problem* prob, int restart);
 

@@ -25,7 +25,8 @@ EXPORTS = ["bk_last_error", "bk_version", "bk_launch_count", "bk_plan_create", "
            "bk_plan_dense_state", "bk_plan_dense_check", "bk_plan_shape", "bk_problem_create",
            "bk_problem_destroy", "bk_problem_set_params", "bk_problem_device_bytes", "bk_problem_info", "bk_linearize", "kkt_apply",
            "precond_apply", "bk_krylov_workspace_bytes", "krylov_solve",
-           "bk_newton_workspace_bytes", "newton_solve", "bk_kkt_residual", "bk_min_time_seed"]
+           "bk_newton_workspace_bytes", "newton_solve", "bk_kkt_residual", "bk_min_time_seed",
+           "bk_abi_struct_size"]
 
 
 class BirkhoffError(RuntimeError):
@@ -107,6 +108,7 @@ def lib():
                                  vp, vp]),
         "bk_kkt_residual": (c_int, [vp, vp, vp, ctypes.POINTER(dbl), vp]),
         "bk_min_time_seed": (c_int, [vp, vp, vp, vp, vp]),
+        "bk_abi_struct_size": (ctypes.c_size_t, [c_int]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):

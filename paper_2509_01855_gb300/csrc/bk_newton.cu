@@ -277,6 +277,16 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
 
 extern "C" {
 
+size_t bk_abi_struct_size(int which) {
+  switch (which) {
+    case 0: return sizeof(bk_krylov_opts);
+    case 1: return sizeof(bk_krylov_info);
+    case 2: return sizeof(bk_newton_opts);
+    case 3: return sizeof(bk_newton_info);
+    default: return 0;
+  }
+}
+
 size_t bk_newton_workspace_bytes(const bk_problem* prob, int restart) {
   const bk::Problem* p = reinterpret_cast<const bk::Problem*>(prob);
   if (!p) return 0;

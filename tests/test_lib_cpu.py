@@ -38,6 +38,16 @@ def test_library_builds_and_exports_every_symbol():
     assert L.bk_version().decode().startswith("birkhoff-gb300")
 
 
+def test_binding_struct_layouts_match_the_library():
+    """The ctypes mirrors of the option and info structs have the compiled sizes (a field added
+    on one side only would shift every field after it)."""
+    from paper_2509_01855_gb300 import _lib
+    L = _lib.lib()
+    for which, cls in enumerate([_lib.KrylovOpts, _lib.KrylovInfo, _lib.NewtonOpts, _lib.NewtonInfo]):
+        assert L.bk_abi_struct_size(which) == ctypes.sizeof(cls), cls.__name__
+    assert L.bk_abi_struct_size(99) == 0
+
+
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     from paper_2509_01855_gb300 import _lib
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
