@@ -145,12 +145,13 @@ def _pmp_rhs(t, y, a):
 
 
 def test_mesh_independence_large_N():
-    """Table tab:m in kind: from the same recipe (minimum-energy seed at t_f = 14) the Newton
-    count is the same for N = 2^10, 2^12, 2^14, and the final time agrees with Pontryagin's
-    extremal (shooting, started from the library's costate at t = 0) to 1e-4."""
+    """Table tab:m in kind: from the same recipe (minimum-energy seed at t_f = 24) the Newton
+    count is the same for N = 2^10, 2^12, 2^14 and 2^20, and the final time agrees with
+    Pontryagin's extremal (shooting, started from the library's costate at t = 0): to 1e-4 at
+    2^10, to 1e-9 from 2^12 on (the discrete optimum has converged spectrally there)."""
     api, lib = _api()
     its, T, sol = {}, {}, {}
-    for N in (1 << 10, 1 << 12, 1 << 14):
+    for N in (1 << 10, 1 << 12, 1 << 14, 1 << 20):
         mt, z, info = _mt_solve(api, lib, N)
         assert info["converged"], (N, info)
         its[N] = info["iterations"]
@@ -177,7 +178,7 @@ def test_mesh_independence_large_N():
     v, _, ier, _ = fsolve(res, [p0[0], p0[2], p0[3], T[N]], full_output=True, xtol=1e-13)
     assert ier == 1 and np.abs(res(v)).max() < 1e-10
     for n_, t_ in T.items():
-        assert abs(t_ - v[3]) < 1e-4, (n_, t_, v[3])
+        assert abs(t_ - v[3]) < (1e-4 if n_ < (1 << 12) else 1e-9), (n_, t_, v[3])
 
 
 def test_fp32_inner_solves_reach_fp64_solution():
