@@ -15,14 +15,14 @@ N = 2^10..2^20: Newton and KKT-solve counts per N, the measure of Table tab:m).
 
 Prints one JSON line on rank 0. With N > 1 (torchrun) every rank solves its own instance
 (replicas; the path has no data-path collective) and the time is the max over ranks.
---impl reference times the FP64 CPU oracle (test infrastructure) on a bounded sample.
+--impl reference times the matrix-free FP64 CPU oracle (test infrastructure) on a bounded sample:
+one solve of the same problem at N = 2^12 per step, labelled with the N it ran.
 """
 import argparse
 import hashlib
 import json
 import math
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -52,12 +52,15 @@ def parse():
     ap.add_argument("--workload", default="newton_f64",
                     choices=["newton_f64", "newton_f32ir", "apply_f64", "apply_f32", "serve"])
     ap.add_argument("--serve-requests", type=int, default=0,
-                    help="serving requests (default 4096 for --workload serve, 512 in the default "
-                         "line; -1 skips serving in the default line)")
+                    help="serving requests (default 4096, offered at 0.8 of the closed-loop rate, plus "
+                         "1024 each at 0.5 and 0.95; -1 skips serving in the default line)")
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--N", type=int, default=20, help="log2 of the grid size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", type=int, default=1, help="1 (default): add the apply sweep N=2^10..2^24")
+    ap.add_argument("--profile", action="store_true",
+                    help="apply workloads: after timing, run one more product (L2 flushed first) between "
+                         "cudaProfilerStart and cudaProfilerStop, for ncu --profile-from-start off")
     return ap.parse_args()
 
 
@@ -236,8 +239,8 @@ def run_newton(args, rank, world, dist):
     last = infos[-1]
     err = None
     if dtype == torch.float32:
-        # trajectory error of the FP32-inner solve against an FP64 solve of the same problem
-        # (untimed; the FP64 GPU path itself matches the dense oracle to 1e-9 at small N)
+        # trajectory difference between the FP32-inner solve and an FP64 solve of the same problem
+        # (untimed; tests/test_gpu_fullsize.py compares both with the oracle at this N)
         p64, _ = make_orbit(N, torch.float64)
         z64 = z0.clone()
         api.newton_solve(p64, z64, workspace=api.newton_workspace(p64))
@@ -251,36 +254,40 @@ def run_newton(args, rank, world, dist):
                     "d2h_bytes_per_step": nbytes},
                solve=dict(newton_iterations=last["iterations"], krylov_iterations=last["krylov_iterations"],
                           kkt_solves=last["kkt_solves"], backtracks=last["backtracks"], residual=last["residual"],
-                          error_vs_f64_solve=err))
+                          error_vs_f64_gpu_solve=err))
     return res
 
 
-TRAFFIC_DOC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "birkhoff_apply_N2p20x4_traffic.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 TRANSFORM_SOURCES = ("bk_birkhoff.cu", "bk_fft.cuh", "bk_plan.cuh", "bk_common.cuh")
 
 
-def recorded_traffic(dtype_name, N):
-    """DRAM bytes of one 4-component product at N = 2^20 from the committed ncu summary, or None
-    when N differs or the transform sources changed since that capture (hash check)."""
-    if N != 1 << 20:
-        return None
-    try:
-        text = open(TRAFFIC_DOC).read()
-    except OSError:
-        return None
-    m = re.search(r"traffic_bytes_per_product %s: (\d+)" % dtype_name, text)
-    h = re.search(r"source_sha256_16: ([0-9a-f]{16})", text)
-    if not m or not h:
-        return None
-    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2509_01855_gb300", "csrc")
+def transform_source_hash():
+    """First 16 hex digits of the SHA-256 of the transform sources (in TRANSFORM_SOURCES order)."""
+    csrc = os.path.join(ROOT, "paper_2509_01855_gb300", "csrc")
     sha = hashlib.sha256()
     for f in TRANSFORM_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             sha.update(fh.read())
-    return int(m.group(1)) if sha.hexdigest()[:16] == h.group(1) else None
+    return sha.hexdigest()[:16]
 
 
-def measure_apply(N, dtype, reps=20, trans=False, dense=None):
+def recorded_traffic(dtype_name, N):
+    """DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one 4-component product
+    at N from profiles/traffic.json, or None when no capture exists for (dtype, N) or the
+    transform sources changed since it was taken (source hash check)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = rec.get("%s_2p%d" % (dtype_name, int(math.log2(N))))
+    if not e or e.get("source_sha256_16") != transform_source_hash():
+        return None
+    return int(e["traffic_bytes_per_product"])
+
+
+def measure_apply(N, dtype, reps=20, trans=False, dense=None, profile=False):
     """Birkhoff apply B v (or B^T v) on 4 components, cold L2 between repetitions (CUDA events).
     dense: None keeps the plan's default path; True / False force the tensor-core dense product
     or the FFT chain (FP32, N <= 1024)."""
@@ -309,6 +316,13 @@ def measure_apply(N, dtype, reps=20, trans=False, dense=None):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     ms = statistics.median(times)
+    if profile:
+        flush.zero_()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        fn(plan, v, out)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     es = v.element_size()
     nbytes = 2 * 4 * (N + 1) * es                     # read v, write B v
     flops = 4 * 2 * 2.5 * N * math.log2(N)             # two DCT-I per component
@@ -382,15 +396,23 @@ def min_time_table(lgs=range(10, 21), a=0.05, rf=6.0, t_seed=24.0):
 
 def cpu_apply_baseline(N):
     """The oracle's FastBV chain (SciPy DCT-I, as it stands) on 4 FP64 components at N, on the
-    host cores; one product, so the default run stays short."""
+    host cores with SciPy's FFT on every core and on one; one product each, so the default run
+    stays short."""
+    import scipy.fft
     from oracle import birkhoff as ob
     v = np.random.default_rng(2509_01855).standard_normal((4, N + 1))
-    ob.fastbv(v[:, :1025], 0.0, TF)        # warm-up at N = 1024 (imports, FFT set-up)
-    t0 = time.perf_counter()
-    ob.fastbv(v, 0.0, TF)
-    sec = time.perf_counter() - t0
     nbytes = 2 * 4 * (N + 1) * 8
-    return {"value": nbytes / sec / 1e9, "unit": "GB/s", "ms": 1e3 * sec, "cores": os.cpu_count(), "kind": "oracle",
+    out = {}
+    for workers in (os.cpu_count() or 1, 1):
+        with scipy.fft.set_workers(workers):
+            ob.fastbv(v[:, :1025], 0.0, TF)        # warm-up at N = 1024 (imports, FFT set-up)
+            t0 = time.perf_counter()
+            ob.fastbv(v, 0.0, TF)
+            sec = time.perf_counter() - t0
+        out["cores_%d" % workers] = {"value": nbytes / sec / 1e9, "ms": 1e3 * sec, "cores": workers}
+    best = out["cores_%d" % (os.cpu_count() or 1)]
+    return {"value": best["value"], "unit": "GB/s", "ms": best["ms"], "cores": best["cores"], "kind": "oracle",
+            "single_core": out.get("cores_1"),
             "sample": "oracle FastBV (SciPy DCT-I) on 4 FP64 components at N=2^%d, one product" % int(math.log2(N))}
 
 
@@ -437,47 +459,73 @@ def run_serve(n_requests, slots, rank=0, world=1, dist=None, loads=(0.8,), extra
 # ------------------------------------------------------------------------------------------
 # Oracle legs (CPU)
 # ------------------------------------------------------------------------------------------
-def oracle_newton_sample(N_sample):
-    """The dense FP64 oracle's Newton solve of the same orbit problem at a small N (seconds)."""
+def oracle_matfree_solve(N_sample, workers=1):
+    """One Newton-Krylov solve of the same orbit problem by the matrix-free FP64 oracle (FastBV
+    chain with SciPy's DCT-I, sequential preconditioner sweeps, plain right-preconditioned
+    GMRES) at N_sample, from the same spiral guess. `workers` sets SciPy's FFT threads; the sweeps
+    and the Krylov loop run on one core. Returns (seconds, info)."""
+    import scipy.fft
     from oracle import problems as op
-    from oracle.kkt import DenseKKT
+    from oracle.matfree import MatFreeKKT
     from paper_2509_01855_gb300 import synth
-    K = DenseKKT(op.Problem(op.ORBIT, 0.0, TF, (A_NOM, RF)), N_sample)
-    X, U = synth.orbit_guess(K.t, RF, TF)
-    vec0 = K.pack(X, U, np.zeros((4, K.L)), np.zeros(3))
-    t0 = time.perf_counter()
-    _, info = K.newton(vec0)
-    return time.perf_counter() - t0, info
+    M = MatFreeKKT(op.Problem(op.ORBIT, 0.0, TF, (A_NOM, RF)), N_sample)
+    X, U = synth.orbit_guess(M.t, RF, TF)
+    vec0 = M.pack(X, U, np.zeros((4, M.L)), np.zeros(3))
+    with scipy.fft.set_workers(workers):
+        t0 = time.perf_counter()
+        _, info = M.newton(vec0)
+        sec = time.perf_counter() - t0
+    return sec, info
 
 
-def cpu_baseline(N_sample=1024):
-    sec, info = oracle_newton_sample(N_sample)
-    return {"value": 1.0 / sec, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "dense FP64 oracle Newton solve of the same orbit problem at N=%d (one solve, "
-                      "%d Newton steps, LAPACK dense KKT solves; N=2^20 is out of reach of a dense "
-                      "oracle)" % (N_sample, info["iters"])}
+def cpu_baseline(N_sample=1 << 14):
+    """The matrix-free oracle's solve of the orbit problem at N_sample on the host cores, with
+    SciPy's FFT on every core (cpu_baseline) and on one (cpu_baseline_single_core)."""
+    out = {}
+    ncores = os.cpu_count() or 1
+    for key, workers in (("cpu_baseline", ncores), ("cpu_baseline_single_core", 1)):
+        sec, info = oracle_matfree_solve(N_sample, workers)
+        out[key] = {"value": 1.0 / sec, "unit": "solves/s", "cores": workers, "kind": "oracle",
+                    "N": N_sample, "seconds": sec, "newton_iterations": info["iters"],
+                    "krylov_iterations": int(sum(info["krylov"])),
+                    "sample": "one matrix-free FP64 oracle Newton-Krylov solve (FastBV with SciPy DCT-I on %d "
+                              "FFT worker(s), sequential sweeps, GMRES) of the same orbit problem at N=2^%d; "
+                              "the GPU line's value is for N=2^20" % (workers, int(math.log2(N_sample)))}
+    return out
+
+
+REF_N = 1 << 12
 
 
 def run_reference(args):
+    """Reference arm: the matrix-free FP64 oracle (test infrastructure, as it stands) on the host
+    cores, one Newton-Krylov solve of the orbit problem per step at N = REF_N. The line states
+    the N it ran (not the GPU arm's 2^20)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    N_sample = 256
+    ncores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle_newton_sample(N_sample)
+        oracle_matfree_solve(REF_N, ncores)
     times = []
+    info = None
     for _ in range(args.steps):
-        sec, info = oracle_newton_sample(N_sample)
+        sec, info = oracle_matfree_solve(REF_N, ncores)
         times.append(sec)
     ms = 1000.0 * sum(times) / len(times)
     value = 1000.0 / ms
-    sample = ("dense FP64 oracle Newton solve of the orbit problem at N=%d per step (the bench "
-              "workload is N=2^%d; a dense oracle cannot reach it)" % (N_sample, args.N))
-    line = {"impl": "reference", "metric": metric_name(args), "value": value, "unit": "solves/s",
+    lg = int(math.log2(REF_N))
+    sample = ("one matrix-free FP64 oracle Newton-Krylov solve of the orbit problem at N=2^%d per step "
+              "(%d Newton, %d Krylov iterations; FastBV with SciPy DCT-I on %d FFT workers, sequential "
+              "sweeps); the GPU arm solves N=2^%d" % (lg, info["iters"], int(sum(info["krylov"])), ncores, args.N))
+    cfg = config(args)
+    cfg.update(N=REF_N, nodes=REF_N + 1, parallelism="host cores x%d" % ncores, l2="n/a (CPU)")
+    line = {"impl": "reference", "metric": "Newton-Krylov solve rate at N=2^%d (orbit raising)" % lg,
+            "value": value, "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config(args),
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(),
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": ncores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -537,7 +585,7 @@ def main():
         lib = _lib.lib()
         c0 = lib.bk_launch_count()
         with ClockSampler(torch.cuda.current_device()) as clk:
-            ms, nbytes, flops = measure_apply(N, dt, reps=max(args.steps, 5))
+            ms, nbytes, flops = measure_apply(N, dt, reps=max(args.steps, 5), profile=args.profile)
         line.update(value=world * nbytes / ms / 1e6, unit="GB/s", ms_per_step=ms,
                     gpu_launches=lib.bk_launch_count() - c0, clocks=clk.summary())
     # roofline of the dominant unit: the 4-component Birkhoff apply (four transform passes)
@@ -550,7 +598,7 @@ def main():
         bound = "hbm"
     line["roofline"] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                         "frac": achieved / peak, "traffic": recorded_traffic(dtype_name, N),
-                        "traffic_source": os.path.relpath(TRAFFIC_DOC, os.path.dirname(os.path.abspath(__file__))),
+                        "traffic_source": "profiles/traffic.json",
                         "kernel": "birkhoff_apply N=2^%d x4 components (%s)" % (args.N, dtype_name),
                         "algorithmic": {"bytes": abytes, "flops": aflops},
                         "peak_source": ("FP64 FMA nominal 1.25 TFLOP/s (2 FP64 FMA/clk/SM)" if bound == "alu"
@@ -565,9 +613,10 @@ def main():
         except Exception as e:  # the headline line must still print
             line["min_time_table"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if args.workload.startswith("newton") and args.serve_requests >= 0:
-        line["serve"] = run_serve(args.serve_requests or 512, args.serve_slots, rank, world, dist)
+        line["serve"] = run_serve(args.serve_requests or 4096, args.serve_slots, rank, world, dist,
+                                  loads=(0.8, 0.5, 0.95))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line.update(cpu_baseline())
         line["cpu_apply_baseline"] = cpu_apply_baseline(N)
     if rank == 0:
         print(json.dumps(line), flush=True)

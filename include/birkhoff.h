@@ -115,7 +115,8 @@ bk_status birkhoff_apply(const bk_plan* plan, const void* v, void* out, int batc
  * applications whose own allocator owns the whole GPU. Such callers cannot create a bk_plan,
  * because plan creation allocates its tables and scratch.
  *   v, out     device arrays of nvec FP64 vectors, `pitch` elements apart (caller-owned; the
- *              library allocates nothing); v == out is not allowed
+ *              library allocates nothing); the two ranges (nvec * pitch doubles each) must
+ *              not overlap (BK_ERR_ARG)
  *   N          power of two, 8192 <= N <= 65536;  nvec: 1..8;  pitch >= N + 1, even
  *   t0, tf     time interval (B = s B^a, s = (tf - t0) / 2)
  * The twiddle tables and the transform scratch live in one 16 MiB array that the library

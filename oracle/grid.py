@@ -64,3 +64,16 @@ def cc_weights_sum(N):
     hk = np.ones(N + 1); hk[0] = 0.5; hk[N] = 0.5    # coefficient halving at k = 0, N
     vj = np.ones(N + 1); vj[0] = 0.5; vj[N] = 0.5    # endpoint halving of the nodal sum
     return (2.0 / N) * vj * (Tkj * (hk * intT)[None, :]).sum(axis=1)
+
+
+def interpolate(values, N, xi, chunk=8192):
+    """Values at the points xi of the degree-N interpolant through `values` on the CGL nodes of
+    size N (last axis), by the barycentric formula of ``lagrange_matrix``; xi is processed in
+    chunks so that large targets fit in memory."""
+    values = np.asarray(values, dtype=np.float64)
+    xi = np.asarray(xi, dtype=np.float64)
+    out = np.empty(values.shape[:-1] + (xi.size,))
+    for a in range(0, xi.size, chunk):
+        Lm = lagrange_matrix(N, xi[a:a + chunk])
+        out[..., a:a + chunk] = values @ Lm.T
+    return out

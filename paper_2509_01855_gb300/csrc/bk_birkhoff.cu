@@ -1634,6 +1634,11 @@ bk_status noalloc_apply(const double* v, double* out, int64_t N, int nvec, int64
   BK_ARG(pitch >= N + 1 && pitch % 2 == 0, "pitch must be >= N + 1 and even");
   BK_ARG(tf != t0 && isfinite(t0) && isfinite(tf), "tf must differ from t0 and both be finite");
   BK_ARG(((uintptr_t)v & 15) == 0 && ((uintptr_t)out & 15) == 0, "vectors must be 16-byte aligned");
+  {
+    // the product reads v after it has started writing out: the two ranges must not overlap
+    const uintptr_t vb = (uintptr_t)v, ob = (uintptr_t)out, span = sizeof(double) * (uintptr_t)pitch * nvec;
+    BK_ARG(vb + span <= ob || ob + span <= vb, "v and out overlap");
+  }
   int dev = 0;
   BK_TRY_CUDA(cudaGetDevice(&dev));
   BK_ARG(dev >= 0 && dev < NOALLOC_MAX_DEV, "device index %d not supported", dev);
