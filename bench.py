@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="newton_f64",
-                    choices=["newton_f64", "newton_f32ir", "apply_f64", "apply_f32", "serve"])
+                    choices=["newton_f64", "newton_f32ir", "apply_f64", "apply_f32", "serve", "peaks"])
     ap.add_argument("--serve-requests", type=int, default=0,
                     help="serving requests (default 4096, offered at 0.8 of the closed-loop rate, plus "
                          "1024 each at 0.5 and 0.95; -1 skips serving in the default line)")
@@ -548,10 +548,50 @@ def config(args):
     return c
 
 
+def tensor_rates(n=8192, reps=10):
+    """Diagnostic (--workload peaks): library GEMM rates on this GPU through torch -- FP64
+    (torch.matmul), INT8 with INT32 accumulation (torch._int_mm), TF32 and BF16 -- best of `reps`
+    CUDA-event timings of an n x n x n product. They decide whether an FP64 dense product split
+    into INT8 slices (Ozaki scheme) could beat FP64 on the CUDA cores."""
+    import torch
+    out = {}
+    cases = [("f64", torch.float64), ("tf32", torch.float32), ("bf16", torch.bfloat16), ("int8", torch.int8)]
+    for name, dt in cases:
+        if dt == torch.int8:
+            a = torch.randint(-100, 100, (n, n), dtype=dt, device="cuda")
+            b = torch.randint(-100, 100, (n, n), dtype=dt, device="cuda")
+            fn = lambda: torch._int_mm(a, b)
+        else:
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            fn = lambda: a @ b
+        torch.backends.cuda.matmul.allow_tf32 = name == "tf32"
+        try:
+            for _ in range(2):
+                fn()
+            best = None
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                e1.synchronize()
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+            out[name] = {"ms": best, "tflops": 2.0 * n ** 3 / best / 1e9}
+        except Exception as e:  # an unsupported kind on this build of torch
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+    torch.backends.cuda.matmul.allow_tf32 = False
+    return {"n": n, "rates": out}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "peaks":
+        print(json.dumps({"workload": "peaks", "gemm": tensor_rates()}), flush=True)
         return
     import torch
     rank, world, dist = dist_setup(args)

@@ -8,8 +8,8 @@
  *
  * Conventions shared by every call
  * --------------------------------
- *  - Grid: N is a power of two, 4 <= N <= 2^24, or any N with 4 <= N <= 1024; the L = N + 1
- *    CGL nodes are
+ *  - Grid: N is a power of two, 4 <= N <= 2^24, or any other N with 4 <= N <= 2^22 (BK_F64) or
+ *    2^23 (BK_F32); the L = N + 1 CGL nodes are
  *    tau_j = -cos(j pi / N), ascending (Eq. CGLpts), mapped to t_j = t0 + s (tau_j + 1),
  *    s = (tf - t0) / 2.
  *  - Vectors are device pointers owned by the caller, one length-L block per component,
@@ -68,12 +68,16 @@ uint64_t bk_launch_count(void);
  * ------------------------------------------------------------------------------------------ */
 
 /* Create a plan for Birkhoff products on the CGL grid of size N over [t0, tf].
- *   N          power of two, 4 <= N <= 2^24, or any N in [4, 1024]. A power of two takes the
- *              FFT chain (bk_plan_set_dense switches a plan with N <= 1024 to the dense product:
- *              BK_F32 on the tensor cores, BK_F64 on the CUDA cores);
- *              any other N takes the dense product in both precisions (B^a formed once in FP64
- *              from its definition: Chebyshev coefficients of the Lagrange basis times the
- *              closed-form integrals of T_k, Eq. intChebPoly=)
+ *   N          power of two, 4 <= N <= 2^24, or any other N in [4, 2^22] (BK_F64) / [4, 2^23]
+ *              (BK_F32). A power of two takes the FFT chain (bk_plan_set_dense switches a plan
+ *              with N <= 1024 to the dense product: BK_F32 on the tensor cores, BK_F64 on the
+ *              CUDA cores); any other N <= 1024 takes the dense product in both precisions (B^a
+ *              formed once in FP64 from its definition: Chebyshev coefficients of the Lagrange
+ *              basis times the closed-form integrals of T_k, Eq. intChebPoly=); any other
+ *              N > 1024 computes each DCT-I's length-N DFT by Bluestein's identity as a circular
+ *              convolution of length M (a power of two, M >= 2N - 1) on the four-step FFT, with
+ *              the chirp exp(-i pi j^2 / N) and the convolution kernel's spectrum as plan tables
+ *              (about 4-8x the work of the nearest power of two)
  *   n_comp     components per batch item (>= 1)
  *   max_batch  largest `batch` later passed to birkhoff_apply / birkhoff_apply_T (>= 1); the
  *              plan's scratch is sized for max_batch * n_comp vectors
@@ -148,7 +152,8 @@ bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int ba
 bk_status bk_plan_set_dense(bk_plan* plan, int on, void* stream);
 
 /* How a plan computes its products. *path: 0 one CTA per vector (small N), 1 four-step FFT,
- * 2 four-step with the split DCT-I, 3 dense tensor-core product. For paths 1 and 2: the FFT
+ * 2 four-step with the split DCT-I, 3 dense product, 4 Bluestein convolution (N not a power of
+ * two above 1024). For paths 1 and 2: the FFT
  * factors N1 x N2 of the (even-half) transform and the complex elements per CTA, as chosen by
  * the tile autotuner at plan creation (or by the occupancy heuristic when tuning is off:
  * environment BK_AUTOTUNE=0). Outputs may be NULL. */
@@ -160,9 +165,36 @@ bk_status bk_plan_shape(const bk_plan* plan, int* path, int* N1, int* N2, int* e
  * n_comp * max_batch <= 16). */
 bk_status bk_plan_dense_state(const bk_plan* plan, int* on);
 
+/* Arithmetic of the FP64 transforms for plans (and problems) created after the call:
+ *   mode 1: four-step FP64 plans (powers of two, N >= 256) compute their DCTs in double-float
+ *           arithmetic, each value the unevaluated sum of two binary32 numbers (48 significand
+ *           bits; Knuth's TwoSum, Dekker's FastTwoSum and an FMA product), on the FP32 pipe,
+ *           which GB300 runs 64 times as fast as its FP64 pipe. Vectors stay binary64 in
+ *           memory. Products agree with binary64 ones to ~1e-14 relative (2-norm).
+ *   mode 0: IEEE binary64 arithmetic throughout.
+ *   mode -1 (the default): double-float for N >= 2^18, where it measured faster (1.8x at
+ *           2^20), binary64 below (the environment variable BK_F64_DF=0 selects mode 0).
+ * Single-CTA plans (N <= 128) and dense products always use binary64. Host only; BK_ERR_ARG for
+ * any other mode. This is the library's choice of arithmetic; the paper's method is exact FP64. */
+bk_status bk_set_f64_transform(int mode);
+
+/* *mode = 1 when the plan's transforms use double-float arithmetic, else 0. */
+bk_status bk_plan_f64_mode(const bk_plan* plan, int* mode);
+
+/* Test mode of the dense tensor-core product (BK_F32 plans on the dense path): while on = 1,
+ * every product first makes one bounded wait on a barrier that nothing signals (1024 polls),
+ * takes the kernel's timeout path (drains its copies in flight, frees its tensor memory, writes
+ * the error word) and leaves its output invalid. For tests of the failure path: the error word
+ * reaches bk_plan_dense_check, and krylov_solve / newton_solve on a dense problem return
+ * BK_ERR_TIMEOUT. Plans created while the environment variable BK_DENSE_TEST_TIMEOUT=1 is set
+ * (problems' plans included) start in this mode. The paper has no counterpart. */
+bk_status bk_plan_dense_test_timeout(bk_plan* plan, int on);
+
 /* Read (and clear) the dense kernel's error word: *err = 0 when every dense product so far
  * completed; otherwise a wait inside the kernel ran out (1: operand copy or MMA completion,
- * 2: accumulator read) and that product's output is not valid. Synchronous (device sync). */
+ * 2: accumulator read) and that product's output is not valid. Synchronous (device sync).
+ * krylov_solve and newton_solve read the same word of their problem's plans before returning
+ * and fail with BK_ERR_TIMEOUT when it is set. */
 bk_status bk_plan_dense_check(const bk_plan* plan, int* err);
 
 /* ------------------------------------------------------------------------------------------

@@ -22,7 +22,9 @@ STATUS = {0: "BK_OK", 1: "BK_ERR_ARG", 2: "BK_ERR_CUDA", 3: "BK_ERR_OOM",
 # Symbols declared in include/birkhoff.h (checked by the CPU test suite).
 EXPORTS = ["bk_last_error", "bk_version", "bk_launch_count", "bk_plan_create", "bk_plan_destroy", "bk_plan_info",
            "bk_plan_grid", "birkhoff_apply", "birkhoff_apply_T", "birkhoff_apply_noalloc", "bk_plan_set_dense",
-           "bk_plan_dense_state", "bk_plan_dense_check", "bk_plan_shape", "bk_problem_create",
+           "bk_plan_dense_state", "bk_plan_dense_check", "bk_plan_shape", "bk_set_f64_transform", "bk_plan_f64_mode",
+           "bk_plan_dense_test_timeout",
+           "bk_problem_create",
            "bk_problem_destroy", "bk_problem_set_params", "bk_problem_device_bytes", "bk_problem_info", "bk_linearize", "kkt_apply",
            "precond_apply", "bk_krylov_workspace_bytes", "krylov_solve",
            "bk_newton_workspace_bytes", "newton_solve", "bk_kkt_residual", "bk_min_time_seed",
@@ -87,6 +89,9 @@ def lib():
         "bk_plan_set_dense": (c_int, [vp, c_int, vp]),
         "bk_plan_dense_check": (c_int, [vp, ctypes.POINTER(c_int)]),
         "bk_plan_dense_state": (c_int, [vp, ctypes.POINTER(c_int)]),
+        "bk_set_f64_transform": (c_int, [c_int]),
+        "bk_plan_f64_mode": (c_int, [vp, ctypes.POINTER(c_int)]),
+        "bk_plan_dense_test_timeout": (c_int, [vp, c_int]),
         "bk_plan_shape": (c_int, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                   ctypes.POINTER(c_int)]),
         "bk_problem_create": (c_int, [ctypes.POINTER(vp), c_int, ctypes.POINTER(dbl), c_int, i64,

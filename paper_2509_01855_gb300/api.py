@@ -55,10 +55,11 @@ class Plan:
         L.check(L.lib().bk_plan_set_dense(self._h, 1 if on else 0, L.stream_ptr(stream)))
 
     def shape(self):
-        """{"path": "single_cta" | "four_step" | "split_four_step" | "dense", "N1", "N2", "elems"}."""
+        """{"path": "single_cta" | "four_step" | "split_four_step" | "dense" | "bluestein", "N1", "N2",
+        "elems"}."""
         v = [ctypes.c_int(0) for _ in range(4)]
         L.check(L.lib().bk_plan_shape(self._h, *[ctypes.byref(x) for x in v]))
-        names = ("single_cta", "four_step", "split_four_step", "dense")
+        names = ("single_cta", "four_step", "split_four_step", "dense", "bluestein")
         return {"path": names[v[0].value], "N1": v[1].value, "N2": v[2].value, "elems": v[3].value}
 
     def is_dense(self):
@@ -66,6 +67,12 @@ class Plan:
         on = ctypes.c_int(0)
         L.check(L.lib().bk_plan_dense_state(self._h, ctypes.byref(on)))
         return bool(on.value)
+
+    def f64_mode(self):
+        """1 when the plan's FP64 transforms run in double-float arithmetic, else 0."""
+        m = ctypes.c_int(0)
+        L.check(L.lib().bk_plan_f64_mode(self._h, ctypes.byref(m)))
+        return m.value
 
     def dense_check(self):
         """Error word of the dense kernel since the last check (0: every product completed)."""
@@ -87,6 +94,12 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def set_f64_transform(mode):
+    """Arithmetic of FP64 transforms for plans and problems created afterwards: 1 double-float,
+    0 binary64, -1 the default (double-float from N = 2^18 on)."""
+    L.check(L.lib().bk_set_f64_transform(int(mode)))
 
 
 def _check_vec(plan, t, batch):

@@ -15,8 +15,8 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-DNDEBUG"]
-SOURCES = ["bk_birkhoff.cu", "bk_birkhoff_f64.cu", "bk_birkhoff_f32.cu", "bk_dense.cu", "bk_kkt.cu", "bk_krylov.cu",
-           "bk_newton.cu"]
+SOURCES = ["bk_birkhoff.cu", "bk_birkhoff_f64.cu", "bk_birkhoff_f32.cu", "bk_birkhoff_df.cu", "bk_dense.cu",
+           "bk_kkt.cu", "bk_krylov.cu", "bk_newton.cu"]
 
 
 def _nvcc():
@@ -44,8 +44,8 @@ def build(verbose=False, force=False):
         sp = os.path.join(CSRC, src)
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(obj)
-        deps = headers + ([os.path.join(CSRC, "bk_birkhoff.cu")] if src in ("bk_birkhoff_f64.cu", "bk_birkhoff_f32.cu")
-                          else [])
+        deps = headers + ([os.path.join(CSRC, "bk_birkhoff.cu")]
+                          if src in ("bk_birkhoff_f64.cu", "bk_birkhoff_f32.cu", "bk_birkhoff_df.cu") else [])
         if force or _needs(obj, sp, deps):
             jobs.append([nvcc] + ARCH + FLAGS + ["-c", sp, "-o", obj])
 

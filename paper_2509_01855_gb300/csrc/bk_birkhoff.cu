@@ -39,6 +39,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <string>
 
 #include "bk_common.cuh"
@@ -46,6 +47,29 @@
 #include "bk_plan.cuh"
 
 namespace bk {
+
+// The kernels compute in T and keep their internal real vectors (the stage buffers between the
+// two DCTs) in T; the caller's vectors are User<T> (binary64 for double-float arithmetic, whose
+// products convert the input once in k_to_arith and the output in the last epilogue).
+template <typename T> using St = T;
+template <typename T> using Us = typename User<T>::t;
+// Conversion of a stored element S to the arithmetic type T and back (identity when S == T).
+template <typename T, typename S> struct Cv;
+template <typename T> struct Cv<T, T> {
+  static __device__ __forceinline__ T in(T x) { return x; }
+  static __device__ __forceinline__ T out(T x) { return x; }
+};
+template <> struct Cv<dfl, double> {
+  static __device__ __forceinline__ dfl in(double x) { return d2df(x); }
+  static __device__ __forceinline__ double out(dfl x) { return df2d(x); }
+};
+// Pass-B output type: the caller's type for the final epilogues, T for the stage buffer.
+template <typename T, int E> struct OutS {
+  typedef typename std::conditional<(E == 2 || E == 3), Us<T>, T>::type t;
+};
+template <typename T, typename S> __device__ __forceinline__ T rdv(const S* __restrict__ p, int64_t i) {
+  return Cv<T, S>::in(p[i]);
+}
 
 #ifndef BK_TRANSFORM_KERNEL_UNIT  // one definition of the library's globals, in the main unit
 // (bk_birkhoff_f64.cu and bk_birkhoff_f32.cu include this file for the transform kernels only)
@@ -146,6 +170,30 @@ __global__ void k_rk_table(T* rk, int64_t n) {
     rk[k] = k == 0 ? T(0) : (T)(1.0 / (4.0 * (double)k));
 }
 
+// Bluestein chirp w_j = exp(-i pi j^2 / N) = (cos, -sin)(pi r / N), r = j^2 mod 2N in integers.
+template <typename T>
+__global__ void k_chirp(typename V2<T>::t* w, int64_t N) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = (j * j) % (2 * N);
+    double sn, cs;
+    sincospi((double)r / (double)N, &sn, &cs);
+    w[j] = mk2<T>((T)cs, (T)(-sn));
+  }
+}
+
+// The convolution kernel b of Bluestein's identity, scaled by 1/M, as M complex values (real
+// pairs): b_m = conj(w_m) for m < N, b_{M-m} = conj(w_m) for 0 < m < N, zero between.
+template <typename T>
+__global__ void k_bs_kernel(T* b, int64_t N, int64_t M) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = m < N ? m : (m > M - N ? M - m : -1);
+    double sn = 0.0, cs = 0.0;
+    if (j >= 0) sincospi((double)((j * j) % (2 * N)) / (double)N, &sn, &cs);
+    b[2 * m] = (T)(cs / (double)M);
+    b[2 * m + 1] = (T)(sn / (double)M);
+  }
+}
+
 #ifndef BK_TRANSFORM_KERNEL_UNIT
 __global__ void k_grid_tables(double* t_nodes, int64_t N, double t0, double s) {
   // tau_j = -cos(j pi / N) = sin(pi (2j - N) / (2N)) (Eq. CGLpts), t_j = t0 + s (tau_j + 1)
@@ -171,37 +219,38 @@ __global__ void k_grid_tables(double* t_nodes, int64_t N, double t0, double s) {
 enum { IN_PLAIN = 0, IN_WINV = 1, ST_FWD = 2, ST_TRN = 3 };
 
 // rk[k] = 1 / (4k) for 1 <= k <= N + 1 (plan table): the stencils multiply instead of divide.
-template <typename T>
-__device__ __forceinline__ T stencil_fwd(const T* __restrict__ Y, int m, int N, T invN, const T* __restrict__ rk) {
+template <typename T, typename S>
+__device__ __forceinline__ T stencil_fwd(const S* __restrict__ Y, int m, int N, T invN, const T* __restrict__ rk) {
   // g_m = chat'_m / 2 for 0 < m < N, g_N = chat'_N, g_0 = 0 (see the file comment). invN is 1/N,
   // or 1 where Y was stored already divided by N.
   if (m == 0) return T(0);
-  if (m == N) return -Y[N - 1] * (invN * T(2) * rk[N]);
-  if (m == 1) return (Y[2] - Y[0]) * (invN * T(0.25));
+  if (m == N) return -rdv<T>(Y, N - 1) * (invN * T(2) * rk[N]);
+  if (m == 1) return (rdv<T>(Y, 2) - rdv<T>(Y, 0)) * (invN * T(0.25));
   if (m == N - 1) {
-    const T yN = Y[N];
-    return (T(0.5) * yN - Y[N - 2]) * (invN * rk[N - 1]) - yN * (invN * T(0.5) * rk[N + 1]);
+    const T yN = rdv<T>(Y, N);
+    return (T(0.5) * yN - rdv<T>(Y, N - 2)) * (invN * rk[N - 1]) - yN * (invN * T(0.5) * rk[N + 1]);
   }
-  return (Y[m + 1] - Y[m - 1]) * (invN * rk[m]);
+  return (rdv<T>(Y, m + 1) - rdv<T>(Y, m - 1)) * (invN * rk[m]);
 }
 
-template <typename T>
-__device__ __forceinline__ T stencil_trn(const T* __restrict__ Q, int m, int N, T Y0, const T* __restrict__ rk,
+template <typename T, typename S>
+__device__ __forceinline__ T stencil_trn(const S* __restrict__ Qs, int m, int N, T Y0, const T* __restrict__ rk,
                                          T cN) {
+  auto Q = [&](int i) { return rdv<T>(Qs, i); };
   // r = W (Y - Y0); t = G^T r; return t_m / W_m. G^T rows:
   //   t_0 = -r_1/4, t_1 = -r_2/8, t_j = r_{j-1}/(4(j-1)) - r_{j+1}/(4(j+1)) (2<=j<=N-2),
   //   t_{N-1} = r_{N-2}/(4(N-2)) - r_N/(2N), t_N = r_{N-1}/(4(N^2-1)).
   // r_k = 2 (Y_k - Y0) for 0 < k < N, r_0 = Y_0 - Y0 = 0, r_N = Y_N - Y0.
   // cN = 1 / (4 (N^2 - 1))
-  if (m == 0) return -(T(2) * (Q[1] - Y0)) * T(0.25);
-  if (m == N) return (T(2) * (Q[N - 1] - Y0)) * cN;
+  if (m == 0) return -(T(2) * (Q(1) - Y0)) * T(0.25);
+  if (m == N) return (T(2) * (Q(N - 1) - Y0)) * cN;
   T t;
   if (m == 1) {
-    t = -(T(2) * (Q[2] - Y0)) * T(0.125);
+    t = -(T(2) * (Q(2) - Y0)) * T(0.125);
   } else if (m == N - 1) {
-    t = (T(2) * (Q[N - 2] - Y0)) * rk[N - 2] - (Q[N] - Y0) * (T(2) * rk[N]);
+    t = (T(2) * (Q(N - 2) - Y0)) * rk[N - 2] - (Q(N) - Y0) * (T(2) * rk[N]);
   } else {
-    t = (Q[m - 1] - Y0) * rk[m - 1] - (Q[m + 1] - Y0) * rk[m + 1];
+    t = (Q(m - 1) - Y0) * rk[m - 1] - (Q(m + 1) - Y0) * rk[m + 1];
     return t;
   }
   return T(0.5) * t;
@@ -215,17 +264,17 @@ template <typename T> struct StencilTab {
   T cN;         // 1/(4(N^2 - 1))
 };
 
-template <typename T, int K>
-__device__ __forceinline__ T load_x(const T* __restrict__ src, int m, int N, T invN, T Y0, StencilTab<T> tb) {
-  if (K == IN_PLAIN) return src[m];
-  if (K == IN_WINV) return (m == 0 || m == N) ? src[m] : T(0.5) * src[m];
+template <typename T, int K, typename S>
+__device__ __forceinline__ T load_x(const S* __restrict__ src, int m, int N, T invN, T Y0, StencilTab<T> tb) {
+  if (K == IN_PLAIN) return rdv<T>(src, m);
+  if (K == IN_WINV) return (m == 0 || m == N) ? rdv<T>(src, m) : T(0.5) * rdv<T>(src, m);
   if (K == ST_FWD) return stencil_fwd<T>(src, m, N, invN, tb.rk);
   return stencil_trn<T>(src, m, N, Y0, tb.rk, tb.cN);
 }
 
 // z_j = x_ext[2j] + i x_ext[2j+1]
-template <typename T, int K>
-__device__ __forceinline__ typename V2<T>::t load_z(const T* __restrict__ src, int j, int N, T invN,
+template <typename T, int K, typename S>
+__device__ __forceinline__ typename V2<T>::t load_z(const S* __restrict__ src, int j, int N, T invN,
                                                     T Y0, StencilTab<T> tb) {
   const int m1 = 2 * j, m2 = 2 * j + 1;
   const int i1 = m1 <= N ? m1 : 2 * N - m1;
@@ -250,17 +299,18 @@ __device__ __forceinline__ typename V2<T>::t load_z(const T* __restrict__ src, i
 // N/2 + N/4. The pair sums a are formed on the fly from x in the loads:
 //   PM_PAIR2 : z_j of the length-Q DCT-I of aa (n = Q)
 //   PM_DCT3A : conj Z_k (k < n = Q/2) of the DCT-III of u' (as PM_DCT3, on a)
-enum { PM_FULL = 0, PM_PAIR = 1, PM_DCT3 = 2, PM_PAIR2 = 3, PM_DCT3A = 4 };
+//   PM_CPLX  : a plain complex vector (pairs of reals) of length n (Bluestein's convolution)
+enum { PM_FULL = 0, PM_PAIR = 1, PM_DCT3 = 2, PM_PAIR2 = 3, PM_DCT3A = 4, PM_CPLX = 5 };
 
-template <typename T, int K>
-__device__ __forceinline__ T pair_sum(const T* __restrict__ src, int i, int Ns) {
+template <typename T, int K, typename S>
+__device__ __forceinline__ T pair_sum(const S* __restrict__ src, int i, int Ns) {
   // a_i = x_i + x_{Ns-i}; IN_WINV halves interior samples (i = 0 pairs the two end samples)
-  const T a = src[i] + src[Ns - i];
+  const T a = rdv<T>(src, i) + rdv<T>(src, Ns - i);
   return (K == IN_WINV && i != 0) ? T(0.5) * a : a;
 }
 
-template <typename T, int K>
-__device__ __forceinline__ typename V2<T>::t load_z_pair(const T* __restrict__ src, int j, int n, StencilTab<T> tb) {
+template <typename T, int K, typename S>
+__device__ __forceinline__ typename V2<T>::t load_z_pair(const S* __restrict__ src, int j, int n, StencilTab<T> tb) {
   const int Ns = 2 * n;
   const int m1 = 2 * j, m2 = 2 * j + 1;
   const int i1 = m1 <= n ? m1 : 2 * n - m1;
@@ -271,19 +321,19 @@ __device__ __forceinline__ typename V2<T>::t load_z_pair(const T* __restrict__ s
 // H_k of the DCT-III input (see above), with the factors folded: for k >= 1 every sample is an
 // interior one, so H_k = c e^{i theta k} ((x_k - x_{N-k}) - i (x_{M-k} - x_{M+k})) with c = 1
 // (IN_PLAIN) or 1/2 (IN_WINV halves interior samples); H_0 = u_0 = W-scaled x_0 - x_N.
-template <typename T, int K>
-__device__ __forceinline__ typename V2<T>::t dct3_H(const T* __restrict__ src, int i, int M,
+template <typename T, int K, typename S>
+__device__ __forceinline__ typename V2<T>::t dct3_H(const S* __restrict__ src, int i, int M,
                                                    const typename V2<T>::t* __restrict__ tpost) {
   const int N = 2 * M;
-  if (i == 0) return mk2<T>(src[0] - src[N], T(0));
-  const T a = src[i] - src[N - i], b = src[M - i] - src[M + i];
+  if (i == 0) return mk2<T>(rdv<T>(src, 0) - rdv<T>(src, N), T(0));
+  const T a = rdv<T>(src, i) - rdv<T>(src, N - i), b = rdv<T>(src, M - i) - rdv<T>(src, M + i);
   typename V2<T>::t cs = tpost[i];  // (cos, sin)(pi i / N)
   if (K == IN_WINV) { cs.x *= T(0.5); cs.y *= T(0.5); }
   return mk2<T>(a * cs.x + b * cs.y, a * cs.y - b * cs.x);
 }
 
-template <typename T, int K>
-__device__ __forceinline__ typename V2<T>::t load_z_dct3(const T* __restrict__ src, int k, int n,
+template <typename T, int K, typename S>
+__device__ __forceinline__ typename V2<T>::t load_z_dct3(const S* __restrict__ src, int k, int n,
                                                         const typename V2<T>::t* __restrict__ tpost,
                                                         const typename V2<T>::t* __restrict__ eo, StencilTab<T> tb) {
   typedef typename V2<T>::t C;
@@ -298,8 +348,8 @@ __device__ __forceinline__ typename V2<T>::t load_z_dct3(const T* __restrict__ s
 }
 
 // z_j of the length-Q DCT-I of aa (n = Q, x of length 4Q + 1): aa_i = a_i + a_{2Q-i}.
-template <typename T, int K>
-__device__ __forceinline__ typename V2<T>::t load_z_pair2(const T* __restrict__ src, int j, int n) {
+template <typename T, int K, typename S>
+__device__ __forceinline__ typename V2<T>::t load_z_pair2(const S* __restrict__ src, int j, int n) {
   const int Nf = 4 * n, M = 2 * n;
   const int m1 = 2 * j, m2 = 2 * j + 1;
   const int i1 = m1 <= n ? m1 : 2 * n - m1;
@@ -311,8 +361,8 @@ __device__ __forceinline__ typename V2<T>::t load_z_pair2(const T* __restrict__ 
 // H_k of the DCT-III of length Q of u' (pair differences of a, x of length 4Q + 1): as dct3_H on
 // a with theta = pi / (2Q), (cos, sin)(pi i / (2Q)) = tpost[2i]; a carries the W^{-1} scaling of
 // IN_WINV already, so the factor c is 1.
-template <typename T, int K>
-__device__ __forceinline__ typename V2<T>::t dct3_H_pairs(const T* __restrict__ src, int i, int Q,
+template <typename T, int K, typename S>
+__device__ __forceinline__ typename V2<T>::t dct3_H_pairs(const S* __restrict__ src, int i, int Q,
                                                          const typename V2<T>::t* __restrict__ tpost) {
   const int M = 2 * Q, Nf = 4 * Q;
   if (i == 0) return mk2<T>(pair_sum<T, K>(src, 0, Nf) - pair_sum<T, K>(src, M, Nf), T(0));
@@ -322,8 +372,8 @@ __device__ __forceinline__ typename V2<T>::t dct3_H_pairs(const T* __restrict__ 
   return mk2<T>(a * cs.x + b * cs.y, a * cs.y - b * cs.x);
 }
 
-template <typename T, int K>
-__device__ __forceinline__ typename V2<T>::t load_z_dct3a(const T* __restrict__ src, int k, int n,
+template <typename T, int K, typename S>
+__device__ __forceinline__ typename V2<T>::t load_z_dct3a(const S* __restrict__ src, int k, int n,
                                                          const typename V2<T>::t* __restrict__ tpost,
                                                          const typename V2<T>::t* __restrict__ eo) {
   typedef typename V2<T>::t C;
@@ -368,7 +418,7 @@ __device__ void dct1_block(const T* __restrict__ X, int kind, T* __restrict__ Y,
   }
   __syncthreads();
   if (N >= 16) {
-    fft16<T>(buf, N, log2N, 1, pad_stride(N), stw);
+    fft16_any<T>(buf, N, log2N, 1, pad_stride(N), stw);
   } else {
     // N = 4 or 8: direct DFT (tw holds omega_N^i, n_tab = N)
     C zk = mk2<T>(T(0), T(0));
@@ -401,7 +451,7 @@ template <typename T> struct InFlight { static constexpr int v = sizeof(T) == 8 
 
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(MaxThr<T>::v)
-    k_birkhoff_small(const T* __restrict__ in, T* __restrict__ out, int N, int log2N, int64_t pitch,
+    k_birkhoff_small(const Us<T>* __restrict__ in, Us<T>* __restrict__ out, int N, int log2N, int64_t pitch,
                      T s, const typename V2<T>::t* __restrict__ tw, const typename V2<T>::t* __restrict__ stw,
                      const typename V2<T>::t* __restrict__ tpost, StencilTab<T> tb) {
   typedef typename V2<T>::t C;
@@ -412,25 +462,26 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
   T* Y = X + Lp;
   C* buf = reinterpret_cast<C*>(Y + Lp);
   const int64_t base = (int64_t)blockIdx.x * pitch;
-  const T* src = in + base;
-  T* dst = out + base;
-  const T invN = T(1) / T(N);
-  for (int m = threadIdx.x; m < L; m += blockDim.x) X[m] = src[m];
+  const Us<T>* src = in + base;
+  Us<T>* dst = out + base;
+  typedef Cv<T, Us<T>> CV;
+  const T invN = T(1.0 / (double)N);
+  for (int m = threadIdx.x; m < L; m += blockDim.x) X[m] = CV::in(src[m]);
   __syncthreads();
   if (!TRANS) {
     dct1_block<T>(X, IN_PLAIN, Y, buf, N, log2N, tw, stw, tpost, invN, T(0), tb);
     dct1_block<T>(Y, ST_FWD, X, buf, N, log2N, tw, stw, tpost, invN, T(0), tb);
     const T y0 = X[0];
-    for (int m = threadIdx.x; m < L; m += blockDim.x) dst[m] = s * (X[m] - y0);
+    for (int m = threadIdx.x; m < L; m += blockDim.x) dst[m] = CV::out(s * (X[m] - y0));
   } else {
     dct1_block<T>(X, IN_WINV, Y, buf, N, log2N, tw, stw, tpost, invN, T(0), tb);
     const T y0 = Y[0];
     dct1_block<T>(Y, ST_TRN, X, buf, N, log2N, tw, stw, tpost, invN, y0, tb);
     const T sN = s * invN;
     for (int m = threadIdx.x; m < L; m += blockDim.x)
-      dst[m] = (m == 0 || m == N) ? sN * X[m] : T(2) * sN * X[m];
+      dst[m] = CV::out((m == 0 || m == N) ? sN * X[m] : T(2) * sN * X[m]);
   }
-  for (int m = L + threadIdx.x; m < pitch; m += blockDim.x) dst[m] = T(0);
+  for (int m = L + threadIdx.x; m < pitch; m += blockDim.x) dst[m] = Us<T>(0);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -442,7 +493,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
 // ---------------------------------------------------------------------------------------------
 template <typename T, int K, int MODE>
 __device__ __forceinline__ void passA_body(
-            int bid, int nbid, const T* __restrict__ src, int64_t src_stride, typename V2<T>::t* __restrict__ Aout,
+            int bid, int nbid, const St<T>* __restrict__ src, int64_t src_stride, typename V2<T>::t* __restrict__ Aout,
             T* __restrict__ partial, int N, int N1, int log2N1, int N2, int NB, int bs,
             const typename V2<T>::t* __restrict__ stw,
             const typename V2<T>::t* __restrict__ twN, T invN, StencilTab<T> tb,
@@ -458,7 +509,7 @@ __device__ __forceinline__ void passA_body(
   if (smem_tw) load_tw_smem<T>(tws, stw, stage_tw_len(log2N1));
   __shared__ T red[32];
   const int vec = blockIdx.y;
-  const T* x = src + (int64_t)vec * src_stride;
+  const St<T>* x = src + (int64_t)vec * src_stride;
   const int c0 = bid * NB;
   const int log2NB = __ffs(NB) - 1, log2N2 = __ffs(N2) - 1;  // NB, N2 are powers of two
   // The stage buffer read by the second DCT already holds Y / N (forward) or Y - Y0
@@ -481,6 +532,7 @@ __device__ __forceinline__ void passA_body(
         const int b = idx & (NB - 1);
         const int j = ((idx >> log2NB) << log2N2) + c0 + b;
         if (MODE == PM_FULL) z[u] = load_z<T, K>(x, j, N, sc, Y0, tb);
+        else if (MODE == PM_CPLX) z[u] = mk2<T>(x[2 * (int64_t)j], x[2 * (int64_t)j + 1]);
         else if (MODE == PM_PAIR) z[u] = load_z_pair<T, K>(x, j, N, tb);
         else if (MODE == PM_PAIR2) z[u] = load_z_pair2<T, K>(x, j, N);
         else if (MODE == PM_DCT3A) z[u] = load_z_dct3a<T, K>(x, j, N, tpost, eo);
@@ -498,16 +550,16 @@ __device__ __forceinline__ void passA_body(
   }
   if (DC) {
     // block reduction of dc (deterministic order)
-    for (int o = 16; o > 0; o >>= 1) dc += __shfl_xor_sync(0xffffffffu, dc, o);
+    for (int o = 16; o > 0; o >>= 1) dc += shfl_xor(dc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dc;
   }
   __syncthreads();
   if (DC && threadIdx.x < 32) {
     T a = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    for (int o = 16; o > 0; o >>= 1) a += shfl_xor(a, o);
     if (threadIdx.x == 0) partial[(int64_t)vec * nbid + bid] = a;
   }
-  fft16<T>(buf, N1, log2N1, NB, bs, smem_tw ? tws : stw);
+  fft16_any<T>(buf, N1, log2N1, NB, bs, smem_tw ? tws : stw);
   C* A = Aout + (int64_t)vec * N;
   // inter-pass twiddles omega_N^{j2 k1}, 4 independent table loads in flight per thread.
   // FP64: one table of omega_N^m (the FP64 pipe, not memory, bounds these kernels).
@@ -519,7 +571,7 @@ __device__ __forceinline__ void passA_body(
       const int idx = idx0 + u * blockDim.x;
       if (idx < total) {
         const int m = (c0 + (idx & (NB - 1))) * (idx >> log2NB);  // < N
-        w[u] = sizeof(T) == 8 ? __ldg(&twN[m]) : cmul(__ldg(&twHi[m >> tw_h]), __ldg(&twLo[m & ((1 << tw_h) - 1)]));
+        w[u] = sizeof(T) == 8 ? ldg(&twN[m]) : cmul(ldg(&twHi[m >> tw_h]), ldg(&twLo[m & ((1 << tw_h) - 1)]));
       }
     }
 #pragma unroll
@@ -535,7 +587,7 @@ __device__ __forceinline__ void passA_body(
 }
 
 #define BK_PASSA_PARAMS(S)                                                                           \
-  const T* __restrict__ src##S, int64_t src_stride##S, typename V2<T>::t* __restrict__ Aout##S,              \
+  const St<T>* __restrict__ src##S, int64_t src_stride##S, typename V2<T>::t* __restrict__ Aout##S,          \
       T* __restrict__ partial##S, int N##S, int N1##S, int log2N1##S, int N2##S, int NB##S, int bs##S,      \
       const typename V2<T>::t* __restrict__ stw##S, const typename V2<T>::t* __restrict__ twN##S,           \
       const typename V2<T>::t* __restrict__ twLo##S, const typename V2<T>::t* __restrict__ twHi##S, int tw_h##S
@@ -586,31 +638,33 @@ __global__ void __launch_bounds__(MaxThr<T>::v, 2)
 // the stencil into the pass-A loads instead exposes its neighbour loads: those passes ran
 // 25-40% longer than plain-load ones.
 template <typename T, int K>
-__global__ void __launch_bounds__(256) k_stencil(const T* __restrict__ stage, int64_t Ls, T* __restrict__ G, int N,
+__global__ void __launch_bounds__(256) k_stencil(const St<T>* __restrict__ stage, int64_t Ls, St<T>* __restrict__ G, int N,
                                                  T sc, StencilTab<T> tb, T* __restrict__ partial) {
   __shared__ T red[8];
   const int vec = blockIdx.y;
-  const T* Y = stage + (int64_t)vec * Ls;
-  T* g = G + (int64_t)vec * Ls;
+  const St<T>* Y = stage + (int64_t)vec * Ls;
+  St<T>* g = G + (int64_t)vec * Ls;
+  typedef Cv<T, St<T>> CV;
   T acc = T(0);
   // interior nodes 2..N-2 by the plain three-point formulas (the boundary cases, if-converted
   // into the same loop, tripled its FP64 instructions); the four boundary nodes by one thread
   const T* __restrict__ rk = tb.rk;
   for (int m = 2 + blockIdx.x * blockDim.x + threadIdx.x; m <= N - 2; m += gridDim.x * blockDim.x) {
-    const T x = K == ST_FWD ? (Y[m + 1] - Y[m - 1]) * (sc * rk[m]) : Y[m - 1] * rk[m - 1] - Y[m + 1] * rk[m + 1];
-    g[m] = x;
+    const T ym = CV::in(Y[m - 1]), yp = CV::in(Y[m + 1]);
+    const T x = K == ST_FWD ? (yp - ym) * (sc * rk[m]) : ym * rk[m - 1] - yp * rk[m + 1];
+    g[m] = CV::out(x);
     acc += T(2) * x;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int mb[4] = {0, 1, N - 1, N};
     for (int i = 0; i < 4; ++i) {
       const T x = load_x<T, K>(Y, mb[i], N, sc, T(0), tb);
-      g[mb[i]] = x;
+      g[mb[i]] = CV::out(x);
       acc += (mb[i] == 0 || mb[i] == N) ? x : T(2) * x;
     }
   }
   if (partial) {
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int o = 16; o > 0; o >>= 1) acc += shfl_xor(acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -621,30 +675,105 @@ __global__ void __launch_bounds__(256) k_stencil(const T* __restrict__ stage, in
   }
 }
 
+// Caller's vectors (pitch apart) converted to the arithmetic type T, Ls apart (double-float
+// products: one conversion per element instead of one per load in the transform passes).
+template <typename T>
+__global__ void __launch_bounds__(256) k_to_arith(const Us<T>* __restrict__ v, int64_t pitch, T* __restrict__ x,
+                                                  int64_t Ls) {
+  const Us<T>* src = v + (int64_t)blockIdx.y * pitch;
+  T* dst = x + (int64_t)blockIdx.y * Ls;
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < Ls; m += (int64_t)gridDim.x * blockDim.x)
+    dst[m] = Cv<T, Us<T>>::in(src[m]);
+}
+
 // Epilogue kinds of pass B:
 //   EP_STORE     : stage[k] = Y_k / N                      (after the first DCT, forward)
 //   EP_STORE_TRN : stage[k] = Y_k - Y0, Y0 from partials   (after the first DCT, transpose)
 //   EP_FWD_OUT   : out[k] = s (Y_k - Y0), Y0 from partials (after the second DCT, forward)
 //   EP_TRN_OUT   : out[k] = (s/N) W_k Y_k                   (after the second DCT, transpose)
-enum { EP_STORE = 0, EP_STORE_TRN = 1, EP_FWD_OUT = 2, EP_TRN_OUT = 3 };
+//   EP_CPLX      : dst[k] = Z_k                          (PB_CPLX: a plain complex FFT)
+//   EP_CPLX_MC   : dst[k] = conj(Z_k tab[k])             (PB_CPLX: spectral product, conjugated)
+enum { EP_STORE = 0, EP_STORE_TRN = 1, EP_FWD_OUT = 2, EP_TRN_OUT = 3, EP_CPLX = 4, EP_CPLX_MC = 5 };
 
+template <typename T, int E, typename S>
+__device__ __forceinline__ void ep_write(S* __restrict__ dst, int k, T yk, int N, T s, T Y0, T invN) {
+  typedef Cv<T, S> CV;
+  if (E == EP_STORE) dst[k] = CV::out(yk * invN);
+  else if (E == EP_STORE_TRN) dst[k] = CV::out(yk - Y0);
+  else if (E == EP_FWD_OUT) dst[k] = CV::out(s * (yk - Y0));
+  else dst[k] = CV::out((k == 0 || k == N) ? s * invN * yk : T(2) * s * invN * yk);
+}
+
+// ---------------------------------------------------------------------------------------------
+// N that is not a power of two (N > 1024): Bluestein's identity j k = (j^2 + k^2 - (k - j)^2)/2
+// turns the length-N complex DFT Z = DFT_N(z) of the DCT-I into a circular convolution of
+// length M (a power of two, M >= 2N - 1), run by the four-step FFT passes above in their plain
+// complex modes:
+//   a_j = z_j w_j (j < N, 0 up to M),  w_j = e^{-i pi j^2 / N} (j^2 reduced mod 2N in integers),
+//   c = IFFT_M(FFT_M(a) . Bh),  Bh = FFT_M(b) / M,  b_m = conj(w_m) = b_{M-m} (|m| < N, else 0),
+//   Z_k = w_k c_k.
+// The inverse FFT runs as conj(FFT(conj .)): the first FFT's pass B stores conj(A . Bh), the
+// second FFT is a forward one, and the post kernel takes conj of its output. Then the real-FFT
+// split gives the DCT-I outputs Y_k (k = 0..N) as for powers of two, with Y_0 = Re Z_0 + Im Z_0.
+// ---------------------------------------------------------------------------------------------
+// a = z w zero-padded to M (one complex per element), z_j from the input kind K (IN_PLAIN / IN_WINV).
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_bs_pre(const St<T>* __restrict__ src, int64_t sstride, int N, int64_t M,
+                                                const typename V2<T>::t* __restrict__ w, T* __restrict__ a) {
+  typedef typename V2<T>::t C;
+  const St<T>* x = src + (int64_t)blockIdx.y * sstride;
+  T* dst = a + (int64_t)blockIdx.y * 2 * M;
+  StencilTab<T> tb;
+  tb.rk = nullptr;
+  tb.cN = T(0);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < M; j += (int64_t)gridDim.x * blockDim.x) {
+    C r = mk2<T>(T(0), T(0));
+    if (j < N) r = cmul(load_z<T, K>(x, (int)j, N, T(1), T(0), tb), w[j]);
+    dst[2 * j] = r.x;
+    dst[2 * j + 1] = r.y;
+  }
+}
+
+// DCT-I outputs from the second FFT's output y (M complex per vector): Z_k = w_k conj(y_k), the
+// real-FFT split of (Z_k, Z_{N-k}) for k <= N/2, and the epilogue E (Y0 = Y_0 = Re Z_0 + Im Z_0).
 template <typename T, int E>
-__device__ __forceinline__ void ep_write(T* __restrict__ dst, int k, T yk, int N, T s, T Y0, T invN) {
-  if (E == EP_STORE) dst[k] = yk * invN;
-  else if (E == EP_STORE_TRN) dst[k] = yk - Y0;
-  else if (E == EP_FWD_OUT) dst[k] = s * (yk - Y0);
-  else dst[k] = (k == 0 || k == N) ? s * invN * yk : T(2) * s * invN * yk;
+__global__ void __launch_bounds__(256) k_bs_post(const T* __restrict__ y, int64_t M, int N,
+                                                 const typename V2<T>::t* __restrict__ w,
+                                                 const typename V2<T>::t* __restrict__ tpost,
+                                                 typename OutS<T, E>::t* __restrict__ dst, int64_t dstride,
+                                                 int64_t zero_to, T s, T invN) {
+  typedef typename V2<T>::t C;
+  const T* yv = y + (int64_t)blockIdx.y * 2 * M;
+  typename OutS<T, E>::t* out = dst + (int64_t)blockIdx.y * dstride;
+  auto Z = [&](int k) {  // w_k conj(y_k)
+    const C yk = mk2<T>(yv[2 * (int64_t)k], -yv[2 * (int64_t)k + 1]);
+    return cmul(w[k], yk);
+  };
+  const C z0 = Z(0);
+  const T Y0 = z0.x + z0.y;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= N / 2; k += gridDim.x * blockDim.x) {
+    const int kc = k == 0 ? 0 : N - k;
+    T yk, ynk;
+    split_pair<T>(Z(k), Z(kc), tpost[k], yk, ynk);
+    ep_write<T, E>(out, k, yk, N, s, Y0, invN);
+    if (N - k != k) ep_write<T, E>(out, N - k, ynk, N, s, Y0, invN);
+  }
+  if ((E == EP_FWD_OUT || E == EP_TRN_OUT) && blockIdx.x == 0) {
+    for (int64_t m = N + 1 + threadIdx.x; m < zero_to; m += blockDim.x) out[m] = typename OutS<T, E>::t(0);
+  }
 }
 
 // Pass-B modes: PB_PAIRS, row pairs {p, N1 - p} and the real-FFT split of a DCT-I (outputs at
 // ostride k of a transform of parent size Npar; (cos, sin)(pi k / n) read as tpost[tps k]);
 // PB_ROWS, plain rows of the DCT-III's inverse FFT (outputs unpacked to the odd indices of the
 // sub-transform, ostride (2m+1) of the whole one).
-enum { PB_PAIRS = 0, PB_ROWS = 1 };
+// PB_CPLX, plain rows of a complex FFT written in natural order k = k1 + N1 k2 as complex pairs
+// (epilogues EP_CPLX, EP_CPLX_MC; `tpost` then holds the spectral table).
+enum { PB_PAIRS = 0, PB_ROWS = 1, PB_CPLX = 2 };
 
 template <typename T, int E, int MODE>
 __device__ __forceinline__ void passB_body(
-            int bid, const typename V2<T>::t* __restrict__ Ain, T* __restrict__ dst, int64_t dst_stride,
+            int bid, const typename V2<T>::t* __restrict__ Ain, typename OutS<T, E>::t* __restrict__ dst, int64_t dst_stride,
             int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial, int N, int N1,
             int N2, int log2N2, int P, const typename V2<T>::t* __restrict__ stw,
             const typename V2<T>::t* __restrict__ tpost, T s, T invN, int ostride, int tps, int Npar) {
@@ -658,19 +787,19 @@ __device__ __forceinline__ void passB_body(
   __shared__ T red[32];
   const int vec = blockIdx.y;
   const C* A = Ain + (int64_t)vec * N;
-  T* out = dst + (int64_t)vec * dst_stride;
+  typename OutS<T, E>::t* out = dst + (int64_t)vec * dst_stride;
   const int p0 = bid * P;
   T Y0 = T(0);
   if (E == EP_STORE_TRN || E == EP_FWD_OUT) {
     T acc = T(0);
     const T* pp = partial + (int64_t)vec * n_partial;
     for (int i = threadIdx.x; i < n_partial; i += blockDim.x) acc += pp[i];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int o = 16; o > 0; o >>= 1) acc += shfl_xor(acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
       T a = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      for (int o = 16; o > 0; o >>= 1) a += shfl_xor(a, o);
       if (threadIdx.x == 0) red[0] = a;
     }
     __syncthreads();
@@ -687,7 +816,7 @@ __device__ __forceinline__ void passB_body(
       if (idx < total) {
         const int q = idx >> log2N2;
         int row;
-        if (MODE == PB_ROWS) {
+        if (MODE == PB_ROWS || MODE == PB_CPLX) {
           row = 2 * p0 + q;
         } else {
           const int p = p0 + (q >> 1);
@@ -706,7 +835,25 @@ __device__ __forceinline__ void passB_body(
     }
   }
   __syncthreads();
-  fft16<T>(buf, N2, log2N2, 2 * P, bs, smem_tw ? tws : stw);
+  fft16_any<T>(buf, N2, log2N2, 2 * P, bs, smem_tw ? tws : stw);
+  if constexpr (MODE == PB_CPLX) {
+    // lanes take consecutive rows, so each store run covers 2P consecutive outputs
+    const int log2R = __ffs(2 * P) - 1;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int q = idx & (2 * P - 1);
+      const int k2 = idx >> log2R;
+      C R = buf[q * bs + padi(k2)];
+      const int64_t k = (int64_t)(2 * p0 + q) + (int64_t)N1 * k2;
+      if (E == EP_CPLX_MC) {
+        const C t = cmul(R, tpost[k]);
+        R.x = t.x;
+        R.y = -t.y;
+      }
+      out[2 * k] = R.x;
+      out[2 * k + 1] = R.y;
+    }
+    return;
+  }
   if (MODE == PB_ROWS) {
     // output p = k1 + N1 k2 of the inverse FFT is z_p = conj(result): r_{2p} = Re, r_{2p+1} = -Im;
     // X_{2j} = r_j, X_{2j+1} = r_{M-1-j} (j < M/2 = N), and Y_{2m+1} = X_m
@@ -778,7 +925,7 @@ __device__ __forceinline__ void passB_body(
   }
   // zero the padding of the output vectors (final epilogues only)
   if ((E == EP_FWD_OUT || E == EP_TRN_OUT) && bid == 0) {
-    for (int64_t m = Npar + 1 + threadIdx.x; m < pitch_zero_to; m += blockDim.x) out[m] = T(0);
+    for (int64_t m = Npar + 1 + threadIdx.x; m < pitch_zero_to; m += blockDim.x) out[m] = typename OutS<T, E>::t(0);
   }
 }
 
@@ -788,7 +935,7 @@ __device__ __forceinline__ void passB_body(
 
 template <typename T, int E, int MODE = PB_PAIRS>
 __global__ void __launch_bounds__(MaxThr<T>::v, 2)
-    k_passB(const typename V2<T>::t* __restrict__ Ain, T* __restrict__ dst, int64_t dst_stride,
+    k_passB(const typename V2<T>::t* __restrict__ Ain, typename OutS<T, E>::t* __restrict__ dst, int64_t dst_stride,
             int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial, int N, int N1,
             int N2, int log2N2, int P, const typename V2<T>::t* __restrict__ stw,
             const typename V2<T>::t* __restrict__ tpost, T s, T invN, int ostride, int tps, int Npar) {
@@ -800,7 +947,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v, 2)
 // and real split (outputs at even indices), the rest the odd half's rows (odd indices).
 template <typename T, int E>
 __global__ void __launch_bounds__(MaxThr<T>::v, 2)
-    k_passB_split(int gE, BK_PASSB_PARAMS(E), BK_PASSB_PARAMS(O), T* __restrict__ dst, int64_t dst_stride,
+    k_passB_split(int gE, BK_PASSB_PARAMS(E), BK_PASSB_PARAMS(O), typename OutS<T, E>::t* __restrict__ dst, int64_t dst_stride,
                   int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial,
                   const typename V2<T>::t* __restrict__ tpost, T s, T invN, int Npar) {
   if ((int)blockIdx.x < gE)
@@ -815,7 +962,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v, 2)
 // differences (outputs 4m + 2) and the DCT-III of x's (outputs 2m + 1).
 template <typename T, int E>
 __global__ void __launch_bounds__(MaxThr<T>::v, 2)
-    k_passB_split3(int h1, int h2, BK_PASSB_PARAMS(E), BK_PASSB_PARAMS(D), BK_PASSB_PARAMS(O), T* __restrict__ dst,
+    k_passB_split3(int h1, int h2, BK_PASSB_PARAMS(E), BK_PASSB_PARAMS(D), BK_PASSB_PARAMS(O), typename OutS<T, E>::t* __restrict__ dst,
                    int64_t dst_stride, int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial,
                    const typename V2<T>::t* __restrict__ tpost, T s, T invN, int Npar) {
   const int b = blockIdx.x;
@@ -888,7 +1035,13 @@ static bk_status build_tables(Plan* p, cudaStream_t st) {
     BK_CHECK_LAUNCH();
     return BK_OK;
   };
-  if (p->small) {
+  if (p->blue) {
+    BK_TRY(build_fs_tables<T>(p->fsM, st));
+    BK_TRY(dmalloc(&p->chirp, sizeof(C) * N));
+    k_chirp<T><<<(int)std::min<int64_t>((N + 255) / 256, 4096), 256, 0, st>>>((C*)p->chirp, N);
+    BK_CHECK_LAUNCH();
+    BK_TRY(dmalloc(&p->bh, sizeof(C) * p->M));   // filled by blue_spectrum once the kernels are set up
+  } else if (p->small) {
     BK_TRY(dmalloc(&p->tw, sizeof(C) * N));
     k_tw_table<T><<<(int)std::min<int64_t>((N + 255) / 256, 4096), 256, 0, st>>>((C*)p->tw, N, (double)N);
     BK_CHECK_LAUNCH();
@@ -1114,7 +1267,7 @@ bk_status set_smem_attrs(const Plan* p) {
     const int cap = (int)FOURSTEP_SMEM_BUDGET;
     BK_TRY(smem_attr(k_passA<T, IN_PLAIN>, cap));
     BK_TRY(smem_attr(k_passA<T, IN_WINV>, cap));
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (std::is_same<T, double>::value) {
       BK_TRY(smem_attr(k_passA<T, ST_FWD>, cap));
       BK_TRY(smem_attr(k_passA<T, ST_TRN>, cap));
     }
@@ -1134,14 +1287,27 @@ bk_status set_smem_attrs(const Plan* p) {
     BK_TRY(smem_attr(k_passB_split3<T, EP_STORE_TRN>, cap));
     BK_TRY(smem_attr(k_passB_split3<T, EP_FWD_OUT>, cap));
     BK_TRY(smem_attr(k_passB_split3<T, EP_TRN_OUT>, cap));
+    if constexpr (!std::is_same<T, dfl>::value) {
+      BK_TRY(smem_attr(k_passA<T, IN_PLAIN, PM_CPLX>, cap));
+      BK_TRY(smem_attr(k_passB<T, EP_CPLX, PB_CPLX>, cap));
+      BK_TRY(smem_attr(k_passB<T, EP_CPLX_MC, PB_CPLX>, cap));
+    }
   }
   return BK_OK;
 }
+// Largest N that is not a power of two (Bluestein, above the dense range): the length-M FFT
+// (M >= 2N - 1) must fit the four-step shapes of the precision.
+static int64_t blue_max(int dtype) { return dtype == BK_F64 ? (int64_t(1) << 22) : (int64_t(1) << 23); }
+
 #ifndef BK_TRANSFORM_KERNEL_UNIT
 // The instances of set_smem_attrs and apply_impl (and with them every transform kernel) are
 // compiled in bk_birkhoff_f64.cu and bk_birkhoff_f32.cu, in parallel with this unit.
 extern template bk_status set_smem_attrs<double>(const Plan* p);
 extern template bk_status set_smem_attrs<float>(const Plan* p);
+extern template bk_status set_smem_attrs<dfl>(const Plan* p);
+template <typename T> bk_status blue_spectrum(Plan* p, cudaStream_t st);
+extern template bk_status blue_spectrum<double>(Plan* p, cudaStream_t st);
+extern template bk_status blue_spectrum<float>(Plan* p, cudaStream_t st);
 #endif
 
 // Power-of-two plans take the FFT chain unless BK_DENSE=1 (read at plan creation; then every
@@ -1152,6 +1318,23 @@ extern template bk_status set_smem_attrs<float>(const Plan* p);
 // building its tables (an O(N^3) FP64 formation of B^a per plan) cut throughput from 191 to
 // 152 solves/s on one GPU. BK_DENSE=0 is the default; N that is not a power of two is always
 // dense.
+// FP64 plans of N >= 2^18 compute their transforms in double-float arithmetic (bk_df.cuh) unless
+// switched off: bk_set_f64_transform(0) for plans created afterwards, or the environment variable
+// BK_F64_DF=0 (read at plan creation); bk_set_f64_transform(1) extends it to every four-step FP64
+// plan (N >= 256). Measured products (4 components, cold L2, FP64 / double-float ms): 2^14 0.095 /
+// 0.109, 2^16 0.123 / 0.132, 2^18 0.272 / 0.228, 2^20 0.978 / 0.553, 2^22 3.87 / 2.50, 2^24 17.6 /
+// 12.3: below 2^18 the passes are latency-bound and the double-float instructions lengthen them.
+#ifndef BK_TRANSFORM_KERNEL_UNIT
+static std::atomic<int> g_f64_df{-1};
+static bool f64_df_default(int64_t N) {
+  const int m = g_f64_df.load();
+  if (m >= 0) return m == 1;
+  const char* e = getenv("BK_F64_DF");
+  if (e && e[0] == '0') return false;
+  return N >= (int64_t(1) << 18);
+}
+#endif
+
 static bool dense_default(int dtype, int64_t N, int nvec) {
   (void)dtype;
   if (!dense_supported(N)) return false;
@@ -1191,13 +1374,13 @@ static bool autotune_enabled() {
 }
 
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int64_t, int, int, int, int>, int> g_tune;
+static std::map<std::tuple<int64_t, int, int, int, int, int>, int> g_tune;
 
 static bk_status autotune_tiles(Plan* p, cudaStream_t st) {
   const int nvec = p->n_comp * p->max_batch;
   int dev = 0;
   BK_TRY_CUDA(cudaGetDevice(&dev));
-  const auto key = std::make_tuple(p->N, p->dtype, nvec, sm_count(), dev);
+  const auto key = std::make_tuple(p->N, p->dtype, (int)p->df, nvec, sm_count(), dev);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
@@ -1257,8 +1440,9 @@ static bk_status autotune_tiles(Plan* p, cudaStream_t st) {
 bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtype, double t0,
                       double tf, int64_t pitch, cudaStream_t st) {
   *out = nullptr;
-  BK_ARG(N >= 4 && (is_pow2(N) ? N <= (int64_t(1) << 24) : dense_supported(N)),
-         "N must be a power of two in [4, 2^24] or any N in [4, 1024], got %lld", (long long)N);
+  BK_ARG(N >= 4 && (is_pow2(N) ? N <= (int64_t(1) << 24) : (dense_supported(N) || N <= blue_max(dtype))),
+         "N must be a power of two in [4, 2^24] or any N in [4, %lld] (this precision), got %lld",
+         (long long)blue_max(dtype), (long long)N);
   BK_ARG(n_comp >= 1 && n_comp <= 64, "n_comp must be in [1, 64], got %d", n_comp);
   BK_ARG(max_batch >= 1, "max_batch must be >= 1, got %d", max_batch);
   BK_ARG(dtype == BK_F64 || dtype == BK_F32, "dtype must be BK_F64 or BK_F32");
@@ -1278,7 +1462,12 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
   p->s = 0.5 * (tf - t0);
   p->pitch = pitch;
   // N not a power of two: the FFT chain does not apply; every product is the dense one
-  p->generic = !is_pow2(N);
+  p->generic = !is_pow2(N) && dense_supported(N);
+  p->blue = !is_pow2(N) && !dense_supported(N);
+  {
+    const char* e = getenv("BK_DENSE_TEST_TIMEOUT");  // test mode of the dense kernel, as bk_plan_dense_test_timeout
+    p->dtest = (e && e[0] == '1') ? 1 : 0;
+  }
   p->small = !p->generic && N <= small_limit(dtype);
   bk_status st_ = BK_OK;
   AllocCounter counter(&p->bytes);
@@ -1298,6 +1487,15 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
       p->smemS = dtype == BK_F64 ? smem_small<double>(N) : smem_small<float>(N);
       p->thrS = round_threads(N / 16);
       if (p->thrS > (dtype == BK_F64 ? 256 : 512)) p->thrS = dtype == BK_F64 ? 256 : 512;
+    } else if (p->blue) {
+      p->M = 1;
+      while (p->M < 2 * N - 1) p->M *= 2;
+      const int64_t nvec = (int64_t)n_comp * max_batch;
+      if ((st_ = configure_fourstep(p->fsM, p->M, dtype, (int)nvec)) != BK_OK) break;
+      const size_t csz = 2 * dtype_size(dtype);
+      if ((st_ = dmalloc(&p->scrA, csz * (size_t)p->M * 2 * nvec)) != BK_OK) break;   // two M-vectors
+      if ((st_ = dmalloc(&p->scrY, dtype_size(dtype) * (size_t)(N + 1) * nvec)) != BK_OK) break;
+      if ((st_ = dmalloc(&p->scrG, dtype_size(dtype) * (size_t)(N + 1) * nvec)) != BK_OK) break;
     } else {
       // split DCT-I from 2^split_min_log2() on: fs the length-N/2 FFT, fso the length-N/4 one
       p->split = ilog2(N) >= split2_min_log2(dtype) ? 2 : (ilog2(N) >= split_min_log2(dtype) ? 1 : 0);
@@ -1313,16 +1511,18 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
       if ((st_ = dmalloc(&p->part1, dtype_size(dtype) * nPartMax * nvec)) != BK_OK) break;
       if ((st_ = dmalloc(&p->part2, dtype_size(dtype) * nPartMax * nvec)) != BK_OK) break;
     }
-    st_ = dtype == BK_F64 ? build_tables<double>(p, st) : build_tables<float>(p, st);
+    p->df = dtype == BK_F64 && !p->small && !p->blue && f64_df_default(N);
+    st_ = dtype == BK_F64 ? (p->df ? build_tables<dfl>(p, st) : build_tables<double>(p, st)) : build_tables<float>(p, st);
     if (st_ != BK_OK) break;
     if ((st_ = dmalloc((void**)&p->t_nodes, sizeof(double) * (size_t)L)) != BK_OK) break;
     k_grid_tables<<<(int)((L + 255) / 256), 256, 0, st>>>(p->t_nodes, N, t0, p->s);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) { st_ = BK_ERR_CUDA; set_error("grid table launch failed"); break; }
-    st_ = dtype == BK_F64 ? set_smem_attrs<double>(p) : set_smem_attrs<float>(p);
+    st_ = dtype == BK_F64 ? (p->df ? set_smem_attrs<dfl>(p) : set_smem_attrs<double>(p)) : set_smem_attrs<float>(p);
     if (st_ != BK_OK) break;
+    if (p->blue && (st_ = dtype == BK_F64 ? blue_spectrum<double>(p, st) : blue_spectrum<float>(p, st)) != BK_OK) break;
     if ((st_ = compute_weights(p, st)) != BK_OK) break;
-    if (!p->small && autotune_enabled()) {
+    if (!p->small && !p->blue && autotune_enabled()) {
       if ((st_ = autotune_tiles(p, st)) != BK_OK) break;
     }
     if (dense_default(dtype, N, n_comp * max_batch)) {
@@ -1349,6 +1549,9 @@ void plan_destroy(Plan* p) {
   free_fs(p->fs);
   free_fs(p->fso);
   free_fs(p->fse);
+  free_fs(p->fsM);
+  dfree(p->chirp);
+  dfree(p->bh);
   dfree(p->eo);
   dfree(p->tpost);
   dfree(p->rk);
@@ -1373,7 +1576,7 @@ void plan_destroy(Plan* p) {
 // receives the even half's DC partial sums (IN_WINV); partB holds the partials the epilogue
 // reads for Y0.
 template <typename T, int K, int E>
-static bk_status split_dct(const Plan* p, const T* src, int64_t sstride, T* dst, int64_t dstride, int64_t zero_to,
+static bk_status split_dct(const Plan* p, const St<T>* src, int64_t sstride, typename OutS<T, E>::t* dst, int64_t dstride, int64_t zero_to,
                            int nvec, void* scrA, T* partA, const T* partB, int npartB, T s, T invN, StencilTab<T> tb,
                            cudaStream_t st) {
   typedef typename V2<T>::t C;
@@ -1401,7 +1604,7 @@ static bk_status split_dct(const Plan* p, const T* src, int64_t sstride, T* dst,
 // One two-level split DCT-I (see PM_PAIR2): pass A of its three parts in one launch, then pass B
 // of the three in one launch writing outputs 4k, 4m + 2 and 2m + 1.
 template <typename T, int K, int E>
-static bk_status split_dct3(const Plan* p, const T* src, int64_t sstride, T* dst, int64_t dstride, int64_t zero_to,
+static bk_status split_dct3(const Plan* p, const St<T>* src, int64_t sstride, typename OutS<T, E>::t* dst, int64_t dstride, int64_t zero_to,
                             int nvec, void* scrA, T* partA, const T* partB, int npartB, T s, T invN, StencilTab<T> tb,
                             cudaStream_t st) {
   typedef typename V2<T>::t C;
@@ -1436,7 +1639,7 @@ static bk_status split_dct3(const Plan* p, const T* src, int64_t sstride, T* dst
 }
 
 template <typename T, int K, int E>
-static bk_status split_any(const Plan* p, const T* src, int64_t sstride, T* dst, int64_t dstride, int64_t zero_to,
+static bk_status split_any(const Plan* p, const St<T>* src, int64_t sstride, typename OutS<T, E>::t* dst, int64_t dstride, int64_t zero_to,
                            int nvec, void* scrA, T* partA, const T* partB, int npartB, T s, T invN, StencilTab<T> tb,
                            cudaStream_t st) {
   if (p->split == 2)
@@ -1444,39 +1647,134 @@ static bk_status split_any(const Plan* p, const T* src, int64_t sstride, T* dst,
   return split_dct<T, K, E>(p, src, sstride, dst, dstride, zero_to, nvec, scrA, partA, partB, npartB, s, invN, tb, st);
 }
 
+// One length-M complex FFT on the plan's Bluestein layout: src (M complex per vector, as real
+// pairs) -> dst (same), through the four-step scratch A; E = EP_CPLX_MC multiplies by the
+// spectral table and conjugates in the store.
+template <typename T, int E>
+static bk_status blue_fft(const Plan* p, const T* src, T* dst, typename V2<T>::t* A, int nvec, cudaStream_t st) {
+  typedef typename V2<T>::t C;
+  const FourStep& f = p->fsM;
+  const int M = (int)p->M;
+  StencilTab<T> tb;
+  tb.rk = nullptr;
+  tb.cN = T(0);
+  k_passA<T, IN_PLAIN, PM_CPLX><<<dim3(f.N2 / f.NB, nvec), f.thrA, f.smemA, st>>>(
+      src, 2 * (int64_t)M, A, nullptr, M, f.N1, ilog2(f.N1), f.N2, f.NB, f.bsA, (const C*)f.stw1, (const C*)f.twN,
+      (const C*)f.twLo, (const C*)f.twHi, f.tw_h, T(1), tb);
+  BK_CHECK_LAUNCH();
+  k_passB<T, E, PB_CPLX><<<dim3(f.N1 / 2 / f.P, nvec), f.thrB, f.smemB, st>>>(
+      A, dst, 2 * (int64_t)M, 0, nullptr, 0, M, f.N1, f.N2, ilog2(f.N2), f.P, (const C*)f.stw2, (const C*)p->bh, T(1),
+      T(1), 1, 1, M);
+  BK_CHECK_LAUNCH();
+  return BK_OK;
+}
+
+// One DCT-I of length N + 1 for N not a power of two: chirp, FFT_M, spectral product, FFT_M,
+// chirp and real split (k_bs_pre, blue_fft x 2, k_bs_post).
+template <typename T, int K, int E>
+static bk_status blue_dct(const Plan* p, const T* src, int64_t sstride, typename OutS<T, E>::t* dst, int64_t dstride,
+                          int64_t zero_to, int nvec, T s, T invN, cudaStream_t st) {
+  typedef typename V2<T>::t C;
+  const int64_t M = p->M;
+  const int N = (int)p->N;
+  T* Ma = (T*)p->scrA;
+  C* Mb = (C*)(Ma + 2 * M * (int64_t)p->n_comp * p->max_batch);
+  const int gp = (int)std::min<int64_t>(1024, (M + 255) / 256);
+  k_bs_pre<T, K><<<dim3(gp, nvec), 256, 0, st>>>(src, sstride, N, M, (const C*)p->chirp, Ma);
+  BK_CHECK_LAUNCH();
+  BK_TRY((blue_fft<T, EP_CPLX_MC>(p, Ma, Ma, Mb, nvec, st)));
+  BK_TRY((blue_fft<T, EP_CPLX>(p, Ma, Ma, Mb, nvec, st)));
+  const int gq = (int)std::min<int64_t>(1024, (N / 2 + 256) / 256);
+  k_bs_post<T, E><<<dim3(gq, nvec), 256, 0, st>>>(Ma, M, N, (const C*)p->chirp, (const C*)p->tpost, dst, dstride,
+                                                  zero_to, s, invN);
+  BK_CHECK_LAUNCH();
+  return BK_OK;
+}
+
+// The spectral table of a Bluestein plan: bh = FFT_M(b) / M (b from k_bs_kernel, already
+// scaled), through the plan's own FFT passes (scratch: the plan's two M-vectors).
 template <typename T>
-bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool trans, double s_scale,
+bk_status blue_spectrum(Plan* p, cudaStream_t st) {
+  typedef typename V2<T>::t C;
+  const int64_t M = p->M;
+  T* Ma = (T*)p->scrA;
+  C* Mb = (C*)(Ma + 2 * M * (int64_t)p->n_comp * p->max_batch);
+  k_bs_kernel<T><<<(int)std::min<int64_t>((M + 255) / 256, 4096), 256, 0, st>>>(Ma, p->N, M);
+  BK_CHECK_LAUNCH();
+  BK_TRY((blue_fft<T, EP_CPLX>(p, Ma, (T*)p->bh, Mb, 1, st)));
+  return BK_OK;
+}
+
+template <typename T>
+bk_status apply_impl(const Plan* p, const Us<T>* vu, Us<T>* out, int nvec, bool trans, double s_scale,
                             cudaStream_t st, void* scrA, void* scrY, void* part1, void* part2, void* scrG) {
   typedef typename V2<T>::t C;
   const int N = (int)p->N;
+  // the first DCT's input: the caller's vectors, or (double-float) their conversion into the
+  // stencil buffer, which the first DCT consumes before the stencil overwrites it
+  const St<T>* v = nullptr;
+  int64_t vstride = p->pitch;
+  if constexpr (std::is_same<T, Us<T>>::value) {
+    v = vu;
+  } else {
+    if (!scrG) {
+      set_error("internal: double-float products need the stencil buffer");
+      return BK_ERR_ARG;
+    }
+    k_to_arith<T><<<dim3(std::max(1, std::min(1024, (N + 256) / 256)), nvec), 256, 0, st>>>(vu, p->pitch, (T*)scrG,
+                                                                                              N + 1);
+    BK_CHECK_LAUNCH();
+    v = (const T*)scrG;
+    vstride = N + 1;
+  }
   const T s = (T)s_scale;
-  const T invN = T(1) / T(N);
+  const T invN = T(1.0 / (double)N);
   StencilTab<T> tb;
   tb.rk = (const T*)p->rk;
   tb.cN = (T)(1.0 / (4.0 * ((double)N * (double)N - 1.0)));
   if (p->small) {
     if (!trans)
-      k_birkhoff_small<T, false><<<nvec, p->thrS, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, (const C*)p->stwS, (const C*)p->tpost, tb);
+      k_birkhoff_small<T, false><<<nvec, p->thrS, p->smemS, st>>>(vu, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, (const C*)p->stwS, (const C*)p->tpost, tb);
     else
-      k_birkhoff_small<T, true><<<nvec, p->thrS, p->smemS, st>>>(v, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, (const C*)p->stwS, (const C*)p->tpost, tb);
+      k_birkhoff_small<T, true><<<nvec, p->thrS, p->smemS, st>>>(vu, out, N, ilog2(N), p->pitch, s, (const C*)p->tw, (const C*)p->stwS, (const C*)p->tpost, tb);
     BK_CHECK_LAUNCH();
     return BK_OK;
   }
+  if constexpr (!std::is_same<T, dfl>::value) {
+    if (p->blue) {
+      const int64_t Ls = N + 1;
+      T* Ystage = (T*)scrY;
+      T* Gst = (T*)scrG;
+      const dim3 gS((unsigned)std::min<int64_t>(1024, (N + 255) / 256), nvec);
+      if (!trans) {
+        BK_TRY((blue_dct<T, IN_PLAIN, EP_STORE>(p, v, vstride, Ystage, Ls, 0, nvec, s, invN, st)));
+        k_stencil<T, ST_FWD><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, nullptr);
+        BK_CHECK_LAUNCH();
+        BK_TRY((blue_dct<T, IN_PLAIN, EP_FWD_OUT>(p, Gst, Ls, out, p->pitch, p->pitch, nvec, s, invN, st)));
+      } else {
+        BK_TRY((blue_dct<T, IN_WINV, EP_STORE_TRN>(p, v, vstride, Ystage, Ls, 0, nvec, s, invN, st)));
+        k_stencil<T, ST_TRN><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, nullptr);
+        BK_CHECK_LAUNCH();
+        BK_TRY((blue_dct<T, IN_PLAIN, EP_TRN_OUT>(p, Gst, Ls, out, p->pitch, p->pitch, nvec, s, invN, st)));
+      }
+      return BK_OK;
+    }
+  }
   if (p->split && scrG) {
     const int64_t Ls = N + 1;
-    T* Ystage = (T*)scrY;
-    T* Gst = (T*)scrG;
+    St<T>* Ystage = (St<T>*)scrY;
+    St<T>* Gst = (St<T>*)scrG;
     T* pa1 = (T*)part1;
     T* pa2 = (T*)part2;
     const int nPA = p->fs.nPartA;
     const dim3 gS(nPA, nvec);
     if (!trans) {
-      BK_TRY((split_any<T, IN_PLAIN, EP_STORE>(p, v, p->pitch, Ystage, Ls, 0, nvec, scrA, nullptr, nullptr, 0, s, invN, tb, st)));
+      BK_TRY((split_any<T, IN_PLAIN, EP_STORE>(p, v, vstride, Ystage, Ls, 0, nvec, scrA, nullptr, nullptr, 0, s, invN, tb, st)));
       k_stencil<T, ST_FWD><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, pa2);
       BK_CHECK_LAUNCH();
       BK_TRY((split_any<T, IN_PLAIN, EP_FWD_OUT>(p, Gst, Ls, out, p->pitch, p->pitch, nvec, scrA, nullptr, pa2, nPA, s, invN, tb, st)));
     } else {
-      BK_TRY((split_any<T, IN_WINV, EP_STORE_TRN>(p, v, p->pitch, Ystage, Ls, 0, nvec, scrA, pa1, pa1, nPA, s, invN, tb, st)));
+      BK_TRY((split_any<T, IN_WINV, EP_STORE_TRN>(p, v, vstride, Ystage, Ls, 0, nvec, scrA, pa1, pa1, nPA, s, invN, tb, st)));
       k_stencil<T, ST_TRN><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, nullptr);
       BK_CHECK_LAUNCH();
       BK_TRY((split_any<T, IN_PLAIN, EP_TRN_OUT>(p, Gst, Ls, out, p->pitch, p->pitch, nvec, scrA, nullptr, nullptr, 0, s, invN, tb, st)));
@@ -1487,7 +1785,7 @@ bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool trans, do
   const int N1 = f.N1, N2 = f.N2, NB = f.NB, P = f.P;
   const int log2N1 = ilog2(N1), log2N2 = ilog2(N2);
   C* A = (C*)scrA;
-  T* Ystage = (T*)scrY;
+  St<T>* Ystage = (St<T>*)scrY;
   T* pa1 = (T*)part1;
   T* pa2 = (T*)part2;
   const int nPA = f.nPartA;
@@ -1498,10 +1796,10 @@ bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool trans, do
   const C* twN = (const C*)f.twN;
   const C* tp = (const C*)p->tpost;
   const int64_t Ls = N + 1;
-  T* Gst = (T*)scrG;  // separate stencil pass when given (see k_stencil)
+  St<T>* Gst = (St<T>*)scrG;  // separate stencil pass when given (see k_stencil)
   const dim3 gS(nPA, nvec);
   if (!trans) {
-    k_passA<T, IN_PLAIN><<<gA, f.thrA, f.smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
+    k_passA<T, IN_PLAIN><<<gA, f.thrA, f.smemA, st>>>(v, vstride, A, pa1, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
     BK_CHECK_LAUNCH();
     k_passB<T, EP_STORE><<<gB, f.thrB, f.smemB, st>>>(A, Ystage, Ls, 0, nullptr, 0, N, N1, N2, log2N2, P, stw2, tp, s, invN, 1, 1, N);
     BK_CHECK_LAUNCH();
@@ -1509,7 +1807,7 @@ bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool trans, do
       k_stencil<T, ST_FWD><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, pa2);
       BK_CHECK_LAUNCH();
       k_passA<T, IN_PLAIN><<<gA, f.thrA, f.smemA, st>>>(Gst, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
-    } else if constexpr (sizeof(T) == 8) {
+    } else if constexpr (std::is_same<T, double>::value) {
       // fused stencil loads: only the allocation-free FP64 entry point has no stencil buffer
       k_passA<T, ST_FWD><<<gA, f.thrA, f.smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
     } else {
@@ -1520,7 +1818,7 @@ bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool trans, do
     k_passB<T, EP_FWD_OUT><<<gB, f.thrB, f.smemB, st>>>(A, out, p->pitch, p->pitch, pa2, nPA, N, N1, N2, log2N2, P, stw2, tp, s, invN, 1, 1, N);
     BK_CHECK_LAUNCH();
   } else {
-    k_passA<T, IN_WINV><<<gA, f.thrA, f.smemA, st>>>(v, p->pitch, A, pa1, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
+    k_passA<T, IN_WINV><<<gA, f.thrA, f.smemA, st>>>(v, vstride, A, pa1, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
     BK_CHECK_LAUNCH();
     k_passB<T, EP_STORE_TRN><<<gB, f.thrB, f.smemB, st>>>(A, Ystage, Ls, 0, pa1, nPA, N, N1, N2, log2N2, P, stw2, tp, s, invN, 1, 1, N);
     BK_CHECK_LAUNCH();
@@ -1529,7 +1827,7 @@ bk_status apply_impl(const Plan* p, const T* v, T* out, int nvec, bool trans, do
       k_stencil<T, ST_TRN><<<gS, 256, 0, st>>>(Ystage, Ls, Gst, N, T(1), tb, nullptr);
       BK_CHECK_LAUNCH();
       k_passA<T, IN_PLAIN><<<gA, f.thrA, f.smemA, st>>>(Gst, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
-    } else if constexpr (sizeof(T) == 8) {
+    } else if constexpr (std::is_same<T, double>::value) {
       k_passA<T, ST_TRN><<<gA, f.thrA, f.smemA, st>>>(Ystage, Ls, A, pa2, N, N1, log2N1, N2, NB, bsA, stw1, twN, (const C*)f.twLo, (const C*)f.twHi, f.tw_h, invN, tb);
     } else {
       set_error("internal: FP32 products need the stencil buffer");
@@ -1549,10 +1847,15 @@ extern template bk_status apply_impl<double>(const Plan* p, const double* v, dou
 extern template bk_status apply_impl<float>(const Plan* p, const float* v, float* out, int nvec, bool trans,
                                             double s_scale, cudaStream_t st, void* scrA, void* scrY, void* part1,
                                             void* part2, void* scrG);
+extern template bk_status apply_impl<dfl>(const Plan* p, const double* v, double* out, int nvec, bool trans,
+                                          double s_scale, cudaStream_t st, void* scrA, void* scrY, void* part1,
+                                          void* part2, void* scrG);
 
 bk_status plan_apply_n(const Plan* p, const void* v, void* out, int nvec, bool trans, double s,
                        cudaStream_t st) {
   if (p->dense) return dense_apply(p, v, out, nvec, trans, s, st);
+  if (p->dtype == BK_F64 && p->df)
+    return apply_impl<dfl>(p, (const double*)v, (double*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2, p->scrG);
   if (p->dtype == BK_F64)
     return apply_impl<double>(p, (const double*)v, (double*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2, p->scrG);
   return apply_impl<float>(p, (const float*)v, (float*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2, p->scrG);
@@ -1760,7 +2063,7 @@ bk_status bk_plan_set_dense(bk_plan* plan, int on, void* stream) {
 bk_status bk_plan_shape(const bk_plan* plan, int* path, int* N1, int* N2, int* elems) {
   BK_ARG(plan != nullptr, "plan is NULL");
   const bk::Plan* p = reinterpret_cast<const bk::Plan*>(plan);
-  const int pth = p->dense ? 3 : (p->small ? 0 : (p->split ? 2 : 1));
+  const int pth = p->dense ? 3 : (p->blue ? 4 : (p->small ? 0 : (p->split ? 2 : 1)));
   if (path) *path = pth;
   if (N1) *N1 = (pth == 1 || pth == 2) ? p->fs.N1 : 0;
   if (N2) *N2 = (pth == 1 || pth == 2) ? p->fs.N2 : 0;
@@ -1768,9 +2071,28 @@ bk_status bk_plan_shape(const bk_plan* plan, int* path, int* N1, int* N2, int* e
   return BK_OK;
 }
 
+bk_status bk_set_f64_transform(int mode) {
+  BK_ARG(mode == 0 || mode == 1 || mode == -1, "mode must be 0 (FP64), 1 (double-float) or -1 (default)");
+  bk::g_f64_df.store(mode);
+  return BK_OK;
+}
+
+bk_status bk_plan_f64_mode(const bk_plan* plan, int* mode) {
+  BK_ARG(plan != nullptr && mode != nullptr, "NULL argument");
+  const bk::Plan* p = reinterpret_cast<const bk::Plan*>(plan);
+  *mode = p->df ? 1 : 0;
+  return BK_OK;
+}
+
 bk_status bk_plan_dense_state(const bk_plan* plan, int* on) {
   BK_ARG(plan != nullptr && on != nullptr, "NULL argument");
   *on = reinterpret_cast<const bk::Plan*>(plan)->dense ? 1 : 0;
+  return BK_OK;
+}
+
+bk_status bk_plan_dense_test_timeout(bk_plan* plan, int on) {
+  BK_ARG(plan != nullptr, "plan is NULL");
+  reinterpret_cast<bk::Plan*>(plan)->dtest = on ? 1 : 0;
   return BK_OK;
 }
 

@@ -7,6 +7,7 @@
 #include <stddef.h>
 
 #include "../../include/birkhoff.h"
+#include "bk_df.cuh"
 
 namespace bk {
 
@@ -50,6 +51,7 @@ void note_launch();
 template <typename T> struct V2;
 template <> struct V2<double> { typedef double2 t; };
 template <> struct V2<float> { typedef float2 t; };
+template <> struct V2<dfl> { typedef dfl2 t; };
 
 template <typename T> __host__ __device__ __forceinline__ typename V2<T>::t mk2(T x, T y) {
   typename V2<T>::t r; r.x = x; r.y = y; return r;

@@ -49,6 +49,7 @@ constexpr int DT_PART = DT_M * DT_KC * 4;              // one TF32 part of a chu
 constexpr int DT_CHUNK = 2 * DT_PART;                  // hi + lo: 32 KB
 constexpr int DT_TMEM_COLS = 32;                       // accumulator columns allocated (>= DT_N)
 constexpr unsigned DT_SPIN = 1u << 20;                 // mbarrier polls before a timeout
+constexpr unsigned DT_TEST_SPIN = 1024;                // polls of the test wait (a barrier nothing signals)
 constexpr int DENSE_MAX_N = 1024;                      // V (2 parts x 16 x K) fits in shared memory
 
 // Byte offset of A element (m, k), m < 128, k < 32, inside one part of a chunk.
@@ -91,9 +92,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (unsigned i = 0; i < DT_SPIN; ++i) {
+// Bounded wait for the phase with the given parity; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned limit = DT_SPIN) {
+  for (unsigned i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -130,11 +131,12 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
 __global__ void __launch_bounds__(128, 1)
     k_dense_tc(const unsigned char* __restrict__ At, const float* __restrict__ V, float* __restrict__ out, int nvec,
                int L, int64_t pitch, int nK, int KS, int S, float s, float* __restrict__ part,
-               unsigned* __restrict__ cnt, int* __restrict__ err) {
+               unsigned* __restrict__ cnt, int* __restrict__ err, int test_timeout) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_full[DT_SMAX];
   __shared__ __align__(8) uint64_t bar_empty[DT_SMAX];
   __shared__ __align__(8) uint64_t bar_done;
+  __shared__ __align__(8) uint64_t bar_never;   // test mode: nothing ever arrives on it
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
   __shared__ int last;
@@ -160,6 +162,7 @@ __global__ void __launch_bounds__(128, 1)
       mbar_init(smem_u32(&bar_empty[i]), 1);
     }
     mbar_init(smem_u32(&bar_done), 1);
+    mbar_init(smem_u32(&bar_never), 1);
     fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -197,8 +200,10 @@ __global__ void __launch_bounds__(128, 1)
     constexpr uint32_t idesc = dt_idesc();
     int issued = nloc < S ? nloc : S;  // chunks whose copies were started
     int c = 0;
-    bool ok = true;
-    for (; c < nloc; ++c) {
+    // test mode: a bounded wait that must run out (its barrier never completes a phase), taken
+    // through the same failure path as a real timeout
+    bool ok = !(test_timeout && !mbar_wait(smem_u32(&bar_never), 0, DT_TEST_SPIN));
+    for (; ok && c < nloc; ++c) {
       const int st = c % S;
       const uint32_t ph = (uint32_t)(c / S) & 1u;
       if (!mbar_wait(smem_u32(&bar_full[st]), ph)) { ok = false; break; }
@@ -233,7 +238,7 @@ __global__ void __launch_bounds__(128, 1)
   // every lane waits (bounded); the warp then agrees, since tcgen05.ld is warp-collective
   const bool mine = mbar_wait(smem_u32(&bar_done), 0);
   __syncwarp();
-  const bool done = __all_sync(0xffffffffu, mine);
+  const bool done = __all_sync(0xffffffffu, mine) && !fail;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   uint32_t r[16];
 #pragma unroll
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(128, 1)
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-  } else if (lane == 0) {
+  } else if (lane == 0 && fail == 0) {
     fail = 2;
   }
   const int row = warp * 32 + lane;
@@ -635,13 +640,26 @@ static bk_status dense_apply64(const Plan* p, const double* v, double* out, int 
   return BK_OK;
 }
 
+// BK_ERR_TIMEOUT (and the word cleared) when a dense product of the plan ran out of a bounded
+// wait since the last check; synchronises the stream. BK_OK for plans off the dense path.
+bk_status dense_status(const Plan* p, cudaStream_t st) {
+  if (!p || !p->dense || !p->derr) return BK_OK;
+  int e = 0;
+  BK_TRY_CUDA(cudaMemcpyAsync(&e, p->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  BK_TRY_CUDA(cudaStreamSynchronize(st));
+  if (e == 0) return BK_OK;
+  BK_TRY_CUDA(cudaMemsetAsync(p->derr, 0, sizeof(int), st));
+  set_error("a dense tensor-core product ran out of a bounded wait (error word %d); its output is invalid", e);
+  return BK_ERR_TIMEOUT;
+}
+
 bk_status dense_apply(const Plan* p, const void* v, void* out, int nvec, bool trans, double s, cudaStream_t st) {
   if (p->dtype == BK_F64) return dense_apply64(p, (const double*)v, (double*)out, nvec, trans, s, st);
   const DenseShape sh = dense_shape(p, nvec);
   const dim3 grid(p->dMt, (nvec + DT_N - 1) / DT_N, sh.KS);
   k_dense_tc<<<grid, 128, sh.smem, st>>>((const unsigned char*)p->dA[trans ? 1 : 0], (const float*)v, (float*)out, nvec,
                                          (int)p->L, p->pitch, p->dnK, sh.KS, sh.S, (float)s, (float*)p->dpart, p->dcnt,
-                                         p->derr);
+                                         p->derr, p->dtest);
   BK_CHECK_LAUNCH();
   return BK_OK;
 }

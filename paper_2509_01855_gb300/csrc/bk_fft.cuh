@@ -15,6 +15,8 @@
 // be the global one or a copy in shared memory (load_tw_smem).
 #pragma once
 
+#include <type_traits>
+
 #include "bk_common.cuh"
 
 namespace bk {
@@ -221,7 +223,82 @@ __device__ __forceinline__ void fft16(typename V2<T>::t* buf, int n, int log2n, 
 template <typename T>
 __device__ __forceinline__ void load_tw_smem(typename V2<T>::t* dst, const typename V2<T>::t* __restrict__ stw,
                                              int len) {
-  for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = __ldg(&stw[i]);
+  for (int i = threadIdx.x; i < len; i += blockDim.x) dst[i] = ldg(&stw[i]);
+}
+
+}  // namespace bk
+
+namespace bk {
+
+// The same FFT with the length and the stage known only at run time: one radix-16 stage body
+// (and one mixed-radix first stage) per kernel instead of one unrolled instance per length and
+// stage. Used by the double-float kernels, whose butterflies are an order of magnitude longer
+// than binary32 or binary64 ones, so that compile time and code size stay bounded; the address
+// arithmetic is generic (padi per element), which costs little next to double-float arithmetic.
+template <typename T, int R>
+__device__ __forceinline__ void stage_rt(typename V2<T>::t* __restrict__ buf, int nbatch, int bs,
+                                         const typename V2<T>::t* __restrict__ stw, int log2n, int log2ns) {
+  typedef typename V2<T>::t C;
+  constexpr int log2R = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
+  constexpr int PER = 16 / R;
+  const int log2nb16 = log2n - 4;
+  const int nb16 = 1 << log2nb16;
+  const int nR = (1 << log2n) >> log2R;
+  const int Ns = 1 << log2ns;
+  const int t = threadIdx.x;
+  const bool active = t < (nbatch << log2nb16);
+  const int tt = t & (nb16 - 1);
+  C* base = buf + (size_t)(t >> log2nb16) * bs;
+  C v[16];
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q * R + r] = base[padi(tt + q * nb16 + r * nR)];
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int j = tt + q * nb16;
+      const int k = j & (Ns - 1);
+      C* u = v + q * R;
+      if (Ns > 1) {
+        const C* tw = stw + k;
+#pragma unroll
+        for (int r = 1; r < R; ++r) u[r] = cmul(u[r], tw[(r - 1) * Ns]);
+      }
+      Radix<C, T, R>::run(u);
+      const int d0 = ((j >> log2ns) << (log2ns + log2R)) + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) base[padi(d0 + r * Ns)] = u[r];
+    }
+  }
+  __syncthreads();
+}
+
+// Run-time-length form of fft16 (same contract: 16 <= n <= 8192, nbatch * n / 16 threads).
+template <typename T>
+__device__ __forceinline__ void fft16_rt(typename V2<T>::t* buf, int n, int log2n, int nbatch, int bs,
+                                         const typename V2<T>::t* __restrict__ stw) {
+  const int rem = log2n & 3;
+  if (rem == 1) stage_rt<T, 2>(buf, nbatch, bs, stw, log2n, 0);
+  else if (rem == 2) stage_rt<T, 4>(buf, nbatch, bs, stw, log2n, 0);
+  else if (rem == 3) stage_rt<T, 8>(buf, nbatch, bs, stw, log2n, 0);
+  int off = 0;
+  for (int l = rem; l < log2n; l += 4) {
+    stage_rt<T, 16>(buf, nbatch, bs, stw + off, log2n, l);
+    if (l > 0) off += 15 << l;
+  }
+}
+
+// fft16 for binary32 / binary64, fft16_rt for double-float.
+template <typename T>
+__device__ __forceinline__ void fft16_any(typename V2<T>::t* buf, int n, int log2n, int nbatch, int bs,
+                                          const typename V2<T>::t* __restrict__ stw) {
+  if constexpr (std::is_same<T, dfl>::value) fft16_rt<T>(buf, n, log2n, nbatch, bs, stw);
+  else fft16<T>(buf, n, log2n, nbatch, bs, stw);
 }
 
 }  // namespace bk

@@ -146,17 +146,18 @@ __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, 
 // Level data of the sweep's affine maps. Level 0 items are segments of SEG nodes, whose map is
 // the product of (I + N_k) over the segment (latest node on the left); a level-(l+1) item is a
 // block of 32 level-l items and its map the product of theirs. The backward sweep uses the
-// transposed maps in reverse order. Level data is in the working precision (each node's map is
-// a product of one factor per level, O(log N) roundings deep, which an FP32 preconditioner
-// feeding FP32 GMRES tolerates; FP64 levels cost FP32 problems FP64-pipe time in every sweep)
-// and 32-interleaved (element c of item i at il32(i, c, NC)), so that a warp reading 32
+// transposed maps in reverse order. Every map M is near the identity (N_k = O(s w_k)), so the
+// level data stores its deviation D = M - I and composes (I + D1)(I + D2) = I + (D1 + D2 +
+// D1 D2): storing M itself would round away the small part, which in FP32 left the sweeps 100x
+// less accurate than a sequential FP32 recurrence at N = 2^17. Level data is in the working
+// precision (FP64 levels cost FP32 problems FP64-pipe time in every sweep) and 32-interleaved (element c of item i at il32(i, c, NC)), so that a warp reading 32
 // consecutive items is coalesced; slot q of a level starts at q * npad * n_x^2, npad = the
 // level's item count rounded up to 32.
 __device__ __forceinline__ int64_t il32(int64_t i, int c, int NC) { return (((i >> 5) * NC + c) << 5) + (i & 31); }
 
-// C = A B (n_x x n_x, row-major)
+// Deviation of a product: (I + A)(I + B) = I + C with C = A + B + A B (n_x x n_x, row-major).
 template <int NX, typename Tm = double>
-__device__ __forceinline__ void mat_mul(const Tm* A, const Tm* B, Tm* C) {
+__device__ __forceinline__ void dev_mul(const Tm* A, const Tm* B, Tm* C) {
 #pragma unroll
   for (int r = 0; r < NX; ++r)
 #pragma unroll
@@ -164,25 +165,25 @@ __device__ __forceinline__ void mat_mul(const Tm* A, const Tm* B, Tm* C) {
       Tm a = 0;
 #pragma unroll
       for (int q = 0; q < NX; ++q) a += A[r * NX + q] * B[q * NX + c];
-      C[r * NX + c] = a;
+      C[r * NX + c] = (A[r * NX + c] + B[r * NX + c]) + a;
     }
 }
 
-// Level-0 maps: prod over the segment's nodes of (I + N_k), one thread per segment.
+// Level-0 maps: prod over the segment's nodes of (I + N_k) as a deviation, one thread per segment.
 template <typename T, int NX>
 __global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, T* __restrict__ A0) {
   const int seg = blockIdx.x * blockDim.x + threadIdx.x;
   if (seg >= nseg) return;
   T A[NX * NX], M[NX * NX], R[NX * NX];
 #pragma unroll
-  for (int i = 0; i < NX * NX; ++i) A[i] = (i % (NX + 1) == 0) ? T(1) : T(0);
+  for (int i = 0; i < NX * NX; ++i) A[i] = T(0);
   constexpr int SEG = Seg<T>::v;
   for (int i = 0; i < SEG; ++i) {
     const int64_t k = (int64_t)seg * SEG + i;
     if (k >= L) break;
 #pragma unroll
-    for (int c = 0; c < NX * NX; ++c) M[c] = Nn[il_index<Seg<T>::v>(k, c, NX * NX)] + ((c % (NX + 1) == 0) ? T(1) : T(0));
-    mat_mul<NX, T>(M, A, R);
+    for (int c = 0; c < NX * NX; ++c) M[c] = Nn[il_index<Seg<T>::v>(k, c, NX * NX)];
+    dev_mul<NX, T>(M, A, R);
 #pragma unroll
     for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
   }
@@ -190,7 +191,8 @@ __global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, T* __re
   for (int c = 0; c < NX * NX; ++c) A0[il32(seg, c, NX * NX)] = A[c];
 }
 
-// Slots of one level, one warp per block of 32 items (items at or beyond n are identity maps):
+// Slots of one level (deviations from I), one warp per block of 32 items (items at or beyond n
+// are identity maps, deviation 0):
 // spans M_k(j) = M_{k-1}(j) M_{k-1}(j - 2^{k-1}) by doubling (defined for j >= 2^k - 1), Pre(i)
 // and Suf(i) as products of the spans that tile [0, i) and (i, 31], and the block's product
 // M_4(31) M_4(15), which is the map of the parent item at the next level.
@@ -203,20 +205,19 @@ __global__ void __launch_bounds__(32) k_lin_level(T* __restrict__ m, int n, T* _
   const int64_t slot = (int64_t)gridDim.x * 32 * NC;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    const T idc = (c % (NX + 1) == 0) ? T(1) : T(0);
-    const T a = i < n ? m[il32(i, c, NC)] : idc;
+    const T a = i < n ? m[il32(i, c, NC)] : T(0);
     S[0][lane][c] = a;
-    if (i >= n) m[il32(i, c, NC)] = idc;
+    if (i >= n) m[il32(i, c, NC)] = T(0);
   }
   __syncwarp();
   for (int k = 1; k < 5; ++k) {
     const int h = 1 << (k - 1);
     T R[NC];
     if (lane >= 2 * h - 1) {
-      mat_mul<NX, T>(S[k - 1][lane], S[k - 1][lane - h], R);
+      dev_mul<NX, T>(S[k - 1][lane], S[k - 1][lane - h], R);
     } else {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) R[c] = (c % (NX + 1) == 0) ? T(1) : T(0);
+      for (int c = 0; c < NC; ++c) R[c] = T(0);
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) S[k][lane][c] = R[c];
@@ -229,11 +230,11 @@ __global__ void __launch_bounds__(32) k_lin_level(T* __restrict__ m, int n, T* _
   T R[NC], Q[NC];
   // Pre(i) = A_{i-1} ... A_0
 #pragma unroll
-  for (int c = 0; c < NC; ++c) R[c] = (c % (NX + 1) == 0) ? T(1) : T(0);
+  for (int c = 0; c < NC; ++c) R[c] = T(0);
   int pos = 0;
   for (int k = 4; k >= 0; --k) {
     if ((lane >> k) & 1) {
-      mat_mul<NX, T>(S[k][pos + (1 << k) - 1], R, Q);
+      dev_mul<NX, T>(S[k][pos + (1 << k) - 1], R, Q);
 #pragma unroll
       for (int c = 0; c < NC; ++c) R[c] = Q[c];
       pos += 1 << k;
@@ -243,12 +244,12 @@ __global__ void __launch_bounds__(32) k_lin_level(T* __restrict__ m, int n, T* _
   for (int c = 0; c < NC; ++c) m[SL_PRE * slot + il32(i, c, NC)] = R[c];
   // Suf(i) = A_31 ... A_{i+1}
 #pragma unroll
-  for (int c = 0; c < NC; ++c) R[c] = (c % (NX + 1) == 0) ? T(1) : T(0);
+  for (int c = 0; c < NC; ++c) R[c] = T(0);
   int end = 31;
   const int len = 31 - lane;
   for (int k = 4; k >= 0; --k) {
     if ((len >> k) & 1) {
-      mat_mul<NX, T>(R, S[k][end], Q);
+      dev_mul<NX, T>(R, S[k][end], Q);
 #pragma unroll
       for (int c = 0; c < NC; ++c) R[c] = Q[c];
       end -= 1 << k;
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(32) k_lin_level(T* __restrict__ m, int n, T* _
       T a = 0;
 #pragma unroll
       for (int q = 0; q < NX; ++q) a += S[4][31][r * NX + q] * S[4][15][q * NX + cc];
-      parent[il32(blockIdx.x, c, NC)] = a;
+      parent[il32(blockIdx.x, c, NC)] = (S[4][31][c] + S[4][15][c]) + a;
     }
   }
 }
@@ -368,10 +369,10 @@ __device__ __forceinline__ void warp_scan(const T* __restrict__ m, int64_t slot,
       for (int c = 0; c < NC; ++c) Mv[c] = M[il32(item, c, NC)];
 #pragma unroll
       for (int r = 0; r < NX; ++r) {
-        T a = e[r];
+        T a = T(0);   // (I + D) pe = pe + D pe
 #pragma unroll
         for (int c = 0; c < NX; ++c) a += (DIR == 0 ? Mv[r * NX + c] : Mv[c * NX + r]) * pe[c];
-        e[r] = a;
+        e[r] = e[r] + (pe[r] + a);
       }
     }
   }
@@ -562,10 +563,10 @@ __global__ void __launch_bounds__(128) k_sw_down0(const T* __restrict__ Kn, cons
     for (int c = 0; c < NC; ++c) Mv[c] = Mt[il32(i, c, NC)];
 #pragma unroll
     for (int r = 0; r < NX; ++r) {
-      T a = el[il32(ia, r, NX)];
+      T a = T(0);   // (I + D) S = S + D S
 #pragma unroll
       for (int c = 0; c < NX; ++c) a += (DIR == 0 ? Mv[r * NX + c] : Mv[c * NX + r]) * S[c];
-      ns[r] = a;
+      ns[r] = el[il32(ia, r, NX)] + (S[r] + a);
     }
 #pragma unroll
     for (int r = 0; r < NX; ++r) S[r] = ns[r];

@@ -454,8 +454,11 @@ bk_status gmres(Problem* pr, OpData& d, int op, const void* b, void* x, const bk
   BK_ARG(ws != nullptr && ((uintptr_t)ws & 255) == 0, "workspace must be 256-byte aligned");
   BK_ARG(aux == nullptr || (d.dtype == BK_F64 && op == BK_OP_KKT), "transposed-product record needs the FP64 KKT operator");
   if (d.dtype == BK_F64)
-    return gmres_impl<double>(pr, d, op, (const double*)b, (double*)x, o, info, ws, st, pr->red_host, aux, weighted);
-  return gmres_impl<float>(pr, d, op, (const float*)b, (float*)x, o, info, ws, st, pr->red_host, nullptr, weighted);
+    BK_TRY(gmres_impl<double>(pr, d, op, (const double*)b, (double*)x, o, info, ws, st, pr->red_host, aux, weighted));
+  else
+    BK_TRY(gmres_impl<float>(pr, d, op, (const float*)b, (float*)x, o, info, ws, st, pr->red_host, nullptr, weighted));
+  // a dense product that ran out of a bounded wait leaves invalid values behind: fail the solve
+  return dense_status(d.plan, st);
 }
 
 bk_krylov_opts krylov_defaults() {

@@ -270,6 +270,8 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
   info->iterations = it;
   info->residual = phi;
   info->converged = phi <= o.tol ? 1 : 0;
+  // residual products on a dense plan that ran out of a bounded wait invalidate the solve
+  BK_TRY(dense_status(pr->d64.plan, st));
   return BK_OK;
 }
 

@@ -29,6 +29,14 @@ struct Plan {
   double t0 = 0, tf = 0, s = 0;
   bool small = true;          // whole chain in one CTA per vector
   bool generic = false;       // N not a power of two: dense products only
+  bool df = false;            // FP64 plan whose transforms compute in double-float arithmetic
+  // N not a power of two above the dense range: each DCT-I's length-N DFT by Bluestein's
+  // convolution of length M (a power of two >= 2N - 1) on the four-step layout fsM
+  bool blue = false;
+  int64_t M = 0;
+  FourStep fsM;
+  void* chirp = nullptr;      // w_j = exp(-i pi j^2 / N), j < N (working type)
+  void* bh = nullptr;         // FFT_M(b) / M of the conjugate chirp b (working type)
   int tileE = 0;              // four-step elements per CTA chosen by the autotuner (0: heuristic)
   size_t smemS = 0;           // dynamic shared memory of the single-CTA kernel
   int thrS = 256;             // threads of the single-CTA kernel
@@ -59,6 +67,7 @@ struct Plan {
   void* dA[2] = {nullptr, nullptr};
   int dMp = 0;                // FP64 layout: rows padded to a multiple of 128
   int* derr = nullptr;        // device error word of the dense kernel (0 = no timeout)
+  int dtest = 0;              // test mode: every dense FP32 product times out on purpose
   int dMt = 0, dnK = 0;       // 128-row output tiles, 32-wide K chunks
   void* dpart = nullptr;      // split-K partial sums (FP32)
   unsigned* dcnt = nullptr;   // split-K arrival counters, one per output tile (self-resetting)
@@ -77,5 +86,6 @@ bk_status plan_apply_n(const Plan* p, const void* v, void* out, int nvec, bool t
 bool dense_supported(int64_t N);
 bk_status dense_build(Plan* p, cudaStream_t st);
 bk_status dense_apply(const Plan* p, const void* v, void* out, int nvec, bool trans, double s, cudaStream_t st);
+bk_status dense_status(const Plan* p, cudaStream_t st);
 
 }  // namespace bk

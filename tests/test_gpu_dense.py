@@ -199,3 +199,45 @@ def test_dense_switch_back_and_unsupported():
     a, V = _dense_run(64, True, 2, 1, dense=True)
     B = ob.dense_B(64, 0.0, 3.0)
     assert _rel(a, V @ B) < TOL32
+
+
+def test_dense_timeout_path_reports_and_recovers():
+    """The dense kernel's bounded-wait failure path, made to run by the test mode (a wait on a
+    barrier nothing signals): the error word reports it, the context stays usable, and with the
+    mode off the same plan computes the right product again."""
+    from oracle import birkhoff as ob
+    from paper_2509_01855_gb300 import _lib, api
+    N = 100
+    plan = api.Plan(N, n_comp=2, max_batch=1, dtype=torch.float32, t0=0.0, tf=2.0)
+    assert plan.is_dense()
+    V = synth.gaussian((2, N + 1), "dense-timeout")
+    v = plan.empty(1)
+    v[0, :, :N + 1] = torch.as_tensor(V)
+    assert _lib.lib().bk_plan_dense_test_timeout(plan.handle, 1) == 0
+    api.birkhoff_apply(plan, v, plan.empty(1))
+    assert plan.dense_check() in (1, 2)     # the copy wait gave up (2 if a warp saw it first)
+    assert _lib.lib().bk_plan_dense_test_timeout(plan.handle, 0) == 0
+    out = api.birkhoff_apply(plan, v, plan.empty(1))
+    assert plan.dense_check() == 0
+    ref = V @ ob.dense_B(N, 0.0, 2.0).T
+    assert np.linalg.norm(out[0, :, :N + 1].cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_dense_timeout_fails_the_krylov_and_newton_solves(monkeypatch):
+    """A solve on a dense FP32 problem whose products time out returns BK_ERR_TIMEOUT (5)."""
+    from paper_2509_01855_gb300 import _lib, api
+    N = 100
+    monkeypatch.setenv("BK_DENSE_TEST_TIMEOUT", "1")
+    prob = api.Problem(_lib.BK_DBL_INT, N, torch.float32, 0.0, 1.0)
+    monkeypatch.delenv("BK_DENSE_TEST_TIMEOUT")
+    t, _ = api.Plan(N, t0=0.0, tf=1.0).grid()
+    X, U = synth.double_integrator_guess(t.numpy())
+    z = prob.pack(X, U)
+    prob.linearize(z)
+    rhs = prob.zeros(_lib.BK_OP_KKT)
+    rhs[: prob.L] = 1.0
+    sol = torch.zeros_like(rhs)
+    info = api.krylov_solve(prob, _lib.BK_OP_KKT, rhs, sol, rtol=1e-4, raise_on_fail=False)
+    assert info["status"] == 5
+    res = api.newton_solve(prob, z, max_iter=2, raise_on_fail=False)
+    assert res["status"] == 5

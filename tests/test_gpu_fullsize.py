@@ -130,4 +130,5 @@ def test_orbit_2p20_matches_oracle_interpolant(dtype, dense_ref):
             zk = prob.pack(X0, U0)
             ik = api.newton_solve(prob, zk, workspace=ws, max_iter=k, raise_on_fail=False, **kw)
             assert ik["iterations"] == k
-            assert abs(ik["residual"] - rinfo["norms"][k]) < 1e-6 * rinfo["norms"][k], (k, ik, rinfo["norms"])
+            # the inner solves stop at 1e-12 (2-norm), so late steps agree to ~1e-12 absolute
+            assert abs(ik["residual"] - rinfo["norms"][k]) < 1e-5 * rinfo["norms"][k] + 1e-12, (k, ik, rinfo["norms"])
