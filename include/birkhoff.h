@@ -139,6 +139,17 @@ bk_status birkhoff_apply_noalloc(const double* v, double* out, int64_t N, int nv
 bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int batch,
                            void* stream);
 
+/* out = B^b v, the b-form Birkhoff product (Eqs. xN=Birka+b, birk-conditions, manyDefs): the
+ * b-form basis B^b_j vanishes at the final point tau^b = 1 instead of tau^a = -1, so
+ * B^b = B^a - 1 w^T (w the Clenshaw-Curtis weights), and B^b v = B v - (B v)_N 1: the a-form
+ * chain, then the last node's value subtracted (x = x^b 1 + B^b V discretises the dynamics
+ * backwards from the final state). Same arguments, layout and errors as birkhoff_apply;
+ * v == out is allowed. Row N of the result is 0 and (B^b 1)_j = t_j - tf. */
+bk_status birkhoff_apply_b(const bk_plan* plan, const void* v, void* out, int batch, void* stream);
+
+/* out = (B^b)^T v = B^T v - s (1 . v) w, the exact transpose of birkhoff_apply_b. */
+bk_status birkhoff_apply_b_T(const bk_plan* plan, const void* v, void* out, int batch, void* stream);
+
 /* Switch a plan with N <= 1024 between the FFT chain (on = 0) and the dense product (on = 1)
  * for birkhoff_apply, birkhoff_apply_T and every operator built on the plan. The dense path
  * multiplies by B^a itself (the matrix of Eq. manyDefs, formed once in FP64 from its

@@ -36,6 +36,22 @@ def dense_Ba(N):
     return B
 
 
+def dense_Bb(N):
+    """[B^b]_ij = B^b_j(tau_i) (Eq. manyDefs), the b-form Birkhoff basis of Eq. birk-conditions:
+    B^b_j(tau^b = 1) = 0 and dB^b_j/dtau(tau_i) = delta_ij, so B^b_j(tau) = -int_{tau}^{1} l_j.
+    Each row by an n-point Gauss-Legendre rule on [tau_i, 1], n = N//2 + 2 (exact for degree N).
+    Row N is zero. O(N^3) work; written from the definition, independently of dense_Ba."""
+    tau = cgl_nodes(N)
+    nq = N // 2 + 2
+    xg, wg = np.polynomial.legendre.leggauss(nq)
+    B = np.zeros((N + 1, N + 1))
+    for i in range(N):
+        half = 0.5 * (1.0 - tau[i])
+        xi = tau[i] + half * (xg + 1.0)
+        B[i] = -half * (wg @ lagrange_matrix(N, xi))
+    return B
+
+
 def dense_B(N, t0=-1.0, tf=1.0):
     """Time-domain Birkhoff matrix s * B^a, s = (t_f - t_0)/2, so that (B 1)_i = t_i - t_0."""
     return 0.5 * (tf - t0) * dense_Ba(N)

@@ -129,6 +129,24 @@ def birkhoff_apply_T(plan, v, out, batch=None, stream=None):
     return out
 
 
+def birkhoff_apply_b(plan, v, out, batch=None, stream=None):
+    """out = B^b v (b-form Birkhoff product: the basis vanishes at the final point)."""
+    batch = v.shape[0] if (batch is None and v.dim() == 3) else (batch or 1)
+    _check_vec(plan, v, batch)
+    _check_vec(plan, out, batch)
+    L.check(L.lib().birkhoff_apply_b(plan.handle, L.ptr(v), L.ptr(out), int(batch), L.stream_ptr(stream)))
+    return out
+
+
+def birkhoff_apply_b_T(plan, v, out, batch=None, stream=None):
+    """out = (B^b)^T v."""
+    batch = v.shape[0] if (batch is None and v.dim() == 3) else (batch or 1)
+    _check_vec(plan, v, batch)
+    _check_vec(plan, out, batch)
+    L.check(L.lib().birkhoff_apply_b_T(plan.handle, L.ptr(v), L.ptr(out), int(batch), L.stream_ptr(stream)))
+    return out
+
+
 class Problem:
     """A bk_problem: dynamics kind, grid and linearisation state."""
 

@@ -1437,10 +1437,14 @@ static bk_status autotune_tiles(Plan* p, cudaStream_t st) {
 }
 
 #ifndef BK_TRANSFORM_KERNEL_UNIT
+bool plan_n_supported(int64_t N, int dtype) {
+  return N >= 4 && (is_pow2(N) ? N <= (int64_t(1) << 24) : (dense_supported(N) || N <= blue_max(dtype)));
+}
+
 bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtype, double t0,
                       double tf, int64_t pitch, cudaStream_t st) {
   *out = nullptr;
-  BK_ARG(N >= 4 && (is_pow2(N) ? N <= (int64_t(1) << 24) : (dense_supported(N) || N <= blue_max(dtype))),
+  BK_ARG(plan_n_supported(N, dtype),
          "N must be a power of two in [4, 2^24] or any N in [4, %lld] (this precision), got %lld",
          (long long)blue_max(dtype), (long long)N);
   BK_ARG(n_comp >= 1 && n_comp <= 64, "n_comp must be in [1, 64], got %d", n_comp);
@@ -1468,10 +1472,11 @@ bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtyp
     const char* e = getenv("BK_DENSE_TEST_TIMEOUT");  // test mode of the dense kernel, as bk_plan_dense_test_timeout
     p->dtest = (e && e[0] == '1') ? 1 : 0;
   }
-  p->small = !p->generic && N <= small_limit(dtype);
+  p->small = !p->generic && !p->blue && N <= small_limit(dtype);
   bk_status st_ = BK_OK;
   AllocCounter counter(&p->bytes);
   do {
+    if ((st_ = dmalloc(&p->bsc, sizeof(double) * (size_t)n_comp * max_batch)) != BK_OK) break;
     if (p->generic) {
       if ((st_ = dmalloc((void**)&p->t_nodes, sizeof(double) * (size_t)L)) != BK_OK) break;
       k_grid_tables<<<(int)((L + 255) / 256), 256, 0, st>>>(p->t_nodes, N, t0, p->s);
@@ -1552,6 +1557,7 @@ void plan_destroy(Plan* p) {
   free_fs(p->fsM);
   dfree(p->chirp);
   dfree(p->bh);
+  dfree(p->bsc);
   dfree(p->eo);
   dfree(p->tpost);
   dfree(p->rk);
@@ -1861,6 +1867,68 @@ bk_status plan_apply_n(const Plan* p, const void* v, void* out, int nvec, bool t
   return apply_impl<float>(p, (const float*)v, (float*)out, nvec, trans, s, st, p->scrA, p->scrY, p->part1, p->part2, p->scrG);
 }
 
+// b-form helpers: c[vec] = out[vec][N] (forward) or s sum_i u[vec][i] (transpose, one block per
+// vector, fixed order), then out[vec][i] -= c[vec] (forward) or c[vec] w_i (transpose), i <= N.
+template <typename T>
+__global__ void k_bform_last(const T* __restrict__ out, int64_t pitch, int64_t N, T* __restrict__ c) {
+  if (threadIdx.x == 0) c[blockIdx.x] = out[(int64_t)blockIdx.x * pitch + N];
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_bform_sum(const T* __restrict__ u, int64_t pitch, int64_t L, double s,
+                                                   T* __restrict__ c) {
+  __shared__ double red[8];
+  const T* x = u + (int64_t)blockIdx.x * pitch;
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < L; i += blockDim.x) a += (double)x[i];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    c[blockIdx.x] = (T)(s * t);
+  }
+}
+template <typename T>
+__global__ void k_bform_sub(T* __restrict__ out, int64_t pitch, int64_t L, const T* __restrict__ c,
+                            const T* __restrict__ w) {
+  const T cv = c[blockIdx.y];
+  T* o = out + (int64_t)blockIdx.y * pitch;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] -= w ? cv * w[i] : cv;
+}
+
+template <typename T>
+static bk_status apply_b_impl(const Plan* p, const void* v, void* out, int nvec, bool trans, cudaStream_t st) {
+  T* c = (T*)p->bsc;
+  const dim3 g((unsigned)std::min<int64_t>(1024, (p->L + 255) / 256), nvec);
+  const T* w = p->dtype == BK_F64 ? (const T*)p->w64 : (const T*)p->wT;
+  if (trans) {
+    // the sum first: v may alias out
+    k_bform_sum<T><<<nvec, 256, 0, st>>>((const T*)v, p->pitch, p->L, p->s, c);
+    BK_CHECK_LAUNCH();
+    BK_TRY(plan_apply_n(p, v, out, nvec, true, p->s, st));
+    k_bform_sub<T><<<g, 256, 0, st>>>((T*)out, p->pitch, p->L, c, w);
+  } else {
+    BK_TRY(plan_apply_n(p, v, out, nvec, false, p->s, st));
+    k_bform_last<T><<<nvec, 32, 0, st>>>((const T*)out, p->pitch, p->N, c);
+    BK_CHECK_LAUNCH();
+    k_bform_sub<T><<<g, 256, 0, st>>>((T*)out, p->pitch, p->L, c, nullptr);
+  }
+  BK_CHECK_LAUNCH();
+  return BK_OK;
+}
+
+bk_status plan_apply_b(const Plan* p, const void* v, void* out, int batch, bool trans, cudaStream_t st) {
+  BK_ARG(p != nullptr, "plan is NULL");
+  BK_ARG(v != nullptr && out != nullptr, "NULL vector");
+  BK_ARG(batch >= 1 && batch <= p->max_batch, "batch %d outside [1, max_batch=%d]", batch, p->max_batch);
+  BK_ARG(((uintptr_t)v & 15) == 0 && ((uintptr_t)out & 15) == 0, "vectors must be 16-byte aligned");
+  const int nvec = batch * p->n_comp;
+  return p->dtype == BK_F64 ? apply_b_impl<double>(p, v, out, nvec, trans, st)
+                            : apply_b_impl<float>(p, v, out, nvec, trans, st);
+}
+
 bk_status plan_apply(const Plan* p, const void* v, void* out, int batch, bool trans, cudaStream_t st) {
   BK_ARG(p != nullptr, "plan is NULL");
   BK_ARG(v != nullptr && out != nullptr, "NULL vector");
@@ -2031,6 +2099,14 @@ bk_status birkhoff_apply(const bk_plan* plan, const void* v, void* out, int batc
 bk_status birkhoff_apply_noalloc(const double* v, double* out, int64_t N, int nvec, int64_t pitch, double t0,
                                  double tf, void* stream) {
   return bk::noalloc_apply(v, out, N, nvec, pitch, t0, tf, (cudaStream_t)stream);
+}
+
+bk_status birkhoff_apply_b(const bk_plan* plan, const void* v, void* out, int batch, void* stream) {
+  return bk::plan_apply_b(reinterpret_cast<const bk::Plan*>(plan), v, out, batch, false, (cudaStream_t)stream);
+}
+
+bk_status birkhoff_apply_b_T(const bk_plan* plan, const void* v, void* out, int batch, void* stream) {
+  return bk::plan_apply_b(reinterpret_cast<const bk::Plan*>(plan), v, out, batch, true, (cudaStream_t)stream);
 }
 
 bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int batch, void* stream) {

@@ -1619,8 +1619,9 @@ static bk_status problem_create(Problem** out, int kind, const double* params, i
   BK_ARG(kind == BK_DBL_INT || kind == BK_ORBIT || kind == BK_BILINEAR || kind == BK_ORBIT_MT,
          "unknown problem kind %d", kind);
   BK_ARG(dtype == BK_F64 || dtype == BK_F32, "dtype must be BK_F64 or BK_F32");
-  BK_ARG(N >= 4 && (is_pow2(N) ? N <= (int64_t(1) << 24) : dense_supported(N)),
-         "N must be a power of two in [4, 2^24] or any N in [4, 1024]");
+  // the problem's FP64 plan bounds N (FP32 problems keep one too)
+  BK_ARG(plan_n_supported(N, BK_F64), "N must be a power of two in [4, 2^24] or any N in [4, 2^22], got %lld",
+         (long long)N);
   BK_ARG(tf > t0, "tf must be > t0");
   BK_ARG(nparams >= 0 && nparams <= 4 && (nparams == 0 || params), "bad params");
   Problem* pr = new Problem();

@@ -37,6 +37,7 @@ struct Plan {
   FourStep fsM;
   void* chirp = nullptr;      // w_j = exp(-i pi j^2 / N), j < N (working type)
   void* bh = nullptr;         // FFT_M(b) / M of the conjugate chirp b (working type)
+  void* bsc = nullptr;        // one scalar per vector (b-form products), working type
   int tileE = 0;              // four-step elements per CTA chosen by the autotuner (0: heuristic)
   size_t smemS = 0;           // dynamic shared memory of the single-CTA kernel
   int thrS = 256;             // threads of the single-CTA kernel
@@ -73,11 +74,16 @@ struct Plan {
   unsigned* dcnt = nullptr;   // split-K arrival counters, one per output tile (self-resetting)
 };
 
+// Grid sizes a plan of this precision supports: powers of two 4..2^24, any other N 4..2^22
+// (BK_F64) or 4..2^23 (BK_F32).
+bool plan_n_supported(int64_t N, int dtype);
 bk_status plan_create(Plan** out, int64_t N, int n_comp, int max_batch, int dtype, double t0,
                       double tf, int64_t pitch, cudaStream_t st);
 void plan_destroy(Plan* p);
 bk_status plan_apply(const Plan* p, const void* v, void* out, int batch, bool trans,
                      cudaStream_t st);
+// b-form product B^b v = B v - (B v)_N 1 (trans: B^bT u = B^T u - s (1 . u) w).
+bk_status plan_apply_b(const Plan* p, const void* v, void* out, int batch, bool trans, cudaStream_t st);
 // Apply to `nvec` vectors with an explicit scale (s = 1 gives B^a itself).
 bk_status plan_apply_n(const Plan* p, const void* v, void* out, int nvec, bool trans, double s,
                        cudaStream_t st);

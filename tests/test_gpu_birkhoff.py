@@ -160,7 +160,7 @@ def test_bad_arguments():
     api = _api()
     from paper_2509_01855_gb300._lib import BirkhoffError
     with pytest.raises(BirkhoffError):
-        api.Plan(1500)           # not a power of two and above the dense limit of 1024
+        api.Plan((1 << 22) + 3)  # not a power of two and above the Bluestein limit of FP64
     with pytest.raises(BirkhoffError):
         api.Plan(2)              # too small
     with pytest.raises(BirkhoffError):

@@ -221,3 +221,18 @@ def test_fastpinvy_block_and_transpose(N):
     assert np.abs(P @ xi.ravel() - Y.ravel()).max() < 1e-12
     yT = ob.fastpinvy_block_T(w, J, Y)
     assert np.abs(P.T @ yT.ravel() - Y.ravel()).max() < 1e-12
+
+
+@pytest.mark.parametrize("N", [4, 9, 16, 33])
+def test_dense_Bb_definition(N):
+    """The b-form matrix of Eq. manyDefs: last row zero (B^b_j(tau^b) = 0), B^b = B^a - 1 w^T
+    (the two bases differ by their value at tau = 1, which for B^a is the weight w_j), and
+    B^b q' = q - q(1) for polynomials q of degree <= N + 1 (brute force)."""
+    from oracle.grid import cgl_nodes
+    Bb = ob.dense_Bb(N)
+    Ba = ob.dense_Ba(N)
+    assert np.abs(Bb[N]).max() == 0.0
+    assert np.abs(Bb - (Ba - np.outer(np.ones(N + 1), Ba[N]))).max() < 1e-13
+    tau = cgl_nodes(N)
+    q = np.polynomial.Polynomial(np.random.default_rng(N).standard_normal(N + 2))
+    assert np.abs(Bb @ q.deriv()(tau) - (q(tau) - q(1.0))).max() < 1e-12 * max(1.0, np.abs(q.coef).sum())
