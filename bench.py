@@ -346,6 +346,71 @@ def apply_sweep(lgs=range(10, 25), reps=5):
     return out
 
 
+def cufft_product(v, s):
+    """Comparison only (never the product path): B v for v of shape (n_c, N + 1) with cuFFT through
+    torch.fft -- the library's formulation (DCT-I = real FFT of the even extension of length 2N,
+    the integration stencil with the aliasing fold, DCT-I back, minus the node-0 value) written
+    with torch ops."""
+    import torch
+    N = v.shape[-1] - 1
+
+    def dct1(x):
+        ext = torch.cat([x, x[..., 1:N].flip(-1)], dim=-1)
+        return torch.fft.rfft(ext, dim=-1).real[..., :N + 1]
+
+    Y = dct1(v)
+    g = torch.zeros_like(Y)
+    k = torch.arange(2, N - 1, dtype=v.dtype, device=v.device)
+    g[..., 1] = (Y[..., 2] - Y[..., 0]) / (4.0 * N)
+    g[..., 2:N - 1] = (Y[..., 3:N] - Y[..., 1:N - 2]) / (4.0 * k * N)
+    g[..., N - 1] = ((0.5 * Y[..., N] - Y[..., N - 2]) / (2.0 * (N - 1) * N) - 0.5 * Y[..., N] / (2.0 * (N + 1) * N)) / 2.0
+    g[..., N] = -Y[..., N - 1] / (2.0 * N * N)
+    y = dct1(g)
+    return s * (y - y[..., :1])
+
+
+def cufft_comparison(lgs=(16, 20, 22), reps=9):
+    """cuFFT-based product (torch.fft) against the library's product on 4 components, cold L2:
+    median ms of each and their relative difference (a comparison; the product path uses only
+    the library's own kernels)."""
+    import torch
+    from paper_2509_01855_gb300 import api
+    rows = {}
+    for lg in lgs:
+        N = 1 << lg
+        for name, dt in (("f64", torch.float64), ("f32", torch.float32)):
+            g = torch.Generator(device="cuda")
+            g.manual_seed(2509_01855)
+            v = torch.randn(4, N + 1, dtype=dt, device="cuda", generator=g)
+            plan = api.Plan(N, n_comp=4, max_batch=1, dtype=dt, t0=0.0, tf=TF)
+            vp = plan.empty(1)
+            vp[0, :, :N + 1] = v
+            op = plan.empty(1)
+            flush = l2_flush_buffer()
+            res = {}
+            for label, fn in (("library", lambda: api.birkhoff_apply(plan, vp, op)),
+                              ("cufft", lambda: cufft_product(v, 0.5 * TF))):
+                for _ in range(3):
+                    fn()
+                ts = []
+                for _ in range(reps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    fn()
+                    e1.record()
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                res[label] = statistics.median(ts)
+            ref = cufft_product(v, 0.5 * TF)
+            lib_out = api.birkhoff_apply(plan, vp, op)[0, :, :N + 1]
+            diff = float((lib_out - ref).norm() / ref.norm())
+            rows["%s_2p%d" % (name, lg)] = {"library_ms": round(res["library"], 5), "cufft_ms": round(res["cufft"], 5),
+                                            "rel_diff": diff}
+            plan.close()
+    return rows
+
+
 def dense_crossover(lgs=range(4, 11), reps=9):
     """FP32 products on 4 components, FFT chain vs the dense tensor-core product (the GPU
     analogue of the paper's Fig. BVisNlogN), cold L2: median ms of B v."""
@@ -538,7 +603,8 @@ def metric_name(args):
 
 
 def config(args):
-    prec = {"newton_f64": "f64", "newton_f32ir": "f32 Krylov + f64 refinement",
+    prec = {"newton_f64": "f64 (double-float arithmetic in the FP64 Birkhoff transforms from N = 2^18)",
+            "newton_f32ir": "f32 Krylov + f64 refinement",
             "apply_f64": "f64", "apply_f32": "f32", "serve": "f32ir"}[args.workload]
     c = {"workload": "orbit_raising_newton_krylov" if args.workload.startswith("newton") else "birkhoff_apply",
          "N": 1 << args.N, "nodes": (1 << args.N) + 1, "precision": prec,
@@ -648,6 +714,7 @@ def main():
     if args.sweep:
         line["apply_sweep"] = apply_sweep()
         line["dense_crossover"] = dense_crossover()
+        line["cufft_comparison"] = cufft_comparison()
         try:
             line["min_time_table"] = min_time_table()
         except Exception as e:  # the headline line must still print

@@ -256,6 +256,22 @@ bk_status bk_problem_set_params(bk_problem* prob, const double* params, int npar
  * extra (bk_krylov_workspace_bytes, bk_newton_workspace_bytes). For memory-based admission. */
 size_t bk_problem_device_bytes(const bk_problem* prob);
 
+/* Precision of the preconditioner of FP64 problems created after the call (the operator, the
+ * Krylov vectors and the Newton residual stay FP64):
+ *   mode 1: the preconditioner's node factors, scan levels, terminal Schur columns and sweeps in
+ *           FP32 (GB300 runs FP32 at 64x its FP64 rate). precond_apply then rounds its input to
+ *           FP32 and widens its output. Flexible GMRES builds the iterate from the preconditioned
+ *           vectors it actually computed, so the solution keeps FP64 accuracy; only the Krylov
+ *           iteration counts can change.
+ *   mode 0 (and -1, the default): FP64 preconditioner (environment BK_F64_PC32=1: FP32). On
+ *           the orbit solve at N = 2^20 the FP32 preconditioner needed 19 instead of 11 GMRES
+ *           iterations down to the tight final inner tolerances and was 13% slower overall.
+ * Host only; BK_ERR_ARG for any other mode. The paper's preconditioner is this one in FP64. */
+bk_status bk_set_f64_precond(int mode);
+
+/* *dtype = BK_F64 or BK_F32: the precision of the problem's preconditioner. */
+bk_status bk_problem_precond_dtype(const bk_problem* prob, int* dtype);
+
 /* Sizes of a problem (any pointer may be NULL):
  *   n_x, n_u, n_e  state, control and terminal-condition counts
  *   pitch          component block pitch in elements

@@ -102,6 +102,12 @@ def set_f64_transform(mode):
     L.check(L.lib().bk_set_f64_transform(int(mode)))
 
 
+def set_f64_precond(mode):
+    """Precision of the preconditioner of FP64 problems created afterwards: 1 FP32, 0 FP64, -1 the
+    default (FP64)."""
+    L.check(L.lib().bk_set_f64_precond(int(mode)))
+
+
 def _check_vec(plan, t, batch):
     if not t.is_cuda or t.dtype != plan.dtype:
         raise ValueError("expected a CUDA tensor of dtype %s" % plan.dtype)
@@ -180,6 +186,12 @@ class Problem:
 
     def device_bytes(self):
         return int(L.lib().bk_problem_device_bytes(self._h))
+
+    def precond_dtype(self):
+        """torch dtype of the preconditioner (float32 for FP64 problems with the FP32 preconditioner)."""
+        d = ctypes.c_int(0)
+        L.check(L.lib().bk_problem_precond_dtype(self._h, ctypes.byref(d)))
+        return _TORCH_DTYPE[d.value]
 
     def vec_len(self, op):
         return self.kkt_len if op == L.BK_OP_KKT else self.state_len

@@ -195,7 +195,11 @@ struct OpData {
 
 struct Problem {
   int kind = 0, n_x = 0, n_u = 0, n_e = 0;
-  int dtype = BK_F64;          // working precision of kkt/precond/krylov
+  int dtype = BK_F64;          // working precision of kkt/krylov (and of the operator)
+  int pdtype = BK_F64;         // precision of the preconditioner's data and sweeps (BK_F32 for an
+                               // FP64 problem created with the FP32 preconditioner)
+  void* pcin = nullptr;        // FP32 copies of a preconditioner input / output (kkt_len each),
+  void* pcout = nullptr;       // when pdtype differs from dtype
   int64_t N = 0, L = 0, P = 0;
   double t0 = 0, tf = 0, s = 0;
   double params[4] = {0, 0, 0, 0};
@@ -225,6 +229,7 @@ struct Problem {
   double dyn_param() const { return kind == BK_ORBIT_MT ? params[0] : 0.0; }
   int64_t state_len() const { return n_x * P; }
   OpData& work() { return dtype == BK_F64 ? d64 : d32; }
+  OpData& pre() { return pdtype == BK_F64 ? d64 : d32; }
 };
 
 // mu (nullable): s B^aT lambda at z_lin, already known to the caller (FP64, n_x * P); when

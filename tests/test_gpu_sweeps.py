@@ -25,13 +25,18 @@ pytestmark = pytest.mark.gpu
 RF, TF = 1.5, 20.0
 
 
-def _setup(N, dtype):
+def _setup(N, dtype, pc32=False):
     """Library problem, matrix-free oracle and a linearisation point (noisy spiral, random
-    multipliers) of the orbit problem."""
+    multipliers) of the orbit problem. FP64 problems get the FP64 preconditioner unless pc32."""
     from paper_2509_01855_gb300 import _lib, api
     oprob = op.Problem(op.ORBIT, 0.0, TF, (0.01, RF))
     M = MatFreeKKT(oprob, N)
-    prob = api.Problem(_lib.BK_ORBIT, N, dtype, 0.0, TF, (0.01, RF))
+    api.set_f64_precond(1 if pc32 else 0)
+    try:
+        prob = api.Problem(_lib.BK_ORBIT, N, dtype, 0.0, TF, (0.01, RF))
+    finally:
+        api.set_f64_precond(-1)
+    assert prob.precond_dtype() == (torch.float32 if pc32 else dtype)
     g = synth.rng("sweep-lin", N)
     X, U = synth.orbit_guess(M.t, RF, TF)
     X = X + 0.01 * g.standard_normal(X.shape)
@@ -127,3 +132,25 @@ def test_kkt_preconditioner_every_level(N, dtype):
     ref = M.precond_solve(d)
     # K-tilde is badly scaled (its control block is s w, w_0 ~ 1/N^2): relative 2-norm
     assert rel(got, ref) < (1e-10 if dtype == torch.float64 else 1e-3)
+
+
+@pytest.mark.parametrize("N", [1 << 16, 1 << 20])
+def test_fp64_problem_with_fp32_preconditioner(N):
+    """An FP64 problem whose preconditioner runs in FP32: precond_apply (FP64 in, FP64 out) within
+    the FP32 bound of the sweeps, for P^-1 and for K-tilde^-1."""
+    api, lib, prob, M, vec = _setup(N, torch.float64, pc32=True)
+    X, U, _, _ = M.split(vec)
+    Jx, _ = M.prob.jac(X, U)
+    Y = synth.gaussian((4, M.L), "sweep-rhs", N)
+    x = from_packed(prob, Y.ravel(), torch.float64, op_kkt=False)
+    out = torch.zeros_like(x)
+    api.precond_apply(prob, lib.BK_OP_STATE, x, out, transpose=False)
+    ref = ob.fastpinvy_block(M.s * M.w, Jx, Y)
+    assert rel(to_packed(prob, out, False), ref.ravel()) < 2e-5
+    if N <= 1 << 16:
+        M.linearize_precond(vec)
+        d = synth.gaussian(M.n, "kkt-pre-rhs", N)
+        xk = from_packed(prob, d, torch.float64)
+        ok = torch.zeros_like(xk)
+        api.precond_apply(prob, lib.BK_OP_KKT, xk, ok)
+        assert rel(to_packed(prob, ok), M.precond_solve(d)) < 1e-3
