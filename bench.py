@@ -411,6 +411,56 @@ def cufft_comparison(lgs=(16, 20, 22), reps=9):
     return rows
 
 
+def batched_apply(reps=15):
+    """Uneven-N batch of products (the serving mix's sizes: one plan of each N = 2^8..2^16 in each
+    precision, 4 components, one vector each): birkhoff_apply_batch against one birkhoff_apply per
+    plan, back to back (warm L2: the batch is ~20 MB), median ms, and the library launches each
+    takes."""
+    import torch
+    from paper_2509_01855_gb300 import _lib, api
+    rows = {}
+    lib = _lib.lib()
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        plans = [api.Plan(1 << k, n_comp=4, max_batch=1, dtype=dt, t0=0.0, tf=TF) for k in range(8, 17)]
+        vs, outs = [], []
+        for i, p in enumerate(plans):
+            v = p.empty(1)
+            g = torch.Generator(device="cuda")
+            g.manual_seed(100 + i)
+            v[0, :, :p.L] = torch.randn(4, p.L, dtype=dt, device="cuda", generator=g)
+            vs.append(v)
+            outs.append(p.empty(1))
+
+        def seq():
+            for p, v, o in zip(plans, vs, outs):
+                api.birkhoff_apply(p, v, o)
+
+        def bat():
+            api.birkhoff_apply_batch(plans, vs, outs)
+        res = {}
+        for label, fn in (("sequential", seq), ("batched", bat)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            c0 = lib.bk_launch_count()
+            fn()
+            torch.cuda.synchronize()
+            launches = lib.bk_launch_count() - c0
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            res[label] = {"ms": round(statistics.median(ts), 5), "launches": int(launches)}
+        rows[name] = dict(res, plans=len(plans), N="2^8..2^16", paths=sorted({p.shape()["path"] for p in plans}))
+        for p in plans:
+            p.close()
+    return rows
+
+
 def dense_crossover(lgs=range(4, 11), reps=9):
     """FP32 products on 4 components, FFT chain vs the dense tensor-core product (the GPU
     analogue of the paper's Fig. BVisNlogN), cold L2: median ms of B v."""
@@ -715,6 +765,7 @@ def main():
         line["apply_sweep"] = apply_sweep()
         line["dense_crossover"] = dense_crossover()
         line["cufft_comparison"] = cufft_comparison()
+        line["batched_apply"] = batched_apply()
         try:
             line["min_time_table"] = min_time_table()
         except Exception as e:  # the headline line must still print

@@ -113,6 +113,20 @@ bk_status bk_plan_grid(const bk_plan* plan, double* t_host, double* w_host);
  * closed form in Eq. c_k=bydef does. */
 bk_status birkhoff_apply(const bk_plan* plan, const void* v, void* out, int batch, void* stream);
 
+/* B v (trans = 0) or B^T v (trans = 1) for `count` plans of one dtype whose N may all differ,
+ * e.g. the requests of a serving batch: entry i computes out[i] = B_i v[i] for batch[i]
+ * vectors of plans[i], exactly as birkhoff_apply(_T)(plans[i], v[i], out[i], batch[i]) would
+ * (bitwise the same values). Plans on the single-CTA path run in one launch, plans on the
+ * unsplit four-step path in one launch per pass (five), each per 16 plans; dense, Bluestein,
+ * split and double-float plans run their own launches within the call.
+ *   plans, v, out, batch   host arrays of `count` entries (1 <= count <= 4096); v[i], out[i]
+ *                          device arrays as for birkhoff_apply; v[i] == out[i] is allowed, but
+ *                          different entries' vectors must not overlap
+ * A four-step plan may appear only once per call (it owns the scratch its passes use); all
+ * plans must have the same dtype. BK_ERR_ARG otherwise, before any work is queued. */
+bk_status birkhoff_apply_batch(const bk_plan* const* plans, const void* const* v, void* const* out,
+                               const int* batch, int count, int trans, void* stream);
+
 /* out = B v for callers that cannot allocate device memory. The paper has no counterpart: this
  * entry point exists for programs that must not call cudaMalloc once they are running, such as
  * real-time or flight control loops whose device memory budget is fixed at start-up, or host
@@ -335,6 +349,26 @@ size_t bk_krylov_workspace_bytes(const bk_problem* prob, int op, int restart);
 bk_status krylov_solve(bk_problem* prob, int op, const void* rhs, void* sol,
                        const bk_krylov_opts* opts, bk_krylov_info* info, void* workspace,
                        void* stream);
+
+/* How GMRES runs its Arnoldi steps (krylov_solve and the inner solves of newton_solve). The
+ * Hessenberg matrix, the Givens rotations and the stopping test always live on the device. With
+ * graphs, a restart cycle is one CUDA graph launch: a conditional WHILE node whose body is one
+ * Arnoldi step, repeated until the device says stop, then one bounded host wait; without them
+ * the host launches each step and reads the stop word after it. Both forms give bitwise the same
+ * iterates.
+ *   mode 0 (or -1, the default): never;  mode 1: for every problem of fixed final time.
+ * Graphs pay when a problem is solved repeatedly with unchanged parameters (the captured kernels
+ * take the time scale s by value, so a new t_f means a new capture).
+ * A problem captures a graph on its first solve for a given workspace and vector layout and keeps
+ * up to four; bk_problem_set_params drops them. Process-wide; host only. BK_ERR_ARG for any
+ * other mode. */
+bk_status bk_set_krylov_graphs(int mode);
+
+/* Bound on the host's wait for a graph cycle (seconds; <= 0 restores the default, 60 s). When a
+ * cycle has not finished within it, the solve returns BK_ERR_TIMEOUT while the cycle may still be
+ * running on the stream: synchronise the stream before reusing its vectors or the workspace.
+ * Process-wide; host only. BK_ERR_ARG above 1e6 s or for NaN. */
+bk_status bk_set_krylov_wait_limit(double seconds);
 
 typedef struct {
   double tol;         /* stop when the weighted KKT residual norm <= tol (default 1e-10)     */

@@ -24,7 +24,7 @@ EXPORTS = ["bk_last_error", "bk_version", "bk_launch_count", "bk_plan_create", "
            "bk_plan_grid", "birkhoff_apply", "birkhoff_apply_T", "birkhoff_apply_noalloc", "bk_plan_set_dense",
            "bk_plan_dense_state", "bk_plan_dense_check", "bk_plan_shape", "bk_set_f64_transform", "bk_plan_f64_mode",
            "bk_plan_dense_test_timeout", "birkhoff_apply_b", "birkhoff_apply_b_T",
-           "bk_set_f64_precond", "bk_problem_precond_dtype",
+           "bk_set_f64_precond", "bk_problem_precond_dtype", "bk_set_krylov_graphs", "bk_set_krylov_wait_limit", "birkhoff_apply_batch",
            "bk_problem_create",
            "bk_problem_destroy", "bk_problem_set_params", "bk_problem_device_bytes", "bk_problem_info", "bk_linearize", "kkt_apply",
            "precond_apply", "bk_krylov_workspace_bytes", "krylov_solve",
@@ -96,6 +96,9 @@ def lib():
         "birkhoff_apply_b": (c_int, [vp, vp, vp, c_int, vp]),
         "birkhoff_apply_b_T": (c_int, [vp, vp, vp, c_int, vp]),
         "bk_set_f64_precond": (c_int, [c_int]),
+        "bk_set_krylov_graphs": (c_int, [c_int]),
+        "birkhoff_apply_batch": (c_int, [vp, vp, vp, vp, c_int, c_int, vp]),
+        "bk_set_krylov_wait_limit": (c_int, [ctypes.c_double]),
         "bk_problem_precond_dtype": (c_int, [vp, ctypes.POINTER(c_int)]),
         "bk_plan_shape": (c_int, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                   ctypes.POINTER(c_int)]),

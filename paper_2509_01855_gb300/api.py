@@ -108,6 +108,17 @@ def set_f64_precond(mode):
     L.check(L.lib().bk_set_f64_precond(int(mode)))
 
 
+def set_krylov_graphs(mode):
+    """GMRES restart cycles as CUDA graphs: 0 or -1 (default) never, 1 for every problem of
+    fixed final time."""
+    L.check(L.lib().bk_set_krylov_graphs(int(mode)))
+
+
+def set_krylov_wait_limit(seconds):
+    """Bound (s) on the host wait for a GMRES graph cycle; <= 0 restores the default."""
+    L.check(L.lib().bk_set_krylov_wait_limit(float(seconds)))
+
+
 def _check_vec(plan, t, batch):
     if not t.is_cuda or t.dtype != plan.dtype:
         raise ValueError("expected a CUDA tensor of dtype %s" % plan.dtype)
@@ -133,6 +144,28 @@ def birkhoff_apply_T(plan, v, out, batch=None, stream=None):
     L.check(L.lib().birkhoff_apply_T(plan.handle, L.ptr(v), L.ptr(out), int(batch),
                                      L.stream_ptr(stream)))
     return out
+
+
+def birkhoff_apply_batch(plans, vs, outs, batches=None, trans=False, stream=None):
+    """out_i = B_i v_i (or B_i^T v_i) for plans of one dtype and any mix of N, in one call (one
+    launch per pass for the plans on the single-CTA and unsplit four-step paths)."""
+    n = len(plans)
+    if not (len(vs) == n and len(outs) == n) or n == 0:
+        raise ValueError("plans, vs and outs must have the same non-zero length")
+    if batches is None:
+        batches = [v.shape[0] if v.dim() == 3 else 1 for v in vs]
+    for p, v, o, b in zip(plans, vs, outs, batches):
+        _check_vec(p, v, b)
+        _check_vec(p, o, b)
+    def addr(x):
+        return x.value if isinstance(x, ctypes.c_void_p) else int(x)
+    arr_p = (ctypes.c_void_p * n)(*[addr(p.handle) for p in plans])
+    arr_v = (ctypes.c_void_p * n)(*[v.data_ptr() for v in vs])
+    arr_o = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    arr_b = (ctypes.c_int * n)(*[int(b) for b in batches])
+    L.check(L.lib().birkhoff_apply_batch(arr_p, arr_v, arr_o, arr_b, n, int(bool(trans)),
+                                         L.stream_ptr(stream)))
+    return outs
 
 
 def birkhoff_apply_b(plan, v, out, batch=None, stream=None):

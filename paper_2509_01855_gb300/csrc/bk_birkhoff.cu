@@ -41,6 +41,7 @@
 #include <tuple>
 #include <type_traits>
 #include <string>
+#include <vector>
 
 #include "bk_common.cuh"
 #include "bk_fft.cuh"
@@ -82,7 +83,13 @@ static thread_local size_t* g_alloc_acc = nullptr;
 AllocCounter::AllocCounter(size_t* acc) : prev(g_alloc_acc) { g_alloc_acc = acc; }
 AllocCounter::~AllocCounter() { g_alloc_acc = prev; }
 
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local unsigned long long t_launches = 0;
+void note_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+unsigned long long thread_launches() { return t_launches; }
+void note_launches(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   char buf[1024];
@@ -449,11 +456,13 @@ template <typename T> struct MaxThr { static constexpr int v = sizeof(T) == 8 ? 
 // per SM), FP64: 4 (FP64-pipe-bound, register-heavy).
 template <typename T> struct InFlight { static constexpr int v = sizeof(T) == 8 ? 4 : 8; };
 
+// Whole chain for vector vec in one CTA (every value independent of the CTA's thread count, so
+// a batched launch with more threads gives the same results).
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(MaxThr<T>::v)
-    k_birkhoff_small(const Us<T>* __restrict__ in, Us<T>* __restrict__ out, int N, int log2N, int64_t pitch,
-                     T s, const typename V2<T>::t* __restrict__ tw, const typename V2<T>::t* __restrict__ stw,
-                     const typename V2<T>::t* __restrict__ tpost, StencilTab<T> tb) {
+__device__ __forceinline__ void small_body(int vec, const Us<T>* __restrict__ in, Us<T>* __restrict__ out, int N,
+                                           int log2N, int64_t pitch, T s, const typename V2<T>::t* __restrict__ tw,
+                                           const typename V2<T>::t* __restrict__ stw,
+                                           const typename V2<T>::t* __restrict__ tpost, StencilTab<T> tb) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem[];
   const int L = N + 1;
@@ -461,7 +470,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
   T* X = reinterpret_cast<T*>(smem);
   T* Y = X + Lp;
   C* buf = reinterpret_cast<C*>(Y + Lp);
-  const int64_t base = (int64_t)blockIdx.x * pitch;
+  const int64_t base = (int64_t)vec * pitch;
   const Us<T>* src = in + base;
   Us<T>* dst = out + base;
   typedef Cv<T, Us<T>> CV;
@@ -484,6 +493,14 @@ __global__ void __launch_bounds__(MaxThr<T>::v)
   for (int m = L + threadIdx.x; m < pitch; m += blockDim.x) dst[m] = Us<T>(0);
 }
 
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(MaxThr<T>::v)
+    k_birkhoff_small(const Us<T>* __restrict__ in, Us<T>* __restrict__ out, int N, int log2N, int64_t pitch,
+                     T s, const typename V2<T>::t* __restrict__ tw, const typename V2<T>::t* __restrict__ stw,
+                     const typename V2<T>::t* __restrict__ tpost, StencilTab<T> tb) {
+  small_body<T, TRANS>(blockIdx.x, in, out, N, log2N, pitch, s, tw, stw, tpost, tb);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Four-step passes for large N (N = N1 * N2, j = N2 j1 + j2, k = k1 + N1 k2).
 // Pass A: per CTA, NB columns j2; FFT over j1 (length N1), twiddle omega_N^{j2 k1}; writes
@@ -499,7 +516,8 @@ __device__ __forceinline__ void passA_body(
             const typename V2<T>::t* __restrict__ twN, T invN, StencilTab<T> tb,
             const typename V2<T>::t* __restrict__ twLo,
             const typename V2<T>::t* __restrict__ twHi, int tw_h,
-            const typename V2<T>::t* __restrict__ tpost, const typename V2<T>::t* __restrict__ eo) {
+            const typename V2<T>::t* __restrict__ tpost, const typename V2<T>::t* __restrict__ eo,
+            int vec_in = -1, int nthr_in = 0) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem[];
   C* buf = reinterpret_cast<C*>(smem);
@@ -508,7 +526,11 @@ __device__ __forceinline__ void passA_body(
   const bool smem_tw = sizeof(T) == 4;
   if (smem_tw) load_tw_smem<T>(tws, stw, stage_tw_len(log2N1));
   __shared__ T red[32];
-  const int vec = blockIdx.y;
+  // vector and working thread count: blockIdx.y and blockDim.x, or given by a batched launch
+  // (whose CTAs may have more threads than this plan's; the extra ones only meet the barriers,
+  // so that the DC partial sums keep this plan's order)
+  const int vec = vec_in >= 0 ? vec_in : (int)blockIdx.y;
+  const int nt = nthr_in > 0 ? nthr_in : (int)blockDim.x;
   const St<T>* x = src + (int64_t)vec * src_stride;
   const int c0 = bid * NB;
   const int log2NB = __ffs(NB) - 1, log2N2 = __ffs(N2) - 1;  // NB, N2 are powers of two
@@ -523,11 +545,11 @@ __device__ __forceinline__ void passA_body(
   const int total = NB * N1;
   // independent element loads in flight per thread before the shared-memory stores
   constexpr int LD = InFlight<T>::v;
-  for (int idx0 = threadIdx.x; idx0 < total; idx0 += LD * blockDim.x) {
+  for (int idx0 = (int)threadIdx.x < nt ? (int)threadIdx.x : total; idx0 < total; idx0 += LD * nt) {
     C z[LD];
 #pragma unroll
     for (int u = 0; u < LD; ++u) {
-      const int idx = idx0 + u * blockDim.x;
+      const int idx = idx0 + u * nt;
       if (idx < total) {
         const int b = idx & (NB - 1);
         const int j = ((idx >> log2NB) << log2N2) + c0 + b;
@@ -541,7 +563,7 @@ __device__ __forceinline__ void passA_body(
     }
 #pragma unroll
     for (int u = 0; u < LD; ++u) {
-      const int idx = idx0 + u * blockDim.x;
+      const int idx = idx0 + u * nt;
       if (idx < total) {
         if (DC) dc += z[u].x + z[u].y;
         buf[(idx & (NB - 1)) * bs + padi(idx >> log2NB)] = z[u];
@@ -555,7 +577,7 @@ __device__ __forceinline__ void passA_body(
   }
   __syncthreads();
   if (DC && threadIdx.x < 32) {
-    T a = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
+    T a = (int)threadIdx.x < (nt >> 5) ? red[threadIdx.x] : T(0);
     for (int o = 16; o > 0; o >>= 1) a += shfl_xor(a, o);
     if (threadIdx.x == 0) partial[(int64_t)vec * nbid + bid] = a;
   }
@@ -637,11 +659,13 @@ __global__ void __launch_bounds__(MaxThr<T>::v, 2)
 // (the DC value R(x)_0 of the DCT, W = 1 at the ends, 2 inside) when `partial` is given. Fusing
 // the stencil into the pass-A loads instead exposes its neighbour loads: those passes ran
 // 25-40% longer than plain-load ones.
+// (bid, nbid, vec: block, blocks per vector and vector, from the launch or a batched launch;
+// 256 threads.)
 template <typename T, int K>
-__global__ void __launch_bounds__(256) k_stencil(const St<T>* __restrict__ stage, int64_t Ls, St<T>* __restrict__ G, int N,
-                                                 T sc, StencilTab<T> tb, T* __restrict__ partial) {
+__device__ __forceinline__ void stencil_body(int bid, int nbid, int vec, const St<T>* __restrict__ stage, int64_t Ls,
+                                             St<T>* __restrict__ G, int N, T sc, StencilTab<T> tb,
+                                             T* __restrict__ partial) {
   __shared__ T red[8];
-  const int vec = blockIdx.y;
   const St<T>* Y = stage + (int64_t)vec * Ls;
   St<T>* g = G + (int64_t)vec * Ls;
   typedef Cv<T, St<T>> CV;
@@ -649,13 +673,13 @@ __global__ void __launch_bounds__(256) k_stencil(const St<T>* __restrict__ stage
   // interior nodes 2..N-2 by the plain three-point formulas (the boundary cases, if-converted
   // into the same loop, tripled its FP64 instructions); the four boundary nodes by one thread
   const T* __restrict__ rk = tb.rk;
-  for (int m = 2 + blockIdx.x * blockDim.x + threadIdx.x; m <= N - 2; m += gridDim.x * blockDim.x) {
+  for (int m = 2 + bid * blockDim.x + threadIdx.x; m <= N - 2; m += nbid * blockDim.x) {
     const T ym = CV::in(Y[m - 1]), yp = CV::in(Y[m + 1]);
     const T x = K == ST_FWD ? (yp - ym) * (sc * rk[m]) : ym * rk[m - 1] - yp * rk[m + 1];
     g[m] = CV::out(x);
     acc += T(2) * x;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (bid == 0 && threadIdx.x == 0) {
     const int mb[4] = {0, 1, N - 1, N};
     for (int i = 0; i < 4; ++i) {
       const T x = load_x<T, K>(Y, mb[i], N, sc, T(0), tb);
@@ -670,9 +694,15 @@ __global__ void __launch_bounds__(256) k_stencil(const St<T>* __restrict__ stage
     if (threadIdx.x == 0) {
       T a = T(0);
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
-      partial[(int64_t)vec * gridDim.x + blockIdx.x] = a;
+      partial[(int64_t)vec * nbid + bid] = a;
     }
   }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_stencil(const St<T>* __restrict__ stage, int64_t Ls, St<T>* __restrict__ G, int N,
+                                                 T sc, StencilTab<T> tb, T* __restrict__ partial) {
+  stencil_body<T, K>(blockIdx.x, gridDim.x, blockIdx.y, stage, Ls, G, N, sc, tb, partial);
 }
 
 // Caller's vectors (pitch apart) converted to the arithmetic type T, Ls apart (double-float
@@ -776,7 +806,8 @@ __device__ __forceinline__ void passB_body(
             int bid, const typename V2<T>::t* __restrict__ Ain, typename OutS<T, E>::t* __restrict__ dst, int64_t dst_stride,
             int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial, int N, int N1,
             int N2, int log2N2, int P, const typename V2<T>::t* __restrict__ stw,
-            const typename V2<T>::t* __restrict__ tpost, T s, T invN, int ostride, int tps, int Npar) {
+            const typename V2<T>::t* __restrict__ tpost, T s, T invN, int ostride, int tps, int Npar,
+            int vec_in = -1, int nthr_in = 0) {
   typedef typename V2<T>::t C;
   extern __shared__ __align__(16) unsigned char smem[];
   const int bs = pad_stride(N2);
@@ -785,7 +816,9 @@ __device__ __forceinline__ void passB_body(
   const bool smem_tw = sizeof(T) == 4;
   if (smem_tw) load_tw_smem<T>(tws, stw, stage_tw_len(log2N2));
   __shared__ T red[32];
-  const int vec = blockIdx.y;
+  // as in passA_body: a batched launch gives the vector and this plan's thread count
+  const int vec = vec_in >= 0 ? vec_in : (int)blockIdx.y;
+  const int nt = nthr_in > 0 ? nthr_in : (int)blockDim.x;
   const C* A = Ain + (int64_t)vec * N;
   typename OutS<T, E>::t* out = dst + (int64_t)vec * dst_stride;
   const int p0 = bid * P;
@@ -793,12 +826,12 @@ __device__ __forceinline__ void passB_body(
   if (E == EP_STORE_TRN || E == EP_FWD_OUT) {
     T acc = T(0);
     const T* pp = partial + (int64_t)vec * n_partial;
-    for (int i = threadIdx.x; i < n_partial; i += blockDim.x) acc += pp[i];
+    for (int i = (int)threadIdx.x < nt ? (int)threadIdx.x : n_partial; i < n_partial; i += nt) acc += pp[i];
     for (int o = 16; o > 0; o >>= 1) acc += shfl_xor(acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
-      T a = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
+      T a = (int)threadIdx.x < (nt >> 5) ? red[threadIdx.x] : T(0);
       for (int o = 16; o > 0; o >>= 1) a += shfl_xor(a, o);
       if (threadIdx.x == 0) red[0] = a;
     }
@@ -975,6 +1008,112 @@ __global__ void __launch_bounds__(MaxThr<T>::v, 2)
   else
     passB_body<T, E, PB_ROWS>(b - h1 - h2, AinO, dst, dst_stride, 0, partial, n_partial, NO, N1O, N2O, log2N2O, PO,
                               stwO, tpost, s, invN, 1, 1, Npar);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched launches over plans of different N (birkhoff_apply_batch): one launch per pass covers
+// up to BATCH_MAX plans. A job is one plan's part of a launch (its vectors, CTAs per vector and
+// shapes); CTA b of the launch belongs to the job q with start[q] <= b < start[q + 1] and runs
+// that job's body with that plan's own thread count, so every value it writes is the one the
+// plan's own launch writes. The descriptors travel as __grid_constant__ kernel parameters.
+// ---------------------------------------------------------------------------------------------
+constexpr int BATCH_MAX = 16;
+
+template <typename T> struct SmallJob {
+  const T* in;
+  T* out;
+  int64_t pitch;
+  const typename V2<T>::t* tw;
+  const typename V2<T>::t* stw;
+  const typename V2<T>::t* tpost;
+  StencilTab<T> tb;
+  T s;
+  int N, log2N, nblk;
+};
+
+template <typename T> struct PassAJob {
+  const T* src;
+  int64_t sstride;
+  typename V2<T>::t* A;
+  T* partial;
+  const typename V2<T>::t* stw;
+  const typename V2<T>::t* twN;
+  const typename V2<T>::t* twLo;
+  const typename V2<T>::t* twHi;
+  StencilTab<T> tb;
+  T invN;
+  int N, N1, log2N1, N2, NB, bs, tw_h, nthr, nblk;
+};
+
+template <typename T> struct PassBJob {
+  const typename V2<T>::t* A;
+  T* dst;
+  int64_t dstride, zero_to;
+  const T* partial;
+  const typename V2<T>::t* stw;
+  const typename V2<T>::t* tpost;
+  T s, invN;
+  int npartial, N, N1, N2, log2N2, P, nthr, nblk;
+};
+
+template <typename T> struct StencilJob {
+  const T* stage;
+  T* G;
+  T* partial;
+  int64_t Ls;
+  StencilTab<T> tb;
+  int N, nblk;
+};
+
+template <typename J> struct Batch {
+  int njob;
+  int start[BATCH_MAX + 1];   // first CTA of each job; start[njob] = the launch's CTAs
+  J j[BATCH_MAX];
+};
+
+template <typename J>
+__device__ __forceinline__ int batch_job(const Batch<J>& b, int cta) {
+  int q = 0;
+  while (q + 1 < b.njob && cta >= b.start[q + 1]) ++q;
+  return q;
+}
+
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(MaxThr<T>::v) k_small_batch(const __grid_constant__ Batch<SmallJob<T>> b) {
+  const int q = batch_job(b, blockIdx.x);
+  const SmallJob<T>& J = b.j[q];
+  small_body<T, TRANS>((int)blockIdx.x - b.start[q], J.in, J.out, J.N, J.log2N, J.pitch, J.s, J.tw, J.stw, J.tpost,
+                       J.tb);
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(MaxThr<T>::v, 2) k_passA_batch(const __grid_constant__ Batch<PassAJob<T>> b) {
+  const int q = batch_job(b, blockIdx.x);
+  const PassAJob<T>& J = b.j[q];
+  const int local = (int)blockIdx.x - b.start[q];
+  const int vec = local / J.nblk;
+  passA_body<T, K, PM_FULL>(local - vec * J.nblk, J.nblk, J.src, J.sstride, J.A, J.partial, J.N, J.N1, J.log2N1, J.N2,
+                            J.NB, J.bs, J.stw, J.twN, J.invN, J.tb, J.twLo, J.twHi, J.tw_h, nullptr, nullptr, vec,
+                            J.nthr);
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(MaxThr<T>::v, 2) k_passB_batch(const __grid_constant__ Batch<PassBJob<T>> b) {
+  const int q = batch_job(b, blockIdx.x);
+  const PassBJob<T>& J = b.j[q];
+  const int local = (int)blockIdx.x - b.start[q];
+  const int vec = local / J.nblk;
+  passB_body<T, E, PB_PAIRS>(local - vec * J.nblk, J.A, J.dst, J.dstride, J.zero_to, J.partial, J.npartial, J.N, J.N1,
+                             J.N2, J.log2N2, J.P, J.stw, J.tpost, J.s, J.invN, 1, 1, J.N, vec, J.nthr);
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_stencil_batch(const __grid_constant__ Batch<StencilJob<T>> b) {
+  const int q = batch_job(b, blockIdx.x);
+  const StencilJob<T>& J = b.j[q];
+  const int local = (int)blockIdx.x - b.start[q];
+  const int vec = local / J.nblk;
+  stencil_body<T, K>(local - vec * J.nblk, J.nblk, vec, J.stage, J.Ls, J.G, J.N, T(1), J.tb, J.partial);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1263,8 +1402,20 @@ bk_status set_smem_attrs(const Plan* p) {
     const int cap = (int)smem_small<T>(p->dtype == BK_F64 ? 4096 : 8192);
     BK_TRY(smem_attr(k_birkhoff_small<T, false>, cap));
     BK_TRY(smem_attr(k_birkhoff_small<T, true>, cap));
+    if constexpr (!std::is_same<T, dfl>::value) {
+      BK_TRY(smem_attr(k_small_batch<T, false>, cap));
+      BK_TRY(smem_attr(k_small_batch<T, true>, cap));
+    }
   } else {
     const int cap = (int)FOURSTEP_SMEM_BUDGET;
+    if constexpr (!std::is_same<T, dfl>::value) {
+      BK_TRY(smem_attr(k_passA_batch<T, IN_PLAIN>, cap));
+      BK_TRY(smem_attr(k_passA_batch<T, IN_WINV>, cap));
+      BK_TRY(smem_attr(k_passB_batch<T, EP_STORE>, cap));
+      BK_TRY(smem_attr(k_passB_batch<T, EP_STORE_TRN>, cap));
+      BK_TRY(smem_attr(k_passB_batch<T, EP_FWD_OUT>, cap));
+      BK_TRY(smem_attr(k_passB_batch<T, EP_TRN_OUT>, cap));
+    }
     BK_TRY(smem_attr(k_passA<T, IN_PLAIN>, cap));
     BK_TRY(smem_attr(k_passA<T, IN_WINV>, cap));
     if constexpr (std::is_same<T, double>::value) {
@@ -1846,6 +1997,187 @@ bk_status apply_impl(const Plan* p, const Us<T>* vu, Us<T>* out, int nvec, bool 
   return BK_OK;
 }
 
+// Batched products of plans of one precision T (binary32 or binary64 arithmetic): the small
+// plans' chains in one launch, the unsplit four-step plans' five passes in one launch each, per
+// chunk of BATCH_MAX plans. Each plan uses its own tables and scratch, so a plan appears at most
+// once among the four-step ones (the caller checks). vec[i] / out[i]: nv[i] vectors pitch apart.
+template <typename T>
+static bk_status launch_small_batch(const Plan* const* ps, const void* const* vin, void* const* vout, const int* nv,
+                                    int n, bool trans, cudaStream_t st) {
+  typedef typename V2<T>::t C;
+  for (int c0 = 0; c0 < n; c0 += BATCH_MAX) {
+    Batch<SmallJob<T>> b;
+    memset(&b, 0, sizeof(b));
+    b.njob = std::min(BATCH_MAX, n - c0);
+    int thr = 32;
+    size_t smem = 0;
+    int cta = 0;
+    for (int q = 0; q < b.njob; ++q) {
+      const Plan* p = ps[c0 + q];
+      SmallJob<T>& J = b.j[q];
+      J.in = (const T*)vin[c0 + q];
+      J.out = (T*)vout[c0 + q];
+      J.pitch = p->pitch;
+      J.tw = (const C*)p->tw;
+      J.stw = (const C*)p->stwS;
+      J.tpost = (const C*)p->tpost;
+      J.tb.rk = (const T*)p->rk;
+      J.tb.cN = (T)(1.0 / (4.0 * ((double)p->N * (double)p->N - 1.0)));
+      J.s = (T)p->s;
+      J.N = (int)p->N;
+      J.log2N = ilog2(p->N);
+      J.nblk = 1;
+      b.start[q] = cta;
+      cta += nv[c0 + q];
+      thr = std::max(thr, p->thrS);
+      smem = std::max(smem, p->smemS);
+    }
+    b.start[b.njob] = cta;
+    if (!trans)
+      k_small_batch<T, false><<<cta, thr, smem, st>>>(b);
+    else
+      k_small_batch<T, true><<<cta, thr, smem, st>>>(b);
+    BK_CHECK_LAUNCH();
+  }
+  return BK_OK;
+}
+
+template <typename T>
+static bk_status launch_fourstep_batch(const Plan* const* ps, const void* const* vin, void* const* vout, const int* nv,
+                                       int n, bool trans, cudaStream_t st) {
+  typedef typename V2<T>::t C;
+  for (int c0 = 0; c0 < n; c0 += BATCH_MAX) {
+    const int nj = std::min(BATCH_MAX, n - c0);
+    Batch<PassAJob<T>> a1, a2;
+    Batch<PassBJob<T>> b1, b2;
+    Batch<StencilJob<T>> sj;
+    memset(&a1, 0, sizeof(a1));
+    memset(&b1, 0, sizeof(b1));
+    memset(&sj, 0, sizeof(sj));
+    a1.njob = b1.njob = sj.njob = nj;
+    int thrA = 32, thrB = 32;
+    size_t smA = 0, smB = 0;
+    int ca = 0, cb = 0, cs = 0;
+    for (int q = 0; q < nj; ++q) {
+      const Plan* p = ps[c0 + q];
+      const FourStep& f = p->fs;
+      const int N = (int)p->N;
+      const int64_t Ls = N + 1;
+      const int nvec = nv[c0 + q];
+      StencilTab<T> tb;
+      tb.rk = (const T*)p->rk;
+      tb.cN = (T)(1.0 / (4.0 * ((double)N * (double)N - 1.0)));
+      const T invN = T(1.0 / (double)N);
+      PassAJob<T>& A = a1.j[q];
+      A.src = (const T*)vin[c0 + q];
+      A.sstride = p->pitch;
+      A.A = (C*)p->scrA;
+      A.partial = (T*)p->part1;
+      A.stw = (const C*)f.stw1;
+      A.twN = (const C*)f.twN;
+      A.twLo = (const C*)f.twLo;
+      A.twHi = (const C*)f.twHi;
+      A.tb = tb;
+      A.invN = invN;
+      A.N = N;
+      A.N1 = f.N1;
+      A.log2N1 = ilog2(f.N1);
+      A.N2 = f.N2;
+      A.NB = f.NB;
+      A.bs = f.bsA;
+      A.tw_h = f.tw_h;
+      A.nthr = f.thrA;
+      A.nblk = f.N2 / f.NB;
+      a1.start[q] = ca;
+      ca += A.nblk * nvec;
+      PassBJob<T>& B = b1.j[q];
+      B.A = (const C*)p->scrA;
+      B.dst = (T*)p->scrY;
+      B.dstride = Ls;
+      B.zero_to = 0;
+      B.partial = trans ? (const T*)p->part1 : nullptr;
+      B.npartial = trans ? f.nPartA : 0;
+      B.stw = (const C*)f.stw2;
+      B.tpost = (const C*)p->tpost;
+      B.s = (T)p->s;
+      B.invN = invN;
+      B.N = N;
+      B.N1 = f.N1;
+      B.N2 = f.N2;
+      B.log2N2 = ilog2(f.N2);
+      B.P = f.P;
+      B.nthr = f.thrB;
+      B.nblk = f.N1 / 2 / f.P;
+      b1.start[q] = cb;
+      cb += B.nblk * nvec;
+      StencilJob<T>& S = sj.j[q];
+      S.stage = (const T*)p->scrY;
+      S.G = (T*)p->scrG;
+      S.partial = trans ? nullptr : (T*)p->part2;
+      S.Ls = Ls;
+      S.tb = tb;
+      S.N = N;
+      S.nblk = f.nPartA;
+      sj.start[q] = cs;
+      cs += S.nblk * nvec;
+      thrA = std::max(thrA, f.thrA);
+      thrB = std::max(thrB, f.thrB);
+      smA = std::max(smA, f.smemA);
+      smB = std::max(smB, f.smemB);
+    }
+    a1.start[nj] = ca;
+    b1.start[nj] = cb;
+    sj.start[nj] = cs;
+    // second DCT: pass A reads the stencil buffer, pass B writes the caller's vectors
+    a2 = a1;
+    b2 = b1;
+    for (int q = 0; q < nj; ++q) {
+      const Plan* p = ps[c0 + q];
+      a2.j[q].src = (const T*)p->scrG;
+      a2.j[q].sstride = p->N + 1;
+      a2.j[q].partial = (T*)p->part2;
+      b2.j[q].dst = (T*)vout[c0 + q];
+      b2.j[q].dstride = p->pitch;
+      b2.j[q].zero_to = p->pitch;
+      b2.j[q].partial = trans ? nullptr : (const T*)p->part2;
+      b2.j[q].npartial = trans ? 0 : p->fs.nPartA;
+    }
+    if (!trans) {
+      k_passA_batch<T, IN_PLAIN><<<ca, thrA, smA, st>>>(a1);
+      BK_CHECK_LAUNCH();
+      k_passB_batch<T, EP_STORE><<<cb, thrB, smB, st>>>(b1);
+      BK_CHECK_LAUNCH();
+      k_stencil_batch<T, ST_FWD><<<cs, 256, 0, st>>>(sj);
+      BK_CHECK_LAUNCH();
+      k_passA_batch<T, IN_PLAIN><<<ca, thrA, smA, st>>>(a2);
+      BK_CHECK_LAUNCH();
+      k_passB_batch<T, EP_FWD_OUT><<<cb, thrB, smB, st>>>(b2);
+      BK_CHECK_LAUNCH();
+    } else {
+      k_passA_batch<T, IN_WINV><<<ca, thrA, smA, st>>>(a1);
+      BK_CHECK_LAUNCH();
+      k_passB_batch<T, EP_STORE_TRN><<<cb, thrB, smB, st>>>(b1);
+      BK_CHECK_LAUNCH();
+      k_stencil_batch<T, ST_TRN><<<cs, 256, 0, st>>>(sj);
+      BK_CHECK_LAUNCH();
+      k_passA_batch<T, IN_PLAIN><<<ca, thrA, smA, st>>>(a2);
+      BK_CHECK_LAUNCH();
+      k_passB_batch<T, EP_TRN_OUT><<<cb, thrB, smB, st>>>(b2);
+      BK_CHECK_LAUNCH();
+    }
+  }
+  return BK_OK;
+}
+
+template <typename T>
+bk_status apply_batch_impl(const Plan* const* small_p, const void* const* small_v, void* const* small_o,
+                           const int* small_n, int nsmall, const Plan* const* fs_p, const void* const* fs_v,
+                           void* const* fs_o, const int* fs_n, int nfs, bool trans, cudaStream_t st) {
+  if (nsmall > 0) BK_TRY(launch_small_batch<T>(small_p, small_v, small_o, small_n, nsmall, trans, st));
+  if (nfs > 0) BK_TRY(launch_fourstep_batch<T>(fs_p, fs_v, fs_o, fs_n, nfs, trans, st));
+  return BK_OK;
+}
+
 #ifndef BK_TRANSFORM_KERNEL_UNIT
 extern template bk_status apply_impl<double>(const Plan* p, const double* v, double* out, int nvec, bool trans,
                                              double s_scale, cudaStream_t st, void* scrA, void* scrY, void* part1,
@@ -1853,6 +2185,12 @@ extern template bk_status apply_impl<double>(const Plan* p, const double* v, dou
 extern template bk_status apply_impl<float>(const Plan* p, const float* v, float* out, int nvec, bool trans,
                                             double s_scale, cudaStream_t st, void* scrA, void* scrY, void* part1,
                                             void* part2, void* scrG);
+extern template bk_status apply_batch_impl<double>(const Plan* const*, const void* const*, void* const*,
+                                                   const int*, int, const Plan* const*, const void* const*,
+                                                   void* const*, const int*, int, bool, cudaStream_t);
+extern template bk_status apply_batch_impl<float>(const Plan* const*, const void* const*, void* const*, const int*,
+                                                  int, const Plan* const*, const void* const*, void* const*,
+                                                  const int*, int, bool, cudaStream_t);
 extern template bk_status apply_impl<dfl>(const Plan* p, const double* v, double* out, int nvec, bool trans,
                                           double s_scale, cudaStream_t st, void* scrA, void* scrY, void* part1,
                                           void* part2, void* scrG);
@@ -1935,6 +2273,48 @@ bk_status plan_apply(const Plan* p, const void* v, void* out, int batch, bool tr
   BK_ARG(batch >= 1 && batch <= p->max_batch, "batch %d outside [1, max_batch=%d]", batch, p->max_batch);
   BK_ARG(((uintptr_t)v & 15) == 0 && ((uintptr_t)out & 15) == 0, "vectors must be 16-byte aligned");
   return plan_apply_n(p, v, out, batch * p->n_comp, trans, p->s, st);
+}
+
+// Products of several plans of one precision, N free per plan: small plans in one launch, unsplit
+// four-step plans in one launch per pass (per BATCH_MAX plans), every other plan (dense,
+// Bluestein, split, double-float) by its own launches.
+bk_status plan_apply_batch(const Plan* const* ps, const void* const* v, void* const* out, const int* batch, int count,
+                           bool trans, cudaStream_t st) {
+  BK_ARG(ps != nullptr && v != nullptr && out != nullptr && batch != nullptr, "NULL argument");
+  BK_ARG(count >= 1 && count <= 4096, "count %d outside [1, 4096]", count);
+  BK_ARG(ps[0] != nullptr, "plan 0 is NULL");
+  const int dtype = ps[0]->dtype;
+  std::vector<const Plan*> sp, fp, op;
+  std::vector<const void*> sv, fv, ov;
+  std::vector<void*> so, fo, oo;
+  std::vector<int> sn, fn, on;
+  for (int i = 0; i < count; ++i) {
+    const Plan* p = ps[i];
+    BK_ARG(p != nullptr, "plan %d is NULL", i);
+    BK_ARG(p->dtype == dtype, "plan %d: every plan of a batch has the same dtype", i);
+    BK_ARG(v[i] != nullptr && out[i] != nullptr, "entry %d: NULL vector", i);
+    BK_ARG(batch[i] >= 1 && batch[i] <= p->max_batch, "entry %d: batch %d outside [1, max_batch=%d]", i, batch[i],
+           p->max_batch);
+    BK_ARG(((uintptr_t)v[i] & 15) == 0 && ((uintptr_t)out[i] & 15) == 0, "entry %d: vectors must be 16-byte aligned",
+           i);
+    const int nv = batch[i] * p->n_comp;
+    if (p->dense || p->blue || p->split || p->df) {
+      op.push_back(p); ov.push_back(v[i]); oo.push_back(out[i]); on.push_back(nv);
+    } else if (p->small) {
+      sp.push_back(p); sv.push_back(v[i]); so.push_back(out[i]); sn.push_back(nv);
+    } else {
+      for (const Plan* q : fp) BK_ARG(q != p, "entry %d: a four-step plan may appear once per batch (its scratch)", i);
+      fp.push_back(p); fv.push_back(v[i]); fo.push_back(out[i]); fn.push_back(nv);
+    }
+  }
+  if (dtype == BK_F64)
+    BK_TRY(apply_batch_impl<double>(sp.data(), sv.data(), so.data(), sn.data(), (int)sp.size(), fp.data(), fv.data(),
+                                    fo.data(), fn.data(), (int)fp.size(), trans, st));
+  else
+    BK_TRY(apply_batch_impl<float>(sp.data(), sv.data(), so.data(), sn.data(), (int)sp.size(), fp.data(), fv.data(),
+                                   fo.data(), fn.data(), (int)fp.size(), trans, st));
+  for (size_t k = 0; k < op.size(); ++k) BK_TRY(plan_apply_n(op[k], ov[k], oo[k], on[k], trans, op[k]->s, st));
+  return BK_OK;
 }
 
 #endif  // BK_TRANSFORM_KERNEL_UNIT
@@ -2107,6 +2487,12 @@ bk_status birkhoff_apply_b(const bk_plan* plan, const void* v, void* out, int ba
 
 bk_status birkhoff_apply_b_T(const bk_plan* plan, const void* v, void* out, int batch, void* stream) {
   return bk::plan_apply_b(reinterpret_cast<const bk::Plan*>(plan), v, out, batch, true, (cudaStream_t)stream);
+}
+
+bk_status birkhoff_apply_batch(const bk_plan* const* plans, const void* const* v, void* const* out, const int* batch,
+                               int count, int trans, void* stream) {
+  return bk::plan_apply_batch(reinterpret_cast<const bk::Plan* const*>(plans), v, out, batch, count, trans != 0,
+                              (cudaStream_t)stream);
 }
 
 bk_status birkhoff_apply_T(const bk_plan* plan, const void* v, void* out, int batch, void* stream) {

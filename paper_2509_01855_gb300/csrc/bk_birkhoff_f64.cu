@@ -9,6 +9,9 @@ namespace bk {
 
 template bk_status set_smem_attrs<double>(const Plan* p);
 template bk_status blue_spectrum<double>(Plan* p, cudaStream_t st);
+template bk_status apply_batch_impl<double>(const Plan* const*, const void* const*, void* const*, const int*, int,
+                                        const Plan* const*, const void* const*, void* const*, const int*, int, bool,
+                                        cudaStream_t);
 template bk_status apply_impl<double>(const Plan* p, const double* v, double* out, int nvec, bool trans, double s_scale,
                                      cudaStream_t st, void* scrA, void* scrY, void* part1, void* part2, void* scrG);
 

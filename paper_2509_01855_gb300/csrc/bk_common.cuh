@@ -31,8 +31,12 @@ void set_error(const char* fmt, ...);
   } while (0)
 
 // Every kernel launch of the library is followed by BK_CHECK_LAUNCH(), which also counts it
-// (bk_launch_count()).
+// (bk_launch_count()). Kernels captured into a graph are counted when the graph runs instead:
+// the capture takes its own launches back (note_launches(-k), k from thread_launches(), the
+// calling thread's count) and each execution adds the kernels it ran.
 void note_launch();
+unsigned long long thread_launches();
+void note_launches(long long n);
 #define BK_CHECK_LAUNCH()          \
   do {                             \
     bk::note_launch();             \

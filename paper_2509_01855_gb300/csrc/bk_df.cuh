@@ -76,15 +76,54 @@ template <> __device__ __forceinline__ dfl2 ldg<dfl2>(const dfl2* p) {
 template <typename T> struct User { typedef T t; };
 template <> struct User<dfl> { typedef double t; };
 
-// binary64 <-> double-float (one rounding each way; the FP64 pipe does the subtraction and the
-// conversions, so these run once per element, in the first and the last kernel of a product)
+// binary64 <-> double-float. GB300's FP64 pipe (which also converts between binary64 and
+// binary32) runs 2 lane operations per clock per SM, so the conversions work on the bit fields
+// with integer operations where the exponents allow it:
+//   d2df: hi = x with its significand truncated to 24 bits (exact), lo = the remaining 29 bits,
+//         an integer r < 2^29 times 2^(e - 1075), converted to binary32 (one rounding, relative
+//         error 2^-24 of lo, i.e. 2^-48 of x) and scaled by that power of two, with x's sign.
+//         Zeros, and exponents whose hi or lo would leave the normal binary32 range, take the
+//         FP64 route: hi = rn(x), lo = rn(x - hi).
+//   df2d: hi and lo widen exactly by moving their fields into binary64 (normal binary32 values;
+//         others take the FP64 conversion), then one binary64 addition.
 __device__ __forceinline__ dfl d2df(double x) {
-  const float h = __double2float_rn(x);
-  return dfl(h, __double2float_rn(x - (double)h));
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ff);
+  if ((u << 1) == 0) return dfl(__uint_as_float((unsigned)(u >> 32)), 0.f);   // +-0
+  if (e < 1023 - 126 + 53 || e > 1023 + 127) {   // tiny, huge or special: FP64 route
+    const float h = __double2float_rn(x);
+    return dfl(h, __double2float_rn(x - (double)h));
+  }
+  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+  const unsigned long long m = u & 0xfffffffffffffull;
+  const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(m >> 29));
+  const unsigned r = (unsigned)(m & 0x1fffffffu);
+  const float scale = __uint_as_float((unsigned)(e - 1075 + 127) << 23);   // 2^(e - 1075), normal here
+  const float lo = __fmul_rn(__uint2float_rn(r), scale);
+  return dfl(hi, __uint_as_float(__float_as_uint(lo) | sign));
 }
-__device__ __forceinline__ double df2d(dfl x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned ef = (b >> 23) & 0xff;
+  if (ef == 0 || ef == 0xff) return (double)f;   // zero, subnormal, inf, nan
+  const unsigned long long db = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                ((unsigned long long)(ef - 127 + 1023) << 52) |
+                                ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)db);
+}
+__device__ __forceinline__ double df2d(dfl x) { return f2d_bits(x.hi) + f2d_bits(x.lo); }
 
 // Warp shuffles of the arithmetic types (one per binary32 word for dfl).
+__device__ __forceinline__ float shfl_up(float v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ double shfl_up(double v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ dfl shfl_up(dfl v, int d) {
+  return dfl(__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d));
+}
+__device__ __forceinline__ float shfl_down(float v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ double shfl_down(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ dfl shfl_down(dfl v, int d) {
+  return dfl(__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d));
+}
 __device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ dfl shfl_xor(dfl v, int o) {

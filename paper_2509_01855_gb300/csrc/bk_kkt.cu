@@ -360,7 +360,7 @@ __device__ __forceinline__ void warp_scan(const T* __restrict__ m, int64_t slot,
     T pe[NX];
 #pragma unroll
     for (int r = 0; r < NX; ++r)
-      pe[r] = DIR == 0 ? __shfl_up_sync(0xffffffffu, e[r], d) : __shfl_down_sync(0xffffffffu, e[r], d);
+      pe[r] = DIR == 0 ? shfl_up(e[r], d) : shfl_down(e[r], d);
     const bool act = DIR == 0 ? lane >= d : lane + d < 32;
     if (act) {
       const int64_t item = blk * 32 + (DIR == 0 ? lane : lane + d - 1);
@@ -438,15 +438,12 @@ __device__ __forceinline__ bool nonzero(float x) { return (__float_as_int(x) << 
 // offsets are all zero has zero scan values: the terminal Schur columns' right-hand sides are
 // unit vectors at the last node, so their up passes do almost no FP64 work.
 template <typename T, int NX, int DIR>
-__global__ void __launch_bounds__(128) k_sw_up0(const T* __restrict__ Kn, const T* __restrict__ Nn,
-                                                const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
-                                                int64_t L, const T* __restrict__ w, T s, Levels<T> lv) {
+__device__ __forceinline__ void sw_up0_warp(int g, SweepTiles<T, NX>& tl, const T* __restrict__ Kn,
+                                            const T* __restrict__ Nn, const T* __restrict__ Y,
+                                            const T* __restrict__ G, int64_t P, int64_t L, const T* __restrict__ w,
+                                            T s, const Levels<T>& lv) {
   constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS, SEG = Seg<T>::v;
-  __shared__ SweepTiles<T, NX> tiles[4];
   const int nblk = (lv.n[0] + 31) >> 5;
-  const int g = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (g >= nblk) return;  // whole warps
-  SweepTiles<T, NX>& tl = tiles[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int64_t seg0 = (int64_t)g * 32;
   const int64_t seg = seg0 + lane;
@@ -504,11 +501,9 @@ __global__ void __launch_bounds__(128) k_sw_up0(const T* __restrict__ Kn, const 
 
 // Up, level l >= 1 (one warp per block of 32 items): scan of the items' offsets.
 template <typename T, int NX, int DIR>
-__global__ void __launch_bounds__(128) k_sw_upL(Levels<T> lv, int l) {
+__device__ __forceinline__ void sw_upL_warp(int b, const Levels<T>& lv, int l) {
   const int n = lv.n[l];
   const int nblk = (n + 31) >> 5;
-  const int b = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (b >= nblk) return;
   const int lane = threadIdx.x & 31;
   const int64_t i = (int64_t)b * 32 + lane;
   const T* o = lv.o[l];
@@ -533,17 +528,14 @@ __global__ void __launch_bounds__(128) k_sw_upL(Levels<T> lv, int l) {
 // Down (one warp per block of 32 segments): incoming state of the lane's segment, composed from
 // the top level down, then the segment's nodes with outputs (staged like the inputs).
 template <typename T, int NX, int DIR>
-__global__ void __launch_bounds__(128) k_sw_down0(const T* __restrict__ Kn, const T* __restrict__ Nn,
-                                                  const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
-                                                  int64_t L, const T* __restrict__ w, T s, Levels<T> lv,
-                                                  T* __restrict__ out, T* __restrict__ bout) {
+__device__ __forceinline__ void sw_down0_warp(int g, SweepTiles<T, NX>& tl, const T* __restrict__ Kn,
+                                              const T* __restrict__ Nn, const T* __restrict__ Y,
+                                              const T* __restrict__ G, int64_t P, int64_t L,
+                                              const T* __restrict__ w, T s, const Levels<T>& lv,
+                                              T* __restrict__ out, T* __restrict__ bout) {
   constexpr int NC = NX * NX;
   constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS, SEG = Seg<T>::v;
-  __shared__ SweepTiles<T, NX> tiles[4];
   const int nblk0 = (lv.n[0] + 31) >> 5;
-  const int g = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (g >= nblk0) return;  // whole warps
-  SweepTiles<T, NX>& tl = tiles[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const int64_t seg0 = (int64_t)g * 32;
   const int64_t seg = seg0 + lane;
@@ -619,13 +611,69 @@ __global__ void __launch_bounds__(128) k_sw_down0(const T* __restrict__ Kn, cons
   }
 }
 
+// The sweep kernels: one warp per block of 32 items, W warps per CTA (4; 1 for grids whose
+// level 0 has fewer blocks than four per SM, so that their warps spread over the SMs: each
+// warp's segments are sequential chains whose FP64 arithmetic would otherwise share one SM's
+// FP64 pipe).
+template <typename T, int NX, int DIR, int W>
+__global__ void __launch_bounds__(32 * W) k_sw_up0(const T* __restrict__ Kn, const T* __restrict__ Nn,
+                                                   const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
+                                                   int64_t L, const T* __restrict__ w, T s, Levels<T> lv) {
+  __shared__ SweepTiles<T, NX> tiles[W];
+  const int g = blockIdx.x * W + (threadIdx.x >> 5);
+  if (g >= ((lv.n[0] + 31) >> 5)) return;  // whole warps
+  sw_up0_warp<T, NX, DIR>(g, tiles[threadIdx.x >> 5], Kn, Nn, Y, G, P, L, w, s, lv);
+}
+
+template <typename T, int NX, int DIR, int W>
+__global__ void __launch_bounds__(32 * W) k_sw_upL(Levels<T> lv, int l) {
+  const int b = blockIdx.x * W + (threadIdx.x >> 5);
+  if (b >= ((lv.n[l] + 31) >> 5)) return;
+  sw_upL_warp<T, NX, DIR>(b, lv, l);
+}
+
+template <typename T, int NX, int DIR, int W>
+__global__ void __launch_bounds__(32 * W) k_sw_down0(const T* __restrict__ Kn, const T* __restrict__ Nn,
+                                                     const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
+                                                     int64_t L, const T* __restrict__ w, T s, Levels<T> lv,
+                                                     T* __restrict__ out, T* __restrict__ bout) {
+  __shared__ SweepTiles<T, NX> tiles[W];
+  const int g = blockIdx.x * W + (threadIdx.x >> 5);
+  if (g >= ((lv.n[0] + 31) >> 5)) return;  // whole warps
+  sw_down0_warp<T, NX, DIR>(g, tiles[threadIdx.x >> 5], Kn, Nn, Y, G, P, L, w, s, lv, out, bout);
+}
+
+// The whole sweep in one CTA for small grids (at most two scan levels and SW1_MAXW blocks of 32
+// segments): one warp per block; the level-0 up pass, the level-1 scan by warp 0 and the down
+// pass are separated by barriers instead of launches (1 launch instead of nlev + 1; the serving
+// mix's small problems run many sweeps per Newton step).
+constexpr int SW1_MAXW = 16;
+template <typename T, int NX, int DIR>
+__global__ void __launch_bounds__(32 * SW1_MAXW) k_sw_one(const T* __restrict__ Kn, const T* __restrict__ Nn,
+                                                          const T* __restrict__ Y, const T* __restrict__ G,
+                                                          int64_t P, int64_t L, const T* __restrict__ w, T s,
+                                                          Levels<T> lv, T* __restrict__ out, T* __restrict__ bout) {
+  extern __shared__ __align__(16) unsigned char sw1_smem[];
+  SweepTiles<T, NX>* tiles = reinterpret_cast<SweepTiles<T, NX>*>(sw1_smem);
+  const int warp = threadIdx.x >> 5;
+  const int nblk0 = (lv.n[0] + 31) >> 5;
+  if (warp < nblk0) sw_up0_warp<T, NX, DIR>(warp, tiles[warp], Kn, Nn, Y, G, P, L, w, s, lv);
+  __syncthreads();
+  if (lv.nlev > 1 && warp == 0) sw_upL_warp<T, NX, DIR>(0, lv, 1);
+  __syncthreads();
+  if (warp < nblk0) sw_down0_warp<T, NX, DIR>(warp, tiles[warp], Kn, Nn, Y, G, P, L, w, s, lv, out, bout);
+}
+
 // The sweep kernels keep up to four 4-warp CTAs per SM; give shared memory the whole L1 array.
 template <typename T, int NX>
 static bk_status sweep_attrs() {
-  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_up0<T, NX, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_up0<T, NX, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_down0<T, NX, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_down0<T, NX, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_up0<T, NX, 0, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_up0<T, NX, 1, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_down0<T, NX, 0, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_down0<T, NX, 1, 4>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  const int sm1 = (int)(SW1_MAXW * sizeof(SweepTiles<T, NX>));
+  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_one<T, NX, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1));
+  BK_TRY_CUDA(cudaFuncSetAttribute(k_sw_one<T, NX, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm1));
   return BK_OK;
 }
 
@@ -650,26 +698,59 @@ static Levels<T> levels_of(const Problem* pr, const OpData& d) {
   return lv;
 }
 
-// Full sweep: out = P^{-1} (Y, forcing G) (DIR 0) or P^{-T} Y with bout = B-tilde^T out (DIR 1).
-// nlev + 1 launches: the level-0 up pass, one scan per upper level, the down pass.
-template <typename T, int NX, int DIR>
-static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* out, T* bout, cudaStream_t st) {
-  // segment length and level data follow the problem's working precision
-  BK_ARG(d.dtype == pr->pdtype && d.Kn != nullptr, "sweeps run in the preconditioner's precision only");
-  const T s = (T)pr->s;
-  const T* w = (const T*)d.w;
-  const Levels<T> lv = levels_of<T>(pr, d);
-  const int g0 = (((pr->lvn[0] + 31) >> 5) + 3) / 4;
-  k_sw_up0<T, NX, DIR><<<g0, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv);
+// Sweep launch form: 0 automatic, 1 one CTA (small grids only), 2 one warp per CTA, 3 four
+// warps per CTA (BK_SWEEP_FORM overrides the automatic choice, for timing).
+static int sweep_form() {
+  static const int f = [] {
+    const char* e = getenv("BK_SWEEP_FORM");
+    const int v = e ? atoi(e) : 0;
+    return v >= 1 && v <= 3 ? v : 0;
+  }();
+  return f;
+}
+
+template <typename T, int NX, int DIR, int W>
+static bk_status run_sweep_multi(Problem* pr, OpData& d, const T* Y, const T* G, T* out, T* bout, const T* w, T s,
+                                 const Levels<T>& lv, cudaStream_t st) {
+  const int g0 = (((pr->lvn[0] + 31) >> 5) + W - 1) / W;
+  k_sw_up0<T, NX, DIR, W><<<g0, 32 * W, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv);
   BK_CHECK_LAUNCH();
   for (int l = 1; l < pr->nlev; ++l) {
-    const int gl = (((pr->lvn[l] + 31) >> 5) + 3) / 4;
-    k_sw_upL<T, NX, DIR><<<gl, 128, 0, st>>>(lv, l);
+    const int gl = (((pr->lvn[l] + 31) >> 5) + W - 1) / W;
+    k_sw_upL<T, NX, DIR, W><<<gl, 32 * W, 0, st>>>(lv, l);
     BK_CHECK_LAUNCH();
   }
-  k_sw_down0<T, NX, DIR><<<g0, 128, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv, out, bout);
+  k_sw_down0<T, NX, DIR, W><<<g0, 32 * W, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv, out,
+                                                    bout);
   BK_CHECK_LAUNCH();
   return BK_OK;
+}
+
+// Full sweep: out = P^{-1} (Y, forcing G) (DIR 0) or P^{-T} Y with bout = B-tilde^T out (DIR 1).
+// Grids with at most two scan levels and 16 level-0 blocks: one launch (k_sw_one). Otherwise
+// nlev + 1 launches (the level-0 up pass, one scan per upper level, the down pass), one warp per
+// CTA while level 0 has fewer than four blocks per SM, else four. Measured orbit solves (GB300,
+// host-form GMRES, ms, one CTA / 1-warp / 4-warp CTAs): FP64 2^8 7.35 / 7.61 / 7.56, FP32 2^16
+// (1-warp range) - / 7.29 / 8.18, FP64 2^16 - / 12.84 / 13.04.
+template <typename T, int NX, int DIR>
+static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* out, T* bout, cudaStream_t st) {
+  // segment length and level data follow the problem's preconditioner precision
+  BK_ARG(d.dtype == pr->pdtype && d.Kn != nullptr, "sweeps run in the preconditioner's precision only");
+  const T* w = (const T*)d.w;
+  const T s = (T)pr->s;
+  const Levels<T> lv = levels_of<T>(pr, d);
+  const int nblk0 = (pr->lvn[0] + 31) >> 5;
+  int form = sweep_form();
+  if (form == 1 && !(pr->nlev <= 2 && nblk0 <= SW1_MAXW)) form = 0;
+  if (form == 0) form = nblk0 < 4 * 152 ? 2 : 3;
+  if (form == 1) {
+    k_sw_one<T, NX, DIR><<<1, 32 * nblk0, nblk0 * sizeof(SweepTiles<T, NX>), st>>>(
+        (const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv, out, bout);
+    BK_CHECK_LAUNCH();
+    return BK_OK;
+  }
+  if (form == 2) return run_sweep_multi<T, NX, DIR, 1>(pr, d, Y, G, out, bout, w, s, lv, st);
+  return run_sweep_multi<T, NX, DIR, 4>(pr, d, Y, G, out, bout, w, s, lv, st);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1216,12 +1297,9 @@ static void free_opdata(OpData& d) {
 }
 
 // --- linearisation ---------------------------------------------------------------------------
-template <typename T, int KIND>
-static bk_status lin_factors(Problem* pr, OpData& d, const double* z, cudaStream_t st) {
-  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
-  k_lin_nodes<T, KIND, NX, NU><<<nblk(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->d64.plan->w64, pr->s, (T*)d.Kn, (T*)d.Nn, (T*)d.xu,
-                                                             pr->dyn_param());
-  BK_CHECK_LAUNCH();
+// Segment maps and scan levels from the node factors N_k (level data of the sweeps).
+template <typename T, int NX>
+static bk_status lin_levels(Problem* pr, OpData& d, cudaStream_t st) {
   k_lin_seg<T, NX><<<(pr->nseg + 127) / 128, 128, 0, st>>>((const T*)d.Nn, pr->L, pr->nseg, (T*)d.lvm[0]);
   BK_CHECK_LAUNCH();
   for (int l = 0; l < pr->nlev; ++l) {
@@ -1230,6 +1308,15 @@ static bk_status lin_factors(Problem* pr, OpData& d, const double* z, cudaStream
     BK_CHECK_LAUNCH();
   }
   return BK_OK;
+}
+
+template <typename T, int KIND>
+static bk_status lin_factors(Problem* pr, OpData& d, const double* z, cudaStream_t st) {
+  constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  k_lin_nodes<T, KIND, NX, NU><<<nblk(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->d64.plan->w64, pr->s, (T*)d.Kn, (T*)d.Nn, (T*)d.xu,
+                                                             pr->dyn_param());
+  BK_CHECK_LAUNCH();
+  return lin_levels<T, NX>(pr, d, st);
 }
 
 template <typename T>
@@ -1592,6 +1679,7 @@ bk_status problem_wnorm(Problem* pr, const double* F, double* wnorm, cudaStream_
 // --- creation ---------------------------------------------------------------------------------
 static void problem_free(Problem* pr) {
   if (!pr) return;
+  gmres_graphs_free(pr);
   free_opdata(pr->d64);
   free_opdata(pr->d32);
   dfree(pr->F);
@@ -1607,6 +1695,7 @@ static void problem_free(Problem* pr) {
 static bk_status problem_set_params(Problem* pr, const double* params, int nparams, double t0, double tf) {
   BK_ARG(tf > t0 && isfinite(t0) && isfinite(tf), "tf must be > t0 and finite");
   BK_ARG(nparams >= 0 && nparams <= 4 && (nparams == 0 || params), "bad params");
+  gmres_graphs_free(pr);   // the graphs bake in s and the kind's parameters
   if (pr->kind == BK_ORBIT || pr->kind == BK_ORBIT_MT) {
     BK_ARG(nparams >= 2, "the orbit kinds need params {a, r_f}");
     BK_ARG(params[1] > 0 && isfinite(params[1]), "r_f must be > 0");

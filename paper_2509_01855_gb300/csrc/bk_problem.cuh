@@ -219,6 +219,7 @@ struct Problem {
   double* red_host = nullptr;  // pinned host mirror of reduction results
   size_t bytes = 0;            // device bytes this problem (and its plans) allocated
   double* sred = nullptr;      // reduction scratch of the free-time terms (FP64, 2048)
+  void* gcache = nullptr;      // captured GMRES cycle graphs (bk_krylov.cu), keyed by their pointers
   int64_t kkt_len() const { return (2 * n_x + n_u) * P + 32; }
   // tail slot of s in a KKT vector (after nu) for a free final time
   int64_t s_idx() const { return (2 * n_x + n_u) * P + n_e; }
@@ -252,5 +253,8 @@ bk_status problem_residual(Problem* pr, const double* z, double* F, double* wnor
                            double* Mu = nullptr, bool mu_given = false);
 // Weighted norm of a residual vector (FP64), synchronous.
 bk_status problem_wnorm(Problem* pr, const double* F, double* wnorm, cudaStream_t st);
+// Drop the problem's captured GMRES cycle graphs (at destruction, and when a parameter that the
+// graphs bake in changes).
+void gmres_graphs_free(Problem* pr);
 
 }  // namespace bk
