@@ -59,8 +59,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", type=int, default=1, help="1 (default): add the apply sweep N=2^10..2^24")
     ap.add_argument("--profile", action="store_true",
-                    help="apply workloads: after timing, run one more product (L2 flushed first) between "
-                         "cudaProfilerStart and cudaProfilerStop, for ncu --profile-from-start off")
+                    help="apply and newton workloads: after timing, run one more product or solve (L2 "
+                         "flushed first) between cudaProfilerStart and cudaProfilerStop, for ncu "
+                         "--profile-from-start off")
     return ap.parse_args()
 
 
@@ -216,6 +217,14 @@ def run_newton(args, rank, world, dist):
     launches = lib.bk_launch_count() - launches0
     ms = sum(times) / len(times)
     ms_max = max_over_ranks(ms, dist)
+    if args.profile:
+        # one more solve (L2 flushed first) between cudaProfilerStart and cudaProfilerStop
+        flush.zero_()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
 
     # end to end through the public API: pinned host initial guess in, solution out
     zh = z0.cpu().pin_memory()

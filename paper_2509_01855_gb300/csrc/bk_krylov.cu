@@ -145,8 +145,21 @@ __device__ __forceinline__ void multidot_body(const T* __restrict__ V, int64_t l
     }
     __syncthreads();
   }
-  if (last_block(cnt))
-    for (int i = 0; i < nv; ++i) block_sum_column(partial, gridDim.x, nv, i, out + i);
+  if (last_block(cnt)) {
+    if (nv == 1) {
+      block_sum_column(partial, gridDim.x, nv, 0, out);
+    } else {
+      // one warp per column (fixed lane striding and shuffle tree: the order does not depend on
+      // scheduling); the columns' sums run side by side instead of one after another
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+      for (int i = warp; i < nv; i += nw) {
+        double a = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) a += __ldcg(partial + (int64_t)b * nv + i);
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) out[i] = a;
+      }
+    }
+  }
 }
 
 template <typename T>
