@@ -123,9 +123,13 @@ __device__ void node_factors(const Tc* x, const Tc* u, Tc h, Tc* K, Tc* Nm, Tc p
     }
 }
 
+// Per node the sweeps need K = (I - h J)^{-1} and N = 2 h J K. Since K (I - h J) = I, h J K = K - I,
+// so both follow from the deviation D = h J K: K = I + D, N = 2 D. Only D is stored (formed as
+// h J K, not as K - I, which would cancel when h J is small), which halves the sweeps' node
+// factor traffic and, with K v = v + D v and N v = 2 D v, their FP64 products.
 template <typename T, int KIND, int NX, int NU>
 __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, const double* __restrict__ w,
-                            double s, T* __restrict__ Kn, T* __restrict__ Nn, T* __restrict__ xu, double pa) {
+                            double s, T* __restrict__ Dn, T* __restrict__ xu, double pa) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
     T x[NXM], u[NUM];
 #pragma unroll
@@ -135,10 +139,7 @@ __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, 
     T K[NX * NX], Nm[NX * NX];
     node_factors<T, KIND, NX>(x, u, (T)(0.5 * s * w[k]), K, Nm, (T)pa);
 #pragma unroll
-    for (int c = 0; c < NX * NX; ++c) {
-      Kn[il_index<Seg<T>::v>(k, c, NX * NX)] = (T)K[c];
-      Nn[il_index<Seg<T>::v>(k, c, NX * NX)] = (T)Nm[c];
-    }
+    for (int c = 0; c < NX * NX; ++c) Dn[il_index<Seg<T>::v>(k, c, NX * NX)] = T(0.5) * Nm[c];   // D = N / 2 (exact)
 #pragma unroll
     for (int m = 0; m < NX + NU; ++m) xu[m * P + k] = (T)z[m * P + k];
   }
@@ -170,9 +171,10 @@ __device__ __forceinline__ void dev_mul(const Tm* A, const Tm* B, Tm* C) {
     }
 }
 
-// Level-0 maps: prod over the segment's nodes of (I + N_k) as a deviation, one thread per segment.
+// Level-0 maps: prod over the segment's nodes of (I + N_k) = (I + 2 D_k) as a deviation, one
+// thread per segment.
 template <typename T, int NX>
-__global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, T* __restrict__ A0) {
+__global__ void k_lin_seg(const T* __restrict__ Dn, int64_t L, int nseg, T* __restrict__ A0) {
   const int seg = blockIdx.x * blockDim.x + threadIdx.x;
   if (seg >= nseg) return;
   T A[NX * NX], M[NX * NX], R[NX * NX];
@@ -183,7 +185,7 @@ __global__ void k_lin_seg(const T* __restrict__ Nn, int64_t L, int nseg, T* __re
     const int64_t k = (int64_t)seg * SEG + i;
     if (k >= L) break;
 #pragma unroll
-    for (int c = 0; c < NX * NX; ++c) M[c] = Nn[il_index<Seg<T>::v>(k, c, NX * NX)];
+    for (int c = 0; c < NX * NX; ++c) M[c] = T(2) * Dn[il_index<Seg<T>::v>(k, c, NX * NX)];
     dev_mul<NX, T>(M, A, R);
 #pragma unroll
     for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
@@ -297,46 +299,42 @@ template <typename T> struct Levels {
   int nlev;
 };
 
+// One node of a sweep with the node's deviation D (K = I + D, N = 2 D):
+//   DIR 0: v = y + h g + st,  out = K v = v + D v,  st <- st + 2 h g + N v = st + 2 h g + 2 D v
+//   DIR 1: y = K^T yin + N^T st = yin + D^T (yin + 2 st),  out = y and y / 2 + st,  st <- st + y
 template <typename T, int NX, int DIR>
-__device__ __forceinline__ void node_step(const T* __restrict__ Kn, const T* __restrict__ Nn, int64_t k,
-                                          const T* yin, const T* gin, T h, T* st, T* out, bool want_out) {
-  T Km[NX * NX], Nm[NX * NX];
+__device__ __forceinline__ void node_step(const T* __restrict__ Dn, int64_t k, const T* yin, const T* gin, T h,
+                                          T* st, T* out, bool want_out) {
+  T Dm[NX * NX];
 #pragma unroll
-  for (int c = 0; c < NX * NX; ++c) {
-    if (DIR == 1 || want_out) Km[c] = Kn[il_index<Seg<T>::v>(k, c, NX * NX)];
-    Nm[c] = Nn[il_index<Seg<T>::v>(k, c, NX * NX)];
-  }
+  for (int c = 0; c < NX * NX; ++c) Dm[c] = Dn[il_index<Seg<T>::v>(k, c, NX * NX)];
   if (DIR == 0) {
-    T v[NX];
+    T v[NX], dv[NX];
 #pragma unroll
     for (int m = 0; m < NX; ++m) v[m] = yin[m] + h * gin[m] + st[m];
-    if (want_out) {
-#pragma unroll
-      for (int r = 0; r < NX; ++r) {
-        T a = T(0);
-#pragma unroll
-        for (int c = 0; c < NX; ++c) a += Km[r * NX + c] * v[c];
-        out[r] = a;
-      }
-    }
-    T ns[NX];
-#pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      T a = st[r] + T(2) * h * gin[r];
-#pragma unroll
-      for (int c = 0; c < NX; ++c) a += Nm[r * NX + c] * v[c];
-      ns[r] = a;
-    }
-#pragma unroll
-    for (int r = 0; r < NX; ++r) st[r] = ns[r];
-  } else {
-    T y[NX];
 #pragma unroll
     for (int r = 0; r < NX; ++r) {
       T a = T(0);
 #pragma unroll
-      for (int c = 0; c < NX; ++c) a += Km[c * NX + r] * yin[c] + Nm[c * NX + r] * st[c];
-      y[r] = a;
+      for (int c = 0; c < NX; ++c) a += Dm[r * NX + c] * v[c];
+      dv[r] = a;
+    }
+    if (want_out) {
+#pragma unroll
+      for (int r = 0; r < NX; ++r) out[r] = v[r] + dv[r];
+    }
+#pragma unroll
+    for (int r = 0; r < NX; ++r) st[r] = (st[r] + T(2) * h * gin[r]) + T(2) * dv[r];
+  } else {
+    T q[NX], y[NX];
+#pragma unroll
+    for (int c = 0; c < NX; ++c) q[c] = yin[c] + T(2) * st[c];
+#pragma unroll
+    for (int r = 0; r < NX; ++r) {
+      T a = T(0);
+#pragma unroll
+      for (int c = 0; c < NX; ++c) a += Dm[c * NX + r] * q[c];
+      y[r] = yin[r] + a;
     }
     if (want_out) {
 #pragma unroll
@@ -438,8 +436,8 @@ __device__ __forceinline__ bool nonzero(float x) { return (__float_as_int(x) << 
 // offsets are all zero has zero scan values: the terminal Schur columns' right-hand sides are
 // unit vectors at the last node, so their up passes do almost no FP64 work.
 template <typename T, int NX, int DIR>
-__device__ __forceinline__ void sw_up0_warp(int g, SweepTiles<T, NX>& tl, const T* __restrict__ Kn,
-                                            const T* __restrict__ Nn, const T* __restrict__ Y,
+__device__ __forceinline__ void sw_up0_warp(int g, SweepTiles<T, NX>& tl, const T* __restrict__ Dn,
+                                            const T* __restrict__ Y,
                                             const T* __restrict__ G, int64_t P, int64_t L, const T* __restrict__ w,
                                             T s, const Levels<T>& lv) {
   constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS, SEG = Seg<T>::v;
@@ -479,7 +477,7 @@ __device__ __forceinline__ void sw_up0_warp(int g, SweepTiles<T, NX>& tl, const 
           yin[m] = tl.a[(m * 32 + lane) * TS + nd];
           gin[m] = G ? tl.b[(m * 32 + lane) * TS + nd] : T(0);
         }
-        node_step<T, NX, DIR>(Kn, Nn, k, yin, gin, T(0.5) * s * tl.w[lane * TS + nd], st, dummy, false);
+        node_step<T, NX, DIR>(Dn, k, yin, gin, T(0.5) * s * tl.w[lane * TS + nd], st, dummy, false);
       }
     }
   }
@@ -528,8 +526,8 @@ __device__ __forceinline__ void sw_upL_warp(int b, const Levels<T>& lv, int l) {
 // Down (one warp per block of 32 segments): incoming state of the lane's segment, composed from
 // the top level down, then the segment's nodes with outputs (staged like the inputs).
 template <typename T, int NX, int DIR>
-__device__ __forceinline__ void sw_down0_warp(int g, SweepTiles<T, NX>& tl, const T* __restrict__ Kn,
-                                              const T* __restrict__ Nn, const T* __restrict__ Y,
+__device__ __forceinline__ void sw_down0_warp(int g, SweepTiles<T, NX>& tl, const T* __restrict__ Dn,
+                                              const T* __restrict__ Y,
                                               const T* __restrict__ G, int64_t P, int64_t L,
                                               const T* __restrict__ w, T s, const Levels<T>& lv,
                                               T* __restrict__ out, T* __restrict__ bout) {
@@ -587,7 +585,7 @@ __device__ __forceinline__ void sw_down0_warp(int g, SweepTiles<T, NX>& tl, cons
           gin[m] = (DIR == 0 && G) ? tl.b[(m * 32 + lane) * TS + nd] : T(0);
         }
         const T wk = tl.w[lane * TS + nd];
-        node_step<T, NX, DIR>(Kn, Nn, k, yin, gin, T(0.5) * s * wk, st, o, true);
+        node_step<T, NX, DIR>(Dn, k, yin, gin, T(0.5) * s * wk, st, o, true);
         // outputs replace the inputs just read (same lane, same node)
 #pragma unroll
         for (int m = 0; m < NX; ++m) tl.a[(m * 32 + lane) * TS + nd] = o[m];
@@ -616,13 +614,12 @@ __device__ __forceinline__ void sw_down0_warp(int g, SweepTiles<T, NX>& tl, cons
 // warp's segments are sequential chains whose FP64 arithmetic would otherwise share one SM's
 // FP64 pipe).
 template <typename T, int NX, int DIR, int W>
-__global__ void __launch_bounds__(32 * W) k_sw_up0(const T* __restrict__ Kn, const T* __restrict__ Nn,
-                                                   const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
+__global__ void __launch_bounds__(32 * W) k_sw_up0(const T* __restrict__ Dn, const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
                                                    int64_t L, const T* __restrict__ w, T s, Levels<T> lv) {
   __shared__ SweepTiles<T, NX> tiles[W];
   const int g = blockIdx.x * W + (threadIdx.x >> 5);
   if (g >= ((lv.n[0] + 31) >> 5)) return;  // whole warps
-  sw_up0_warp<T, NX, DIR>(g, tiles[threadIdx.x >> 5], Kn, Nn, Y, G, P, L, w, s, lv);
+  sw_up0_warp<T, NX, DIR>(g, tiles[threadIdx.x >> 5], Dn, Y, G, P, L, w, s, lv);
 }
 
 template <typename T, int NX, int DIR, int W>
@@ -633,14 +630,13 @@ __global__ void __launch_bounds__(32 * W) k_sw_upL(Levels<T> lv, int l) {
 }
 
 template <typename T, int NX, int DIR, int W>
-__global__ void __launch_bounds__(32 * W) k_sw_down0(const T* __restrict__ Kn, const T* __restrict__ Nn,
-                                                     const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
+__global__ void __launch_bounds__(32 * W) k_sw_down0(const T* __restrict__ Dn, const T* __restrict__ Y, const T* __restrict__ G, int64_t P,
                                                      int64_t L, const T* __restrict__ w, T s, Levels<T> lv,
                                                      T* __restrict__ out, T* __restrict__ bout) {
   __shared__ SweepTiles<T, NX> tiles[W];
   const int g = blockIdx.x * W + (threadIdx.x >> 5);
   if (g >= ((lv.n[0] + 31) >> 5)) return;  // whole warps
-  sw_down0_warp<T, NX, DIR>(g, tiles[threadIdx.x >> 5], Kn, Nn, Y, G, P, L, w, s, lv, out, bout);
+  sw_down0_warp<T, NX, DIR>(g, tiles[threadIdx.x >> 5], Dn, Y, G, P, L, w, s, lv, out, bout);
 }
 
 // The whole sweep in one CTA for small grids (at most two scan levels and SW1_MAXW blocks of 32
@@ -649,19 +645,18 @@ __global__ void __launch_bounds__(32 * W) k_sw_down0(const T* __restrict__ Kn, c
 // mix's small problems run many sweeps per Newton step).
 constexpr int SW1_MAXW = 16;
 template <typename T, int NX, int DIR>
-__global__ void __launch_bounds__(32 * SW1_MAXW) k_sw_one(const T* __restrict__ Kn, const T* __restrict__ Nn,
-                                                          const T* __restrict__ Y, const T* __restrict__ G,
+__global__ void __launch_bounds__(32 * SW1_MAXW) k_sw_one(const T* __restrict__ Dn, const T* __restrict__ Y, const T* __restrict__ G,
                                                           int64_t P, int64_t L, const T* __restrict__ w, T s,
                                                           Levels<T> lv, T* __restrict__ out, T* __restrict__ bout) {
   extern __shared__ __align__(16) unsigned char sw1_smem[];
   SweepTiles<T, NX>* tiles = reinterpret_cast<SweepTiles<T, NX>*>(sw1_smem);
   const int warp = threadIdx.x >> 5;
   const int nblk0 = (lv.n[0] + 31) >> 5;
-  if (warp < nblk0) sw_up0_warp<T, NX, DIR>(warp, tiles[warp], Kn, Nn, Y, G, P, L, w, s, lv);
+  if (warp < nblk0) sw_up0_warp<T, NX, DIR>(warp, tiles[warp], Dn, Y, G, P, L, w, s, lv);
   __syncthreads();
   if (lv.nlev > 1 && warp == 0) sw_upL_warp<T, NX, DIR>(0, lv, 1);
   __syncthreads();
-  if (warp < nblk0) sw_down0_warp<T, NX, DIR>(warp, tiles[warp], Kn, Nn, Y, G, P, L, w, s, lv, out, bout);
+  if (warp < nblk0) sw_down0_warp<T, NX, DIR>(warp, tiles[warp], Dn, Y, G, P, L, w, s, lv, out, bout);
 }
 
 // The sweep kernels keep up to four 4-warp CTAs per SM; give shared memory the whole L1 array.
@@ -713,15 +708,14 @@ template <typename T, int NX, int DIR, int W>
 static bk_status run_sweep_multi(Problem* pr, OpData& d, const T* Y, const T* G, T* out, T* bout, const T* w, T s,
                                  const Levels<T>& lv, cudaStream_t st) {
   const int g0 = (((pr->lvn[0] + 31) >> 5) + W - 1) / W;
-  k_sw_up0<T, NX, DIR, W><<<g0, 32 * W, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv);
+  k_sw_up0<T, NX, DIR, W><<<g0, 32 * W, 0, st>>>((const T*)d.Dn, Y, G, pr->P, pr->L, w, s, lv);
   BK_CHECK_LAUNCH();
   for (int l = 1; l < pr->nlev; ++l) {
     const int gl = (((pr->lvn[l] + 31) >> 5) + W - 1) / W;
     k_sw_upL<T, NX, DIR, W><<<gl, 32 * W, 0, st>>>(lv, l);
     BK_CHECK_LAUNCH();
   }
-  k_sw_down0<T, NX, DIR, W><<<g0, 32 * W, 0, st>>>((const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv, out,
-                                                    bout);
+  k_sw_down0<T, NX, DIR, W><<<g0, 32 * W, 0, st>>>((const T*)d.Dn, Y, G, pr->P, pr->L, w, s, lv, out, bout);
   BK_CHECK_LAUNCH();
   return BK_OK;
 }
@@ -735,7 +729,7 @@ static bk_status run_sweep_multi(Problem* pr, OpData& d, const T* Y, const T* G,
 template <typename T, int NX, int DIR>
 static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* out, T* bout, cudaStream_t st) {
   // segment length and level data follow the problem's preconditioner precision
-  BK_ARG(d.dtype == pr->pdtype && d.Kn != nullptr, "sweeps run in the preconditioner's precision only");
+  BK_ARG(d.dtype == pr->pdtype && d.Dn != nullptr, "sweeps run in the preconditioner's precision only");
   const T* w = (const T*)d.w;
   const T s = (T)pr->s;
   const Levels<T> lv = levels_of<T>(pr, d);
@@ -745,7 +739,7 @@ static bk_status run_sweep(Problem* pr, OpData& d, const T* Y, const T* G, T* ou
   if (form == 0) form = nblk0 < 4 * 152 ? 2 : 3;
   if (form == 1) {
     k_sw_one<T, NX, DIR><<<1, 32 * nblk0, nblk0 * sizeof(SweepTiles<T, NX>), st>>>(
-        (const T*)d.Kn, (const T*)d.Nn, Y, G, pr->P, pr->L, w, s, lv, out, bout);
+        (const T*)d.Dn, Y, G, pr->P, pr->L, w, s, lv, out, bout);
     BK_CHECK_LAUNCH();
     return BK_OK;
   }
@@ -1258,8 +1252,7 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
   const bool pre = dtype == pr->pdtype;
   const int64_t il = (int64_t)round_up(pr->nseg, 32) * seg_nodes(pr->pdtype) * nx * nx;
   if (pre) {
-    BK_TRY(dmalloc(&d.Kn, es * il));
-    BK_TRY(dmalloc(&d.Nn, es * il));
+    BK_TRY(dmalloc(&d.Dn, es * il));   // the node deviations D (K = I + D, N = 2 D)
   }
   for (int l = 0; pre && l < pr->nlev; ++l) {
     const size_t npad = (size_t)round_up(pr->lvn[l], 32);
@@ -1286,7 +1279,7 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
 
 static void free_opdata(OpData& d) {
   if (d.plan) plan_destroy(d.plan);
-  void* ps[] = {d.xu, d.mu, d.Kn, d.Nn, d.Zc, d.HWc, d.Qc, d.Sinv, d.t1, d.t2, d.t3, d.brd, d.brq, d.bgam};
+  void* ps[] = {d.xu, d.mu, d.Dn, d.Zc, d.HWc, d.Qc, d.Sinv, d.t1, d.t2, d.t3, d.brd, d.brq, d.bgam};
   for (void* p : ps) dfree(p);
   for (int l = 0; l < MAXLEV; ++l) {
     dfree(d.lvm[l]);
@@ -1300,7 +1293,7 @@ static void free_opdata(OpData& d) {
 // Segment maps and scan levels from the node factors N_k (level data of the sweeps).
 template <typename T, int NX>
 static bk_status lin_levels(Problem* pr, OpData& d, cudaStream_t st) {
-  k_lin_seg<T, NX><<<(pr->nseg + 127) / 128, 128, 0, st>>>((const T*)d.Nn, pr->L, pr->nseg, (T*)d.lvm[0]);
+  k_lin_seg<T, NX><<<(pr->nseg + 127) / 128, 128, 0, st>>>((const T*)d.Dn, pr->L, pr->nseg, (T*)d.lvm[0]);
   BK_CHECK_LAUNCH();
   for (int l = 0; l < pr->nlev; ++l) {
     k_lin_level<T, NX><<<(pr->lvn[l] + 31) / 32, 32, 0, st>>>((T*)d.lvm[l], pr->lvn[l],
@@ -1313,7 +1306,7 @@ static bk_status lin_levels(Problem* pr, OpData& d, cudaStream_t st) {
 template <typename T, int KIND>
 static bk_status lin_factors(Problem* pr, OpData& d, const double* z, cudaStream_t st) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
-  k_lin_nodes<T, KIND, NX, NU><<<nblk(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->d64.plan->w64, pr->s, (T*)d.Kn, (T*)d.Nn, (T*)d.xu,
+  k_lin_nodes<T, KIND, NX, NU><<<nblk(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->d64.plan->w64, pr->s, (T*)d.Dn, (T*)d.xu,
                                                              pr->dyn_param());
   BK_CHECK_LAUNCH();
   return lin_levels<T, NX>(pr, d, st);

@@ -173,8 +173,8 @@ struct OpData {
   void* xu = nullptr;          // linearisation point X, U ((n_x + n_u) * P)
   void* mu = nullptr;          // mu = s (B^a)^T lambda (n_x * P)
   void* w = nullptr;           // Clenshaw-Curtis weights (L), working type
-  void* Kn = nullptr;          // per-node K_k = (I - h_k J_k)^{-1}, interleaved (n_x^2 per node)
-  void* Nn = nullptr;          // per-node N_k = 2 h_k J_k K_k, interleaved
+  void* Dn = nullptr;          // per-node D_k = h_k J_k K_k, K_k = (I - h_k J_k)^{-1} = I + D_k and
+                               // N_k = 2 h_k J_k K_k = 2 D_k; interleaved (n_x^2 per node)
   void* lvm[MAXLEV] = {};      // per level: NSLOT matrix slots (n_x^2 per item each), working type
   void* lvo[MAXLEV] = {};      // per level >= 1: item offsets from zero (n_x per item), per sweep
   void* lve[MAXLEV] = {};      // per level: inclusive in-block scan values (n_x per item), per sweep
