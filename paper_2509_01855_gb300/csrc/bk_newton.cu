@@ -23,6 +23,7 @@
 // recomputed for every trial (s B^aT lambda is bilinear in s and lambda, so the update above
 // does not apply).
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <utility>
@@ -118,6 +119,16 @@ size_t newton_workspace(const Problem* pr, int restart) {
   return b + 1024;
 }
 
+// Floor of the FP32 inner tolerance (BK_F32_FORCING_FLOOR overrides it, for tuning).
+static double f32_forcing_floor() {
+  static const double f = [] {
+    const char* e = getenv("BK_F32_FORCING_FLOOR");
+    const double v = e ? atof(e) : 0.0;
+    return v >= 1e-8 && v <= 1e-2 ? v : 1e-4;
+  }();
+  return f;
+}
+
 static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk_newton_info* info, void* ws,
                              cudaStream_t st) {
   const int64_t n = pr->kkt_len();
@@ -178,7 +189,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
       ko.rtol = 1e-12;
     } else {
       const double r = phi / info->residual0;
-      const double lo = pr->dtype == BK_F64 ? 1e-12 : 1e-4;
+      const double lo = pr->dtype == BK_F64 ? 1e-12 : f32_forcing_floor();
       ko.rtol = fmin(1e-2, fmax(lo, 0.1 * r * r));
     }
     const int keep = (fast && o.precond_reuse > 0) ? (o.precond_reuse >= 2 ? LIN_KEEP_PRECOND : LIN_KEEP_SCHUR)
