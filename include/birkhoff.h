@@ -357,11 +357,11 @@ bk_status krylov_solve(bk_problem* prob, int op, const void* rhs, void* sol,
  * the host launches each step and reads the stop word after it. Both forms give bitwise the same
  * iterates.
  *   mode 0 (or -1, the default): never;  mode 1: for every problem of fixed final time.
- * Graphs pay when a problem is solved repeatedly with unchanged parameters (the captured kernels
- * take the time scale s by value, so a new t_f means a new capture).
+
  * A problem captures a graph on its first solve for a given workspace and vector layout and keeps
- * up to four; bk_problem_set_params drops them. Process-wide; host only. BK_ERR_ARG for any
- * other mode. */
+ * up to four; the captured kernels read the time scale from the problem's device copy, so
+ * bk_problem_set_params (which must not overlap a solve of the problem) keeps them valid.
+ * Process-wide; host only. BK_ERR_ARG for any other mode. */
 bk_status bk_set_krylov_graphs(int mode);
 
 /* Bound on the host's wait for a graph cycle (seconds; <= 0 restores the default, 60 s). When a

@@ -297,6 +297,7 @@ template <typename T> struct Levels {
   T* e[MAXLEV];        // inclusive in-block scan values
   int n[MAXLEV];       // items per level
   int nlev;
+  const double* sdev;  // the time scale on the device (null: the kernel argument s)
 };
 
 // One node of a sweep with the node's deviation D (K = I + D, N = 2 D):
@@ -445,6 +446,7 @@ __device__ __forceinline__ void sw_up0_warp(int g, SweepTiles<T, NX>& tl, const 
   const int lane = threadIdx.x & 31;
   const int64_t seg0 = (int64_t)g * 32;
   const int64_t seg = seg0 + lane;
+  if (lv.sdev) s = T(*lv.sdev);
   T st[NX];
 #pragma unroll
   for (int m = 0; m < NX; ++m) st[m] = T(0);
@@ -535,6 +537,7 @@ __device__ __forceinline__ void sw_down0_warp(int g, SweepTiles<T, NX>& tl, cons
   constexpr int CH = SweepChunk<T>::CH, TS = SweepChunk<T>::TS, SEG = Seg<T>::v;
   const int nblk0 = (lv.n[0] + 31) >> 5;
   const int lane = threadIdx.x & 31;
+  if (lv.sdev) s = T(*lv.sdev);
   const int64_t seg0 = (int64_t)g * 32;
   const int64_t seg = seg0 + lane;
   const bool live = seg < lv.n[0];
@@ -679,6 +682,10 @@ static bk_status sweep_attrs_nx(int nx) {
   return sweep_attrs<T, 4>();
 }
 
+// The time scale the GMRES-step kernels read: the device copy for a fixed final time, none
+// (the kernel argument) for a free one, whose s changes inside a Newton step.
+static const double* sdev_of(const Problem* pr) { return pr->free_time ? nullptr : pr->s_dev; }
+
 template <typename T>
 static Levels<T> levels_of(const Problem* pr, const OpData& d) {
   Levels<T> lv;
@@ -690,6 +697,7 @@ static Levels<T> levels_of(const Problem* pr, const OpData& d) {
     lv.e[l] = (T*)d.lve[l];
     lv.n[l] = pr->lvn[l];
   }
+  lv.sdev = sdev_of(pr);
   return lv;
 }
 
@@ -779,13 +787,15 @@ __global__ void k_jvp(const T* __restrict__ xu, const T* __restrict__ dX, const 
   }
 }
 
-// out = chi - Bt (state operator), padding zeroed.
+// out = chi - Bt (state operator), padding zeroed. With sdev, Bt holds B^a (J chi) and the time
+// scale is applied here from the device; without, Bt = s B^a (J chi).
 template <typename T, int NX>
 __global__ void k_state_post(const T* __restrict__ chi, const T* __restrict__ Bt, int64_t P, int64_t L,
-                             T* __restrict__ out) {
+                             T* __restrict__ out, const double* __restrict__ sdev) {
+  const T s = sdev ? T(*sdev) : T(1);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < NX * P; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = i % P;
-    out[i] = k < L ? chi[i] - Bt[i] : T(0);
+    out[i] = k < L ? chi[i] - (sdev ? s * Bt[i] : Bt[i]) : T(0);
   }
 }
 
@@ -801,11 +811,14 @@ struct TermSpec {
 // (k_free_finish), i.e. -(B^aT lambda) . (J dz) - (B^a f) . dlambda.
 template <typename T, int KIND>
 __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, const T* __restrict__ w, T s,
-                           const T* __restrict__ in, const T* __restrict__ Bt, const T* __restrict__ Mu, int64_t P,
+                           const T* __restrict__ in, const T* __restrict__ Bt, T* __restrict__ Mu, int64_t P,
                            int64_t L, TermSpec ts, T cost_uu, T* __restrict__ out, T pa, int64_t s_idx,
-                           double* __restrict__ part) {
+                           double* __restrict__ part, const double* __restrict__ sdev) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu, NV = NX + NU;
   __shared__ double red[32];
+  // sdev: Bt and Mu arrive unscaled (B^a, B^aT products) and take the device time scale here;
+  // the scaled Mu is written back (the caller's record of s B^aT dlambda)
+  if (sdev) s = T(*sdev);
   const T dss = part ? in[s_idx] / s : T(0);
   double sacc = 0.0;
   const T* dX = in;
@@ -824,7 +837,16 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
     }
     T x[NXM], u[NUM], m_[NXM], Jx[NXM * NXM], Ju[NXM * NUM], H[(NXM + NUM) * (NXM + NUM)], dz[NXM + NUM], mp[NXM];
 #pragma unroll
-    for (int m = 0; m < NX; ++m) { x[m] = xu[m * P + k]; m_[m] = mu[m * P + k]; dz[m] = dX[m * P + k]; mp[m] = Mu[m * P + k]; }
+    for (int m = 0; m < NX; ++m) {
+      x[m] = xu[m * P + k];
+      m_[m] = mu[m * P + k];
+      dz[m] = dX[m * P + k];
+      mp[m] = Mu[m * P + k];
+      if (sdev) {
+        mp[m] = s * mp[m];
+        Mu[m * P + k] = mp[m];
+      }
+    }
 #pragma unroll
     for (int q = 0; q < NU; ++q) { u[q] = xu[(NX + q) * P + k]; dz[NX + q] = dU[q * P + k]; }
     Dyn<KIND>::template jac<T>(x, u, Jx, Ju, pa);
@@ -865,7 +887,7 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
       else oU[(a - NX) * P + k] = acc;
     }
 #pragma unroll
-    for (int m = 0; m < NX; ++m) oL[m * P + k] = dz[m] - Bt[m * P + k];
+    for (int m = 0; m < NX; ++m) oL[m * P + k] = dz[m] - (sdev ? s * Bt[m * P + k] : Bt[m * P + k]);
     if (k == L - 1) {
       for (int r = 0; r < 32; ++r) oNu[r] = r < ts.n_e ? dX[ts.idx[r] * P + k] : T(0);
     }
@@ -986,8 +1008,9 @@ __global__ void k_border_fix(const T* __restrict__ q, const double* __restrict__
 template <typename T, int KIND>
 __global__ void k_pre_u(const T* __restrict__ xu, const T* __restrict__ w, T s, T cost_uu, const T* __restrict__ ru,
                         const T* __restrict__ b, int64_t P, int64_t L, T* __restrict__ yu, T* __restrict__ g,
-                        T gsign, const T* __restrict__ mu, T pa) {
+                        T gsign, const T* __restrict__ mu, T pa, const double* __restrict__ sdev = nullptr) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
+  if (sdev) s = T(*sdev);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
     if (k >= L) {
 #pragma unroll
@@ -1453,8 +1476,9 @@ static bk_status apply_typed(Problem* pr, OpData& d, int op, const T* in, T* out
     // the product ignores t1's padding (elements L..P-1), so it is never written
     k_jvp<T, KIND><<<nblk(L), 256, 0, st>>>((const T*)d.xu, in, nullptr, P, L, t1, (T)pr->dyn_param(), nullptr, T(0));
     BK_CHECK_LAUNCH();
-    BK_TRY(plan_apply_n(d.plan, t1, t2, NX, false, pr->s, st));
-    k_state_post<T, NX><<<nblk(NX * P), 256, 0, st>>>(in, t2, P, L, out);
+    const double* sd = sdev_of(pr);
+    BK_TRY(plan_apply_n(d.plan, t1, t2, NX, false, sd ? 1.0 : pr->s, st));
+    k_state_post<T, NX><<<nblk(NX * P), 256, 0, st>>>(in, t2, P, L, out, sd);
     BK_CHECK_LAUNCH();
     return BK_OK;
   }
@@ -1463,12 +1487,15 @@ static bk_status apply_typed(Problem* pr, OpData& d, int op, const T* in, T* out
   k_jvp<T, KIND><<<nblk(L), 256, 0, st>>>((const T*)d.xu, in, in + NX * P, P, L, t1, pa,
                                           ft ? in + pr->s_idx() : nullptr, (T)(1.0 / pr->s));
   BK_CHECK_LAUNCH();
-  BK_TRY(plan_apply_n(d.plan, t1, t2, NX, false, pr->s, st));
+  // fixed final time: both products unscaled, k_kkt_post applies s from the device (so that a
+  // captured GMRES step does not hold s); free final time: s (which changes within a step) by value
+  const double* sd = sdev_of(pr);
+  BK_TRY(plan_apply_n(d.plan, t1, t2, NX, false, sd ? 1.0 : pr->s, st));
   T* Mu = mu_out ? mu_out : t3;
-  BK_TRY(plan_apply_n(d.plan, in + (NX + NU) * P, Mu, NX, true, pr->s, st));
+  BK_TRY(plan_apply_n(d.plan, in + (NX + NU) * P, Mu, NX, true, sd ? 1.0 : pr->s, st));
   k_kkt_post<T, KIND><<<ft ? FT_NB : nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.mu, (const T*)d.w, (T)pr->s, in,
                                                             t2, Mu, P, L, term_spec(pr), (T)pr->cost_uu(), out, pa,
-                                                            pr->s_idx(), ft ? pr->sred : nullptr);
+                                                            pr->s_idx(), ft ? pr->sred : nullptr, sd);
   BK_CHECK_LAUNCH();
   if (ft) {
     k_free_finish<T><<<1, 256, 0, st>>>(pr->sred, FT_NB, -1.0 / pr->s, out + pr->s_idx());
@@ -1520,7 +1547,7 @@ static bk_status precond_typed(Problem* pr, OpData& d, int op, const T* in, T* o
   T* g = (T*)d.t2;
   BK_TRY((run_sweep<T, NX, 1>(pr, d, rx, nullptr, yl, b, st)));
   k_pre_u<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.w, (T)pr->s, (T)1, ru, b, P, L, yu, g, T(1),
-                                            (const T*)d.mu, (T)pr->dyn_param());
+                                            (const T*)d.mu, (T)pr->dyn_param(), sdev_of(pr));
   BK_CHECK_LAUNCH();
   BK_TRY((run_sweep<T, NX, 0>(pr, d, rl, g, yx, nullptr, st)));
   if (pr->n_e > 0) {
@@ -1678,6 +1705,7 @@ static void problem_free(Problem* pr) {
   dfree(pr->F);
   dfree(pr->red);
   dfree(pr->sred);
+  dfree(pr->s_dev);
   dfree(pr->pcin);
   dfree(pr->pcout);
   if (pr->red_host) cudaFreeHost(pr->red_host);
@@ -1688,7 +1716,8 @@ static void problem_free(Problem* pr) {
 static bk_status problem_set_params(Problem* pr, const double* params, int nparams, double t0, double tf) {
   BK_ARG(tf > t0 && isfinite(t0) && isfinite(tf), "tf must be > t0 and finite");
   BK_ARG(nparams >= 0 && nparams <= 4 && (nparams == 0 || params), "bad params");
-  gmres_graphs_free(pr);   // the graphs bake in s and the kind's parameters
+  // captured GMRES graphs read s from the device copy (fixed final time) and no other
+  // parameter; a free final time keeps no graphs
   if (pr->kind == BK_ORBIT || pr->kind == BK_ORBIT_MT) {
     BK_ARG(nparams >= 2, "the orbit kinds need params {a, r_f}");
     BK_ARG(params[1] > 0 && isfinite(params[1]), "r_f must be > 0");
@@ -1704,6 +1733,7 @@ static bk_status problem_set_params(Problem* pr, const double* params, int npara
   pr->tf = tf;
   pr->s = 0.5 * (tf - t0);
   pr->linearized = false;
+  if (pr->s_dev) BK_TRY_CUDA(cudaMemcpy(pr->s_dev, &pr->s, sizeof(double), cudaMemcpyHostToDevice));
   return BK_OK;
 }
 
@@ -1787,6 +1817,11 @@ static bk_status problem_create(Problem** out, int kind, const double* params, i
   if (s == BK_OK && pr->pdtype != dtype) s = dmalloc(&pr->pcout, sizeof(float) * pr->kkt_len());
   if (s == BK_OK) s = dmalloc((void**)&pr->F, sizeof(double) * pr->kkt_len());
   if (s == BK_OK) s = dmalloc((void**)&pr->red, sizeof(double) * 2048);
+  if (s == BK_OK) s = dmalloc((void**)&pr->s_dev, 256);
+  if (s == BK_OK && cudaMemcpy(pr->s_dev, &pr->s, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    set_error("time scale copy failed");
+    s = BK_ERR_CUDA;
+  }
   if (s == BK_OK && pr->free_time) s = dmalloc((void**)&pr->sred, sizeof(double) * 2048);
   if (s == BK_OK && cudaMallocHost((void**)&pr->red_host, sizeof(double) * 512) != cudaSuccess) {
     set_error("cudaMallocHost failed");

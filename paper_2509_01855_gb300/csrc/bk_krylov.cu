@@ -544,7 +544,10 @@ static bk_status arnoldi_step(const GmCtx<T>& c, int jh, bool graph, cudaGraphCo
 
 // --- graph cycles ------------------------------------------------------------------------------
 // A captured cycle bakes in every pointer and host scalar its kernels take, so the key holds
-// them all: workspace, operator data, aux record, flags, lengths and the time scale s.
+// them all: workspace, operator data, aux record, flags and lengths. The time scale s is not
+// among them: for a fixed final time the step's kernels read it from the problem's device copy,
+// which bk_problem_set_params updates (a free final time, whose s changes inside a Newton step,
+// never runs graphs).
 struct GmGraph {
   const void* ws;
   const void* d;
@@ -585,9 +588,8 @@ static std::atomic<long long> g_wait_ns{-1};
 static constexpr double WAIT_DEFAULT_S = 60.0;
 
 // Off by default. Measured on GB300 (orbit solves, N = 2^8..2^16): graph cycles make a solve
-// 7-12% faster when a problem is solved again with the same parameters, but in the serving mix,
-// where every request changes t_f (and with it the time scale s that the captured kernels take by
-// value), the capture per request cut the closed-loop rate from ~555 to ~440 solves/s.
+// 5-13% faster, but in the serving mix (16 host threads, one problem per slot) they lowered the
+// closed-loop rate from ~570 to ~510 solves/s.
 static bool graphs_wanted(const Problem* pr) {
   if (pr->free_time) return false;   // s changes every Newton step
   return g_graph_mode.load() == 1;
@@ -623,7 +625,7 @@ static GmGraph* graph_get(const GmCtx<T>& c, const void* ws, int m) {
   key.precond = c.precond;
   key.m = m;
   key.n = c.n;
-  key.s = pr->s;
+  key.s = 0.0;
   for (GmGraph& e : gc->v)
     if (e.ws == key.ws && e.d == key.d && e.auxT == key.auxT && e.auxTd == key.auxTd && e.auxld == key.auxld &&
         e.auxn == key.auxn && e.op == key.op && e.weighted == key.weighted && e.precond == key.precond &&

@@ -220,6 +220,8 @@ struct Problem {
   size_t bytes = 0;            // device bytes this problem (and its plans) allocated
   double* sred = nullptr;      // reduction scratch of the free-time terms (FP64, 2048)
   void* gcache = nullptr;      // captured GMRES cycle graphs (bk_krylov.cu), keyed by their pointers
+  double* s_dev = nullptr;     // device copy of s (fixed final time): the GMRES-step kernels read s
+                               // from here, so captured graphs stay valid when the parameters change
   int64_t kkt_len() const { return (2 * n_x + n_u) * P + 32; }
   // tail slot of s in a KKT vector (after nu) for a free final time
   int64_t s_idx() const { return (2 * n_x + n_u) * P + n_e; }
