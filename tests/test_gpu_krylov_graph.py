@@ -142,3 +142,49 @@ def test_settings_reject_bad_values():
         api.set_krylov_wait_limit(float("nan"))
     with pytest.raises(_lib.BirkhoffError):
         api.set_krylov_wait_limit(1e7)
+
+
+def test_graph_cycles_from_concurrent_threads():
+    """Four host threads, each with its own problem (its own t_f), stream and workspace, solve
+    with graph cycles at the same time (captures are serialised inside the library, the cycles
+    run concurrently); every solution equals the host-form solution of the same problem."""
+    import threading
+    from paper_2509_01855_gb300 import _lib, api
+    N = 512
+    M = MatFreeKKT(op.Problem(op.ORBIT, 0.0, TF, (0.01, RF)), N)
+    X, U = synth.orbit_guess(M.t, RF, TF)
+    vec = M.pack(X, U, np.zeros((4, M.L)), np.zeros(3))
+    tfs = [18.0, 20.0, 22.0, 24.0]
+
+    def solve_all(mode):
+        api.set_krylov_graphs(mode)
+        out, errs = [None] * len(tfs), []
+
+        def work(i):
+            try:
+                st = torch.cuda.Stream()
+                with torch.cuda.stream(st):
+                    prob = api.Problem(_lib.BK_ORBIT, N, torch.float64, 0.0, tfs[i], (0.01, RF))
+                    ws = api.newton_workspace(prob)
+                    for rep in range(2):
+                        z = from_packed(prob, vec)
+                        info = api.newton_solve(prob, z, tol=1e-10, workspace=ws, stream=st)
+                    st.synchronize()
+                    out[i] = (z.clone(), info)
+            except Exception as e:  # reported below
+                errs.append(e)
+
+        threads = [threading.Thread(target=work, args=(i,)) for i in range(len(tfs))]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        api.set_krylov_graphs(-1)
+        assert not errs, errs
+        return out
+
+    ref = solve_all(0)
+    got = solve_all(1)
+    for (zr, ir), (zg, ig) in zip(ref, got):
+        assert ir["converged"] and ir == ig
+        assert torch.equal(zr, zg)
