@@ -451,6 +451,12 @@ __device__ void dct1_block(const T* __restrict__ X, int kind, T* __restrict__ Y,
 // Thread cap of the transform kernels: each thread stages 16 complex values, so FP64 kernels
 // are limited to 256 threads (up to 255 registers each) and FP32 ones to 512.
 template <typename T> struct MaxThr { static constexpr int v = sizeof(T) == 8 ? 256 : 512; };
+// Resident CTAs per SM the pass kernels are compiled for (register cap 64K / (threads x this)).
+// Double-float: 3 (80 registers instead of 128, spills unchanged at ~50 bytes, 24 instead of 16
+// warps per SM for the 128-thread tiles; the latency-bound passes gained: 4-component products
+// 2^20 0.553 -> 0.519 ms, 2^22 2.48 -> 2.11 ms; 4 CTAs (64 registers) lost: 0.576, 2.33 ms).
+// binary32 at 3 would cap the 512-thread tiles at 42 registers and spill ~400 bytes.
+template <typename T> struct MinB { static constexpr int v = std::is_same<T, dfl>::value ? 3 : 2; };
 // Element loads each thread keeps in flight in the pass kernels' load phases.
 // FP32: 8 (latency-bound passes; 16 spilled under the 64-register cap of two 512-thread CTAs
 // per SM), FP64: 4 (FP64-pipe-bound, register-heavy).
@@ -619,7 +625,7 @@ __device__ __forceinline__ void passA_body(
 
 // Pass A of one transform (unsplit, or one half of a split DCT-I).
 template <typename T, int K, int MODE = PM_FULL>
-__global__ void __launch_bounds__(MaxThr<T>::v, 2)
+__global__ void __launch_bounds__(MaxThr<T>::v, MinB<T>::v)
     k_passA(BK_PASSA_PARAMS(), T invN, StencilTab<T> tb, const typename V2<T>::t* __restrict__ tpost = nullptr,
             const typename V2<T>::t* __restrict__ eo = nullptr) {
   passA_body<T, K, MODE>(blockIdx.x, gridDim.x, BK_PASSA_ARGS(), invN, tb, BK_PASSA_TAIL(), tpost, eo);
@@ -628,7 +634,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v, 2)
 // Pass A of both halves of a split DCT-I in one launch: CTAs [0, gE) run the even half (pair
 // sums), the rest the odd half (DCT-III); one launch fills the GPU better than two smaller ones.
 template <typename T, int K>
-__global__ void __launch_bounds__(MaxThr<T>::v, 2)
+__global__ void __launch_bounds__(MaxThr<T>::v, MinB<T>::v)
     k_passA_split(int gE, BK_PASSA_PARAMS(E), BK_PASSA_PARAMS(O), T invN, StencilTab<T> tb,
                   const typename V2<T>::t* __restrict__ tpost, const typename V2<T>::t* __restrict__ eo) {
   if ((int)blockIdx.x < gE)
@@ -640,7 +646,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v, 2)
 // Pass A of the three parts of a two-level split DCT-I in one launch: CTAs [0, g1) the DCT-I of
 // aa, [g1, g1 + g2) the DCT-III of a's pair differences, the rest the DCT-III of x's.
 template <typename T, int K>
-__global__ void __launch_bounds__(MaxThr<T>::v, 2)
+__global__ void __launch_bounds__(MaxThr<T>::v, MinB<T>::v)
     k_passA_split3(int g1, int g2, BK_PASSA_PARAMS(E), BK_PASSA_PARAMS(D), BK_PASSA_PARAMS(O), T invN,
                    StencilTab<T> tb, const typename V2<T>::t* __restrict__ tpost,
                    const typename V2<T>::t* __restrict__ eo) {
@@ -967,7 +973,7 @@ __device__ __forceinline__ void passB_body(
       const typename V2<T>::t* __restrict__ stw##S
 
 template <typename T, int E, int MODE = PB_PAIRS>
-__global__ void __launch_bounds__(MaxThr<T>::v, 2)
+__global__ void __launch_bounds__(MaxThr<T>::v, MinB<T>::v)
     k_passB(const typename V2<T>::t* __restrict__ Ain, typename OutS<T, E>::t* __restrict__ dst, int64_t dst_stride,
             int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial, int N, int N1,
             int N2, int log2N2, int P, const typename V2<T>::t* __restrict__ stw,
@@ -979,7 +985,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v, 2)
 // Pass B of both halves of a split DCT-I in one launch: CTAs [0, gE) the even half's row pairs
 // and real split (outputs at even indices), the rest the odd half's rows (odd indices).
 template <typename T, int E>
-__global__ void __launch_bounds__(MaxThr<T>::v, 2)
+__global__ void __launch_bounds__(MaxThr<T>::v, MinB<T>::v)
     k_passB_split(int gE, BK_PASSB_PARAMS(E), BK_PASSB_PARAMS(O), typename OutS<T, E>::t* __restrict__ dst, int64_t dst_stride,
                   int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial,
                   const typename V2<T>::t* __restrict__ tpost, T s, T invN, int Npar) {
@@ -994,7 +1000,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v, 2)
 // Pass B of a two-level split: the DCT-I of aa (outputs 4k), the DCT-III of a's pair
 // differences (outputs 4m + 2) and the DCT-III of x's (outputs 2m + 1).
 template <typename T, int E>
-__global__ void __launch_bounds__(MaxThr<T>::v, 2)
+__global__ void __launch_bounds__(MaxThr<T>::v, MinB<T>::v)
     k_passB_split3(int h1, int h2, BK_PASSB_PARAMS(E), BK_PASSB_PARAMS(D), BK_PASSB_PARAMS(O), typename OutS<T, E>::t* __restrict__ dst,
                    int64_t dst_stride, int64_t pitch_zero_to, const T* __restrict__ partial, int n_partial,
                    const typename V2<T>::t* __restrict__ tpost, T s, T invN, int Npar) {
@@ -1087,7 +1093,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v) k_small_batch(const __grid_const
 }
 
 template <typename T, int K>
-__global__ void __launch_bounds__(MaxThr<T>::v, 2) k_passA_batch(const __grid_constant__ Batch<PassAJob<T>> b) {
+__global__ void __launch_bounds__(MaxThr<T>::v, MinB<T>::v) k_passA_batch(const __grid_constant__ Batch<PassAJob<T>> b) {
   const int q = batch_job(b, blockIdx.x);
   const PassAJob<T>& J = b.j[q];
   const int local = (int)blockIdx.x - b.start[q];
@@ -1098,7 +1104,7 @@ __global__ void __launch_bounds__(MaxThr<T>::v, 2) k_passA_batch(const __grid_co
 }
 
 template <typename T, int E>
-__global__ void __launch_bounds__(MaxThr<T>::v, 2) k_passB_batch(const __grid_constant__ Batch<PassBJob<T>> b) {
+__global__ void __launch_bounds__(MaxThr<T>::v, MinB<T>::v) k_passB_batch(const __grid_constant__ Batch<PassBJob<T>> b) {
   const int q = batch_job(b, blockIdx.x);
   const PassBJob<T>& J = b.j[q];
   const int local = (int)blockIdx.x - b.start[q];
