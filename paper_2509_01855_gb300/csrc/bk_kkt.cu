@@ -880,8 +880,11 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
         for (int m = 0; m < NX; ++m) acc -= Ju[m * NU + (a - NX)] * (mp[m] + dss * m_[m]);
       }
       if (a < NX && k == L - 1) {
-        for (int r = 0; r < ts.n_e; ++r)
-          if (ts.idx[r] == a) acc += dNu[r];
+        // compile-time indices into the parameter struct (a run-time index would copy it to
+        // local memory in every thread)
+#pragma unroll
+        for (int r = 0; r < NEM; ++r)
+          if (r < ts.n_e && ts.idx[r] == a) acc += dNu[r];
       }
       if (a < NX) oX[a * P + k] = acc;
       else oU[(a - NX) * P + k] = acc;
@@ -889,7 +892,9 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
 #pragma unroll
     for (int m = 0; m < NX; ++m) oL[m * P + k] = dz[m] - (sdev ? s * Bt[m * P + k] : Bt[m * P + k]);
     if (k == L - 1) {
-      for (int r = 0; r < 32; ++r) oNu[r] = r < ts.n_e ? dX[ts.idx[r] * P + k] : T(0);
+#pragma unroll
+      for (int r = 0; r < NEM; ++r) oNu[r] = r < ts.n_e ? dX[ts.idx[r] * P + k] : T(0);
+      for (int r = NEM; r < 32; ++r) oNu[r] = T(0);
     }
   }
   if (part) {
@@ -1156,9 +1161,11 @@ __global__ void k_resid_post(const double* __restrict__ z, const double* __restr
       double g = lam[p * P + k];
 #pragma unroll
       for (int m = 0; m < NX; ++m) g -= Jx[m * NX + p] * mp[m];
-      if (k == L - 1)
-        for (int r = 0; r < ts.n_e; ++r)
-          if (ts.idx[r] == p) g += nu[r];
+      if (k == L - 1) {
+#pragma unroll
+        for (int r = 0; r < NEM; ++r)
+          if (r < ts.n_e && ts.idx[r] == p) g += nu[r];
+      }
       F[p * P + k] = g;
       acc += g * g * iw;
     }
@@ -1178,11 +1185,16 @@ __global__ void k_resid_post(const double* __restrict__ z, const double* __restr
       if (partial2) acc2 += lam[m * P + k] * Bf[m * P + k];
     }
     if (k == L - 1) {
-      for (int r = 0; r < 32; ++r) {
-        double e = r < ts.n_e ? x[ts.idx[r]] - ts.val[r] : 0.0;
+#pragma unroll
+      for (int r = 0; r < NEM; ++r) {
+        double xr = 0.0;   // x[ts.idx[r]] by selects: x stays in registers
+#pragma unroll
+        for (int m = 0; m < NX; ++m) xr = ts.idx[r] == m ? x[m] : xr;
+        const double e = r < ts.n_e ? xr - ts.val[r] : 0.0;
         F[(NV + NX) * P + r] = e;
         acc += e * e;
       }
+      for (int r = NEM; r < 32; ++r) F[(NV + NX) * P + r] = 0.0;
     }
   }
   double tot = block_sum<double>(acc, red);
