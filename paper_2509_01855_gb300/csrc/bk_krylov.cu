@@ -44,6 +44,54 @@ static constexpr int MAXM = 100;
 // FP32 elements per thread summed in FP32 before each FP64 accumulation.
 constexpr int RUN32 = 16;
 
+// 16-byte vector of T (float4 / double2) and its element count: the dot and update passes move
+// their operands 16 bytes per load when every vector is 16-byte aligned (the basis is; a caller's
+// right-hand side or solution may not be, and then takes the element loop).
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { typedef float4 t; static constexpr int n = 4; };
+template <> struct Vec16<double> { typedef double2 t; static constexpr int n = 2; };
+__device__ __forceinline__ float vdot(float4 a, float4 b, float c) {
+  return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, c))));
+}
+__device__ __forceinline__ double vdot(double2 a, double2 b, double c) { return fma(a.y, b.y, fma(a.x, b.x, c)); }
+
+template <typename T, int CNT>
+__device__ __forceinline__ void dot_group_vec(const T* __restrict__ V, int64_t ld, const T* __restrict__ w, int64_t lo,
+                                              int64_t hi, double* acc) {
+  typedef typename Vec16<T>::t VT;
+  constexpr int VW = Vec16<T>::n;
+  const int64_t c0 = lo / VW, c1 = hi / VW;   // lo is a multiple of VW
+  const VT* wv = reinterpret_cast<const VT*>(w);
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll 2
+    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+      const VT wk = wv[c];
+#pragma unroll
+      for (int q = 0; q < CNT; ++q) acc[q] = vdot(reinterpret_cast<const VT*>(V + (int64_t)q * ld)[c], wk, acc[q]);
+    }
+  } else {
+    int64_t c = c0 + threadIdx.x;
+    while (c < c1) {
+      float a[CNT];
+#pragma unroll
+      for (int q = 0; q < CNT; ++q) a[q] = 0.f;
+#pragma unroll 2
+      for (int it = 0; it < RUN32 / VW && c < c1; ++it, c += blockDim.x) {
+        const VT wk = wv[c];
+#pragma unroll
+        for (int q = 0; q < CNT; ++q) a[q] = vdot(reinterpret_cast<const VT*>(V + (int64_t)q * ld)[c], wk, a[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < CNT; ++q) acc[q] += (double)a[q];
+    }
+  }
+  // the slice's last elements (fewer than VW) one by one
+  for (int64_t k = c1 * VW + threadIdx.x; k < hi; k += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < CNT; ++q) acc[q] += (double)V[(int64_t)q * ld + k] * (double)w[k];
+  }
+}
+
 template <typename T, int CNT>
 __device__ __forceinline__ void dot_group(const T* __restrict__ V, int64_t ld, const T* __restrict__ w, int64_t lo,
                                           int64_t hi, double* acc) {
@@ -112,24 +160,40 @@ __device__ __forceinline__ void multidot_body(const T* __restrict__ V, int64_t l
                                               int64_t n, double* __restrict__ partial, double* __restrict__ out,
                                               unsigned* __restrict__ cnt) {
   __shared__ double red[8][8];
-  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  const int64_t lo = blockIdx.x * chunk;
+  // slices of a multiple of 4 elements, so that 16-byte loads start on a slice boundary
+  const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x + 3) & ~int64_t(3);
+  const int64_t lo = blockIdx.x * chunk < n ? blockIdx.x * chunk : n;
   const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  const bool vec = ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w) |
+                     (uintptr_t)(ld * (int64_t)sizeof(T))) & 15) == 0;
   for (int i0 = 0; i0 < nv; i0 += 8) {
     const int ng = nv - i0 < 8 ? nv - i0 : 8;
     const T* Vg = V + (int64_t)i0 * ld;
     double acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.0;
-    switch (ng) {
-      case 1: dot_group<T, 1>(Vg, ld, w, lo, hi, acc); break;
-      case 2: dot_group<T, 2>(Vg, ld, w, lo, hi, acc); break;
-      case 3: dot_group<T, 3>(Vg, ld, w, lo, hi, acc); break;
-      case 4: dot_group<T, 4>(Vg, ld, w, lo, hi, acc); break;
-      case 5: dot_group<T, 5>(Vg, ld, w, lo, hi, acc); break;
-      case 6: dot_group<T, 6>(Vg, ld, w, lo, hi, acc); break;
-      case 7: dot_group<T, 7>(Vg, ld, w, lo, hi, acc); break;
-      default: dot_group<T, 8>(Vg, ld, w, lo, hi, acc); break;
+    if (vec) {
+      switch (ng) {
+        case 1: dot_group_vec<T, 1>(Vg, ld, w, lo, hi, acc); break;
+        case 2: dot_group_vec<T, 2>(Vg, ld, w, lo, hi, acc); break;
+        case 3: dot_group_vec<T, 3>(Vg, ld, w, lo, hi, acc); break;
+        case 4: dot_group_vec<T, 4>(Vg, ld, w, lo, hi, acc); break;
+        case 5: dot_group_vec<T, 5>(Vg, ld, w, lo, hi, acc); break;
+        case 6: dot_group_vec<T, 6>(Vg, ld, w, lo, hi, acc); break;
+        case 7: dot_group_vec<T, 7>(Vg, ld, w, lo, hi, acc); break;
+        default: dot_group_vec<T, 8>(Vg, ld, w, lo, hi, acc); break;
+      }
+    } else {
+      switch (ng) {
+        case 1: dot_group<T, 1>(Vg, ld, w, lo, hi, acc); break;
+        case 2: dot_group<T, 2>(Vg, ld, w, lo, hi, acc); break;
+        case 3: dot_group<T, 3>(Vg, ld, w, lo, hi, acc); break;
+        case 4: dot_group<T, 4>(Vg, ld, w, lo, hi, acc); break;
+        case 5: dot_group<T, 5>(Vg, ld, w, lo, hi, acc); break;
+        case 6: dot_group<T, 6>(Vg, ld, w, lo, hi, acc); break;
+        case 7: dot_group<T, 7>(Vg, ld, w, lo, hi, acc); break;
+        default: dot_group<T, 8>(Vg, ld, w, lo, hi, acc); break;
+      }
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -187,7 +251,69 @@ __device__ __forceinline__ void multiaxpy_body(const T* __restrict__ V, int64_t 
   __syncthreads();
   double sq = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  if constexpr (sizeof(T) == 8) {
+  const bool vec = ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(w) |
+                     (uintptr_t)(ld * (int64_t)sizeof(T))) & 15) == 0;
+  if (vec) {
+    // 16-byte loads and stores; each element's update is the same chain as below (the same
+    // values), only the per-thread order of the squares' sum differs
+    typedef typename Vec16<T>::t VT;
+    constexpr int VW = Vec16<T>::n;
+    const int64_t nc = n / VW;
+    VT* wv = reinterpret_cast<VT*>(w);
+    if constexpr (sizeof(T) == 8) {
+      for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += stride) {
+        const VT wk = wv[c];
+        double ax = alpha == 0.0 ? 0.0 : alpha * wk.x, ay = alpha == 0.0 ? 0.0 : alpha * wk.y;
+        for (int i = 0; i < nv; ++i) {
+          const VT v = reinterpret_cast<const VT*>(V + (int64_t)i * ld)[c];
+          ax += cs[i] * v.x;
+          ay += cs[i] * v.y;
+        }
+        VT o;
+        o.x = ax;
+        o.y = ay;
+        wv[c] = o;
+        sq += ax * ax;
+        sq += ay * ay;
+      }
+    } else {
+      const float al = (float)alpha;
+      int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+      while (c < nc) {
+        float s32 = 0.f;
+        for (int it = 0; it < RUN32 / VW && c < nc; ++it, c += stride) {
+          const VT wk = wv[c];
+          float a0 = alpha == 0.0 ? 0.f : al * wk.x, a1 = alpha == 0.0 ? 0.f : al * wk.y;
+          float a2 = alpha == 0.0 ? 0.f : al * wk.z, a3 = alpha == 0.0 ? 0.f : al * wk.w;
+          for (int i = 0; i < nv; ++i) {
+            const VT v = reinterpret_cast<const VT*>(V + (int64_t)i * ld)[c];
+            a0 = fmaf(cs32[i], v.x, a0);
+            a1 = fmaf(cs32[i], v.y, a1);
+            a2 = fmaf(cs32[i], v.z, a2);
+            a3 = fmaf(cs32[i], v.w, a3);
+          }
+          VT o;
+          o.x = a0;
+          o.y = a1;
+          o.z = a2;
+          o.w = a3;
+          wv[c] = o;
+          s32 = fmaf(a0, a0, s32);
+          s32 = fmaf(a1, a1, s32);
+          s32 = fmaf(a2, a2, s32);
+          s32 = fmaf(a3, a3, s32);
+        }
+        sq += (double)s32;
+      }
+    }
+    // the last n mod VW elements one by one
+    for (int64_t k = nc * VW + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride) {
+      T a = alpha == 0.0 ? T(0) : T(alpha) * w[k];
+      for (int i = 0; i < nv; ++i) a += (sizeof(T) == 8 ? T(cs[i]) : T(cs32[i])) * V[(int64_t)i * ld + k];
+      w[k] = a;
+      sq += (double)a * (double)a;
+    }
+  } else if constexpr (sizeof(T) == 8) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += stride) {
       double a = alpha == 0.0 ? 0.0 : alpha * w[k];
       int i = 0;
