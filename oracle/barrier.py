@@ -1,0 +1,171 @@
+"""Control bounds by a logarithmic barrier (oracle). Test infrastructure only.
+
+The general problem (P) of the paper (Eq. probPbold) carries path constraints h(x, u, t) <= 0,
+which the paper states but gives no method for (its solver treats the equality-constrained
+Prob-PNa). This module adds the simplest path constraints, constant bounds on each control,
+
+    l_q <= u_q(t) <= h_q        (one pair per control component; +-inf: no bound),
+
+to the a-form discretisation of DenseKKT by a primal logarithmic barrier on the quadrature of
+the constraint over time (Fiacco and McCormick's barrier method, in the primal form of Nocedal
+and Wright, Numerical Optimization, 2nd ed., Section 19.6):
+
+    J_mu = J - mu * s * sum_i w_i sum_q [ log(u_qi - l_q) + log(h_q - u_qi) ].
+
+The quadrature weight keeps the barrier a discretisation of mu * integral log(...) dt, so the
+barrier problem, like the unbounded one, does not change with N. Its KKT conditions are those of
+DenseKKT with, in the gradient rows of U,
+
+    g_U += -mu s w_i (1 / (u - l) - 1 / (h - u)),
+
+and in the control block of the Hessian the diagonal mu s w_i (1 / (u - l)^2 + 1 / (h - u)^2).
+The outer loop solves the barrier problem by the Newton-Lagrange iteration for a decreasing
+sequence mu_0, mu_0 / 10, ... down to mu_final, each stage to ||F_mu||_W <= max(tol, 10 mu), and
+keeps the controls strictly inside their bounds by the fraction-to-boundary rule: the step length
+starts at min(1, 0.995 * max{alpha : l < u + alpha du < h}). The barrier solution lies O(mu) from
+the bounded optimum; the barrier Hessian of an active bound grows like 1 / mu, so mu_final is a
+compromise between that distance and the conditioning of the last stages (1e-8 by default).
+The bound multipliers are recovered as z_l = mu s w / (u - l), z_h = mu s w / (h - u).
+"""
+import numpy as np
+
+from .kkt import DenseKKT
+
+TAU = 0.995     # fraction-to-boundary
+
+
+class BarrierKKT(DenseKKT):
+    """DenseKKT of a problem with control bounds lo, hi (length n_u, +-inf for none) and the
+    barrier parameter mu (set before each stage)."""
+
+    def __init__(self, prob, N, lo, hi, Ba=None):
+        super().__init__(prob, N, Ba)
+        self.lo = np.asarray(lo, float).reshape(prob.n_u)
+        self.hi = np.asarray(hi, float).reshape(prob.n_u)
+        self.mu = 0.0
+
+    def _bar_terms(self, U, s):
+        """Per control and node: the barrier gradient and Hessian diagonal (zero where unbounded)."""
+        g = np.zeros_like(U)
+        h = np.zeros_like(U)
+        for q in range(self.prob.n_u):
+            if np.isfinite(self.lo[q]):
+                d = U[q] - self.lo[q]
+                g[q] -= 1.0 / d
+                h[q] += 1.0 / (d * d)
+            if np.isfinite(self.hi[q]):
+                d = self.hi[q] - U[q]
+                g[q] += 1.0 / d
+                h[q] += 1.0 / (d * d)
+        c = self.mu * s * self.w[None, :]
+        return c * g, c * h
+
+    def residual(self, vec):
+        F = super().residual(vec)
+        p, L = self.prob, self.L
+        X, U, lam, nu = self.split(vec)
+        g, _ = self._bar_terms(U, self.s_of(vec))
+        F[p.n_x * L:self.nz] += g.ravel()
+        return F
+
+    def matrix(self, vec):
+        K = super().matrix(vec)
+        p, L = self.prob, self.L
+        X, U, lam, nu = self.split(vec)
+        _, h = self._bar_terms(U, self.s_of(vec))
+        i0 = p.n_x * L
+        K[i0:self.nz, i0:self.nz] += np.diag(h.ravel())
+        return K
+
+    def precond_matrix(self, vec):
+        """K-tilde with the barrier's Hessian diagonal added to its control block (which stays
+        diagonal, so the block elimination of the library's preconditioner is unchanged)."""
+        Kt = super().precond_matrix(vec)
+        p, L = self.prob, self.L
+        X, U, lam, nu = self.split(vec)
+        _, h = self._bar_terms(U, self.s_of(vec))
+        i0 = p.n_x * L
+        Kt[i0:self.nz, i0:self.nz] += np.diag(h.ravel())
+        return Kt
+
+    def max_step(self, vec, d):
+        """Fraction-to-boundary: TAU times the largest alpha <= 1 / TAU keeping l < u + alpha du < h."""
+        p, L = self.prob, self.L
+        U = vec[p.n_x * L:self.nz].reshape(p.n_u, L)
+        dU = d[p.n_x * L:self.nz].reshape(p.n_u, L)
+        amax = 1.0 / TAU
+        for q in range(p.n_u):
+            if np.isfinite(self.lo[q]):
+                m = dU[q] < 0
+                if m.any():
+                    amax = min(amax, float(np.min((self.lo[q] - U[q][m]) / dU[q][m])))
+            if np.isfinite(self.hi[q]):
+                m = dU[q] > 0
+                if m.any():
+                    amax = min(amax, float(np.min((self.hi[q] - U[q][m]) / dU[q][m])))
+        return min(1.0, TAU * amax)
+
+    def interior(self, vec, margin=1e-3):
+        """vec with its controls moved at least `margin` (relative to the bound gap, or absolute
+        for one-sided bounds) inside their bounds."""
+        v = np.array(vec, float)
+        p, L = self.prob, self.L
+        U = v[p.n_x * L:self.nz].reshape(p.n_u, L)
+        for q in range(p.n_u):
+            lo, hi = self.lo[q], self.hi[q]
+            gap = hi - lo if np.isfinite(lo) and np.isfinite(hi) else 1.0
+            if np.isfinite(lo):
+                U[q] = np.maximum(U[q], lo + margin * gap)
+            if np.isfinite(hi):
+                U[q] = np.minimum(U[q], hi - margin * gap)
+        return v
+
+    def newton_stage(self, vec, tol, max_iter=50, armijo=1e-4, max_backtrack=40):
+        """Newton-Lagrange on F_mu = 0 with the fraction-to-boundary step cap and backtracking
+        on ||F_mu||_W. Returns (vec, iterations, final norm)."""
+        F = self.residual(vec)
+        nrm = self.weighted_norm(F)
+        it = 0
+        while nrm > tol and it < max_iter:
+            d = np.linalg.solve(self.matrix(vec), -F)
+            alpha = self.max_step(vec, d)
+            accepted = False
+            for _ in range(max_backtrack):
+                trial = vec + alpha * d
+                Ft = self.residual(trial)
+                nt = self.weighted_norm(Ft)
+                if nt <= (1.0 - armijo * alpha) * nrm:
+                    accepted = True
+                    break
+                alpha *= 0.5
+            if not accepted:
+                break
+            vec, F, nrm = trial, Ft, nt
+            it += 1
+        return vec, it, nrm
+
+    def solve(self, vec0, mu0=1e-1, mu_final=1e-8, tol=1e-10, factor=0.1):
+        """The barrier outer loop (module docstring). Returns (vec, info)."""
+        vec = self.interior(vec0)
+        mu = mu0
+        total = 0
+        stages = []
+        while True:
+            self.mu = mu
+            last = mu <= mu_final * (1.0 + 1e-12)
+            vec, it, nrm = self.newton_stage(vec, max(tol, 10.0 * mu))
+            total += it
+            stages.append((mu, it, nrm))
+            if last:
+                break
+            mu = max(mu * factor, mu_final)
+        return vec, dict(iters=total, stages=stages, converged=bool(stages[-1][2] <= max(tol, 10.0 * mu)))
+
+    def bound_multipliers(self, vec):
+        """z_l, z_h = mu s w / (u - l), mu s w / (h - u) (zero where unbounded)."""
+        p, L = self.prob, self.L
+        U = vec[p.n_x * L:self.nz].reshape(p.n_u, L)
+        c = self.mu * self.s_of(vec) * self.w[None, :]
+        zl = np.where(np.isfinite(self.lo)[:, None], c / (U - np.where(np.isfinite(self.lo), self.lo, 0.0)[:, None]), 0.0)
+        zh = np.where(np.isfinite(self.hi)[:, None], c / (np.where(np.isfinite(self.hi), self.hi, 0.0)[:, None] - U), 0.0)
+        return zl, zh

@@ -1,0 +1,124 @@
+"""Pins of the control-bound oracle (oracle/barrier.py) against the mathematics it restates.
+
+- Its KKT matrix is the Jacobian of its residual (central finite differences), barrier terms
+  included, for the double integrator and the orbit problem.
+- With bounds far from the solution the barrier solve reproduces the unbounded optimum
+  (double integrator: x = 3t^2 - 2t^3) to the barrier's O(mu) perturbation.
+- With |u| <= 5 on the double integrator (the unbounded optimum 6 - 12 t reaches 6; 4 would be
+  the feasibility limit, reached only by bang-bang control) the solution is the one
+  Pontryagin's principle gives, computed independently here: u = clip(alpha (1 - 2t), -5, 5)
+  (the costate is linear in t and the problem is antisymmetric about t = 1/2), with alpha fixed by x(1) = 1 through adaptive
+  quadrature and a bracketing root finder.
+- The iterates stay strictly inside the bounds and the recovered bound multipliers are
+  nonnegative and vanish where the bound is inactive.
+"""
+import numpy as np
+import pytest
+from scipy.integrate import quad
+from scipy.optimize import brentq
+
+from oracle import problems as op
+from oracle.barrier import BarrierKKT
+from paper_2509_01855_gb300 import synth
+
+
+def _fd_jacobian(K, vec, h=1e-6):
+    n = len(vec)
+    J = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = h
+        J[:, j] = (K.residual(vec + e) - K.residual(vec - e)) / (2 * h)
+    return J
+
+
+@pytest.mark.parametrize("kind", [op.DBL_INT, op.ORBIT])
+def test_barrier_matrix_is_residual_jacobian(kind):
+    if kind == op.DBL_INT:
+        prob = op.Problem(op.DBL_INT, 0.0, 1.0)
+        lo, hi = [-4.0], [5.0]
+    else:
+        prob = op.Problem(op.ORBIT, 0.0, 20.0, (0.01, 1.5))
+        lo, hi = [-0.05, -np.inf], [0.05, 0.04]
+    N = 12
+    K = BarrierKKT(prob, N, lo, hi)
+    K.mu = 0.3
+    g = synth.rng("barrier-fd", kind)
+    if kind == op.DBL_INT:
+        X, U = synth.double_integrator_guess(K.t)
+        U = U + 0.5 * g.standard_normal(U.shape)
+    else:
+        X, U = synth.orbit_guess(K.t, 1.5, 20.0)
+        U = 0.01 * g.standard_normal(U.shape)
+    X = X + 0.01 * g.standard_normal(X.shape)
+    vec = K.pack(X, U, 0.1 * g.standard_normal((prob.n_x, K.L)), 0.1 * g.standard_normal(prob.n_e))
+    vec = K.interior(vec, margin=0.05)
+    A = K.matrix(vec)
+    J = _fd_jacobian(K, vec)
+    assert np.max(np.abs(A - J)) < 1e-5 * max(1.0, np.max(np.abs(A)))
+    # the barrier contributes: without it the matrices differ
+    K.mu = 0.0
+    assert np.max(np.abs(K.matrix(vec) - A)) > 1e-3
+
+
+def test_inactive_bounds_give_the_unbounded_solution():
+    prob = op.Problem(op.DBL_INT, 0.0, 1.0)
+    K = BarrierKKT(prob, 32, [-100.0], [100.0])
+    X, U = synth.double_integrator_guess(K.t)
+    vec, info = K.solve(K.pack(X, U, np.zeros((2, K.L)), np.zeros(2)), mu_final=1e-10)
+    assert info["converged"], info
+    Xs = K.split(vec)[0]
+    t = K.t
+    assert np.max(np.abs(Xs[0] - (3 * t**2 - 2 * t**3))) < 1e-8
+    assert np.max(np.abs(K.split(vec)[1][0] - (6 - 12 * t))) < 1e-6
+
+
+def _pontryagin_bounded(umax=5.0):
+    """u(t) = clip(alpha (1 - 2t), -umax, umax) with x(1) = int_0^1 (1 - t) u dt = 1."""
+    def u_of(alpha):
+        return lambda t: float(np.clip(alpha * (1 - 2 * t), -umax, umax))
+
+    def x1(alpha):
+        t1, t2 = 0.5 * (1 - umax / alpha), 0.5 * (1 + umax / alpha)
+        return quad(lambda t: (1 - t) * u_of(alpha)(t), 0.0, 1.0, points=[t1, t2], epsabs=1e-14)[0] - 1.0
+    alpha = brentq(x1, umax + 1e-9, 1e3, xtol=1e-14)
+    u = u_of(alpha)
+
+    def x(t):
+        return quad(lambda tau: (t - tau) * u(tau), 0.0, t, epsabs=1e-14, limit=200)[0]
+    return alpha, u, x
+
+
+def test_active_bounds_match_pontryagin():
+    alpha, u, x = _pontryagin_bounded(5.0)
+    assert alpha > 6.0   # steeper than the unbounded optimum 6 - 12 t, clipped at +-5
+    prob = op.Problem(op.DBL_INT, 0.0, 1.0)
+    K = BarrierKKT(prob, 64, [-5.0], [5.0])
+    X, U = synth.double_integrator_guess(K.t)
+    vec, info = K.solve(K.pack(X, U, np.zeros((2, K.L)), np.zeros(2)))
+    assert info["converged"], info
+    Xs, Us = K.split(vec)[:2]
+    t = K.t
+    ue = np.array([u(tt) for tt in t])
+    xe = np.array([x(tt) for tt in t])
+    assert np.all(Us[0] > -5.0) and np.all(Us[0] < 5.0)
+    assert np.max(np.abs(Us[0] - ue)) < 2e-2       # the kinks limit the discrete accuracy
+    assert np.max(np.abs(Xs[0] - xe)) < 2e-4
+    # multipliers: nonnegative, and only where the bound is (nearly) active
+    zl, zh = K.bound_multipliers(vec)
+    assert np.all(zl >= 0) and np.all(zh >= 0)
+    inner = np.abs(ue) < 4.0
+    assert np.max(np.abs(zl[0][inner]) + np.abs(zh[0][inner])) < 1e-6 * np.max(zl[0] + zh[0])
+
+
+def test_max_step_keeps_controls_inside():
+    prob = op.Problem(op.DBL_INT, 0.0, 1.0)
+    K = BarrierKKT(prob, 8, [-1.0], [1.0])
+    X, U = synth.double_integrator_guess(K.t)
+    vec = K.pack(X, U, np.zeros((2, K.L)), np.zeros(2))
+    d = np.zeros_like(vec)
+    d[2 * K.L:3 * K.L] = np.linspace(-3.0, 3.0, K.L)
+    a = K.max_step(vec, d)
+    Un = (vec + a * d)[2 * K.L:3 * K.L]
+    assert 0 < a < 1 and np.all(np.abs(Un) < 1.0)
+    assert abs(np.max(np.abs(Un)) - 0.995) < 1e-12
