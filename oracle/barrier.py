@@ -20,11 +20,13 @@ DenseKKT with, in the gradient rows of U,
 
 and in the control block of the Hessian the diagonal mu s w_i (1 / (u - l)^2 + 1 / (h - u)^2).
 The outer loop solves the barrier problem by the Newton-Lagrange iteration for a decreasing
-sequence mu_0, mu_0 / 10, ... down to mu_final, each stage to ||F_mu||_W <= max(tol, 10 mu), and
-keeps the controls strictly inside their bounds by the fraction-to-boundary rule: the step length
-starts at min(1, 0.995 * max{alpha : l < u + alpha du < h}). The barrier solution lies O(mu) from
-the bounded optimum; the barrier Hessian of an active bound grows like 1 / mu, so mu_final is a
-compromise between that distance and the conditioning of the last stages (1e-8 by default).
+sequence mu_0, mu_0 / 10, ... down to mu_final, the intermediate stages to ||F_mu||_W <=
+max(tol, 10 mu) and the last to tol, and keeps the controls strictly inside their bounds by the
+fraction-to-boundary rule: the step length starts at min(1, 0.995 * max{alpha : l < u + alpha du
+< h}). The barrier solution lies O(mu) from the bounded optimum; the barrier Hessian of an
+active bound grows like 1 / mu, so mu_final is a compromise between that distance and the
+conditioning of the last stage: at 1e-6 (the default) the double integrator's last stage reaches
+1e-10 in 8 Newton steps, at 1e-7 it stalls near 1e-9.
 The bound multipliers are recovered as z_l = mu s w / (u - l), z_h = mu s w / (h - u).
 """
 import numpy as np
@@ -144,7 +146,7 @@ class BarrierKKT(DenseKKT):
             it += 1
         return vec, it, nrm
 
-    def solve(self, vec0, mu0=1e-1, mu_final=1e-8, tol=1e-10, factor=0.1):
+    def solve(self, vec0, mu0=1e-1, mu_final=1e-6, tol=1e-10, factor=0.1):
         """The barrier outer loop (module docstring). Returns (vec, info)."""
         vec = self.interior(vec0)
         mu = mu0
@@ -153,13 +155,13 @@ class BarrierKKT(DenseKKT):
         while True:
             self.mu = mu
             last = mu <= mu_final * (1.0 + 1e-12)
-            vec, it, nrm = self.newton_stage(vec, max(tol, 10.0 * mu))
+            vec, it, nrm = self.newton_stage(vec, tol if last else max(tol, 10.0 * mu))
             total += it
             stages.append((mu, it, nrm))
             if last:
                 break
             mu = max(mu * factor, mu_final)
-        return vec, dict(iters=total, stages=stages, converged=bool(stages[-1][2] <= max(tol, 10.0 * mu)))
+        return vec, dict(iters=total, stages=stages, converged=bool(stages[-1][2] <= tol))
 
     def bound_multipliers(self, vec):
         """z_l, z_h = mu s w / (u - l), mu s w / (h - u) (zero where unbounded)."""

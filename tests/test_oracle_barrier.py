@@ -108,7 +108,7 @@ def test_active_bounds_match_pontryagin():
     zl, zh = K.bound_multipliers(vec)
     assert np.all(zl >= 0) and np.all(zh >= 0)
     inner = np.abs(ue) < 4.0
-    assert np.max(np.abs(zl[0][inner]) + np.abs(zh[0][inner])) < 1e-6 * np.max(zl[0] + zh[0])
+    assert np.max(np.abs(zl[0][inner]) + np.abs(zh[0][inner])) < 1e-4 * np.max(zl[0] + zh[0])   # O(mu)
 
 
 def test_max_step_keeps_controls_inside():
