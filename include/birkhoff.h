@@ -266,6 +266,30 @@ void bk_problem_destroy(bk_problem* prob);
 bk_status bk_problem_set_params(bk_problem* prob, const double* params, int nparams, double t0,
                                 double tf);
 
+/* Control bounds lo[q] <= u_q(t) <= hi[q] (the simplest path constraints h(x, u, t) <= 0 of
+ * problem (P), Eq. probPbold; the paper states them but solves only the equality-constrained
+ * Eq. Prob-PNa). They enter as a logarithmic barrier on the quadrature,
+ *   J_mu = J - mu s sum_i w_i sum_q [log(u_qi - lo_q) + log(hi_q - u_qi)],
+ * whose gradient joins the control rows of the residual and whose Hessian diagonal joins the
+ * control block of the KKT matrix and of the preconditioner (still diagonal, so its block
+ * elimination is unchanged). newton_solve then runs barrier stages (bk_problem_set_barrier).
+ *   lo, hi  host arrays of n entries; -inf / +inf for a missing bound; lo[q] < hi[q]
+ *   n       the problem's control count, or 0 to remove the bounds (lo, hi may be NULL then)
+ * bk_kkt_residual, kkt_apply and precond_apply include the barrier terms at mu_final. Host only;
+ * must not overlap work queued on the problem. BK_ERR_ARG for bad sizes or bounds;
+ * BK_ERR_UNSUPPORTED for BK_BILINEAR (no cost) and BK_ORBIT_MT (free final time). */
+bk_status bk_problem_set_control_bounds(bk_problem* prob, const double* lo, const double* hi,
+                                        int n);
+
+/* Barrier schedule of a bounded problem: newton_solve runs Newton stages with
+ * mu = mu0, mu0 / 10, ... down to mu_final (each to ||F_mu||_W <= max(tol, 10 mu), the last to
+ * tol). Defaults 0.1 and 1e-6: the barrier solution lies O(mu_final) from the bounded optimum,
+ * and the barrier Hessian of an active bound grows like 1 / mu_final, which limits how far the
+ * last stage converges (at 1e-7 the double integrator's last stage stalled near ||F||_W = 1e-9
+ * in the FP64 reference computation). mu0 = mu_final: one stage. Host only; BK_ERR_ARG unless
+ * 0 < mu_final <= mu0 <= 1e6. */
+bk_status bk_problem_set_barrier(bk_problem* prob, double mu0, double mu_final);
+
 /* Device bytes the problem holds (its plans, linearisation data and scratch); workspaces are
  * extra (bk_krylov_workspace_bytes, bk_newton_workspace_bytes). For memory-based admission. */
 size_t bk_problem_device_bytes(const bk_problem* prob);
@@ -427,6 +451,13 @@ size_t bk_newton_workspace_bytes(const bk_problem* prob, int restart);
  * tail slot (it must start > 0; trials with s <= 0 are rejected), the residual carries the time
  * gradient, and the inner tolerance defaults to 1e-12 instead of the forcing term. Start it from
  * bk_min_time_seed.
+ * Control bounds (bk_problem_set_control_bounds): the controls in z_inout are first moved 1e-3
+ * of the bound gap inside the bounds, then each barrier stage runs the steps above, with every
+ * step length starting at the fraction-to-boundary bound min(1, 0.995 max{alpha : lo < u +
+ * alpha du < hi}) so that the iterates stay strictly inside, and halved on backtracking (the
+ * quadratic model is dominated by the barrier's curvature); info counts the steps of all
+ * stages, residual0 is the first stage's and residual the last stage's; max_iter (default 100
+ * with bounds) caps the total.
  * Returns BK_ERR_NOT_CONVERGED / BK_ERR_INFEASIBLE with z_inout holding the last iterate. */
 bk_status newton_solve(bk_problem* prob, double* z_inout, const bk_newton_opts* opts,
                        bk_newton_info* info, void* workspace, void* stream);

@@ -217,6 +217,26 @@ class Problem:
         L.check(L.lib().bk_problem_set_params(self._h, arr, len(params), float(t0), float(tf)))
         self.t0, self.tf, self.params = float(t0), float(tf), tuple(params)
 
+    def set_control_bounds(self, lo=None, hi=None):
+        """Bounds lo[q] <= u_q(t) <= hi[q] on the controls (sequences of length n_u, +-inf or
+        None for no bound; both None clears them). newton_solve then solves the problem with a
+        logarithmic barrier on the bounds (fixed-final-time kinds with a cost only)."""
+        if lo is None and hi is None:
+            L.check(L.lib().bk_problem_set_control_bounds(self._h, None, None, 0))
+            return
+        n = self.n_u
+        lo = [-float("inf")] * n if lo is None else [float(x) for x in lo]
+        hi = [float("inf")] * n if hi is None else [float(x) for x in hi]
+        if len(lo) != n or len(hi) != n:
+            raise ValueError(f"bounds need {n} entries each")
+        L.check(L.lib().bk_problem_set_control_bounds(self._h, (ctypes.c_double * n)(*lo),
+                                                      (ctypes.c_double * n)(*hi), n))
+
+    def set_barrier(self, mu0=0.1, mu_final=1e-6):
+        """Barrier schedule of a bounded solve: stages mu0, mu0/10, ... down to mu_final. The
+        residual and operator calls use mu_final."""
+        L.check(L.lib().bk_problem_set_barrier(self._h, float(mu0), float(mu_final)))
+
     def device_bytes(self):
         return int(L.lib().bk_problem_device_bytes(self._h))
 
@@ -336,7 +356,7 @@ def newton_workspace(prob, restart=30):
     return torch.empty(max(1, (nbytes + 255) // 256 * 32), dtype=torch.float64, device="cuda")
 
 
-def newton_solve(prob, z, tol=1e-10, max_iter=30, krylov_rtol=0.0, restart=30, max_krylov=0,
+def newton_solve(prob, z, tol=1e-10, max_iter=0, krylov_rtol=0.0, restart=30, max_krylov=0,
                  ir_rtol=1e-10, max_refine=0, precond_reuse=0, workspace=None, stream=None,
                  raise_on_fail=True, weighted_inner=False):
     """Newton-Lagrange solve in place on the FP64 KKT vector z; returns the info fields.

@@ -813,7 +813,7 @@ template <typename T, int KIND>
 __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, const T* __restrict__ w, T s,
                            const T* __restrict__ in, const T* __restrict__ Bt, T* __restrict__ Mu, int64_t P,
                            int64_t L, TermSpec ts, T cost_uu, T* __restrict__ out, T pa, int64_t s_idx,
-                           double* __restrict__ part, const double* __restrict__ sdev) {
+                           double* __restrict__ part, const double* __restrict__ sdev, BarSpec bs) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu, NV = NX + NU;
   __shared__ double red[32];
   // sdev: Bt and Mu arrive unscaled (B^a, B^aT products) and take the device time scale here;
@@ -852,6 +852,8 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
     Dyn<KIND>::template jac<T>(x, u, Jx, Ju, pa);
     Dyn<KIND>::template hess<T>(x, u, m_, H, pa);
     const T swk = s * w[k] * cost_uu;
+    T gb[NUM], hb[NUM];   // control bounds: the barrier's Hessian diagonal at the linearisation
+    bar_terms<T, NU>(bs, u, s * w[k], gb, hb);
     if (part) {
       T fx[NXM];
       Dyn<KIND>::template f<T>(x, u, fx, pa);
@@ -870,7 +872,7 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
       T acc = T(0);
 #pragma unroll
       for (int b = 0; b < NV; ++b) acc -= H[a * NV + b] * dz[b];
-      if (a >= NX) acc += swk * dz[a];
+      if (a >= NX) acc += (swk + hb[a - NX]) * dz[a];
       if (a < NX) {
         acc += dL[a * P + k];
 #pragma unroll
@@ -1013,7 +1015,7 @@ __global__ void k_border_fix(const T* __restrict__ q, const double* __restrict__
 template <typename T, int KIND>
 __global__ void k_pre_u(const T* __restrict__ xu, const T* __restrict__ w, T s, T cost_uu, const T* __restrict__ ru,
                         const T* __restrict__ b, int64_t P, int64_t L, T* __restrict__ yu, T* __restrict__ g,
-                        T gsign, const T* __restrict__ mu, T pa, const double* __restrict__ sdev = nullptr) {
+                        T gsign, const T* __restrict__ mu, T pa, const double* __restrict__ sdev, BarSpec bs) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   if (sdev) s = T(*sdev);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
@@ -1033,13 +1035,16 @@ __global__ void k_pre_u(const T* __restrict__ xu, const T* __restrict__ w, T s, 
     T mk[NXM];
 #pragma unroll
     for (int m = 0; m < NX; ++m) mk[m] = Dyn<KIND>::huu_needs_mu ? mu[m * P + k] : T(0);
-    const T inv = T(1) / Dyn<KIND>::template pre_huu<T>(mk, s * w[k] * cost_uu, pa);
+    const T huu = Dyn<KIND>::template pre_huu<T>(mk, s * w[k] * cost_uu, pa);
+    // control bounds: the barrier's Hessian diagonal joins the (diagonal) control block
+    T gb[NUM], hb[NUM];
+    bar_terms<T, NU>(bs, u, s * w[k], gb, hb);
 #pragma unroll
     for (int q = 0; q < NU; ++q) {
       T a = ru ? ru[q * P + k] : T(0);
 #pragma unroll
       for (int m = 0; m < NX; ++m) a += s * Ju[m * NU + q] * b[m * P + k];
-      y[q] = a * inv;
+      y[q] = a * (T(1) / (huu + hb[q]));
       yu[q * P + k] = y[q];
     }
 #pragma unroll
@@ -1134,7 +1139,7 @@ template <int KIND>
 __global__ void k_resid_post(const double* __restrict__ z, const double* __restrict__ w, double s,
                              const double* __restrict__ Bf, const double* __restrict__ Mu, int64_t P, int64_t L,
                              TermSpec ts, X0Spec x0, double cost_uu, double* __restrict__ F,
-                             double* __restrict__ partial, double pa, double* __restrict__ partial2) {
+                             double* __restrict__ partial, double pa, double* __restrict__ partial2, BarSpec bs) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu, NV = NX + NU;
   __shared__ double red[32];
   const double* X = z;
@@ -1169,9 +1174,11 @@ __global__ void k_resid_post(const double* __restrict__ z, const double* __restr
       F[p * P + k] = g;
       acc += g * g * iw;
     }
+    double gb[NUM], hb[NUM];   // control bounds: the barrier's gradient
+    bar_terms<double, NU>(bs, u, s * wk, gb, hb);
 #pragma unroll
     for (int q = 0; q < NU; ++q) {
-      double g = s * wk * cost_uu * u[q];
+      double g = s * wk * cost_uu * u[q] + gb[q];
 #pragma unroll
       for (int m = 0; m < NX; ++m) g -= Ju[m * NU + q] * mp[m];
       F[(NX + q) * P + k] = g;
@@ -1376,7 +1383,7 @@ static bk_status lin_schur_launch(Problem* pr, OpData& d, cudaStream_t st) {
     // yu = s Ju^T b / (s w) = -H~^{-1} W and g = Ju yu = -Ju H~^{-1} W.
     T* HW = HWc + (int64_t)r * NU * P;
     k_pre_u<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.w, s, (T)1, nullptr, bz, P, L, HW, g, T(1),
-                                              (const T*)d.mu, (T)pr->dyn_param());
+                                              (const T*)d.mu, (T)pr->dyn_param(), nullptr, bar_spec(pr));
     BK_CHECK_LAUNCH();
     // Q = P^{-1} Pu HW: forward sweep with Y = 0 and forcing -Ju HW = Ju (-HW) = g
     k_unit<T><<<nblk(NX * P), 256, 0, st>>>(unit, NX * P, -1);
@@ -1507,7 +1514,7 @@ static bk_status apply_typed(Problem* pr, OpData& d, int op, const T* in, T* out
   BK_TRY(plan_apply_n(d.plan, in + (NX + NU) * P, Mu, NX, true, sd ? 1.0 : pr->s, st));
   k_kkt_post<T, KIND><<<ft ? FT_NB : nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.mu, (const T*)d.w, (T)pr->s, in,
                                                             t2, Mu, P, L, term_spec(pr), (T)pr->cost_uu(), out, pa,
-                                                            pr->s_idx(), ft ? pr->sred : nullptr, sd);
+                                                            pr->s_idx(), ft ? pr->sred : nullptr, sd, bar_spec(pr));
   BK_CHECK_LAUNCH();
   if (ft) {
     k_free_finish<T><<<1, 256, 0, st>>>(pr->sred, FT_NB, -1.0 / pr->s, out + pr->s_idx());
@@ -1559,7 +1566,7 @@ static bk_status precond_typed(Problem* pr, OpData& d, int op, const T* in, T* o
   T* g = (T*)d.t2;
   BK_TRY((run_sweep<T, NX, 1>(pr, d, rx, nullptr, yl, b, st)));
   k_pre_u<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.w, (T)pr->s, (T)1, ru, b, P, L, yu, g, T(1),
-                                            (const T*)d.mu, (T)pr->dyn_param(), sdev_of(pr));
+                                            (const T*)d.mu, (T)pr->dyn_param(), sdev_of(pr), bar_spec(pr));
   BK_CHECK_LAUNCH();
   BK_TRY((run_sweep<T, NX, 0>(pr, d, rl, g, yx, nullptr, st)));
   if (pr->n_e > 0) {
@@ -1651,7 +1658,7 @@ static bk_status residual_launch(Problem* pr, const double* z, double* F, bool w
   const int nb = 592;
   k_resid_post<KIND><<<nb, 256, 0, st>>>(z, pr->d64.plan->w64, pr->s, Bf, Mu, P, L, term_spec(pr), x0,
                                          pr->cost_uu(), F, pr->red, pr->dyn_param(),
-                                         pr->free_time ? pr->sred : nullptr);
+                                         pr->free_time ? pr->sred : nullptr, bar_spec(pr));
   BK_CHECK_LAUNCH();
   if (pr->free_time) {
     // the time gradient g_s goes into F whether or not the norm is wanted
@@ -1937,6 +1944,44 @@ bk_status bk_problem_info(const bk_problem* prob, int* n_x, int* n_u, int* n_e, 
 bk_status bk_problem_set_params(bk_problem* prob, const double* params, int nparams, double t0, double tf) {
   BK_ARG(prob != nullptr, "problem is NULL");
   return bk::problem_set_params(reinterpret_cast<bk::Problem*>(prob), params, nparams, t0, tf);
+}
+
+bk_status bk_problem_set_control_bounds(bk_problem* prob, const double* lo, const double* hi, int n) {
+  BK_ARG(prob != nullptr, "problem is NULL");
+  bk::Problem* p = reinterpret_cast<bk::Problem*>(prob);
+  if (n == 0) {
+    p->has_bounds = false;
+    p->bar_mu = 0.0;
+    return BK_OK;
+  }
+  BK_ARG(lo != nullptr && hi != nullptr, "bounds are NULL");
+  BK_ARG(n == p->n_u, "n must be 0 or the problem's control count %d (got %d)", p->n_u, n);
+  if (!p->has_cost || p->free_time) {
+    bk::set_error("control bounds need a fixed-final-time problem with a cost (BK_DBL_INT, BK_ORBIT)");
+    return BK_ERR_UNSUPPORTED;
+  }
+  for (int q = 0; q < n; ++q) {
+    BK_ARG(!isnan(lo[q]) && !isnan(hi[q]) && lo[q] < hi[q] && lo[q] != INFINITY && hi[q] != -INFINITY,
+           "control %d: need lo < hi (got %g, %g)", q, lo[q], hi[q]);
+  }
+  for (int q = 0; q < bk::NUM; ++q) {
+    p->ulo[q] = q < n ? lo[q] : -INFINITY;
+    p->uhi[q] = q < n ? hi[q] : INFINITY;
+  }
+  p->has_bounds = true;
+  p->bar_mu = p->bar_mu_final;
+  return BK_OK;
+}
+
+bk_status bk_problem_set_barrier(bk_problem* prob, double mu0, double mu_final) {
+  BK_ARG(prob != nullptr, "problem is NULL");
+  BK_ARG(isfinite(mu0) && isfinite(mu_final) && mu_final > 0.0 && mu0 >= mu_final && mu0 <= 1e6,
+         "need 0 < mu_final <= mu0 <= 1e6 (got %g, %g)", mu0, mu_final);
+  bk::Problem* p = reinterpret_cast<bk::Problem*>(prob);
+  p->bar_mu0 = mu0;
+  p->bar_mu_final = mu_final;
+  if (p->has_bounds) p->bar_mu = mu_final;
+  return BK_OK;
 }
 
 size_t bk_problem_device_bytes(const bk_problem* prob) {

@@ -718,6 +718,7 @@ static constexpr double WAIT_DEFAULT_S = 60.0;
 // closed-loop rate from ~570 to ~510 solves/s.
 static bool graphs_wanted(const Problem* pr) {
   if (pr->free_time) return false;   // s changes every Newton step
+  if (pr->has_bounds) return false;  // the barrier parameter changes between stages
   return g_graph_mode.load() == 1;
 }
 

@@ -2,10 +2,14 @@
 //
 // Discretisation (Eq. Prob-PNa with V = f(X, U) eliminated and x^a fixed):
 //   c(X, U) = X - x0 (x) 1 - s (B^a (x) I) f(X, U),  e(X) = X[term, N] - target,
-//   J = s sum_i w_i F(x_i, u_i).
+//   J = s sum_i w_i F(x_i, u_i)  (control bounds lo <= u <= hi add the barrier
+//   - mu s sum_i w_i sum_q [log(u_qi - lo_q) + log(hi_q - u_qi)]).
 // KKT vectors (component-major, pitch P per block): [X | U | lambda | nu (padded to 32)]; a free
 // final time (BK_ORBIT_MT) keeps s = (t_f - t_0)/2 in the tail slot after nu.
 #pragma once
+
+#include <math.h>
+#include <string.h>
 
 #include "bk_common.cuh"
 #include "bk_plan.cuh"
@@ -166,6 +170,40 @@ template <> struct Dyn<BK_ORBIT_MT> {
 // ---------------------------------------------------------------------------------------------
 // Problem
 // ---------------------------------------------------------------------------------------------
+// Control bounds and barrier parameter as a kernel argument (static indices only).
+struct BarSpec {
+  double mu;          // 0: no barrier terms
+  double lo[NUM], hi[NUM];
+  int has_lo[NUM], has_hi[NUM];
+};
+
+// Barrier gradient g_q and Hessian diagonal h_q of -mu swk sum_q [log(u_q - lo_q) + log(hi_q - u_q)]
+// at one node (swk = s w_k); zero without bounds.
+template <typename T, int NU>
+__device__ __forceinline__ void bar_terms(const BarSpec& b, const T* u, T swk, T* g, T* h) {
+  const T c = T(b.mu) * swk;
+#pragma unroll
+  for (int q = 0; q < NU; ++q) {
+    T gq = T(0), hq = T(0);
+    if (b.mu > 0.0) {
+      if (b.has_lo[q]) {
+        const T d = u[q] - T(b.lo[q]);
+        const T id = T(1) / d;
+        gq -= id;
+        hq += id * id;
+      }
+      if (b.has_hi[q]) {
+        const T d = T(b.hi[q]) - u[q];
+        const T id = T(1) / d;
+        gq += id;
+        hq += id * id;
+      }
+    }
+    g[q] = c * gq;
+    h[q] = c * hq;
+  }
+}
+
 // Per-precision operator state: a plan and the linearisation data in that precision.
 struct OpData {
   int dtype = BK_F64;
@@ -220,6 +258,12 @@ struct Problem {
   size_t bytes = 0;            // device bytes this problem (and its plans) allocated
   double* sred = nullptr;      // reduction scratch of the free-time terms (FP64, 2048)
   void* gcache = nullptr;      // captured GMRES cycle graphs (bk_krylov.cu), keyed by their pointers
+  // control bounds lo_q <= u_q <= hi_q (+-inf: none) by a logarithmic barrier on the quadrature
+  // (problem (P)'s path constraints in their simplest form); bar_mu is the current barrier
+  // parameter (0 outside newton_solve's barrier stages), mu0 / mu_final its schedule
+  bool has_bounds = false;
+  double ulo[NUM] = {0, 0}, uhi[NUM] = {0, 0};
+  double bar_mu = 0.0, bar_mu0 = 0.1, bar_mu_final = 1e-6;
   double* s_dev = nullptr;     // device copy of s (fixed final time): the GMRES-step kernels read s
                                // from here, so captured graphs stay valid when the parameters change
   int64_t kkt_len() const { return (2 * n_x + n_u) * P + 32; }
@@ -234,6 +278,20 @@ struct Problem {
   OpData& work() { return dtype == BK_F64 ? d64 : d32; }
   OpData& pre() { return pdtype == BK_F64 ? d64 : d32; }
 };
+
+// Control bounds and the current barrier parameter of a problem (mu = 0: no barrier terms).
+inline BarSpec bar_spec(const Problem* pr) {
+  BarSpec b;
+  memset(&b, 0, sizeof(b));
+  b.mu = pr->has_bounds ? pr->bar_mu : 0.0;
+  for (int q = 0; q < NUM; ++q) {
+    b.lo[q] = pr->ulo[q];
+    b.hi[q] = pr->uhi[q];
+    b.has_lo[q] = q < pr->n_u && isfinite(pr->ulo[q]) ? 1 : 0;
+    b.has_hi[q] = q < pr->n_u && isfinite(pr->uhi[q]) ? 1 : 0;
+  }
+  return b;
+}
 
 // mu (nullable): s B^aT lambda at z_lin, already known to the caller (FP64, n_x * P); when
 // null it is computed with one transposed product. `keep` keeps part of the preconditioner of
