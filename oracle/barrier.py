@@ -28,6 +28,20 @@ active bound grows like 1 / mu, so mu_final is a compromise between that distanc
 conditioning of the last stage: at 1e-6 (the default) the double integrator's last stage reaches
 1e-10 in 8 Newton steps, at 1e-7 it stalls near 1e-9.
 The bound multipliers are recovered as z_l = mu s w / (u - l), z_h = mu s w / (h - u).
+
+Primal-dual form (Nocedal and Wright, Section 19.2 and 19.6; the form interior-point codes such
+as IPOPT take). The bound multipliers become unknowns z_l, z_h >= 0 (one per bounded control
+and node, scaled like the gradient rows, i.e. with the quadrature weight in them), and the
+barrier problem's KKT conditions are
+
+    g_U - z_l + z_h = 0,    C_l = (u - l) z_l - mu s w = 0,    C_h = (h - u) z_h - mu s w = 0
+
+beside the unchanged state, costate and terminal rows. At C_l = C_h = 0 they reduce to the
+primal conditions above, so both forms have the same solution; Newton's method on the
+primal-dual system linearises the complementarity products instead of 1 / (u - l), which is
+what lets it take long steps near the bounds. solve_pd runs the same stages as solve with the
+full primal-dual Newton system (solved densely), the fraction-to-boundary rule on u and on
+z_l, z_h, and backtracking on the merit ||F||_W^2 + sum (C_l^2 + C_h^2) / w.
 """
 import numpy as np
 
@@ -171,3 +185,136 @@ class BarrierKKT(DenseKKT):
         zl = np.where(np.isfinite(self.lo)[:, None], c / (U - np.where(np.isfinite(self.lo), self.lo, 0.0)[:, None]), 0.0)
         zh = np.where(np.isfinite(self.hi)[:, None], c / (np.where(np.isfinite(self.hi), self.hi, 0.0)[:, None] - U), 0.0)
         return zl, zh
+
+    # ---- primal-dual form ------------------------------------------------------------------
+    def _bounded(self):
+        return np.isfinite(self.lo), np.isfinite(self.hi)
+
+    def pd_init(self, vec):
+        """Multipliers on the central path of the current mu: z = mu s w / (distance to the bound)."""
+        p, L = self.prob, self.L
+        U = vec[p.n_x * L:self.nz].reshape(p.n_u, L)
+        c = self.mu * self.s_of(vec) * self.w[None, :]
+        ml, mh = self._bounded()
+        zl = np.zeros_like(U)
+        zh = np.zeros_like(U)
+        for q in range(p.n_u):
+            if ml[q]:
+                zl[q] = c[0] / (U[q] - self.lo[q])
+            if mh[q]:
+                zh[q] = c[0] / (self.hi[q] - U[q])
+        return zl, zh
+
+    def pd_residual(self, vec, zl, zh):
+        """(F, C_l, C_h): F the unbarriered KKT residual with -z_l + z_h in the control rows,
+        C_l, C_h the complementarity residuals (zero rows where a control has no such bound)."""
+        F = DenseKKT.residual(self, vec)
+        p, L = self.prob, self.L
+        U = vec[p.n_x * L:self.nz].reshape(p.n_u, L)
+        c = self.mu * self.s_of(vec) * self.w
+        ml, mh = self._bounded()
+        Cl = np.zeros_like(U)
+        Ch = np.zeros_like(U)
+        G = F[p.n_x * L:self.nz].reshape(p.n_u, L)
+        for q in range(p.n_u):
+            if ml[q]:
+                G[q] -= zl[q]
+                Cl[q] = (U[q] - self.lo[q]) * zl[q] - c
+            if mh[q]:
+                G[q] += zh[q]
+                Ch[q] = (self.hi[q] - U[q]) * zh[q] - c
+        return F, Cl, Ch
+
+    def pd_merit(self, F, Cl, Ch):
+        """sqrt(||F||_W^2 + sum (C_l^2 + C_h^2) / w): complementarity weighted like the gradient rows."""
+        return float(np.sqrt(self.weighted_norm(F) ** 2 + ((Cl * Cl + Ch * Ch) / self.w[None, :]).sum()))
+
+    def pd_matrix(self, vec, zl, zh):
+        """Jacobian of [F; C_l; C_h] with respect to [vec; z_l; z_h], the multipliers of every
+        control component included (rows and columns of an absent bound: the identity, which
+        keeps that multiplier at zero)."""
+        p, L = self.prob, self.L
+        n, m = self.n, p.n_u * L
+        U = vec[p.n_x * L:self.nz].reshape(p.n_u, L)
+        ml, mh = self._bounded()
+        A = np.zeros((n + 2 * m, n + 2 * m))
+        A[:n, :n] = DenseKKT.matrix(self, vec)
+        for q in range(p.n_u):
+            rows_u = p.n_x * L + q * L + np.arange(L)      # control rows / columns of u_q
+            il = n + q * L + np.arange(L)                    # z_l,q
+            ih = n + m + q * L + np.arange(L)                # z_h,q
+            if ml[q]:
+                A[rows_u, il] = -1.0
+                A[il, rows_u] = zl[q]
+                A[il, il] = U[q] - self.lo[q]
+            else:
+                A[il, il] = 1.0
+            if mh[q]:
+                A[rows_u, ih] = 1.0
+                A[ih, rows_u] = -zh[q]
+                A[ih, ih] = self.hi[q] - U[q]
+            else:
+                A[ih, ih] = 1.0
+        return A
+
+    def pd_step(self, vec, zl, zh):
+        """Newton step of the primal-dual system: (d, dz_l, dz_h)."""
+        p, L = self.prob, self.L
+        F, Cl, Ch = self.pd_residual(vec, zl, zh)
+        n, m = self.n, p.n_u * L
+        sol = np.linalg.solve(self.pd_matrix(vec, zl, zh), -np.concatenate([F, Cl.ravel(), Ch.ravel()]))
+        return sol[:n], sol[n:n + m].reshape(p.n_u, L), sol[n + m:].reshape(p.n_u, L)
+
+    def pd_max_step(self, vec, d, zl, zh, dzl, dzh):
+        """Fraction-to-boundary for u (max_step) and for z_l, z_h >= 0: TAU times the largest
+        alpha <= 1 / TAU keeping z + alpha dz > 0, the smaller of the two, capped at 1."""
+        a = self.max_step(vec, d)
+        zmax = 1.0 / TAU
+        for z, dz in ((zl, dzl), (zh, dzh)):
+            m = dz < 0
+            if m.any():
+                zmax = min(zmax, float(np.min(-z[m] / dz[m])))
+        return min(a, 1.0, TAU * zmax)
+
+    def pd_newton_stage(self, vec, zl, zh, tol, max_iter=50, armijo=1e-4, max_backtrack=40):
+        """Newton's method on the primal-dual system at the current mu, backtracking (halving)
+        on pd_merit from the fraction-to-boundary step. Returns (vec, zl, zh, iterations, merit)."""
+        F, Cl, Ch = self.pd_residual(vec, zl, zh)
+        nrm = self.pd_merit(F, Cl, Ch)
+        it = 0
+        while nrm > tol and it < max_iter:
+            d, dzl, dzh = self.pd_step(vec, zl, zh)
+            alpha = self.pd_max_step(vec, d, zl, zh, dzl, dzh)
+            accepted = False
+            for _ in range(max_backtrack):
+                trial = (vec + alpha * d, zl + alpha * dzl, zh + alpha * dzh)
+                nt = self.pd_merit(*self.pd_residual(*trial))
+                if nt <= (1.0 - armijo * alpha) * nrm:
+                    accepted = True
+                    break
+                alpha *= 0.5
+            if not accepted:
+                break
+            (vec, zl, zh), nrm = trial, nt
+            it += 1
+        return vec, zl, zh, it, nrm
+
+    def solve_pd(self, vec0, mu0=1e-1, mu_final=1e-6, tol=1e-10, factor=0.1):
+        """The stages of solve on the primal-dual system, from the interior point of solve and
+        multipliers on the first stage's central path. Returns (vec, zl, zh, info)."""
+        vec = self.interior(vec0)
+        mu = mu0
+        self.mu = mu
+        zl, zh = self.pd_init(vec)
+        total = 0
+        stages = []
+        while True:
+            self.mu = mu
+            last = mu <= mu_final * (1.0 + 1e-12)
+            vec, zl, zh, it, nrm = self.pd_newton_stage(vec, zl, zh, tol if last else max(tol, 10.0 * mu))
+            total += it
+            stages.append((mu, it, nrm))
+            if last:
+                break
+            mu = max(mu * factor, mu_final)
+        return vec, zl, zh, dict(iters=total, stages=stages, converged=bool(stages[-1][2] <= tol))

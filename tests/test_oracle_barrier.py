@@ -11,6 +11,10 @@
   quadrature and a bracketing root finder.
 - The iterates stay strictly inside the bounds and the recovered bound multipliers are
   nonnegative and vanish where the bound is inactive.
+- Primal-dual form: its Newton matrix is the Jacobian of its residual (finite differences), the
+  step by eliminating the multipliers (the form the library solves) equals the full solve, its
+  residual on the central path is the primal one, and its solve reaches the primal solve's
+  solution and multipliers in fewer Newton steps.
 """
 import numpy as np
 import pytest
@@ -19,6 +23,7 @@ from scipy.optimize import brentq
 
 from oracle import problems as op
 from oracle.barrier import BarrierKKT
+from oracle.kkt import DenseKKT
 from paper_2509_01855_gb300 import synth
 
 
@@ -122,3 +127,109 @@ def test_max_step_keeps_controls_inside():
     Un = (vec + a * d)[2 * K.L:3 * K.L]
     assert 0 < a < 1 and np.all(np.abs(Un) < 1.0)
     assert abs(np.max(np.abs(Un)) - 0.995) < 1e-12
+
+
+# ---- primal-dual form --------------------------------------------------------------------------
+def _pd_point(kind, N=10):
+    if kind == op.DBL_INT:
+        prob = op.Problem(op.DBL_INT, 0.0, 1.0)
+        lo, hi = [-4.0], [5.0]
+    else:
+        prob = op.Problem(op.ORBIT, 0.0, 20.0, (0.01, 1.5))
+        lo, hi = [-0.05, -np.inf], [0.05, 0.04]
+    K = BarrierKKT(prob, N, lo, hi)
+    K.mu = 0.3
+    g = synth.rng("barrier-pd", kind)
+    if kind == op.DBL_INT:
+        X, U = synth.double_integrator_guess(K.t)
+        U = U + 0.5 * g.standard_normal(U.shape)
+    else:
+        X, U = synth.orbit_guess(K.t, 1.5, 20.0)
+        U = 0.01 * g.standard_normal(U.shape)
+    X = X + 0.01 * g.standard_normal(X.shape)
+    vec = K.pack(X, U, 0.1 * g.standard_normal((prob.n_x, K.L)), 0.1 * g.standard_normal(prob.n_e))
+    vec = K.interior(vec, margin=0.05)
+    zl, zh = K.pd_init(vec)
+    # off the central path
+    zl = zl * np.exp(0.3 * g.standard_normal(zl.shape)) * np.isfinite(K.lo)[:, None]
+    zh = zh * np.exp(0.3 * g.standard_normal(zh.shape)) * np.isfinite(K.hi)[:, None]
+    return K, vec, zl, zh
+
+
+@pytest.mark.parametrize("kind", [op.DBL_INT, op.ORBIT])
+def test_pd_matrix_is_residual_jacobian(kind):
+    K, vec, zl, zh = _pd_point(kind)
+    p, L, n = K.prob, K.L, K.n
+    m = p.n_u * L
+
+    def full(x):
+        F, Cl, Ch = K.pd_residual(x[:n], x[n:n + m].reshape(p.n_u, L), x[n + m:].reshape(p.n_u, L))
+        return np.concatenate([F, Cl.ravel(), Ch.ravel()])
+    x0 = np.concatenate([vec, zl.ravel(), zh.ravel()])
+    h = 1e-6
+    J = np.zeros((n + 2 * m, n + 2 * m))
+    for j in range(n + 2 * m):
+        e = np.zeros(n + 2 * m)
+        e[j] = h
+        J[:, j] = (full(x0 + e) - full(x0 - e)) / (2 * h)
+    A = K.pd_matrix(vec, zl, zh)
+    # rows and columns of absent bounds hold the identity in pd_matrix (the residual ignores them)
+    live = np.ones(n + 2 * m, bool)
+    for q in range(p.n_u):
+        if not np.isfinite(K.lo[q]):
+            live[n + q * L:n + (q + 1) * L] = False
+        if not np.isfinite(K.hi[q]):
+            live[n + m + q * L:n + m + (q + 1) * L] = False
+    Al, Jl = A[np.ix_(live, live)], J[np.ix_(live, live)]
+    assert np.max(np.abs(Al - Jl)) < 1e-5 * max(1.0, np.max(np.abs(Al)))
+    assert np.all(A[~live][:, live] == 0) and np.all(A[live][:, ~live] == 0)
+
+
+@pytest.mark.parametrize("kind", [op.DBL_INT, op.ORBIT])
+def test_pd_step_by_elimination(kind):
+    """The reduced form of the primal-dual step: eliminating dz_l, dz_h leaves the unbarriered KKT
+    matrix with Sigma = z_l / (u - l) + z_h / (h - u) added to its control diagonal and the control
+    rows of the right-hand side corrected by -C_l / (u - l) + C_h / (h - u); then
+    dz_l = (-C_l - z_l du) / (u - l), dz_h = (-C_h + z_h du) / (h - u). It equals the full solve."""
+    K, vec, zl, zh = _pd_point(kind)
+    p, L = K.prob, K.L
+    d, dzl, dzh = K.pd_step(vec, zl, zh)
+    F, Cl, Ch = K.pd_residual(vec, zl, zh)
+    U = K.split(vec)[1]
+    ml, mh = np.isfinite(K.lo), np.isfinite(K.hi)
+    dl = np.where(ml[:, None], U - np.where(ml, K.lo, 0.0)[:, None], 1.0)
+    dh = np.where(mh[:, None], np.where(mh, K.hi, 0.0)[:, None] - U, 1.0)
+    sig = np.where(ml[:, None], zl / dl, 0.0) + np.where(mh[:, None], zh / dh, 0.0)
+    A = DenseKKT.matrix(K, vec)
+    i0 = p.n_x * L
+    A[i0:K.nz, i0:K.nz] += np.diag(sig.ravel())
+    rhs = -F
+    rhs[i0:K.nz] += (np.where(ml[:, None], -Cl / dl, 0.0) + np.where(mh[:, None], Ch / dh, 0.0)).ravel()
+    dr = np.linalg.solve(A, rhs)
+    dU = dr[i0:K.nz].reshape(p.n_u, L)
+    assert np.max(np.abs(dr - d)) < 1e-9 * np.max(np.abs(d))
+    assert np.max(np.abs(np.where(ml[:, None], (-Cl - zl * dU) / dl, 0.0) - dzl)) < 1e-9 * max(1.0, np.abs(dzl).max())
+    assert np.max(np.abs(np.where(mh[:, None], (-Ch + zh * dU) / dh, 0.0) - dzh)) < 1e-9 * max(1.0, np.abs(dzh).max())
+
+
+def test_pd_and_primal_forms_share_the_solution():
+    """At a point on the central path (z = mu s w / distance) the primal-dual residual is the
+    primal residual; solve_pd and solve reach the same barrier solution, solve_pd in fewer steps,
+    and solve_pd's multipliers are the ones recovered from the primal solution."""
+    K, vec, _, _ = _pd_point(op.DBL_INT, N=16)
+    zl, zh = K.pd_init(vec)
+    F, Cl, Ch = K.pd_residual(vec, zl, zh)
+    assert np.max(np.abs(Cl)) < 1e-15 and np.max(np.abs(Ch)) < 1e-15
+    assert np.max(np.abs(F - K.residual(vec))) < 1e-12 * np.max(np.abs(F))
+    prob = op.Problem(op.DBL_INT, 0.0, 1.0)
+    K = BarrierKKT(prob, 64, [-5.0], [5.0])
+    X, U = synth.double_integrator_guess(K.t)
+    v0 = K.pack(X, U, np.zeros((2, K.L)), np.zeros(2))
+    vp, ip = K.solve(v0)
+    vd, zl, zh, idd = K.solve_pd(v0)
+    assert ip["converged"] and idd["converged"], (ip, idd)
+    assert np.max(np.abs(vd - vp)) < 1e-8
+    assert idd["iters"] < ip["iters"]
+    zl_p, zh_p = K.bound_multipliers(vp)
+    assert np.max(np.abs(zl - zl_p)) < 1e-6 * np.max(zl_p) and np.max(np.abs(zh - zh_p)) < 1e-6 * np.max(zh_p)
+    assert np.all(zl > 0) and np.all(zh > 0)
