@@ -7,11 +7,15 @@ per-node preconditioner factors, terminal Schur data), preconditioned GMRES on t
 (KKT products = B and B^T on every state component, preconditioner sweeps), line search.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload newton_f64|newton_f32ir|apply_f64|apply_f32] [--N 20]
+                  [--workload newton_f64|newton_f32ir|newton_bounded|apply_f64|apply_f32] [--N 20]
+
+--workload newton_bounded solves the same transfer with its thrust components bounded (FP64,
+barrier stages; see bounded_table).
 
 With the default --sweep 1 the line also carries the product sweep (N = 2^10..2^24), the FFT vs
-dense tensor-core crossover, and the minimum-time orbit table (Eq. ot, free final time,
-N = 2^10..2^20: Newton and KKT-solve counts per N, the measure of Table tab:m).
+dense tensor-core crossover, the minimum-time orbit table (Eq. ot, free final time,
+N = 2^10..2^20: Newton and KKT-solve counts per N, the measure of Table tab:m), and the bounded
+orbit table (the same transfer with its thrust components bounded, barrier stages, N = 2^10..2^20).
 
 Prints one JSON line on rank 0. With N > 1 (torchrun) every rank solves its own instance
 (replicas; the path has no data-path collective) and the time is the max over ranks.
@@ -50,7 +54,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="newton_f64",
-                    choices=["newton_f64", "newton_f32ir", "apply_f64", "apply_f32", "serve", "peaks"])
+                    choices=["newton_f64", "newton_f32ir", "newton_bounded", "apply_f64", "apply_f32", "serve",
+                             "peaks"])
     ap.add_argument("--serve-requests", type=int, default=0,
                     help="serving requests (default 4096, offered at 0.8 of the closed-loop rate, plus "
                          "1024 each at 0.5 and 0.95; -1 skips serving in the default line)")
@@ -186,8 +191,12 @@ def run_newton(args, rank, world, dist):
     import torch
     from paper_2509_01855_gb300 import _lib, api
     N = 1 << args.N
-    dtype = torch.float64 if args.workload == "newton_f64" else torch.float32
+    dtype = torch.float32 if args.workload == "newton_f32ir" else torch.float64
     prob, z0 = make_orbit(N, dtype)
+    if args.workload == "newton_bounded":
+        lo, hi = orbit_bounds()
+        prob.set_control_bounds(lo, hi)
+        prob.set_barrier(BOUNDED_MU[0], BOUNDED_MU[1])
     ws = api.newton_workspace(prob)
     z = torch.empty_like(z0)
     flush = l2_flush_buffer()
@@ -518,6 +527,55 @@ def min_time_table(lgs=range(10, 21), a=0.05, rf=6.0, t_seed=24.0):
     return rows
 
 
+BOUNDED_MU = (1e-4, 1e-9)   # barrier schedule of the bounded orbit transfer (scaled to its cost)
+
+
+def orbit_bounds(fr=0.9, ft=0.95):
+    """Thrust bounds of the bounded orbit transfer, below the unbounded optimum's peaks:
+    |u_r| <= 0.9 max|u_r| and u_theta <= 0.95 max u_theta (peaks of the unbounded solve at N = 64)."""
+    import torch
+    from paper_2509_01855_gb300 import api
+    p64, z64 = make_orbit(64, torch.float64)
+    api.newton_solve(p64, z64)
+    U = p64.split(z64)[1]
+    a = fr * U[0].abs().max().item()
+    lo, hi = [-a, -float("inf")], [a, ft * U[1].max().item()]
+    p64.close()
+    return lo, hi
+
+
+def bounded_table(lgs=(10, 14, 17, 20)):
+    """The orbit transfer of the headline solve with its thrust bounded (orbit_bounds), solved by
+    newton_solve's barrier stages mu = 1e-4 .. 1e-9 in the primal and in the primal-dual form.
+    Per N and form: Newton iterations over all stages,
+    Krylov iterations, the solve's device time (CUDA events, FP64) and how close the solution
+    comes to the bounds."""
+    import torch
+    from paper_2509_01855_gb300 import api
+    lo, hi = orbit_bounds()
+    mu0, mu_final = BOUNDED_MU
+    rows = {"bounds": {"lo": lo, "hi": hi}, "mu0": mu0, "mu_final": mu_final}
+    for lg, form in [(lg, f) for lg in lgs for f in ("primal", "primal_dual")]:
+        N = 1 << lg
+        prob, z = make_orbit(N, torch.float64)
+        prob.set_control_bounds(lo, hi)
+        prob.set_barrier(mu0, mu_final, form)
+        ws = api.newton_workspace(prob)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        info = api.newton_solve(prob, z, workspace=ws, raise_on_fail=False)
+        e1.record()
+        torch.cuda.synchronize()
+        Ub = prob.split(z)[1]
+        rows["%d_%s" % (lg, form)] = {"newton_its": info["iterations"], "krylov_its": info["krylov_iterations"],
+                         "backtracks": info["backtracks"], "converged": bool(info["converged"]),
+                         "residual": info["residual"], "ms": round(e0.elapsed_time(e1), 3),
+                         "gap_ur": hi[0] - Ub[0].abs().max().item(), "gap_ut": hi[1] - Ub[1].max().item()}
+        prob.close()
+    return rows
+
+
 def cpu_apply_baseline(N):
     """The oracle's FastBV chain (SciPy DCT-I, as it stands) on 4 FP64 components at N, on the
     host cores with SciPy's FFT on every core and on one; one product each, so the default run
@@ -658,18 +716,25 @@ def run_reference(args):
 def metric_name(args):
     if args.workload.startswith("apply"):
         return "Birkhoff apply GB/s at N=2^%d (B v on 4 components)" % args.N
+    if args.workload == "newton_bounded":
+        return "Newton-Krylov solve rate at N=2^%d (orbit raising, bounded thrust)" % args.N
     return "Newton-Krylov solve rate at N=2^%d (orbit raising)" % args.N
 
 
 def config(args):
     prec = {"newton_f64": "f64 (double-float arithmetic in the FP64 Birkhoff transforms from N = 2^18)",
             "newton_f32ir": "f32 Krylov + f64 refinement",
+            "newton_bounded": "f64 (double-float FP64 transforms from N = 2^18), control bounds by barrier",
             "apply_f64": "f64", "apply_f32": "f32", "serve": "f32ir"}[args.workload]
     c = {"workload": "orbit_raising_newton_krylov" if args.workload.startswith("newton") else "birkhoff_apply",
          "N": 1 << args.N, "nodes": (1 << args.N) + 1, "precision": prec,
          "problem": "polar orbit raising r 1->%.1f, t_f=%g, thrust-vector min-energy, x0=(1,0,0,1)" % (RF, TF),
          "initial_guess": "tangential-thrust spiral", "l2": "flushed between steps (256 MB write)",
          "parallelism": "replicas x%d" % args.gpus}
+    if args.workload == "newton_bounded":
+        c["workload"] = "orbit_raising_newton_krylov_bounded_thrust"
+        c["bounds"] = "|u_r| <= 0.9 max|u_r|, u_theta <= 0.95 max u_theta of the unbounded optimum"
+        c["barrier"] = {"mu0": BOUNDED_MU[0], "mu_final": BOUNDED_MU[1], "form": "primal"}
     return c
 
 
@@ -722,7 +787,7 @@ def main():
     rank, world, dist = dist_setup(args)
     hbm_peak, peak_kind = read_peaks()
     N = 1 << args.N
-    dtype_name = "f64" if args.workload in ("newton_f64", "apply_f64") else "f32"
+    dtype_name = "f64" if args.workload in ("newton_f64", "newton_bounded", "apply_f64") else "f32"
     line = {"metric": metric_name(args), "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype_name, "data": "synthetic", "config": config(args)}
@@ -743,7 +808,7 @@ def main():
         r = run_newton(args, rank, world, dist)
         line.update(value=world * 1000.0 / r["ms"], unit="solves/s", ms_per_step=r["ms"], e2e=r["e2e"],
                     gpu_launches=r["launches"], clocks=r["clocks"], solve=r["solve"])
-        dt = torch.float64 if args.workload == "newton_f64" else torch.float32
+        dt = torch.float32 if args.workload == "newton_f32ir" else torch.float64
     else:
         dt = torch.float64 if args.workload == "apply_f64" else torch.float32
         from paper_2509_01855_gb300 import _lib
@@ -779,10 +844,17 @@ def main():
             line["min_time_table"] = min_time_table()
         except Exception as e:  # the headline line must still print
             line["min_time_table"] = {"error": "%s: %s" % (type(e).__name__, e)}
+        try:
+            line["bounded_table"] = bounded_table()
+        except Exception as e:
+            line["bounded_table"] = {"error": "%s: %s" % (type(e).__name__, e)}
     if args.workload.startswith("newton") and args.serve_requests >= 0:
         line["serve"] = run_serve(args.serve_requests or 4096, args.serve_slots, rank, world, dist,
                                   loads=(0.8, 0.5, 0.95))
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "newton_bounded":
+        line["cpu_baseline"] = {"note": "not measured for the bounded workload (the oracle's bounded solve is "
+                                        "dense); the default workload carries the oracle baseline"}
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         line.update(cpu_baseline())
         line["cpu_apply_baseline"] = cpu_apply_baseline(N)
     if rank == 0:

@@ -281,14 +281,30 @@ bk_status bk_problem_set_params(bk_problem* prob, const double* params, int npar
 bk_status bk_problem_set_control_bounds(bk_problem* prob, const double* lo, const double* hi,
                                         int n);
 
+/* Form in which newton_solve treats the barrier problem of a bounded problem (Nocedal and
+ * Wright, Numerical Optimization, Sections 19.2 and 19.6). */
+typedef enum {
+  BK_BARRIER_PRIMAL = 0,       /* Newton on the barrier problem's own KKT conditions           */
+  BK_BARRIER_PRIMAL_DUAL = 1   /* bound multipliers z_l, z_h as unknowns with the complementarity
+                                  conditions (u - lo) z_l = (hi - u) z_h = mu s w, eliminated in
+                                  every step (the KKT system keeps its form with
+                                  z_l / (u - lo) + z_h / (hi - u) on the control diagonal); inner
+                                  GMRES in the merit's norm                                   */
+} bk_barrier_form;
+
 /* Barrier schedule of a bounded problem: newton_solve runs Newton stages with
- * mu = mu0, mu0 / 10, ... down to mu_final (each to ||F_mu||_W <= max(tol, 10 mu), the last to
- * tol). Defaults 0.1 and 1e-6: the barrier solution lies O(mu_final) from the bounded optimum,
- * and the barrier Hessian of an active bound grows like 1 / mu_final, which limits how far the
- * last stage converges (at 1e-7 the double integrator's last stage stalled near ||F||_W = 1e-9
- * in the FP64 reference computation). mu0 = mu_final: one stage. Host only; BK_ERR_ARG unless
- * 0 < mu_final <= mu0 <= 1e6. */
-bk_status bk_problem_set_barrier(bk_problem* prob, double mu0, double mu_final);
+ * mu = mu0, mu0 / 10, ... down to mu_final (each to a merit <= max(tol, 10 mu), the last to
+ * tol), in the given form. Defaults 0.1, 1e-6, BK_BARRIER_PRIMAL. mu scales with the cost: the
+ * barrier's gradient mu s w / (distance to the bound) should start comparable to the cost's
+ * gradient (the orbit transfer, with thrusts near 1e-2, takes mu0 = 1e-4). The barrier solution
+ * lies O(mu_final) from the bounded optimum, and the barrier Hessian of an active bound grows
+ * like 1 / mu_final, which limits how far the last stage converges. On the orbit transfer
+ * with bounded thrust (mu 1e-4 .. 1e-9) the primal form took 34-40 Newton steps and the
+ * primal-dual form 33 at every N from 2^10 to 2^20, the primal form the faster at 2^20 (fewer
+ * GMRES iterations); on the double integrator with |u| <= 5 (mu 0.1 .. 1e-6) the primal-dual
+ * form takes 18 Newton steps against 46. mu0 = mu_final: one stage. Host only; BK_ERR_ARG unless
+ * 0 < mu_final <= mu0 <= 1e6 and form is one of bk_barrier_form. */
+bk_status bk_problem_set_barrier(bk_problem* prob, double mu0, double mu_final, int form);
 
 /* Device bytes the problem holds (its plans, linearisation data and scratch); workspaces are
  * extra (bk_krylov_workspace_bytes, bk_newton_workspace_bytes). For memory-based admission. */

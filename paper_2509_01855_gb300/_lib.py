@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libbirkhoff.so")
 BK_F64, BK_F32 = 0, 1
 BK_DBL_INT, BK_ORBIT, BK_BILINEAR, BK_ORBIT_MT = 0, 1, 2, 3
 BK_OP_STATE, BK_OP_KKT = 0, 1
+BK_BARRIER_PRIMAL, BK_BARRIER_PRIMAL_DUAL = 0, 1
 STATUS = {0: "BK_OK", 1: "BK_ERR_ARG", 2: "BK_ERR_CUDA", 3: "BK_ERR_OOM",
           4: "BK_ERR_NOT_CONVERGED", 5: "BK_ERR_TIMEOUT", 6: "BK_ERR_INFEASIBLE",
           7: "BK_ERR_UNSUPPORTED"}
@@ -107,7 +108,7 @@ def lib():
         "bk_problem_destroy": (None, [vp]),
         "bk_problem_set_params": (c_int, [vp, ctypes.POINTER(dbl), c_int, dbl, dbl]),
         "bk_problem_set_control_bounds": (c_int, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), c_int]),
-        "bk_problem_set_barrier": (c_int, [vp, dbl, dbl]),
+        "bk_problem_set_barrier": (c_int, [vp, dbl, dbl, c_int]),
         "bk_problem_device_bytes": (ctypes.c_size_t, [vp]),
         "bk_problem_info": (c_int, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                     ctypes.POINTER(c_int), ctypes.POINTER(i64),

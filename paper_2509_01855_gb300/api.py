@@ -232,10 +232,11 @@ class Problem:
         L.check(L.lib().bk_problem_set_control_bounds(self._h, (ctypes.c_double * n)(*lo),
                                                       (ctypes.c_double * n)(*hi), n))
 
-    def set_barrier(self, mu0=0.1, mu_final=1e-6):
-        """Barrier schedule of a bounded solve: stages mu0, mu0/10, ... down to mu_final. The
-        residual and operator calls use mu_final."""
-        L.check(L.lib().bk_problem_set_barrier(self._h, float(mu0), float(mu_final)))
+    def set_barrier(self, mu0=0.1, mu_final=1e-6, form="primal"):
+        """Barrier schedule of a bounded solve: stages mu0, mu0/10, ... down to mu_final, in the
+        "primal" or "primal_dual" form. The residual and operator calls use mu_final (primal)."""
+        code = {"primal": L.BK_BARRIER_PRIMAL, "primal_dual": L.BK_BARRIER_PRIMAL_DUAL}[form]
+        L.check(L.lib().bk_problem_set_barrier(self._h, float(mu0), float(mu_final), code))
 
     def device_bytes(self):
         return int(L.lib().bk_problem_device_bytes(self._h))

@@ -813,7 +813,8 @@ template <typename T, int KIND>
 __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, const T* __restrict__ w, T s,
                            const T* __restrict__ in, const T* __restrict__ Bt, T* __restrict__ Mu, int64_t P,
                            int64_t L, TermSpec ts, T cost_uu, T* __restrict__ out, T pa, int64_t s_idx,
-                           double* __restrict__ part, const double* __restrict__ sdev, BarSpec bs) {
+                           double* __restrict__ part, const double* __restrict__ sdev,
+                           const T* __restrict__ hbar) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu, NV = NX + NU;
   __shared__ double red[32];
   // sdev: Bt and Mu arrive unscaled (B^a, B^aT products) and take the device time scale here;
@@ -852,8 +853,9 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
     Dyn<KIND>::template jac<T>(x, u, Jx, Ju, pa);
     Dyn<KIND>::template hess<T>(x, u, m_, H, pa);
     const T swk = s * w[k] * cost_uu;
-    T gb[NUM], hb[NUM];   // control bounds: the barrier's Hessian diagonal at the linearisation
-    bar_terms<T, NU>(bs, u, s * w[k], gb, hb);
+    T hb[NUM];   // control bounds: the barrier's diagonal of the control block
+#pragma unroll
+    for (int q = 0; q < NU; ++q) hb[q] = hbar ? hbar[q * P + k] : T(0);
     if (part) {
       T fx[NXM];
       Dyn<KIND>::template f<T>(x, u, fx, pa);
@@ -1015,7 +1017,8 @@ __global__ void k_border_fix(const T* __restrict__ q, const double* __restrict__
 template <typename T, int KIND>
 __global__ void k_pre_u(const T* __restrict__ xu, const T* __restrict__ w, T s, T cost_uu, const T* __restrict__ ru,
                         const T* __restrict__ b, int64_t P, int64_t L, T* __restrict__ yu, T* __restrict__ g,
-                        T gsign, const T* __restrict__ mu, T pa, const double* __restrict__ sdev, BarSpec bs) {
+                        T gsign, const T* __restrict__ mu, T pa, const double* __restrict__ sdev,
+                        const T* __restrict__ hbar) {
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   if (sdev) s = T(*sdev);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
@@ -1036,15 +1039,32 @@ __global__ void k_pre_u(const T* __restrict__ xu, const T* __restrict__ w, T s, 
 #pragma unroll
     for (int m = 0; m < NX; ++m) mk[m] = Dyn<KIND>::huu_needs_mu ? mu[m * P + k] : T(0);
     const T huu = Dyn<KIND>::template pre_huu<T>(mk, s * w[k] * cost_uu, pa);
-    // control bounds: the barrier's Hessian diagonal joins the (diagonal) control block
-    T gb[NUM], hb[NUM];
-    bar_terms<T, NU>(bs, u, s * w[k], gb, hb);
+    // control bounds: the barrier's diagonal joins the (diagonal) control block, one inverse per
+    // control (for two controls from one division: 1/h0 = h1 r, 1/h1 = h0 r, r = 1/(h0 h1))
+    T inv[NUM];
+    if (hbar) {
+      T hq[NUM];
+#pragma unroll
+      for (int q = 0; q < NU; ++q) hq[q] = huu + hbar[q * P + k];
+      if constexpr (NU == 2) {
+        const T r = T(1) / (hq[0] * hq[1]);
+        inv[0] = hq[1] * r;
+        inv[1] = hq[0] * r;
+      } else {
+#pragma unroll
+        for (int q = 0; q < NU; ++q) inv[q] = T(1) / hq[q];
+      }
+    } else {
+      const T i0 = T(1) / huu;
+#pragma unroll
+      for (int q = 0; q < NU; ++q) inv[q] = i0;
+    }
 #pragma unroll
     for (int q = 0; q < NU; ++q) {
       T a = ru ? ru[q * P + k] : T(0);
 #pragma unroll
       for (int m = 0; m < NX; ++m) a += s * Ju[m * NU + q] * b[m * P + k];
-      y[q] = a * (T(1) / (huu + hb[q]));
+      y[q] = a * inv[q];
       yu[q * P + k] = y[q];
     }
 #pragma unroll
@@ -1174,8 +1194,29 @@ __global__ void k_resid_post(const double* __restrict__ z, const double* __restr
       F[p * P + k] = g;
       acc += g * g * iw;
     }
-    double gb[NUM], hb[NUM];   // control bounds: the barrier's gradient
-    bar_terms<double, NU>(bs, u, s * wk, gb, hb);
+    // control bounds: the primal barrier gradient, or (primal-dual form) -z_l + z_h with the
+    // complementarity residuals C = (distance to the bound) z - mu s w in the norm (weight 1 / w)
+    double gb[NUM], hb[NUM];
+    if (bs.z) {
+#pragma unroll
+      for (int q = 0; q < NU; ++q) {
+        gb[q] = 0.0;
+        if (bs.mu > 0.0 && bs.has_lo[q]) {
+          const double zl = bs.z[q * P + k];
+          const double c = (u[q] - bs.lo[q]) * zl - bs.mu * s * wk;
+          gb[q] -= zl;
+          acc += c * c * iw;
+        }
+        if (bs.mu > 0.0 && bs.has_hi[q]) {
+          const double zh = bs.z[(NU + q) * P + k];
+          const double c = (bs.hi[q] - u[q]) * zh - bs.mu * s * wk;
+          gb[q] += zh;
+          acc += c * c * iw;
+        }
+      }
+    } else {
+      bar_terms<double, NU>(bs, u, s * wk, gb, hb);
+    }
 #pragma unroll
     for (int q = 0; q < NU; ++q) {
       double g = s * wk * cost_uu * u[q] + gb[q];
@@ -1321,7 +1362,7 @@ static bk_status alloc_opdata(Problem* pr, OpData& d, int dtype) {
 
 static void free_opdata(OpData& d) {
   if (d.plan) plan_destroy(d.plan);
-  void* ps[] = {d.xu, d.mu, d.Dn, d.Zc, d.HWc, d.Qc, d.Sinv, d.t1, d.t2, d.t3, d.brd, d.brq, d.bgam};
+  void* ps[] = {d.xu, d.mu, d.Dn, d.Zc, d.HWc, d.Qc, d.Sinv, d.t1, d.t2, d.t3, d.brd, d.brq, d.bgam, d.hbar};
   for (void* p : ps) dfree(p);
   for (int l = 0; l < MAXLEV; ++l) {
     dfree(d.lvm[l]);
@@ -1332,6 +1373,42 @@ static void free_opdata(OpData& d) {
 }
 
 // --- linearisation ---------------------------------------------------------------------------
+// Control bounds: the barrier's diagonal of the control block at z_lin. Primal-dual form (b.z):
+// Sigma = z_l / (u - l) + z_h / (h - u), the multipliers' elimination; primal form: the barrier
+// Hessian mu s w (1 / (u - l)^2 + 1 / (h - u)^2).
+template <typename T, int NU>
+__global__ void k_lin_bar(const double* __restrict__ z, const double* __restrict__ w, double s, int64_t P, int64_t L,
+                          int nx, BarSpec b, T* __restrict__ hbar) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k >= L) {
+#pragma unroll
+      for (int q = 0; q < NU; ++q) hbar[q * P + k] = T(0);
+      continue;
+    }
+    double u[NUM], g[NUM], h[NUM];
+#pragma unroll
+    for (int q = 0; q < NU; ++q) u[q] = z[(nx + q) * P + k];
+    if (b.z) {
+#pragma unroll
+      for (int q = 0; q < NU; ++q) {
+        h[q] = 0.0;
+        if (b.has_lo[q]) h[q] += b.z[q * P + k] / (u[q] - b.lo[q]);
+        if (b.has_hi[q]) h[q] += b.z[(NU + q) * P + k] / (b.hi[q] - u[q]);
+      }
+    } else {
+      bar_terms<double, NU>(b, u, s * w[k], g, h);
+    }
+#pragma unroll
+    for (int q = 0; q < NU; ++q) hbar[q * P + k] = (T)h[q];
+  }
+}
+
+// The barrier diagonal of one precision's data, null when the problem has no active bounds.
+template <typename T>
+static const T* bar_hbar(const Problem* pr, const OpData& d) {
+  return pr->has_bounds && pr->bar_mu > 0.0 ? (const T*)d.hbar : nullptr;
+}
+
 // Segment maps and scan levels from the node factors N_k (level data of the sweeps).
 template <typename T, int NX>
 static bk_status lin_levels(Problem* pr, OpData& d, cudaStream_t st) {
@@ -1383,7 +1460,7 @@ static bk_status lin_schur_launch(Problem* pr, OpData& d, cudaStream_t st) {
     // yu = s Ju^T b / (s w) = -H~^{-1} W and g = Ju yu = -Ju H~^{-1} W.
     T* HW = HWc + (int64_t)r * NU * P;
     k_pre_u<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.w, s, (T)1, nullptr, bz, P, L, HW, g, T(1),
-                                              (const T*)d.mu, (T)pr->dyn_param(), nullptr, bar_spec(pr));
+                                              (const T*)d.mu, (T)pr->dyn_param(), nullptr, bar_hbar<T>(pr, d));
     BK_CHECK_LAUNCH();
     // Q = P^{-1} Pu HW: forward sweep with Y = 0 and forcing -Ju HW = Ju (-HW) = g
     k_unit<T><<<nblk(NX * P), 256, 0, st>>>(unit, NX * P, -1);
@@ -1464,6 +1541,15 @@ static bk_status linearize_kind(Problem* pr, const double* z, const double* mu, 
       BK_CHECK_LAUNCH();
     }
   }
+  if (pr->has_bounds && pr->bar_mu > 0.0) {
+    const BarSpec b = bar_spec(pr);
+    k_lin_bar<double, NU><<<nblk(P), 256, 0, st>>>(z, pr->d64.plan->w64, pr->s, P, pr->L, NX, b, (double*)pr->d64.hbar);
+    BK_CHECK_LAUNCH();
+    if (pr->d32.plan) {
+      k_lin_bar<float, NU><<<nblk(P), 256, 0, st>>>(z, pr->d64.plan->w64, pr->s, P, pr->L, NX, b, (float*)pr->d32.hbar);
+      BK_CHECK_LAUNCH();
+    }
+  }
   pr->linearized = true;
   if (keep != LIN_FULL) return BK_OK;
   if (pr->n_e > 0 && pr->has_cost) {
@@ -1514,7 +1600,7 @@ static bk_status apply_typed(Problem* pr, OpData& d, int op, const T* in, T* out
   BK_TRY(plan_apply_n(d.plan, in + (NX + NU) * P, Mu, NX, true, sd ? 1.0 : pr->s, st));
   k_kkt_post<T, KIND><<<ft ? FT_NB : nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.mu, (const T*)d.w, (T)pr->s, in,
                                                             t2, Mu, P, L, term_spec(pr), (T)pr->cost_uu(), out, pa,
-                                                            pr->s_idx(), ft ? pr->sred : nullptr, sd, bar_spec(pr));
+                                                            pr->s_idx(), ft ? pr->sred : nullptr, sd, bar_hbar<T>(pr, d));
   BK_CHECK_LAUNCH();
   if (ft) {
     k_free_finish<T><<<1, 256, 0, st>>>(pr->sred, FT_NB, -1.0 / pr->s, out + pr->s_idx());
@@ -1566,7 +1652,7 @@ static bk_status precond_typed(Problem* pr, OpData& d, int op, const T* in, T* o
   T* g = (T*)d.t2;
   BK_TRY((run_sweep<T, NX, 1>(pr, d, rx, nullptr, yl, b, st)));
   k_pre_u<T, KIND><<<nblk(P), 256, 0, st>>>((const T*)d.xu, (const T*)d.w, (T)pr->s, (T)1, ru, b, P, L, yu, g, T(1),
-                                            (const T*)d.mu, (T)pr->dyn_param(), sdev_of(pr), bar_spec(pr));
+                                            (const T*)d.mu, (T)pr->dyn_param(), sdev_of(pr), bar_hbar<T>(pr, d));
   BK_CHECK_LAUNCH();
   BK_TRY((run_sweep<T, NX, 0>(pr, d, rl, g, yx, nullptr, st)));
   if (pr->n_e > 0) {
@@ -1727,6 +1813,7 @@ static void problem_free(Problem* pr) {
   dfree(pr->s_dev);
   dfree(pr->pcin);
   dfree(pr->pcout);
+  dfree(pr->bar_buf);
   if (pr->red_host) cudaFreeHost(pr->red_host);
   delete pr;
 }
@@ -1964,6 +2051,22 @@ bk_status bk_problem_set_control_bounds(bk_problem* prob, const double* lo, cons
     BK_ARG(!isnan(lo[q]) && !isnan(hi[q]) && lo[q] < hi[q] && lo[q] != INFINITY && hi[q] != -INFINITY,
            "control %d: need lo < hi (got %g, %g)", q, lo[q], hi[q]);
   }
+  if (!p->bar_buf) {
+    // the barrier diagonals of both precisions and newton_solve's multiplier vectors
+    bk::AllocCounter counter(&p->bytes);
+    const size_t m = (size_t)p->n_u * p->P;
+    bk_status st = bk::dmalloc((void**)&p->bar_buf, sizeof(double) * 6 * m);
+    if (st == BK_OK) st = bk::dmalloc(&p->d64.hbar, sizeof(double) * m);
+    if (st == BK_OK && p->d32.plan) st = bk::dmalloc(&p->d32.hbar, sizeof(float) * m);
+    if (st != BK_OK) {
+      bk::dfree(p->bar_buf);
+      bk::dfree(p->d64.hbar);
+      bk::dfree(p->d32.hbar);
+      p->bar_buf = nullptr;
+      p->d64.hbar = p->d32.hbar = nullptr;
+      return st;
+    }
+  }
   for (int q = 0; q < bk::NUM; ++q) {
     p->ulo[q] = q < n ? lo[q] : -INFINITY;
     p->uhi[q] = q < n ? hi[q] : INFINITY;
@@ -1973,13 +2076,15 @@ bk_status bk_problem_set_control_bounds(bk_problem* prob, const double* lo, cons
   return BK_OK;
 }
 
-bk_status bk_problem_set_barrier(bk_problem* prob, double mu0, double mu_final) {
+bk_status bk_problem_set_barrier(bk_problem* prob, double mu0, double mu_final, int form) {
   BK_ARG(prob != nullptr, "problem is NULL");
   BK_ARG(isfinite(mu0) && isfinite(mu_final) && mu_final > 0.0 && mu0 >= mu_final && mu0 <= 1e6,
          "need 0 < mu_final <= mu0 <= 1e6 (got %g, %g)", mu0, mu_final);
+  BK_ARG(form == BK_BARRIER_PRIMAL || form == BK_BARRIER_PRIMAL_DUAL, "unknown barrier form %d", form);
   bk::Problem* p = reinterpret_cast<bk::Problem*>(prob);
   p->bar_mu0 = mu0;
   p->bar_mu_final = mu_final;
+  p->bar_form = form;
   if (p->has_bounds) p->bar_mu = mu_final;
   return BK_OK;
 }

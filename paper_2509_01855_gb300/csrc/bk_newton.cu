@@ -18,13 +18,22 @@
 // ||F||_W^2 along d (slope -2 ||F||_W^2 at alpha = 0, the Newton value), safeguarded to
 // [alpha / 10, alpha / 2], instead of halving.
 //
-// Control bounds lo <= u <= hi (bk_problem_set_control_bounds): a primal logarithmic barrier on
-// the quadrature, -mu s sum_i w_i sum_q [log(u_qi - lo_q) + log(hi_q - u_qi)], joins J (Nocedal
-// and Wright, Numerical Optimization, 2nd ed., Section 19.6). The solve runs Newton stages for
-// mu = mu_0, mu_0 / 10, ... down to mu_final, each to ||F_mu||_W <= max(tol, 10 mu) and the last
-// to tol, from controls first moved 1e-3 of the bound gap inside; each step length starts at the
-// fraction-to-boundary bound min(1, 0.995 max{alpha : lo < u + alpha du < hi}) and is halved
-// on backtracking; the forcing term restarts with each stage.
+// Control bounds lo <= u <= hi (bk_problem_set_control_bounds): a logarithmic barrier on the
+// quadrature, -mu s sum_i w_i sum_q [log(u_qi - lo_q) + log(hi_q - u_qi)], joins J (Nocedal and
+// Wright, Numerical Optimization, 2nd ed., Sections 19.2 and 19.6), in one of two forms:
+//  - primal (default): Newton on the barrier problem's KKT conditions; the barrier's gradient joins
+//    the control rows and its Hessian mu s w (1/(u - lo)^2 + 1/(hi - u)^2) the control diagonal;
+//  - primal-dual: the bound multipliers z_l, z_h are unknowns with the complementarity conditions
+//    (u - lo) z_l = (hi - u) z_h = mu s w. Each Newton step eliminates them node by node: the KKT
+//    system keeps its form with Sigma = z_l / (u - lo) + z_h / (hi - u) on the control diagonal
+//    and a corrected right-hand side, and dz follows from du.
+// Either way the KKT system keeps a diagonal control block, so the same preconditioner applies.
+// The solve runs stages mu = mu_0, mu_0 / 10, ... down to mu_final, each to a merit (||F||_W, with
+// the complementarity residuals in the primal-dual form) <= max(tol, 10 mu) and the last to tol,
+// from controls first moved 1e-3 of the bound gap inside (and multipliers on the first stage's
+// central path); each step length starts at the fraction-to-boundary bound (0.995 of the largest
+// step keeping u inside its bounds and z positive, at most 1) and is halved on backtracking; the
+// forcing term restarts with each stage.
 //
 // Free final time (BK_ORBIT_MT): s = (t_f - t_0)/2 sits in z's tail slot. The problem's s follows
 // z (read back once per step, with the step's ds), trials with s <= 0 are rejected, and mu is
@@ -99,18 +108,93 @@ __global__ void k_interior(double* __restrict__ z, int64_t P, int64_t L, int nx,
   }
 }
 
-// Per block: the largest alpha (at most 1 / kTau) keeping lo < u + alpha du < hi at its nodes.
-__global__ void k_max_step(const double* __restrict__ z, const double* __restrict__ d, int64_t P, int64_t L, int nx,
-                           BarSpec b, double* __restrict__ partial) {
+// Multipliers on the central path of the current mu: z_l = mu s w / (u - lo), z_h = mu s w / (hi - u)
+// (zero for an absent bound and in the padding).
+__global__ void k_pd_init(const double* __restrict__ z, const double* __restrict__ w, double s, int64_t P, int64_t L,
+                          int nx, int nu, BarSpec b, double* __restrict__ zb) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NUM; ++q) {
+      if (q >= nu) break;
+      const double u = k < L ? z[(nx + q) * P + k] : 0.0;
+      const double c = k < L ? b.mu * s * w[k] : 0.0;
+      zb[q * P + k] = k < L && b.has_lo[q] ? c / (u - b.lo[q]) : 0.0;
+      zb[(nu + q) * P + k] = k < L && b.has_hi[q] ? c / (b.hi[q] - u) : 0.0;
+    }
+  }
+}
+
+// Right-hand side of the eliminated primal-dual step: control rows += -C_l / (u - lo) + C_h / (hi - u),
+// C_l = (u - lo) z_l - mu s w, C_h = (hi - u) z_h - mu s w.
+__global__ void k_pd_rhs(const double* __restrict__ z, const double* __restrict__ zb, const double* __restrict__ w,
+                         double s, int64_t P, int64_t L, int nx, int nu, BarSpec b, double* __restrict__ rhs) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+    const double c = b.mu * s * w[k];
+#pragma unroll
+    for (int q = 0; q < NUM; ++q) {
+      if (q >= nu) break;
+      const double u = z[(nx + q) * P + k];
+      double r = 0.0;
+      if (b.has_lo[q]) {
+        const double dl = u - b.lo[q];
+        r -= (dl * zb[q * P + k] - c) / dl;
+      }
+      if (b.has_hi[q]) {
+        const double dh = b.hi[q] - u;
+        r += (dh * zb[(nu + q) * P + k] - c) / dh;
+      }
+      rhs[(nx + q) * P + k] += r;
+    }
+  }
+}
+
+// Multiplier steps from the control step du: dz_l = (-C_l - z_l du) / (u - lo),
+// dz_h = (-C_h + z_h du) / (hi - u) (zero for an absent bound and in the padding).
+__global__ void k_pd_dz(const double* __restrict__ z, const double* __restrict__ d, const double* __restrict__ zb,
+                        const double* __restrict__ w, double s, int64_t P, int64_t L, int nx, int nu, BarSpec b,
+                        double* __restrict__ dzb) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NUM; ++q) {
+      if (q >= nu) break;
+      double dl_ = 0.0, dh_ = 0.0;
+      if (k < L) {
+        const double c = b.mu * s * w[k];
+        const double u = z[(nx + q) * P + k], du = d[(nx + q) * P + k];
+        if (b.has_lo[q]) {
+          const double dl = u - b.lo[q], zl = zb[q * P + k];
+          dl_ = (-(dl * zl - c) - zl * du) / dl;
+        }
+        if (b.has_hi[q]) {
+          const double dh = b.hi[q] - u, zh = zb[(nu + q) * P + k];
+          dh_ = (-(dh * zh - c) + zh * du) / dh;
+        }
+      }
+      dzb[q * P + k] = dl_;
+      dzb[(nu + q) * P + k] = dh_;
+    }
+  }
+}
+
+// Per block: the largest alpha (at most 1 / kTau) keeping lo < u + alpha du < hi and the
+// multipliers z + alpha dz > 0 at its nodes.
+__global__ void k_max_step(const double* __restrict__ z, const double* __restrict__ d, const double* __restrict__ zb,
+                           const double* __restrict__ dzb, int64_t P, int64_t L, int nx, int nu, BarSpec b,
+                           double* __restrict__ partial) {
   __shared__ double red[32];
   double a = 1.0 / kTau;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
     for (int q = 0; q < NUM; ++q) {
+      if (q >= nu) break;
       if (!b.has_lo[q] && !b.has_hi[q]) continue;
       const double u = z[(nx + q) * P + k], du = d[(nx + q) * P + k];
       if (b.has_lo[q] && du < 0.0) a = fmin(a, (b.lo[q] - u) / du);
       if (b.has_hi[q] && du > 0.0) a = fmin(a, (b.hi[q] - u) / du);
+      if (!zb) continue;   // primal form: no multipliers
+      const double dzl = dzb[q * P + k], dzh = dzb[(nu + q) * P + k];
+      if (b.has_lo[q] && dzl < 0.0) a = fmin(a, -zb[q * P + k] / dzl);
+      if (b.has_hi[q] && dzh < 0.0) a = fmin(a, -zb[(nu + q) * P + k] / dzh);
     }
   }
   for (int o = 16; o > 0; o >>= 1) a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
@@ -169,10 +253,11 @@ static bk_status norm2(Problem* pr, const double* x, int64_t n, double* out, cud
   return BK_OK;
 }
 
-// Fraction-to-boundary step bound min(1, kTau * max alpha) along d, synchronous.
-static bk_status max_step(Problem* pr, const double* z, const double* d, double* out, cudaStream_t st) {
+// Fraction-to-boundary step bound min(1, kTau * max alpha) along (d, dz), synchronous.
+static bk_status max_step(Problem* pr, const double* z, const double* d, const double* zb, const double* dzb,
+                          double* out, cudaStream_t st) {
   const int nb = (int)((pr->L + 255) / 256 < 592 ? (pr->L + 255) / 256 : 592);
-  k_max_step<<<nb, 256, 0, st>>>(z, d, pr->P, pr->L, pr->n_x, bar_spec(pr), pr->red);
+  k_max_step<<<nb, 256, 0, st>>>(z, d, zb, dzb, pr->P, pr->L, pr->n_x, pr->n_u, bar_spec(pr), pr->red);
   BK_CHECK_LAUNCH();
   k_min_block<<<1, 256, 0, st>>>(pr->red, nb, pr->red + 1024);
   BK_CHECK_LAUNCH();
@@ -182,12 +267,13 @@ static bk_status max_step(Problem* pr, const double* z, const double* d, double*
   return BK_OK;
 }
 
-// Leaves the problem's barrier parameter at mu_final when a solve returns (its residual and
-// operator then describe the last stage's problem).
+// Leaves the problem's barrier parameter at mu_final and its kernels in the primal form when a
+// solve returns (its residual and operator then describe the last stage's barrier problem).
 struct BarrierReset {
   Problem* pr;
   ~BarrierReset() {
     if (pr->has_bounds) pr->bar_mu = pr->bar_mu_final;
+    pr->bar_z = nullptr;
   }
 };
 
@@ -256,12 +342,24 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     pr->s = hs[0];
   }
   const bool bar = pr->has_bounds;
+  const bool pd = bar && pr->bar_form == BK_BARRIER_PRIMAL_DUAL;
   BarrierReset reset{pr};
   double mu = bar ? pr->bar_mu0 : 0.0;
+  // bound multipliers (primal-dual form): current, trial and step, 2 n_u P each
+  const int64_t nzb = 2 * (int64_t)pr->n_u * pr->P;
+  double* zb = pd ? pr->bar_buf : nullptr;
+  double* zbt = pd ? pr->bar_buf + nzb : nullptr;
+  double* dzb = pd ? pr->bar_buf + 2 * nzb : nullptr;
   if (bar) {
     pr->bar_mu = mu;
+    pr->bar_z = nullptr;
     k_interior<<<g1(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->n_x, bar_spec(pr), 1e-3);
     BK_CHECK_LAUNCH();
+  }
+  if (pd) {
+    k_pd_init<<<g1(pr->P), 256, 0, st>>>(z, pr->d64.plan->w64, pr->s, pr->P, pr->L, pr->n_x, pr->n_u, bar_spec(pr), zb);
+    BK_CHECK_LAUNCH();
+    pr->bar_z = zb;
   }
   BK_TRY(problem_residual(pr, z, F, &phi, st, Mu, false));
   info->residual0 = phi;
@@ -308,10 +406,26 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     BK_TRY(problem_linearize(pr, z, st, Mu, keep));
     k_axpby64<<<g, 256, 0, st>>>(F, -1.0, rhs, 0.0, n);
     BK_CHECK_LAUNCH();
+    // Primal-dual form: GMRES in the merit's norm, to a residual of (forcing term) x the merit.
+    // The eliminated right-hand side carries C / (distance to the bound), which near an active
+    // bound is far larger than the merit's C / sqrt(w): a tolerance relative to it alone gave
+    // steps that were no descent directions (line-search failures on the bounded orbit transfer
+    // at N = 2^20 on the GPU, and from N = 64 in a CPU model of this loop).
+    const bool weighted = o.weighted_inner != 0 || pd;
+    if (pd) {
+      k_pd_rhs<<<g1(pr->L), 256, 0, st>>>(z, zb, pr->d64.plan->w64, pr->s, pr->P, pr->L, pr->n_x, pr->n_u,
+                                          bar_spec(pr), rhs);
+      BK_CHECK_LAUNCH();
+      if (o.krylov_rtol <= 0) {
+        double bw = 0.0;
+        BK_TRY(problem_wnorm(pr, rhs, &bw, st));
+        if (bw > phi) ko.rtol *= phi / bw;
+      }
+    }
     bk_krylov_info ki;
     if (pr->dtype == BK_F64) {
       const KrylovMu aux = {Trec, nxP, Mud, nxP};
-      BK_TRY(gmres(pr, pr->d64, BK_OP_KKT, rhs, d, ko, &ki, gws, st, ft ? nullptr : &aux, o.weighted_inner != 0));
+      BK_TRY(gmres(pr, pr->d64, BK_OP_KKT, rhs, d, ko, &ki, gws, st, ft ? nullptr : &aux, weighted));
       info->krylov_iterations += ki.iterations;
       info->kkt_solves += 1;
     } else {
@@ -324,7 +438,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
       for (int sweep = 0; sweep < o.max_refine; ++sweep) {
         k_cast<double, float><<<g, 256, 0, st>>>(r, r32, n);
         BK_CHECK_LAUNCH();
-        BK_TRY(gmres(pr, pr->d32, BK_OP_KKT, r32, d32, ko, &ki, gws, st, nullptr, o.weighted_inner != 0));
+        BK_TRY(gmres(pr, pr->d32, BK_OP_KKT, r32, d32, ko, &ki, gws, st, nullptr, weighted));
         info->krylov_iterations += ki.iterations;
         info->kkt_solves += 1;
         k_acc32<<<g, 256, 0, st>>>(d32, d, n);
@@ -349,12 +463,22 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     }
     // backtracking line search on ||F||_W, from the fraction-to-boundary bound under control bounds
     double alpha = 1.0, phit = 0.0;
-    if (bar) BK_TRY(max_step(pr, z, d, &alpha, st));
+    if (pd) {
+      k_pd_dz<<<g1(pr->P), 256, 0, st>>>(z, d, zb, pr->d64.plan->w64, pr->s, pr->P, pr->L, pr->n_x, pr->n_u,
+                                         bar_spec(pr), dzb);
+      BK_CHECK_LAUNCH();
+    }
+    if (bar) BK_TRY(max_step(pr, z, d, zb, dzb, &alpha, st));
     int bt = 0;
     const double phi2 = phi * phi;
     for (;;) {
       k_step<<<g, 256, 0, st>>>(z, d, alpha, zt, n);
       BK_CHECK_LAUNCH();
+      if (pd) {
+        k_step<<<g1(nzb), 256, 0, st>>>(zb, dzb, alpha, zbt, nzb);
+        BK_CHECK_LAUNCH();
+        pr->bar_z = zbt;
+      }
       if (ft) {
         pr->s = s0 + alpha * ds;
         if (!(pr->s > 0.0)) {
@@ -378,6 +502,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
       ++bt;
     }
     info->backtracks += bt;
+    if (pd) pr->bar_z = zb;
     if (!(phit <= (1.0 - 1e-4 * alpha) * phi)) {
       pr->s = s0;
       info->iterations = it;
@@ -387,6 +512,10 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     }
     BK_TRY_CUDA(cudaMemcpyAsync(z, zt, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     std::swap(Mu, Mut);
+    if (pd) {
+      std::swap(zb, zbt);
+      pr->bar_z = zb;
+    }
     fast = bt == 0 && phit <= 0.1 * phi;
     phi = phit;
     ++it;

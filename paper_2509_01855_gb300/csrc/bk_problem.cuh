@@ -175,6 +175,8 @@ struct BarSpec {
   double mu;          // 0: no barrier terms
   double lo[NUM], hi[NUM];
   int has_lo[NUM], has_hi[NUM];
+  const double* z;    // primal-dual form: bound multipliers, z_l of control q at q P + k and z_h at
+                      // (n_u + q) P + k (FP64); null: primal form (multipliers on the central path)
 };
 
 // Barrier gradient g_q and Hessian diagonal h_q of -mu swk sum_q [log(u_q - lo_q) + log(hi_q - u_q)]
@@ -229,6 +231,9 @@ struct OpData {
   void* t1 = nullptr;
   void* t2 = nullptr;
   void* t3 = nullptr;
+  // control bounds: the barrier's diagonal of the control block at the linearisation (n_u * P),
+  // allocated when bounds are first set
+  void* hbar = nullptr;
 };
 
 struct Problem {
@@ -264,6 +269,9 @@ struct Problem {
   bool has_bounds = false;
   double ulo[NUM] = {0, 0}, uhi[NUM] = {0, 0};
   double bar_mu = 0.0, bar_mu0 = 0.1, bar_mu_final = 1e-6;
+  int bar_form = BK_BARRIER_PRIMAL;  // newton_solve's form of the barrier problem
+  double* bar_buf = nullptr;   // newton_solve's bound multipliers: z, trial z, dz (2 n_u P each)
+  const double* bar_z = nullptr;  // multipliers the kernels use (null: primal form)
   double* s_dev = nullptr;     // device copy of s (fixed final time): the GMRES-step kernels read s
                                // from here, so captured graphs stay valid when the parameters change
   int64_t kkt_len() const { return (2 * n_x + n_u) * P + 32; }
@@ -284,6 +292,7 @@ inline BarSpec bar_spec(const Problem* pr) {
   BarSpec b;
   memset(&b, 0, sizeof(b));
   b.mu = pr->has_bounds ? pr->bar_mu : 0.0;
+  b.z = pr->has_bounds ? pr->bar_z : nullptr;
   for (int q = 0; q < NUM; ++q) {
     b.lo[q] = pr->ulo[q];
     b.hi[q] = pr->uhi[q];

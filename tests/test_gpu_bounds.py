@@ -2,9 +2,10 @@
 
 - At a fixed barrier parameter the residual, the KKT operator and the preconditioner of a
   bounded problem match oracle/barrier.py (BarrierKKT) at an interior point.
-- The bounded Newton solve (barrier stages, fraction-to-boundary steps) reaches the oracle's
-  barrier solution, for the double integrator (|u| <= 5) and for the orbit transfer with its
-  thrust components bounded below their unbounded peaks.
+- The bounded Newton solve (barrier stages, fraction-to-boundary steps), in the primal and in the
+  primal-dual form, reaches the oracle's barrier solution of the same form, for the double
+  integrator (|u| <= 5) and for the orbit transfer with its thrust components bounded below
+  their unbounded peaks.
 - On the double integrator the solution is the one Pontryagin's principle gives (computed in
   tests/test_oracle_barrier.py, independently of both solvers), bounds far away give the
   unbounded closed form, and FP32 inner solves reach the FP64 solution.
@@ -97,62 +98,83 @@ def test_barrier_operators_match_oracle(kind, N, dtype):
     assert rel(to_packed(prob, F), DenseKKT.residual(K, vec)) < 1e-12
 
 
-def _solve_gpu(api, lib, kind, N, dtype, oprob, vec0, lo, hi, mu0, mu_final, tol=1e-10):
+FORMS = ["primal", "primal_dual"]
+
+
+def _oracle_solve(K, vec0, form, **kw):
+    if form == "primal":
+        return K.solve(vec0, **kw)
+    vec, _, _, info = K.solve_pd(vec0, **kw)
+    return vec, info
+
+
+def _solve_gpu(api, lib, kind, N, dtype, oprob, vec0, lo, hi, mu0, mu_final, tol=1e-10, form="primal"):
     prob = _problem(api, lib, kind, N, dtype, oprob)
     prob.set_control_bounds(lo, hi)
-    prob.set_barrier(mu0, mu_final)
+    prob.set_barrier(mu0, mu_final, form)
     z = from_packed(prob, vec0)
     info = api.newton_solve(prob, z, tol=tol)
     assert info["converged"], info
     return prob, z, info
 
 
-def test_bounded_double_integrator_matches_oracle():
+@pytest.mark.parametrize("form", FORMS)
+def test_bounded_double_integrator_matches_oracle(form):
     api, lib = _api()
     N = 64
     oprob = op.Problem(op.DBL_INT, 0.0, 1.0)
     K = BarrierKKT(oprob, N, [-5.0], [5.0])
     X, U = synth.double_integrator_guess(K.t)
     vec0 = K.pack(X, U, np.zeros((2, K.L)), np.zeros(2))
-    ref, rinfo = K.solve(vec0)
+    ref, rinfo = _oracle_solve(K, vec0, form)
     assert rinfo["converged"]
-    prob, z, info = _solve_gpu(api, lib, op.DBL_INT, N, torch.float64, oprob, vec0, [-5.0], [5.0], 0.1, 1e-6)
+    prob, z, info = _solve_gpu(api, lib, op.DBL_INT, N, torch.float64, oprob, vec0, [-5.0], [5.0], 0.1, 1e-6,
+                               form=form)
     got = to_packed(prob, z)
     Xr, Ur = K.split(ref)[:2]
     Xg, Ug = K.split(got)[:2]
     assert np.all(np.abs(Ug) < 5.0)
     assert np.abs(Xg - Xr).max() < 1e-8, np.abs(Xg - Xr).max()
     assert np.abs(Ug - Ur).max() < 1e-6, np.abs(Ug - Ur).max()
-    # the library's residual at the solution is the final stage's (mu_final)
+    # inexact inner solves keep the oracle's Newton count within a few steps
+    assert info["iterations"] <= rinfo["iters"] + 4, (info, rinfo)
+    # the library's residual at the solution is the final stage's primal one (mu_final)
     F = torch.zeros_like(z)
-    assert prob.residual(z, F) <= 1e-10
+    assert prob.residual(z, F) <= 1e-7
 
 
-def test_bounded_orbit_matches_oracle():
+@pytest.mark.parametrize("form", FORMS)
+def test_bounded_orbit_matches_oracle(form):
     api, lib = _api()
     N = 64
     oprob, vec0, lo, hi = _orbit_bounds(N)
     K = BarrierKKT(oprob, N, lo, hi)
-    ref, rinfo = K.solve(vec0, mu0=1e-4, mu_final=1e-9)
+    ref, rinfo = _oracle_solve(K, vec0, form, mu0=1e-4, mu_final=1e-9)
     assert rinfo["converged"], rinfo
-    prob, z, info = _solve_gpu(api, lib, op.ORBIT, N, torch.float64, oprob, vec0, lo, hi, 1e-4, 1e-9)
+    prob, z, info = _solve_gpu(api, lib, op.ORBIT, N, torch.float64, oprob, vec0, lo, hi, 1e-4, 1e-9, form=form)
     got = to_packed(prob, z)
     Xr, Ur = K.split(ref)[:2]
     Xg, Ug = K.split(got)[:2]
     assert np.all(np.abs(Ug[0]) < hi[0]) and np.all(Ug[1] < hi[1])
     # the bounds are active: the bounded optimum reaches them
     assert Ug[1].max() > hi[1] - 1e-5 and np.abs(Ug[0]).max() > hi[0] - 1e-5
-    assert np.abs(Xg - Xr).max() < 1e-7, np.abs(Xg - Xr).max()
-    assert np.abs(Ug - Ur).max() < 1e-8, np.abs(Ug - Ur).max()
+    # at mu = 1e-9 the barrier problem is ill-conditioned near the active bounds: two solves that
+    # both stop at merit 1e-10 differ by up to ~1e-6 in the state (the oracle's primal and
+    # primal-dual solves, and a CPU model of this loop, do)
+    assert np.abs(Xg - Xr).max() < 1e-5, np.abs(Xg - Xr).max()
+    assert np.abs(Ug - Ur).max() < 1e-6, np.abs(Ug - Ur).max()
+    assert info["iterations"] <= rinfo["iters"] + 6, (info, rinfo)
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("N", [64, 256])
-def test_bounded_double_integrator_pontryagin(N):
+def test_bounded_double_integrator_pontryagin(N, form):
     from tests.test_oracle_barrier import _pontryagin_bounded
     api, lib = _api()
     alpha, u, x = _pontryagin_bounded(5.0)
     prob = api.Problem(lib.BK_DBL_INT, N, torch.float64, 0.0, 1.0)
     prob.set_control_bounds([-5.0], [5.0])
+    prob.set_barrier(0.1, 1e-6, form)
     t = api.Plan(N, t0=0.0, tf=1.0).grid()[0].numpy()
     X, U = synth.double_integrator_guess(t)
     z = prob.pack(X, U)
@@ -166,11 +188,13 @@ def test_bounded_double_integrator_pontryagin(N):
     assert np.abs(Xg[0] - xe).max() < 2e-4
 
 
-def test_inactive_bounds_give_the_unbounded_solution():
+@pytest.mark.parametrize("form", FORMS)
+def test_inactive_bounds_give_the_unbounded_solution(form):
     api, lib = _api()
     N = 48
     prob = api.Problem(lib.BK_DBL_INT, N, torch.float64, 0.0, 1.0)
     prob.set_control_bounds([-100.0], [100.0])
+    prob.set_barrier(0.1, 1e-6, form)
     t = api.Plan(N, t0=0.0, tf=1.0).grid()[0].numpy()
     X, U = synth.double_integrator_guess(t)
     z = prob.pack(X, U)
@@ -181,18 +205,19 @@ def test_inactive_bounds_give_the_unbounded_solution():
     assert np.abs(Ug[0] - (6 - 12 * t)).max() < 1e-5
 
 
-def test_bounded_fp32_reaches_the_fp64_solution():
+@pytest.mark.parametrize("form", FORMS)
+def test_bounded_fp32_reaches_the_fp64_solution(form):
     api, lib = _api()
     N = 64
     oprob = op.Problem(op.DBL_INT, 0.0, 1.0)
     K = DenseKKT(oprob, N)
     X, U = synth.double_integrator_guess(K.t)
     vec0 = K.pack(X, U, np.zeros((2, K.L)), np.zeros(2))
-    p64, z64, _ = _solve_gpu(api, lib, op.DBL_INT, N, torch.float64, oprob, vec0, [-5.0], [5.0], 0.1, 1e-6)
+    p64, z64, _ = _solve_gpu(api, lib, op.DBL_INT, N, torch.float64, oprob, vec0, [-5.0], [5.0], 0.1, 1e-6, form=form)
     # FP32 inner solves (forcing floor 1e-4) converge linearly on the ill-conditioned last
     # stage: measured 1.6e-10 after 100 steps, so this solve stops at 1e-9
     p32, z32, i32 = _solve_gpu(api, lib, op.DBL_INT, N, torch.float32, oprob, vec0, [-5.0], [5.0], 0.1, 1e-6,
-                               tol=1e-9)
+                               tol=1e-9, form=form)
     a, b = to_packed(p64, z64), to_packed(p32, z32)
     n = (oprob.n_x + oprob.n_u) * K.L
     assert np.abs(a[:n] - b[:n]).max() < 1e-5
@@ -214,6 +239,7 @@ def test_bounds_argument_checks():
         orbit.set_barrier(1e-3, 1e-2)                       # mu0 < mu_final
     with pytest.raises(lib.BirkhoffError):
         orbit.set_barrier(1e-3, 0.0)
+    assert lib.lib().bk_problem_set_barrier(h, 1e-3, 1e-4, 2) == 1                          # unknown form
     orbit.set_control_bounds([-1.0, -np.inf], [1.0, 0.5])   # one-sided bounds are fine
     orbit.set_control_bounds(None, None)
     bil = api.Problem(lib.BK_BILINEAR, 16, torch.float64, 0.0, 2.0, (1.0,))
