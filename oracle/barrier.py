@@ -42,6 +42,20 @@ primal-dual system linearises the complementarity products instead of 1 / (u - l
 what lets it take long steps near the bounds. solve_pd runs the same stages as solve with the
 full primal-dual Newton system (solved densely), the fraction-to-boundary rule on u and on
 z_l, z_h, and backtracking on the merit ||F||_W^2 + sum (C_l^2 + C_h^2) / w.
+
+Endpoint bounds (problem (P)'s e^L <= e <= e^U for the terminal conditions of the library's
+kinds, e_r = x_{idx_r}(t_f)): a terminal row r may hold bounds l_r < x < h_r instead of its
+equality. Their barrier psi_r(x) = -mu [log(x - l_r) + log(h_r - x)] (no quadrature weight: a
+point term) keeps the KKT form with nu_r as its multiplier: the gradient row of x_{idx_r}(t_f)
+keeps + nu_r, and row r of the terminal block becomes nu_r = psi_r'(x), written as
+
+    F_r = (psi_r'(x) - nu_r) / psi_r''(x)
+
+so that its Newton row is a (x-entry) and -1 / psi_r'' (nu-entry): the terminal selection E of
+the equality row, with a diagonal that the preconditioner's n_e x n_e Schur complement takes
+as it is (a = 1 - (psi' - nu) psi_3 / psi''^2 -> 1 at the solution, psi_3 the third
+derivative; K-tilde keeps E). It holds in both forms above; the fraction-to-boundary rule and
+the interior start cover x(t_f) too.
 """
 import numpy as np
 
@@ -54,11 +68,60 @@ class BarrierKKT(DenseKKT):
     """DenseKKT of a problem with control bounds lo, hi (length n_u, +-inf for none) and the
     barrier parameter mu (set before each stage)."""
 
-    def __init__(self, prob, N, lo, hi, Ba=None):
+    def __init__(self, prob, N, lo, hi, Ba=None, ebounds=None):
         super().__init__(prob, N, Ba)
         self.lo = np.asarray(lo, float).reshape(prob.n_u)
         self.hi = np.asarray(hi, float).reshape(prob.n_u)
         self.mu = 0.0
+        # endpoint bounds: {terminal row r: (l_r, h_r)}, the other rows keep their equality
+        self.ebounds = dict(ebounds or {})
+        for r, (a, b) in self.ebounds.items():
+            assert 0 <= r < prob.n_e and a < b
+
+    # ---- endpoint bounds ---------------------------------------------------------------------
+    def _psi(self, r, x):
+        """The first three derivatives of psi_r at x (terms of an infinite bound left out)."""
+        a, b = self.ebounds[r]
+        d1 = d2 = d3 = 0.0
+        if np.isfinite(a):
+            t = 1.0 / (x - a)
+            d1 -= t
+            d2 += t * t
+            d3 -= 2.0 * t ** 3
+        if np.isfinite(b):
+            t = 1.0 / (b - x)
+            d1 += t
+            d2 += t * t
+            d3 += 2.0 * t ** 3
+        return self.mu * d1, self.mu * d2, self.mu * d3
+
+    def _end_x(self, vec):
+        X = self.split(vec)[0]
+        return {r: X[self.prob.term_idx[r], -1] for r in self.ebounds}
+
+    def _end_residual(self, vec, F):
+        nu = self.split(vec)[3]
+        for r, x in self._end_x(vec).items():
+            g1, g2, _ = self._psi(r, x)
+            F[self.nz + self.nc + r] = (g1 - nu[r]) / g2
+        return F
+
+    def _end_matrix(self, vec, K):
+        nu = self.split(vec)[3]
+        for r, x in self._end_x(vec).items():
+            g1, g2, g3 = self._psi(r, x)
+            i = self.nz + self.nc + r
+            K[i, :] = 0.0
+            K[i, self.prob.term_idx[r] * self.L + self.L - 1] = 1.0 - (g1 - nu[r]) * g3 / (g2 * g2)
+            K[i, i] = -1.0 / g2
+        return K
+
+    def _end_precond(self, vec, Kt):
+        for r, x in self._end_x(vec).items():
+            _, g2, _ = self._psi(r, x)
+            i = self.nz + self.nc + r
+            Kt[i, i] = -1.0 / g2
+        return Kt
 
     def _bar_terms(self, U, s):
         """Per control and node: the barrier gradient and Hessian diagonal (zero where unbounded)."""
@@ -82,7 +145,7 @@ class BarrierKKT(DenseKKT):
         X, U, lam, nu = self.split(vec)
         g, _ = self._bar_terms(U, self.s_of(vec))
         F[p.n_x * L:self.nz] += g.ravel()
-        return F
+        return self._end_residual(vec, F)
 
     def matrix(self, vec):
         K = super().matrix(vec)
@@ -91,7 +154,7 @@ class BarrierKKT(DenseKKT):
         _, h = self._bar_terms(U, self.s_of(vec))
         i0 = p.n_x * L
         K[i0:self.nz, i0:self.nz] += np.diag(h.ravel())
-        return K
+        return self._end_matrix(vec, K)
 
     def precond_matrix(self, vec):
         """K-tilde with the barrier's Hessian diagonal added to its control block (which stays
@@ -102,7 +165,7 @@ class BarrierKKT(DenseKKT):
         _, h = self._bar_terms(U, self.s_of(vec))
         i0 = p.n_x * L
         Kt[i0:self.nz, i0:self.nz] += np.diag(h.ravel())
-        return Kt
+        return self._end_precond(vec, Kt)
 
     def max_step(self, vec, d):
         """Fraction-to-boundary: TAU times the largest alpha <= 1 / TAU keeping l < u + alpha du < h."""
@@ -119,6 +182,14 @@ class BarrierKKT(DenseKKT):
                 m = dU[q] > 0
                 if m.any():
                     amax = min(amax, float(np.min((self.hi[q] - U[q][m]) / dU[q][m])))
+        dX = self.split(d)[0]
+        for r, x in self._end_x(vec).items():
+            a, b = self.ebounds[r]
+            dx = dX[p.term_idx[r], -1]
+            if np.isfinite(a) and dx < 0:
+                amax = min(amax, (a - x) / dx)
+            if np.isfinite(b) and dx > 0:
+                amax = min(amax, (b - x) / dx)
         return min(1.0, TAU * amax)
 
     def interior(self, vec, margin=1e-3):
@@ -134,6 +205,14 @@ class BarrierKKT(DenseKKT):
                 U[q] = np.maximum(U[q], lo + margin * gap)
             if np.isfinite(hi):
                 U[q] = np.minimum(U[q], hi - margin * gap)
+        X = v[:p.n_x * L].reshape(p.n_x, L)
+        for r, (lo, hi) in self.ebounds.items():
+            gap = hi - lo if np.isfinite(lo) and np.isfinite(hi) else 1.0
+            i = p.term_idx[r]
+            if np.isfinite(lo):
+                X[i, -1] = max(X[i, -1], lo + margin * gap)
+            if np.isfinite(hi):
+                X[i, -1] = min(X[i, -1], hi - margin * gap)
         return v
 
     def newton_stage(self, vec, tol, max_iter=50, armijo=1e-4, max_backtrack=40):
@@ -223,7 +302,7 @@ class BarrierKKT(DenseKKT):
             if mh[q]:
                 G[q] += zh[q]
                 Ch[q] = (self.hi[q] - U[q]) * zh[q] - c
-        return F, Cl, Ch
+        return self._end_residual(vec, F), Cl, Ch
 
     def pd_merit(self, F, Cl, Ch):
         """sqrt(||F||_W^2 + sum (C_l^2 + C_h^2) / w): complementarity weighted like the gradient rows."""
@@ -238,7 +317,7 @@ class BarrierKKT(DenseKKT):
         U = vec[p.n_x * L:self.nz].reshape(p.n_u, L)
         ml, mh = self._bounded()
         A = np.zeros((n + 2 * m, n + 2 * m))
-        A[:n, :n] = DenseKKT.matrix(self, vec)
+        A[:n, :n] = self._end_matrix(vec, DenseKKT.matrix(self, vec))
         for q in range(p.n_u):
             rows_u = p.n_x * L + q * L + np.arange(L)      # control rows / columns of u_q
             il = n + q * L + np.arange(L)                    # z_l,q

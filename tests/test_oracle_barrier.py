@@ -15,6 +15,10 @@
   step by eliminating the multipliers (the form the library solves) equals the full solve, its
   residual on the central path is the primal one, and its solve reaches the primal solve's
   solution and multipliers in fewer Newton steps.
+- Endpoint bounds: both forms' Newton matrices are their residuals' Jacobians with a bounded
+  terminal row, and the double integrator with x(1) in [l, h] (v(1) = 0) reaches the closed form
+  x = p (3t^2 - 2t^3) with p the admissible value nearest 0 (energy 6 p^2): 0.8 for [0.8, 1.2]
+  and [0.8, inf), 0 for [-1, 2].
 """
 import numpy as np
 import pytest
@@ -233,3 +237,65 @@ def test_pd_and_primal_forms_share_the_solution():
     zl_p, zh_p = K.bound_multipliers(vp)
     assert np.max(np.abs(zl - zl_p)) < 1e-6 * np.max(zl_p) and np.max(np.abs(zh - zh_p)) < 1e-6 * np.max(zh_p)
     assert np.all(zl > 0) and np.all(zh > 0)
+
+
+# ---- endpoint bounds -------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", [op.DBL_INT, op.ORBIT])
+def test_endpoint_bound_matrices_are_residual_jacobians(kind):
+    """Both forms, with a bounded terminal row beside control bounds (the barrier's terms in the
+    terminal block included)."""
+    K, vec, zl, zh = _pd_point(kind)
+    if kind == op.DBL_INT:
+        K.ebounds = {0: (0.7, 1.3)}
+    else:
+        K.ebounds = {0: (1.2, np.inf)}
+    vec = K.interior(vec, margin=0.05)
+    A = K.matrix(vec)
+    J = _fd_jacobian(K, vec)
+    assert np.max(np.abs(A - J)) < 1e-5 * max(1.0, np.max(np.abs(A)))
+    p, L, n = K.prob, K.L, K.n
+    m = p.n_u * L
+
+    def full(x):
+        F, Cl, Ch = K.pd_residual(x[:n], x[n:n + m].reshape(p.n_u, L), x[n + m:].reshape(p.n_u, L))
+        return np.concatenate([F, Cl.ravel(), Ch.ravel()])
+    x0 = np.concatenate([vec, zl.ravel(), zh.ravel()])
+    h = 1e-6
+    Apd = K.pd_matrix(vec, zl, zh)
+    live = np.ones(n + 2 * m, bool)
+    for q in range(p.n_u):
+        if not np.isfinite(K.lo[q]):
+            live[n + q * L:n + (q + 1) * L] = False
+        if not np.isfinite(K.hi[q]):
+            live[n + m + q * L:n + m + (q + 1) * L] = False
+    cols = np.nonzero(live)[0]
+    Jpd = np.zeros((n + 2 * m, len(cols)))
+    for jj, j in enumerate(cols):
+        e = np.zeros(n + 2 * m)
+        e[j] = h
+        Jpd[:, jj] = (full(x0 + e) - full(x0 - e)) / (2 * h)
+    Al = Apd[np.ix_(live, cols)]
+    assert np.max(np.abs(Al - Jpd[live])) < 1e-5 * max(1.0, np.max(np.abs(Al)))
+
+
+@pytest.mark.parametrize("form", ["primal", "primal_dual"])
+@pytest.mark.parametrize("bounds,p_star", [((0.8, 1.2), 0.8), ((0.8, np.inf), 0.8), ((-1.0, 2.0), 0.0)])
+def test_endpoint_bounds_double_integrator_closed_form(bounds, p_star, form):
+    """x(1) in [l, h] and v(1) = 0 with cost int u^2 / 2: the energy of the cubic x = p (3t^2 - 2t^3)
+    is 6 p^2, so the optimum takes the admissible p nearest 0: p = 0.8 (bound active) or p = 0 for
+    [-1, 2] (inactive: the barrier moves it by about mu / 24)."""
+    prob = op.Problem(op.DBL_INT, 0.0, 1.0)
+    K = BarrierKKT(prob, 32, [-np.inf], [np.inf], ebounds={0: bounds})
+    X, U = synth.double_integrator_guess(K.t)
+    v0 = K.pack(X, U, np.zeros((2, K.L)), np.zeros(2))
+    if form == "primal":
+        vec, info = K.solve(v0)
+    else:
+        vec, _, _, info = K.solve_pd(v0)
+    assert info["converged"], info
+    Xs, Us = K.split(vec)[:2]
+    t = K.t
+    assert abs(Xs[0, -1] - p_star) < 1e-6
+    assert np.max(np.abs(Xs[0] - p_star * (3 * t**2 - 2 * t**3))) < 1e-6
+    assert np.max(np.abs(Us[0] - p_star * (6 - 12 * t))) < 1e-5
+    assert bounds[0] < Xs[0, -1] < bounds[1]
