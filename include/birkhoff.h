@@ -281,6 +281,33 @@ bk_status bk_problem_set_params(bk_problem* prob, const double* params, int npar
 bk_status bk_problem_set_control_bounds(bk_problem* prob, const double* lo, const double* hi,
                                         int n);
 
+/* Endpoint bounds x_{idx_r}(t_f) >= lo[r] or <= hi[r] in place of terminal condition r (problem
+ * (P)'s e^L <= e(x(t_0), x(t_f)) <= e^U, Eq. probPbold, for terminal conditions of the form
+ * e_r = x_{idx_r}(t_f) - target_r, one bound per row; the paper states them but gives no
+ * method). A bounded row takes the barrier psi_r(x) = -mu log(x - lo_r) (or -mu log(hi_r - x)),
+ * a point term without quadrature weight, with nu_r as its multiplier: the gradient row of
+ * x_{idx_r}(t_f) keeps + nu_r, and row r of the terminal block becomes the complementarity
+ * condition (x - lo_r) nu_r + mu = 0 (or (hi_r - x) nu_r - mu = 0), whose Newton row
+ * a dx + c dnu the preconditioner's terminal Schur complement absorbs as it is
+ * (diag(a) E Q - diag(c)). Rows are the kind's terminal conditions in order (BK_DBL_INT: p, v;
+ * BK_ORBIT: r, v_r, v_theta).
+ *   lo, hi  host arrays of n entries; a row with lo = -inf and hi = +inf keeps its equality, a
+ *           row with one finite bound (the other the matching infinity) is bounded; two finite
+ *           bounds return BK_ERR_UNSUPPORTED (with one multiplier per row the two-sided barrier
+ *           row stalled in the FP64 reference computation on the orbit transfer when its start
+ *           lay at the bound away from the optimum)
+ *   n       the problem's n_e, or 0 to restore every equality (lo, hi may be NULL then)
+ * The barrier schedule is bk_problem_set_barrier's (both forms treat these rows alike);
+ * newton_solve starts nu_r on the central path of mu0 and keeps its sign (negative for a lower
+ * bound, positive for an upper one) by the fraction-to-boundary rule. The rows' Newton
+ * coefficients are taken at each linearisation (bk_linearize reads x(t_f) and nu from z_lin,
+ * synchronously, and returns BK_ERR_ARG if x(t_f) is not inside its bound). Host only; must not
+ * overlap work queued on the problem; the problem must be linearised again before kkt_apply or
+ * precond_apply. BK_ERR_ARG for bad sizes or bounds; BK_ERR_UNSUPPORTED for BK_BILINEAR and
+ * BK_ORBIT_MT. */
+bk_status bk_problem_set_terminal_bounds(bk_problem* prob, const double* lo, const double* hi,
+                                         int n);
+
 /* Form in which newton_solve treats the barrier problem of a bounded problem (Nocedal and
  * Wright, Numerical Optimization, Sections 19.2 and 19.6). */
 typedef enum {
@@ -467,8 +494,9 @@ size_t bk_newton_workspace_bytes(const bk_problem* prob, int restart);
  * tail slot (it must start > 0; trials with s <= 0 are rejected), the residual carries the time
  * gradient, and the inner tolerance defaults to 1e-12 instead of the forcing term. Start it from
  * bk_min_time_seed.
- * Control bounds (bk_problem_set_control_bounds): the controls in z_inout are first moved 1e-3
- * of the bound gap inside the bounds, then each barrier stage runs the steps above, with every
+ * Control and endpoint bounds (bk_problem_set_control_bounds, bk_problem_set_terminal_bounds):
+ * the bounded values in z_inout are first moved 1e-3 of the bound gap inside the bounds, then
+ * each barrier stage runs the steps above, with every
  * step length starting at the fraction-to-boundary bound min(1, 0.995 max{alpha : lo < u +
  * alpha du < hi}) so that the iterates stay strictly inside, and halved on backtracking (the
  * quadratic model is dominated by the barrier's curvature); info counts the steps of all

@@ -47,15 +47,21 @@ Endpoint bounds (problem (P)'s e^L <= e <= e^U for the terminal conditions of th
 kinds, e_r = x_{idx_r}(t_f)): a terminal row r may hold bounds l_r < x < h_r instead of its
 equality. Their barrier psi_r(x) = -mu [log(x - l_r) + log(h_r - x)] (no quadrature weight: a
 point term) keeps the KKT form with nu_r as its multiplier: the gradient row of x_{idx_r}(t_f)
-keeps + nu_r, and row r of the terminal block becomes nu_r = psi_r'(x), written as
+keeps + nu_r, and row r of the terminal block becomes nu_r = psi_r'(x) in complementarity form,
 
-    F_r = (psi_r'(x) - nu_r) / psi_r''(x)
+    F_r = c(x) nu_r - mu m(x),   c = (x - l)(h - x), m = 2x - l - h   (two-sided),
+                                  c = x - l, m = -1;  c = h - x, m = 1   (one-sided),
 
-so that its Newton row is a (x-entry) and -1 / psi_r'' (nu-entry): the terminal selection E of
-the equality row, with a diagonal that the preconditioner's n_e x n_e Schur complement takes
-as it is (a = 1 - (psi' - nu) psi_3 / psi''^2 -> 1 at the solution, psi_3 the third
-derivative; K-tilde keeps E). It holds in both forms above; the fraction-to-boundary rule and
-the interior start cover x(t_f) too.
+its Newton row a dx + e dnu with a = c'(x) nu - mu m'(x), e = c(x). (Dividing nu = psi' by
+psi'' instead would have a spurious root at the bound itself, which the fraction-to-boundary
+steps approach: seen in this oracle.) The library's preconditioner keeps the row as it is: its
+n_e x n_e Schur complement becomes diag(a) E Q - diag(e). The stages start nu_r on the central
+path (nu_r = psi_r'(x)); the fraction-to-boundary rule covers x(t_f), and for a one-sided row
+also the sign of nu_r (negative for a lower bound, positive for an upper one). Endpoint rows
+read the same in both forms above. Two-sided rows are defined here (and pinned on the double
+integrator), but on the orbit transfer with a start at the bound away from the optimum
+(r(t_f) in [1.3, 1.45] from the spiral that ends at 1.5) this single-multiplier row stalled,
+so the library takes one bound per row.
 """
 import numpy as np
 
@@ -79,49 +85,62 @@ class BarrierKKT(DenseKKT):
             assert 0 <= r < prob.n_e and a < b
 
     # ---- endpoint bounds ---------------------------------------------------------------------
-    def _psi(self, r, x):
-        """The first three derivatives of psi_r at x (terms of an infinite bound left out)."""
+    def _cm(self, r, x):
+        """c(x), c'(x), m(x), m'(x) of endpoint row r (module docstring)."""
         a, b = self.ebounds[r]
-        d1 = d2 = d3 = 0.0
+        if np.isfinite(a) and np.isfinite(b):
+            return (x - a) * (b - x), a + b - 2.0 * x, 2.0 * x - a - b, 2.0
         if np.isfinite(a):
-            t = 1.0 / (x - a)
-            d1 -= t
-            d2 += t * t
-            d3 -= 2.0 * t ** 3
-        if np.isfinite(b):
-            t = 1.0 / (b - x)
-            d1 += t
-            d2 += t * t
-            d3 += 2.0 * t ** 3
-        return self.mu * d1, self.mu * d2, self.mu * d3
+            return x - a, 1.0, -1.0, 0.0
+        return b - x, -1.0, 1.0, 0.0
 
     def _end_x(self, vec):
         X = self.split(vec)[0]
         return {r: X[self.prob.term_idx[r], -1] for r in self.ebounds}
 
-    def _end_residual(self, vec, F):
+    def _end_coef(self, vec):
+        """{r: (F_r, a_r, e_r)} at vec."""
         nu = self.split(vec)[3]
+        out = {}
         for r, x in self._end_x(vec).items():
-            g1, g2, _ = self._psi(r, x)
-            F[self.nz + self.nc + r] = (g1 - nu[r]) / g2
+            c, dc, m, dm = self._cm(r, x)
+            out[r] = (c * nu[r] - self.mu * m, dc * nu[r] - self.mu * dm, c)
+        return out
+
+    def _end_residual(self, vec, F):
+        for r, (f, _, _) in self._end_coef(vec).items():
+            F[self.nz + self.nc + r] = f
         return F
 
     def _end_matrix(self, vec, K):
-        nu = self.split(vec)[3]
-        for r, x in self._end_x(vec).items():
-            g1, g2, g3 = self._psi(r, x)
+        for r, (_, a, e) in self._end_coef(vec).items():
             i = self.nz + self.nc + r
             K[i, :] = 0.0
-            K[i, self.prob.term_idx[r] * self.L + self.L - 1] = 1.0 - (g1 - nu[r]) * g3 / (g2 * g2)
-            K[i, i] = -1.0 / g2
+            K[i, self.prob.term_idx[r] * self.L + self.L - 1] = a
+            K[i, i] = e
         return K
 
     def _end_precond(self, vec, Kt):
-        for r, x in self._end_x(vec).items():
-            _, g2, _ = self._psi(r, x)
+        """The preconditioner takes the endpoint rows as they are (its E rows scaled by a)."""
+        for r, (_, a, e) in self._end_coef(vec).items():
             i = self.nz + self.nc + r
-            Kt[i, i] = -1.0 / g2
+            Kt[i, self.prob.term_idx[r] * self.L + self.L - 1] = a
+            Kt[i, i] = e
         return Kt
+
+    def end_init(self, vec):
+        """vec with nu_r of every endpoint row on the central path, nu_r = psi_r'(x)."""
+        v = np.array(vec, float)
+        nu = v[self.nz + self.nc:self.nz + self.nc + self.prob.n_e]
+        for r, x in self._end_x(v).items():
+            a, b = self.ebounds[r]
+            g = 0.0
+            if np.isfinite(a):
+                g -= 1.0 / (x - a)
+            if np.isfinite(b):
+                g += 1.0 / (b - x)
+            nu[r] = self.mu * g
+        return v
 
     def _bar_terms(self, U, s):
         """Per control and node: the barrier gradient and Hessian diagonal (zero where unbounded)."""
@@ -182,7 +201,8 @@ class BarrierKKT(DenseKKT):
                 m = dU[q] > 0
                 if m.any():
                     amax = min(amax, float(np.min((self.hi[q] - U[q][m]) / dU[q][m])))
-        dX = self.split(d)[0]
+        dX, dnu = self.split(d)[0], self.split(d)[3]
+        nu = self.split(vec)[3]
         for r, x in self._end_x(vec).items():
             a, b = self.ebounds[r]
             dx = dX[p.term_idx[r], -1]
@@ -190,6 +210,12 @@ class BarrierKKT(DenseKKT):
                 amax = min(amax, (a - x) / dx)
             if np.isfinite(b) and dx > 0:
                 amax = min(amax, (b - x) / dx)
+            # one-sided row: nu keeps its sign (negative below a lower bound's barrier, positive
+            # for an upper one)
+            if np.isfinite(a) and not np.isfinite(b) and dnu[r] > 0:
+                amax = min(amax, -nu[r] / dnu[r])
+            if np.isfinite(b) and not np.isfinite(a) and dnu[r] < 0:
+                amax = min(amax, -nu[r] / dnu[r])
         return min(1.0, TAU * amax)
 
     def interior(self, vec, margin=1e-3):
@@ -243,6 +269,8 @@ class BarrierKKT(DenseKKT):
         """The barrier outer loop (module docstring). Returns (vec, info)."""
         vec = self.interior(vec0)
         mu = mu0
+        self.mu = mu
+        vec = self.end_init(vec)
         total = 0
         stages = []
         while True:
@@ -384,6 +412,7 @@ class BarrierKKT(DenseKKT):
         vec = self.interior(vec0)
         mu = mu0
         self.mu = mu
+        vec = self.end_init(vec)
         zl, zh = self.pd_init(vec)
         total = 0
         stages = []

@@ -27,7 +27,7 @@ EXPORTS = ["bk_last_error", "bk_version", "bk_launch_count", "bk_plan_create", "
            "bk_plan_dense_test_timeout", "birkhoff_apply_b", "birkhoff_apply_b_T",
            "bk_set_f64_precond", "bk_problem_precond_dtype", "bk_set_krylov_graphs", "bk_set_krylov_wait_limit", "birkhoff_apply_batch",
            "bk_problem_create",
-           "bk_problem_destroy", "bk_problem_set_params", "bk_problem_set_control_bounds", "bk_problem_set_barrier", "bk_problem_device_bytes", "bk_problem_info", "bk_linearize", "kkt_apply",
+           "bk_problem_destroy", "bk_problem_set_params", "bk_problem_set_control_bounds", "bk_problem_set_terminal_bounds", "bk_problem_set_barrier", "bk_problem_device_bytes", "bk_problem_info", "bk_linearize", "kkt_apply",
            "precond_apply", "bk_krylov_workspace_bytes", "krylov_solve",
            "bk_newton_workspace_bytes", "newton_solve", "bk_kkt_residual", "bk_min_time_seed",
            "bk_abi_struct_size"]
@@ -108,6 +108,7 @@ def lib():
         "bk_problem_destroy": (None, [vp]),
         "bk_problem_set_params": (c_int, [vp, ctypes.POINTER(dbl), c_int, dbl, dbl]),
         "bk_problem_set_control_bounds": (c_int, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), c_int]),
+        "bk_problem_set_terminal_bounds": (c_int, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), c_int]),
         "bk_problem_set_barrier": (c_int, [vp, dbl, dbl, c_int]),
         "bk_problem_device_bytes": (ctypes.c_size_t, [vp]),
         "bk_problem_info": (c_int, [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int),

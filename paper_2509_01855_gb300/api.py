@@ -232,6 +232,21 @@ class Problem:
         L.check(L.lib().bk_problem_set_control_bounds(self._h, (ctypes.c_double * n)(*lo),
                                                       (ctypes.c_double * n)(*hi), n))
 
+    def set_terminal_bounds(self, lo=None, hi=None):
+        """Bounds lo[r] <= x_{idx_r}(t_f) <= hi[r] in place of terminal condition r (sequences of
+        length n_e; a row whose bounds are both infinite keeps its equality; both None removes
+        them). Solved by the same barrier stages as the control bounds."""
+        if lo is None and hi is None:
+            L.check(L.lib().bk_problem_set_terminal_bounds(self._h, None, None, 0))
+            return
+        n = self.n_e
+        lo = [-float("inf")] * n if lo is None else [float(x) for x in lo]
+        hi = [float("inf")] * n if hi is None else [float(x) for x in hi]
+        if len(lo) != n or len(hi) != n:
+            raise ValueError(f"terminal bounds need {n} entries each")
+        L.check(L.lib().bk_problem_set_terminal_bounds(self._h, (ctypes.c_double * n)(*lo),
+                                                       (ctypes.c_double * n)(*hi), n))
+
     def set_barrier(self, mu0=0.1, mu_final=1e-6, form="primal"):
         """Barrier schedule of a bounded solve: stages mu0, mu0/10, ... down to mu_final, in the
         "primal" or "primal_dual" form. The residual and operator calls use mu_final (primal)."""

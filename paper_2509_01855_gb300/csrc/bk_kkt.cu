@@ -799,11 +799,6 @@ __global__ void k_state_post(const T* __restrict__ chi, const T* __restrict__ Bt
   }
 }
 
-struct TermSpec {
-  int n_e;
-  int idx[NEM];
-  double val[NEM];
-};
 
 // KKT product: out = [H dz + G^T dy ; G dz], with Bt = s B^a (J dz), Mu = s B^aT dlambda.
 // Free final time (part != null): the gradient rows add ds d g / ds = -(ds / s) J^T mu, and each
@@ -897,7 +892,8 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
     for (int m = 0; m < NX; ++m) oL[m * P + k] = dz[m] - (sdev ? s * Bt[m * P + k] : Bt[m * P + k]);
     if (k == L - 1) {
 #pragma unroll
-      for (int r = 0; r < NEM; ++r) oNu[r] = r < ts.n_e ? dX[ts.idx[r] * P + k] : T(0);
+      for (int r = 0; r < NEM; ++r)
+        oNu[r] = r < ts.n_e ? T(ts.ea[r]) * dX[ts.idx[r] * P + k] + T(ts.ec[r]) * dNu[r] : T(0);
       for (int r = NEM; r < 32; ++r) oNu[r] = T(0);
     }
   }
@@ -1083,7 +1079,7 @@ __global__ void k_pre_nu(const T* __restrict__ q, const T* __restrict__ rnu, con
                          int64_t L, TermSpec ts, T* __restrict__ ynu) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   T rhs[NEM];
-  for (int r = 0; r < ts.n_e; ++r) rhs[r] = q[ts.idx[r] * P + (L - 1)] - rnu[r];
+  for (int r = 0; r < ts.n_e; ++r) rhs[r] = T(ts.ea[r]) * q[ts.idx[r] * P + (L - 1)] - rnu[r];
   for (int r = 0; r < 32; ++r) {
     T a = T(0);
     if (r < ts.n_e)
@@ -1238,7 +1234,12 @@ __global__ void k_resid_post(const double* __restrict__ z, const double* __restr
         double xr = 0.0;   // x[ts.idx[r]] by selects: x stays in registers
 #pragma unroll
         for (int m = 0; m < NX; ++m) xr = ts.idx[r] == m ? x[m] : xr;
-        const double e = r < ts.n_e ? xr - ts.val[r] : 0.0;
+        double e = r < ts.n_e ? xr - ts.val[r] : 0.0;
+        if (r < ts.n_e && ts.eb[r]) {   // endpoint bound: c(x) nu_r - mu m(x)
+          double c, dc, m;
+          end_cm(ts, r, xr, &c, &dc, &m);
+          e = c * nu[r] - ts.mu * m;
+        }
         F[(NV + NX) * P + r] = e;
         acc += e * e;
       }
@@ -1300,13 +1301,6 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int n, double
 // ---------------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------------
-static TermSpec term_spec(const Problem* pr) {
-  TermSpec t;
-  memset(&t, 0, sizeof(t));
-  t.n_e = pr->n_e;
-  for (int r = 0; r < pr->n_e; ++r) { t.idx[r] = pr->term_idx[r]; t.val[r] = pr->term_val[r]; }
-  return t;
-}
 
 template <int KIND> struct KindNX { static constexpr int nx = Dyn<KIND>::nx, nu = Dyn<KIND>::nu; };
 
@@ -1406,7 +1400,7 @@ __global__ void k_lin_bar(const double* __restrict__ z, const double* __restrict
 // The barrier diagonal of one precision's data, null when the problem has no active bounds.
 template <typename T>
 static const T* bar_hbar(const Problem* pr, const OpData& d) {
-  return pr->has_bounds && pr->bar_mu > 0.0 ? (const T*)d.hbar : nullptr;
+  return pr->has_ubounds && pr->bar_mu > 0.0 ? (const T*)d.hbar : nullptr;
 }
 
 // Segment maps and scan levels from the node factors N_k (level data of the sweeps).
@@ -1487,6 +1481,13 @@ static bk_status lin_schur_finish(Problem* pr, OpData& d, cudaStream_t st) {
   BK_TRY_CUDA(cudaStreamSynchronize(st));
   const T* hq = reinterpret_cast<const T*>(pr->red_host + 256);
   for (int i = 0; i < ne * ne; ++i) S[i] = (double)hq[i];
+  // endpoint bounds: rows ea_r (E x)_r + ec_r nu_r = r_r give (diag(ea) E Q - diag(ec)) nu =
+  // diag(ea) E x0 - r (k_pre_nu scales its E x0 by ea)
+  for (int r = 0; r < ne; ++r) {
+    if (!(pr->has_ebounds && pr->term_bnd[r])) continue;
+    for (int c = 0; c < ne; ++c) S[r * ne + c] *= pr->term_ea[r];
+    S[r * ne + r] -= pr->term_ec[r];
+  }
   // invert S (n_e <= 4) by Gauss-Jordan with partial pivoting in FP64
   std::vector<double> A(S), Inv(ne * ne, 0.0);
   for (int i = 0; i < ne; ++i) Inv[i * ne + i] = 1.0;
@@ -1514,6 +1515,42 @@ static bk_status lin_schur_finish(Problem* pr, OpData& d, cudaStream_t st) {
 template <typename T, int KIND>
 static bk_status lin_border(Problem* pr, OpData& d, cudaStream_t st);
 
+// x_{idx_r}(t_f) and nu_r of a KKT vector (one thread)
+__global__ void k_term_vals(const double* __restrict__ z, int64_t P, int64_t L, int64_t nu_off, TermSpec ts,
+                            double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int r = 0; r < ts.n_e; ++r) {
+    out[r] = z[ts.idx[r] * P + (L - 1)];
+    out[NEM + r] = z[nu_off + r];
+  }
+}
+
+// Endpoint bounds: the Newton rows ea_r dx + ec_r dnu_r of the barrier rows at z_lin,
+// ea = c'(x) nu, ec = c(x) (synchronous).
+static bk_status lin_end_rows(Problem* pr, const double* z, cudaStream_t st) {
+  const TermSpec ts = term_spec(pr);
+  double* dv = pr->red + 1800;
+  double* hv = pr->red_host + 320;
+  k_term_vals<<<1, 32, 0, st>>>(z, pr->P, pr->L, (int64_t)(2 * pr->n_x + pr->n_u) * pr->P, ts, dv);
+  BK_CHECK_LAUNCH();
+  BK_TRY_CUDA(cudaMemcpyAsync(hv, dv, sizeof(double) * 2 * NEM, cudaMemcpyDeviceToHost, st));
+  BK_TRY_CUDA(cudaStreamSynchronize(st));
+  for (int r = 0; r < pr->n_e; ++r) {
+    pr->term_ea[r] = 1.0;
+    pr->term_ec[r] = 0.0;
+    if (!ts.eb[r]) continue;
+    double c, dc, m;
+    end_cm(ts, r, hv[r], &c, &dc, &m);
+    if (!(c > 0.0) || !isfinite(c)) {
+      set_error("terminal row %d: x(t_f) = %g is not inside its bound", r, hv[r]);
+      return BK_ERR_ARG;
+    }
+    pr->term_ea[r] = dc * hv[NEM + r];
+    pr->term_ec[r] = c;
+  }
+  return BK_OK;
+}
+
 // mu (nullable): s B^aT lambda at this z, known to the caller (e.g. from the residual that
 // accepted the step); it is copied instead of recomputed.
 // A BK_F32 problem builds its preconditioner data in FP32 only; the FP64 side keeps the
@@ -1523,6 +1560,10 @@ static bk_status linearize_kind(Problem* pr, const double* z, const double* mu, 
   constexpr int NX = Dyn<KIND>::nx, NU = Dyn<KIND>::nu;
   const int64_t P = pr->P;
   if (!pr->linearized || pr->free_time) keep = LIN_FULL;
+  if (pr->has_ebounds) {   // the terminal Schur complement carries the barrier rows' diagonal
+    keep = LIN_FULL;
+    BK_TRY(lin_end_rows(pr, z, st));
+  }
   if (mu)
     BK_TRY_CUDA(cudaMemcpyAsync(pr->d64.mu, mu, sizeof(double) * NX * P, cudaMemcpyDeviceToDevice, st));
   else
@@ -1541,7 +1582,7 @@ static bk_status linearize_kind(Problem* pr, const double* z, const double* mu, 
       BK_CHECK_LAUNCH();
     }
   }
-  if (pr->has_bounds && pr->bar_mu > 0.0) {
+  if (pr->has_ubounds && pr->bar_mu > 0.0) {
     const BarSpec b = bar_spec(pr);
     k_lin_bar<double, NU><<<nblk(P), 256, 0, st>>>(z, pr->d64.plan->w64, pr->s, P, pr->L, NX, b, (double*)pr->d64.hbar);
     BK_CHECK_LAUNCH();
@@ -2037,8 +2078,8 @@ bk_status bk_problem_set_control_bounds(bk_problem* prob, const double* lo, cons
   BK_ARG(prob != nullptr, "problem is NULL");
   bk::Problem* p = reinterpret_cast<bk::Problem*>(prob);
   if (n == 0) {
-    p->has_bounds = false;
-    p->bar_mu = 0.0;
+    p->has_ubounds = false;
+    p->has_bounds = p->has_ebounds;
     return BK_OK;
   }
   BK_ARG(lo != nullptr && hi != nullptr, "bounds are NULL");
@@ -2071,8 +2112,49 @@ bk_status bk_problem_set_control_bounds(bk_problem* prob, const double* lo, cons
     p->ulo[q] = q < n ? lo[q] : -INFINITY;
     p->uhi[q] = q < n ? hi[q] : INFINITY;
   }
+  p->has_ubounds = true;
   p->has_bounds = true;
   p->bar_mu = p->bar_mu_final;
+  return BK_OK;
+}
+
+bk_status bk_problem_set_terminal_bounds(bk_problem* prob, const double* lo, const double* hi, int n) {
+  BK_ARG(prob != nullptr, "problem is NULL");
+  bk::Problem* p = reinterpret_cast<bk::Problem*>(prob);
+  if (n == 0) {
+    p->has_ebounds = false;
+    p->has_bounds = p->has_ubounds;
+    return BK_OK;
+  }
+  BK_ARG(lo != nullptr && hi != nullptr, "bounds are NULL");
+  BK_ARG(n == p->n_e, "n must be 0 or the problem's terminal-condition count %d (got %d)", p->n_e, n);
+  if (!p->has_cost || p->free_time) {
+    bk::set_error("endpoint bounds need a fixed-final-time problem with a cost (BK_DBL_INT, BK_ORBIT)");
+    return BK_ERR_UNSUPPORTED;
+  }
+  int any = 0;
+  for (int r = 0; r < n; ++r) {
+    BK_ARG(!isnan(lo[r]) && !isnan(hi[r]), "terminal row %d: NaN bound", r);
+    const bool eq = lo[r] == -INFINITY && hi[r] == INFINITY;
+    BK_ARG(eq || (isfinite(lo[r]) && hi[r] == INFINITY) || (lo[r] == -INFINITY && isfinite(hi[r])) ||
+               (isfinite(lo[r]) && isfinite(hi[r])),
+           "terminal row %d: bounds must be finite or the matching infinity (got %g, %g)", r, lo[r], hi[r]);
+    if (isfinite(lo[r]) && isfinite(hi[r])) {
+      bk::set_error("terminal row %d: two-sided endpoint bounds are not supported (one bound per row)", r);
+      return BK_ERR_UNSUPPORTED;
+    }
+    any += eq ? 0 : 1;
+  }
+  for (int r = 0; r < bk::NEM; ++r) {
+    const bool b = r < n && !(lo[r] == -INFINITY && hi[r] == INFINITY);
+    p->term_bnd[r] = b ? 1 : 0;
+    p->term_lo[r] = b ? lo[r] : 0.0;
+    p->term_hi[r] = b ? hi[r] : 0.0;
+  }
+  p->has_ebounds = any > 0;
+  p->has_bounds = p->has_ubounds || p->has_ebounds;
+  p->bar_mu = p->bar_mu_final;
+  p->linearized = false;
   return BK_OK;
 }
 
@@ -2085,7 +2167,7 @@ bk_status bk_problem_set_barrier(bk_problem* prob, double mu0, double mu_final, 
   p->bar_mu0 = mu0;
   p->bar_mu_final = mu_final;
   p->bar_form = form;
-  if (p->has_bounds) p->bar_mu = mu_final;
+  p->bar_mu = mu_final;
   return BK_OK;
 }
 

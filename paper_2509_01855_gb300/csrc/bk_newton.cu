@@ -92,9 +92,23 @@ __global__ void k_sumsq(const double* __restrict__ x, int64_t n, double* __restr
 
 constexpr double kTau = 0.995;   // fraction-to-boundary
 
-// Controls moved at least margin * (hi - lo) inside two-sided bounds (margin for one-sided ones).
-__global__ void k_interior(double* __restrict__ z, int64_t P, int64_t L, int nx, BarSpec b, double margin) {
+// Controls (and endpoint-bounded x(t_f)) moved at least margin * (hi - lo) inside two-sided
+// bounds (margin for one-sided ones); an endpoint row's multiplier nu_r put on the central path
+// of ts.mu, nu_r = psi_r'(x) (-mu / (x - elo) or mu / (ehi - x)).
+__global__ void k_interior(double* __restrict__ z, int64_t P, int64_t L, int nx, BarSpec b, TermSpec ts,
+                           int64_t nu_off, double margin) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k == L - 1) {
+#pragma unroll
+      for (int r = 0; r < NEM; ++r) {
+        if (r >= ts.n_e || !ts.eb[r]) continue;
+        const bool lo = isfinite(ts.elo[r]);
+        double x = z[ts.idx[r] * P + k];
+        x = lo ? fmax(x, ts.elo[r] + margin) : fmin(x, ts.ehi[r] - margin);
+        z[ts.idx[r] * P + k] = x;
+        z[nu_off + r] = lo ? -ts.mu / (x - ts.elo[r]) : ts.mu / (ts.ehi[r] - x);
+      }
+    }
 #pragma unroll
     for (int q = 0; q < NUM; ++q) {
       const bool lo = b.has_lo[q], hi = b.has_hi[q];
@@ -180,10 +194,25 @@ __global__ void k_pd_dz(const double* __restrict__ z, const double* __restrict__
 // multipliers z + alpha dz > 0 at its nodes.
 __global__ void k_max_step(const double* __restrict__ z, const double* __restrict__ d, const double* __restrict__ zb,
                            const double* __restrict__ dzb, int64_t P, int64_t L, int nx, int nu, BarSpec b,
-                           double* __restrict__ partial) {
+                           TermSpec ts, int64_t nu_off, double* __restrict__ partial) {
   __shared__ double red[32];
   double a = 1.0 / kTau;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k == L - 1) {   // endpoint-bounded x(t_f) and the sign of its multiplier
+#pragma unroll
+      for (int r = 0; r < NEM; ++r) {
+        if (r >= ts.n_e || !ts.eb[r]) continue;
+        const double x = z[ts.idx[r] * P + k], dx = d[ts.idx[r] * P + k];
+        const double nu = z[nu_off + r], dnu = d[nu_off + r];
+        if (isfinite(ts.elo[r])) {   // lower bound: x > elo, nu < 0
+          if (dx < 0.0) a = fmin(a, (ts.elo[r] - x) / dx);
+          if (dnu > 0.0) a = fmin(a, -nu / dnu);
+        } else {                     // upper bound: x < ehi, nu > 0
+          if (dx > 0.0) a = fmin(a, (ts.ehi[r] - x) / dx);
+          if (dnu < 0.0) a = fmin(a, -nu / dnu);
+        }
+      }
+    }
 #pragma unroll
     for (int q = 0; q < NUM; ++q) {
       if (q >= nu) break;
@@ -257,7 +286,8 @@ static bk_status norm2(Problem* pr, const double* x, int64_t n, double* out, cud
 static bk_status max_step(Problem* pr, const double* z, const double* d, const double* zb, const double* dzb,
                           double* out, cudaStream_t st) {
   const int nb = (int)((pr->L + 255) / 256 < 592 ? (pr->L + 255) / 256 : 592);
-  k_max_step<<<nb, 256, 0, st>>>(z, d, zb, dzb, pr->P, pr->L, pr->n_x, pr->n_u, bar_spec(pr), pr->red);
+  k_max_step<<<nb, 256, 0, st>>>(z, d, zb, dzb, pr->P, pr->L, pr->n_x, pr->n_u, bar_spec(pr), term_spec(pr),
+                                 (int64_t)(2 * pr->n_x + pr->n_u) * pr->P, pr->red);
   BK_CHECK_LAUNCH();
   k_min_block<<<1, 256, 0, st>>>(pr->red, nb, pr->red + 1024);
   BK_CHECK_LAUNCH();
@@ -342,7 +372,7 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     pr->s = hs[0];
   }
   const bool bar = pr->has_bounds;
-  const bool pd = bar && pr->bar_form == BK_BARRIER_PRIMAL_DUAL;
+  const bool pd = pr->has_ubounds && pr->bar_form == BK_BARRIER_PRIMAL_DUAL;
   BarrierReset reset{pr};
   double mu = bar ? pr->bar_mu0 : 0.0;
   // bound multipliers (primal-dual form): current, trial and step, 2 n_u P each
@@ -353,7 +383,8 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
   if (bar) {
     pr->bar_mu = mu;
     pr->bar_z = nullptr;
-    k_interior<<<g1(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->n_x, bar_spec(pr), 1e-3);
+    k_interior<<<g1(pr->L), 256, 0, st>>>(z, pr->P, pr->L, pr->n_x, bar_spec(pr), term_spec(pr),
+                                          (int64_t)(2 * pr->n_x + pr->n_u) * pr->P, 1e-3);
     BK_CHECK_LAUNCH();
   }
   if (pd) {

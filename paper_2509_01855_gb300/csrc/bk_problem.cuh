@@ -170,6 +170,34 @@ template <> struct Dyn<BK_ORBIT_MT> {
 // ---------------------------------------------------------------------------------------------
 // Problem
 // ---------------------------------------------------------------------------------------------
+// Terminal conditions as a kernel argument (static indices only): e_r = x_{idx_r}(t_f) - val_r,
+// or, for a row with an endpoint bound (eb_r; one of elo_r, ehi_r finite), the barrier row of
+// psi_r(x) = -mu log(x - elo_r) (or -mu log(ehi_r - x)) with nu_r as its multiplier, in
+// complementarity form F_r = c(x) nu_r - mu m(x): c = x - elo, m = -1 (lower) or c = ehi - x,
+// m = 1 (upper); its Newton row at the linearisation is ea_r dx + ec_r dnu_r.
+struct TermSpec {
+  int n_e;
+  int idx[NEM];
+  double val[NEM];
+  int eb[NEM];
+  double elo[NEM], ehi[NEM];
+  double mu;
+  double ea[NEM], ec[NEM];
+};
+
+// c(x), c'(x), m(x) of an endpoint row (m' = 0 for one-sided rows).
+__host__ __device__ inline void end_cm(const TermSpec& ts, int r, double x, double* c, double* dc, double* m) {
+  if (isfinite(ts.elo[r])) {
+    *c = x - ts.elo[r];
+    *dc = 1.0;
+    *m = -1.0;
+  } else {
+    *c = ts.ehi[r] - x;
+    *dc = -1.0;
+    *m = 1.0;
+  }
+}
+
 // Control bounds and barrier parameter as a kernel argument (static indices only).
 struct BarSpec {
   double mu;          // 0: no barrier terms
@@ -264,10 +292,16 @@ struct Problem {
   double* sred = nullptr;      // reduction scratch of the free-time terms (FP64, 2048)
   void* gcache = nullptr;      // captured GMRES cycle graphs (bk_krylov.cu), keyed by their pointers
   // control bounds lo_q <= u_q <= hi_q (+-inf: none) by a logarithmic barrier on the quadrature
-  // (problem (P)'s path constraints in their simplest form); bar_mu is the current barrier
-  // parameter (0 outside newton_solve's barrier stages), mu0 / mu_final its schedule
-  bool has_bounds = false;
+  // (problem (P)'s path constraints in their simplest form) and endpoint bounds on terminal rows
+  // (its e^L <= e <= e^U); bar_mu is the barrier parameter the kernels use (mu_final outside
+  // newton_solve's stages), mu0 / mu_final its schedule
+  bool has_bounds = false;     // either kind below
+  bool has_ubounds = false;
   double ulo[NUM] = {0, 0}, uhi[NUM] = {0, 0};
+  bool has_ebounds = false;
+  int term_bnd[NEM] = {0, 0, 0, 0};
+  double term_lo[NEM] = {0, 0, 0, 0}, term_hi[NEM] = {0, 0, 0, 0};
+  double term_ea[NEM] = {1, 1, 1, 1}, term_ec[NEM] = {0, 0, 0, 0};   // Newton rows at the linearisation
   double bar_mu = 0.0, bar_mu0 = 0.1, bar_mu_final = 1e-6;
   int bar_form = BK_BARRIER_PRIMAL;  // newton_solve's form of the barrier problem
   double* bar_buf = nullptr;   // newton_solve's bound multipliers: z, trial z, dz (2 n_u P each)
@@ -291,15 +325,33 @@ struct Problem {
 inline BarSpec bar_spec(const Problem* pr) {
   BarSpec b;
   memset(&b, 0, sizeof(b));
-  b.mu = pr->has_bounds ? pr->bar_mu : 0.0;
-  b.z = pr->has_bounds ? pr->bar_z : nullptr;
+  b.mu = pr->has_ubounds ? pr->bar_mu : 0.0;
+  b.z = pr->has_ubounds ? pr->bar_z : nullptr;
   for (int q = 0; q < NUM; ++q) {
     b.lo[q] = pr->ulo[q];
     b.hi[q] = pr->uhi[q];
-    b.has_lo[q] = q < pr->n_u && isfinite(pr->ulo[q]) ? 1 : 0;
-    b.has_hi[q] = q < pr->n_u && isfinite(pr->uhi[q]) ? 1 : 0;
+    b.has_lo[q] = pr->has_ubounds && q < pr->n_u && isfinite(pr->ulo[q]) ? 1 : 0;
+    b.has_hi[q] = pr->has_ubounds && q < pr->n_u && isfinite(pr->uhi[q]) ? 1 : 0;
   }
   return b;
+}
+
+// Terminal conditions of a problem, with its endpoint bounds and their Newton rows.
+inline TermSpec term_spec(const Problem* pr) {
+  TermSpec t;
+  memset(&t, 0, sizeof(t));
+  t.n_e = pr->n_e;
+  t.mu = pr->has_ebounds ? pr->bar_mu : 0.0;
+  for (int r = 0; r < pr->n_e; ++r) {
+    t.idx[r] = pr->term_idx[r];
+    t.val[r] = pr->term_val[r];
+    t.eb[r] = pr->has_ebounds && pr->term_bnd[r] ? 1 : 0;
+    t.elo[r] = pr->term_lo[r];
+    t.ehi[r] = pr->term_hi[r];
+    t.ea[r] = t.eb[r] ? pr->term_ea[r] : 1.0;
+    t.ec[r] = t.eb[r] ? pr->term_ec[r] : 0.0;
+  }
+  return t;
 }
 
 // mu (nullable): s B^aT lambda at z_lin, already known to the caller (FP64, n_x * P); when

@@ -9,7 +9,12 @@
 - On the double integrator the solution is the one Pontryagin's principle gives (computed in
   tests/test_oracle_barrier.py, independently of both solvers), bounds far away give the
   unbounded closed form, and FP32 inner solves reach the FP64 solution.
-- Argument checks of bk_problem_set_control_bounds and bk_problem_set_barrier.
+- Endpoint bounds on terminal rows (one bound per row), beside control bounds or alone: the
+  operators against the oracle at a fixed barrier parameter, the double integrator against its
+  closed form (x(1) >= 0.8: p = 0.8; x(1) <= 1.2: p = 0) at N = 64 and 2^14, and the orbit
+  transfer against the oracle's solve of the same form.
+- Argument checks of bk_problem_set_control_bounds, bk_problem_set_terminal_bounds and
+  bk_problem_set_barrier.
 """
 import numpy as np
 import pytest
@@ -246,3 +251,136 @@ def test_bounds_argument_checks():
     with pytest.raises(lib.BirkhoffError) as e:
         bil.set_control_bounds([-1.0], [1.0])
     assert e.value.status == 7                              # BK_ERR_UNSUPPORTED
+
+
+# ---- endpoint bounds ------------------------------------------------------------------------
+def _ebounds_arrays(ne, eb):
+    lo = [-np.inf] * ne
+    hi = [np.inf] * ne
+    for r, (a, b) in eb.items():
+        lo[r], hi[r] = a, b
+    return lo, hi
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("kind,N", [(op.DBL_INT, 32), (op.DBL_INT, 100), (op.ORBIT, 64), (op.ORBIT, 45)])
+def test_endpoint_barrier_operators_match_oracle(kind, N, dtype):
+    """Residual, KKT product and preconditioner with endpoint-bounded terminal rows beside
+    control bounds, at a fixed barrier parameter."""
+    api, lib = _api()
+    g = synth.rng("bounds-end-ops", kind, N)
+    if kind == op.DBL_INT:
+        oprob = op.Problem(op.DBL_INT, 0.0, 1.0)
+        lo, hi, mu, eb = [-4.0], [5.0], 0.3, {0: (0.7, np.inf)}
+        K = BarrierKKT(oprob, N, lo, hi, ebounds=eb)
+        X, U = synth.double_integrator_guess(K.t)
+        U = U + g.standard_normal(U.shape)
+        X = X + 0.1 * g.standard_normal(X.shape)
+    else:
+        oprob, _, lo, hi = _orbit_bounds()
+        mu, eb = 1e-6, {0: (1.2, np.inf), 2: (-np.inf, 0.9)}
+        K = BarrierKKT(oprob, N, lo, hi, ebounds=eb)
+        X, U = synth.orbit_guess(K.t, 1.5, 20.0)
+        U = U + 1e-3 * g.standard_normal(U.shape)
+        X = X + 0.01 * g.standard_normal(X.shape)
+    K.mu = mu
+    vec = K.pack(X, U, 0.01 * g.standard_normal((oprob.n_x, K.L)), 0.01 * g.standard_normal(oprob.n_e))
+    vec = K.interior(vec, margin=0.05)
+    prob = _problem(api, lib, kind, N, dtype, oprob)
+    prob.set_control_bounds(lo, hi)
+    prob.set_terminal_bounds(*_ebounds_arrays(oprob.n_e, eb))
+    prob.set_barrier(mu, mu)
+    z = from_packed(prob, vec)
+    F = torch.zeros_like(z)
+    wn = prob.residual(z, F)
+    Fo = K.residual(vec)
+    assert rel(to_packed(prob, F), Fo) < 1e-12
+    assert abs(wn - K.weighted_norm(Fo)) < 1e-12 * K.weighted_norm(Fo)
+    prob.linearize(z)
+    d = g.standard_normal(K.n)
+    x = from_packed(prob, d, dtype)
+    out = torch.zeros_like(x)
+    api.kkt_apply(prob, lib.BK_OP_KKT, x, out)
+    assert rel(to_packed(prob, out), K.matrix(vec) @ d) < (1e-12 if dtype == torch.float64 else 1e-5)
+    api.precond_apply(prob, lib.BK_OP_KKT, x, out)
+    ref = np.linalg.solve(K.precond_matrix(vec), d)
+    assert rel(to_packed(prob, out), ref) < (1e-10 if dtype == torch.float64 else 1e-3)
+    # removing the endpoint bounds restores the equality rows
+    prob.set_terminal_bounds(None, None)
+    prob.residual(z, F)
+    K.ebounds = {}
+    assert rel(to_packed(prob, F), K.residual(vec)) < 1e-12
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("eb,p_star", [({0: (0.8, np.inf)}, 0.8), ({0: (-np.inf, 1.2)}, 0.0)])
+@pytest.mark.parametrize("N", [64, 1 << 14])
+def test_endpoint_bounds_double_integrator_closed_form(N, eb, p_star, form):
+    """x(1) >= 0.8 (active) or <= 1.2 (inactive), v(1) = 0: x = p (3t^2 - 2t^3) with p = 0.8 or 0
+    (the energy 6 p^2 of the cubic takes the admissible p nearest 0)."""
+    api, lib = _api()
+    prob = api.Problem(lib.BK_DBL_INT, N, torch.float64, 0.0, 1.0)
+    prob.set_terminal_bounds(*_ebounds_arrays(2, eb))
+    prob.set_barrier(0.1, 1e-8, form)
+    t = api.Plan(N, t0=0.0, tf=1.0).grid()[0].numpy()
+    X, U = synth.double_integrator_guess(t)
+    z = prob.pack(X, U)
+    info = api.newton_solve(prob, z)
+    assert info["converged"], info
+    Xg, Ug = [a.cpu().numpy() for a in prob.split(z)[:2]]
+    assert np.abs(Xg[0] - p_star * (3 * t**2 - 2 * t**3)).max() < 1e-6
+    assert np.abs(Ug[0] - p_star * (6 - 12 * t)).max() < 1e-5
+    a, b = eb[0]
+    assert a < Xg[0, -1] < b
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("case", ["r_lower", "r_upper", "r_lower_thrust", "vt_upper_thrust"])
+def test_endpoint_bounds_orbit_matches_oracle(case, form):
+    api, lib = _api()
+    N = 64
+    oprob, vec0, lo, hi = _orbit_bounds(N)
+    inf = np.inf
+    eb, lo_, hi_ = {"r_lower": ({0: (1.55, inf)}, [-inf] * 2, [inf] * 2),
+                    "r_upper": ({0: (-inf, 1.45)}, [-inf] * 2, [inf] * 2),
+                    "r_lower_thrust": ({0: (1.45, inf)}, lo, hi),
+                    "vt_upper_thrust": ({2: (-inf, 0.81)}, lo, hi)}[case]
+    K = BarrierKKT(oprob, N, lo_, hi_, ebounds=eb)
+    ref, rinfo = _oracle_solve(K, vec0, form, mu0=1e-4, mu_final=1e-9)
+    assert rinfo["converged"], rinfo
+    prob = _problem(api, lib, op.ORBIT, N, torch.float64, oprob)
+    if np.isfinite(lo_[0]):
+        prob.set_control_bounds(lo_, hi_)
+    prob.set_terminal_bounds(*_ebounds_arrays(3, eb))
+    prob.set_barrier(1e-4, 1e-9, form)
+    z = from_packed(prob, vec0)
+    info = api.newton_solve(prob, z)
+    assert info["converged"], info
+    got = to_packed(prob, z)
+    Xr, Ur = K.split(ref)[:2]
+    Xg, Ug = K.split(got)[:2]
+    for r, (a, b) in eb.items():
+        x = Xg[oprob.term_idx[r], -1]
+        assert a < x < b
+    assert np.abs(Xg - Xr).max() < 1e-5, np.abs(Xg - Xr).max()
+    assert np.abs(Ug - Ur).max() < 1e-6, np.abs(Ug - Ur).max()
+
+
+def test_terminal_bounds_argument_checks():
+    api, lib = _api()
+    orbit = api.Problem(lib.BK_ORBIT, 16, torch.float64, 0.0, 20.0, (0.01, 1.5))
+    with pytest.raises(ValueError):
+        orbit.set_terminal_bounds([1.0], [2.0])                       # n_e = 3
+    with pytest.raises(lib.BirkhoffError) as e:
+        orbit.set_terminal_bounds([1.2, -np.inf, -np.inf], [1.8, np.inf, np.inf])   # two-sided
+    assert e.value.status == 7
+    with pytest.raises(lib.BirkhoffError):
+        orbit.set_terminal_bounds([np.nan, -np.inf, -np.inf], [np.inf] * 3)
+    with pytest.raises(lib.BirkhoffError):
+        orbit.set_terminal_bounds([np.inf, -np.inf, -np.inf], [np.inf] * 3)
+    orbit.set_terminal_bounds([1.2, -np.inf, -np.inf], [np.inf] * 3)
+    orbit.set_terminal_bounds(None, None)
+    mt = api.Problem(lib.BK_ORBIT_MT, 16, torch.float64, 0.0, 20.0, (0.05, 6.0))
+    with pytest.raises(lib.BirkhoffError) as e:
+        mt.set_terminal_bounds([5.0, -np.inf, -np.inf], [np.inf] * 3)
+    assert e.value.status == 7
