@@ -547,9 +547,9 @@ def orbit_bounds(fr=0.9, ft=0.95):
 def bounded_table(lgs=(10, 14, 17, 20)):
     """The orbit transfer of the headline solve with its thrust bounded (orbit_bounds), solved by
     newton_solve's barrier stages mu = 1e-4 .. 1e-9 in the primal and in the primal-dual form.
-    Per N and form: Newton iterations over all stages,
-    Krylov iterations, the solve's device time (CUDA events, FP64) and how close the solution
-    comes to the bounds."""
+    Per N and form: Newton iterations over all stages, Krylov iterations, the solve's device time
+    (CUDA events, FP64) and how close the solution comes to the bounds. Then the same transfer
+    with the endpoint bound r(t_f) >= 1.55 in place of r(t_f) = 1.5 (no thrust bounds)."""
     import torch
     from paper_2509_01855_gb300 import api
     lo, hi = orbit_bounds()
@@ -572,6 +572,24 @@ def bounded_table(lgs=(10, 14, 17, 20)):
                          "backtracks": info["backtracks"], "converged": bool(info["converged"]),
                          "residual": info["residual"], "ms": round(e0.elapsed_time(e1), 3),
                          "gap_ur": hi[0] - Ub[0].abs().max().item(), "gap_ut": hi[1] - Ub[1].max().item()}
+        prob.close()
+    # endpoint bound instead of the thrust bounds: r(t_f) >= 1.55 in place of r(t_f) = 1.5
+    for lg in lgs:
+        N = 1 << lg
+        prob, z = make_orbit(N, torch.float64)
+        prob.set_terminal_bounds([1.55, -float("inf"), -float("inf")], [float("inf")] * 3)
+        prob.set_barrier(mu0, mu_final)
+        ws = api.newton_workspace(prob)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        info = api.newton_solve(prob, z, workspace=ws, raise_on_fail=False)
+        e1.record()
+        torch.cuda.synchronize()
+        rows["%d_endpoint_r_ge_1.55" % lg] = {
+            "newton_its": info["iterations"], "krylov_its": info["krylov_iterations"],
+            "converged": bool(info["converged"]), "ms": round(e0.elapsed_time(e1), 3),
+            "r_tf": prob.split(z)[0][0, -1].item()}
         prob.close()
     return rows
 
