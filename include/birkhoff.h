@@ -459,8 +459,10 @@ typedef struct {
                          ||.||_W (the system scaled by D = diag(w^-1/2 on gradient rows, w^1/2
                          on constraint rows, 1 on the tail), preconditioner applied to D^-1 v),
                          so that every inexact step with relative residual < 1 descends
-                         ||F||_W; 0 (default): the 2-norm. BK_ORBIT_MT then also takes the
-                         forcing term instead of its default 1e-12                           */
+                         ||F||_W; 0 (default): the 2-norm, except for problems with endpoint
+                         bounds or in the primal-dual barrier form, which always take the
+                         merit's norm. BK_ORBIT_MT then also takes the forcing term instead
+                         of its default 1e-12                                                */
 } bk_newton_opts;
 
 typedef struct {

@@ -442,7 +442,11 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     // bound is far larger than the merit's C / sqrt(w): a tolerance relative to it alone gave
     // steps that were no descent directions (line-search failures on the bounded orbit transfer
     // at N = 2^20 on the GPU, and from N = 64 in a CPU model of this loop).
-    const bool weighted = o.weighted_inner != 0 || pd;
+    // Endpoint bounds: GMRES in the merit's norm too. The barrier rows sit at the last node, whose
+    // gradient row the merit divides by w_N ~ 1/N^2; with 2-norm inner solves the bounded orbit
+    // transfer (r(t_f) >= 1.55) stopped on line-search failures from N = 2^10 on GB300, in the
+    // merit's norm it took 20 Newton steps at N = 2^6, 2^10 and 2^14.
+    const bool weighted = o.weighted_inner != 0 || pd || pr->has_ebounds;
     if (pd) {
       k_pd_rhs<<<g1(pr->L), 256, 0, st>>>(z, zb, pr->d64.plan->w64, pr->s, pr->P, pr->L, pr->n_x, pr->n_u,
                                           bar_spec(pr), rhs);

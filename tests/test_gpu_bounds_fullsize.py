@@ -8,6 +8,8 @@
   mu log(5 - u) sits delta = mu / (a - 5 + delta) <= sqrt(mu) inside the bound, so with
   mu_final = 1e-6 the controls agree to 2e-3 (twice sqrt(mu_final), worst next to the kinks) and
   the states, integrals of the controls, to 1e-4.
+- Orbit transfer with the endpoint bound r(t_f) >= 1.55 at N = 2^10, 2^14, 2^20: the oracle's
+  Newton count and r(t_f) at N = 64.
 - Orbit transfer with bounded thrust (the bench's bounded workload) at N = 2^20: the primal and
   the primal-dual form, two different Newton iterations, reach the same barrier solution; the
   controls stay strictly inside the bounds and reach them; the Newton counts are those at
@@ -88,3 +90,34 @@ def test_bounded_orbit_full_size_forms_agree():
     assert np.abs(Up - Ud).max() < 1e-6, np.abs(Up - Ud).max()
     for form in ("primal", "primal_dual"):
         assert abs(its[form, 20] - its[form, 10]) <= 6, its
+
+
+def test_endpoint_bounded_orbit_mesh_independent():
+    """r(t_f) >= 1.55 in place of r(t_f) = 1.5 (no thrust bounds): the bound is active, the solves
+    at N = 2^10, 2^14 and 2^20 take the Newton count of the oracle's solve at N = 64 (20, the same
+    at every N in the oracle) within two steps, and r(t_f) sits the barrier's offset
+    mu_final / |nu| above the bound, the value the oracle's solve gives at N = 64, to 1e-9."""
+    from oracle import problems as op
+    from oracle.barrier import BarrierKKT
+    api, lib = _api()
+    inf = float("inf")
+    oprob = op.Problem(op.ORBIT, 0.0, 20.0, (0.01, 1.5))
+    K = BarrierKKT(oprob, 64, [-inf] * 2, [inf] * 2, ebounds={0: (1.55, inf)})
+    X, U = synth.orbit_guess(K.t, 1.5, 20.0)
+    ref, rinfo = K.solve(K.pack(X, U, np.zeros((4, K.L)), np.zeros(3)), mu0=1e-4, mu_final=1e-9)
+    assert rinfo["converged"]
+    r_ref = K.split(ref)[0][0, -1]
+    for lg in (10, 14, 20):
+        N = 1 << lg
+        prob = api.Problem(lib.BK_ORBIT, N, torch.float64, 0.0, 20.0, (0.01, 1.5))
+        t = api.Plan(N, t0=0.0, tf=20.0).grid()[0].numpy()
+        X, U = synth.orbit_guess(t, 1.5, 20.0)
+        z = prob.pack(X, U)
+        prob.set_terminal_bounds([1.55, -inf, -inf], [inf] * 3)
+        prob.set_barrier(1e-4, 1e-9)
+        info = api.newton_solve(prob, z)
+        assert info["converged"], (lg, info)
+        assert abs(info["iterations"] - rinfo["iters"]) <= 2, (lg, info, rinfo)
+        r = prob.split(z)[0][0, -1].item()
+        assert 1.55 < r and abs(r - r_ref) < 1e-9, (lg, r, r_ref)
+        prob.close()
