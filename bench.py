@@ -573,6 +573,21 @@ def bounded_table(lgs=(10, 14, 17, 20)):
                          "residual": info["residual"], "ms": round(e0.elapsed_time(e1), 3),
                          "gap_ur": hi[0] - Ub[0].abs().max().item(), "gap_ut": hi[1] - Ub[1].max().item()}
         prob.close()
+    # FP32 Krylov inner solves with the FP64 Newton residual (primal form), to 1e-9
+    prob, z = make_orbit(1 << max(lgs), torch.float32)
+    prob.set_control_bounds(lo, hi)
+    prob.set_barrier(mu0, mu_final)
+    ws = api.newton_workspace(prob)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    info = api.newton_solve(prob, z, tol=1e-9, workspace=ws, raise_on_fail=False)
+    e1.record()
+    torch.cuda.synchronize()
+    rows["%d_primal_f32inner_tol1e-9" % max(lgs)] = {
+        "newton_its": info["iterations"], "krylov_its": info["krylov_iterations"],
+        "converged": bool(info["converged"]), "residual": info["residual"], "ms": round(e0.elapsed_time(e1), 3)}
+    prob.close()
     # endpoint bound instead of the thrust bounds: r(t_f) >= 1.55 in place of r(t_f) = 1.5
     for lg in lgs:
         N = 1 << lg

@@ -384,3 +384,21 @@ def test_terminal_bounds_argument_checks():
     with pytest.raises(lib.BirkhoffError) as e:
         mt.set_terminal_bounds([5.0, -np.inf, -np.inf], [np.inf] * 3)
     assert e.value.status == 7
+
+
+@pytest.mark.parametrize("N", [64, 1 << 14])
+def test_endpoint_bounds_fp32_inner(N):
+    """FP32 Krylov inner solves with the FP64 Newton residual reach the closed form of
+    x(1) >= 0.8 (p = 0.8) too (stopping at 1e-9, as the FP32 control-bound solve does)."""
+    api, lib = _api()
+    prob = api.Problem(lib.BK_DBL_INT, N, torch.float32, 0.0, 1.0)
+    prob.set_terminal_bounds([0.8, -np.inf], [np.inf, np.inf])
+    prob.set_barrier(0.1, 1e-8)
+    t = api.Plan(N, t0=0.0, tf=1.0).grid()[0].numpy()
+    X, U = synth.double_integrator_guess(t)
+    z = prob.pack(X, U)
+    info = api.newton_solve(prob, z, tol=1e-9)
+    assert info["converged"], info
+    Xg, Ug = [a.cpu().numpy() for a in prob.split(z)[:2]]
+    assert np.abs(Xg[0] - 0.8 * (3 * t**2 - 2 * t**3)).max() < 1e-6
+    assert 0.8 < Xg[0, -1]
