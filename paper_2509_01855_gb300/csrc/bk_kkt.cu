@@ -61,20 +61,24 @@ constexpr int FT_NB = 608;
 // ---------------------------------------------------------------------------------------------
 // Linearisation kernels (FP64 arithmetic, results stored in T)
 // ---------------------------------------------------------------------------------------------
-// Node factors in the compute type Tc: FP64 for FP64 problems; FP32 for FP32 problems, whose
-// preconditioner works to FP32 accuracy anyway (the level products stay FP64).
+// Node deviation in the compute type Tc (FP64 for FP64 problems; FP32 for FP32 problems, whose
+// preconditioner works to FP32 accuracy anyway; the level products stay FP64):
+// D = h J K = (I - h J)^{-1} h J, since K = (I - h J)^{-1} commutes with h J. One LU
+// factorisation of I - h J with partial pivoting and the n_x columns of h J as right-hand
+// sides: about 120 operations per node at n_x = 4, where inverting I - h J by Gauss-Jordan and
+// multiplying by h J took about 240 (the kernel is bound by the FP64 pipe). Solving for D
+// directly keeps its relative accuracy when h J is small (forming K - I would cancel).
 template <typename Tc, int KIND, int NX>
-__device__ void node_factors(const Tc* x, const Tc* u, Tc h, Tc* K, Tc* Nm, Tc pa) {
+__device__ void node_deviation(const Tc* x, const Tc* u, Tc h, Tc* D, Tc pa) {
   Tc Jx[NXM * NXM], Ju[NXM * NUM];
   Dyn<KIND>::template jac<Tc>(x, u, Jx, Ju, pa);
-  // A = I - h J; K = A^{-1} by Gauss-Jordan with partial pivoting
-  Tc A[NX * NX], Inv[NX * NX];
+  Tc A[NX * NX], B[NX * NX], ip[NX];
 #pragma unroll
   for (int r = 0; r < NX; ++r)
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
-      A[r * NX + c] = (r == c ? Tc(1) : Tc(0)) - h * Jx[r * NX + c];
-      Inv[r * NX + c] = r == c ? Tc(1) : Tc(0);
+      B[r * NX + c] = h * Jx[r * NX + c];
+      A[r * NX + c] = (r == c ? Tc(1) : Tc(0)) - B[r * NX + c];
     }
 #pragma unroll
   for (int c = 0; c < NX; ++c) {
@@ -84,49 +88,48 @@ __device__ void node_factors(const Tc* x, const Tc* u, Tc h, Tc* K, Tc* Nm, Tc p
     for (int r = c + 1; r < NX; ++r)
       if (fabs((Tc)A[r * NX + c]) > best) { best = fabs((Tc)A[r * NX + c]); piv = r; }
     // row swap by selects over the candidate rows: every index stays a compile-time constant,
-    // so A and Inv live in registers (indexing by the run-time pivot put them in local memory)
+    // so A and B live in registers (indexing by the run-time pivot put them in local memory)
 #pragma unroll
     for (int r = c + 1; r < NX; ++r) {
       const bool sw = r == piv;
 #pragma unroll
       for (int q = 0; q < NX; ++q) {
-        const Tc a = A[c * NX + q], b = A[r * NX + q];
-        A[c * NX + q] = sw ? b : a;
-        A[r * NX + q] = sw ? a : b;
-        const Tc ia = Inv[c * NX + q], ib = Inv[r * NX + q];
-        Inv[c * NX + q] = sw ? ib : ia;
-        Inv[r * NX + q] = sw ? ia : ib;
+        if (q >= c) {
+          const Tc a = A[c * NX + q], b = A[r * NX + q];
+          A[c * NX + q] = sw ? b : a;
+          A[r * NX + q] = sw ? a : b;
+        }
+        const Tc ba = B[c * NX + q], bb = B[r * NX + q];
+        B[c * NX + q] = sw ? bb : ba;
+        B[r * NX + q] = sw ? ba : bb;
       }
     }
-    const Tc ip = Tc(1) / A[c * NX + c];
+    ip[c] = Tc(1) / A[c * NX + c];
 #pragma unroll
-    for (int q = 0; q < NX; ++q) { A[c * NX + q] *= ip; Inv[c * NX + q] *= ip; }
+    for (int r = c + 1; r < NX; ++r) {
+      const Tc f = A[r * NX + c] * ip[c];
 #pragma unroll
-    for (int r = 0; r < NX; ++r) {
-      if (r == c) continue;
-      const Tc f = A[r * NX + c];
+      for (int q = c + 1; q < NX; ++q) A[r * NX + q] -= f * A[c * NX + q];
 #pragma unroll
-      for (int q = 0; q < NX; ++q) { A[r * NX + q] -= f * A[c * NX + q]; Inv[r * NX + q] -= f * Inv[c * NX + q]; }
+      for (int q = 0; q < NX; ++q) B[r * NX + q] -= f * B[c * NX + q];
     }
   }
+  // back substitution, the n_x right-hand sides together
 #pragma unroll
-  for (int i = 0; i < NX * NX; ++i) K[i] = Inv[i];
-  // N = 2 h J K
+  for (int c = NX - 1; c >= 0; --c)
 #pragma unroll
-  for (int r = 0; r < NX; ++r)
+    for (int q = 0; q < NX; ++q) {
+      Tc a = B[c * NX + q];
 #pragma unroll
-    for (int c = 0; c < NX; ++c) {
-      Tc a = Tc(0);
-#pragma unroll
-      for (int q = 0; q < NX; ++q) a += Jx[r * NX + q] * Inv[q * NX + c];
-      Nm[r * NX + c] = Tc(2) * h * a;
+      for (int k = c + 1; k < NX; ++k) a -= A[c * NX + k] * D[k * NX + q];
+      D[c * NX + q] = a * ip[c];
     }
 }
 
 // Per node the sweeps need K = (I - h J)^{-1} and N = 2 h J K. Since K (I - h J) = I, h J K = K - I,
-// so both follow from the deviation D = h J K: K = I + D, N = 2 D. Only D is stored (formed as
-// h J K, not as K - I, which would cancel when h J is small), which halves the sweeps' node
-// factor traffic and, with K v = v + D v and N v = 2 D v, their FP64 products.
+// so both follow from the deviation D = h J K: K = I + D, N = 2 D. Only D is stored (solved for
+// directly by node_deviation), which halves the sweeps' node factor traffic and, with
+// K v = v + D v and N v = 2 D v, their FP64 products.
 template <typename T, int KIND, int NX, int NU>
 __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, const double* __restrict__ w,
                             double s, T* __restrict__ Dn, T* __restrict__ xu, double pa) {
@@ -136,10 +139,10 @@ __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, 
     for (int m = 0; m < NX; ++m) x[m] = (T)z[m * P + k];
 #pragma unroll
     for (int q = 0; q < NU; ++q) u[q] = (T)z[(NX + q) * P + k];
-    T K[NX * NX], Nm[NX * NX];
-    node_factors<T, KIND, NX>(x, u, (T)(0.5 * s * w[k]), K, Nm, (T)pa);
+    T D[NX * NX];
+    node_deviation<T, KIND, NX>(x, u, (T)(0.5 * s * w[k]), D, (T)pa);
 #pragma unroll
-    for (int c = 0; c < NX * NX; ++c) Dn[il_index<Seg<T>::v>(k, c, NX * NX)] = T(0.5) * Nm[c];   // D = N / 2 (exact)
+    for (int c = 0; c < NX * NX; ++c) Dn[il_index<Seg<T>::v>(k, c, NX * NX)] = D[c];
 #pragma unroll
     for (int m = 0; m < NX + NU; ++m) xu[m * P + k] = (T)z[m * P + k];
   }
@@ -157,36 +160,46 @@ __global__ void k_lin_nodes(const double* __restrict__ z, int64_t P, int64_t L, 
 // level's item count rounded up to 32.
 __device__ __forceinline__ int64_t il32(int64_t i, int c, int NC) { return (((i >> 5) * NC + c) << 5) + (i & 31); }
 
-// Deviation of a product: (I + A)(I + B) = I + C with C = A + B + A B (n_x x n_x, row-major).
+// Deviation of a product: (I + A)(I + B) = I + C with C = A + B + A B (n_x x n_x, row-major),
+// each entry one FMA chain started from A + B (n_x^2 (n_x + 1) operations).
 template <int NX, typename Tm = double>
 __device__ __forceinline__ void dev_mul(const Tm* A, const Tm* B, Tm* C) {
 #pragma unroll
   for (int r = 0; r < NX; ++r)
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
-      Tm a = 0;
+      Tm a = A[r * NX + c] + B[r * NX + c];
 #pragma unroll
-      for (int q = 0; q < NX; ++q) a += A[r * NX + q] * B[q * NX + c];
-      C[r * NX + c] = (A[r * NX + c] + B[r * NX + c]) + a;
+      for (int q = 0; q < NX; ++q) a = fma(A[r * NX + q], B[q * NX + c], a);
+      C[r * NX + c] = a;
     }
 }
 
 // Level-0 maps: prod over the segment's nodes of (I + N_k) = (I + 2 D_k) as a deviation, one
-// thread per segment.
+// thread per segment: A <- (I + 2 D)(I + A) - I = A + 2 (D + D A), from A = 2 D of its first node.
 template <typename T, int NX>
 __global__ void k_lin_seg(const T* __restrict__ Dn, int64_t L, int nseg, T* __restrict__ A0) {
   const int seg = blockIdx.x * blockDim.x + threadIdx.x;
   if (seg >= nseg) return;
-  T A[NX * NX], M[NX * NX], R[NX * NX];
-#pragma unroll
-  for (int i = 0; i < NX * NX; ++i) A[i] = T(0);
   constexpr int SEG = Seg<T>::v;
-  for (int i = 0; i < SEG; ++i) {
-    const int64_t k = (int64_t)seg * SEG + i;
+  T A[NX * NX], D[NX * NX], R[NX * NX];
+  const int64_t k0 = (int64_t)seg * SEG;
+#pragma unroll
+  for (int c = 0; c < NX * NX; ++c) A[c] = T(2) * Dn[il_index<Seg<T>::v>(k0, c, NX * NX)];
+  for (int i = 1; i < SEG; ++i) {
+    const int64_t k = k0 + i;
     if (k >= L) break;
 #pragma unroll
-    for (int c = 0; c < NX * NX; ++c) M[c] = T(2) * Dn[il_index<Seg<T>::v>(k, c, NX * NX)];
-    dev_mul<NX, T>(M, A, R);
+    for (int c = 0; c < NX * NX; ++c) D[c] = Dn[il_index<Seg<T>::v>(k, c, NX * NX)];
+#pragma unroll
+    for (int r = 0; r < NX; ++r)
+#pragma unroll
+      for (int c = 0; c < NX; ++c) {
+        T a = D[r * NX + c];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) a = fma(D[r * NX + q], A[q * NX + c], a);
+        R[r * NX + c] = fma(T(2), a, A[r * NX + c]);
+      }
 #pragma unroll
     for (int c = 0; c < NX * NX; ++c) A[c] = R[c];
   }
