@@ -790,10 +790,12 @@ __global__ void k_jvp(const T* __restrict__ xu, const T* __restrict__ dX, const 
     for (int m = 0; m < NX; ++m) {
       T a = ds ? dss * fx[m] : T(0);
 #pragma unroll
-      for (int p = 0; p < NX; ++p) a += Jx[m * NX + p] * dX[p * P + k];
+      for (int p = 0; p < NX; ++p)
+        if (Dyn<KIND>::jx_nz(m, p)) a += Jx[m * NX + p] * dX[p * P + k];
       if (dU) {
 #pragma unroll
-        for (int q = 0; q < NU; ++q) a += Ju[m * NU + q] * dU[q * P + k];
+        for (int q = 0; q < NU; ++q)
+          if (Dyn<KIND>::ju_nz(m, q)) a += Ju[m * NU + q] * dU[q * P + k];
       }
       t[m * P + k] = a;
     }
@@ -871,9 +873,11 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
       for (int m = 0; m < NX; ++m) {
         T jd = T(0);
 #pragma unroll
-        for (int p = 0; p < NX; ++p) jd += Jx[m * NX + p] * dz[p];
+        for (int p = 0; p < NX; ++p)
+          if (Dyn<KIND>::jx_nz(m, p)) jd += Jx[m * NX + p] * dz[p];
 #pragma unroll
-        for (int q = 0; q < NU; ++q) jd += Ju[m * NU + q] * dz[NX + q];
+        for (int q = 0; q < NU; ++q)
+          if (Dyn<KIND>::ju_nz(m, q)) jd += Ju[m * NU + q] * dz[NX + q];
         sacc += (double)m_[m] * (double)jd + (double)fx[m] * (double)mp[m];
       }
     }
@@ -881,15 +885,18 @@ __global__ void k_kkt_post(const T* __restrict__ xu, const T* __restrict__ mu, c
     for (int a = 0; a < NV; ++a) {
       T acc = T(0);
 #pragma unroll
-      for (int b = 0; b < NV; ++b) acc -= H[a * NV + b] * dz[b];
+      for (int b = 0; b < NV; ++b)
+        if (Dyn<KIND>::h_nz(a, b)) acc -= H[a * NV + b] * dz[b];
       if (a >= NX) acc += (swk + hb[a - NX]) * dz[a];
       if (a < NX) {
         acc += dL[a * P + k];
 #pragma unroll
-        for (int m = 0; m < NX; ++m) acc -= Jx[m * NX + a] * (mp[m] + dss * m_[m]);
+        for (int m = 0; m < NX; ++m)
+          if (Dyn<KIND>::jx_nz(m, a)) acc -= Jx[m * NX + a] * (mp[m] + dss * m_[m]);
       } else {
 #pragma unroll
-        for (int m = 0; m < NX; ++m) acc -= Ju[m * NU + (a - NX)] * (mp[m] + dss * m_[m]);
+        for (int m = 0; m < NX; ++m)
+          if (Dyn<KIND>::ju_nz(m, a - NX)) acc -= Ju[m * NU + (a - NX)] * (mp[m] + dss * m_[m]);
       }
       if (a < NX && k == L - 1) {
         // compile-time indices into the parameter struct (a run-time index would copy it to
@@ -949,14 +956,16 @@ __global__ void k_border(const T* __restrict__ xu, const T* __restrict__ mu, con
     for (int p = 0; p < NX; ++p) {
       T g = T(0);
 #pragma unroll
-      for (int m = 0; m < NX; ++m) g -= Jx[m * NX + p] * m_[m];
+      for (int m = 0; m < NX; ++m)
+        if (Dyn<KIND>::jx_nz(m, p)) g -= Jx[m * NX + p] * m_[m];
       a[p * P + k] = g * inv_s;
     }
 #pragma unroll
     for (int q = 0; q < NU; ++q) {
       T g = T(0);
 #pragma unroll
-      for (int m = 0; m < NX; ++m) g -= Ju[m * NU + q] * m_[m];
+      for (int m = 0; m < NX; ++m)
+        if (Dyn<KIND>::ju_nz(m, q)) g -= Ju[m * NU + q] * m_[m];
       a[(NX + q) * P + k] = g * inv_s;
     }
 #pragma unroll
@@ -1072,7 +1081,8 @@ __global__ void k_pre_u(const T* __restrict__ xu, const T* __restrict__ w, T s, 
     for (int q = 0; q < NU; ++q) {
       T a = ru ? ru[q * P + k] : T(0);
 #pragma unroll
-      for (int m = 0; m < NX; ++m) a += s * Ju[m * NU + q] * b[m * P + k];
+      for (int m = 0; m < NX; ++m)
+        if (Dyn<KIND>::ju_nz(m, q)) a += s * Ju[m * NU + q] * b[m * P + k];
       y[q] = a * inv[q];
       yu[q * P + k] = y[q];
     }
@@ -1080,7 +1090,8 @@ __global__ void k_pre_u(const T* __restrict__ xu, const T* __restrict__ w, T s, 
     for (int m = 0; m < NX; ++m) {
       T a = T(0);
 #pragma unroll
-      for (int q = 0; q < NU; ++q) a += Ju[m * NU + q] * y[q];
+      for (int q = 0; q < NU; ++q)
+        if (Dyn<KIND>::ju_nz(m, q)) a += Ju[m * NU + q] * y[q];
       g[m * P + k] = gsign * a;
     }
   }
@@ -1194,7 +1205,8 @@ __global__ void k_resid_post(const double* __restrict__ z, const double* __restr
     for (int p = 0; p < NX; ++p) {
       double g = lam[p * P + k];
 #pragma unroll
-      for (int m = 0; m < NX; ++m) g -= Jx[m * NX + p] * mp[m];
+      for (int m = 0; m < NX; ++m)
+        if (Dyn<KIND>::jx_nz(m, p)) g -= Jx[m * NX + p] * mp[m];
       if (k == L - 1) {
 #pragma unroll
         for (int r = 0; r < NEM; ++r)
@@ -1230,7 +1242,8 @@ __global__ void k_resid_post(const double* __restrict__ z, const double* __restr
     for (int q = 0; q < NU; ++q) {
       double g = s * wk * cost_uu * u[q] + gb[q];
 #pragma unroll
-      for (int m = 0; m < NX; ++m) g -= Ju[m * NU + q] * mp[m];
+      for (int m = 0; m < NX; ++m)
+        if (Dyn<KIND>::ju_nz(m, q)) g -= Ju[m * NU + q] * mp[m];
       F[(NX + q) * P + k] = g;
       acc += g * g * iw;
     }

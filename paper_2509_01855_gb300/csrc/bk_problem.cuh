@@ -37,12 +37,26 @@ enum { SL_A = 0, SL_M1 = 1, SL_PRE = 5, SL_SUF = 6, NSLOT = 7 };
 // ---------------------------------------------------------------------------------------------
 template <int KIND> struct Dyn;
 
+// Structural nonzeros of J_x (n_x x n_x), J_u (n_x x n_u) and the Lagrangian Hessian
+// H ((n_x + n_u)^2) of a kind: the node-local kernels skip the products with structural zeros
+// (the indices are compile-time constants after unrolling, so the skipped terms and their loads
+// vanish). Kinds without a pattern take the dense one.
+struct DenseNZ {
+  __host__ __device__ static constexpr bool jx_nz(int, int) { return true; }
+  __host__ __device__ static constexpr bool ju_nz(int, int) { return true; }
+  __host__ __device__ static constexpr bool h_nz(int, int) { return true; }
+};
+
 __device__ inline void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ inline void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
 
 // Minimum-energy double integrator: x = (p, v), x' = (v, u), F = u^2 / 2.
 template <> struct Dyn<BK_DBL_INT> {
   static constexpr int nx = 2, nu = 1;
+  // J_x = [[0, 1], [0, 0]], J_u = [0; 1], H = 0 (f is linear)
+  __host__ __device__ static constexpr bool jx_nz(int r, int c) { return r == 0 && c == 1; }
+  __host__ __device__ static constexpr bool ju_nz(int r, int q) { return r == 1 && q == 0; }
+  __host__ __device__ static constexpr bool h_nz(int, int) { return false; }
   // control block of the KKT preconditioner at a node: s w_k times the running cost's curvature
   static constexpr bool huu_needs_mu = false;
   template <typename T> __device__ static T pre_huu(const T* mu, T swk, T) { return swk; }
@@ -64,6 +78,16 @@ template <> struct Dyn<BK_DBL_INT> {
 // x = (r, theta, v_r, v_theta), u = (u_r, u_theta).
 template <> struct Dyn<BK_ORBIT> {
   static constexpr int nx = 4, nu = 2;
+  // the entries jac and hess set below (theta enters no right-hand side; u enters linearly)
+  __host__ __device__ static constexpr bool jx_nz(int r, int c) {
+    return (r == 0 && c == 2) || (r == 1 && (c == 0 || c == 3)) || (r == 2 && (c == 0 || c == 3)) ||
+           (r == 3 && (c == 0 || c == 2 || c == 3));
+  }
+  __host__ __device__ static constexpr bool ju_nz(int r, int q) { return (r == 2 && q == 0) || (r == 3 && q == 1); }
+  __host__ __device__ static constexpr bool h_nz(int a, int b) {
+    return (a == 0 && (b == 0 || b == 2 || b == 3)) || (b == 0 && (a == 2 || a == 3)) || (a == 2 && b == 3) ||
+           (a == 3 && (b == 2 || b == 3));
+  }
   // control block of the KKT preconditioner at a node: s w_k times the running cost's curvature
   static constexpr bool huu_needs_mu = false;
   template <typename T> __device__ static T pre_huu(const T* mu, T swk, T) { return swk; }
@@ -112,7 +136,7 @@ template <> struct Dyn<BK_ORBIT> {
 };
 
 // Scalar bilinear x' = u x (no cost): linearised at (X, U) the state Jacobian is diag(U).
-template <> struct Dyn<BK_BILINEAR> {
+template <> struct Dyn<BK_BILINEAR> : DenseNZ {
   static constexpr int nx = 1, nu = 1;
   // control block of the KKT preconditioner at a node: s w_k times the running cost's curvature
   static constexpr bool huu_needs_mu = false;
@@ -129,7 +153,7 @@ template <> struct Dyn<BK_BILINEAR> {
 
 // Minimum-time orbit transfer of Eq. ot: the same state, fixed-magnitude thrust a (sin u, cos u)
 // steered by the angle u (pa = a), cost T = t_f - t_0 with the final time free.
-template <> struct Dyn<BK_ORBIT_MT> {
+template <> struct Dyn<BK_ORBIT_MT> : DenseNZ {
   static constexpr int nx = 4, nu = 1;
   template <typename T> __device__ static void f(const T* x, const T* u, T* fx, T a) {
     const T r = x[0], vr = x[2], vt = x[3];
