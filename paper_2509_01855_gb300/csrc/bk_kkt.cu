@@ -162,15 +162,21 @@ __device__ __forceinline__ int64_t il32(int64_t i, int c, int NC) { return (((i 
 
 // Deviation of a product: (I + A)(I + B) = I + C with C = A + B + A B (n_x x n_x, row-major),
 // each entry one FMA chain started from A + B (n_x^2 (n_x + 1) operations).
+// Columns in ZeroCols<NX> are zero in A and B, hence in C, and are skipped.
 template <int NX, typename Tm = double>
 __device__ __forceinline__ void dev_mul(const Tm* A, const Tm* B, Tm* C) {
 #pragma unroll
   for (int r = 0; r < NX; ++r)
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
+      if (zcol<NX>(c)) {
+        C[r * NX + c] = Tm(0);
+        continue;
+      }
       Tm a = A[r * NX + c] + B[r * NX + c];
 #pragma unroll
-      for (int q = 0; q < NX; ++q) a = fma(A[r * NX + q], B[q * NX + c], a);
+      for (int q = 0; q < NX; ++q)
+        if (!zcol<NX>(q)) a = fma(A[r * NX + q], B[q * NX + c], a);
       C[r * NX + c] = a;
     }
 }
@@ -185,19 +191,24 @@ __global__ void k_lin_seg(const T* __restrict__ Dn, int64_t L, int nseg, T* __re
   T A[NX * NX], D[NX * NX], R[NX * NX];
   const int64_t k0 = (int64_t)seg * SEG;
 #pragma unroll
-  for (int c = 0; c < NX * NX; ++c) A[c] = T(2) * Dn[il_index<Seg<T>::v>(k0, c, NX * NX)];
+  for (int c = 0; c < NX * NX; ++c) A[c] = zcol<NX>(c % NX) ? T(0) : T(2) * Dn[il_index<Seg<T>::v>(k0, c, NX * NX)];
   for (int i = 1; i < SEG; ++i) {
     const int64_t k = k0 + i;
     if (k >= L) break;
 #pragma unroll
-    for (int c = 0; c < NX * NX; ++c) D[c] = Dn[il_index<Seg<T>::v>(k, c, NX * NX)];
+    for (int c = 0; c < NX * NX; ++c) D[c] = zcol<NX>(c % NX) ? T(0) : Dn[il_index<Seg<T>::v>(k, c, NX * NX)];
 #pragma unroll
     for (int r = 0; r < NX; ++r)
 #pragma unroll
       for (int c = 0; c < NX; ++c) {
+        if (zcol<NX>(c)) {
+          R[r * NX + c] = T(0);
+          continue;
+        }
         T a = D[r * NX + c];
 #pragma unroll
-        for (int q = 0; q < NX; ++q) a = fma(D[r * NX + q], A[q * NX + c], a);
+        for (int q = 0; q < NX; ++q)
+          if (!zcol<NX>(q)) a = fma(D[r * NX + q], A[q * NX + c], a);
         R[r * NX + c] = fma(T(2), a, A[r * NX + c]);
       }
 #pragma unroll
@@ -319,9 +330,9 @@ template <typename T> struct Levels {
 template <typename T, int NX, int DIR>
 __device__ __forceinline__ void node_step(const T* __restrict__ Dn, int64_t k, const T* yin, const T* gin, T h,
                                           T* st, T* out, bool want_out) {
-  T Dm[NX * NX];
+  T Dm[NX * NX];   // entries in a zero column (ZeroCols) are neither loaded nor used
 #pragma unroll
-  for (int c = 0; c < NX * NX; ++c) Dm[c] = Dn[il_index<Seg<T>::v>(k, c, NX * NX)];
+  for (int c = 0; c < NX * NX; ++c) Dm[c] = zcol<NX>(c % NX) ? T(0) : Dn[il_index<Seg<T>::v>(k, c, NX * NX)];
   if (DIR == 0) {
     T v[NX], dv[NX];
 #pragma unroll
@@ -330,7 +341,8 @@ __device__ __forceinline__ void node_step(const T* __restrict__ Dn, int64_t k, c
     for (int r = 0; r < NX; ++r) {
       T a = T(0);
 #pragma unroll
-      for (int c = 0; c < NX; ++c) a += Dm[r * NX + c] * v[c];
+      for (int c = 0; c < NX; ++c)
+        if (!zcol<NX>(c)) a += Dm[r * NX + c] * v[c];
       dv[r] = a;
     }
     if (want_out) {
@@ -347,7 +359,8 @@ __device__ __forceinline__ void node_step(const T* __restrict__ Dn, int64_t k, c
     for (int r = 0; r < NX; ++r) {
       T a = T(0);
 #pragma unroll
-      for (int c = 0; c < NX; ++c) a += Dm[c * NX + r] * q[c];
+      for (int c = 0; c < NX; ++c)
+        if (!zcol<NX>(r)) a += Dm[c * NX + r] * q[c];
       y[r] = yin[r] + a;
     }
     if (want_out) {
@@ -379,12 +392,13 @@ __device__ __forceinline__ void warp_scan(const T* __restrict__ m, int64_t slot,
       const T* M = m + k * slot;
       T Mv[NC];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) Mv[c] = M[il32(item, c, NC)];
+      for (int c = 0; c < NC; ++c) Mv[c] = zcol<NX>(c % NX) ? T(0) : M[il32(item, c, NC)];
 #pragma unroll
       for (int r = 0; r < NX; ++r) {
         T a = T(0);   // (I + D) pe = pe + D pe
 #pragma unroll
-        for (int c = 0; c < NX; ++c) a += (DIR == 0 ? Mv[r * NX + c] : Mv[c * NX + r]) * pe[c];
+        for (int c = 0; c < NX; ++c)
+          if (!zcol<NX>(DIR == 0 ? c : r)) a += (DIR == 0 ? Mv[r * NX + c] : Mv[c * NX + r]) * pe[c];
         e[r] = e[r] + (pe[r] + a);
       }
     }
@@ -567,12 +581,13 @@ __device__ __forceinline__ void sw_down0_warp(int g, SweepTiles<T, NX>& tl, cons
     const int64_t ia = DIR == 0 ? i - 1 : i + 1;
     T Mv[NC], ns[NX];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) Mv[c] = Mt[il32(i, c, NC)];
+    for (int c = 0; c < NC; ++c) Mv[c] = zcol<NX>(c % NX) ? T(0) : Mt[il32(i, c, NC)];
 #pragma unroll
     for (int r = 0; r < NX; ++r) {
       T a = T(0);   // (I + D) S = S + D S
 #pragma unroll
-      for (int c = 0; c < NX; ++c) a += (DIR == 0 ? Mv[r * NX + c] : Mv[c * NX + r]) * S[c];
+      for (int c = 0; c < NX; ++c)
+        if (!zcol<NX>(DIR == 0 ? c : r)) a += (DIR == 0 ? Mv[r * NX + c] : Mv[c * NX + r]) * S[c];
       ns[r] = el[il32(ia, r, NX)] + (S[r] + a);
     }
 #pragma unroll

@@ -154,6 +154,8 @@ template <> struct Dyn<BK_BILINEAR> : DenseNZ {
 // Minimum-time orbit transfer of Eq. ot: the same state, fixed-magnitude thrust a (sin u, cos u)
 // steered by the angle u (pa = a), cost T = t_f - t_0 with the final time free.
 template <> struct Dyn<BK_ORBIT_MT> : DenseNZ {
+  // the state Jacobian of BK_ORBIT (theta enters no right-hand side); J_u and H dense
+  __host__ __device__ static constexpr bool jx_nz(int r, int c) { return Dyn<BK_ORBIT>::jx_nz(r, c); }
   static constexpr int nx = 4, nu = 1;
   template <typename T> __device__ static void f(const T* x, const T* u, T* fx, T a) {
     const T r = x[0], vr = x[2], vt = x[3];
@@ -190,6 +192,26 @@ template <> struct Dyn<BK_ORBIT_MT> : DenseNZ {
     return a * sqrt(mu[2] * mu[2] + mu[3] * mu[3]) + T(1e-3) * swk;
   }
 };
+
+// Columns of J_x that are zero in every compiled kind with n_x = NX (bit c: column c). A zero
+// column of h J stays exactly zero in the node deviation D = (I - h J)^{-1} h J (its right-hand
+// side column is zero) and in every deviation of a product of (I + 2 D) maps, so the sweeps and
+// the level products skip those entries and their loads without changing any result. Orbit kinds
+// (n_x = 4): theta enters no right-hand side (column 1); double integrator (n_x = 2): the
+// position enters none (column 0).
+template <int NX> struct ZeroCols { static constexpr int mask = NX == 4 ? 0x2 : (NX == 2 ? 0x1 : 0); };
+template <int NX> __host__ __device__ constexpr bool zcol(int c) { return ((ZeroCols<NX>::mask >> c) & 1) != 0; }
+
+template <int KIND> constexpr bool zero_cols_hold() {
+  constexpr int NX = Dyn<KIND>::nx;
+  for (int c = 0; c < NX; ++c)
+    for (int r = 0; r < NX; ++r)
+      if (zcol<NX>(c) && Dyn<KIND>::jx_nz(r, c)) return false;
+  return true;
+}
+static_assert(zero_cols_hold<BK_DBL_INT>() && zero_cols_hold<BK_ORBIT>() && zero_cols_hold<BK_BILINEAR>() &&
+                  zero_cols_hold<BK_ORBIT_MT>(),
+              "a kind's state Jacobian has an entry in a column ZeroCols skips");
 
 // ---------------------------------------------------------------------------------------------
 // Problem
