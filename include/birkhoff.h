@@ -4,7 +4,9 @@
  * Method: arXiv 2509.01855, "A Million-Point Fast Trajectory Optimization Solver".
  * The library computes, on one GPU, the matrix-free Birkhoff products B v and B^T v on a
  * Chebyshev-Gauss-Lobatto (CGL) grid, the KKT operator of a Newton step built from them, the
- * Birkhoff preconditioner, a right-preconditioned Krylov solve and the Newton driver.
+ * Birkhoff preconditioner, a right-preconditioned Krylov solve and the Newton driver, which
+ * also handles bounds on the controls and one-sided bounds on terminal conditions (the simplest
+ * inequalities of the paper's general problem (P)) by logarithmic barriers.
  *
  * Conventions shared by every call
  * --------------------------------
