@@ -416,8 +416,9 @@ static bk_status newton_impl(Problem* pr, double* z, const bk_newton_opts& o, bk
     if (it >= o.max_iter) break;
     // Inner tolerance: fixed if the caller set one, else a forcing term that tightens with the
     // outer residual, rtol_k = 0.1 (phi_k / phi_0)^2 clamped to [floor, 1e-2] (Eisenstat and
-    // Walker's choice 2 with gamma = 0.1, alpha = 2): loose early steps, tight final ones,
-    // quadratic outer convergence kept. Floor 1e-12 in FP64, 1e-4 in FP32.
+    // Walker's choice 2 with gamma = 0.1, alpha = 2; phi_0 the merit at the start of the solve,
+    // or of the barrier stage under bounds): loose early steps, tight final ones, quadratic outer
+    // convergence kept. Floor 1e-12 in FP64, 1e-4 in FP32.
     if (o.krylov_rtol > 0) {
       ko.rtol = o.krylov_rtol;
     } else if (ft && !o.weighted_inner) {
