@@ -226,6 +226,7 @@ class MatFreeKKT:
             huu = np.tile(p.a * np.hypot(mu[2], mu[3]) + 1e-3 * sw, (nu_, 1))
         else:
             huu = np.tile(sw * p.cost_hess_uu(), (nu_, 1))
+        huu = huu + getattr(self, "_huu_extra", 0.0)   # a barrier's diagonal (matfree_barrier.py)
         pc = dict(vec=vec, s=s, sw=sw, Jx=Jx, Ju=Ju, huu=huu)
         self._pc = pc
         # Schur columns: for each terminal row r, E^T e_r -> l_r, u_r, x_r

@@ -10,6 +10,8 @@
   the states, integrals of the controls, to 1e-4.
 - Orbit transfer with the endpoint bound r(t_f) >= 1.55 at N = 2^10, 2^14, 2^20: the oracle's
   Newton count and r(t_f) at N = 64.
+- Residual, KKT product and preconditioner with control and endpoint bounds at N = 2^12 and
+  2^14 against the matrix-free barrier oracle on the same grid.
 - Orbit transfer with bounded thrust (the bench's bounded workload) at N = 2^20: the primal and
   the primal-dual form, two different Newton iterations, reach the same barrier solution; the
   controls stay strictly inside the bounds and reach them; the Newton counts are those at
@@ -121,3 +123,45 @@ def test_endpoint_bounded_orbit_mesh_independent():
         r = prob.split(z)[0][0, -1].item()
         assert 1.55 < r and abs(r - r_ref) < 1e-9, (lg, r, r_ref)
         prob.close()
+
+
+@pytest.mark.parametrize("lg", [12, 14])
+def test_bounded_operators_match_matfree_oracle(lg):
+    """Residual, KKT product and preconditioner with control bounds and endpoint bounds at
+    N = 2^12 and 2^14 (multi-CTA transforms, three sweep levels) against the matrix-free barrier
+    oracle on the same grid (oracle/matfree_barrier.py, pinned to the dense one)."""
+    from oracle import problems as op
+    from oracle.matfree_barrier import MatFreeBarrierKKT
+    from tests.helpers import from_packed, rel, to_packed
+    api, lib = _api()
+    N = 1 << lg
+    inf = float("inf")
+    lo, hi, eb, mu = [-0.05, -inf], [0.05, 0.04], {0: (1.2, inf), 2: (-inf, 0.9)}, 1e-5
+    oprob = op.Problem(op.ORBIT, 0.0, 20.0, (0.01, 1.5))
+    M = MatFreeBarrierKKT(oprob, N, lo, hi, ebounds=eb)
+    M.mu = mu
+    g = synth.rng("bounds-matfree", lg)
+    X, U = synth.orbit_guess(M.t, 1.5, 20.0)
+    X = X + 0.01 * g.standard_normal(X.shape)
+    U = U + 0.005 * g.standard_normal(U.shape)
+    vec = M.pack(X, U, 0.1 * g.standard_normal((4, M.L)), 0.1 * g.standard_normal(3))
+    vec = M.interior(vec, margin=0.05)
+    prob = api.Problem(lib.BK_ORBIT, N, torch.float64, 0.0, 20.0, (0.01, 1.5))
+    prob.set_control_bounds(lo, hi)
+    prob.set_terminal_bounds([1.2, -inf, -inf], [inf, inf, 0.9])
+    prob.set_barrier(mu, mu)
+    z = from_packed(prob, vec)
+    F = torch.zeros_like(z)
+    prob.residual(z, F)
+    Fo = M.residual(vec)
+    assert rel(to_packed(prob, F), Fo) < 1e-12
+    prob.linearize(z)
+    d = g.standard_normal(M.n)
+    x = from_packed(prob, d)
+    out = torch.zeros_like(x)
+    api.kkt_apply(prob, lib.BK_OP_KKT, x, out)
+    assert rel(to_packed(prob, out), M.apply(vec, d)) < 1e-12
+    M.linearize_precond(vec)
+    api.precond_apply(prob, lib.BK_OP_KKT, x, out)
+    assert rel(to_packed(prob, out), M.precond_solve(d)) < 1e-10
+    prob.close()
